@@ -1,0 +1,265 @@
+/*
+ * adjamr.h -- C ABI of the GB300 (sm_103a) implementation of the data-parallel
+ * hot path of adjoint-guided block-structured AMR for linear hyperbolic
+ * waves (Davis & LeVeque, "Adjoint methods for guiding adaptive mesh
+ * refinement in wave propagation problems").
+ *
+ * Conventions for every call:
+ *  - returns adjamr_status (0 = OK); adjamr_last_error(ctx) gives text;
+ *    no C++ exception crosses this ABI;
+ *  - input pointers are borrowed for the duration of the call only (the
+ *    library copies what it keeps); output buffers are caller-allocated;
+ *  - the context owns all device memory it allocates; adjoint snapshot sets
+ *    are reference-counted handles that several contexts may share;
+ *  - work is stream-ordered on the context's CUDA stream (a cudaStream_t
+ *    passed as void*, NULL = the legacy default stream); calls that return
+ *    host data synchronise that stream, the others do not;
+ *  - one context must not be used by two host threads at the same time.
+ *
+ * Fields are FP64.  State layout seen through this ABI: per patch, field-
+ * major, row-major interior cells: q[f][j][i] (1D: q[f][i]).
+ * Field order: acoustics (p, u[, v]); shallow water (eta, mu, gamma).
+ */
+#ifndef ADJAMR_H
+#define ADJAMR_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ADJAMR_MAX_LEVELS 8
+
+typedef enum adjamr_status {
+    ADJAMR_OK = 0,
+    ADJAMR_EINVAL = 1,   /* invalid argument */
+    ADJAMR_ENOMEM = 2,   /* device or host allocation failed */
+    ADJAMR_EBUDGET = 3,  /* request does not fit the memory budget */
+    ADJAMR_ECFL = 4,     /* Courant number exceeded cfl_max during the call */
+    ADJAMR_ETIMEOUT = 5, /* a bounded device wait gave up */
+    ADJAMR_ECUDA = 6,    /* a CUDA runtime call failed */
+    ADJAMR_ESTATE = 7,   /* call not valid in the current state */
+    ADJAMR_ENEST = 8     /* hierarchy not properly nested (internal invariant) */
+} adjamr_status;
+
+/* Systems (Sec. 2 Eq. eq:qtAqx; Sec. 5.1-5.3 matrices; adjoints Sec. 2 Eq.
+ * adjoint1, time-reversed as in Sec. 4). */
+enum {
+    ADJAMR_ACOUSTICS = 0,          /* q_t + A q_x (+ B q_y) = 0, wave form */
+    ADJAMR_ACOUSTICS_ADJOINT = 1,  /* q~_t - (A^T q~)_x (- (B^T q~)_y) = 0, f-wave */
+    ADJAMR_SW = 2,                 /* linearised shallow water, f-wave with bathymetry */
+    ADJAMR_SW_ADJOINT = 3          /* its adjoint, f-wave */
+};
+
+/* Physical boundary conditions (Sec. 5.1-5.2 walls; Sec. 5.2.3 outflow). */
+enum { ADJAMR_BC_EXTRAP = 0, ADJAMR_BC_WALL = 1, ADJAMR_BC_PERIODIC = 2 };
+
+/* Time combination of adjoint snapshots in the flag test (Sec. 4 "both
+ * taken into account"): maximum over the bracketing snapshots, or q^
+ * linear in time between snapshots. */
+enum { ADJAMR_FLAG_BRACKET_MAX = 0, ADJAMR_FLAG_LINEAR = 1 };
+
+enum { ADJAMR_MEDIUM_LAYERED = 1, ADJAMR_MEDIUM_DENSE = 2 };
+
+/* Step launch modes: one launch per level over the whole tile work-list
+ * (the default), a persistent grid of (#SMs x occupancy) CTAs over the
+ * work-list, or one launch per patch (the comparison baseline). */
+enum { ADJAMR_LAUNCH_WORKLIST = 0, ADJAMR_LAUNCH_PERSISTENT = 1, ADJAMR_LAUNCH_PER_PATCH = 2 };
+
+/* Initial condition callback: fills q_out[f*n + k] for the n cell centres
+ * (xc[k], yc[k]) of level `level` (yc = 0 in 1D).  Called on the host by
+ * adjamr_init_grid_hierarchy and by an initial regrid. */
+typedef void (*adjamr_qinit_fn)(int level, int n, const double *xc, const double *yc, double *q_out,
+                                void *user);
+
+/* Run parameters (Sec. 3: levels, ratios, regridding; Sec. 4/5: flagging
+ * tolerance and time range of interest [ts, tf]). */
+typedef struct adjamr_params {
+    int dim;                     /* 1 or 2 */
+    int eqn;                     /* ADJAMR_ACOUSTICS .. ADJAMR_SW_ADJOINT */
+    double lo[2], hi[2];         /* domain [lo, hi] (y ignored in 1D) */
+    int n0[2];                   /* level-0 cells per direction */
+    int nlevels;                 /* 1 .. ADJAMR_MAX_LEVELS */
+    int ratio[ADJAMR_MAX_LEVELS];/* ratio[l]: refinement from level l to l+1, space and time */
+    int bc[4];                   /* x-lo, x-hi, y-lo, y-hi */
+    double cfl;                  /* desired Courant number: sets dt_0 */
+    double cfl_max;              /* ADJAMR_ECFL if exceeded */
+    double cmax;                 /* maximum wave speed of the medium */
+    double dt0;                  /* > 0: use this level-0 step instead of the CFL rule */
+    double t0, tf, ts;           /* start, final time, start of the time range of interest */
+    double tol;                  /* flag tolerance: flag iff max |q^ . q| > tol */
+    int regrid_interval;         /* regrid finer levels every k steps of a level (0 = never) */
+    int buffer;                  /* flag buffer width (cells) */
+    double cluster_eff;          /* Berger-Rigoutsos efficiency cut-off */
+    int min_patch, max_patch;    /* patch edge range on refined levels (cells of that level) */
+    int max_patch0;              /* level-0 tile edge */
+    int flag_mode;               /* ADJAMR_FLAG_* */
+    adjamr_qinit_fn qinit;       /* may be NULL (state starts at zero) */
+    void *qinit_user;
+    void *stream;                /* cudaStream_t or NULL */
+    int tile_x, tile_y;          /* step-kernel tile (0 = default 32 x 8) */
+    int launch_mode;             /* ADJAMR_LAUNCH_* */
+} adjamr_params;
+
+/* Medium (Sec. 5.1/5.2 piecewise-constant layers; Sec. 5.3 bathymetry).
+ * LAYERED (acoustics): layer k holds cells whose centre coordinate along
+ *   `axis` (0 = x, 1 = y) satisfies iface[k-1] <= c < iface[k]; f0 = rho,
+ *   f1 = K per layer.
+ * DENSE: dense[l] points to [nmed][M_l][N_l] doubles covering level l's whole
+ *   index space (acoustics nmed = 2: rho, K; shallow water nmed = 1: hbar).
+ * Ghost cells outside the domain take the medium of the boundary-mapped
+ * cell. */
+typedef struct adjamr_medium {
+    int kind;
+    int axis, nlayers;
+    const double *iface, *f0, *f1;
+    const double *const *dense;
+    int ndense;
+} adjamr_medium;
+
+/* phi = weight * indicator([x0,x1] x [y0,y1]) on field 0 (Sec. 2 Eq.
+ * eq:J_general; Sec. 5.1 Eq. eq:phi_1d / Sec. 5.2 Eq. eq:phi_2d). */
+typedef struct adjamr_target { double x0, x1, y0, y1, weight; } adjamr_target;
+
+typedef struct adjamr_patch { int level, ilo, jlo, nx, ny; } adjamr_patch;
+
+/* Counters since creation (cell-updates count interior cells advanced one
+ * step on their level). */
+typedef struct adjamr_stats {
+    long long cell_updates;
+    long long adjoint_cell_updates;
+    long long kernel_launches;
+    long long regrids;
+    double cfl_max_seen;
+    double step_kernel_ms;       /* CUDA-event time of step kernels, if timing enabled */
+    long long step_kernel_launches;
+} adjamr_stats;
+
+typedef struct adjamr_ctx adjamr_ctx;
+typedef struct adjamr_adjoint adjamr_adjoint;
+
+/* Create a hierarchy: level 0 tiles the domain with near-equal patches of at
+ * most max_patch0 cells per side; its state is sampled from p->qinit at cell
+ * centres.  Finer levels are created by adjamr_regrid.  Errors: EINVAL for
+ * inconsistent parameters, ENOMEM, ECUDA. */
+adjamr_status adjamr_init_grid_hierarchy(const adjamr_params *p, adjamr_ctx **out);
+
+/* Set the medium; copies the layer table or the dense per-level arrays to
+ * the device and fills the per-cell coefficients of existing patches
+ * (impedance, sound speed, edge coefficients).  Must precede stepping. */
+adjamr_status adjamr_set_medium(adjamr_ctx *ctx, const adjamr_medium *m);
+
+/* Adjoint snapshots (Sec. 4): snaps[nsnap][m][ay][ax] in FORWARD time order,
+ * snapshot n at t_n = t0 + n (tf - t0)/(nsnap - 1), on a uniform ax x ay grid
+ * covering the domain; wet[ay][ax] (NULL = all wet).  snaps_on_device != 0:
+ * `snaps` is a device pointer (copied device-to-device).  The returned
+ * handle holds a device copy and one reference; it is attached to ctx. */
+adjamr_status adjamr_load_adjoint_snapshots(adjamr_ctx *ctx, const double *snaps, int nsnap, int ax, int ay,
+                                            const unsigned char *wet, int snaps_on_device,
+                                            adjamr_adjoint **out);
+
+/* Solve the adjoint on the fixed grid described by ap (nlevels = 1, eqn =
+ * adjoint system) from q~(x, 0) = phi (host [m][ay][ax]) and store nsnap
+ * snapshots on the device (Sec. 4: q^(x, tf - t_n) = q~(x, t_n)).  The step
+ * is dt = dT/ceil(dT/dt_cfl), dT = (tf - t0)/(nsnap - 1).  The handle is
+ * attached to ctx (ctx may be NULL: then it is only returned). */
+adjamr_status adjamr_solve_adjoint(adjamr_ctx *ctx, const adjamr_params *ap, const adjamr_medium *am,
+                                   const double *phi, int nsnap, adjamr_adjoint **out);
+
+/* Attach a (shared) snapshot set to ctx; takes a reference. */
+adjamr_status adjamr_set_adjoint(adjamr_ctx *ctx, adjamr_adjoint *adj);
+/* Copy snapshots to the host: dst[nsnap][m][ay][ax]. */
+adjamr_status adjamr_adjoint_read(adjamr_adjoint *adj, double *dst, size_t cap);
+/* Drop one reference; frees the device copy with the last one. */
+void adjamr_adjoint_release(adjamr_adjoint *adj);
+
+/* Rebuild levels base_level+1 .. nlevels-1 top-down (Sec. 3):
+ * adjoint flags on level l, buffered, properly nested, clustered by
+ * Berger-Rigoutsos, split to max_patch, refined; new cells copied from old
+ * patches of the same level or interpolated from level l (init != 0: sampled
+ * from qinit).  Synchronises the stream (flags are clustered on the host). */
+adjamr_status adjamr_regrid(adjamr_ctx *ctx, int base_level, int init);
+
+/* Advance the hierarchy by nsteps level-0 steps (Berger-Oliger recursion,
+ * Sec. 3: coarse step, r fine steps with time-interpolated ghost cells,
+ * average down; regrid every regrid_interval steps).  level must be 0.
+ * Returns ECFL if the Courant number exceeded cfl_max. */
+adjamr_status adjamr_advance_level(adjamr_ctx *ctx, int level, int nsteps);
+
+/* Adjoint flags of the interior cells of `level` at its current time (Sec.
+ * 4, Sec. 5.1.2): flags_out[k] in patch order, row-major per patch (may be
+ * NULL); *nflag = number flagged.  Synchronises. */
+adjamr_status adjamr_flag_cells(adjamr_ctx *ctx, int level, double tol, unsigned char *flags_out,
+                                long long *nflag);
+
+/* J = sum over the composite grid of weight * q0 * |cell ∩ box| (Sec. 2 Eq.
+ * eq:J_general), fixed pairwise summation order.  Synchronises. */
+adjamr_status adjamr_integrate_functional(adjamr_ctx *ctx, const adjamr_target *phi, double *J_out);
+
+/* Patch layout of a level, sorted by (jlo, ilo).  *n = number of patches
+ * (written even if cap is too small; then EINVAL). */
+adjamr_status adjamr_get_patches(adjamr_ctx *ctx, int level, adjamr_patch *out, int cap, int *n);
+
+/* Interior state of a level, patch by patch (q[f][j][i] per patch).
+ * cap in doubles.  Synchronises. */
+adjamr_status adjamr_read_level(adjamr_ctx *ctx, int level, double *dst, size_t cap);
+/* Overwrite the interior state of a level (same layout). */
+adjamr_status adjamr_write_level(adjamr_ctx *ctx, int level, const double *src, size_t count);
+
+/* Fill the ghost cells of `level` for its current time (as a step would). */
+adjamr_status adjamr_fill_ghosts(adjamr_ctx *ctx, int level);
+
+/* Ghosted storage of patch k of `level`: q[m][sy][sx] with sx = nx + 4,
+ * sy = ny + 4 (1D: 1); med[nmed][sy][sx] = primary medium (rho, K | hbar). */
+adjamr_status adjamr_read_patch_ghosted(adjamr_ctx *ctx, int level, int k, double *q, double *med);
+
+/* Step every patch of `level` once, without recursion, regrid or ghost fill
+ * (for sampled parity checks). */
+adjamr_status adjamr_step_level_only(adjamr_ctx *ctx, int level);
+
+adjamr_status adjamr_get_stats(adjamr_ctx *ctx, adjamr_stats *out);
+/* Enable/disable CUDA-event timing of step kernels (adds events only). */
+adjamr_status adjamr_set_timing(adjamr_ctx *ctx, int enable);
+/* Level-0 step and number of level-0 steps to reach tf. */
+adjamr_status adjamr_time_info(adjamr_ctx *ctx, double *dt0, int *nsteps_to_tf);
+const char *adjamr_last_error(adjamr_ctx *ctx);
+void adjamr_destroy(adjamr_ctx *ctx);
+
+/* Measurement utility (no counterpart in the paper): FP64 instruction
+ * throughput of this GPU, kind 0 = DFMA (2 flops), 1 = DADD, 2 = DMUL, from
+ * 8 independent chains per thread over 8 CTAs of 256 threads per SM,
+ * `iters` iterations, timed with CUDA events on the legacy stream.  Writes
+ * flop/s and the timed kernel's milliseconds. */
+adjamr_status adjamr_fp64_peak(int kind, int iters, double *flops_per_s, double *ms);
+
+/* ------------------------------------------------------------------ */
+/* Batched independent patches (uneven sizes, mixed levels): every patch is */
+/* its own domain with extrapolation ghosts; one step advances all of them  */
+/* with their own dt.  Used for the fused-vs-per-patch comparison.          */
+/* ------------------------------------------------------------------ */
+typedef struct adjamr_batch adjamr_batch;
+
+/* npatch patches, 2D acoustics: patch k covers [x0[k], x1[k]] x [y0[k], y1[k]]
+ * with nx[k] x ny[k] cells (dx = (x1 - x0)/nx as on a level) and steps with
+ * dt[k]; medium_id[k] indexes `media` (LAYERED only); q0 = interiors
+ * concatenated in patch order (q[3][ny][nx] each). */
+adjamr_status adjamr_batch_create(int npatch, const int *nx, const int *ny, const double *x0, const double *y0,
+                                  const double *x1, const double *y1, const double *dt, const int *medium_id,
+                                  const adjamr_medium *media, int nmedia, const double *q0, void *stream,
+                                  adjamr_batch **out);
+/* Order of the tile work-list: patch order given here (a permutation). */
+adjamr_status adjamr_batch_set_order(adjamr_batch *b, const int *order);
+/* Advance all patches nsteps steps with the given launch mode and tile. */
+adjamr_status adjamr_batch_step(adjamr_batch *b, int nsteps, int launch_mode, int tile_x, int tile_y);
+/* Capture one step (ghost fill + fused step) in a CUDA graph and replay it
+ * nsteps times. */
+adjamr_status adjamr_batch_step_graph(adjamr_batch *b, int nsteps, int launch_mode, int tile_x, int tile_y);
+adjamr_status adjamr_batch_read(adjamr_batch *b, double *dst, size_t cap);
+adjamr_status adjamr_batch_cells(adjamr_batch *b, long long *cells);
+void adjamr_batch_destroy(adjamr_batch *b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ADJAMR_H */

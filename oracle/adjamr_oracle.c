@@ -99,6 +99,7 @@ typedef struct {
     int nsnap, an[2];
     double *snaps;
     unsigned char *wet;
+    long long cell_updates;
     char err[256];
 } OHier;
 
@@ -872,6 +873,7 @@ static double step_level_patches(OHier *h, int l)
         double *qo = xcalloc((size_t)h->m * p->nx * p->ny, sizeof(double));
         double c = step_patch(h->P.dim, h->P.eqn, p->nx, p->ny, p->q[cur], p->med, L->dt, L->dx, L->dy, qo);
         cfl = fmax(cfl, c);
+        h->cell_updates += (long long)p->nx * p->ny;
         for (int f = 0; f < h->m; f++)
             for (int j = 0; j < p->ny; j++)
                 for (int i = 0; i < p->nx; i++)
@@ -1375,6 +1377,7 @@ int orc_get_patches(void *hv, int level, int *boxes /* [np][4]: ilo, jlo, nx, ny
 }
 
 double orc_level_dt(void *hv, int level) { return ((OHier *)hv)->L[level].dt; }
+long long orc_cell_updates(void *hv) { return ((OHier *)hv)->cell_updates; }
 long orc_level_nstep(void *hv, int level) { return ((OHier *)hv)->L[level].nstep; }
 const char *orc_error(void *hv) { return ((OHier *)hv)->err; }
 

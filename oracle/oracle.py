@@ -73,6 +73,8 @@ def lib():
             L.orc_get_patches.argtypes = [vp, i, P(ctypes.c_int)]
             L.orc_level_dt.restype = d
             L.orc_level_dt.argtypes = [vp, i]
+            L.orc_cell_updates.restype = ctypes.c_longlong
+            L.orc_cell_updates.argtypes = [vp]
             L.orc_level_nstep.restype = ctypes.c_long
             L.orc_level_nstep.argtypes = [vp, i]
             L.orc_error.restype = ctypes.c_char_p
@@ -194,6 +196,9 @@ class OracleHierarchy:
     def nsteps_total(self) -> int:
         dt = lib().orc_level_dt(self.h, 0)
         return int(round((self.P.tf - self.P.t0) / dt))
+
+    def cell_updates(self) -> int:
+        return int(lib().orc_cell_updates(self.h))
 
     def level_dt(self, level: int) -> float:
         return lib().orc_level_dt(self.h, level)

@@ -1,0 +1,1577 @@
+// Host side of libadjamr: the AMR hierarchy on one GB300.
+//
+// Fields and medium coefficients live in one device arena per level
+// (structure of arrays: [field][cell], every patch a contiguous block with a
+// 2-cell ghost ring).  The host keeps only metadata: patch boxes, lookup
+// buckets, and the device descriptor tables (ghost map, average-down map,
+// tile work-list) rebuilt at each regrid.  Between regrids a level step is
+// three kernel launches on the context's stream (ghost fill, fused step,
+// average-down); regrids flag on the device, copy the flag bitmap to the
+// host, cluster there (Berger-Rigoutsos, Sec. 3) and initialise the new
+// patches on the device.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace adjamr;
+
+namespace {
+
+struct Box {
+    int i0, i1, j0, j1;  // inclusive
+};
+
+struct HPatch {
+    int ilo, jlo, nx, ny, sx, sy;
+    long long base;
+};
+
+struct Level {
+    int N = 0, M = 0;
+    double dx = 0, dy = 0, dt = 0;
+    long long nstep = 0;
+    int cur = 0;
+    std::vector<HPatch> patches;
+    long long ncell = 0, ninterior = 0;
+    double *q[2] = {nullptr, nullptr};
+    double *aux = nullptr, *med = nullptr;
+    PatchDesc *d_patches = nullptr;
+    WorkItem *d_work = nullptr;
+    int nwork = 0, work_tx = 0, work_ty = 0;
+    std::vector<WorkItem> h_work;
+    GhostDesc *d_ghost = nullptr;
+    long long nghost = 0;
+    AvgDesc *d_avg = nullptr;
+    long long navg = 0;
+    long long *d_prefix = nullptr;
+    MediumDev *d_med = nullptr;
+    // lookup buckets (cells per bucket side)
+    int bs = 16, nbx = 0, nby = 0;
+    std::vector<std::vector<int>> buckets;
+};
+
+}  // namespace
+
+struct adjamr_adjoint {
+    int refs = 1;
+    int S = 0, m = 0, ax = 0, ay = 0, dim = 0;
+    double *d_snaps = nullptr;
+    unsigned char *d_wet = nullptr;
+    size_t bytes = 0;
+};
+
+struct adjamr_ctx {
+    adjamr_params P;
+    int m = 0, naux = 0, nmed = 0, gy = 0;
+    Level L[ADJAMR_MAX_LEVELS];
+    long long T[ADJAMR_MAX_LEVELS] = {};
+    long long rebuilt_tick[ADJAMR_MAX_LEVELS];
+    cudaStream_t s = nullptr;
+    std::string err;
+    bool have_medium = false;
+    MediumDev mh[ADJAMR_MAX_LEVELS];
+    std::vector<double *> dense_dev;
+    adjamr_adjoint *adj = nullptr;
+    unsigned long long *d_cfl = nullptr, *d_count = nullptr;
+    unsigned char *d_flagbuf = nullptr;
+    size_t flagbuf_bytes = 0;
+    double *d_fscratch = nullptr, *d_fout = nullptr;
+    size_t fscratch_n = 0;
+    adjamr_stats st = {};
+    int tx = 32, ty = 8, launch_mode = 0, grid_persistent = 0;
+    bool timing = false;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // step-kernel timing without host synchronisation: event pairs recorded
+    // around every step launch, read when the stream is synchronised
+    std::vector<cudaEvent_t> tev;
+    size_t tev_used = 0;
+};
+
+namespace {
+
+#define CKR(ctx, x)                                                                                   \
+    do {                                                                                              \
+        cudaError_t _e = (x);                                                                         \
+        if (_e != cudaSuccess) {                                                                      \
+            (ctx)->err = std::string(#x) + ": " + cudaGetErrorString(_e);                             \
+            return ADJAMR_ECUDA;                                                                      \
+        }                                                                                             \
+    } while (0)
+
+#define TRY(x)                                                                                        \
+    do {                                                                                              \
+        adjamr_status _s = (x);                                                                       \
+        if (_s != ADJAMR_OK) return _s;                                                               \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t n, cudaStream_t s)
+{
+    *p = nullptr;
+    if (n == 0) return cudaSuccess;
+    return cudaMallocAsync((void **)p, n * sizeof(T), s);
+}
+
+template <typename T>
+void dfree(T *&p, cudaStream_t s)
+{
+    if (p) cudaFreeAsync((void *)p, s);
+    p = nullptr;
+}
+
+template <typename T>
+cudaError_t upload(T **p, const std::vector<T> &v, cudaStream_t s)
+{
+    cudaError_t e = dalloc(p, v.size(), s);
+    if (e != cudaSuccess || v.empty()) return e;
+    return cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+}
+
+int part_len(int n, int p, int k) { return n / p + (k < n % p ? 1 : 0); }
+int part_off(int n, int p, int k)
+{
+    int o = 0;
+    for (int q = 0; q < k; q++) o += part_len(n, p, q);
+    return o;
+}
+
+// boundary map of (I, J) on level l: in-domain cell plus sign flags of
+// components 1 (x-normal) and 2 (y-normal)
+void bc_map(const adjamr_ctx *c, int l, int &I, int &J, int &f1, int &f2)
+{
+    const Level &L = c->L[l];
+    f1 = f2 = 0;
+    if (I < 0) {
+        if (c->P.bc[0] == ADJAMR_BC_EXTRAP) I = 0;
+        else if (c->P.bc[0] == ADJAMR_BC_WALL) { I = -1 - I; f1 ^= 1; }
+        else I += L.N;
+    } else if (I >= L.N) {
+        if (c->P.bc[1] == ADJAMR_BC_EXTRAP) I = L.N - 1;
+        else if (c->P.bc[1] == ADJAMR_BC_WALL) { I = 2 * L.N - 1 - I; f1 ^= 1; }
+        else I -= L.N;
+    }
+    if (c->P.dim == 2) {
+        if (J < 0) {
+            if (c->P.bc[2] == ADJAMR_BC_EXTRAP) J = 0;
+            else if (c->P.bc[2] == ADJAMR_BC_WALL) { J = -1 - J; f2 ^= 1; }
+            else J += L.M;
+        } else if (J >= L.M) {
+            if (c->P.bc[3] == ADJAMR_BC_EXTRAP) J = L.M - 1;
+            else if (c->P.bc[3] == ADJAMR_BC_WALL) { J = 2 * L.M - 1 - J; f2 ^= 1; }
+            else J -= L.M;
+        }
+    }
+}
+
+long long cell_of(const adjamr_ctx *c, const HPatch &p, int i, int j)
+{
+    return p.base + (long long)(j + c->gy) * p.sx + (i + 2);
+}
+
+void build_buckets(Level &L)
+{
+    L.nbx = (L.N + L.bs - 1) / L.bs;
+    L.nby = (L.M + L.bs - 1) / L.bs;
+    L.buckets.assign((size_t)L.nbx * L.nby, {});
+    for (int k = 0; k < (int)L.patches.size(); k++) {
+        const HPatch &p = L.patches[k];
+        for (int by = p.jlo / L.bs; by <= (p.jlo + p.ny - 1) / L.bs; by++)
+            for (int bx = p.ilo / L.bs; bx <= (p.ilo + p.nx - 1) / L.bs; bx++)
+                L.buckets[(size_t)by * L.nbx + bx].push_back(k);
+    }
+}
+
+int find_patch(const Level &L, int I, int J)
+{
+    if (I < 0 || J < 0 || I >= L.N || J >= L.M || L.buckets.empty()) return -1;
+    const std::vector<int> &b = L.buckets[(size_t)(J / L.bs) * L.nbx + I / L.bs];
+    for (int k : b) {
+        const HPatch &p = L.patches[k];
+        if (I >= p.ilo && I < p.ilo + p.nx && J >= p.jlo && J < p.jlo + p.ny) return k;
+    }
+    return -1;
+}
+
+void free_level(adjamr_ctx *c, Level &L)
+{
+    cudaStream_t s = c->s;
+    dfree(L.q[0], s);
+    dfree(L.q[1], s);
+    dfree(L.aux, s);
+    dfree(L.med, s);
+    dfree(L.d_patches, s);
+    dfree(L.d_work, s);
+    dfree(L.d_ghost, s);
+    dfree(L.d_avg, s);
+    dfree(L.d_prefix, s);
+    L.patches.clear();
+    L.h_work.clear();
+    L.buckets.clear();
+    L.ncell = L.ninterior = 0;
+    L.nwork = 0;
+    L.nghost = L.navg = 0;
+    L.work_tx = L.work_ty = 0;
+}
+
+// (re)build the tile work-list of a level for tile (tx, ty)
+adjamr_status build_work(adjamr_ctx *c, int l, int tx, int ty)
+{
+    Level &L = c->L[l];
+    if (L.work_tx == tx && L.work_ty == ty && L.d_work) return ADJAMR_OK;
+    dfree(L.d_work, c->s);
+    L.h_work.clear();
+    int txx = (c->P.dim == 1) ? tx : tx;
+    for (int k = 0; k < (int)L.patches.size(); k++) {
+        const HPatch &p = L.patches[k];
+        int tyy = (c->P.dim == 2) ? ty : 1;
+        for (int y0 = 0; y0 < p.ny; y0 += tyy)
+            for (int x0 = 0; x0 < p.nx; x0 += txx) L.h_work.push_back({k, x0, y0, 0});
+    }
+    L.nwork = (int)L.h_work.size();
+    CKR(c, upload(&L.d_work, L.h_work, c->s));
+    L.work_tx = tx;
+    L.work_ty = ty;
+    return ADJAMR_OK;
+}
+
+// allocate the arena of a level for the given boxes (level index space)
+adjamr_status alloc_level(adjamr_ctx *c, int l, const std::vector<Box> &boxes)
+{
+    Level &L = c->L[l];
+    L.patches.clear();
+    long long off = 0;
+    for (const Box &b : boxes) {
+        HPatch p;
+        p.ilo = b.i0;
+        p.jlo = b.j0;
+        p.nx = b.i1 - b.i0 + 1;
+        p.ny = b.j1 - b.j0 + 1;
+        p.sx = p.nx + 4;
+        p.sy = p.ny + 2 * c->gy;
+        p.base = off;
+        off += ((long long)p.sx * p.sy + 3) / 4 * 4;  // 32-byte aligned blocks
+        L.patches.push_back(p);
+    }
+    L.ncell = off;
+    L.ninterior = 0;
+    std::vector<PatchDesc> pd;
+    std::vector<long long> prefix;
+    prefix.push_back(0);
+    double dtdx = L.dt / L.dx, dtdy = (c->P.dim == 2) ? L.dt / L.dy : 0.0;
+    for (const HPatch &p : L.patches) {
+        PatchDesc d;
+        d.ilo = p.ilo; d.jlo = p.jlo; d.nx = p.nx; d.ny = p.ny; d.sx = p.sx; d.sy = p.sy; d.base = p.base;
+        d.dtdx = dtdx; d.dtdy = dtdy; d.hx = 0.5 * dtdx; d.hy = 0.5 * dtdy;
+        pd.push_back(d);
+        L.ninterior += (long long)p.nx * p.ny;
+        prefix.push_back(L.ninterior);
+    }
+    CKR(c, dalloc(&L.q[0], (size_t)c->m * L.ncell, c->s));
+    CKR(c, dalloc(&L.q[1], (size_t)c->m * L.ncell, c->s));
+    CKR(c, dalloc(&L.aux, (size_t)c->naux * L.ncell, c->s));
+    CKR(c, dalloc(&L.med, (size_t)c->nmed * L.ncell, c->s));
+    if (L.ncell > 0) {
+        CKR(c, cudaMemsetAsync(L.q[0], 0, sizeof(double) * c->m * L.ncell, c->s));
+        CKR(c, cudaMemsetAsync(L.q[1], 0, sizeof(double) * c->m * L.ncell, c->s));
+    }
+    CKR(c, upload(&L.d_patches, pd, c->s));
+    CKR(c, upload(&L.d_prefix, prefix, c->s));
+    build_buckets(L);
+    L.work_tx = L.work_ty = 0;
+    return build_work(c, l, c->tx, c->ty);
+}
+
+LevelGeom geom_of(const adjamr_ctx *c, int l)
+{
+    LevelGeom g;
+    g.dim = c->P.dim;
+    g.N = c->L[l].N;
+    g.M = c->L[l].M;
+    g.lo0 = c->P.lo[0];
+    g.lo1 = c->P.lo[1];
+    g.dx = c->L[l].dx;
+    g.dy = c->L[l].dy;
+    for (int k = 0; k < 4; k++) g.bc[k] = c->P.bc[k];
+    return g;
+}
+
+// medium coefficients of every storage cell of a level
+adjamr_status fill_aux(adjamr_ctx *c, int l)
+{
+    Level &L = c->L[l];
+    if (!c->have_medium || L.patches.empty()) return ADJAMR_OK;
+    std::vector<AuxDesc> ad;
+    ad.reserve((size_t)L.ncell);
+    for (const HPatch &p : L.patches)
+        for (int j = -c->gy; j < p.ny + c->gy; j++)
+            for (int i = -2; i < p.nx + 2; i++) ad.push_back({cell_of(c, p, i, j), p.ilo + i, p.jlo + j});
+    AuxDesc *d = nullptr;
+    CKR(c, upload(&d, ad, c->s));
+    CKR(c, launch_aux_fill(c->P.eqn, c->P.dim, d, (long long)ad.size(), L.aux, L.med, L.ncell, L.d_med, geom_of(c, l),
+                           c->s));
+    c->st.kernel_launches++;
+    dfree(d, c->s);
+    return ADJAMR_OK;
+}
+
+// coarse interpolation descriptor for fine in-domain cell (I, J) of level l
+adjamr_status coarse_desc(adjamr_ctx *c, int l, int I, int J, GhostDesc &g)
+{
+    const Level &C = c->L[l - 1];
+    int r = c->P.ratio[l - 1];
+    int ic = I / r, jc = (c->P.dim == 2) ? J / r : 0;
+    g.kind = 1;
+    g.mx = I - ic * r;
+    g.my = (c->P.dim == 2) ? J - jc * r : 0;
+    const int di[5] = {0, -1, 1, 0, 0}, dj[5] = {0, 0, 0, -1, 1};
+    long long *dst[5] = {&g.src, &g.cxm, &g.cxp, &g.cym, &g.cyp};
+    int nref = (c->P.dim == 2) ? 5 : 3;
+    for (int k = 0; k < 5; k++) *dst[k] = 0;
+    for (int k = 0; k < nref; k++) {
+        int a = ic + di[k], b = jc + dj[k], f1, f2;
+        bc_map(c, l - 1, a, b, f1, f2);
+        int pk = find_patch(C, a, b);
+        if (pk < 0) {
+            char buf[160];
+            snprintf(buf, sizeof buf, "nesting violated: level %d cell (%d,%d) not covered", l - 1, a, b);
+            c->err = buf;
+            return ADJAMR_ENEST;
+        }
+        const HPatch &p = C.patches[pk];
+        *dst[k] = cell_of(c, p, a - p.ilo, b - p.jlo);
+        g.signs |= (f1 << (2 + 2 * k)) | (f2 << (3 + 2 * k));
+    }
+    return ADJAMR_OK;
+}
+
+// ghost map of level l (needs level l-1 when l > 0)
+adjamr_status build_ghost_map(adjamr_ctx *c, int l)
+{
+    Level &L = c->L[l];
+    dfree(L.d_ghost, c->s);
+    L.nghost = 0;
+    std::vector<GhostDesc> gd;
+    for (const HPatch &p : L.patches)
+        for (int j = -c->gy; j < p.ny + c->gy; j++)
+            for (int i = -2; i < p.nx + 2; i++) {
+                if (i >= 0 && i < p.nx && j >= 0 && j < p.ny) continue;
+                int I = p.ilo + i, J = p.jlo + j, f1, f2;
+                bc_map(c, l, I, J, f1, f2);
+                GhostDesc g;
+                std::memset(&g, 0, sizeof g);
+                g.dst = cell_of(c, p, i, j);
+                int sk = find_patch(L, I, J);
+                if (sk >= 0) {
+                    const HPatch &sp = L.patches[sk];
+                    g.kind = 0;
+                    g.src = cell_of(c, sp, I - sp.ilo, J - sp.jlo);
+                } else {
+                    if (l == 0) {
+                        c->err = "level 0 does not cover the domain";
+                        return ADJAMR_ENEST;
+                    }
+                    TRY(coarse_desc(c, l, I, J, g));
+                }
+                g.signs |= f1 | (f2 << 1);
+                gd.push_back(g);
+            }
+    L.nghost = (long long)gd.size();
+    CKR(c, upload(&L.d_ghost, gd, c->s));
+    return ADJAMR_OK;
+}
+
+// average-down map of level l (fine) into level l-1
+adjamr_status build_avg_map(adjamr_ctx *c, int l)
+{
+    Level &F = c->L[l];
+    const Level &C = c->L[l - 1];
+    dfree(F.d_avg, c->s);
+    F.navg = 0;
+    int r = c->P.ratio[l - 1];
+    std::vector<AvgDesc> ad;
+    for (const HPatch &p : F.patches) {
+        int a0 = p.ilo / r, a1 = (p.ilo + p.nx) / r;
+        int b0 = (c->P.dim == 2) ? p.jlo / r : 0, b1 = (c->P.dim == 2) ? (p.jlo + p.ny) / r : 1;
+        for (int b = b0; b < b1; b++)
+            for (int a = a0; a < a1; a++) {
+                int ck = find_patch(C, a, b);
+                if (ck < 0) {
+                    c->err = "average-down: coarse cell not covered";
+                    return ADJAMR_ENEST;
+                }
+                const HPatch &cp = C.patches[ck];
+                AvgDesc d;
+                d.dst = cell_of(c, cp, a - cp.ilo, b - cp.jlo);
+                d.src = cell_of(c, p, a * r - p.ilo, (c->P.dim == 2) ? b * r - p.jlo : 0);
+                d.fsx = p.sx;
+                d.pad = 0;
+                ad.push_back(d);
+            }
+    }
+    F.navg = (long long)ad.size();
+    CKR(c, upload(&F.d_avg, ad, c->s));
+    return ADJAMR_OK;
+}
+
+// ---------------------------------------------------------------- clustering
+// Berger-Rigoutsos on a flag field [M][N] with a nesting mask, using
+// integral images for box counts and signatures.
+struct Clusterer {
+    int N, M, dim, mc;
+    double eff;
+    std::vector<long long> SF, SB;  // integral images of flags and of non-nestable cells
+    std::vector<Box> out;
+
+    long long sum(const std::vector<long long> &S, int i0, int i1, int j0, int j1) const
+    {
+        // inclusive box, (N+1)-pitch integral image
+        long long W = N + 1;
+        return S[(long long)(j1 + 1) * W + (i1 + 1)] - S[(long long)j0 * W + (i1 + 1)] -
+               S[(long long)(j1 + 1) * W + i0] + S[(long long)j0 * W + i0];
+    }
+
+    void init(const std::vector<unsigned char> &flags, const std::vector<unsigned char> &nest)
+    {
+        long long W = N + 1;
+        SF.assign((size_t)(M + 1) * W, 0);
+        SB.assign((size_t)(M + 1) * W, 0);
+        for (int j = 0; j < M; j++) {
+            long long rf = 0, rb = 0;
+            for (int i = 0; i < N; i++) {
+                rf += flags[(size_t)j * N + i];
+                rb += nest[(size_t)j * N + i] ? 0 : 1;
+                SF[(size_t)(j + 1) * W + i + 1] = SF[(size_t)j * W + i + 1] + rf;
+                SB[(size_t)(j + 1) * W + i + 1] = SB[(size_t)j * W + i + 1] + rb;
+            }
+        }
+    }
+
+    void run(Box b)
+    {
+        std::vector<Box> stack{b};
+        while (!stack.empty()) {
+            Box x = stack.back();
+            stack.pop_back();
+            Box l, r;
+            if (split(x, l, r)) {
+                stack.push_back(r);
+                stack.push_back(l);
+            }
+        }
+    }
+
+    // returns true and the two halves if x must be split; false if x was
+    // accepted (pushed to out) or holds no flag
+    bool split(Box x, Box &L, Box &R)
+    {
+        if (sum(SF, x.i0, x.i1, x.j0, x.j1) == 0) return false;
+        std::vector<long long> cs(x.i1 - x.i0 + 1), rs(x.j1 - x.j0 + 1);
+        for (int i = x.i0; i <= x.i1; i++) cs[i - x.i0] = sum(SF, i, i, x.j0, x.j1);
+        for (int j = x.j0; j <= x.j1; j++) rs[j - x.j0] = sum(SF, x.i0, x.i1, j, j);
+        int a = 0, bb = (int)cs.size() - 1, c0 = 0, c1 = (int)rs.size() - 1;
+        while (cs[a] == 0) a++;
+        while (cs[bb] == 0) bb--;
+        while (rs[c0] == 0) c0++;
+        while (rs[c1] == 0) c1--;
+        Box b{x.i0 + a, x.i0 + bb, x.j0 + c0, x.j0 + c1};
+        std::vector<long long> sx(cs.begin() + a, cs.begin() + bb + 1), sy(rs.begin() + c0, rs.begin() + c1 + 1);
+        long long nf = 0;
+        for (long long v : sx) nf += v;
+        int lx = b.i1 - b.i0 + 1, ly = b.j1 - b.j0 + 1;
+        long long area = (long long)lx * ly;
+        bool nestable = sum(SB, b.i0, b.i1, b.j0, b.j1) == 0;
+        if (nestable && (double)nf / (double)area >= eff) {
+            out.push_back(b);
+            return false;
+        }
+        int m = nestable ? mc : 1;
+        int ndim = (dim == 2) ? 2 : 1;
+        const std::vector<long long> *sig[2] = {&sx, &sy};
+        int los[2] = {b.i0, b.j0}, his[2] = {b.i1, b.j1};
+        // (1) zero signature closest to the centre
+        int bd = -1, bp = 0, bdist = 0;
+        for (int d = 0; d < ndim; d++) {
+            const std::vector<long long> &s = *sig[d];
+            for (int k = los[d] + 1; k < his[d]; k++) {
+                if (s[k - los[d]] != 0) continue;
+                int dist = std::abs(2 * k - (los[d] + his[d]));
+                if (bd < 0 || dist < bdist) { bd = d; bp = k; bdist = dist; }
+            }
+        }
+        if (bd >= 0) {
+            L = b; R = b;
+            if (bd == 0) { L.i1 = bp - 1; R.i0 = bp + 1; }
+            else { L.j1 = bp - 1; R.j0 = bp + 1; }
+            return true;
+        }
+        // (2) strongest sign change of the second difference
+        long long bstr = -1;
+        for (int d = 0; d < ndim; d++) {
+            const std::vector<long long> &s = *sig[d];
+            int lo = los[d], hi = his[d];
+            for (int k = lo + 1; k <= hi - 2; k++) {
+                long long d0 = s[k - 1 - lo] - 2 * s[k - lo] + s[k + 1 - lo];
+                long long d1 = s[k - lo] - 2 * s[k + 1 - lo] + s[k + 2 - lo];
+                bool change = (d0 < 0 && d1 > 0) || (d0 > 0 && d1 < 0);
+                if (!change || k - lo + 1 < m || hi - k < m) continue;
+                long long str = d1 > d0 ? d1 - d0 : d0 - d1;
+                int dist = std::abs(2 * k + 1 - (lo + hi));
+                if (str > bstr || (str == bstr && dist < bdist)) { bstr = str; bdist = dist; bd = d; bp = k; }
+            }
+        }
+        if (bd >= 0) {
+            L = b; R = b;
+            if (bd == 0) { L.i1 = bp; R.i0 = bp + 1; }
+            else { L.j1 = bp; R.j0 = bp + 1; }
+            return true;
+        }
+        // (3) bisect the longer side (x on ties), else the other one
+        int order[2] = {0, 1};
+        if (ndim == 2 && ly > lx) { order[0] = 1; order[1] = 0; }
+        for (int q = 0; q < ndim; q++) {
+            int d = order[q];
+            int len = d ? ly : lx, lo = d ? b.j0 : b.i0;
+            if (len / 2 < m || len - len / 2 < m) continue;
+            int mid = lo + len / 2;
+            L = b; R = b;
+            if (d == 0) { L.i1 = mid - 1; R.i0 = mid; }
+            else { L.j1 = mid - 1; R.j0 = mid; }
+            return true;
+        }
+        out.push_back(b);
+        return false;
+    }
+};
+
+// separable Chebyshev dilation of a 0/1 field by w cells (wy in y), in place
+void dilate(std::vector<unsigned char> &f, int N, int M, int w, int wy)
+{
+    std::vector<unsigned char> t(f.size());
+    for (int j = 0; j < M; j++) {
+        int run = -1;  // distance to the last set cell to the left is tracked by a sliding count
+        std::vector<int> pre(N + 1, 0);
+        for (int i = 0; i < N; i++) pre[i + 1] = pre[i] + f[(size_t)j * N + i];
+        for (int i = 0; i < N; i++) {
+            int a = std::max(0, i - w), b = std::min(N - 1, i + w);
+            t[(size_t)j * N + i] = (pre[b + 1] - pre[a]) > 0;
+        }
+        (void)run;
+    }
+    if (wy == 0) {
+        f.swap(t);
+        return;
+    }
+    std::vector<int> pre(M + 1);
+    for (int i = 0; i < N; i++) {
+        pre[0] = 0;
+        for (int j = 0; j < M; j++) pre[j + 1] = pre[j] + t[(size_t)j * N + i];
+        for (int j = 0; j < M; j++) {
+            int a = std::max(0, j - wy), b = std::min(M - 1, j + wy);
+            f[(size_t)j * N + i] = (pre[b + 1] - pre[a]) > 0;
+        }
+    }
+}
+
+adjamr_status flag_dense(adjamr_ctx *c, int l, double tol, unsigned char *d_dense, unsigned char *d_patchflags,
+                         long long *nflag_out);
+
+// Rebuild levels base+1 .. nlevels-1 top-down (Sec. 3).
+void harvest_timing(adjamr_ctx *c);
+
+adjamr_status regrid_from(adjamr_ctx *c, int base, int init)
+{
+    const adjamr_params &P = c->P;
+    for (int lev = base; lev < P.nlevels - 1; lev++) {
+        Level &C = c->L[lev];
+        Level &F = c->L[lev + 1];
+        const int r = P.ratio[lev], N = C.N, M = C.M, dim = P.dim;
+        const long long tick = C.nstep * c->T[lev];
+        // ---- adjoint flags of level lev on its index space (device) ----
+        size_t nb = (size_t)N * M;
+        if (c->flagbuf_bytes < nb) {
+            dfree(c->d_flagbuf, c->s);
+            CKR(c, dalloc(&c->d_flagbuf, nb, c->s));
+            c->flagbuf_bytes = nb;
+        }
+        CKR(c, cudaMemsetAsync(c->d_flagbuf, 0, nb, c->s));
+        long long nf = 0;
+        TRY(flag_dense(c, lev, P.tol, c->d_flagbuf, nullptr, &nf));
+        std::vector<unsigned char> fl(nb, 0);
+        if (nf > 0) {
+            CKR(c, cudaMemcpyAsync(fl.data(), c->d_flagbuf, nb, cudaMemcpyDeviceToHost, c->s));
+            CKR(c, cudaStreamSynchronize(c->s));
+        }
+        harvest_timing(c);
+        // ---- buffer, nesting mask ----
+        dilate(fl, N, M, P.buffer, dim == 2 ? P.buffer : 0);
+        std::vector<unsigned char> unc(nb, 1);
+        for (const HPatch &p : C.patches)
+            for (int j = 0; j < p.ny; j++)
+                std::memset(&unc[(size_t)(p.jlo + j) * N + p.ilo], 0, (size_t)p.nx);
+        dilate(unc, N, M, 2, dim == 2 ? 2 : 0);
+        std::vector<unsigned char> nest(nb);
+        for (size_t k = 0; k < nb; k++) {
+            nest[k] = !unc[k];
+            if (!nest[k]) fl[k] = 0;
+        }
+        // ---- Berger-Rigoutsos ----
+        Clusterer cl;
+        cl.N = N;
+        cl.M = M;
+        cl.dim = dim;
+        cl.mc = (P.min_patch + r - 1) / r;
+        cl.eff = P.cluster_eff;
+        std::vector<Box> fin;
+        if (nf > 0) {
+            cl.init(fl, nest);
+            cl.run(Box{0, N - 1, 0, M - 1});
+            for (const Box &b : cl.out) {
+                int lx = b.i1 - b.i0 + 1, ly = b.j1 - b.j0 + 1;
+                int px = 1, py = 1;
+                while (r * ((lx + px - 1) / px) > P.max_patch) px++;
+                if (dim == 2)
+                    while (r * ((ly + py - 1) / py) > P.max_patch) py++;
+                for (int bj = 0; bj < py; bj++)
+                    for (int bi = 0; bi < px; bi++) {
+                        Box s;
+                        s.i0 = b.i0 + part_off(lx, px, bi);
+                        s.i1 = s.i0 + part_len(lx, px, bi) - 1;
+                        s.j0 = (dim == 2) ? b.j0 + part_off(ly, py, bj) : 0;
+                        s.j1 = (dim == 2) ? s.j0 + part_len(ly, py, bj) - 1 : 0;
+                        fin.push_back(s);
+                    }
+            }
+            std::sort(fin.begin(), fin.end(), [](const Box &a, const Box &b) {
+                return a.j0 != b.j0 ? a.j0 < b.j0 : a.i0 < b.i0;
+            });
+        }
+        // ---- new level lev+1 (refined boxes) ----
+        std::vector<Box> fb;
+        for (const Box &b : fin)
+            fb.push_back(Box{b.i0 * r, (b.i1 + 1) * r - 1, dim == 2 ? b.j0 * r : 0, dim == 2 ? (b.j1 + 1) * r - 1 : 0});
+        Level old;
+        std::swap(old.patches, F.patches);
+        std::swap(old.buckets, F.buckets);
+        old.N = F.N; old.M = F.M; old.bs = F.bs; old.nbx = F.nbx; old.nby = F.nby;
+        old.q[0] = F.q[0]; old.q[1] = F.q[1]; old.ncell = F.ncell; old.cur = F.cur;
+        old.aux = F.aux; old.med = F.med; old.d_patches = F.d_patches; old.d_work = F.d_work;
+        old.d_ghost = F.d_ghost; old.d_avg = F.d_avg; old.d_prefix = F.d_prefix;
+        F.q[0] = F.q[1] = nullptr;
+        F.aux = F.med = nullptr;
+        F.d_patches = nullptr; F.d_work = nullptr; F.d_ghost = nullptr; F.d_avg = nullptr; F.d_prefix = nullptr;
+        TRY(alloc_level(c, lev + 1, fb));
+        F.cur = 0;
+        F.nstep = C.nstep * r;
+        TRY(fill_aux(c, lev + 1));
+        if (!F.patches.empty()) {
+            if (init && P.qinit) {
+                long long n = F.ninterior;
+                std::vector<double> xc(n), yc(n), qv((size_t)n * c->m);
+                long long o = 0;
+                for (const HPatch &p : F.patches)
+                    for (int j = 0; j < p.ny; j++)
+                        for (int i = 0; i < p.nx; i++, o++) {
+                            xc[o] = P.lo[0] + ((double)(p.ilo + i) + 0.5) * F.dx;
+                            yc[o] = (dim == 2) ? P.lo[1] + ((double)(p.jlo + j) + 0.5) * F.dy : 0.0;
+                        }
+                P.qinit(lev + 1, (int)n, xc.data(), yc.data(), qv.data(), P.qinit_user);
+                std::vector<double> host((size_t)c->m * F.ncell, 0.0);
+                o = 0;
+                for (const HPatch &p : F.patches)
+                    for (int j = 0; j < p.ny; j++)
+                        for (int i = 0; i < p.nx; i++, o++)
+                            for (int f = 0; f < c->m; f++) host[(size_t)f * F.ncell + cell_of(c, p, i, j)] = qv[(size_t)f * n + o];
+                CKR(c, cudaMemcpyAsync(F.q[0], host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, c->s));
+            } else {
+                std::vector<GhostDesc> gd;
+                gd.reserve((size_t)F.ninterior);
+                for (const HPatch &p : F.patches)
+                    for (int j = 0; j < p.ny; j++)
+                        for (int i = 0; i < p.nx; i++) {
+                            int I = p.ilo + i, J = p.jlo + j;
+                            GhostDesc g;
+                            std::memset(&g, 0, sizeof g);
+                            g.dst = cell_of(c, p, i, j);
+                            int ok = find_patch(old, I, J);
+                            if (ok >= 0) {
+                                const HPatch &op = old.patches[ok];
+                                g.kind = 2;
+                                g.src = cell_of(c, op, I - op.ilo, J - op.jlo);
+                            } else {
+                                TRY(coarse_desc(c, lev + 1, I, J, g));
+                            }
+                            gd.push_back(g);
+                        }
+                GhostDesc *d = nullptr;
+                CKR(c, upload(&d, gd, c->s));
+                CKR(c, launch_regrid_init(dim, c->m, d, (long long)gd.size(), F.q[0], F.ncell,
+                                          old.q[0] ? old.q[old.cur] : F.q[0], old.ncell, C.q[C.cur], C.ncell, r, c->s));
+                c->st.kernel_launches++;
+                dfree(d, c->s);
+            }
+            TRY(build_ghost_map(c, lev + 1));
+            TRY(build_avg_map(c, lev + 1));
+        }
+        free_level(c, old);
+        c->rebuilt_tick[lev + 1] = tick;
+        c->st.regrids++;
+        if (F.patches.empty()) {
+            for (int q = lev + 2; q < P.nlevels; q++) free_level(c, c->L[q]);
+            break;
+        }
+    }
+    return ADJAMR_OK;
+}
+
+adjamr_status flag_dense(adjamr_ctx *c, int l, double tol, unsigned char *d_dense, unsigned char *d_patchflags,
+                         long long *nflag_out)
+{
+    Level &L = c->L[l];
+    *nflag_out = 0;
+    if (L.patches.empty()) return ADJAMR_OK;
+    const adjamr_params &P = c->P;
+    FlagArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.q = L.q[L.cur];
+    a.stride = L.ncell;
+    a.patches = L.d_patches;
+    a.cell_prefix = L.d_prefix;
+    a.np = (int)L.patches.size();
+    a.dim = P.dim;
+    a.m = c->m;
+    a.mode = P.flag_mode;
+    a.ncells = L.ninterior;
+    a.lo0 = P.lo[0]; a.lo1 = P.lo[1]; a.hi0 = P.hi[0]; a.hi1 = P.hi[1];
+    a.dx = L.dx; a.dy = L.dy;
+    a.tol = tol;
+    a.flags_patch = d_patchflags;
+    a.flags_dense = d_dense;
+    a.N = L.N;
+    a.count = c->d_count;
+    double t = P.t0 + (double)L.nstep * L.dt;
+    double T = std::fmin(t + (P.tf - P.ts), P.tf);
+    a.t = t;
+    a.T = T;
+    a.t0 = P.t0;
+    if (c->adj) {
+        int S = c->adj->S;
+        a.S = S;
+        a.snaps = c->adj->d_snaps;
+        a.wet = c->adj->d_wet;
+        a.ax = c->adj->ax;
+        a.ay = c->adj->ay;
+        a.dts = (P.tf - P.t0) / (double)(S - 1);
+        int nlo = 0, nhi = S - 1;
+        for (int n = 0; n < S; n++)
+            if (P.t0 + (double)n * a.dts <= t) nlo = n;
+        for (int n = S - 1; n >= 0; n--)
+            if (P.t0 + (double)n * a.dts >= T) nhi = n;
+        a.nlo = nlo;
+        a.nhi = nhi;
+    } else {
+        a.S = 0;
+        a.ax = a.ay = 1;
+    }
+    CKR(c, cudaMemsetAsync(c->d_count, 0, sizeof(unsigned long long), c->s));
+    CKR(c, launch_flag(a, c->s));
+    c->st.kernel_launches++;
+    unsigned long long cnt = 0;
+    CKR(c, cudaMemcpyAsync(&cnt, c->d_count, sizeof cnt, cudaMemcpyDeviceToHost, c->s));
+    CKR(c, cudaStreamSynchronize(c->s));
+    *nflag_out = (long long)cnt;
+    return ADJAMR_OK;
+}
+
+adjamr_status ghost_fill(adjamr_ctx *c, int l, int k)
+{
+    Level &L = c->L[l];
+    if (L.nghost == 0) return ADJAMR_OK;
+    const double *qo = nullptr, *qn = nullptr;
+    long long sc = 0;
+    int r = 1;
+    if (l > 0) {
+        Level &C = c->L[l - 1];
+        qo = C.q[C.cur];
+        qn = C.q[1 - C.cur];
+        sc = C.ncell;
+        r = c->P.ratio[l - 1];
+    }
+    CKR(c, launch_ghost_fill(c->P.dim, c->m, L.d_ghost, L.nghost, L.q[L.cur], L.ncell, qo, qn, sc, k, r, c->s));
+    c->st.kernel_launches++;
+    return ADJAMR_OK;
+}
+
+adjamr_status step_patches(adjamr_ctx *c, int l)
+{
+    Level &L = c->L[l];
+    if (L.patches.empty()) return ADJAMR_OK;
+    TRY(build_work(c, l, c->tx, c->ty));
+    cudaEvent_t tb = nullptr, te = nullptr;
+    if (c->timing) {
+        while (c->tev.size() < c->tev_used + 2) {
+            cudaEvent_t e;
+            CKR(c, cudaEventCreate(&e));
+            c->tev.push_back(e);
+        }
+        tb = c->tev[c->tev_used];
+        te = c->tev[c->tev_used + 1];
+        c->tev_used += 2;
+        CKR(c, cudaEventRecord(tb, c->s));
+    }
+    const double *q = L.q[L.cur];
+    double *qn = L.q[1 - L.cur];
+    if (c->launch_mode == ADJAMR_LAUNCH_PER_PATCH) {
+        int w0 = 0;
+        for (int k = 0; k < (int)L.patches.size(); k++) {
+            int w1 = w0;
+            while (w1 < L.nwork && L.h_work[w1].patch == k) w1++;
+            CKR(c, launch_step(c->P.dim, c->P.eqn, c->tx, c->ty, q, qn, L.aux, L.ncell, L.d_patches, L.d_work + w0,
+                               w1 - w0, 0, c->d_cfl, c->s));
+            c->st.kernel_launches++;
+            c->st.step_kernel_launches++;
+            w0 = w1;
+        }
+    } else {
+        int grid = 0;
+        if (c->launch_mode == ADJAMR_LAUNCH_PERSISTENT) grid = std::min(L.nwork, c->grid_persistent);
+        CKR(c, launch_step(c->P.dim, c->P.eqn, c->tx, c->ty, q, qn, L.aux, L.ncell, L.d_patches, L.d_work, L.nwork,
+                           grid, c->d_cfl, c->s));
+        c->st.kernel_launches++;
+        c->st.step_kernel_launches++;
+    }
+    if (c->timing) CKR(c, cudaEventRecord(te, c->s));
+    c->st.cell_updates += L.ninterior;
+    return ADJAMR_OK;
+}
+
+adjamr_status average_down(adjamr_ctx *c, int lf)
+{
+    Level &F = c->L[lf];
+    Level &C = c->L[lf - 1];
+    if (F.navg == 0) return ADJAMR_OK;
+    CKR(c, launch_average_down(c->P.dim, c->m, F.d_avg, F.navg, F.q[F.cur], F.ncell, C.q[1 - C.cur], C.ncell,
+                               c->P.ratio[lf - 1], c->s));
+    c->st.kernel_launches++;
+    return ADJAMR_OK;
+}
+
+// sum the recorded step-kernel event pairs (stream already synchronised)
+void harvest_timing(adjamr_ctx *c)
+{
+    for (size_t k = 0; k + 1 < c->tev_used; k += 2) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->tev[k], c->tev[k + 1]) == cudaSuccess) c->st.step_kernel_ms += ms;
+    }
+    c->tev_used = 0;
+}
+
+// Berger-Oliger recursion (Sec. 3)
+adjamr_status step_level(adjamr_ctx *c, int l)
+{
+    Level &L = c->L[l];
+    const adjamr_params &P = c->P;
+    int k = P.regrid_interval;
+    if (l < P.nlevels - 1 && k > 0 && L.nstep > 0 && L.nstep % k == 0 && c->rebuilt_tick[l + 1] != L.nstep * c->T[l])
+        TRY(regrid_from(c, l, 0));
+    int sub = 0;
+    if (l > 0) sub = (int)(L.nstep - c->L[l - 1].nstep * P.ratio[l - 1]);
+    TRY(ghost_fill(c, l, sub));
+    TRY(step_patches(c, l));
+    if (l < P.nlevels - 1 && !c->L[l + 1].patches.empty()) {
+        int r = P.ratio[l];
+        c->L[l + 1].nstep = L.nstep * r;
+        for (int s = 0; s < r; s++) TRY(step_level(c, l + 1));
+        TRY(average_down(c, l + 1));
+    }
+    L.cur = 1 - L.cur;
+    L.nstep++;
+    return ADJAMR_OK;
+}
+
+adjamr_status set_medium_impl(adjamr_ctx *c, const adjamr_medium *m)
+{
+    if (!m) return ADJAMR_EINVAL;
+    for (double *p : c->dense_dev) cudaFreeAsync(p, c->s);
+    c->dense_dev.clear();
+    for (int l = 0; l < c->P.nlevels; l++) {
+        MediumDev &md = c->mh[l];
+        std::memset(&md, 0, sizeof md);
+        md.kind = m->kind;
+        md.nmed = c->nmed;
+        md.N = c->L[l].N;
+        md.M = c->L[l].M;
+        if (m->kind == ADJAMR_MEDIUM_LAYERED) {
+            if (m->nlayers < 1 || m->nlayers > 32 || !m->f0 || !m->f1 || (m->nlayers > 1 && !m->iface)) {
+                c->err = "layered medium: bad layer table";
+                return ADJAMR_EINVAL;
+            }
+            md.axis = m->axis;
+            md.nl = m->nlayers;
+            for (int k = 0; k < m->nlayers - 1; k++) md.iface[k] = m->iface[k];
+            for (int k = 0; k < m->nlayers; k++) {
+                md.f0[k] = m->f0[k];
+                md.f1[k] = m->f1[k];
+            }
+        } else if (m->kind == ADJAMR_MEDIUM_DENSE) {
+            if (!m->dense || m->ndense < c->P.nlevels || !m->dense[l]) {
+                c->err = "dense medium: one array per level required";
+                return ADJAMR_EINVAL;
+            }
+            size_t n = (size_t)c->nmed * md.N * md.M;
+            double *d = nullptr;
+            CKR(c, dalloc(&d, n, c->s));
+            CKR(c, cudaMemcpyAsync(d, m->dense[l], n * sizeof(double), cudaMemcpyHostToDevice, c->s));
+            c->dense_dev.push_back(d);
+            md.dense = d;
+        } else {
+            c->err = "unknown medium kind";
+            return ADJAMR_EINVAL;
+        }
+        Level &L = c->L[l];
+        dfree(L.d_med, c->s);
+        CKR(c, dalloc(&L.d_med, 1, c->s));
+        CKR(c, cudaMemcpyAsync(L.d_med, &md, sizeof md, cudaMemcpyHostToDevice, c->s));
+    }
+    CKR(c, cudaStreamSynchronize(c->s));
+    c->have_medium = true;
+    for (int l = 0; l < c->P.nlevels; l++) TRY(fill_aux(c, l));
+    return ADJAMR_OK;
+}
+
+adjamr_status create_impl(const adjamr_params *p, adjamr_ctx **out)
+{
+    if (!p || !out) return ADJAMR_EINVAL;
+    *out = nullptr;
+    if (p->dim < 1 || p->dim > 2 || p->nlevels < 1 || p->nlevels > ADJAMR_MAX_LEVELS || p->n0[0] < 1 ||
+        (p->dim == 2 && p->n0[1] < 1) || p->eqn < 0 || p->eqn > 3 || (p->dim == 1 && p->eqn > 1) ||
+        !(p->hi[0] > p->lo[0]) || (p->dim == 2 && !(p->hi[1] > p->lo[1])) || p->max_patch0 < 1 ||
+        p->max_patch < 1 || (p->dt0 <= 0.0 && !(p->cmax > 0.0)) || !(p->tf > p->t0))
+        return ADJAMR_EINVAL;
+    for (int l = 0; l < p->nlevels - 1; l++)
+        if (p->ratio[l] < 2) return ADJAMR_EINVAL;
+    for (int k = 0; k < 4; k++)
+        if (p->bc[k] < 0 || p->bc[k] > 2) return ADJAMR_EINVAL;
+    adjamr_ctx *c = new (std::nothrow) adjamr_ctx();
+    if (!c) return ADJAMR_ENOMEM;
+    c->P = *p;
+    c->s = (cudaStream_t)p->stream;
+    c->m = (p->dim == 2) ? 3 : 2;
+    c->naux = naux_of(p->eqn);
+    c->nmed = nmed_of(p->eqn);
+    c->gy = (p->dim == 2) ? 2 : 0;
+    c->tx = p->tile_x > 0 ? p->tile_x : (p->dim == 2 ? 32 : 256);
+    c->ty = p->tile_y > 0 ? p->tile_y : (p->dim == 2 ? 8 : 1);
+    c->launch_mode = p->launch_mode;
+    for (int l = 0; l < ADJAMR_MAX_LEVELS; l++) c->rebuilt_tick[l] = -1;
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        delete c;
+        return ADJAMR_ECUDA;
+    }
+    {
+        // keep freed arena blocks in the stream-ordered pool across syncs:
+        // regrids free and re-allocate level arenas every few steps
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            unsigned long long thr = ~0ull;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+    }
+    int occ = step_occupancy(p->dim, p->eqn, c->tx, c->ty);
+    if (p->dim == 2 && occ <= 0) {
+        delete c;
+        return ADJAMR_EINVAL;  // unsupported tile shape
+    }
+    c->grid_persistent = nsm * std::max(occ, 1);
+    int N = p->n0[0], M = (p->dim == 2) ? p->n0[1] : 1;
+    for (int l = 0; l < p->nlevels; l++) {
+        Level &L = c->L[l];
+        L.N = N;
+        L.M = M;
+        L.dx = (p->hi[0] - p->lo[0]) / (double)N;
+        L.dy = (p->dim == 2) ? (p->hi[1] - p->lo[1]) / (double)M : 1.0;
+        if (l < p->nlevels - 1) {
+            N *= p->ratio[l];
+            if (p->dim == 2) M *= p->ratio[l];
+        }
+    }
+    double dt0 = p->dt0;
+    if (dt0 <= 0.0) {
+        double dmin = (p->dim == 2) ? std::fmin(c->L[0].dx, c->L[0].dy) : c->L[0].dx;
+        double dtc = p->cfl * dmin / p->cmax;
+        double ns = std::ceil((p->tf - p->t0) / dtc);
+        dt0 = (p->tf - p->t0) / ns;
+    }
+    c->L[0].dt = dt0;
+    for (int l = 1; l < p->nlevels; l++) c->L[l].dt = c->L[l - 1].dt / (double)p->ratio[l - 1];
+    long long T = 1;
+    for (int l = p->nlevels - 1; l >= 0; l--) {
+        c->T[l] = T;
+        if (l > 0) T *= p->ratio[l - 1];
+    }
+    adjamr_status st;
+#define FAIL(x)                                                                                       \
+    do {                                                                                              \
+        st = (x);                                                                                     \
+        if (st != ADJAMR_OK) {                                                                        \
+            adjamr_destroy(c);                                                                        \
+            return st;                                                                                \
+        }                                                                                             \
+    } while (0)
+    if (cudaMalloc(&c->d_cfl, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&c->d_count, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&c->d_fout, sizeof(double)) != cudaSuccess) {
+        adjamr_destroy(c);
+        return ADJAMR_ENOMEM;
+    }
+    cudaMemsetAsync(c->d_cfl, 0, sizeof(unsigned long long), c->s);
+    cudaEventCreate(&c->ev0);
+    cudaEventCreate(&c->ev1);
+    // level 0 tiles the domain
+    Level &L0 = c->L[0];
+    int px = (L0.N + p->max_patch0 - 1) / p->max_patch0;
+    int py = (p->dim == 2) ? (L0.M + p->max_patch0 - 1) / p->max_patch0 : 1;
+    std::vector<Box> boxes;
+    for (int b = 0; b < py; b++)
+        for (int a = 0; a < px; a++) {
+            Box x;
+            x.i0 = part_off(L0.N, px, a);
+            x.i1 = x.i0 + part_len(L0.N, px, a) - 1;
+            x.j0 = (p->dim == 2) ? part_off(L0.M, py, b) : 0;
+            x.j1 = (p->dim == 2) ? x.j0 + part_len(L0.M, py, b) - 1 : 0;
+            boxes.push_back(x);
+        }
+    FAIL(alloc_level(c, 0, boxes));
+    FAIL(build_ghost_map(c, 0));
+    if (p->qinit) {
+        long long n = L0.ninterior;
+        std::vector<double> xc(n), yc(n), qv((size_t)n * c->m), host((size_t)c->m * L0.ncell, 0.0);
+        long long o = 0;
+        for (const HPatch &q : L0.patches)
+            for (int j = 0; j < q.ny; j++)
+                for (int i = 0; i < q.nx; i++, o++) {
+                    xc[o] = p->lo[0] + ((double)(q.ilo + i) + 0.5) * L0.dx;
+                    yc[o] = (p->dim == 2) ? p->lo[1] + ((double)(q.jlo + j) + 0.5) * L0.dy : 0.0;
+                }
+        p->qinit(0, (int)n, xc.data(), yc.data(), qv.data(), p->qinit_user);
+        o = 0;
+        for (const HPatch &q : L0.patches)
+            for (int j = 0; j < q.ny; j++)
+                for (int i = 0; i < q.nx; i++, o++)
+                    for (int f = 0; f < c->m; f++) host[(size_t)f * L0.ncell + cell_of(c, q, i, j)] = qv[(size_t)f * n + o];
+        if (cudaMemcpyAsync(L0.q[0], host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, c->s) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(c->s) != cudaSuccess) {
+            adjamr_destroy(c);
+            return ADJAMR_ECUDA;
+        }
+    }
+#undef FAIL
+    if (cudaStreamSynchronize(c->s) != cudaSuccess) {
+        adjamr_destroy(c);
+        return ADJAMR_ECUDA;
+    }
+    *out = c;
+    return ADJAMR_OK;
+}
+
+// interior of a level, patch by patch, field-major per patch
+adjamr_status read_level_impl(adjamr_ctx *c, int l, double *dst, size_t cap, bool write, const double *src)
+{
+    Level &L = c->L[l];
+    size_t need = (size_t)c->m * L.ninterior;
+    if (cap < need) {
+        c->err = "buffer too small";
+        return ADJAMR_EINVAL;
+    }
+    if (L.ncell == 0) return ADJAMR_OK;
+    std::vector<double> host((size_t)c->m * L.ncell);
+    double *buf = L.q[L.cur];
+    CKR(c, cudaMemcpyAsync(host.data(), buf, host.size() * sizeof(double), cudaMemcpyDeviceToHost, c->s));
+    CKR(c, cudaStreamSynchronize(c->s));
+    size_t o = 0;
+    for (const HPatch &p : L.patches)
+        for (int f = 0; f < c->m; f++)
+            for (int j = 0; j < p.ny; j++)
+                for (int i = 0; i < p.nx; i++, o++) {
+                    size_t idx = (size_t)f * L.ncell + cell_of(c, p, i, j);
+                    if (write) host[idx] = src[o];
+                    else dst[o] = host[idx];
+                }
+    if (write) {
+        CKR(c, cudaMemcpyAsync(buf, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, c->s));
+        CKR(c, cudaStreamSynchronize(c->s));
+    }
+    return ADJAMR_OK;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+extern "C" {
+
+adjamr_status adjamr_init_grid_hierarchy(const adjamr_params *p, adjamr_ctx **out)
+{
+    try {
+        return create_impl(p, out);
+    } catch (...) {
+        return ADJAMR_ENOMEM;
+    }
+}
+
+adjamr_status adjamr_set_medium(adjamr_ctx *ctx, const adjamr_medium *m)
+{
+    if (!ctx) return ADJAMR_EINVAL;
+    try {
+        return set_medium_impl(ctx, m);
+    } catch (...) {
+        return ADJAMR_ENOMEM;
+    }
+}
+
+adjamr_status adjamr_load_adjoint_snapshots(adjamr_ctx *ctx, const double *snaps, int nsnap, int ax, int ay,
+                                            const unsigned char *wet, int on_device, adjamr_adjoint **out)
+{
+    if (!ctx || !snaps || nsnap < 2 || ax < 1) return ADJAMR_EINVAL;
+    if (ctx->P.dim == 1) ay = 1;
+    if (ay < 1 || (ctx->P.dim == 2 && ax < 2) || (ctx->P.dim == 2 && ay < 2)) return ADJAMR_EINVAL;
+    adjamr_adjoint *a = new (std::nothrow) adjamr_adjoint();
+    if (!a) return ADJAMR_ENOMEM;
+    a->S = nsnap;
+    a->m = ctx->m;
+    a->ax = ax;
+    a->ay = ay;
+    a->dim = ctx->P.dim;
+    size_t n = (size_t)nsnap * a->m * ax * ay;
+    a->bytes = n * sizeof(double) + (size_t)ax * ay;
+    if (cudaMalloc(&a->d_snaps, n * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&a->d_wet, (size_t)ax * ay) != cudaSuccess) {
+        adjamr_adjoint_release(a);
+        return ADJAMR_ENOMEM;
+    }
+    cudaError_t e = cudaMemcpyAsync(a->d_snaps, snaps, n * sizeof(double),
+                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->s);
+    if (e == cudaSuccess) {
+        if (wet) e = cudaMemcpyAsync(a->d_wet, wet, (size_t)ax * ay, cudaMemcpyHostToDevice, ctx->s);
+        else e = cudaMemsetAsync(a->d_wet, 1, (size_t)ax * ay, ctx->s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->s);
+    if (e != cudaSuccess) {
+        ctx->err = cudaGetErrorString(e);
+        adjamr_adjoint_release(a);
+        return ADJAMR_ECUDA;
+    }
+    if (ctx->adj) adjamr_adjoint_release(ctx->adj);
+    ctx->adj = a;
+    if (out) {
+        a->refs++;
+        *out = a;
+    }
+    return ADJAMR_OK;
+}
+
+adjamr_status adjamr_set_adjoint(adjamr_ctx *ctx, adjamr_adjoint *adj)
+{
+    if (!ctx || !adj || adj->m != ctx->m || adj->dim != ctx->P.dim) return ADJAMR_EINVAL;
+    adj->refs++;
+    if (ctx->adj) adjamr_adjoint_release(ctx->adj);
+    ctx->adj = adj;
+    return ADJAMR_OK;
+}
+
+adjamr_status adjamr_adjoint_read(adjamr_adjoint *adj, double *dst, size_t cap)
+{
+    if (!adj || !dst) return ADJAMR_EINVAL;
+    size_t n = (size_t)adj->S * adj->m * adj->ax * adj->ay;
+    if (cap < n) return ADJAMR_EINVAL;
+    if (cudaMemcpy(dst, adj->d_snaps, n * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) return ADJAMR_ECUDA;
+    return ADJAMR_OK;
+}
+
+void adjamr_adjoint_release(adjamr_adjoint *adj)
+{
+    if (!adj) return;
+    if (--adj->refs > 0) return;
+    if (adj->d_snaps) cudaFree(adj->d_snaps);
+    if (adj->d_wet) cudaFree(adj->d_wet);
+    delete adj;
+}
+
+adjamr_status adjamr_solve_adjoint(adjamr_ctx *ctx, const adjamr_params *ap, const adjamr_medium *am,
+                                   const double *phi, int nsnap, adjamr_adjoint **out)
+{
+    if (!ap || !am || !phi || nsnap < 2 || ap->nlevels != 1 || (ap->eqn != ADJAMR_ACOUSTICS_ADJOINT &&
+                                                                 ap->eqn != ADJAMR_SW_ADJOINT))
+        return ADJAMR_EINVAL;
+    try {
+        adjamr_params q = *ap;
+        q.qinit = nullptr;
+        q.dt0 = 1.0;  // replaced below
+        q.stream = ctx ? (void *)ctx->s : ap->stream;
+        adjamr_ctx *a = nullptr;
+        TRY(create_impl(&q, &a));
+        adjamr_status st = set_medium_impl(a, am);
+        if (st != ADJAMR_OK) {
+            if (ctx) ctx->err = a->err;
+            adjamr_destroy(a);
+            return st;
+        }
+        Level &L = a->L[0];
+        int nx = L.N, ny = L.M, m = a->m;
+        double dmin = (ap->dim == 2) ? std::fmin(L.dx, L.dy) : L.dx;
+        double dts = (ap->tf - ap->t0) / (double)(nsnap - 1);
+        double dtc = ap->cfl * dmin / ap->cmax;
+        int nsub = (int)std::ceil(dts / dtc);
+        L.dt = dts / (double)nsub;
+        // patch descriptors carry dt/dx: rebuild them with the final step
+        {
+            std::vector<Box> boxes;
+            for (const HPatch &p : L.patches) boxes.push_back(Box{p.ilo, p.ilo + p.nx - 1, p.jlo, p.jlo + p.ny - 1});
+            free_level(a, L);
+            st = alloc_level(a, 0, boxes);
+            if (st == ADJAMR_OK) st = build_ghost_map(a, 0);
+            if (st == ADJAMR_OK) st = fill_aux(a, 0);
+            if (st != ADJAMR_OK) {
+                if (ctx) ctx->err = a->err;
+                adjamr_destroy(a);
+                return st;
+            }
+        }
+        // phi into the interior (patch order)
+        {
+            std::vector<double> pv((size_t)m * L.ninterior);
+            size_t o = 0;
+            for (const HPatch &p : L.patches)
+                for (int f = 0; f < m; f++)
+                    for (int j = 0; j < p.ny; j++)
+                        for (int i = 0; i < p.nx; i++) pv[o++] = phi[((size_t)f * ny + p.jlo + j) * nx + p.ilo + i];
+            st = read_level_impl(a, 0, nullptr, pv.size(), true, pv.data());
+            if (st != ADJAMR_OK) {
+                adjamr_destroy(a);
+                return st;
+            }
+        }
+        // dense cell map for snapshot gathers
+        std::vector<long long> map((size_t)nx * ny);
+        for (const HPatch &p : L.patches)
+            for (int j = 0; j < p.ny; j++)
+                for (int i = 0; i < p.nx; i++) map[(size_t)(p.jlo + j) * nx + p.ilo + i] = cell_of(a, p, i, j);
+        long long *d_map = nullptr;
+        adjamr_adjoint *h = new adjamr_adjoint();
+        h->S = nsnap;
+        h->m = m;
+        h->ax = nx;
+        h->ay = ny;
+        h->dim = ap->dim;
+        size_t per = (size_t)m * nx * ny;
+        h->bytes = per * nsnap * sizeof(double) + (size_t)nx * ny;
+        cudaError_t e = cudaMalloc(&h->d_snaps, per * nsnap * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&h->d_wet, (size_t)nx * ny);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->d_wet, 1, (size_t)nx * ny, a->s);
+        if (e == cudaSuccess) e = upload(&d_map, map, a->s);
+        for (int sidx = 0; sidx < nsnap && e == cudaSuccess; sidx++) {
+            if (sidx > 0)
+                for (int k = 0; k < nsub && st == ADJAMR_OK; k++) {
+                    st = ghost_fill(a, 0, 0);
+                    if (st == ADJAMR_OK) st = step_patches(a, 0);
+                    L.cur = 1 - L.cur;
+                    L.nstep++;
+                }
+            if (st != ADJAMR_OK) break;
+            e = launch_gather_interior(m, d_map, (long long)nx * ny, L.q[L.cur], L.ncell,
+                                       h->d_snaps + (size_t)(nsnap - 1 - sidx) * per, a->s);
+        }
+        if (e == cudaSuccess && st == ADJAMR_OK) e = cudaStreamSynchronize(a->s);
+        dfree(d_map, a->s);
+        long long adj_updates = a->st.cell_updates;
+        if (e != cudaSuccess || st != ADJAMR_OK) {
+            if (ctx) ctx->err = e != cudaSuccess ? cudaGetErrorString(e) : a->err;
+            adjamr_destroy(a);
+            adjamr_adjoint_release(h);
+            return e != cudaSuccess ? ADJAMR_ECUDA : st;
+        }
+        adjamr_destroy(a);
+        if (ctx) {
+            ctx->st.adjoint_cell_updates += adj_updates;
+            if (ctx->adj) adjamr_adjoint_release(ctx->adj);
+            ctx->adj = h;
+            if (out) {
+                h->refs++;
+                *out = h;
+            }
+        } else if (out) {
+            *out = h;
+        } else {
+            adjamr_adjoint_release(h);
+        }
+        return ADJAMR_OK;
+    } catch (...) {
+        return ADJAMR_ENOMEM;
+    }
+}
+
+adjamr_status adjamr_regrid(adjamr_ctx *ctx, int base_level, int init)
+{
+    if (!ctx || base_level < 0 || base_level >= ctx->P.nlevels) return ADJAMR_EINVAL;
+    if (!ctx->have_medium) return ADJAMR_ESTATE;
+    try {
+        TRY(regrid_from(ctx, base_level, init));
+        CKR(ctx, cudaStreamSynchronize(ctx->s));
+        return ADJAMR_OK;
+    } catch (...) {
+        return ADJAMR_ENOMEM;
+    }
+}
+
+adjamr_status adjamr_advance_level(adjamr_ctx *ctx, int level, int nsteps)
+{
+    if (!ctx || level != 0 || nsteps < 0) return ADJAMR_EINVAL;
+    if (!ctx->have_medium) return ADJAMR_ESTATE;
+    try {
+        CKR(ctx, cudaMemsetAsync(ctx->d_cfl, 0, sizeof(unsigned long long), ctx->s));
+        for (int s = 0; s < nsteps; s++) TRY(step_level(ctx, 0));
+        unsigned long long bits = 0;
+        CKR(ctx, cudaMemcpyAsync(&bits, ctx->d_cfl, sizeof bits, cudaMemcpyDeviceToHost, ctx->s));
+        CKR(ctx, cudaStreamSynchronize(ctx->s));
+        harvest_timing(ctx);
+        double cfl;
+        std::memcpy(&cfl, &bits, sizeof cfl);
+        ctx->st.cfl_max_seen = std::fmax(ctx->st.cfl_max_seen, cfl);
+        if (cfl > ctx->P.cfl_max) {
+            ctx->err = "CFL number exceeded cfl_max";
+            return ADJAMR_ECFL;
+        }
+        return ADJAMR_OK;
+    } catch (...) {
+        return ADJAMR_ENOMEM;
+    }
+}
+
+adjamr_status adjamr_flag_cells(adjamr_ctx *ctx, int level, double tol, unsigned char *flags_out, long long *nflag)
+{
+    if (!ctx || level < 0 || level >= ctx->P.nlevels) return ADJAMR_EINVAL;
+    try {
+        Level &L = ctx->L[level];
+        unsigned char *d = nullptr;
+        CKR(ctx, dalloc(&d, (size_t)std::max<long long>(L.ninterior, 1), ctx->s));
+        long long n = 0;
+        adjamr_status st = flag_dense(ctx, level, tol, nullptr, d, &n);
+        if (st == ADJAMR_OK && flags_out && L.ninterior > 0) {
+            CKR(ctx, cudaMemcpyAsync(flags_out, d, (size_t)L.ninterior, cudaMemcpyDeviceToHost, ctx->s));
+            CKR(ctx, cudaStreamSynchronize(ctx->s));
+        }
+        dfree(d, ctx->s);
+        if (nflag) *nflag = n;
+        return st;
+    } catch (...) {
+        return ADJAMR_ENOMEM;
+    }
+}
+
+adjamr_status adjamr_integrate_functional(adjamr_ctx *ctx, const adjamr_target *t, double *J_out)
+{
+    if (!ctx || !t || !J_out) return ADJAMR_EINVAL;
+    try {
+        const adjamr_params &P = ctx->P;
+        std::vector<std::vector<long long>> idx(P.nlevels);
+        std::vector<std::vector<double>> area(P.nlevels);
+        size_t total = 0;
+        for (int l = 0; l < P.nlevels; l++) {
+            const Level &L = ctx->L[l];
+            if (L.patches.empty()) break;
+            int r = (l < P.nlevels - 1) ? P.ratio[l] : 1;
+            const Level *F = (l < P.nlevels - 1 && !ctx->L[l + 1].patches.empty()) ? &ctx->L[l + 1] : nullptr;
+            for (const HPatch &p : L.patches)
+                for (int j = 0; j < p.ny; j++)
+                    for (int i = 0; i < p.nx; i++) {
+                        int I = p.ilo + i, J = p.jlo + j;
+                        double xl = P.lo[0] + (double)I * L.dx, xr = P.lo[0] + (double)(I + 1) * L.dx;
+                        double ox = std::fmin(xr, t->x1) - std::fmax(xl, t->x0);
+                        if (!(ox > 0.0)) continue;
+                        double a = ox;
+                        if (P.dim == 2) {
+                            double yl = P.lo[1] + (double)J * L.dy, yr = P.lo[1] + (double)(J + 1) * L.dy;
+                            double oy = std::fmin(yr, t->y1) - std::fmax(yl, t->y0);
+                            if (!(oy > 0.0)) continue;
+                            a = ox * oy;
+                        }
+                        if (F && find_patch(*F, I * r, P.dim == 2 ? J * r : 0) >= 0) continue;
+                        idx[l].push_back(cell_of(ctx, p, i, j));
+                        area[l].push_back(a);
+                    }
+            total += idx[l].size();
+        }
+        if (ctx->fscratch_n < total + 1) {
+            dfree(ctx->d_fscratch, ctx->s);
+            CKR(ctx, dalloc(&ctx->d_fscratch, total + 1, ctx->s));
+            ctx->fscratch_n = total + 1;
+        }
+        size_t off = 0;
+        std::vector<long long *> tmp_i;
+        std::vector<double *> tmp_a;
+        for (int l = 0; l < P.nlevels; l++) {
+            if (idx[l].empty()) continue;
+            long long *di = nullptr;
+            double *da = nullptr;
+            CKR(ctx, upload(&di, idx[l], ctx->s));
+            CKR(ctx, upload(&da, area[l], ctx->s));
+            Level &L = ctx->L[l];
+            // terms of this level; the tree reduction runs once over all levels
+            CKR(ctx, launch_func_terms(di, da, (long long)idx[l].size(), L.q[L.cur], t->weight, ctx->d_fscratch + off,
+                                       ctx->s));
+            ctx->st.kernel_launches++;
+            off += idx[l].size();
+            tmp_i.push_back(di);
+            tmp_a.push_back(da);
+        }
+        CKR(ctx, launch_pairwise(ctx->d_fscratch, (long long)total, ctx->d_fout, ctx->s));
+        ctx->st.kernel_launches++;
+        for (long long *p : tmp_i) dfree(p, ctx->s);
+        for (double *p : tmp_a) dfree(p, ctx->s);
+        double J = 0.0;
+        CKR(ctx, cudaMemcpyAsync(&J, ctx->d_fout, sizeof J, cudaMemcpyDeviceToHost, ctx->s));
+        CKR(ctx, cudaStreamSynchronize(ctx->s));
+        *J_out = J;
+        return ADJAMR_OK;
+    } catch (...) {
+        return ADJAMR_ENOMEM;
+    }
+}
+
+}  // extern "C"
+
+extern "C" {
+
+adjamr_status adjamr_get_patches(adjamr_ctx *ctx, int level, adjamr_patch *out, int cap, int *n)
+{
+    if (!ctx || level < 0 || level >= ctx->P.nlevels) return ADJAMR_EINVAL;
+    const Level &L = ctx->L[level];
+    int np = (int)L.patches.size();
+    if (n) *n = np;
+    if (!out) return ADJAMR_OK;
+    if (cap < np) return ADJAMR_EINVAL;
+    for (int k = 0; k < np; k++) {
+        const HPatch &p = L.patches[k];
+        out[k].level = level;
+        out[k].ilo = p.ilo;
+        out[k].jlo = p.jlo;
+        out[k].nx = p.nx;
+        out[k].ny = p.ny;
+    }
+    return ADJAMR_OK;
+}
+
+adjamr_status adjamr_read_level(adjamr_ctx *ctx, int level, double *dst, size_t cap)
+{
+    if (!ctx || level < 0 || level >= ctx->P.nlevels || (!dst && cap)) return ADJAMR_EINVAL;
+    try {
+        return read_level_impl(ctx, level, dst, cap, false, nullptr);
+    } catch (...) {
+        return ADJAMR_ENOMEM;
+    }
+}
+
+adjamr_status adjamr_write_level(adjamr_ctx *ctx, int level, const double *src, size_t count)
+{
+    if (!ctx || level < 0 || level >= ctx->P.nlevels || (!src && count)) return ADJAMR_EINVAL;
+    try {
+        return read_level_impl(ctx, level, nullptr, count, true, src);
+    } catch (...) {
+        return ADJAMR_ENOMEM;
+    }
+}
+
+adjamr_status adjamr_fill_ghosts(adjamr_ctx *ctx, int level)
+{
+    if (!ctx || level < 0 || level >= ctx->P.nlevels) return ADJAMR_EINVAL;
+    int sub = 0;
+    if (level > 0) sub = (int)(ctx->L[level].nstep - ctx->L[level - 1].nstep * ctx->P.ratio[level - 1]);
+    TRY(ghost_fill(ctx, level, sub));
+    CKR(ctx, cudaStreamSynchronize(ctx->s));
+    return ADJAMR_OK;
+}
+
+adjamr_status adjamr_read_patch_ghosted(adjamr_ctx *ctx, int level, int k, double *q, double *med)
+{
+    if (!ctx || level < 0 || level >= ctx->P.nlevels) return ADJAMR_EINVAL;
+    Level &L = ctx->L[level];
+    if (k < 0 || k >= (int)L.patches.size()) return ADJAMR_EINVAL;
+    const HPatch &p = L.patches[k];
+    size_t n = (size_t)p.sx * p.sy;
+    for (int f = 0; f < ctx->m && q; f++)
+        CKR(ctx, cudaMemcpyAsync(q + f * n, L.q[L.cur] + (size_t)f * L.ncell + p.base, n * sizeof(double),
+                                 cudaMemcpyDeviceToHost, ctx->s));
+    for (int f = 0; f < ctx->nmed && med; f++)
+        CKR(ctx, cudaMemcpyAsync(med + f * n, L.med + (size_t)f * L.ncell + p.base, n * sizeof(double),
+                                 cudaMemcpyDeviceToHost, ctx->s));
+    CKR(ctx, cudaStreamSynchronize(ctx->s));
+    return ADJAMR_OK;
+}
+
+adjamr_status adjamr_step_level_only(adjamr_ctx *ctx, int level)
+{
+    if (!ctx || level < 0 || level >= ctx->P.nlevels) return ADJAMR_EINVAL;
+    if (!ctx->have_medium) return ADJAMR_ESTATE;
+    Level &L = ctx->L[level];
+    TRY(step_patches(ctx, level));
+    L.cur = 1 - L.cur;
+    L.nstep++;
+    CKR(ctx, cudaStreamSynchronize(ctx->s));
+    return ADJAMR_OK;
+}
+
+adjamr_status adjamr_get_stats(adjamr_ctx *ctx, adjamr_stats *out)
+{
+    if (!ctx || !out) return ADJAMR_EINVAL;
+    *out = ctx->st;
+    return ADJAMR_OK;
+}
+
+adjamr_status adjamr_set_timing(adjamr_ctx *ctx, int enable)
+{
+    if (!ctx) return ADJAMR_EINVAL;
+    ctx->timing = enable != 0;
+    return ADJAMR_OK;
+}
+
+adjamr_status adjamr_time_info(adjamr_ctx *ctx, double *dt0, int *nsteps)
+{
+    if (!ctx) return ADJAMR_EINVAL;
+    double dt = ctx->L[0].dt;
+    if (dt0) *dt0 = dt;
+    if (nsteps) *nsteps = (int)std::llround((ctx->P.tf - ctx->P.t0) / dt);
+    return ADJAMR_OK;
+}
+
+const char *adjamr_last_error(adjamr_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void adjamr_destroy(adjamr_ctx *ctx)
+{
+    if (!ctx) return;
+    for (int l = 0; l < ADJAMR_MAX_LEVELS; l++) {
+        free_level(ctx, ctx->L[l]);
+        dfree(ctx->L[l].d_med, ctx->s);
+    }
+    for (double *p : ctx->dense_dev) cudaFreeAsync(p, ctx->s);
+    dfree(ctx->d_flagbuf, ctx->s);
+    dfree(ctx->d_fscratch, ctx->s);
+    cudaStreamSynchronize(ctx->s);
+    if (ctx->d_cfl) cudaFree(ctx->d_cfl);
+    if (ctx->d_count) cudaFree(ctx->d_count);
+    if (ctx->d_fout) cudaFree(ctx->d_fout);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    for (cudaEvent_t e : ctx->tev) cudaEventDestroy(e);
+    if (ctx->adj) adjamr_adjoint_release(ctx->adj);
+    delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,128 @@
+// Internal structures of libadjamr: device descriptors shared by the host
+// hierarchy code (hierarchy.cpp) and the CUDA kernels (kernels_*.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "adjamr.h"
+
+namespace adjamr {
+
+constexpr double kGrav = 9.81;
+
+// Per-cell coefficient arrays ("aux"), hoisted medium-only quantities.
+// Edge coefficients are stored at the cell on the high side of the edge
+// (x-edge i-1/2 at cell i, y-edge j-1/2 at cell j).
+//  ACOUSTICS:          c, Z, 1/(Z_{i-1}+Z_i), 1/(Z_{j-1}+Z_j)
+//  ACOUSTICS_ADJOINT:  c, Z, izs_x, izs_y, 1/rho, K
+//  SW:                 ce_x, 1/ce_x, g*he_x, ce_y, 1/ce_y, g*he_y
+//  SW_ADJOINT:         ce_x, 1/ce_x, ce_y, 1/ce_y, g*hbar
+__host__ __device__ constexpr int naux_of(int eqn) { return eqn == 0 ? 4 : (eqn == 3 ? 5 : 6); }
+__host__ __device__ constexpr int nmed_of(int eqn) { return (eqn == 2 || eqn == 3) ? 1 : 2; }
+
+// A patch in a level arena.  Storage cell (si, sj) (si in [0, sx), sj in
+// [0, sy)) of field f lives at f*stride + base + sj*sx + si; interior cell
+// (i, j) is storage (i + 2, j + gy), gy = 2 in 2D and 0 in 1D.
+struct PatchDesc {
+    int ilo, jlo, nx, ny;
+    int sx, sy;
+    long long base;
+    double dtdx, dtdy, hx, hy;
+};
+
+// One tile of the step work-list.
+struct WorkItem {
+    int patch, x0, y0, pad;
+};
+
+// One ghost cell (or one new cell at regrid).
+//  kind 0: copy the cell `src` of the same arena (with sign flips);
+//  kind 1: minmod-limited linear interpolation from the coarser level around
+//          coarse cell `src` with neighbours cxm, cxp, cym, cyp (each with
+//          its own boundary sign), fine offset (mx, my) inside the coarse cell;
+//  kind 2 (regrid only): copy cell `src` of the OLD arena of this level.
+// signs: bits 0,1 = negate components 1,2 of the result; bits 2+2k, 3+2k =
+// negate components 1,2 of coarse reference k (0 centre, 1 xm, 2 xp, 3 ym, 4 yp).
+struct GhostDesc {
+    long long dst;
+    long long src, cxm, cxp, cym, cyp;
+    int kind, signs;
+    int mx, my;
+};
+
+// Average-down of one coarse cell: dst in the coarse arena, src = fine child
+// (0, 0) in the fine arena, fsx = fine row pitch.
+struct AvgDesc {
+    long long dst, src;
+    int fsx, pad;
+};
+
+// Aux-fill of one storage cell of a new patch: arena index and the global
+// level index of the cell (may lie outside the domain: boundary-mapped on
+// the device).
+struct AuxDesc {
+    long long idx;
+    int I, J;
+};
+
+struct MediumDev {
+    int kind, axis, nl, nmed;
+    double iface[32], f0[32], f1[32];
+    const double *dense;   // [nmed][M][N] of this level (DENSE)
+    int N, M;
+};
+
+struct LevelGeom {
+    int dim, N, M;
+    double lo0, lo1, dx, dy;
+    int bc[4];
+};
+
+// ---- kernel launchers (kernels_step.cu / kernels_amr.cu) ----
+cudaError_t launch_step(int dim, int eqn, int tx, int ty, const double *q, double *qn, const double *aux,
+                        long long stride, const PatchDesc *patches, const WorkItem *work, int nwork, int grid,
+                        unsigned long long *cfl_bits, cudaStream_t s);
+int step_occupancy(int dim, int eqn, int tx, int ty);
+
+cudaError_t launch_ghost_fill(int dim, int m, const GhostDesc *g, long long n, double *qf, long long sf,
+                              const double *qc_old, const double *qc_new, long long sc, int k, int r,
+                              cudaStream_t s);
+cudaError_t launch_regrid_init(int dim, int m, const GhostDesc *g, long long n, double *qf, long long sf,
+                               const double *qold, long long so, const double *qc, long long sc, int r,
+                               cudaStream_t s);
+cudaError_t launch_average_down(int dim, int m, const AvgDesc *a, long long n, const double *qf, long long sf,
+                                double *qc, long long sc, int r, cudaStream_t s);
+// Fill primary medium (med) and derived coefficients (aux) of the listed
+// storage cells of one level.  mdev: device copy of the level's medium.
+cudaError_t launch_aux_fill(int eqn, int dim, const AuxDesc *d, long long n, double *aux, double *med,
+                            long long stride, const MediumDev *mdev, LevelGeom geom, cudaStream_t s);
+
+struct FlagArgs {
+    const double *q;
+    long long stride;
+    const PatchDesc *patches;
+    const long long *cell_prefix;   // [np+1] interior-cell prefix over patches
+    int np, dim, m, mode;
+    long long ncells;
+    double lo0, lo1, hi0, hi1, dx, dy;
+    const double *snaps;            // [S][m][ay][ax]
+    const unsigned char *wet;       // [ay][ax]
+    int ax, ay, nlo, nhi, S;
+    double t, T, t0, dts, tol;
+    unsigned char *flags_patch;     // [ncells] (may be null)
+    unsigned char *flags_dense;     // [M][N] of the level (may be null)
+    int N;
+    unsigned long long *count;
+};
+cudaError_t launch_flag(const FlagArgs &a, cudaStream_t s);
+
+// terms weight*(q0*area) of the functional into out[0..n)
+cudaError_t launch_func_terms(const long long *idx, const double *area, long long n, const double *q, double weight,
+                              double *out, cudaStream_t s);
+// fixed pairwise tree sum of a[0..n) (destroys a) into *out
+cudaError_t launch_pairwise(double *a, long long n, double *out, cudaStream_t s);
+
+cudaError_t launch_gather_interior(int m, const long long *map, long long n, const double *q, long long stride,
+                                   double *dst, cudaStream_t s);
+
+}  // namespace adjamr

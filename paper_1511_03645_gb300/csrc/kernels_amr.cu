@@ -1,0 +1,428 @@
+// AMR kernels (Sec. 3 and Sec. 4), FP64, sm_103a:
+//  - ghost fill: same-level copy / physical boundary (via a boundary-mapped
+//    source cell) / coarse space-time interpolation (linear in time between
+//    the coarse old and new states, minmod-limited linear in space);
+//  - regrid init of new patches (copy from the old arena or space
+//    interpolation from the coarser level);
+//  - averaging fine -> coarse;
+//  - medium coefficients of new patches;
+//  - adjoint flagging (bilinear interpolation in space; bracketing
+//    snapshots or linear-in-time window maximum) with a warp-ballot count;
+//  - the functional J with a fixed pairwise summation tree.
+// Operation order follows the canonical operations (compiled with
+// --fmad=false), as does the CPU oracle.
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace adjamr {
+namespace {
+
+constexpr int kT = 256;
+
+__device__ __forceinline__ double minmod(double a, double b)
+{
+    if (a > 0.0 && b > 0.0) return fmin(a, b);
+    if (a < 0.0 && b < 0.0) return fmax(a, b);
+    return 0.0;
+}
+
+__device__ __forceinline__ double sgn(double v, int signs, int comp, int ref)
+{
+    // comp 0 is never flipped; comps 1, 2 by bits (2*ref + comp - 1)
+    if (comp == 0) return v;
+    return ((signs >> (2 * ref + comp - 1)) & 1) ? -v : v;
+}
+
+// value of field f at coarse reference `ref` (cell index c), at time k/r
+__device__ __forceinline__ double coarse_val(const double *__restrict__ qo, const double *__restrict__ qn_,
+                                             long long sc, long long c, int f, int k, int r, int signs, int ref)
+{
+    double v0 = qo[(long long)f * sc + c];
+    double v;
+    if (k == 0) {
+        v = v0;
+    } else {
+        double th = (double)k / (double)r;
+        double v1 = qn_[(long long)f * sc + c];
+        v = (1.0 - th) * v0 + th * v1;
+    }
+    return sgn(v, signs, f, ref + 1);
+}
+
+__device__ __forceinline__ double interp_field(const GhostDesc &g, const double *__restrict__ qo,
+                                               const double *__restrict__ qn_, long long sc, int f, int k, int r,
+                                               int dim)
+{
+    double fx = (double)(2 * g.mx + 1 - r) / (double)(2 * r);
+    double q0 = coarse_val(qo, qn_, sc, g.src, f, k, r, g.signs, 0);
+    double qxm = coarse_val(qo, qn_, sc, g.cxm, f, k, r, g.signs, 1);
+    double qxp = coarse_val(qo, qn_, sc, g.cxp, f, k, r, g.signs, 2);
+    double sx = minmod(qxp - q0, q0 - qxm);
+    double v = q0 + sx * fx;
+    if (dim == 2) {
+        double fy = (double)(2 * g.my + 1 - r) / (double)(2 * r);
+        double qym = coarse_val(qo, qn_, sc, g.cym, f, k, r, g.signs, 3);
+        double qyp = coarse_val(qo, qn_, sc, g.cyp, f, k, r, g.signs, 4);
+        double sy = minmod(qyp - q0, q0 - qym);
+        v = v + sy * fy;
+    }
+    return v;
+}
+
+__global__ void k_ghost_fill(int dim, int m, const GhostDesc *__restrict__ gd, long long n, double *qf, long long sf,
+                             const double *__restrict__ qo, const double *__restrict__ qn_, long long sc, int k,
+                             int r)
+{
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    GhostDesc g = gd[t];
+    for (int f = 0; f < m; f++) {
+        double v;
+        if (g.kind == 0) v = qf[(long long)f * sf + g.src];
+        else v = interp_field(g, qo, qn_, sc, f, k, r, dim);
+        qf[(long long)f * sf + g.dst] = sgn(v, g.signs, f, 0);
+    }
+}
+
+__global__ void k_regrid_init(int dim, int m, const GhostDesc *__restrict__ gd, long long n, double *qf, long long sf,
+                              const double *__restrict__ qold, long long so, const double *__restrict__ qc,
+                              long long sc, int r)
+{
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    GhostDesc g = gd[t];
+    for (int f = 0; f < m; f++) {
+        double v;
+        if (g.kind == 2) v = qold[(long long)f * so + g.src];
+        else v = interp_field(g, qc, qc, sc, f, 0, r, dim);
+        qf[(long long)f * sf + g.dst] = v;
+    }
+}
+
+__global__ void k_average_down(int dim, int m, const AvgDesc *__restrict__ ad, long long n,
+                               const double *__restrict__ qf, long long sf, double *qc, long long sc, int r)
+{
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    AvgDesc a = ad[t];
+    int rr = (dim == 2) ? r : 1;
+    double inv = 1.0 / (double)(r * rr);
+    for (int f = 0; f < m; f++) {
+        const double *src = qf + (long long)f * sf + a.src;
+        double s = 0.0;
+        for (int jj = 0; jj < rr; jj++)
+            for (int ii = 0; ii < r; ii++) s = s + src[(long long)jj * a.fsx + ii];
+        qc[(long long)f * sc + a.dst] = s * inv;
+    }
+}
+
+// boundary map of a level index (no signs: the medium is even)
+// (the final clamp only matters for the left neighbour of the outermost ghost
+// cell on grids narrower than 3 cells, a value no step reads)
+__device__ __forceinline__ int map_index(int I, int N, int bclo, int bchi)
+{
+    if (I < 0) {
+        if (bclo == ADJAMR_BC_EXTRAP) I = 0;
+        else if (bclo == ADJAMR_BC_WALL) I = -1 - I;
+        else I = I + N;
+    } else if (I >= N) {
+        if (bchi == ADJAMR_BC_EXTRAP) I = N - 1;
+        else if (bchi == ADJAMR_BC_WALL) I = 2 * N - 1 - I;
+        else I = I - N;
+    }
+    return min(max(I, 0), N - 1);
+}
+
+__device__ void medium_at(const MediumDev &md, const LevelGeom &g, int I, int J, double *out)
+{
+    I = map_index(I, g.N, g.bc[0], g.bc[1]);
+    if (g.dim == 2) J = map_index(J, g.M, g.bc[2], g.bc[3]);
+    else J = 0;
+    if (md.kind == ADJAMR_MEDIUM_LAYERED) {
+        double c = (md.axis == 0) ? g.lo0 + ((double)I + 0.5) * g.dx : g.lo1 + ((double)J + 0.5) * g.dy;
+        int k = 0;
+        while (k < md.nl - 1 && md.iface[k] <= c) k++;
+        out[0] = md.f0[k];
+        out[1] = md.f1[k];
+    } else {
+        long long idx = (long long)J * md.N + I;
+        out[0] = md.dense[idx];
+        if (md.nmed > 1) out[1] = md.dense[(long long)md.N * md.M + idx];
+    }
+}
+
+__global__ void k_aux_fill(int eqn, int dim, const AuxDesc *__restrict__ ad, long long n, double *aux, double *med,
+                           long long stride, const MediumDev *__restrict__ mdp, LevelGeom g)
+{
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const MediumDev &md = *mdp;
+    AuxDesc d = ad[t];
+    double c0[2] = {0, 0}, cl[2] = {0, 0}, cb[2] = {0, 0};
+    medium_at(md, g, d.I, d.J, c0);
+    medium_at(md, g, d.I - 1, d.J, cl);
+    if (dim == 2) medium_at(md, g, d.I, d.J - 1, cb);
+    med[d.idx] = c0[0];
+    if (eqn == 0 || eqn == 1) med[stride + d.idx] = c0[1];
+    if (eqn == 0 || eqn == 1) {
+        double c = sqrt(c0[1] / c0[0]);
+        double Z = c0[0] * c;
+        double ccl = sqrt(cl[1] / cl[0]);
+        double Zl = cl[0] * ccl;
+        aux[d.idx] = c;
+        aux[stride + d.idx] = Z;
+        aux[2 * stride + d.idx] = 1.0 / (Zl + Z);
+        if (dim == 2) {
+            double ccb = sqrt(cb[1] / cb[0]);
+            double Zb = cb[0] * ccb;
+            aux[3 * stride + d.idx] = 1.0 / (Zb + Z);
+        } else {
+            aux[3 * stride + d.idx] = 0.0;
+        }
+        if (eqn == 1) {
+            aux[4 * stride + d.idx] = 1.0 / c0[0];
+            aux[5 * stride + d.idx] = c0[1];
+        }
+    } else {
+        double hx = 0.5 * (cl[0] + c0[0]);
+        double ghx = kGrav * hx;
+        double cex = sqrt(ghx);
+        double hy = (dim == 2) ? 0.5 * (cb[0] + c0[0]) : hx;
+        double ghy = kGrav * hy;
+        double cey = sqrt(ghy);
+        if (eqn == 2) {
+            aux[d.idx] = cex;
+            aux[stride + d.idx] = 1.0 / cex;
+            aux[2 * stride + d.idx] = ghx;
+            aux[3 * stride + d.idx] = cey;
+            aux[4 * stride + d.idx] = 1.0 / cey;
+            aux[5 * stride + d.idx] = ghy;
+        } else {
+            aux[d.idx] = cex;
+            aux[stride + d.idx] = 1.0 / cex;
+            aux[2 * stride + d.idx] = cey;
+            aux[3 * stride + d.idx] = 1.0 / cey;
+            aux[4 * stride + d.idx] = kGrav * c0[0];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- flagging
+__device__ __forceinline__ void bilinear_setup(double x, double lo, double hi, int na, int &a, double &w)
+{
+    double dxa = (hi - lo) / (double)na;
+    double xi = (x - lo) / dxa - 0.5;
+    xi = fmin(fmax(xi, 0.0), (double)(na - 1));
+    a = (int)floor(xi);
+    if (a > na - 2) a = na - 2;
+    if (a < 0) a = 0;
+    w = xi - (double)a;
+}
+
+__device__ __forceinline__ double adj_interp(const FlagArgs &A, int n, int f, int a, double wx, int b, double wy)
+{
+    const double *s = A.snaps + ((long long)n * A.m + f) * (long long)A.ax * A.ay;
+    if (A.dim == 1) {
+        if (A.ax == 1) return s[0];
+        return (1.0 - wx) * s[a] + wx * s[a + 1];
+    }
+    double omx = 1.0 - wx;
+    long long r0 = (long long)b * A.ax, r1 = (long long)(b + 1) * A.ax;
+    double v0 = omx * s[r0 + a] + wx * s[r0 + a + 1];
+    double v1 = omx * s[r1 + a] + wx * s[r1 + a + 1];
+    return (1.0 - wy) * v0 + wy * v1;
+}
+
+__device__ __forceinline__ double snap_time(const FlagArgs &A, int n) { return A.t0 + (double)n * A.dts; }
+
+__global__ void k_flag(FlagArgs A)
+{
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    bool flagged = false;
+    if (t < A.ncells) {
+        // patch containing interior cell t (binary search on the prefix)
+        int lo = 0, hi = A.np - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (A.cell_prefix[mid] <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        const PatchDesc P = A.patches[lo];
+        long long k = t - A.cell_prefix[lo];
+        int j = (int)(k / P.nx), i = (int)(k - (long long)j * P.nx);
+        int gy = (A.dim == 2) ? 2 : 0;
+        long long cell = P.base + (long long)(j + gy) * P.sx + (i + 2);
+        int I = P.ilo + i, J = P.jlo + j;
+        double x = A.lo0 + ((double)I + 0.5) * A.dx;
+        double y = (A.dim == 2) ? A.lo1 + ((double)J + 0.5) * A.dy : 0.0;
+        double Q[3];
+        for (int f = 0; f < A.m; f++) Q[f] = A.q[(long long)f * A.stride + cell];
+        double val = 0.0;
+        if (A.S >= 2) {
+            int a, b = 0;
+            double wx, wy = 0.0;
+            bilinear_setup(x, A.lo0, A.hi0, A.ax, a, wx);
+            if (A.dim == 2) bilinear_setup(y, A.lo1, A.hi1, A.ay, b, wy);
+            if (A.mode == ADJAMR_FLAG_BRACKET_MAX) {
+                for (int n = A.nlo; n <= A.nhi; n++) {
+                    double d = 0.0;
+                    for (int f = 0; f < A.m; f++) {
+                        double av = adj_interp(A, n, f, a, wx, b, wy);
+                        d = (f == 0) ? av * Q[0] : d + av * Q[f];
+                    }
+                    val = fmax(val, fabs(d));
+                }
+            } else {
+                // q^ linear in time: values at t, at T, and snapshots strictly inside
+                for (int pass = 0; pass < 2; pass++) {
+                    double tau = pass == 0 ? A.t : A.T;
+                    int n = 0;
+                    while (n < A.S - 2 && snap_time(A, n + 1) <= tau) n++;
+                    double w = (tau - snap_time(A, n)) / A.dts;
+                    double d = 0.0;
+                    for (int f = 0; f < A.m; f++) {
+                        double a0 = adj_interp(A, n, f, a, wx, b, wy), a1 = adj_interp(A, n + 1, f, a, wx, b, wy);
+                        double av = (1.0 - w) * a0 + w * a1;
+                        d = (f == 0) ? av * Q[0] : d + av * Q[f];
+                    }
+                    val = fmax(val, fabs(d));
+                }
+                for (int n = 0; n < A.S; n++) {
+                    double tn = snap_time(A, n);
+                    if (!(tn > A.t && tn < A.T)) continue;
+                    double d = 0.0;
+                    for (int f = 0; f < A.m; f++) {
+                        double av = adj_interp(A, n, f, a, wx, b, wy);
+                        d = (f == 0) ? av * Q[0] : d + av * Q[f];
+                    }
+                    val = fmax(val, fabs(d));
+                }
+            }
+            // dry adjoint cell: the inner product is zero (Sec. 5.3)
+            double dxa = (A.hi0 - A.lo0) / (double)A.ax;
+            int ac = (int)floor((x - A.lo0) / dxa);
+            ac = min(max(ac, 0), A.ax - 1);
+            int bc = 0;
+            if (A.dim == 2) {
+                double dya = (A.hi1 - A.lo1) / (double)A.ay;
+                bc = (int)floor((y - A.lo1) / dya);
+                bc = min(max(bc, 0), A.ay - 1);
+            }
+            if (A.wet && !A.wet[(long long)bc * A.ax + ac]) val = 0.0;
+        }
+        flagged = val > A.tol;
+        if (A.flags_patch) A.flags_patch[t] = flagged ? 1 : 0;
+        if (A.flags_dense) A.flags_dense[(long long)J * A.N + I] = flagged ? 1 : 0;
+    }
+    unsigned bal = __ballot_sync(0xffffffffu, flagged);
+    if ((threadIdx.x & 31) == 0 && bal) atomicAdd(A.count, (unsigned long long)__popc(bal));
+}
+
+// ---------------------------------------------------------------- functional
+__global__ void k_func_terms(const long long *__restrict__ idx, const double *__restrict__ area, long long n,
+                             const double *__restrict__ q, double weight, double *out)
+{
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) out[t] = weight * (q[idx[t]] * area[t]);
+}
+
+// one CTA: repeated pairwise passes a[i] = a[2i] + a[2i+1], odd tail carried.
+// Chunks of blockDim pairs are processed with a uniform trip count, so every
+// thread meets every barrier; within a chunk all pairs are read before any
+// result is written (chunk c writes [cB, (c+1)B), later chunks read >= 2(c+1)B).
+__global__ void k_pairwise(double *a, long long n, double *out)
+{
+    const long long B = blockDim.x;
+    while (n > 1) {
+        long long h = n / 2;
+        for (long long base = 0; base < h; base += B) {
+            long long i = base + threadIdx.x;
+            double s = 0.0;
+            if (i < h) s = a[2 * i] + a[2 * i + 1];
+            __syncthreads();
+            if (i < h) a[i] = s;
+            __syncthreads();
+        }
+        if (threadIdx.x == 0 && (n & 1)) a[h] = a[n - 1];
+        __syncthreads();
+        n = (n + 1) / 2;
+    }
+    if (threadIdx.x == 0) *out = (n == 1) ? a[0] : 0.0;
+}
+
+__global__ void k_gather(int m, const long long *__restrict__ map, long long n, const double *__restrict__ q,
+                         long long stride, double *dst)
+{
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    for (int f = 0; f < m; f++) dst[(long long)f * n + t] = q[(long long)f * stride + map[t]];
+}
+
+inline unsigned nblk(long long n) { return (unsigned)((n + kT - 1) / kT); }
+
+}  // namespace
+
+cudaError_t launch_ghost_fill(int dim, int m, const GhostDesc *g, long long n, double *qf, long long sf,
+                              const double *qc_old, const double *qc_new, long long sc, int k, int r, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_ghost_fill<<<nblk(n), kT, 0, s>>>(dim, m, g, n, qf, sf, qc_old, qc_new, sc, k, r);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_regrid_init(int dim, int m, const GhostDesc *g, long long n, double *qf, long long sf,
+                               const double *qold, long long so, const double *qc, long long sc, int r,
+                               cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_regrid_init<<<nblk(n), kT, 0, s>>>(dim, m, g, n, qf, sf, qold, so, qc, sc, r);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_average_down(int dim, int m, const AvgDesc *a, long long n, const double *qf, long long sf,
+                                double *qc, long long sc, int r, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_average_down<<<nblk(n), kT, 0, s>>>(dim, m, a, n, qf, sf, qc, sc, r);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_aux_fill(int eqn, int dim, const AuxDesc *d, long long n, double *aux, double *med,
+                            long long stride, const MediumDev *mdev, LevelGeom geom, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_aux_fill<<<nblk(n), kT, 0, s>>>(eqn, dim, d, n, aux, med, stride, mdev, geom);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flag(const FlagArgs &a, cudaStream_t s)
+{
+    if (a.ncells <= 0) return cudaSuccess;
+    k_flag<<<nblk(a.ncells), kT, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_func_terms(const long long *idx, const double *area, long long n, const double *q, double weight,
+                              double *out, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_func_terms<<<nblk(n), kT, 0, s>>>(idx, area, n, q, weight, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pairwise(double *a, long long n, double *out, cudaStream_t s)
+{
+    k_pairwise<<<1, 1024, 0, s>>>(a, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_interior(int m, const long long *map, long long n, const double *q, long long stride,
+                                   double *dst, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_gather<<<nblk(n), kT, 0, s>>>(m, map, n, q, stride, dst);
+    return cudaGetLastError();
+}
+
+}  // namespace adjamr

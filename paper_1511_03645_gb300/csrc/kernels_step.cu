@@ -1,0 +1,559 @@
+// High-resolution wave-propagation step (Sec. 3; LeVeque 1997 unsplit
+// method with transverse Riemann problems), FP64, sm_103a.
+//
+// One CTA advances one tile of one patch from a tile work-list.  The tile's
+// state and medium coefficients plus a 2-cell halo are staged in shared
+// memory; every edge quantity of the tile (waves, fluctuations, limited
+// corrections, transverse terms) lives in shared memory; the new state is
+// written once.  The same kernel serves a one-launch-per-level work-list, a
+// persistent grid looping over the work-list, and one launch per patch.
+//
+// Operation order follows the canonical operations of the design record
+// exactly (compiled with --fmad=false): the CPU oracle evaluates the same
+// IEEE operations in the same order, so results agree bit for bit.
+//
+// Systems: 0 acoustics (wave form, eigenvectors of A: (-Z_l,1) at -c_l,
+// (Z_r,1) at +c_r), 1 adjoint acoustics (f-wave, eigenvectors of -A^T:
+// (1,Z_l) at -c_l, (1,-Z_r) at +c_r), 2 linearised shallow water (f-wave,
+// df = (d mu, g h_e d eta), eigenvectors (1,-+c_e)), 3 adjoint shallow water
+// (f-wave, eigenvectors (c_e,1) at -c_e, (-c_e,1) at +c_e).
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace adjamr {
+namespace {
+
+constexpr int kThreads = 256;
+
+// Edge coefficients gathered from the per-cell aux arrays.
+struct Edge {
+    double s1, s2;       // speeds of the left- and right-going waves
+    double Zl, Zr, izs;  // acoustics
+    double ce, ice, ghe; // shallow water
+};
+
+// aux index layout per system (see internal.h)
+template <int EQN, int DIR>
+__device__ __forceinline__ void load_edge(const double *__restrict__ sa, int stride, int l, int r, Edge &e)
+{
+    if constexpr (EQN == 0 || EQN == 1) {
+        e.s1 = -sa[l];               // c at left cell
+        e.s2 = sa[r];                // c at right cell
+        e.Zl = sa[stride + l];
+        e.Zr = sa[stride + r];
+        e.izs = sa[(2 + DIR) * stride + r];
+    } else if constexpr (EQN == 2) {
+        e.ce = sa[(3 * DIR) * stride + r];
+        e.ice = sa[(3 * DIR + 1) * stride + r];
+        e.ghe = sa[(3 * DIR + 2) * stride + r];
+        e.s1 = -e.ce;
+        e.s2 = e.ce;
+    } else {
+        e.ce = sa[(2 * DIR) * stride + r];
+        e.ice = sa[(2 * DIR + 1) * stride + r];
+        e.s1 = -e.ce;
+        e.s2 = e.ce;
+    }
+}
+
+// eigen-decomposition of d = (d0, dn) at the edge (canonical order)
+template <int EQN>
+__device__ __forceinline__ void decompose(const Edge &e, double d0, double dn, double *w1, double *w2)
+{
+    if constexpr (EQN == 0) {
+        double a1 = (e.Zr * dn - d0) * e.izs;
+        double a2 = (d0 + e.Zl * dn) * e.izs;
+        w1[0] = -(e.Zl * a1);
+        w1[1] = a1;
+        w2[0] = e.Zr * a2;
+        w2[1] = a2;
+    } else if constexpr (EQN == 1) {
+        double b1 = (e.Zr * d0 + dn) * e.izs;
+        double b2 = (e.Zl * d0 - dn) * e.izs;
+        w1[0] = b1;
+        w1[1] = e.Zl * b1;
+        w2[0] = b2;
+        w2[1] = -(e.Zr * b2);
+    } else if constexpr (EQN == 2) {
+        double b1 = (d0 - dn * e.ice) * 0.5;
+        double b2 = (d0 + dn * e.ice) * 0.5;
+        w1[0] = b1;
+        w1[1] = -(e.ce * b1);
+        w2[0] = b2;
+        w2[1] = e.ce * b2;
+    } else {
+        double b1 = (dn + d0 * e.ice) * 0.5;
+        double b2 = (dn - d0 * e.ice) * 0.5;
+        w1[0] = e.ce * b1;
+        w1[1] = b1;
+        w2[0] = -(e.ce * b2);
+        w2[1] = b2;
+    }
+}
+
+// jump (wave form) or flux difference (f-wave forms) across the edge;
+// NRM = index of the normal component (1 = u, 2 = v); DIR selects aux.
+template <int EQN>
+__device__ __forceinline__ void edge_jump(const Edge &e, const double *__restrict__ sa, int stride, int l, int r,
+                                          double ql0, double qln, double qr0, double qrn, double &d0, double &dn)
+{
+    if constexpr (EQN == 0) {
+        d0 = qr0 - ql0;
+        dn = qrn - qln;
+    } else if constexpr (EQN == 2) {
+        d0 = qrn - qln;
+        dn = e.ghe * (qr0 - ql0);
+    } else if constexpr (EQN == 1) {
+        double fl0 = -(sa[4 * stride + l] * qln), fln = -(sa[5 * stride + l] * ql0);
+        double fr0 = -(sa[4 * stride + r] * qrn), frn = -(sa[5 * stride + r] * qr0);
+        d0 = fr0 - fl0;
+        dn = frn - fln;
+    } else {
+        double fl0 = -(sa[4 * stride + l] * qln), fln = -ql0;
+        double fr0 = -(sa[4 * stride + r] * qrn), frn = -qr0;
+        d0 = fr0 - fl0;
+        dn = frn - fln;
+    }
+}
+
+__device__ __forceinline__ double mc_phi(double w0, double w1, double u0, double u1)
+{
+    double wn = w0 * w0 + w1 * w1;
+    if (wn == 0.0) return 0.0;
+    double dot = u0 * w0 + u1 * w1;
+    double th = dot / wn;
+    return fmax(0.0, fmin(fmin(0.5 * (1.0 + th), 2.0), 2.0 * th));
+}
+
+template <int EQN>
+__device__ __forceinline__ double corr_coef(double s, double dtd)
+{
+    double a = fabs(s);
+    if constexpr (EQN == 0) {
+        return a * (1.0 - dtd * a);
+    } else {
+        double t = 1.0 - dtd * a;
+        return (s < 0.0) ? -t : t;
+    }
+}
+
+__device__ __forceinline__ void cfl_reduce(double c, unsigned long long *cfl_bits)
+{
+    for (int o = 16; o > 0; o >>= 1) c = fmax(c, __shfl_xor_sync(0xffffffffu, c, o));
+    if ((threadIdx.x & 31) == 0 && c > 0.0) atomicMax(cfl_bits, (unsigned long long)__double_as_longlong(c));
+}
+
+// ---------------------------------------------------------------- 2D
+template <int EQN, int TX, int TY>
+struct Smem2D {
+    static constexpr int NA = naux_of(EQN);
+    static constexpr int PX = TX + 4, PY = TY + 4;          // staged tile + halo
+    static constexpr int XEX = TX + 3, XEY = TY + 2;        // x-edges [-1, tx+1] x rows [-1, ty]
+    static constexpr int YEX = TX + 2, YEY = TY + 3;        // y-edges: cols [-1, tx] x [-1, ty+1]
+    static constexpr int XNX = TX + 1, XNY = TY + 2;        // Fn: x-edges [0, tx] x rows [-1, ty]
+    static constexpr int YNX = TX + 2, YNY = TY + 1;        // Gn: cols [-1, tx] x y-edges [0, ty]
+    static constexpr int nQ = 3 * PX * PY, nA = NA * PX * PY;
+    static constexpr int nXW = 4 * XEX * XEY, nXF = 4 * XEX * XEY;
+    static constexpr int nYW = 4 * YEX * YEY, nYF = 4 * YEX * YEY;
+    static constexpr int nXN = 2 * XNX * XNY, nYN = 2 * YNX * YNY;
+    static constexpr int total = nQ + nA + nXW + nXF + nYW + nYF + nXN + nYN;
+    static constexpr size_t bytes = sizeof(double) * (size_t)total;
+};
+
+template <int EQN, int TX, int TY>
+__global__ void __launch_bounds__(kThreads) k_step2d(const double *__restrict__ q, double *__restrict__ qn,
+                                                     const double *__restrict__ aux, long long stride,
+                                                     const PatchDesc *__restrict__ patches,
+                                                     const WorkItem *__restrict__ work, int nwork,
+                                                     unsigned long long *cfl_bits)
+{
+    using S = Smem2D<EQN, TX, TY>;
+    extern __shared__ double sm[];
+    double *sQ = sm;
+    double *sA = sQ + S::nQ;
+    double *XW = sA + S::nA;   // waves w1_0, w1_n, w2_0, w2_n at x-edges; later SX + FF
+    double *XF = XW + S::nXW;  // fluctuations am_0, am_n, ap_0, ap_n at x-edges
+    double *YW = XF + S::nXF;  // same at y-edges; later SY + GG
+    double *YF = YW + S::nYW;
+    double *XN = YF + S::nYF;  // Fn (2 comps)
+    double *YN = XN + S::nXN;  // Gn (2 comps)
+    constexpr int PX = S::PX, PY = S::PY, PS = PX * PY;
+    constexpr int XEX = S::XEX, XEY = S::XEY, XES = XEX * XEY;
+    constexpr int YEX = S::YEX, YEY = S::YEY, YES = YEX * YEY;
+    constexpr int XNX = S::XNX, XNS = XNX * S::XNY;
+    constexpr int YNX = S::YNX, YNS = YNX * S::YNY;
+    // reuse of the wave arrays after the limiter phase
+    double *SX = XW;                       // [2][TY+2][TX]   cells [0,tx) x rows [-1,ty]
+    double *FF = XW + 2 * (TY + 2) * TX;   // [2][TY][TX+1]   x-edges [0,tx] x rows [0,ty)
+    double *SY = YW;                       // [2][TY][TX+2]   cols [-1,tx] x rows [0,ty)
+    double *GG = YW + 2 * TY * (TX + 2);   // [2][TY+1][TX]   cols [0,tx) x y-edges [0,ty]
+    constexpr int SXS = (TY + 2) * TX, FFS = TY * (TX + 1), SYS = TY * (TX + 2), GGS = (TY + 1) * TX;
+
+    const int tid = threadIdx.x;
+    double cfl = 0.0;
+    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+        const WorkItem wi = work[w];
+        const PatchDesc P = patches[wi.patch];
+        const int x0 = wi.x0, y0 = wi.y0;
+        const int tx = min(TX, P.nx - x0), ty = min(TY, P.ny - y0);
+        const int rx = tx + 4, ry = ty + 4;
+        const double dtdx = P.dtdx, dtdy = P.dtdy, hx = P.hx, hy = P.hy;
+        // ---- stage state and coefficients (tile + 2-cell halo) ----
+        {
+            const long long gb = P.base + (long long)y0 * P.sx + x0;
+            const int nrow = rx;
+            for (int k = tid; k < (3 + S::NA) * ry * nrow; k += kThreads) {
+                int f = k / (ry * nrow), rem = k - f * ry * nrow;
+                int r = rem / nrow, c = rem - r * nrow;
+                long long g = gb + (long long)r * P.sx + c;
+                if (f < 3) sQ[f * PS + r * PX + c] = q[(long long)f * stride + g];
+                else sA[(f - 3) * PS + r * PX + c] = aux[(long long)(f - 3) * stride + g];
+            }
+        }
+        __syncthreads();
+        // ---- normal Riemann problems at x-edges and y-edges ----
+        for (int k = tid; k < (tx + 3) * (ty + 2) + (tx + 2) * (ty + 3); k += kThreads) {
+            if (k < (tx + 3) * (ty + 2)) {
+                int er = k / (tx + 3), ec = k - er * (tx + 3);     // row ry = er-1, edge ex = ec-1
+                int l = (er + 1) * PX + ec, r = l + 1;             // cells (ex-1, ry) and (ex, ry) staged
+                Edge e;
+                load_edge<EQN, 0>(sA, PS, l, r, e);
+                double d0, dn, w1[2], w2[2];
+                edge_jump<EQN>(e, sA, PS, l, r, sQ[l], sQ[PS + l], sQ[r], sQ[PS + r], d0, dn);
+                decompose<EQN>(e, d0, dn, w1, w2);
+                int o = er * XEX + ec;
+                XW[o] = w1[0]; XW[XES + o] = w1[1]; XW[2 * XES + o] = w2[0]; XW[3 * XES + o] = w2[1];
+                if constexpr (EQN == 0) {
+                    XF[o] = e.s1 * w1[0]; XF[XES + o] = e.s1 * w1[1];
+                    XF[2 * XES + o] = e.s2 * w2[0]; XF[3 * XES + o] = e.s2 * w2[1];
+                } else {
+                    XF[o] = w1[0]; XF[XES + o] = w1[1]; XF[2 * XES + o] = w2[0]; XF[3 * XES + o] = w2[1];
+                }
+            } else {
+                int kk = k - (tx + 3) * (ty + 2);
+                int er = kk / (tx + 2), ec = kk - er * (tx + 2);  // y-edge ey = er-1, column cx = ec-1
+                int l = er * PX + ec + 1, r = l + PX;              // cells (cx, ey-1) and (cx, ey)
+                Edge e;
+                load_edge<EQN, 1>(sA, PS, l, r, e);
+                double d0, dn, w1[2], w2[2];
+                edge_jump<EQN>(e, sA, PS, l, r, sQ[l], sQ[2 * PS + l], sQ[r], sQ[2 * PS + r], d0, dn);
+                decompose<EQN>(e, d0, dn, w1, w2);
+                int o = er * YEX + ec;
+                YW[o] = w1[0]; YW[YES + o] = w1[1]; YW[2 * YES + o] = w2[0]; YW[3 * YES + o] = w2[1];
+                if constexpr (EQN == 0) {
+                    YF[o] = e.s1 * w1[0]; YF[YES + o] = e.s1 * w1[1];
+                    YF[2 * YES + o] = e.s2 * w2[0]; YF[3 * YES + o] = e.s2 * w2[1];
+                } else {
+                    YF[o] = w1[0]; YF[YES + o] = w1[1]; YF[2 * YES + o] = w2[0]; YF[3 * YES + o] = w2[1];
+                }
+            }
+        }
+        __syncthreads();
+        // ---- MC-limited second-order corrections Fn (x) and Gn (y) ----
+        for (int k = tid; k < (tx + 1) * (ty + 2) + (tx + 2) * (ty + 1); k += kThreads) {
+            if (k < (tx + 1) * (ty + 2)) {
+                int er = k / (tx + 1), ec = k - er * (tx + 1);      // row ry = er-1, edge ex = ec
+                int o = er * XEX + ec + 1;                          // edge ex in XW
+                int l = (er + 1) * PX + ec + 1, r = l + 1;
+                Edge e;
+                load_edge<EQN, 0>(sA, PS, l, r, e);
+                int u1 = (e.s1 > 0.0) ? o - 1 : o + 1;
+                int u2 = (e.s2 > 0.0) ? o - 1 : o + 1;
+                double w10 = XW[o], w1n = XW[XES + o], w20 = XW[2 * XES + o], w2n = XW[3 * XES + o];
+                double p1 = mc_phi(w10, w1n, XW[u1], XW[XES + u1]);
+                double p2 = mc_phi(w20, w2n, XW[2 * XES + u2], XW[3 * XES + u2]);
+                double cf1 = corr_coef<EQN>(e.s1, dtdx), cf2 = corr_coef<EQN>(e.s2, dtdx);
+                int on = er * XNX + ec;
+                XN[on] = 0.5 * (cf1 * (p1 * w10) + cf2 * (p2 * w20));
+                XN[XNS + on] = 0.5 * (cf1 * (p1 * w1n) + cf2 * (p2 * w2n));
+            } else {
+                int kk = k - (tx + 1) * (ty + 2);
+                int er = kk / (tx + 2), ec = kk - er * (tx + 2);   // y-edge ey = er, column cx = ec-1
+                int o = (er + 1) * YEX + ec;
+                int l = (er + 1) * PX + ec + 1, r = l + PX;
+                Edge e;
+                load_edge<EQN, 1>(sA, PS, l, r, e);
+                int u1 = (e.s1 > 0.0) ? o - YEX : o + YEX;
+                int u2 = (e.s2 > 0.0) ? o - YEX : o + YEX;
+                double w10 = YW[o], w1n = YW[YES + o], w20 = YW[2 * YES + o], w2n = YW[3 * YES + o];
+                double p1 = mc_phi(w10, w1n, YW[u1], YW[YES + u1]);
+                double p2 = mc_phi(w20, w2n, YW[2 * YES + u2], YW[3 * YES + u2]);
+                double cf1 = corr_coef<EQN>(e.s1, dtdy), cf2 = corr_coef<EQN>(e.s2, dtdy);
+                int on = er * YNX + ec;
+                YN[on] = 0.5 * (cf1 * (p1 * w10) + cf2 * (p2 * w20));
+                YN[YNS + on] = 0.5 * (cf1 * (p1 * w1n) + cf2 * (p2 * w2n));
+            }
+        }
+        __syncthreads();
+        // ---- fluctuations entering each cell, corrections included ----
+        for (int k = tid; k < tx * (ty + 2) + (tx + 2) * ty; k += kThreads) {
+            if (k < tx * (ty + 2)) {
+                int er = k / tx, c = k - er * tx;                  // cell (c, ry = er-1)
+                int oL = er * XEX + c + 1, oR = oL + 1;            // x-edges c and c+1
+                int nL = er * XNX + c, nR = nL + 1;
+                for (int kk = 0; kk < 2; kk++) {
+                    double apT = XF[(2 + kk) * XES + oL] - XN[kk * XNS + nL];
+                    double amT = XF[kk * XES + oR] + XN[kk * XNS + nR];
+                    SX[kk * SXS + er * TX + c] = apT + amT;
+                }
+            } else {
+                int kk0 = k - tx * (ty + 2);
+                int r = kk0 / (tx + 2), ec = kk0 - r * (tx + 2);  // cell (cx = ec-1, r)
+                int oB = (r + 1) * YEX + ec, oT = oB + YEX;        // y-edges r and r+1
+                int nB = r * YNX + ec, nT = nB + YNX;
+                for (int kk = 0; kk < 2; kk++) {
+                    double bpT = YF[(2 + kk) * YES + oB] - YN[kk * YNS + nB];
+                    double bmT = YF[kk * YES + oT] + YN[kk * YNS + nT];
+                    SY[kk * SYS + r * (TX + 2) + ec] = bpT + bmT;
+                }
+            }
+        }
+        __syncthreads();
+        // ---- transverse corrections: full edge fluxes F and G, and CFL ----
+        for (int k = tid; k < (tx + 1) * ty + tx * (ty + 1); k += kThreads) {
+            if (k < (tx + 1) * ty) {
+                int r = k / (tx + 1), ec = k - r * (tx + 1);       // x-edge ex = ec, row r
+                int l = (r + 2) * PX + ec + 1, rr = l + 1;
+                Edge e;
+                load_edge<EQN, 0>(sA, PS, l, rr, e);
+                double dR = SY[r * (TX + 2) + ec + 1];            // Sy of the cell right of the edge
+                double dL = SY[r * (TX + 2) + ec];                // Sy of the cell left of the edge
+                double w1[2], w2[2], v1[2], v2[2];
+                decompose<EQN>(e, dR, 0.0, w1, w2);
+                decompose<EQN>(e, dL, 0.0, v1, v2);
+                int on = (r + 1) * XNX + ec;
+                for (int kk = 0; kk < 2; kk++)
+                    FF[kk * FFS + r * (TX + 1) + ec] = XN[kk * XNS + on] - hy * (e.s1 * w1[kk] + e.s2 * v2[kk]);
+                cfl = fmax(cfl, dtdx * fmax(fabs(e.s1), fabs(e.s2)));
+            } else {
+                int kk0 = k - (tx + 1) * ty;
+                int er = kk0 / tx, c = kk0 - er * tx;              // y-edge ey = er, column c
+                int l = (er + 1) * PX + c + 2, rr = l + PX;
+                Edge e;
+                load_edge<EQN, 1>(sA, PS, l, rr, e);
+                double dU = SX[(er + 1) * TX + c];                 // Sx of the cell above the edge
+                double dD = SX[er * TX + c];                       // Sx of the cell below
+                double w1[2], w2[2], v1[2], v2[2];
+                decompose<EQN>(e, dU, 0.0, w1, w2);
+                decompose<EQN>(e, dD, 0.0, v1, v2);
+                int on = er * YNX + c + 1;
+                for (int kk = 0; kk < 2; kk++)
+                    GG[kk * GGS + er * TX + c] = YN[kk * YNS + on] - hx * (e.s1 * w1[kk] + e.s2 * v2[kk]);
+                cfl = fmax(cfl, dtdy * fmax(fabs(e.s1), fabs(e.s2)));
+            }
+        }
+        __syncthreads();
+        // ---- cell update q - (X + Y) ----
+        for (int k = tid; k < tx * ty; k += kThreads) {
+            int r = k / tx, c = k - r * tx;
+            int oL = (r + 1) * XEX + c + 1, oR = oL + 1;
+            int oB = (r + 1) * YEX + c + 1, oT = oB + YEX;
+            int fL = r * (TX + 1) + c, fR = fL + 1;
+            int gB = r * TX + c, gT = gB + TX;
+            double X0 = dtdx * ((XF[2 * XES + oL] + XF[oR]) + (FF[fR] - FF[fL]));
+            double X1 = dtdx * ((XF[3 * XES + oL] + XF[XES + oR]) + (FF[FFS + fR] - FF[FFS + fL]));
+            double Y0 = dtdy * ((YF[2 * YES + oB] + YF[oT]) + (GG[gT] - GG[gB]));
+            double Y1 = dtdy * ((YF[3 * YES + oB] + YF[YES + oT]) + (GG[GGS + gT] - GG[GGS + gB]));
+            int s = (r + 2) * PX + c + 2;
+            long long g = P.base + (long long)(y0 + r + 2) * P.sx + (x0 + c + 2);
+            qn[g] = sQ[s] - (X0 + Y0);
+            qn[stride + g] = sQ[PS + s] - (X1 + 0.0);
+            qn[2 * stride + g] = sQ[2 * PS + s] - (0.0 + Y1);
+        }
+        __syncthreads();
+    }
+    cfl_reduce(cfl, cfl_bits);
+}
+
+// ---------------------------------------------------------------- 1D
+template <int EQN, int TX>
+struct Smem1D {
+    static constexpr int NA = naux_of(EQN);
+    static constexpr int PX = TX + 4, XE = TX + 3, XN = TX + 1;
+    static constexpr int total = 2 * PX + NA * PX + 8 * XE + 2 * XN;
+    static constexpr size_t bytes = sizeof(double) * (size_t)total;
+};
+
+template <int EQN, int TX>
+__global__ void __launch_bounds__(kThreads) k_step1d(const double *__restrict__ q, double *__restrict__ qn,
+                                                     const double *__restrict__ aux, long long stride,
+                                                     const PatchDesc *__restrict__ patches,
+                                                     const WorkItem *__restrict__ work, int nwork,
+                                                     unsigned long long *cfl_bits)
+{
+    using S = Smem1D<EQN, TX>;
+    extern __shared__ double sm[];
+    constexpr int PX = S::PX, XE = S::XE, XNn = S::XN;
+    double *sQ = sm;
+    double *sA = sQ + 2 * PX;
+    double *XW = sA + S::NA * PX;
+    double *XF = XW + 4 * XE;
+    double *XN = XF + 4 * XE;
+    const int tid = threadIdx.x;
+    double cfl = 0.0;
+    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+        const WorkItem wi = work[w];
+        const PatchDesc P = patches[wi.patch];
+        const int x0 = wi.x0;
+        const int tx = min(TX, P.nx - x0), rx = tx + 4;
+        const double dtdx = P.dtdx;
+        for (int k = tid; k < (2 + S::NA) * rx; k += kThreads) {
+            int f = k / rx, c = k - f * rx;
+            long long g = P.base + x0 + c;
+            if (f < 2) sQ[f * PX + c] = q[(long long)f * stride + g];
+            else sA[(f - 2) * PX + c] = aux[(long long)(f - 2) * stride + g];
+        }
+        __syncthreads();
+        for (int k = tid; k < tx + 3; k += kThreads) {    // edge ex = k-1 between staged cells k, k+1
+            int l = k, r = k + 1;
+            Edge e;
+            load_edge<EQN, 0>(sA, PX, l, r, e);
+            double d0, dn, w1[2], w2[2];
+            edge_jump<EQN>(e, sA, PX, l, r, sQ[l], sQ[PX + l], sQ[r], sQ[PX + r], d0, dn);
+            decompose<EQN>(e, d0, dn, w1, w2);
+            XW[k] = w1[0]; XW[XE + k] = w1[1]; XW[2 * XE + k] = w2[0]; XW[3 * XE + k] = w2[1];
+            if constexpr (EQN == 0) {
+                XF[k] = e.s1 * w1[0]; XF[XE + k] = e.s1 * w1[1];
+                XF[2 * XE + k] = e.s2 * w2[0]; XF[3 * XE + k] = e.s2 * w2[1];
+            } else {
+                XF[k] = w1[0]; XF[XE + k] = w1[1]; XF[2 * XE + k] = w2[0]; XF[3 * XE + k] = w2[1];
+            }
+        }
+        __syncthreads();
+        for (int k = tid; k < tx + 1; k += kThreads) {    // edge ex = k
+            int o = k + 1, l = k + 1, r = k + 2;
+            Edge e;
+            load_edge<EQN, 0>(sA, PX, l, r, e);
+            int u1 = (e.s1 > 0.0) ? o - 1 : o + 1;
+            int u2 = (e.s2 > 0.0) ? o - 1 : o + 1;
+            double w10 = XW[o], w1n = XW[XE + o], w20 = XW[2 * XE + o], w2n = XW[3 * XE + o];
+            double p1 = mc_phi(w10, w1n, XW[u1], XW[XE + u1]);
+            double p2 = mc_phi(w20, w2n, XW[2 * XE + u2], XW[3 * XE + u2]);
+            double cf1 = corr_coef<EQN>(e.s1, dtdx), cf2 = corr_coef<EQN>(e.s2, dtdx);
+            XN[k] = 0.5 * (cf1 * (p1 * w10) + cf2 * (p2 * w20));
+            XN[XNn + k] = 0.5 * (cf1 * (p1 * w1n) + cf2 * (p2 * w2n));
+            cfl = fmax(cfl, dtdx * fmax(fabs(e.s1), fabs(e.s2)));
+        }
+        __syncthreads();
+        for (int c = tid; c < tx; c += kThreads) {
+            int oL = c + 1, oR = c + 2;
+            double X0 = dtdx * ((XF[2 * XE + oL] + XF[oR]) + (XN[c + 1] - XN[c]));
+            double X1 = dtdx * ((XF[3 * XE + oL] + XF[XE + oR]) + (XN[XNn + c + 1] - XN[XNn + c]));
+            long long g = P.base + x0 + c + 2;
+            qn[g] = sQ[c + 2] - X0;
+            qn[stride + g] = sQ[PX + c + 2] - X1;
+        }
+        __syncthreads();
+    }
+    cfl_reduce(cfl, cfl_bits);
+}
+
+// the dynamic shared-memory limit is raised once per kernel (outside any
+// stream capture: the first launch of each kernel happens uncaptured)
+template <auto Kern>
+cudaError_t ensure_smem_attr(size_t smem)
+{
+    static cudaError_t state = cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return state;
+}
+
+template <auto Kern>
+cudaError_t launch_kernel(size_t smem, int nwork, int grid, const double *q, double *qn, const double *aux,
+                          long long stride, const PatchDesc *patches, const WorkItem *work,
+                          unsigned long long *cfl_bits, cudaStream_t s)
+{
+    auto kern = Kern;
+    cudaError_t e = ensure_smem_attr<Kern>(smem);
+    if (e != cudaSuccess) return e;
+    if (nwork <= 0) return cudaSuccess;
+    int g = grid > 0 ? grid : nwork;
+    kern<<<g, kThreads, smem, s>>>(q, qn, aux, stride, patches, work, nwork, cfl_bits);
+    return cudaGetLastError();
+}
+
+template <int EQN>
+cudaError_t dispatch2d(int tx, int ty, int nwork, int grid, const double *q, double *qn, const double *aux,
+                       long long stride, const PatchDesc *p, const WorkItem *w, unsigned long long *c,
+                       cudaStream_t s)
+{
+#define ADJ_TILE(X, Y)                                                                                    \
+    if (tx == X && ty == Y)                                                                               \
+        return launch_kernel<k_step2d<EQN, X, Y>>(Smem2D<EQN, X, Y>::bytes, nwork, grid, q, qn, aux, stride, p, w, \
+                                                  c, s);
+    ADJ_TILE(32, 8)
+    ADJ_TILE(16, 8)
+    ADJ_TILE(16, 16)
+    ADJ_TILE(32, 16)
+    ADJ_TILE(64, 8)
+    ADJ_TILE(8, 8)
+#undef ADJ_TILE
+    return cudaErrorInvalidValue;
+}
+
+template <int EQN>
+cudaError_t dispatch1d(int tx, int nwork, int grid, const double *q, double *qn, const double *aux, long long stride,
+                       const PatchDesc *p, const WorkItem *w, unsigned long long *c, cudaStream_t s)
+{
+    if (tx == 256)
+        return launch_kernel<k_step1d<EQN, 256>>(Smem1D<EQN, 256>::bytes, nwork, grid, q, qn, aux, stride, p, w, c, s);
+    if (tx == 128)
+        return launch_kernel<k_step1d<EQN, 128>>(Smem1D<EQN, 128>::bytes, nwork, grid, q, qn, aux, stride, p, w, c, s);
+    return cudaErrorInvalidValue;
+}
+
+template <int EQN>
+int occ2d(int tx, int ty)
+{
+    int n = 0;
+#define ADJ_OCC(X, Y)                                                                                   \
+    if (tx == X && ty == Y) {                                                                           \
+        if (ensure_smem_attr<k_step2d<EQN, X, Y>>(Smem2D<EQN, X, Y>::bytes) == cudaSuccess)            \
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2d<EQN, X, Y>, kThreads,            \
+                                                          Smem2D<EQN, X, Y>::bytes);                    \
+    }
+    ADJ_OCC(32, 8)
+    ADJ_OCC(16, 8)
+    ADJ_OCC(16, 16)
+    ADJ_OCC(32, 16)
+    ADJ_OCC(64, 8)
+    ADJ_OCC(8, 8)
+#undef ADJ_OCC
+    return n;
+}
+
+}  // namespace
+
+cudaError_t launch_step(int dim, int eqn, int tx, int ty, const double *q, double *qn, const double *aux,
+                        long long stride, const PatchDesc *patches, const WorkItem *work, int nwork, int grid,
+                        unsigned long long *cfl_bits, cudaStream_t s)
+{
+    if (dim == 1) {
+        switch (eqn) {
+        case 0: return dispatch1d<0>(tx, nwork, grid, q, qn, aux, stride, patches, work, cfl_bits, s);
+        case 1: return dispatch1d<1>(tx, nwork, grid, q, qn, aux, stride, patches, work, cfl_bits, s);
+        default: return cudaErrorInvalidValue;
+        }
+    }
+    switch (eqn) {
+    case 0: return dispatch2d<0>(tx, ty, nwork, grid, q, qn, aux, stride, patches, work, cfl_bits, s);
+    case 1: return dispatch2d<1>(tx, ty, nwork, grid, q, qn, aux, stride, patches, work, cfl_bits, s);
+    case 2: return dispatch2d<2>(tx, ty, nwork, grid, q, qn, aux, stride, patches, work, cfl_bits, s);
+    case 3: return dispatch2d<3>(tx, ty, nwork, grid, q, qn, aux, stride, patches, work, cfl_bits, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+int step_occupancy(int dim, int eqn, int tx, int ty)
+{
+    if (dim == 1) return 4;
+    switch (eqn) {
+    case 0: return occ2d<0>(tx, ty);
+    case 1: return occ2d<1>(tx, ty);
+    case 2: return occ2d<2>(tx, ty);
+    case 3: return occ2d<3>(tx, ty);
+    default: return 0;
+    }
+}
+
+}  // namespace adjamr

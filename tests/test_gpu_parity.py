@@ -1,0 +1,319 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the
+same seeded inputs.  States, adjoint snapshots and J must agree within 1e-12
+relative (both follow the same operation order, so they agree exactly);
+flags and patch layouts must agree bit for bit."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1511_03645_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def A():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1511_03645_gb300 import adjamr
+    adjamr.load()
+    return adjamr
+
+
+def close(a, b, rtol=RTOL):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    assert a.shape == b.shape, (a.shape, b.shape)
+    if a.size == 0:
+        return
+    scale = max(float(np.max(np.abs(b))), 1e-300)
+    err = float(np.max(np.abs(a - b)))
+    assert err <= rtol * scale, f"max abs diff {err:.3e} vs scale {scale:.3e}"
+
+
+def scatter_write(h, level, dense):
+    parts = [dense[:, jlo:jlo + ny, ilo:ilo + nx].reshape(-1) for ilo, jlo, nx, ny in h.patches(level)]
+    h.write_level(level, np.concatenate(parts))
+
+
+def dense_wl(dim, eqn, N, fields, bc, L=8.0, tf=1.0):
+    if dim == 2:
+        wl = W.config2(n0=N, lo=-L / 2, hi=L / 2, bc=bc, max_patch=64)
+    else:
+        wl = W.config1(n0=N, bc=bc[:2])
+        wl.lo, wl.hi = (-L / 2, 0.0), (L / 2, 1.0)
+    wl.eqn = eqn
+    wl.tf = tf
+    if eqn in (W.EQ_SW, W.EQ_SW_ADJ):
+        cmax = float(np.sqrt(W.GRAV * fields.max()))
+    else:
+        cmax = float(np.sqrt(fields[1] / fields[0]).max())
+    wl.medium = W.Medium(kind="dense", fields=[fields], cmax=cmax)
+    return wl
+
+
+# ---------------------------------------------------------- single level
+CASES = [
+    (1, W.EQ_ACOUSTICS, (W.BC_EXTRAP, W.BC_WALL, 0, 0)),
+    (1, W.EQ_ACOUSTICS_ADJ, (W.BC_PERIODIC, W.BC_PERIODIC, 0, 0)),
+    (2, W.EQ_ACOUSTICS, (W.BC_EXTRAP, W.BC_WALL, W.BC_PERIODIC, W.BC_PERIODIC)),
+    (2, W.EQ_ACOUSTICS_ADJ, (W.BC_WALL, W.BC_EXTRAP, W.BC_WALL, W.BC_EXTRAP)),
+    (2, W.EQ_SW, (W.BC_WALL, W.BC_WALL, W.BC_EXTRAP, W.BC_EXTRAP)),
+    (2, W.EQ_SW_ADJ, (W.BC_PERIODIC, W.BC_PERIODIC, W.BC_WALL, W.BC_WALL)),
+]
+
+
+@pytest.mark.parametrize("dim,eqn,bc", CASES)
+def test_uniform_grid_steps_match_oracle_bitwise(A, dim, eqn, bc):
+    """Random medium and state on a multi-patch uniform grid with ragged
+    tiles; 7 steps; every interior value identical."""
+    rng = np.random.default_rng(100 + 10 * dim + eqn)
+    N = 83 if dim == 2 else 301
+    M = N if dim == 2 else 1
+    if eqn in (W.EQ_SW, W.EQ_SW_ADJ):
+        fields = rng.uniform(100, 4000, (1, M, N))
+        L = 8e5
+    else:
+        fields = np.stack([rng.uniform(1, 3, (M, N)), rng.uniform(1, 30, (M, N))])
+        L = 8.0
+    wl = dense_wl(dim, eqn, N, fields, bc, L=L, tf=1.0)
+    wl.max_patch0 = 40 if dim == 2 else 120
+    q0 = rng.normal(size=(wl.m, M, N))
+    o = O.OracleHierarchy(wl, nlevels=1, with_qinit=False)
+    g = A.Hierarchy(wl, nlevels=1, with_qinit=False)
+    assert np.array_equal(g.patches(0), o.patches(0))
+    scatter_write(o, 0, q0)
+    scatter_write(g, 0, q0)
+    o.advance(7)
+    g.advance(7)
+    a, b = g.read_level(0), o.read_level(0)
+    close(a, b)
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("tile", [(16, 8), (16, 16), (32, 16), (64, 8), (8, 8)])
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_tile_shapes_and_launch_modes_agree_bitwise(A, tile, mode):
+    """Every tile shape and launch mode (work-list, persistent, per patch)
+    computes the same bits as the default configuration."""
+    rng = np.random.default_rng(7)
+    N = 70
+    fields = np.stack([rng.uniform(1, 3, (N, N)), rng.uniform(1, 30, (N, N))])
+    wl = dense_wl(2, W.EQ_ACOUSTICS, N, fields, (W.BC_EXTRAP,) * 4)
+    wl.max_patch0 = 33
+    q0 = rng.normal(size=(3, N, N))
+    ref = A.Hierarchy(wl, nlevels=1, with_qinit=False)
+    g = A.Hierarchy(wl, nlevels=1, with_qinit=False, tile=tile, launch_mode=mode)
+    scatter_write(ref, 0, q0)
+    scatter_write(g, 0, q0)
+    ref.advance(5)
+    g.advance(5)
+    assert np.array_equal(ref.read_level(0), g.read_level(0))
+
+
+# ---------------------------------------------------------- adjoint solve
+@pytest.mark.parametrize("which", ["1d", "2d", "sw"])
+def test_adjoint_snapshots_match_oracle(A, which):
+    if which == "1d":
+        wl = W.config1(adj_n=300, nsnap=25, tf=6.0, bc=(W.BC_WALL, W.BC_EXTRAP))
+        med = None
+    elif which == "2d":
+        wl = W.config2(seed=4, n0=40, adj_n=90, nsnap=14, tf=2.0)
+        med = None
+    else:
+        wl = W.config3(seed=1, n0=20, ratios=(2,), adj_n=50, nsnap=8, tf=3600.0, dense_levels=2)
+        xa = (np.arange(50) + 0.5) * (2e6 / 50)
+        X, Y = np.meshgrid(xa, xa)
+        med = W.bathymetry(X, Y, wl.extra["mounts"])[None]
+    ref = O.adjoint_solve(wl, medium_dense=med)
+    adj = A.solve_adjoint(wl, medium_dense=med)
+    got = adj.read()
+    close(got, ref)
+    assert np.array_equal(got, ref)
+    assert np.abs(ref[0]).max() > 0
+
+
+# ---------------------------------------------------------- AMR runs
+def _amr_pair(A, wl, snaps=None, stream=None, **kw):
+    if snaps is None:
+        snaps = O.adjoint_solve(wl)
+    o = O.OracleHierarchy(wl, **kw)
+    o.set_adjoint(snaps)
+    o.regrid(0, init=True)
+    g = A.Hierarchy(wl, stream=stream, **kw)
+    g.load_adjoint(snaps)
+    g.regrid(0, init=True)
+    return o, g
+
+
+def _compare_all(o, g, nlev):
+    for lev in range(nlev):
+        assert np.array_equal(g.patches(lev), o.patches(lev)), f"layout of level {lev}"
+        a, b = g.read_level(lev), o.read_level(lev)
+        close(a, b)
+
+
+@pytest.mark.parametrize("which", ["c1", "c2", "c2_linear", "c2_walls", "c3"])
+def test_amr_run_matches_oracle(A, which):
+    """Adjoint-guided AMR runs (reduced sizes of the workloads): layouts of
+    every level bit-exact after every regrid, states within 1e-12, flags
+    bit-exact, J within 1e-12."""
+    if which == "c1":
+        wl = W.config1(n0=100, tf=6.0, adj_n=400, nsnap=30)
+        chunks = 6
+    elif which.startswith("c2"):
+        bc = (W.BC_WALL,) * 4 if which == "c2_walls" else (W.BC_EXTRAP,) * 4
+        wl = W.config2(seed=3, n0=32, ratios=(2, 4), tf=2.0, adj_n=64, nsnap=20, ts=0.0, tol=1e-4, bc=bc,
+                       min_patch=8, max_patch=32)
+        if which == "c2_linear":
+            wl.flag_mode = W.FLAG_LINEAR
+        chunks = 4
+    else:
+        wl = W.config3(seed=2, n0=24, ratios=(2, 2), tf=4 * 3600.0, adj_n=48, nsnap=20, tol=1e-3, L=2.0e6,
+                       dense_levels=3)
+        chunks = 4
+    snaps = O.adjoint_solve(wl, medium_dense=None if wl.medium.kind != "dense" else _adj_medium(wl))
+    o, g = _amr_pair(A, wl, snaps=snaps)
+    _compare_all(o, g, wl.nlevels)
+    n = o.nsteps_total()
+    assert g.nsteps_total() == n
+    refined = 0
+    for c in range(chunks):
+        k = n // chunks if c < chunks - 1 else n - (chunks - 1) * (n // chunks)
+        o.advance(k)
+        g.advance(k)
+        _compare_all(o, g, wl.nlevels)
+        refined += sum(len(o.patches(lev)) for lev in range(1, wl.nlevels))
+        for lev in range(wl.nlevels - 1):
+            fo, co = o.flag(lev, wl.tol)
+            fg, cg = g.flag(lev, wl.tol)
+            assert co == cg and np.array_equal(fo, fg)
+    assert refined > 0, "the case never refined"
+    Jo, Jg = o.functional(), g.functional()
+    assert abs(Jg - Jo) <= RTOL * max(abs(Jo), 1e-300)
+
+
+def _adj_medium(wl):
+    nx = wl.adj_n[0]
+    xa = wl.lo[0] + (np.arange(nx) + 0.5) * (wl.hi[0] - wl.lo[0]) / nx
+    X, Y = np.meshgrid(xa, xa)
+    return W.bathymetry(X, Y, wl.extra["mounts"], wl.hi[0])[None]
+
+
+def test_edge_cases_no_refinement_and_full_refinement(A):
+    """tol = +inf: no finer level; tol < 0: the finest level covers the
+    domain; both agree with the oracle bit for bit."""
+    wl = W.config2(seed=5, n0=20, ratios=(2,), tf=0.5, adj_n=40, nsnap=6)
+    for tol in (math.inf, -1.0):
+        snaps = O.adjoint_solve(wl)
+        o, g = _amr_pair(A, wl, snaps=snaps, tol=tol)
+        n = o.nsteps_total()
+        o.advance(n)
+        g.advance(n)
+        _compare_all(o, g, wl.nlevels)
+        if tol > 0:
+            assert len(g.patches(1)) == 0
+        else:
+            cov = sum(int(nx) * int(ny) for _, _, nx, ny in g.patches(1))
+            assert cov == 40 * 40
+
+
+def test_cfl_violation_is_reported(A):
+    """Courant number above cfl_max returns ADJAMR_ECFL, not a crash."""
+    wl = W.config2(seed=5, n0=16, ratios=(2,), tf=0.5)
+    wl.cfl_max = 0.5
+    g = A.Hierarchy(wl, nlevels=1)
+    with pytest.raises(A.AdjamrError) as ei:
+        g.advance(2)
+    assert ei.value.code == A.ECFL
+
+
+def test_torch_stream_interop(A):
+    """Work issued on a PyTorch stream; results identical to the default stream."""
+    import torch
+    wl = W.config2(seed=6, n0=24, ratios=(2,), tf=0.6, adj_n=48, nsnap=8, ts=0.0, tol=1e-4)
+    snaps = O.adjoint_solve(wl)
+    s = torch.cuda.Stream()
+    o, g = _amr_pair(A, wl, snaps=snaps, stream=s.cuda_stream)
+    n = o.nsteps_total()
+    o.advance(n)
+    g.advance(n)
+    _compare_all(o, g, wl.nlevels)
+
+
+# ---------------------------------------------------------- batched patches
+def test_batched_patches_modes_agree_and_match_oracle(A):
+    """4096 uneven patches (the batching stress configuration): the fused
+    work-list launch, the persistent grid, one launch per patch, and the
+    CUDA-graph replay all produce the same bits; sampled patches (smallest,
+    largest, and random) match the oracle run of that patch alone."""
+    pb = W.config4(seed=0)
+    results = []
+    for mode, graph in ((0, False), (1, False), (2, False), (0, True), (1, True)):
+        import torch
+        s = torch.cuda.Stream()
+        b = A.Batch(pb, stream=s.cuda_stream)
+        b.step(4, mode=mode, tile=(32, 8), graph=graph)
+        results.append(b.read())
+        b.close()
+    for r in results[1:]:
+        assert np.array_equal(r, results[0])
+    cells = pb.nx.astype(np.int64) * pb.ny
+    offs = np.concatenate([[0], np.cumsum(3 * cells)])
+    rng = np.random.default_rng(1)
+    sample = sorted({int(np.argmin(cells)), int(np.argmax(cells))} | set(rng.choice(pb.npatch, 6, replace=False).tolist()))
+    for k in sample:
+        nx, ny = int(pb.nx[k]), int(pb.ny[k])
+        x0, y0 = float(pb.x0[k]), float(pb.y0[k])
+        x1, y1 = x0 + nx * float(pb.dx[k]), y0 + ny * float(pb.dx[k])
+        wl = W.config2(n0=nx, lo=x0, hi=x1, bc=(W.BC_EXTRAP,) * 4)
+        wl.n0 = (nx, ny)
+        wl.lo, wl.hi = (x0, y0), (x1, y1)
+        wl.medium = pb.media[int(pb.medium_id[k])]
+        wl.max_patch0 = 1024
+        o = O.OracleHierarchy(wl, nlevels=1, with_qinit=False, dt0=float(pb.dt[k]))
+        o.write_level(0, pb.qinit_patch(k).reshape(-1))
+        o.advance(4)
+        got = results[0][offs[k]:offs[k + 1]]
+        assert np.array_equal(got, o.read_level(0)), f"patch {k}"
+
+
+# ---------------------------------------------------------- full size, sampled
+def test_full_size_config2_sampled_step_parity(A):
+    """Config 2 at full size (100^2 coarse, ratios 2 and 4, adjoint 400^2 x
+    200 snapshots) in the benchmark's launch configuration: after an adjoint-
+    guided run of 40 coarse steps, one step of sampled finest-level patches is
+    recomputed by the oracle from the GPU's own ghosted input and must match
+    bit for bit; layouts satisfy the nesting and size invariants."""
+    wl = W.config2(seed=0, ts=0.0, tol=1e-3)
+    adj = A.solve_adjoint(wl)
+    g = A.Hierarchy(wl)
+    g.set_adjoint(adj)
+    g.regrid(0, init=True)
+    g.advance(40)
+    L = wl.nlevels - 1
+    P = g.patches(L)
+    assert len(P) > 0
+    g.fill_ghosts(L)
+    rng = np.random.default_rng(0)
+    ks = sorted(set(rng.choice(len(P), min(6, len(P)), replace=False).tolist()))
+    inputs = [g.patch_ghosted(L, k) for k in ks]
+    dt = g.time_info()[0] / (wl.ratios[0] * wl.ratios[1])
+    dx, dy = wl.level_dx(L)
+    g.step_level_only(L)
+    flat = g.read_level(L)
+    offs = np.concatenate([[0], np.cumsum([3 * int(nx) * int(ny) for _, _, nx, ny in P])])
+    for k, (q, med) in zip(ks, inputs):
+        ref, _ = O.step_patch(2, W.EQ_ACOUSTICS, q, med, dt, dx, dy)
+        assert np.array_equal(flat[offs[k]:offs[k + 1]], ref.reshape(-1)), f"patch {k}"
+    for lev in range(1, wl.nlevels):
+        for ilo, jlo, nx, ny in g.patches(lev):
+            assert nx <= wl.max_patch and ny <= wl.max_patch
+    # the adjoint snapshot at t_f is phi itself
+    snaps = adj.read()
+    close(snaps[-1], wl.adjoint_phi())
