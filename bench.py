@@ -320,6 +320,29 @@ def run_ours(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_case_batch(args):
+    """Profiling case: the 4096-patch batch (about 2.7 GB on the device, larger
+    than L2), fused work-list steps only."""
+    import torch
+    from paper_1511_03645_gb300 import adjamr as A
+    from paper_1511_03645_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    s = torch.cuda.Stream()
+    b = A.Batch(W.config4(seed=0), stream=s.cuda_stream)
+    b.step(args.warmup, mode=0)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    b.step(args.steps, mode=0)
+    e1.record(s)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    print(json.dumps({"case": "batch", "cells": b.cells(), "ms_per_step": ms,
+                      "cell_updates_per_s": b.cells() / (ms * 1e-3)}), flush=True)
+    b.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -328,7 +351,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--case", default="main", choices=["main", "batch"])
     args = ap.parse_args()
+    if args.case == "batch":
+        run_case_batch(args)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":

@@ -174,7 +174,7 @@ def test_amr_run_matches_oracle(A, which):
             wl.flag_mode = W.FLAG_LINEAR
         chunks = 4
     else:
-        wl = W.config3(seed=2, n0=24, ratios=(2, 2), tf=4 * 3600.0, adj_n=48, nsnap=20, tol=1e-3, L=2.0e6,
+        wl = W.config3(seed=2, n0=24, ratios=(2, 2), tf=4 * 3600.0, adj_n=48, nsnap=20, tol=1e-5, L=2.0e6,
                        dense_levels=3)
         chunks = 4
     snaps = O.adjoint_solve(wl, medium_dense=None if wl.medium.kind != "dense" else _adj_medium(wl))
