@@ -87,6 +87,17 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def aggregate(td, local_ms, local_cells, device):
+    """Replicas: whole-job time is the slowest rank's, work is the sum over
+    ranks.  Returns (max ms, total cell-updates)."""
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    c = torch.tensor([float(local_cells)], dtype=torch.float64, device=device)
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    td.all_reduce(c, op=td.ReduceOp.SUM)
+    return float(t.item()), float(c.item())
+
+
 def workload():
     from paper_1511_03645_gb300 import workloads as W
     return W.config2(seed=0, ts=0.0, tol=1e-3)
@@ -220,12 +231,7 @@ def run_ours(args, rank, world):
     ck = clocks.stop()
     total_ms = sum(times)
     if dist:
-        tt = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        td.all_reduce(tt, op=td.ReduceOp.MAX)
-        total_ms = float(tt.item())
-        cc = torch.tensor([float(cu)], device="cuda", dtype=torch.float64)
-        td.all_reduce(cc, op=td.ReduceOp.SUM)
-        cu_all = float(cc.item())
+        total_ms, cu_all = aggregate(td, total_ms, cu, "cuda")
     else:
         cu_all = float(cu)
     value = cu_all / (total_ms * 1e-3)

@@ -259,6 +259,49 @@ adjamr_status adjamr_batch_read(adjamr_batch *b, double *dst, size_t cap);
 adjamr_status adjamr_batch_cells(adjamr_batch *b, long long *cells);
 void adjamr_batch_destroy(adjamr_batch *b);
 
+/* ------------------------------------------------------------------ */
+/* Serving: many forward solves against shared device-resident adjoint     */
+/* snapshot sets.  Requests are admitted in arrival order as soon as a     */
+/* slot is free and their projected device memory fits the budget; every   */
+/* slot runs on its own CUDA stream so admitted requests overlap on the    */
+/* device.  A request's result does not depend on the other requests.      */
+/* ------------------------------------------------------------------ */
+typedef struct adjamr_server adjamr_server;
+
+typedef struct adjamr_request {
+    adjamr_params params;      /* params.stream is ignored (the slot's stream is used) */
+    adjamr_medium medium;      /* LAYERED; the layer table is copied at submit */
+    adjamr_adjoint *adjoint;   /* shared snapshot set; a reference is held until done */
+    adjamr_target target;      /* J is computed at tf */
+} adjamr_request;
+
+typedef struct adjamr_result {
+    int done;
+    adjamr_status status;
+    double J;
+    long long cell_updates, kernel_launches;
+    double t_submit, t_admit, t_finish;  /* seconds on the server's steady clock */
+    size_t bytes_reserved;
+    char error[128];
+} adjamr_result;
+
+/* Projected device bytes of one solve (upper bound: every level fully
+ * refined), used for admission. */
+size_t adjamr_estimate_bytes(const adjamr_params *p);
+/* max_slots worker threads on the current device; budget in bytes. */
+adjamr_status adjamr_server_create(size_t budget_bytes, int max_slots, adjamr_server **out);
+/* Queue a request; EBUDGET if it can never fit the budget. */
+adjamr_status adjamr_server_submit(adjamr_server *srv, const adjamr_request *rq, long long *ticket);
+/* Non-blocking status of a ticket (res.done = 0 while queued or running). */
+adjamr_status adjamr_server_poll(adjamr_server *srv, long long ticket, adjamr_result *out);
+/* Block until the ticket is done. */
+adjamr_status adjamr_server_wait(adjamr_server *srv, long long ticket, adjamr_result *out);
+adjamr_status adjamr_server_info(adjamr_server *srv, size_t *used_bytes, int *active, int *queued);
+double adjamr_server_now(adjamr_server *srv);
+/* Stops the workers after the running requests finish; queued requests are
+ * dropped (status ESTATE). */
+void adjamr_server_destroy(adjamr_server *srv);
+
 #ifdef __cplusplus
 }
 #endif

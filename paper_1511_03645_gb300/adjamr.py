@@ -66,6 +66,17 @@ class Patch(ctypes.Structure):
                 ("ny", ctypes.c_int)]
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("params", Params), ("medium", Medium), ("adjoint", ctypes.c_void_p), ("target", Target)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("done", ctypes.c_int), ("status", ctypes.c_int), ("J", ctypes.c_double),
+                ("cell_updates", ctypes.c_longlong), ("kernel_launches", ctypes.c_longlong),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_finish", ctypes.c_double),
+                ("bytes_reserved", ctypes.c_size_t), ("error", ctypes.c_char * 128)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("cell_updates", ctypes.c_longlong), ("adjoint_cell_updates", ctypes.c_longlong),
                 ("kernel_launches", ctypes.c_longlong), ("regrids", ctypes.c_longlong),
@@ -82,7 +93,8 @@ SYMBOLS = [
     "adjamr_step_level_only", "adjamr_get_stats", "adjamr_set_timing", "adjamr_time_info", "adjamr_last_error",
     "adjamr_destroy", "adjamr_batch_create", "adjamr_batch_set_order", "adjamr_batch_step",
     "adjamr_batch_step_graph", "adjamr_batch_read", "adjamr_batch_cells", "adjamr_batch_destroy",
-    "adjamr_fp64_peak",
+    "adjamr_fp64_peak", "adjamr_estimate_bytes", "adjamr_server_create", "adjamr_server_submit",
+    "adjamr_server_poll", "adjamr_server_wait", "adjamr_server_info", "adjamr_server_now", "adjamr_server_destroy",
 ]
 
 
@@ -134,6 +146,11 @@ def load(build_if_missing: bool = True):
             "adjamr_batch_read": [vp, dp, sz],
             "adjamr_batch_cells": [vp, P(ll)],
             "adjamr_fp64_peak": [i, i, dp, dp],
+            "adjamr_server_create": [sz, i, P(vp)],
+            "adjamr_server_submit": [vp, P(Request), P(ll)],
+            "adjamr_server_poll": [vp, ll, P(Result)],
+            "adjamr_server_wait": [vp, ll, P(Result)],
+            "adjamr_server_info": [vp, P(sz), ip, ip],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -147,6 +164,12 @@ def load(build_if_missing: bool = True):
         L.adjamr_adjoint_release.restype = None
         L.adjamr_batch_destroy.argtypes = [vp]
         L.adjamr_batch_destroy.restype = None
+        L.adjamr_server_destroy.argtypes = [vp]
+        L.adjamr_server_destroy.restype = None
+        L.adjamr_server_now.argtypes = [vp]
+        L.adjamr_server_now.restype = ctypes.c_double
+        L.adjamr_estimate_bytes.argtypes = [P(Params)]
+        L.adjamr_estimate_bytes.restype = ctypes.c_size_t
         _lib = L
         return L
 
@@ -478,3 +501,74 @@ def fp64_peak(kind=0, iters=4096):
     ms = ctypes.c_double()
     _check(load().adjamr_fp64_peak(kind, iters, ctypes.byref(f), ctypes.byref(ms)), None, "fp64_peak")
     return f.value, ms.value
+
+
+class Server:
+    """Serving loop: continuous admission of forward solves by memory budget,
+    one CUDA stream per slot (include/adjamr.h, adjamr_server_*)."""
+
+    def __init__(self, budget_bytes: int, max_slots: int):
+        L = load()
+        h = ctypes.c_void_p()
+        _check(L.adjamr_server_create(int(budget_bytes), int(max_slots), ctypes.byref(h)), None, "server_create")
+        self.h = h
+        self._keep = {}
+
+    def submit(self, wl, adj: Adjoint) -> int:
+        L = load()
+        cb = wl.qinit_callback() if wl.qinit is not None else None
+        rq = Request()
+        rq.params = make_params(wl, qinit=cb)
+        mh = _MediumHolder(wl.medium)
+        rq.medium = mh.m
+        rq.adjoint = adj.h
+        t = wl.target
+        rq.target = Target(t.x0, t.x1, t.y0, t.y1, t.weight)
+        tk = ctypes.c_longlong()
+        _check(L.adjamr_server_submit(self.h, ctypes.byref(rq), ctypes.byref(tk)), None, "server_submit")
+        self._keep[tk.value] = (cb, mh, rq)
+        return tk.value
+
+    @staticmethod
+    def _res(r: Result) -> dict:
+        d = {k: getattr(r, k) for k, _ in Result._fields_ if k != "error"}
+        d["error"] = r.error.decode(errors="replace")
+        return d
+
+    def poll(self, ticket: int) -> dict:
+        r = Result()
+        _check(load().adjamr_server_poll(self.h, ticket, ctypes.byref(r)), None, "server_poll")
+        return self._res(r)
+
+    def wait(self, ticket: int) -> dict:
+        r = Result()
+        _check(load().adjamr_server_wait(self.h, ticket, ctypes.byref(r)), None, "server_wait")
+        self._keep.pop(ticket, None)
+        return self._res(r)
+
+    def info(self):
+        used = ctypes.c_size_t()
+        a = ctypes.c_int()
+        q = ctypes.c_int()
+        _check(load().adjamr_server_info(self.h, ctypes.byref(used), ctypes.byref(a), ctypes.byref(q)), None,
+               "server_info")
+        return used.value, a.value, q.value
+
+    def now(self) -> float:
+        return load().adjamr_server_now(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().adjamr_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def estimate_bytes(wl) -> int:
+    p = make_params(wl)
+    return int(load().adjamr_estimate_bytes(ctypes.byref(p)))

@@ -20,7 +20,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libadjamr.so")
 
 CU = ["kernels_step.cu", "kernels_amr.cu", "fp64_peak.cu"]
-CPP = ["hierarchy.cpp", "batch.cpp"]
+CPP = ["hierarchy.cpp", "batch.cpp", "serve.cpp"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -80,7 +80,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
     if failed:
         raise RuntimeError("libadjamr build failed: " + ", ".join(failed))
     tmp = LIB + f".tmp{os.getpid()}"
-    link = [nvcc, ARCH, "-shared", "-cudart", "static", "-o", tmp] + objs
+    link = [nvcc, ARCH, "-shared", "-cudart", "static", "-o", tmp] + objs + ["-lpthread"]
     r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
     if r.returncode != 0:
         raise RuntimeError("libadjamr link failed:\n" + r.stdout)

@@ -49,7 +49,12 @@ struct Level {
     long long nghost = 0;
     AvgDesc *d_avg = nullptr;
     long long navg = 0;
-    long long *d_prefix = nullptr;
+    long long *d_prefix = nullptr;   // interior cells per patch (prefix)
+    long long *d_gprefix = nullptr;  // ghost cells per patch (prefix)
+    long long *d_sprefix = nullptr;  // storage cells per patch (prefix)
+    long long *d_aprefix = nullptr;  // coarse-footprint cells per patch (prefix)
+    long long nstore = 0, nghost_cells = 0, navg_cells = 0;
+    int *d_owner = nullptr;          // [M][N] arena index of each interior cell, or -1
     MediumDev *d_med = nullptr;
     // lookup buckets (cells per bucket side)
     int bs = 16, nbx = 0, nby = 0;
@@ -57,14 +62,6 @@ struct Level {
 };
 
 }  // namespace
-
-struct adjamr_adjoint {
-    int refs = 1;
-    int S = 0, m = 0, ax = 0, ay = 0, dim = 0;
-    double *d_snaps = nullptr;
-    unsigned char *d_wet = nullptr;
-    size_t bytes = 0;
-};
 
 struct adjamr_ctx {
     adjamr_params P;
@@ -79,6 +76,7 @@ struct adjamr_ctx {
     std::vector<double *> dense_dev;
     adjamr_adjoint *adj = nullptr;
     unsigned long long *d_cfl = nullptr, *d_count = nullptr;
+    int *d_err = nullptr;  // device-side invariant violations (nesting), checked after syncs
     unsigned char *d_flagbuf = nullptr;
     size_t flagbuf_bytes = 0;
     double *d_fscratch = nullptr, *d_fout = nullptr;
@@ -141,34 +139,6 @@ int part_off(int n, int p, int k)
     return o;
 }
 
-// boundary map of (I, J) on level l: in-domain cell plus sign flags of
-// components 1 (x-normal) and 2 (y-normal)
-void bc_map(const adjamr_ctx *c, int l, int &I, int &J, int &f1, int &f2)
-{
-    const Level &L = c->L[l];
-    f1 = f2 = 0;
-    if (I < 0) {
-        if (c->P.bc[0] == ADJAMR_BC_EXTRAP) I = 0;
-        else if (c->P.bc[0] == ADJAMR_BC_WALL) { I = -1 - I; f1 ^= 1; }
-        else I += L.N;
-    } else if (I >= L.N) {
-        if (c->P.bc[1] == ADJAMR_BC_EXTRAP) I = L.N - 1;
-        else if (c->P.bc[1] == ADJAMR_BC_WALL) { I = 2 * L.N - 1 - I; f1 ^= 1; }
-        else I -= L.N;
-    }
-    if (c->P.dim == 2) {
-        if (J < 0) {
-            if (c->P.bc[2] == ADJAMR_BC_EXTRAP) J = 0;
-            else if (c->P.bc[2] == ADJAMR_BC_WALL) { J = -1 - J; f2 ^= 1; }
-            else J += L.M;
-        } else if (J >= L.M) {
-            if (c->P.bc[3] == ADJAMR_BC_EXTRAP) J = L.M - 1;
-            else if (c->P.bc[3] == ADJAMR_BC_WALL) { J = 2 * L.M - 1 - J; f2 ^= 1; }
-            else J -= L.M;
-        }
-    }
-}
-
 long long cell_of(const adjamr_ctx *c, const HPatch &p, int i, int j)
 {
     return p.base + (long long)(j + c->gy) * p.sx + (i + 2);
@@ -210,6 +180,10 @@ void free_level(adjamr_ctx *c, Level &L)
     dfree(L.d_ghost, s);
     dfree(L.d_avg, s);
     dfree(L.d_prefix, s);
+    dfree(L.d_gprefix, s);
+    dfree(L.d_sprefix, s);
+    dfree(L.d_aprefix, s);
+    dfree(L.d_owner, s);
     L.patches.clear();
     L.h_work.clear();
     L.buckets.clear();
@@ -240,6 +214,17 @@ adjamr_status build_work(adjamr_ctx *c, int l, int tx, int ty)
     return ADJAMR_OK;
 }
 
+LevelIdx idx_of(const adjamr_ctx *c, int l)
+{
+    LevelIdx g;
+    g.dim = c->P.dim;
+    g.N = c->L[l].N;
+    g.M = c->L[l].M;
+    g.gy = c->gy;
+    for (int k = 0; k < 4; k++) g.bc[k] = c->P.bc[k];
+    return g;
+}
+
 // allocate the arena of a level for the given boxes (level index space)
 adjamr_status alloc_level(adjamr_ctx *c, int l, const std::vector<Box> &boxes)
 {
@@ -261,16 +246,23 @@ adjamr_status alloc_level(adjamr_ctx *c, int l, const std::vector<Box> &boxes)
     L.ncell = off;
     L.ninterior = 0;
     std::vector<PatchDesc> pd;
-    std::vector<long long> prefix;
-    prefix.push_back(0);
+    std::vector<long long> prefix{0}, gprefix{0}, sprefix{0}, aprefix{0};
     double dtdx = L.dt / L.dx, dtdy = (c->P.dim == 2) ? L.dt / L.dy : 0.0;
+    int rc = (l > 0) ? c->P.ratio[l - 1] : 1;
+    L.nstore = L.nghost_cells = L.navg_cells = 0;
     for (const HPatch &p : L.patches) {
         PatchDesc d;
         d.ilo = p.ilo; d.jlo = p.jlo; d.nx = p.nx; d.ny = p.ny; d.sx = p.sx; d.sy = p.sy; d.base = p.base;
         d.dtdx = dtdx; d.dtdy = dtdy; d.hx = 0.5 * dtdx; d.hy = 0.5 * dtdy;
         pd.push_back(d);
         L.ninterior += (long long)p.nx * p.ny;
+        L.nstore += (long long)p.sx * p.sy;
+        L.nghost_cells += (long long)p.sx * p.sy - (long long)p.nx * p.ny;
+        L.navg_cells += (l > 0) ? (long long)(p.nx / rc) * (c->P.dim == 2 ? p.ny / rc : 1) : 0;
         prefix.push_back(L.ninterior);
+        gprefix.push_back(L.nghost_cells);
+        sprefix.push_back(L.nstore);
+        aprefix.push_back(L.navg_cells);
     }
     CKR(c, dalloc(&L.q[0], (size_t)c->m * L.ncell, c->s));
     CKR(c, dalloc(&L.q[1], (size_t)c->m * L.ncell, c->s));
@@ -282,6 +274,16 @@ adjamr_status alloc_level(adjamr_ctx *c, int l, const std::vector<Box> &boxes)
     }
     CKR(c, upload(&L.d_patches, pd, c->s));
     CKR(c, upload(&L.d_prefix, prefix, c->s));
+    CKR(c, upload(&L.d_gprefix, gprefix, c->s));
+    CKR(c, upload(&L.d_sprefix, sprefix, c->s));
+    CKR(c, upload(&L.d_aprefix, aprefix, c->s));
+    CKR(c, dalloc(&L.d_owner, (size_t)L.N * L.M, c->s));
+    CKR(c, cudaMemsetAsync(L.d_owner, 0xff, sizeof(int) * (size_t)L.N * L.M, c->s));
+    if (!L.patches.empty()) {
+        CKR(c, launch_owner_fill(L.d_patches, L.d_prefix, (int)L.patches.size(), L.ninterior, idx_of(c, l), L.d_owner,
+                                 c->s));
+        c->st.kernel_launches++;
+    }
     build_buckets(L);
     L.work_tx = L.work_ty = 0;
     return build_work(c, l, c->tx, c->ty);
@@ -306,116 +308,40 @@ adjamr_status fill_aux(adjamr_ctx *c, int l)
 {
     Level &L = c->L[l];
     if (!c->have_medium || L.patches.empty()) return ADJAMR_OK;
-    std::vector<AuxDesc> ad;
-    ad.reserve((size_t)L.ncell);
-    for (const HPatch &p : L.patches)
-        for (int j = -c->gy; j < p.ny + c->gy; j++)
-            for (int i = -2; i < p.nx + 2; i++) ad.push_back({cell_of(c, p, i, j), p.ilo + i, p.jlo + j});
-    AuxDesc *d = nullptr;
-    CKR(c, upload(&d, ad, c->s));
-    CKR(c, launch_aux_fill(c->P.eqn, c->P.dim, d, (long long)ad.size(), L.aux, L.med, L.ncell, L.d_med, geom_of(c, l),
-                           c->s));
+    CKR(c, launch_aux_patches(c->P.eqn, L.d_patches, L.d_sprefix, (int)L.patches.size(), L.nstore, idx_of(c, l),
+                              L.aux, L.med, L.ncell, L.d_med, geom_of(c, l), c->s));
     c->st.kernel_launches++;
-    dfree(d, c->s);
     return ADJAMR_OK;
 }
 
-// coarse interpolation descriptor for fine in-domain cell (I, J) of level l
-adjamr_status coarse_desc(adjamr_ctx *c, int l, int I, int J, GhostDesc &g)
-{
-    const Level &C = c->L[l - 1];
-    int r = c->P.ratio[l - 1];
-    int ic = I / r, jc = (c->P.dim == 2) ? J / r : 0;
-    g.kind = 1;
-    g.mx = I - ic * r;
-    g.my = (c->P.dim == 2) ? J - jc * r : 0;
-    const int di[5] = {0, -1, 1, 0, 0}, dj[5] = {0, 0, 0, -1, 1};
-    long long *dst[5] = {&g.src, &g.cxm, &g.cxp, &g.cym, &g.cyp};
-    int nref = (c->P.dim == 2) ? 5 : 3;
-    for (int k = 0; k < 5; k++) *dst[k] = 0;
-    for (int k = 0; k < nref; k++) {
-        int a = ic + di[k], b = jc + dj[k], f1, f2;
-        bc_map(c, l - 1, a, b, f1, f2);
-        int pk = find_patch(C, a, b);
-        if (pk < 0) {
-            char buf[160];
-            snprintf(buf, sizeof buf, "nesting violated: level %d cell (%d,%d) not covered", l - 1, a, b);
-            c->err = buf;
-            return ADJAMR_ENEST;
-        }
-        const HPatch &p = C.patches[pk];
-        *dst[k] = cell_of(c, p, a - p.ilo, b - p.jlo);
-        g.signs |= (f1 << (2 + 2 * k)) | (f2 << (3 + 2 * k));
-    }
-    return ADJAMR_OK;
-}
-
-// ghost map of level l (needs level l-1 when l > 0)
+// ghost map of level l (needs level l-1 when l > 0), built on the device
 adjamr_status build_ghost_map(adjamr_ctx *c, int l)
 {
     Level &L = c->L[l];
     dfree(L.d_ghost, c->s);
-    L.nghost = 0;
-    std::vector<GhostDesc> gd;
-    for (const HPatch &p : L.patches)
-        for (int j = -c->gy; j < p.ny + c->gy; j++)
-            for (int i = -2; i < p.nx + 2; i++) {
-                if (i >= 0 && i < p.nx && j >= 0 && j < p.ny) continue;
-                int I = p.ilo + i, J = p.jlo + j, f1, f2;
-                bc_map(c, l, I, J, f1, f2);
-                GhostDesc g;
-                std::memset(&g, 0, sizeof g);
-                g.dst = cell_of(c, p, i, j);
-                int sk = find_patch(L, I, J);
-                if (sk >= 0) {
-                    const HPatch &sp = L.patches[sk];
-                    g.kind = 0;
-                    g.src = cell_of(c, sp, I - sp.ilo, J - sp.jlo);
-                } else {
-                    if (l == 0) {
-                        c->err = "level 0 does not cover the domain";
-                        return ADJAMR_ENEST;
-                    }
-                    TRY(coarse_desc(c, l, I, J, g));
-                }
-                g.signs |= f1 | (f2 << 1);
-                gd.push_back(g);
-            }
-    L.nghost = (long long)gd.size();
-    CKR(c, upload(&L.d_ghost, gd, c->s));
+    L.nghost = L.nghost_cells;
+    if (L.nghost == 0) return ADJAMR_OK;
+    CKR(c, dalloc(&L.d_ghost, (size_t)L.nghost, c->s));
+    const int *oc = (l > 0) ? c->L[l - 1].d_owner : nullptr;
+    LevelIdx gc = (l > 0) ? idx_of(c, l - 1) : idx_of(c, l);
+    int r = (l > 0) ? c->P.ratio[l - 1] : 1;
+    CKR(c, launch_ghost_build(L.d_patches, L.d_gprefix, (int)L.patches.size(), L.nghost, idx_of(c, l), L.d_owner, oc,
+                              gc, r, L.d_ghost, c->d_err, c->s));
+    c->st.kernel_launches++;
     return ADJAMR_OK;
 }
 
-// average-down map of level l (fine) into level l-1
+// average-down map of level l (fine) into level l-1, built on the device
 adjamr_status build_avg_map(adjamr_ctx *c, int l)
 {
     Level &F = c->L[l];
-    const Level &C = c->L[l - 1];
     dfree(F.d_avg, c->s);
-    F.navg = 0;
-    int r = c->P.ratio[l - 1];
-    std::vector<AvgDesc> ad;
-    for (const HPatch &p : F.patches) {
-        int a0 = p.ilo / r, a1 = (p.ilo + p.nx) / r;
-        int b0 = (c->P.dim == 2) ? p.jlo / r : 0, b1 = (c->P.dim == 2) ? (p.jlo + p.ny) / r : 1;
-        for (int b = b0; b < b1; b++)
-            for (int a = a0; a < a1; a++) {
-                int ck = find_patch(C, a, b);
-                if (ck < 0) {
-                    c->err = "average-down: coarse cell not covered";
-                    return ADJAMR_ENEST;
-                }
-                const HPatch &cp = C.patches[ck];
-                AvgDesc d;
-                d.dst = cell_of(c, cp, a - cp.ilo, b - cp.jlo);
-                d.src = cell_of(c, p, a * r - p.ilo, (c->P.dim == 2) ? b * r - p.jlo : 0);
-                d.fsx = p.sx;
-                d.pad = 0;
-                ad.push_back(d);
-            }
-    }
-    F.navg = (long long)ad.size();
-    CKR(c, upload(&F.d_avg, ad, c->s));
+    F.navg = F.navg_cells;
+    if (F.navg == 0) return ADJAMR_OK;
+    CKR(c, dalloc(&F.d_avg, (size_t)F.navg, c->s));
+    CKR(c, launch_avg_build(F.d_patches, F.d_aprefix, (int)F.patches.size(), F.navg, c->P.dim, c->P.ratio[l - 1],
+                            c->L[l - 1].d_owner, idx_of(c, l - 1), F.d_avg, c->d_err, c->s));
+    c->st.kernel_launches++;
     return ADJAMR_OK;
 }
 
@@ -579,7 +505,7 @@ void dilate(std::vector<unsigned char> &f, int N, int M, int w, int wy)
 }
 
 adjamr_status flag_dense(adjamr_ctx *c, int l, double tol, unsigned char *d_dense, unsigned char *d_patchflags,
-                         long long *nflag_out);
+                         long long *nflag_out, unsigned char *h_dense = nullptr, size_t h_bytes = 0);
 
 // Rebuild levels base+1 .. nlevels-1 top-down (Sec. 3).
 void harvest_timing(adjamr_ctx *c);
@@ -601,12 +527,8 @@ adjamr_status regrid_from(adjamr_ctx *c, int base, int init)
         }
         CKR(c, cudaMemsetAsync(c->d_flagbuf, 0, nb, c->s));
         long long nf = 0;
-        TRY(flag_dense(c, lev, P.tol, c->d_flagbuf, nullptr, &nf));
         std::vector<unsigned char> fl(nb, 0);
-        if (nf > 0) {
-            CKR(c, cudaMemcpyAsync(fl.data(), c->d_flagbuf, nb, cudaMemcpyDeviceToHost, c->s));
-            CKR(c, cudaStreamSynchronize(c->s));
-        }
+        TRY(flag_dense(c, lev, P.tol, c->d_flagbuf, nullptr, &nf, fl.data(), nb));
         harvest_timing(c);
         // ---- buffer, nesting mask ----
         dilate(fl, N, M, P.buffer, dim == 2 ? P.buffer : 0);
@@ -662,9 +584,12 @@ adjamr_status regrid_from(adjamr_ctx *c, int base, int init)
         old.q[0] = F.q[0]; old.q[1] = F.q[1]; old.ncell = F.ncell; old.cur = F.cur;
         old.aux = F.aux; old.med = F.med; old.d_patches = F.d_patches; old.d_work = F.d_work;
         old.d_ghost = F.d_ghost; old.d_avg = F.d_avg; old.d_prefix = F.d_prefix;
+        old.d_gprefix = F.d_gprefix; old.d_sprefix = F.d_sprefix; old.d_aprefix = F.d_aprefix; old.d_owner = F.d_owner;
         F.q[0] = F.q[1] = nullptr;
         F.aux = F.med = nullptr;
         F.d_patches = nullptr; F.d_work = nullptr; F.d_ghost = nullptr; F.d_avg = nullptr; F.d_prefix = nullptr;
+        F.d_gprefix = F.d_sprefix = F.d_aprefix = nullptr;
+        F.d_owner = nullptr;
         TRY(alloc_level(c, lev + 1, fb));
         F.cur = 0;
         F.nstep = C.nstep * r;
@@ -689,31 +614,11 @@ adjamr_status regrid_from(adjamr_ctx *c, int base, int init)
                             for (int f = 0; f < c->m; f++) host[(size_t)f * F.ncell + cell_of(c, p, i, j)] = qv[(size_t)f * n + o];
                 CKR(c, cudaMemcpyAsync(F.q[0], host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, c->s));
             } else {
-                std::vector<GhostDesc> gd;
-                gd.reserve((size_t)F.ninterior);
-                for (const HPatch &p : F.patches)
-                    for (int j = 0; j < p.ny; j++)
-                        for (int i = 0; i < p.nx; i++) {
-                            int I = p.ilo + i, J = p.jlo + j;
-                            GhostDesc g;
-                            std::memset(&g, 0, sizeof g);
-                            g.dst = cell_of(c, p, i, j);
-                            int ok = find_patch(old, I, J);
-                            if (ok >= 0) {
-                                const HPatch &op = old.patches[ok];
-                                g.kind = 2;
-                                g.src = cell_of(c, op, I - op.ilo, J - op.jlo);
-                            } else {
-                                TRY(coarse_desc(c, lev + 1, I, J, g));
-                            }
-                            gd.push_back(g);
-                        }
-                GhostDesc *d = nullptr;
-                CKR(c, upload(&d, gd, c->s));
-                CKR(c, launch_regrid_init(dim, c->m, d, (long long)gd.size(), F.q[0], F.ncell,
-                                          old.q[0] ? old.q[old.cur] : F.q[0], old.ncell, C.q[C.cur], C.ncell, r, c->s));
+                CKR(c, launch_init_new(F.d_patches, F.d_prefix, (int)F.patches.size(), F.ninterior, idx_of(c, lev + 1),
+                                       c->m, F.q[0], F.ncell, old.patches.empty() ? nullptr : old.d_owner,
+                                       old.q[0] ? old.q[old.cur] : F.q[0], old.ncell, C.d_owner, idx_of(c, lev),
+                                       C.q[C.cur], C.ncell, r, c->d_err, c->s));
                 c->st.kernel_launches++;
-                dfree(d, c->s);
             }
             TRY(build_ghost_map(c, lev + 1));
             TRY(build_avg_map(c, lev + 1));
@@ -730,7 +635,7 @@ adjamr_status regrid_from(adjamr_ctx *c, int base, int init)
 }
 
 adjamr_status flag_dense(adjamr_ctx *c, int l, double tol, unsigned char *d_dense, unsigned char *d_patchflags,
-                         long long *nflag_out)
+                         long long *nflag_out, unsigned char *h_dense, size_t h_bytes)
 {
     Level &L = c->L[l];
     *nflag_out = 0;
@@ -783,6 +688,7 @@ adjamr_status flag_dense(adjamr_ctx *c, int l, double tol, unsigned char *d_dens
     c->st.kernel_launches++;
     unsigned long long cnt = 0;
     CKR(c, cudaMemcpyAsync(&cnt, c->d_count, sizeof cnt, cudaMemcpyDeviceToHost, c->s));
+    if (h_dense) CKR(c, cudaMemcpyAsync(h_dense, d_dense, h_bytes, cudaMemcpyDeviceToHost, c->s));
     CKR(c, cudaStreamSynchronize(c->s));
     *nflag_out = (long long)cnt;
     return ADJAMR_OK;
@@ -858,6 +764,19 @@ adjamr_status average_down(adjamr_ctx *c, int lf)
     CKR(c, launch_average_down(c->P.dim, c->m, F.d_avg, F.navg, F.q[F.cur], F.ncell, C.q[1 - C.cur], C.ncell,
                                c->P.ratio[lf - 1], c->s));
     c->st.kernel_launches++;
+    return ADJAMR_OK;
+}
+
+// device-side invariant violations recorded by the regrid builders
+adjamr_status check_err(adjamr_ctx *c)
+{
+    int e = 0;
+    CKR(c, cudaMemcpyAsync(&e, c->d_err, sizeof e, cudaMemcpyDeviceToHost, c->s));
+    CKR(c, cudaStreamSynchronize(c->s));
+    if (e) {
+        c->err = "hierarchy not properly nested (device check " + std::to_string(e) + ")";
+        return ADJAMR_ENEST;
+    }
     return ADJAMR_OK;
 }
 
@@ -1028,11 +947,12 @@ adjamr_status create_impl(const adjamr_params *p, adjamr_ctx **out)
     } while (0)
     if (cudaMalloc(&c->d_cfl, sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc(&c->d_count, sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMalloc(&c->d_fout, sizeof(double)) != cudaSuccess) {
+        cudaMalloc(&c->d_fout, sizeof(double)) != cudaSuccess || cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess) {
         adjamr_destroy(c);
         return ADJAMR_ENOMEM;
     }
     cudaMemsetAsync(c->d_cfl, 0, sizeof(unsigned long long), c->s);
+    cudaMemsetAsync(c->d_err, 0, sizeof(int), c->s);
     cudaEventCreate(&c->ev0);
     cudaEventCreate(&c->ev1);
     // level 0 tiles the domain
@@ -1325,7 +1245,7 @@ adjamr_status adjamr_regrid(adjamr_ctx *ctx, int base_level, int init)
     try {
         TRY(regrid_from(ctx, base_level, init));
         CKR(ctx, cudaStreamSynchronize(ctx->s));
-        return ADJAMR_OK;
+        return check_err(ctx);
     } catch (...) {
         return ADJAMR_ENOMEM;
     }
@@ -1342,6 +1262,7 @@ adjamr_status adjamr_advance_level(adjamr_ctx *ctx, int level, int nsteps)
         CKR(ctx, cudaMemcpyAsync(&bits, ctx->d_cfl, sizeof bits, cudaMemcpyDeviceToHost, ctx->s));
         CKR(ctx, cudaStreamSynchronize(ctx->s));
         harvest_timing(ctx);
+        TRY(check_err(ctx));
         double cfl;
         std::memcpy(&cfl, &bits, sizeof cfl);
         ctx->st.cfl_max_seen = std::fmax(ctx->st.cfl_max_seen, cfl);
@@ -1567,6 +1488,7 @@ void adjamr_destroy(adjamr_ctx *ctx)
     if (ctx->d_cfl) cudaFree(ctx->d_cfl);
     if (ctx->d_count) cudaFree(ctx->d_count);
     if (ctx->d_fout) cudaFree(ctx->d_fout);
+    if (ctx->d_err) cudaFree(ctx->d_err);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     for (cudaEvent_t e : ctx->tev) cudaEventDestroy(e);

@@ -4,7 +4,23 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#ifdef __cplusplus
+#include <atomic>
+#endif
+
 #include "adjamr.h"
+
+#ifndef __CUDACC__
+// A device-resident adjoint snapshot set, shared by reference count
+// (contexts and serving slots on several host threads hold references).
+struct adjamr_adjoint {
+    std::atomic<int> refs{1};
+    int S = 0, m = 0, ax = 0, ay = 0, dim = 0;
+    double *d_snaps = nullptr;
+    unsigned char *d_wet = nullptr;
+    size_t bytes = 0;
+};
+#endif
 
 namespace adjamr {
 
@@ -124,5 +140,38 @@ cudaError_t launch_pairwise(double *a, long long n, double *out, cudaStream_t s)
 
 cudaError_t launch_gather_interior(int m, const long long *map, long long n, const double *q, long long stride,
                                    double *dst, cudaStream_t s);
+
+}  // namespace adjamr
+
+namespace adjamr {
+
+// Geometry of a level for device-side index work (boundary maps, owners).
+struct LevelIdx {
+    int dim, N, M, gy;
+    int bc[4];
+};
+
+// Device-side regrid support.  owner[J*N + I] = arena index of interior cell
+// (I, J) of the level, or -1.  Prefix arrays have np+1 entries.
+cudaError_t launch_owner_fill(const PatchDesc *p, const long long *prefix, int np, long long ncells, LevelIdx g,
+                              int *owner, cudaStream_t s);
+// ghost descriptors of every patch of a level; gprefix = ghost-cell prefix.
+// owner_c / gc describe the coarser level (owner_c null on level 0).
+cudaError_t launch_ghost_build(const PatchDesc *p, const long long *gprefix, int np, long long nghost, LevelIdx g,
+                               const int *owner, const int *owner_c, LevelIdx gc, int r, GhostDesc *out, int *err,
+                               cudaStream_t s);
+// average-down descriptors; aprefix = prefix of coarse-footprint cells per fine patch
+cudaError_t launch_avg_build(const PatchDesc *p, const long long *aprefix, int np, long long navg, int dim, int r,
+                             const int *owner_c, LevelIdx gc, AvgDesc *out, int *err, cudaStream_t s);
+// new interior cells: copy from the old arena (owner_old) or interpolate from
+// the coarser level (owner_c, qc) at its current time
+cudaError_t launch_init_new(const PatchDesc *p, const long long *prefix, int np, long long ncells, LevelIdx g, int m,
+                            double *qf, long long sf, const int *owner_old, const double *qold, long long so,
+                            const int *owner_c, LevelIdx gc, const double *qc, long long sc, int r, int *err,
+                            cudaStream_t s);
+// medium coefficients of every storage cell; sprefix = storage-cell prefix
+cudaError_t launch_aux_patches(int eqn, const PatchDesc *p, const long long *sprefix, int np, long long nstore,
+                               LevelIdx g, double *aux, double *med, long long stride, const MediumDev *mdev,
+                               LevelGeom geom, cudaStream_t s);
 
 }  // namespace adjamr

@@ -152,37 +152,33 @@ __device__ void medium_at(const MediumDev &md, const LevelGeom &g, int I, int J,
     }
 }
 
-__global__ void k_aux_fill(int eqn, int dim, const AuxDesc *__restrict__ ad, long long n, double *aux, double *med,
-                           long long stride, const MediumDev *__restrict__ mdp, LevelGeom g)
+__device__ void aux_cell(int eqn, int dim, const MediumDev &md, const LevelGeom &g, int I, int J, long long idx,
+                         double *aux, double *med, long long stride)
 {
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    const MediumDev &md = *mdp;
-    AuxDesc d = ad[t];
     double c0[2] = {0, 0}, cl[2] = {0, 0}, cb[2] = {0, 0};
-    medium_at(md, g, d.I, d.J, c0);
-    medium_at(md, g, d.I - 1, d.J, cl);
-    if (dim == 2) medium_at(md, g, d.I, d.J - 1, cb);
-    med[d.idx] = c0[0];
-    if (eqn == 0 || eqn == 1) med[stride + d.idx] = c0[1];
+    medium_at(md, g, I, J, c0);
+    medium_at(md, g, I - 1, J, cl);
+    if (dim == 2) medium_at(md, g, I, J - 1, cb);
+    med[idx] = c0[0];
+    if (eqn == 0 || eqn == 1) med[stride + idx] = c0[1];
     if (eqn == 0 || eqn == 1) {
         double c = sqrt(c0[1] / c0[0]);
         double Z = c0[0] * c;
         double ccl = sqrt(cl[1] / cl[0]);
         double Zl = cl[0] * ccl;
-        aux[d.idx] = c;
-        aux[stride + d.idx] = Z;
-        aux[2 * stride + d.idx] = 1.0 / (Zl + Z);
+        aux[idx] = c;
+        aux[stride + idx] = Z;
+        aux[2 * stride + idx] = 1.0 / (Zl + Z);
         if (dim == 2) {
             double ccb = sqrt(cb[1] / cb[0]);
             double Zb = cb[0] * ccb;
-            aux[3 * stride + d.idx] = 1.0 / (Zb + Z);
+            aux[3 * stride + idx] = 1.0 / (Zb + Z);
         } else {
-            aux[3 * stride + d.idx] = 0.0;
+            aux[3 * stride + idx] = 0.0;
         }
         if (eqn == 1) {
-            aux[4 * stride + d.idx] = 1.0 / c0[0];
-            aux[5 * stride + d.idx] = c0[1];
+            aux[4 * stride + idx] = 1.0 / c0[0];
+            aux[5 * stride + idx] = c0[1];
         }
     } else {
         double hx = 0.5 * (cl[0] + c0[0]);
@@ -192,20 +188,230 @@ __global__ void k_aux_fill(int eqn, int dim, const AuxDesc *__restrict__ ad, lon
         double ghy = kGrav * hy;
         double cey = sqrt(ghy);
         if (eqn == 2) {
-            aux[d.idx] = cex;
-            aux[stride + d.idx] = 1.0 / cex;
-            aux[2 * stride + d.idx] = ghx;
-            aux[3 * stride + d.idx] = cey;
-            aux[4 * stride + d.idx] = 1.0 / cey;
-            aux[5 * stride + d.idx] = ghy;
+            aux[idx] = cex;
+            aux[stride + idx] = 1.0 / cex;
+            aux[2 * stride + idx] = ghx;
+            aux[3 * stride + idx] = cey;
+            aux[4 * stride + idx] = 1.0 / cey;
+            aux[5 * stride + idx] = ghy;
         } else {
-            aux[d.idx] = cex;
-            aux[stride + d.idx] = 1.0 / cex;
-            aux[2 * stride + d.idx] = cey;
-            aux[3 * stride + d.idx] = 1.0 / cey;
-            aux[4 * stride + d.idx] = kGrav * c0[0];
+            aux[idx] = cex;
+            aux[stride + idx] = 1.0 / cex;
+            aux[2 * stride + idx] = cey;
+            aux[3 * stride + idx] = 1.0 / cey;
+            aux[4 * stride + idx] = kGrav * c0[0];
         }
     }
+}
+
+__global__ void k_aux_fill(int eqn, int dim, const AuxDesc *__restrict__ ad, long long n, double *aux, double *med,
+                           long long stride, const MediumDev *__restrict__ mdp, LevelGeom g)
+{
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    AuxDesc d = ad[t];
+    aux_cell(eqn, dim, *mdp, g, d.I, d.J, d.idx, aux, med, stride);
+}
+
+// ---------------------------------------------------------------- device-side regrid support
+__device__ __forceinline__ int find_in_prefix(const long long *__restrict__ prefix, int np, long long t)
+{
+    int lo = 0, hi = np - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// boundary map with the sign flags of components 1 (x-normal) and 2 (y-normal)
+__device__ __forceinline__ void bc_map_dev(const LevelIdx &g, int &I, int &J, int &f1, int &f2)
+{
+    f1 = f2 = 0;
+    if (I < 0) {
+        if (g.bc[0] == ADJAMR_BC_EXTRAP) I = 0;
+        else if (g.bc[0] == ADJAMR_BC_WALL) { I = -1 - I; f1 = 1; }
+        else I += g.N;
+    } else if (I >= g.N) {
+        if (g.bc[1] == ADJAMR_BC_EXTRAP) I = g.N - 1;
+        else if (g.bc[1] == ADJAMR_BC_WALL) { I = 2 * g.N - 1 - I; f1 = 1; }
+        else I -= g.N;
+    }
+    if (g.dim == 2) {
+        if (J < 0) {
+            if (g.bc[2] == ADJAMR_BC_EXTRAP) J = 0;
+            else if (g.bc[2] == ADJAMR_BC_WALL) { J = -1 - J; f2 = 1; }
+            else J += g.M;
+        } else if (J >= g.M) {
+            if (g.bc[3] == ADJAMR_BC_EXTRAP) J = g.M - 1;
+            else if (g.bc[3] == ADJAMR_BC_WALL) { J = 2 * g.M - 1 - J; f2 = 1; }
+            else J -= g.M;
+        }
+    } else {
+        J = 0;
+    }
+}
+
+__device__ __forceinline__ int owner_at(const int *__restrict__ owner, const LevelIdx &g, int I, int J)
+{
+    if (I < 0 || I >= g.N || J < 0 || J >= g.M) return -1;
+    return owner[(long long)J * g.N + I];
+}
+
+// coarse-interpolation descriptor at in-domain fine cell (I, J); false if a
+// coarse reference is not a cell of the coarser level (nesting violated)
+__device__ bool coarse_desc_dev(int I, int J, int r, const int *__restrict__ owner_c, const LevelIdx &gc,
+                                GhostDesc &g)
+{
+    int ic = I / r, jc = (gc.dim == 2) ? J / r : 0;
+    g.kind = 1;
+    g.mx = I - ic * r;
+    g.my = (gc.dim == 2) ? J - jc * r : 0;
+    const int di[5] = {0, -1, 1, 0, 0}, dj[5] = {0, 0, 0, -1, 1};
+    long long ref[5] = {0, 0, 0, 0, 0};
+    int nref = (gc.dim == 2) ? 5 : 3;
+    bool ok = true;
+    for (int k = 0; k < nref; k++) {
+        int a = ic + di[k], b = jc + dj[k], f1, f2;
+        bc_map_dev(gc, a, b, f1, f2);
+        int o = owner_at(owner_c, gc, a, b);
+        if (o < 0) {
+            ok = false;
+            o = 0;
+        }
+        ref[k] = o;
+        g.signs |= (f1 << (2 + 2 * k)) | (f2 << (3 + 2 * k));
+    }
+    g.src = ref[0];
+    g.cxm = ref[1];
+    g.cxp = ref[2];
+    g.cym = ref[3];
+    g.cyp = ref[4];
+    return ok;
+}
+
+__global__ void k_owner_fill(const PatchDesc *__restrict__ pd, const long long *__restrict__ prefix, int np,
+                             long long ncells, LevelIdx g, int *owner)
+{
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ncells) return;
+    int p = find_in_prefix(prefix, np, t);
+    const PatchDesc P = pd[p];
+    long long k = t - prefix[p];
+    int j = (int)(k / P.nx), i = (int)(k - (long long)j * P.nx);
+    owner[(long long)(P.jlo + j) * g.N + P.ilo + i] = (int)(P.base + (long long)(j + g.gy) * P.sx + (i + 2));
+}
+
+__global__ void k_ghost_build(const PatchDesc *__restrict__ pd, const long long *__restrict__ gprefix, int np,
+                              long long nghost, LevelIdx g, const int *__restrict__ owner,
+                              const int *__restrict__ owner_c, LevelIdx gc, int r, GhostDesc *out, int *err)
+{
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nghost) return;
+    int p = find_in_prefix(gprefix, np, t);
+    const PatchDesc P = pd[p];
+    long long k = t - gprefix[p];
+    const long long bottom = (long long)g.gy * P.sx, mid = (long long)P.ny * 4;
+    int si, sj;
+    if (k < bottom) {
+        sj = (int)(k / P.sx);
+        si = (int)(k - (long long)sj * P.sx);
+    } else if (k < bottom + mid) {
+        long long kk = k - bottom;
+        int c = (int)(kk & 3);
+        sj = g.gy + (int)(kk >> 2);
+        si = (c < 2) ? c : P.nx + c;
+    } else {
+        long long kk = k - bottom - mid;
+        int rr = (int)(kk / P.sx);
+        sj = g.gy + P.ny + rr;
+        si = (int)(kk - (long long)rr * P.sx);
+    }
+    int I = P.ilo + si - 2, J = P.jlo + sj - g.gy, f1, f2;
+    bc_map_dev(g, I, J, f1, f2);
+    GhostDesc d;
+    d.dst = P.base + (long long)sj * P.sx + si;
+    d.src = d.cxm = d.cxp = d.cym = d.cyp = 0;
+    d.kind = 0;
+    d.signs = 0;
+    d.mx = d.my = 0;
+    int o = owner_at(owner, g, I, J);
+    if (o >= 0) {
+        d.src = o;
+    } else if (owner_c) {
+        if (!coarse_desc_dev(I, J, r, owner_c, gc, d)) atomicOr(err, 1);
+    } else {
+        atomicOr(err, 2);
+        d.src = d.dst;  // harmless self-copy
+    }
+    d.signs |= f1 | (f2 << 1);
+    out[t] = d;
+}
+
+__global__ void k_avg_build(const PatchDesc *__restrict__ pd, const long long *__restrict__ aprefix, int np,
+                            long long navg, int dim, int r, const int *__restrict__ owner_c, LevelIdx gc,
+                            AvgDesc *out, int *err)
+{
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= navg) return;
+    int p = find_in_prefix(aprefix, np, t);
+    const PatchDesc P = pd[p];
+    long long k = t - aprefix[p];
+    int na = P.nx / r;
+    int bj = (int)(k / na), ai = (int)(k - (long long)bj * na);
+    int a = P.ilo / r + ai, b = (dim == 2) ? P.jlo / r + bj : 0;
+    int o = owner_at(owner_c, gc, a, b);
+    if (o < 0) {
+        atomicOr(err, 4);
+        o = 0;
+    }
+    AvgDesc d;
+    d.dst = o;
+    int gy = (dim == 2) ? 2 : 0;
+    int fj = (dim == 2) ? b * r - P.jlo : 0;
+    d.src = P.base + (long long)(fj + gy) * P.sx + (a * r - P.ilo + 2);
+    d.fsx = P.sx;
+    d.pad = 0;
+    out[t] = d;
+}
+
+__global__ void k_init_new(const PatchDesc *__restrict__ pd, const long long *__restrict__ prefix, int np,
+                           long long ncells, LevelIdx g, int m, double *qf, long long sf,
+                           const int *__restrict__ owner_old, const double *__restrict__ qold, long long so,
+                           const int *__restrict__ owner_c, LevelIdx gc, const double *__restrict__ qc, long long sc,
+                           int r, int *err)
+{
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ncells) return;
+    int p = find_in_prefix(prefix, np, t);
+    const PatchDesc P = pd[p];
+    long long k = t - prefix[p];
+    int j = (int)(k / P.nx), i = (int)(k - (long long)j * P.nx);
+    int I = P.ilo + i, J = P.jlo + j;
+    long long dst = P.base + (long long)(j + g.gy) * P.sx + (i + 2);
+    int o = owner_old ? owner_at(owner_old, g, I, J) : -1;
+    if (o >= 0) {
+        for (int f = 0; f < m; f++) qf[(long long)f * sf + dst] = qold[(long long)f * so + o];
+        return;
+    }
+    GhostDesc d;
+    d.signs = 0;
+    if (!coarse_desc_dev(I, J, r, owner_c, gc, d)) atomicOr(err, 8);
+    for (int f = 0; f < m; f++) qf[(long long)f * sf + dst] = interp_field(d, qc, qc, sc, f, 0, r, g.dim);
+}
+
+__global__ void k_aux_patches(int eqn, const PatchDesc *__restrict__ pd, const long long *__restrict__ sprefix,
+                              int np, long long nstore, LevelIdx g, double *aux, double *med, long long stride,
+                              const MediumDev *__restrict__ mdp, LevelGeom geom)
+{
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nstore) return;
+    int p = find_in_prefix(sprefix, np, t);
+    const PatchDesc P = pd[p];
+    long long k = t - sprefix[p];
+    int sj = (int)(k / P.sx), si = (int)(k - (long long)sj * P.sx);
+    aux_cell(eqn, g.dim, *mdp, geom, P.ilo + si - 2, P.jlo + sj - g.gy, P.base + k, aux, med, stride);
 }
 
 // ---------------------------------------------------------------- flagging
@@ -393,6 +599,51 @@ cudaError_t launch_aux_fill(int eqn, int dim, const AuxDesc *d, long long n, dou
 {
     if (n <= 0) return cudaSuccess;
     k_aux_fill<<<nblk(n), kT, 0, s>>>(eqn, dim, d, n, aux, med, stride, mdev, geom);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_owner_fill(const PatchDesc *p, const long long *prefix, int np, long long ncells, LevelIdx g,
+                              int *owner, cudaStream_t s)
+{
+    if (ncells <= 0) return cudaSuccess;
+    k_owner_fill<<<nblk(ncells), kT, 0, s>>>(p, prefix, np, ncells, g, owner);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ghost_build(const PatchDesc *p, const long long *gprefix, int np, long long nghost, LevelIdx g,
+                               const int *owner, const int *owner_c, LevelIdx gc, int r, GhostDesc *out, int *err,
+                               cudaStream_t s)
+{
+    if (nghost <= 0) return cudaSuccess;
+    k_ghost_build<<<nblk(nghost), kT, 0, s>>>(p, gprefix, np, nghost, g, owner, owner_c, gc, r, out, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_avg_build(const PatchDesc *p, const long long *aprefix, int np, long long navg, int dim, int r,
+                             const int *owner_c, LevelIdx gc, AvgDesc *out, int *err, cudaStream_t s)
+{
+    if (navg <= 0) return cudaSuccess;
+    k_avg_build<<<nblk(navg), kT, 0, s>>>(p, aprefix, np, navg, dim, r, owner_c, gc, out, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_new(const PatchDesc *p, const long long *prefix, int np, long long ncells, LevelIdx g, int m,
+                            double *qf, long long sf, const int *owner_old, const double *qold, long long so,
+                            const int *owner_c, LevelIdx gc, const double *qc, long long sc, int r, int *err,
+                            cudaStream_t s)
+{
+    if (ncells <= 0) return cudaSuccess;
+    k_init_new<<<nblk(ncells), kT, 0, s>>>(p, prefix, np, ncells, g, m, qf, sf, owner_old, qold, so, owner_c, gc, qc,
+                                            sc, r, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_aux_patches(int eqn, const PatchDesc *p, const long long *sprefix, int np, long long nstore,
+                               LevelIdx g, double *aux, double *med, long long stride, const MediumDev *mdev,
+                               LevelGeom geom, cudaStream_t s)
+{
+    if (nstore <= 0) return cudaSuccess;
+    k_aux_patches<<<nblk(nstore), kT, 0, s>>>(eqn, p, sprefix, np, nstore, g, aux, med, stride, mdev, geom);
     return cudaGetLastError();
 }
 

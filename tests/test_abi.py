@@ -13,7 +13,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     src = open(os.path.join(ROOT, "include", "adjamr.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:adjamr_status|void|const char \*)\s*(adjamr_\w+)\s*\(", src, flags=re.M)))
+    return sorted(set(re.findall(r"^\s*(?:adjamr_status|void|const char \*|size_t|double)\s*(adjamr_\w+)\s*\(", src,
+                                 flags=re.M)))
 
 
 def test_header_declares_the_boundary_calls():
