@@ -464,24 +464,40 @@ __global__ void k_flag(FlagArgs A)
         double y = (A.dim == 2) ? A.lo1 + ((double)J + 0.5) * A.dy : 0.0;
         double Q[3];
         for (int f = 0; f < A.m; f++) Q[f] = A.q[(long long)f * A.stride + cell];
-        double val = 0.0;
+        // flag iff the window maximum of |q^ . q| exceeds tol: the scan stops
+        // at the first term above tol (the decision is that of the full max);
+        // a dry adjoint cell sets the inner product to zero (Sec. 5.3)
+        bool hit = false;
         if (A.S >= 2) {
+            double dxa = (A.hi0 - A.lo0) / (double)A.ax;
+            int ac = (int)floor((x - A.lo0) / dxa);
+            ac = min(max(ac, 0), A.ax - 1);
+            int bc = 0;
+            if (A.dim == 2) {
+                double dya = (A.hi1 - A.lo1) / (double)A.ay;
+                bc = (int)floor((y - A.lo1) / dya);
+                bc = min(max(bc, 0), A.ay - 1);
+            }
+            bool dry = A.wet && !A.wet[(long long)bc * A.ax + ac];
             int a, b = 0;
             double wx, wy = 0.0;
             bilinear_setup(x, A.lo0, A.hi0, A.ax, a, wx);
             if (A.dim == 2) bilinear_setup(y, A.lo1, A.hi1, A.ay, b, wy);
-            if (A.mode == ADJAMR_FLAG_BRACKET_MAX) {
-                for (int n = A.nlo; n <= A.nhi; n++) {
+            if (dry) {
+                hit = 0.0 > A.tol;
+            } else if (A.mode == ADJAMR_FLAG_BRACKET_MAX) {
+                for (int n = A.nlo; n <= A.nhi && !hit; n++) {
                     double d = 0.0;
                     for (int f = 0; f < A.m; f++) {
                         double av = adj_interp(A, n, f, a, wx, b, wy);
                         d = (f == 0) ? av * Q[0] : d + av * Q[f];
                     }
-                    val = fmax(val, fabs(d));
+                    hit = fabs(d) > A.tol;
                 }
+                if (A.nlo > A.nhi) hit = 0.0 > A.tol;
             } else {
                 // q^ linear in time: values at t, at T, and snapshots strictly inside
-                for (int pass = 0; pass < 2; pass++) {
+                for (int pass = 0; pass < 2 && !hit; pass++) {
                     double tau = pass == 0 ? A.t : A.T;
                     int n = 0;
                     while (n < A.S - 2 && snap_time(A, n + 1) <= tau) n++;
@@ -492,9 +508,9 @@ __global__ void k_flag(FlagArgs A)
                         double av = (1.0 - w) * a0 + w * a1;
                         d = (f == 0) ? av * Q[0] : d + av * Q[f];
                     }
-                    val = fmax(val, fabs(d));
+                    hit = fabs(d) > A.tol;
                 }
-                for (int n = 0; n < A.S; n++) {
+                for (int n = 0; n < A.S && !hit; n++) {
                     double tn = snap_time(A, n);
                     if (!(tn > A.t && tn < A.T)) continue;
                     double d = 0.0;
@@ -502,22 +518,13 @@ __global__ void k_flag(FlagArgs A)
                         double av = adj_interp(A, n, f, a, wx, b, wy);
                         d = (f == 0) ? av * Q[0] : d + av * Q[f];
                     }
-                    val = fmax(val, fabs(d));
+                    hit = fabs(d) > A.tol;
                 }
             }
-            // dry adjoint cell: the inner product is zero (Sec. 5.3)
-            double dxa = (A.hi0 - A.lo0) / (double)A.ax;
-            int ac = (int)floor((x - A.lo0) / dxa);
-            ac = min(max(ac, 0), A.ax - 1);
-            int bc = 0;
-            if (A.dim == 2) {
-                double dya = (A.hi1 - A.lo1) / (double)A.ay;
-                bc = (int)floor((y - A.lo1) / dya);
-                bc = min(max(bc, 0), A.ay - 1);
-            }
-            if (A.wet && !A.wet[(long long)bc * A.ax + ac]) val = 0.0;
+        } else {
+            hit = 0.0 > A.tol;
         }
-        flagged = val > A.tol;
+        flagged = hit;
         if (A.flags_patch) A.flags_patch[t] = flagged ? 1 : 0;
         if (A.flags_dense) A.flags_dense[(long long)J * A.N + I] = flagged ? 1 : 0;
     }

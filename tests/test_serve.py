@@ -61,9 +61,15 @@ def test_results_identical_alone_and_in_the_mix(A):
 
 
 def test_admission_respects_the_budget(A):
+    """Equal-size requests and a budget that holds one of them: they run one
+    at a time, in arrival order, and the reserved bytes never exceed the
+    budget."""
     media, reqs, wls = _small_requests(n=4, seed=4)
+    for wl in wls:
+        wl.n0 = (32, 32)
     adj = A.solve_adjoint(wls[0])
-    need = max(A.estimate_bytes(wl) for wl in wls)
+    need = A.estimate_bytes(wls[0])
+    assert all(A.estimate_bytes(wl) == need for wl in wls)
     srv = A.Server(budget_bytes=need + 1, max_slots=4)   # room for one request at a time
     tks = [srv.submit(wl, adj) for wl in wls]
     peak_active = 0
