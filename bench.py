@@ -292,6 +292,12 @@ def run_ours(args, rank, world):
                "note": "per step: snapshot set + level-0 state host->device, J device->host; "
                        "regrid flag bitmaps also cross (internal)"}
 
+    serving = None
+    if rank == 0 and args.serve_sample > 0:
+        serving = serve_stream(A, W, args.serve_sample, [0.8], args.slots, nmin=64, nmax=256)
+        serving["note"] = ("bounded sample of the serving configuration (n0 64..256); the full 512-request stream "
+                           "is `bench.py --case serve`")
+
     if rank != 0:
         return
     # CPU baseline: the oracle as it stands, bounded sample
@@ -316,6 +322,7 @@ def run_ours(args, rank, world):
                      "cells_per_launch": cells_per_launch, "avg_launch_us": avg_launch_s * 1e6},
         "fp64_peak": {"dfma_tflops": peak_fma / 1e12, "dadd_tflops": peak_add / 1e12},
         "batched": batched,
+        "serving": serving,
         "e2e": e2e,
         "cpu_baseline": cpu,
         "clocks": ck,
@@ -324,6 +331,78 @@ def run_ours(args, rank, world):
         "J": Js[0],
     }
     print(json.dumps(line), flush=True)
+
+
+def serve_stream(A, W, nreq, rate_factors, slots, seed=0, nmin=64, nmax=512, budget=120 << 30, log_fn=log):
+    """Serving (config 5): requests from a seeded Poisson process, each a 2D
+    acoustics AMR solve flagged against the device-resident adjoint set of its
+    medium; admission by a device-memory budget.  First the saturation
+    throughput is measured with all requests submitted at once; then the
+    stream is replayed at each rate factor times that throughput.  Returns a
+    dict with p50/p99 latency (completion - arrival) per rate."""
+    import torch
+    media, reqs = W.config5(seed=seed, nreq=nreq, rate=1.0, nmin=nmin, nmax=nmax)
+    wls = [W.request_workload(r, media) for r in reqs]
+    for wl in wls:
+        wl.ts = 0.0
+        wl.tol = 1e-3
+    t = time.perf_counter()
+    adjs = {}
+    for r, wl in zip(reqs, wls):
+        if r.medium_id not in adjs:
+            adjs[r.medium_id] = A.solve_adjoint(wl)
+    torch.cuda.synchronize()
+    adj_s = time.perf_counter() - t
+    out = {"requests": nreq, "slots": slots, "budget_bytes": int(budget), "media": len(adjs),
+           "adjoint_sets_s": adj_s, "n0_range": [nmin, nmax]}
+    # saturation: everything at once
+    srv = A.Server(budget, slots)
+    t0 = srv.now()
+    tks = [srv.submit(wl, adjs[r.medium_id]) for r, wl in zip(reqs, wls)]
+    res = [srv.wait(tk) for tk in tks]
+    t1 = max(x["t_finish"] for x in res)
+    srv.close()
+    assert all(x["status"] == 0 for x in res), [x["error"] for x in res if x["status"]]
+    sat = nreq / (t1 - t0)
+    cells = sum(x["cell_updates"] for x in res)
+    out["saturation_req_per_s"] = sat
+    out["saturation_cell_updates_per_s"] = cells / (t1 - t0)
+    J_alone = {tk: x["J"] for tk, x in zip(range(nreq), res)}
+    runs = []
+    gaps = np.diff([r.arrival for r in reqs])
+    for fac in rate_factors:
+        rate = fac * sat
+        arr = np.concatenate([[0.0], np.cumsum(gaps)]) / rate   # unit-rate stream scaled to this rate
+        srv = A.Server(budget, slots)
+        start = srv.now()
+        tks = []
+        for k, (r, wl) in enumerate(zip(reqs, wls)):
+            while srv.now() - start < arr[k]:
+                time.sleep(min(0.001, max(0.0, arr[k] - (srv.now() - start))))
+            tks.append(srv.submit(wl, adjs[r.medium_id]))
+        res = [srv.wait(tk) for tk in tks]
+        srv.close()
+        lat = np.array([x["t_finish"] - x["t_submit"] for x in res])
+        span = max(x["t_finish"] for x in res) - start
+        same = all(x["J"] == J_alone[k] for k, x in enumerate(res))
+        runs.append({"rate_factor": fac, "offered_req_per_s": rate, "p50_latency_s": float(np.percentile(lat, 50)),
+                     "p99_latency_s": float(np.percentile(lat, 99)), "achieved_req_per_s": nreq / span,
+                     "cell_updates_per_s": sum(x["cell_updates"] for x in res) / span,
+                     "results_equal_to_saturation_run": bool(same)})
+        log_fn(f"serve rate x{fac}: p50 {runs[-1]['p50_latency_s']:.3f} s p99 {runs[-1]['p99_latency_s']:.3f} s")
+    out["runs"] = runs
+    return out
+
+
+def run_case_serve(args):
+    """Full serving configuration (512 requests, n0 64..512, 8 media)."""
+    import torch
+    from paper_1511_03645_gb300 import adjamr as A
+    from paper_1511_03645_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    A.load()
+    res = serve_stream(A, W, args.nreq, [0.5, 0.8, 1.0], args.slots)
+    print(json.dumps({"case": "serve", **res}), flush=True)
 
 
 def run_case_batch(args):
@@ -357,10 +436,16 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--case", default="main", choices=["main", "batch"])
+    ap.add_argument("--case", default="main", choices=["main", "batch", "serve"])
+    ap.add_argument("--nreq", type=int, default=512)
+    ap.add_argument("--slots", type=int, default=16)
+    ap.add_argument("--serve-sample", type=int, default=32)
     args = ap.parse_args()
     if args.case == "batch":
         run_case_batch(args)
+        return
+    if args.case == "serve":
+        run_case_serve(args)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -67,6 +67,7 @@ def test_admission_respects_the_budget(A):
     media, reqs, wls = _small_requests(n=4, seed=4)
     for wl in wls:
         wl.n0 = (32, 32)
+        wl.ratios = (2,)
     adj = A.solve_adjoint(wls[0])
     need = A.estimate_bytes(wls[0])
     assert all(A.estimate_bytes(wl) == need for wl in wls)
