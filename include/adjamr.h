@@ -260,6 +260,38 @@ adjamr_status adjamr_batch_cells(adjamr_batch *b, long long *cells);
 void adjamr_batch_destroy(adjamr_batch *b);
 
 /* ------------------------------------------------------------------ */
+/* Weighted sum without device allocation.                                 */
+/* ------------------------------------------------------------------ */
+/* No counterpart in the paper: this is a service for callers that cannot
+ * allocate device memory at the point where they need J-type sums -- for
+ * instance code running while its stream is being captured into a CUDA
+ * graph (an allocation there would break or serialise the capture), a
+ * solver loop with a fixed memory plan whose device memory all belongs to
+ * another framework's pool, or a latency-critical path that must never
+ * reach the allocator.
+ *
+ * *out = pairwise sum over k < n of weight*(q[k]*w[k]) -- the same terms and
+ * the same fixed pairwise tree as adjamr_integrate_functional (pairs (2i,
+ * 2i+1), an odd tail carried up), so the result equals that entry point's J
+ * for the same terms.  q, w: device arrays of n doubles; out: device pointer
+ * to one double; stream: cudaStream_t (NULL = legacy default stream).
+ * Stream-ordered, does not synchronise.
+ *
+ * Allocates nothing: its scratch is a static device array of
+ * ADJAMR_NOALLOC_MAX_TERMS doubles (8 MiB) that every GPU loading the
+ * library holds until the process exits.  n > ADJAMR_NOALLOC_MAX_TERMS is
+ * rejected with ADJAMR_EBUDGET before any work is issued.  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress) and
+ * caches it: make that first call before any stream capture.  All calls share
+ * the one array, so calls whose work overlaps on the GPU (different streams,
+ * no ordering between them) race and give wrong results; calls ordered on
+ * one stream are safe.  Nothing in the array needs clearing: each call writes
+ * every entry it reads before reading it. */
+#define ADJAMR_NOALLOC_MAX_TERMS (1 << 20)
+adjamr_status adjamr_weighted_sum_noalloc(const double *q, const double *w, long long n, double weight, double *out,
+                                          void *stream);
+
+/* ------------------------------------------------------------------ */
 /* Serving: many forward solves against shared device-resident adjoint     */
 /* snapshot sets.  Requests are admitted in arrival order as soon as a     */
 /* slot is free and their projected device memory fits the budget; every   */

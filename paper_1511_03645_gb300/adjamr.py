@@ -95,6 +95,7 @@ SYMBOLS = [
     "adjamr_batch_step_graph", "adjamr_batch_read", "adjamr_batch_cells", "adjamr_batch_destroy",
     "adjamr_fp64_peak", "adjamr_estimate_bytes", "adjamr_server_create", "adjamr_server_submit",
     "adjamr_server_poll", "adjamr_server_wait", "adjamr_server_info", "adjamr_server_now", "adjamr_server_destroy",
+    "adjamr_weighted_sum_noalloc",
 ]
 
 
@@ -151,6 +152,7 @@ def load(build_if_missing: bool = True):
             "adjamr_server_poll": [vp, ll, P(Result)],
             "adjamr_server_wait": [vp, ll, P(Result)],
             "adjamr_server_info": [vp, P(sz), ip, ip],
+            "adjamr_weighted_sum_noalloc": [vp, vp, ll, d, vp, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -572,3 +574,14 @@ class Server:
 def estimate_bytes(wl) -> int:
     p = make_params(wl)
     return int(load().adjamr_estimate_bytes(ctypes.byref(p)))
+
+
+NOALLOC_MAX_TERMS = 1 << 20
+
+
+def weighted_sum_noalloc(q_ptr: int, w_ptr: int, n: int, weight: float, out_ptr: int, stream=None):
+    """adjamr_weighted_sum_noalloc on caller-owned device buffers (raw device
+    pointers, e.g. tensor.data_ptr()); the library allocates nothing."""
+    rc = load().adjamr_weighted_sum_noalloc(ctypes.c_void_p(q_ptr), ctypes.c_void_p(w_ptr), int(n), float(weight),
+                                            ctypes.c_void_p(out_ptr), ctypes.c_void_p(stream) if stream else None)
+    _check(rc, None, "weighted_sum_noalloc")

@@ -19,7 +19,7 @@ INC = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libadjamr.so")
 
-CU = ["kernels_step.cu", "kernels_amr.cu", "fp64_peak.cu"]
+CU = ["kernels_step.cu", "kernels_amr.cu", "fp64_peak.cu", "noalloc.cu"]
 CPP = ["hierarchy.cpp", "batch.cpp", "serve.cpp"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
