@@ -134,6 +134,9 @@ typedef struct adjamr_stats {
     double cfl_max_seen;
     double step_kernel_ms;       /* CUDA-event time of step kernels, if timing enabled */
     long long step_kernel_launches;
+    double regrid_host_ms;       /* host wall time inside regrids (includes their synchronisations) */
+    double cluster_host_ms;      /* of which: buffering, nesting and Berger-Rigoutsos on the host */
+    long long level_rebuilds;    /* levels rebuilt by regrids */
 } adjamr_stats;
 
 typedef struct adjamr_ctx adjamr_ctx;

@@ -11,8 +11,8 @@
  * operations"), not because they share source.
  *
  * Compile with -O2 -ffp-contract=off: every floating-point operation below
- * is a single IEEE-754 operation (+ - * / sqrt fmin fmax fabs), evaluated in
- * the order written.
+ * is a single IEEE-754 operation (+ - * / sqrt fma fmin fmax fabs; fma is the
+ * C99 fused multiply-add, rounded once), evaluated in the order written.
  *
  * What it computes, by paper section:
  *  - Sec. 2, Eq. (eq:qtAqx), (adjoint1): forward q_t + A q_x (+ B q_y) = 0
@@ -239,29 +239,29 @@ static void edge_coef(int eqn, const double *ml, const double *mr, OEdge *e)
 static void decompose(int eqn, const OEdge *e, double d0, double dn, double *w1, double *w2)
 {
     if (eqn == O_ACOU) {
-        double a1 = (e->Zr * dn - d0) * e->izs;
-        double a2 = (d0 + e->Zl * dn) * e->izs;
+        double a1 = fma(e->Zr, dn, -d0) * e->izs;
+        double a2 = fma(e->Zl, dn, d0) * e->izs;
         w1[0] = -(e->Zl * a1);
         w1[1] = a1;
         w2[0] = e->Zr * a2;
         w2[1] = a2;
     } else if (eqn == O_ACOU_ADJ) {
-        double b1 = (e->Zr * d0 + dn) * e->izs;
-        double b2 = (e->Zl * d0 - dn) * e->izs;
+        double b1 = fma(e->Zr, d0, dn) * e->izs;
+        double b2 = fma(e->Zl, d0, -dn) * e->izs;
         w1[0] = b1;
         w1[1] = e->Zl * b1;
         w2[0] = b2;
         w2[1] = -(e->Zr * b2);
     } else if (eqn == O_SW) {
-        double b1 = (d0 - dn * e->ice) * 0.5;
-        double b2 = (d0 + dn * e->ice) * 0.5;
+        double b1 = fma(-dn, e->ice, d0) * 0.5;
+        double b2 = fma(dn, e->ice, d0) * 0.5;
         w1[0] = b1;
         w1[1] = -(e->ce * b1);
         w2[0] = b2;
         w2[1] = e->ce * b2;
     } else {
-        double b1 = (dn + d0 * e->ice) * 0.5;
-        double b2 = (dn - d0 * e->ice) * 0.5;
+        double b1 = fma(d0, e->ice, dn) * 0.5;
+        double b2 = fma(-d0, e->ice, dn) * 0.5;
         w1[0] = e->ce * b1;
         w1[1] = b1;
         w2[0] = -(e->ce * b2);
@@ -348,11 +348,11 @@ static void trans_plus(int eqn, const OEdge *e, double d0, double dn, double *ou
  * th = (W_upwind . W) / (W . W); phi = 0 when W . W = 0. */
 static double mc_phi(const double *w, const double *wu)
 {
-    double wn = w[0] * w[0] + w[1] * w[1];
+    double wn = fma(w[0], w[0], w[1] * w[1]);
     if (wn == 0.0) return 0.0;
-    double dot = wu[0] * w[0] + wu[1] * w[1];
+    double dot = fma(wu[0], w[0], wu[1] * w[1]);
     double th = dot / wn;
-    return fmax(0.0, fmin(fmin(0.5 * (1.0 + th), 2.0), 2.0 * th));
+    return fmax(0.0, fmin(fmin(fma(0.5, th, 0.5), 2.0), 2.0 * th));
 }
 
 /* second-order correction flux Fn = 1/2 sum_p cf_p phi_p W_p at edge r, with
@@ -366,10 +366,10 @@ static void limit_edge(int eqn, double dtdx, OEdgeRes *r, const OEdgeRes *rm, co
     double a1 = fabs(r->e.s1), a2 = fabs(r->e.s2);
     double cf1, cf2;
     if (eqn == O_ACOU) {
-        cf1 = a1 * (1.0 - dtdx * a1);
-        cf2 = a2 * (1.0 - dtdx * a2);
+        cf1 = a1 * fma(-dtdx, a1, 1.0);
+        cf2 = a2 * fma(-dtdx, a2, 1.0);
     } else {
-        double t1 = 1.0 - dtdx * a1, t2 = 1.0 - dtdx * a2;
+        double t1 = fma(-dtdx, a1, 1.0), t2 = fma(-dtdx, a2, 1.0);
         cf1 = (r->e.s1 < 0.0) ? -t1 : t1;
         cf2 = (r->e.s2 < 0.0) ? -t2 : t2;
     }
@@ -417,10 +417,10 @@ static double step_patch(int dim, int eqn, int nx, int ny, const double *q, cons
         }
         for (int i = 0; i < nx; i++) {
             const OEdgeRes *L = &X[i + 1], *R = &X[i + 2];
-            for (int k = 0; k < 2; k++) {
-                double xu = dtdx * ((L->ap[k] + R->am[k]) + (R->Fn[k] - L->Fn[k]));
-                qout[(long)k * nx + i] = Q(k, i, 0) - xu;
-            }
+            double A0 = (L->ap[0] + R->am[0]) + (R->Fn[0] - L->Fn[0]);
+            double A1 = (L->ap[1] + R->am[1]) + (R->Fn[1] - L->Fn[1]);
+            qout[i] = Q(0, i, 0) - dtdx * A0;
+            qout[(long)nx + i] = fma(-dtdx, A1, Q(1, i, 0));
         }
         free(X);
         return cfl;
@@ -491,7 +491,7 @@ static double step_patch(int dim, int eqn, int nx, int ny, const double *q, cons
             double tm[2], tp[2];
             trans_minus(eqn, &r->e, SY(0, e, j), 0.0, tm);
             trans_plus(eqn, &r->e, SY(0, e - 1, j), 0.0, tp);
-            for (int k = 0; k < 2; k++) FF(k, e, j) = r->Fn[k] - hy * (tm[k] + tp[k]);
+            for (int k = 0; k < 2; k++) FF(k, e, j) = fma(-hy, tm[k] + tp[k], r->Fn[k]);
             double c = dtdx * fmax(fabs(r->e.s1), fabs(r->e.s2));
             cfl = fmax(cfl, c);
         }
@@ -504,25 +504,25 @@ static double step_patch(int dim, int eqn, int nx, int ny, const double *q, cons
             double tm[2], tp[2];
             trans_minus(eqn, &r->e, SX(0, i, e), 0.0, tm);
             trans_plus(eqn, &r->e, SX(0, i, e - 1), 0.0, tp);
-            for (int k = 0; k < 2; k++) GG(k, i, e) = r->Fn[k] - hx * (tm[k] + tp[k]);
+            for (int k = 0; k < 2; k++) GG(k, i, e) = fma(-hx, tm[k] + tp[k], r->Fn[k]);
             double c = dtdy * fmax(fabs(r->e.s1), fabs(r->e.s2));
             cfl = fmax(cfl, c);
         }
-    /* cell update: Q - (X + Y), X from x-edges (comps p, u), Y from y-edges (comps p, v) */
+    /* cell update: p - (X_p + Y_p) with X = dtdx*A from the x-edges and Y =
+       dtdy*B from the y-edges; the velocities see one direction each:
+       u - dtdx*A_u and v - dtdy*B_v, each with one rounding. */
     for (int j = 0; j < ny; j++)
         for (int i = 0; i < nx; i++) {
             const OEdgeRes *L = &XE(i, j), *R = &XE(i + 1, j);
             const OEdgeRes *B = &YE(i, j), *T = &YE(i, j + 1);
-            double Xv[3], Yv[3];
+            double Ax[2], By[2];
             for (int k = 0; k < 2; k++) {
-                double xu = dtdx * ((L->ap[k] + R->am[k]) + (FF(k, i + 1, j) - FF(k, i, j)));
-                double yu = dtdy * ((B->ap[k] + T->am[k]) + (GG(k, i, j + 1) - GG(k, i, j)));
-                Xv[k == 0 ? 0 : 1] = xu;
-                Yv[k == 0 ? 0 : 2] = yu;
+                Ax[k] = (L->ap[k] + R->am[k]) + (FF(k, i + 1, j) - FF(k, i, j));
+                By[k] = (B->ap[k] + T->am[k]) + (GG(k, i, j + 1) - GG(k, i, j));
             }
-            Xv[2] = 0.0;
-            Yv[1] = 0.0;
-            for (int f = 0; f < 3; f++) qout[((long)f * ny + j) * nx + i] = Q(f, i, j) - (Xv[f] + Yv[f]);
+            qout[((long)0 * ny + j) * nx + i] = Q(0, i, j) - (dtdx * Ax[0] + dtdy * By[0]);
+            qout[((long)1 * ny + j) * nx + i] = fma(-dtdx, Ax[1], Q(1, i, j));
+            qout[((long)2 * ny + j) * nx + i] = fma(-dtdy, By[1], Q(2, i, j));
         }
     free(X);
     free(Y);
@@ -541,6 +541,7 @@ static double step_patch(int dim, int eqn, int nx, int ny, const double *q, cons
     (void)m;
     return cfl;
 }
+
 
 /* exported: one step of a standalone ghosted patch */
 int orc_step_patch(int dim, int eqn, int nx, int ny, const double *q, const double *med, double dt, double dx,

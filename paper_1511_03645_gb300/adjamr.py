@@ -81,7 +81,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("cell_updates", ctypes.c_longlong), ("adjoint_cell_updates", ctypes.c_longlong),
                 ("kernel_launches", ctypes.c_longlong), ("regrids", ctypes.c_longlong),
                 ("cfl_max_seen", ctypes.c_double), ("step_kernel_ms", ctypes.c_double),
-                ("step_kernel_launches", ctypes.c_longlong)]
+                ("step_kernel_launches", ctypes.c_longlong), ("regrid_host_ms", ctypes.c_double),
+                ("cluster_host_ms", ctypes.c_double), ("level_rebuilds", ctypes.c_longlong)]
 
 
 # every entry point declared in include/adjamr.h

@@ -10,6 +10,7 @@
 // host, cluster there (Berger-Rigoutsos, Sec. 3) and initialise the new
 // patches on the device.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -77,6 +78,8 @@ struct adjamr_ctx {
     adjamr_adjoint *adj = nullptr;
     unsigned long long *d_cfl = nullptr, *d_count = nullptr;
     int *d_err = nullptr;  // device-side invariant violations (nesting), checked after syncs
+    int *d_bbox = nullptr; // bounding box of flagged cells of the last flag call
+    std::vector<unsigned char> h_fl, h_unc, h_nest;  // host clustering scratch (regrid window)
     unsigned char *d_flagbuf = nullptr;
     size_t flagbuf_bytes = 0;
     double *d_fscratch = nullptr, *d_fout = nullptr;
@@ -505,12 +508,28 @@ void dilate(std::vector<unsigned char> &f, int N, int M, int w, int wy)
 }
 
 adjamr_status flag_dense(adjamr_ctx *c, int l, double tol, unsigned char *d_dense, unsigned char *d_patchflags,
-                         long long *nflag_out, unsigned char *h_dense = nullptr, size_t h_bytes = 0);
+                         long long *nflag_out, int *bbox_out = nullptr);
 
 // Rebuild levels base+1 .. nlevels-1 top-down (Sec. 3).
 void harvest_timing(adjamr_ctx *c);
 
+adjamr_status regrid_body(adjamr_ctx *c, int base, int init);
+
+double ms_since(std::chrono::steady_clock::time_point t)
+{
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t).count();
+}
+
 adjamr_status regrid_from(adjamr_ctx *c, int base, int init)
+{
+    c->st.regrids++;
+    auto t0 = std::chrono::steady_clock::now();
+    adjamr_status st = regrid_body(c, base, init);
+    c->st.regrid_host_ms += ms_since(t0);
+    return st;
+}
+
+adjamr_status regrid_body(adjamr_ctx *c, int base, int init)
 {
     const adjamr_params &P = c->P;
     for (int lev = base; lev < P.nlevels - 1; lev++) {
@@ -527,33 +546,58 @@ adjamr_status regrid_from(adjamr_ctx *c, int base, int init)
         }
         CKR(c, cudaMemsetAsync(c->d_flagbuf, 0, nb, c->s));
         long long nf = 0;
-        std::vector<unsigned char> fl(nb, 0);
-        TRY(flag_dense(c, lev, P.tol, c->d_flagbuf, nullptr, &nf, fl.data(), nb));
+        int bb[4];
+        TRY(flag_dense(c, lev, P.tol, c->d_flagbuf, nullptr, &nf, bb));
         harvest_timing(c);
-        // ---- buffer, nesting mask ----
-        dilate(fl, N, M, P.buffer, dim == 2 ? P.buffer : 0);
-        std::vector<unsigned char> unc(nb, 1);
-        for (const HPatch &p : C.patches)
-            for (int j = 0; j < p.ny; j++)
-                std::memset(&unc[(size_t)(p.jlo + j) * N + p.ilo], 0, (size_t)p.nx);
-        dilate(unc, N, M, 2, dim == 2 ? 2 : 0);
-        std::vector<unsigned char> nest(nb);
-        for (size_t k = 0; k < nb; k++) {
-            nest[k] = !unc[k];
-            if (!nest[k]) fl[k] = 0;
-        }
-        // ---- Berger-Rigoutsos ----
-        Clusterer cl;
-        cl.N = N;
-        cl.M = M;
-        cl.dim = dim;
-        cl.mc = (P.min_patch + r - 1) / r;
-        cl.eff = P.cluster_eff;
+        auto tc = std::chrono::steady_clock::now();
         std::vector<Box> fin;
         if (nf > 0) {
+            // Window = bounding box of the flags grown by the buffer and the
+            // nesting distance, clipped to the domain.  Clustering starts by
+            // shrinking to the flags' bounding box, so the window gives the
+            // same boxes as the whole index space.
+            const int grow = P.buffer + 2;
+            const int wi0 = std::max(0, bb[0] - grow), wi1 = std::min(N - 1, bb[1] + grow);
+            const int wj0 = (dim == 2) ? std::max(0, bb[2] - grow) : 0;
+            const int wj1 = (dim == 2) ? std::min(M - 1, bb[3] + grow) : 0;
+            const int wN = wi1 - wi0 + 1, wM = wj1 - wj0 + 1;
+            const size_t wn = (size_t)wN * wM;
+            std::vector<unsigned char> &fl = c->h_fl, &unc = c->h_unc, &nest = c->h_nest;
+            fl.resize(wn);
+            unc.assign(wn, 1);
+            nest.resize(wn);
+            CKR(c, cudaMemcpy2DAsync(fl.data(), (size_t)wN, c->d_flagbuf + (size_t)wj0 * N + wi0, (size_t)N, (size_t)wN,
+                                     (size_t)wM, cudaMemcpyDeviceToHost, c->s));
+            CKR(c, cudaStreamSynchronize(c->s));
+            // buffer, nesting mask (every cell within 2 cells covered by this level)
+            dilate(fl, wN, wM, P.buffer, dim == 2 ? P.buffer : 0);
+            for (const HPatch &p : C.patches) {
+                int a0 = std::max(p.ilo, wi0), a1 = std::min(p.ilo + p.nx - 1, wi1);
+                int b0 = std::max(p.jlo, wj0), b1 = std::min(p.jlo + p.ny - 1, wj1);
+                if (a0 > a1 || b0 > b1) continue;
+                for (int j = b0; j <= b1; j++) std::memset(&unc[(size_t)(j - wj0) * wN + (a0 - wi0)], 0, (size_t)(a1 - a0 + 1));
+            }
+            // cells beyond the window but inside the domain: the window reaches
+            // 2 cells past every flag the buffer can create, so they never
+            // decide a flagged cell's nesting
+            dilate(unc, wN, wM, 2, dim == 2 ? 2 : 0);
+            for (size_t k = 0; k < wn; k++) {
+                nest[k] = !unc[k];
+                if (!nest[k]) fl[k] = 0;
+            }
+            Clusterer cl;
+            cl.N = wN;
+            cl.M = wM;
+            cl.dim = dim;
+            cl.mc = (P.min_patch + r - 1) / r;
+            cl.eff = P.cluster_eff;
             cl.init(fl, nest);
-            cl.run(Box{0, N - 1, 0, M - 1});
-            for (const Box &b : cl.out) {
+            cl.run(Box{0, wN - 1, 0, wM - 1});
+            for (Box b : cl.out) {
+                b.i0 += wi0;
+                b.i1 += wi0;
+                b.j0 += wj0;
+                b.j1 += wj0;
                 int lx = b.i1 - b.i0 + 1, ly = b.j1 - b.j0 + 1;
                 int px = 1, py = 1;
                 while (r * ((lx + px - 1) / px) > P.max_patch) px++;
@@ -573,6 +617,7 @@ adjamr_status regrid_from(adjamr_ctx *c, int base, int init)
                 return a.j0 != b.j0 ? a.j0 < b.j0 : a.i0 < b.i0;
             });
         }
+        c->st.cluster_host_ms += ms_since(tc);
         // ---- new level lev+1 (refined boxes) ----
         std::vector<Box> fb;
         for (const Box &b : fin)
@@ -625,7 +670,7 @@ adjamr_status regrid_from(adjamr_ctx *c, int base, int init)
         }
         free_level(c, old);
         c->rebuilt_tick[lev + 1] = tick;
-        c->st.regrids++;
+        c->st.level_rebuilds++;
         if (F.patches.empty()) {
             for (int q = lev + 2; q < P.nlevels; q++) free_level(c, c->L[q]);
             break;
@@ -635,7 +680,7 @@ adjamr_status regrid_from(adjamr_ctx *c, int base, int init)
 }
 
 adjamr_status flag_dense(adjamr_ctx *c, int l, double tol, unsigned char *d_dense, unsigned char *d_patchflags,
-                         long long *nflag_out, unsigned char *h_dense, size_t h_bytes)
+                         long long *nflag_out, int *bbox_out)
 {
     Level &L = c->L[l];
     *nflag_out = 0;
@@ -683,14 +728,19 @@ adjamr_status flag_dense(adjamr_ctx *c, int l, double tol, unsigned char *d_dens
         a.S = 0;
         a.ax = a.ay = 1;
     }
+    static const int bbox_init[4] = {0x7fffffff, -1, 0x7fffffff, -1};
+    a.bbox = c->d_bbox;
     CKR(c, cudaMemsetAsync(c->d_count, 0, sizeof(unsigned long long), c->s));
+    CKR(c, cudaMemcpyAsync(c->d_bbox, bbox_init, sizeof bbox_init, cudaMemcpyHostToDevice, c->s));
     CKR(c, launch_flag(a, c->s));
     c->st.kernel_launches++;
     unsigned long long cnt = 0;
+    int bb[4];
     CKR(c, cudaMemcpyAsync(&cnt, c->d_count, sizeof cnt, cudaMemcpyDeviceToHost, c->s));
-    if (h_dense) CKR(c, cudaMemcpyAsync(h_dense, d_dense, h_bytes, cudaMemcpyDeviceToHost, c->s));
+    CKR(c, cudaMemcpyAsync(bb, c->d_bbox, sizeof bb, cudaMemcpyDeviceToHost, c->s));
     CKR(c, cudaStreamSynchronize(c->s));
     *nflag_out = (long long)cnt;
+    if (bbox_out) std::memcpy(bbox_out, bb, sizeof bb);
     return ADJAMR_OK;
 }
 
@@ -947,7 +997,8 @@ adjamr_status create_impl(const adjamr_params *p, adjamr_ctx **out)
     } while (0)
     if (cudaMalloc(&c->d_cfl, sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc(&c->d_count, sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMalloc(&c->d_fout, sizeof(double)) != cudaSuccess || cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess) {
+        cudaMalloc(&c->d_fout, sizeof(double)) != cudaSuccess || cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&c->d_bbox, 4 * sizeof(int)) != cudaSuccess) {
         adjamr_destroy(c);
         return ADJAMR_ENOMEM;
     }
@@ -1489,6 +1540,7 @@ void adjamr_destroy(adjamr_ctx *ctx)
     if (ctx->d_count) cudaFree(ctx->d_count);
     if (ctx->d_fout) cudaFree(ctx->d_fout);
     if (ctx->d_err) cudaFree(ctx->d_err);
+    if (ctx->d_bbox) cudaFree(ctx->d_bbox);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     for (cudaEvent_t e : ctx->tev) cudaEventDestroy(e);

@@ -129,6 +129,7 @@ struct FlagArgs {
     unsigned char *flags_dense;     // [M][N] of the level (may be null)
     int N;
     unsigned long long *count;
+    int *bbox;                      // [4]: min I, max I, min J, max J of flagged cells (atomics)
 };
 cudaError_t launch_flag(const FlagArgs &a, cudaStream_t s);
 

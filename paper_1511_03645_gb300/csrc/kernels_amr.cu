@@ -446,6 +446,7 @@ __global__ void k_flag(FlagArgs A)
 {
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     bool flagged = false;
+    int fI = 0x7fffffff, fJ = 0x7fffffff, gI = -1, gJ = -1;  // bounding-box contributions
     if (t < A.ncells) {
         // patch containing interior cell t (binary search on the prefix)
         int lo = 0, hi = A.np - 1;
@@ -527,9 +528,27 @@ __global__ void k_flag(FlagArgs A)
         flagged = hit;
         if (A.flags_patch) A.flags_patch[t] = flagged ? 1 : 0;
         if (A.flags_dense) A.flags_dense[(long long)J * A.N + I] = flagged ? 1 : 0;
+        if (flagged) {
+            fI = gI = I;
+            fJ = gJ = J;
+        }
     }
     unsigned bal = __ballot_sync(0xffffffffu, flagged);
-    if ((threadIdx.x & 31) == 0 && bal) atomicAdd(A.count, (unsigned long long)__popc(bal));
+    if (bal) {
+        fI = __reduce_min_sync(0xffffffffu, fI);
+        fJ = __reduce_min_sync(0xffffffffu, fJ);
+        gI = __reduce_max_sync(0xffffffffu, gI);
+        gJ = __reduce_max_sync(0xffffffffu, gJ);
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(A.count, (unsigned long long)__popc(bal));
+            if (A.bbox) {
+                atomicMin(A.bbox + 0, fI);
+                atomicMax(A.bbox + 1, gI);
+                atomicMin(A.bbox + 2, fJ);
+                atomicMax(A.bbox + 3, gJ);
+            }
+        }
+    }
 }
 
 // ---------------------------------------------------------------- functional

@@ -9,8 +9,9 @@
 // persistent grid looping over the work-list, and one launch per patch.
 //
 // Operation order follows the canonical operations of the design record
-// exactly (compiled with --fmad=false): the CPU oracle evaluates the same
-// IEEE operations in the same order, so results agree bit for bit.
+// exactly (compiled with --fmad=false, so only the explicit fma() calls of
+// that order fuse): the CPU oracle evaluates the same IEEE operations in the
+// same order, so results agree bit for bit.
 //
 // Systems: 0 acoustics (wave form, eigenvectors of A: (-Z_l,1) at -c_l,
 // (Z_r,1) at +c_r), 1 adjoint acoustics (f-wave, eigenvectors of -A^T:
@@ -62,29 +63,29 @@ template <int EQN>
 __device__ __forceinline__ void decompose(const Edge &e, double d0, double dn, double *w1, double *w2)
 {
     if constexpr (EQN == 0) {
-        double a1 = (e.Zr * dn - d0) * e.izs;
-        double a2 = (d0 + e.Zl * dn) * e.izs;
+        double a1 = fma(e.Zr, dn, -d0) * e.izs;
+        double a2 = fma(e.Zl, dn, d0) * e.izs;
         w1[0] = -(e.Zl * a1);
         w1[1] = a1;
         w2[0] = e.Zr * a2;
         w2[1] = a2;
     } else if constexpr (EQN == 1) {
-        double b1 = (e.Zr * d0 + dn) * e.izs;
-        double b2 = (e.Zl * d0 - dn) * e.izs;
+        double b1 = fma(e.Zr, d0, dn) * e.izs;
+        double b2 = fma(e.Zl, d0, -dn) * e.izs;
         w1[0] = b1;
         w1[1] = e.Zl * b1;
         w2[0] = b2;
         w2[1] = -(e.Zr * b2);
     } else if constexpr (EQN == 2) {
-        double b1 = (d0 - dn * e.ice) * 0.5;
-        double b2 = (d0 + dn * e.ice) * 0.5;
+        double b1 = fma(-dn, e.ice, d0) * 0.5;
+        double b2 = fma(dn, e.ice, d0) * 0.5;
         w1[0] = b1;
         w1[1] = -(e.ce * b1);
         w2[0] = b2;
         w2[1] = e.ce * b2;
     } else {
-        double b1 = (dn + d0 * e.ice) * 0.5;
-        double b2 = (dn - d0 * e.ice) * 0.5;
+        double b1 = fma(d0, e.ice, dn) * 0.5;
+        double b2 = fma(-d0, e.ice, dn) * 0.5;
         w1[0] = e.ce * b1;
         w1[1] = b1;
         w2[0] = -(e.ce * b2);
@@ -117,13 +118,57 @@ __device__ __forceinline__ void edge_jump(const Edge &e, const double *__restric
     }
 }
 
+// Transverse split of a fluctuation (d0, 0) whose normal component is 0:
+// left-going part s1*w1 and right-going part s2*w2 of its decomposition.
+// Equal to decompose(e, d0, 0.0, ...) except possibly for the sign of a zero
+// (terms like Z*0.0 are dropped), which no later operation can turn into a
+// different non-zero value.
+template <int EQN>
+__device__ __forceinline__ void trans_split(const Edge &e, double d0, double *am, double *ap)
+{
+    if constexpr (EQN == 0) {
+        double a1 = (-d0) * e.izs;
+        double a2 = d0 * e.izs;
+        am[0] = e.s1 * (-(e.Zl * a1));
+        am[1] = e.s1 * a1;
+        ap[0] = e.s2 * (e.Zr * a2);
+        ap[1] = e.s2 * a2;
+    } else if constexpr (EQN == 1) {
+        double b1 = (e.Zr * d0) * e.izs;
+        double b2 = (e.Zl * d0) * e.izs;
+        am[0] = e.s1 * b1;
+        am[1] = e.s1 * (e.Zl * b1);
+        ap[0] = e.s2 * b2;
+        ap[1] = e.s2 * (-(e.Zr * b2));
+    } else if constexpr (EQN == 2) {
+        double b = d0 * 0.5;
+        am[0] = e.s1 * b;
+        am[1] = e.s1 * (-(e.ce * b));
+        ap[0] = e.s2 * b;
+        ap[1] = e.s2 * (e.ce * b);
+    } else {
+        double t = d0 * e.ice;
+        double b1 = t * 0.5;
+        double b2 = (-t) * 0.5;
+        am[0] = e.s1 * (e.ce * b1);
+        am[1] = e.s1 * b1;
+        ap[0] = e.s2 * (-(e.ce * b2));
+        ap[1] = e.s2 * b2;
+    }
+}
+
+// MC limiter of the canonical operations.  Two exact shortcuts skip the
+// division: dot <= 0 gives theta <= 0 and phi = 0 (up to the sign of zero);
+// dot >= 4 wn gives a rounded theta >= 4 and phi = 2.
 __device__ __forceinline__ double mc_phi(double w0, double w1, double u0, double u1)
 {
-    double wn = w0 * w0 + w1 * w1;
+    double wn = fma(w0, w0, w1 * w1);
     if (wn == 0.0) return 0.0;
-    double dot = u0 * w0 + u1 * w1;
+    double dot = fma(u0, w0, u1 * w1);
+    if (dot <= 0.0) return 0.0;
+    if (dot >= 4.0 * wn) return 2.0;
     double th = dot / wn;
-    return fmax(0.0, fmin(fmin(0.5 * (1.0 + th), 2.0), 2.0 * th));
+    return fmax(0.0, fmin(fmin(fma(0.5, th, 0.5), 2.0), 2.0 * th));
 }
 
 template <int EQN>
@@ -131,9 +176,9 @@ __device__ __forceinline__ double corr_coef(double s, double dtd)
 {
     double a = fabs(s);
     if constexpr (EQN == 0) {
-        return a * (1.0 - dtd * a);
+        return a * fma(-dtd, a, 1.0);
     } else {
-        double t = 1.0 - dtd * a;
+        double t = fma(-dtd, a, 1.0);
         return (s < 0.0) ? -t : t;
     }
 }
@@ -319,12 +364,12 @@ __global__ void __launch_bounds__(kThreads) k_step2d(const double *__restrict__ 
                 load_edge<EQN, 0>(sA, PS, l, rr, e);
                 double dR = SY[r * (TX + 2) + ec + 1];            // Sy of the cell right of the edge
                 double dL = SY[r * (TX + 2) + ec];                // Sy of the cell left of the edge
-                double w1[2], w2[2], v1[2], v2[2];
-                decompose<EQN>(e, dR, 0.0, w1, w2);
-                decompose<EQN>(e, dL, 0.0, v1, v2);
+                double am[2], ap[2], bm[2], bp[2];
+                trans_split<EQN>(e, dR, am, ap);
+                trans_split<EQN>(e, dL, bm, bp);
                 int on = (r + 1) * XNX + ec;
                 for (int kk = 0; kk < 2; kk++)
-                    FF[kk * FFS + r * (TX + 1) + ec] = XN[kk * XNS + on] - hy * (e.s1 * w1[kk] + e.s2 * v2[kk]);
+                    FF[kk * FFS + r * (TX + 1) + ec] = fma(-hy, am[kk] + bp[kk], XN[kk * XNS + on]);
                 cfl = fmax(cfl, dtdx * fmax(fabs(e.s1), fabs(e.s2)));
             } else {
                 int kk0 = k - (tx + 1) * ty;
@@ -334,12 +379,12 @@ __global__ void __launch_bounds__(kThreads) k_step2d(const double *__restrict__ 
                 load_edge<EQN, 1>(sA, PS, l, rr, e);
                 double dU = SX[(er + 1) * TX + c];                 // Sx of the cell above the edge
                 double dD = SX[er * TX + c];                       // Sx of the cell below
-                double w1[2], w2[2], v1[2], v2[2];
-                decompose<EQN>(e, dU, 0.0, w1, w2);
-                decompose<EQN>(e, dD, 0.0, v1, v2);
+                double am[2], ap[2], bm[2], bp[2];
+                trans_split<EQN>(e, dU, am, ap);
+                trans_split<EQN>(e, dD, bm, bp);
                 int on = er * YNX + c + 1;
                 for (int kk = 0; kk < 2; kk++)
-                    GG[kk * GGS + er * TX + c] = YN[kk * YNS + on] - hx * (e.s1 * w1[kk] + e.s2 * v2[kk]);
+                    GG[kk * GGS + er * TX + c] = fma(-hx, am[kk] + bp[kk], YN[kk * YNS + on]);
                 cfl = fmax(cfl, dtdy * fmax(fabs(e.s1), fabs(e.s2)));
             }
         }
@@ -351,15 +396,15 @@ __global__ void __launch_bounds__(kThreads) k_step2d(const double *__restrict__ 
             int oB = (r + 1) * YEX + c + 1, oT = oB + YEX;
             int fL = r * (TX + 1) + c, fR = fL + 1;
             int gB = r * TX + c, gT = gB + TX;
-            double X0 = dtdx * ((XF[2 * XES + oL] + XF[oR]) + (FF[fR] - FF[fL]));
-            double X1 = dtdx * ((XF[3 * XES + oL] + XF[XES + oR]) + (FF[FFS + fR] - FF[FFS + fL]));
-            double Y0 = dtdy * ((YF[2 * YES + oB] + YF[oT]) + (GG[gT] - GG[gB]));
-            double Y1 = dtdy * ((YF[3 * YES + oB] + YF[YES + oT]) + (GG[GGS + gT] - GG[GGS + gB]));
+            double A0 = (XF[2 * XES + oL] + XF[oR]) + (FF[fR] - FF[fL]);
+            double A1 = (XF[3 * XES + oL] + XF[XES + oR]) + (FF[FFS + fR] - FF[FFS + fL]);
+            double B0 = (YF[2 * YES + oB] + YF[oT]) + (GG[gT] - GG[gB]);
+            double B1 = (YF[3 * YES + oB] + YF[YES + oT]) + (GG[GGS + gT] - GG[GGS + gB]);
             int s = (r + 2) * PX + c + 2;
             long long g = P.base + (long long)(y0 + r + 2) * P.sx + (x0 + c + 2);
-            qn[g] = sQ[s] - (X0 + Y0);
-            qn[stride + g] = sQ[PS + s] - (X1 + 0.0);
-            qn[2 * stride + g] = sQ[2 * PS + s] - (0.0 + Y1);
+            qn[g] = sQ[s] - (dtdx * A0 + dtdy * B0);
+            qn[stride + g] = fma(-dtdx, A1, sQ[PS + s]);        // u sees the x-edges only
+            qn[2 * stride + g] = fma(-dtdy, B1, sQ[2 * PS + s]); // v sees the y-edges only
         }
         __syncthreads();
     }
@@ -438,11 +483,11 @@ __global__ void __launch_bounds__(kThreads) k_step1d(const double *__restrict__ 
         __syncthreads();
         for (int c = tid; c < tx; c += kThreads) {
             int oL = c + 1, oR = c + 2;
-            double X0 = dtdx * ((XF[2 * XE + oL] + XF[oR]) + (XN[c + 1] - XN[c]));
-            double X1 = dtdx * ((XF[3 * XE + oL] + XF[XE + oR]) + (XN[XNn + c + 1] - XN[XNn + c]));
+            double A0 = (XF[2 * XE + oL] + XF[oR]) + (XN[c + 1] - XN[c]);
+            double A1 = (XF[3 * XE + oL] + XF[XE + oR]) + (XN[XNn + c + 1] - XN[XNn + c]);
             long long g = P.base + x0 + c + 2;
-            qn[g] = sQ[c + 2] - X0;
-            qn[stride + g] = sQ[PX + c + 2] - X1;
+            qn[g] = sQ[c + 2] - dtdx * A0;
+            qn[stride + g] = fma(-dtdx, A1, sQ[PX + c + 2]);
         }
         __syncthreads();
     }
