@@ -213,6 +213,7 @@ def run_ours(args, rank, world):
     regrid_ms = 0.0
     cluster_ms = 0.0
     rebuilds = 0
+    phases = [0.0] * 6
     for h in hs:
         with torch.cuda.stream(s):
             flush.zero_()
@@ -231,6 +232,7 @@ def run_ours(args, rank, world):
         regrid_ms += st["regrid_host_ms"]
         cluster_ms += st["cluster_host_ms"]
         rebuilds += st["level_rebuilds"]
+        phases = [a + b for a, b in zip(phases, st["regrid_phase_ms"])]
         Js.append(J)
     torch.cuda.synchronize()
     if dist:
@@ -337,7 +339,10 @@ def run_ours(args, rank, world):
         "gpu_launches": int(launches),
         "breakdown_per_step_ms": {"step_kernels": step_ms / args.steps, "regrid_host_wall": regrid_ms / args.steps,
                                   "of_which_clustering": cluster_ms / args.steps,
-                                  "level_rebuilds": rebuilds / args.steps},
+                                  "level_rebuilds": rebuilds / args.steps,
+                                  "regrid_phases": dict(zip(["flag_and_wait", "window_copy", "clustering",
+                                                             "arena_alloc_upload", "builder_kernels", "release_old"],
+                                                            [v / args.steps for v in phases]))},
         "adjoint_solve_s": adj_s,
         "J": Js[0],
     }

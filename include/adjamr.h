@@ -137,6 +137,10 @@ typedef struct adjamr_stats {
     double regrid_host_ms;       /* host wall time inside regrids (includes their synchronisations) */
     double cluster_host_ms;      /* of which: buffering, nesting and Berger-Rigoutsos on the host */
     long long level_rebuilds;    /* levels rebuilt by regrids */
+    /* host wall time by regrid phase: [0] flag kernel + count/box readback (waits for queued work),
+     * [1] flag-window copy, [2] clustering, [3] arena allocation and descriptor upload,
+     * [4] builder kernels (medium, init, ghost and average-down maps), [5] release of the old arena */
+    double regrid_phase_ms[6];
 } adjamr_stats;
 
 typedef struct adjamr_ctx adjamr_ctx;

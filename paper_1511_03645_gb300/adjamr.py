@@ -82,7 +82,8 @@ class Stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_longlong), ("regrids", ctypes.c_longlong),
                 ("cfl_max_seen", ctypes.c_double), ("step_kernel_ms", ctypes.c_double),
                 ("step_kernel_launches", ctypes.c_longlong), ("regrid_host_ms", ctypes.c_double),
-                ("cluster_host_ms", ctypes.c_double), ("level_rebuilds", ctypes.c_longlong)]
+                ("cluster_host_ms", ctypes.c_double), ("level_rebuilds", ctypes.c_longlong),
+                ("regrid_phase_ms", ctypes.c_double * 6)]
 
 
 # every entry point declared in include/adjamr.h
@@ -356,7 +357,9 @@ class Hierarchy:
     def stats(self) -> dict:
         s = Stats()
         _check(load().adjamr_get_stats(self.h, ctypes.byref(s)), self.h, "get_stats")
-        return {k: getattr(s, k) for k, _ in Stats._fields_}
+        d = {k: getattr(s, k) for k, _ in Stats._fields_}
+        d["regrid_phase_ms"] = list(s.regrid_phase_ms)
+        return d
 
     # ---- queries ----
     def patches(self, level: int) -> np.ndarray:

@@ -547,7 +547,9 @@ adjamr_status regrid_body(adjamr_ctx *c, int base, int init)
         CKR(c, cudaMemsetAsync(c->d_flagbuf, 0, nb, c->s));
         long long nf = 0;
         int bb[4];
+        auto tp = std::chrono::steady_clock::now();
         TRY(flag_dense(c, lev, P.tol, c->d_flagbuf, nullptr, &nf, bb));
+        c->st.regrid_phase_ms[0] += ms_since(tp);
         harvest_timing(c);
         auto tc = std::chrono::steady_clock::now();
         std::vector<Box> fin;
@@ -566,9 +568,13 @@ adjamr_status regrid_body(adjamr_ctx *c, int base, int init)
             fl.resize(wn);
             unc.assign(wn, 1);
             nest.resize(wn);
+            tp = std::chrono::steady_clock::now();
             CKR(c, cudaMemcpy2DAsync(fl.data(), (size_t)wN, c->d_flagbuf + (size_t)wj0 * N + wi0, (size_t)N, (size_t)wN,
                                      (size_t)wM, cudaMemcpyDeviceToHost, c->s));
             CKR(c, cudaStreamSynchronize(c->s));
+            double wcopy = ms_since(tp);
+            c->st.regrid_phase_ms[1] += wcopy;
+            c->st.cluster_host_ms -= wcopy;
             // buffer, nesting mask (every cell within 2 cells covered by this level)
             dilate(fl, wN, wM, P.buffer, dim == 2 ? P.buffer : 0);
             for (const HPatch &p : C.patches) {
@@ -618,6 +624,7 @@ adjamr_status regrid_body(adjamr_ctx *c, int base, int init)
             });
         }
         c->st.cluster_host_ms += ms_since(tc);
+        c->st.regrid_phase_ms[2] = c->st.cluster_host_ms;
         // ---- new level lev+1 (refined boxes) ----
         std::vector<Box> fb;
         for (const Box &b : fin)
@@ -635,7 +642,10 @@ adjamr_status regrid_body(adjamr_ctx *c, int base, int init)
         F.d_patches = nullptr; F.d_work = nullptr; F.d_ghost = nullptr; F.d_avg = nullptr; F.d_prefix = nullptr;
         F.d_gprefix = F.d_sprefix = F.d_aprefix = nullptr;
         F.d_owner = nullptr;
+        tp = std::chrono::steady_clock::now();
         TRY(alloc_level(c, lev + 1, fb));
+        c->st.regrid_phase_ms[3] += ms_since(tp);
+        tp = std::chrono::steady_clock::now();
         F.cur = 0;
         F.nstep = C.nstep * r;
         TRY(fill_aux(c, lev + 1));
@@ -668,7 +678,10 @@ adjamr_status regrid_body(adjamr_ctx *c, int base, int init)
             TRY(build_ghost_map(c, lev + 1));
             TRY(build_avg_map(c, lev + 1));
         }
+        c->st.regrid_phase_ms[4] += ms_since(tp);
+        tp = std::chrono::steady_clock::now();
         free_level(c, old);
+        c->st.regrid_phase_ms[5] += ms_since(tp);
         c->rebuilt_tick[lev + 1] = tick;
         c->st.level_rebuilds++;
         if (F.patches.empty()) {

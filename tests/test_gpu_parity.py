@@ -317,3 +317,77 @@ def test_full_size_config2_sampled_step_parity(A):
     # the adjoint snapshot at t_f is phi itself
     snaps = adj.read()
     close(snaps[-1], wl.adjoint_phi())
+
+
+def test_full_size_config1_matches_oracle_everywhere(A):
+    """Config 1 at full size (200 coarse cells, ratio 4, adjoint 800 cells x
+    100 snapshots, t_f = 20): the whole run, element by element, with the
+    layout and the flags compared at every tenth of the run."""
+    wl = W.config1()
+    snaps = O.adjoint_solve(wl)
+    adj = A.solve_adjoint(wl)
+    assert np.array_equal(adj.read(), snaps)
+    o = O.OracleHierarchy(wl)
+    o.set_adjoint(snaps)
+    o.regrid(0, init=True)
+    g = A.Hierarchy(wl)
+    g.set_adjoint(adj)
+    g.regrid(0, init=True)
+    n = o.nsteps_total()
+    refined = 0
+    for c in range(10):
+        k = n // 10 if c < 9 else n - 9 * (n // 10)
+        o.advance(k)
+        g.advance(k)
+        _compare_all(o, g, wl.nlevels)
+        refined += len(o.patches(1))
+        fo, co = o.flag(0, wl.tol)
+        fg, cg = g.flag(0, wl.tol)
+        assert co == cg and np.array_equal(fo, fg)
+    assert refined > 0
+    assert abs(g.functional() - o.functional()) <= RTOL * max(abs(o.functional()), 1e-300)
+
+
+def test_full_size_config3_sampled_step_parity(A):
+    """Config 3 at full size (coarse 200^2 over 2000 km, ratios 4, 4, 2 --
+    finest 6400^2 index space -- adjoint 1000^2 x 300 snapshots solved on the
+    GPU): after an adjoint-guided run of 4 coarse steps, one step of sampled
+    patches of every refined level is recomputed by the oracle from the GPU's
+    own ghosted input (f-wave shallow water over the bathymetry) and must
+    match bit for bit."""
+    wl = W.config3(seed=0)
+    nx = wl.adj_n[0]
+    xa = wl.lo[0] + (np.arange(nx) + 0.5) * (wl.hi[0] - wl.lo[0]) / nx
+    X, Y = np.meshgrid(xa, xa)
+    adj_med = W.bathymetry(X, Y, wl.extra["mounts"], wl.hi[0])[None]
+    adj = A.solve_adjoint(wl, medium_dense=adj_med)
+    snaps_last = adj.read()[-1]
+    close(snaps_last, wl.adjoint_phi())
+    g = A.Hierarchy(wl)
+    g.set_adjoint(adj)
+    g.regrid(0, init=True)
+    g.advance(4)
+    dt0 = g.time_info()[0]
+    rng = np.random.default_rng(3)
+    checked = 0
+    for L in range(1, wl.nlevels):
+        P = g.patches(L)
+        if len(P) == 0:
+            continue
+        g.fill_ghosts(L)
+        ks = sorted(set(rng.choice(len(P), min(3, len(P)), replace=False).tolist()))
+        inputs = [g.patch_ghosted(L, k) for k in ks]
+        flat_before = g.read_level(L)
+        g.step_level_only(L)
+        flat = g.read_level(L)
+        dt = dt0
+        for k in range(L):
+            dt = dt / wl.ratios[k]
+        dx, dy = wl.level_dx(L)
+        offs = np.concatenate([[0], np.cumsum([3 * int(a) * int(b) for _, _, a, b in P])])
+        for k, (q, med) in zip(ks, inputs):
+            ref, _ = O.step_patch(2, W.EQ_SW, q, med, dt, dx, dy)
+            assert np.array_equal(flat[offs[k]:offs[k + 1]], ref.reshape(-1)), f"level {L} patch {k}"
+            checked += 1
+        assert flat_before.shape == flat.shape
+    assert checked > 0
