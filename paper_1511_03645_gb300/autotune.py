@@ -1,0 +1,123 @@
+"""Autotuner for the fused step kernel: tile shape x work-list order x launch
+mode, measured with CUDA events on the GPU in use and cached per (GPU,
+workload key) in ``_build/autotune.json``.
+
+Every tile shape, order and launch mode computes the same bits (the work of
+a tile does not depend on the schedule), so tuning changes speed only.
+"""
+from __future__ import annotations
+
+import json
+import os
+import threading
+
+import numpy as np
+
+from . import adjamr as A
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CACHE = os.path.join(HERE, "_build", "autotune.json")
+TILES = [(32, 8), (16, 8), (16, 16), (32, 16), (64, 8), (8, 8)]
+_lock = threading.Lock()
+
+
+def _gpu_key():
+    import torch
+    p = torch.cuda.get_device_properties(torch.cuda.current_device())
+    return f"{p.name}|sm{p.major}{p.minor}|{p.multi_processor_count}"
+
+
+def _load():
+    try:
+        with open(CACHE) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(key, value):
+    with _lock:
+        d = _load()
+        d[key] = value
+        os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+        tmp = CACHE + f".tmp{os.getpid()}"
+        with open(tmp, "w") as fh:
+            json.dump(d, fh, indent=1, sort_keys=True)
+        os.replace(tmp, CACHE)
+
+
+def _time(stream, fn, reps=1):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def batch_orders(pb):
+    """Candidate work-list orders for a batch of patches."""
+    n = pb.npatch
+    cells = pb.nx.astype(np.int64) * pb.ny
+    return {
+        "natural": np.arange(n, dtype=np.int32),
+        "shuffled": np.asarray(pb.order, dtype=np.int32),
+        "largest_first": np.argsort(-cells, kind="stable").astype(np.int32),
+    }
+
+
+def tune_batch(pb, key: str, stream=None, steps: int = 4, use_cache: bool = True) -> dict:
+    """Best (tile, order, launch mode, graph) for a batch; returns a dict with
+    the choice and the measured cell-updates/s of every candidate."""
+    import torch
+    ck = f"{_gpu_key()}|batch|{key}"
+    if use_cache:
+        hit = _load().get(ck)
+        if hit:
+            return hit
+    s = torch.cuda.Stream() if stream is None else stream
+    b = A.Batch(pb, stream=s.cuda_stream)
+    cells = b.cells()
+    results = []
+    for oname, order in batch_orders(pb).items():
+        b.set_order(order)
+        for tile in TILES:
+            for mode in (A.LAUNCH_WORKLIST, A.LAUNCH_PERSISTENT):
+                b.step(1, mode=mode, tile=tile)
+                ms = _time(s, lambda: b.step(steps, mode=mode, tile=tile)) / steps
+                results.append({"order": oname, "tile": list(tile), "mode": mode, "ms": ms,
+                                "cell_updates_per_s": cells / (ms * 1e-3)})
+    b.close()
+    best = max(results, key=lambda r: r["cell_updates_per_s"])
+    out = {"best": best, "candidates": results}
+    _store(ck, out)
+    return out
+
+
+def tune_amr(wl, adj, key: str, stream=None, coarse_steps: int = 40, use_cache: bool = True) -> dict:
+    """Best tile shape for an AMR solve, timed on its first coarse steps
+    (regrids included)."""
+    import torch
+    ck = f"{_gpu_key()}|amr|{key}"
+    if use_cache:
+        hit = _load().get(ck)
+        if hit:
+            return hit
+    s = torch.cuda.Stream() if stream is None else stream
+    results = []
+    for tile in TILES:
+        h = A.Hierarchy(wl, stream=s.cuda_stream, tile=tile)
+        h.set_adjoint(adj)
+        h.regrid(0, init=True)
+        h.advance(2)   # warm-up
+        torch.cuda.synchronize()
+        ms = _time(s, lambda: h.advance(coarse_steps))
+        results.append({"tile": list(tile), "ms": ms, "cell_updates": h.stats()["cell_updates"]})
+        h.close()
+    best = min(results, key=lambda r: r["ms"])
+    out = {"best": best, "candidates": results}
+    _store(ck, out)
+    return out

@@ -56,6 +56,7 @@ struct Level {
     long long *d_aprefix = nullptr;  // coarse-footprint cells per patch (prefix)
     long long nstore = 0, nghost_cells = 0, navg_cells = 0;
     int *d_owner = nullptr;          // [M][N] arena index of each interior cell, or -1
+    char *d_meta = nullptr;          // one allocation holding d_patches and the prefix arrays
     MediumDev *d_med = nullptr;
     // lookup buckets (cells per bucket side)
     int bs = 16, nbx = 0, nby = 0;
@@ -79,7 +80,13 @@ struct adjamr_ctx {
     unsigned long long *d_cfl = nullptr, *d_count = nullptr;
     int *d_err = nullptr;  // device-side invariant violations (nesting), checked after syncs
     int *d_bbox = nullptr; // bounding box of flagged cells of the last flag call
-    std::vector<unsigned char> h_fl, h_unc, h_nest;  // host clustering scratch (regrid window)
+    std::vector<unsigned char> h_fl, h_unc, h_nest, h_tmp;  // host clustering scratch (regrid window)
+    std::vector<int> h_cnt;
+    // pinned staging for descriptor uploads; reused once the event of the
+    // previous copy has completed
+    char *h_stage = nullptr;
+    size_t h_stage_bytes = 0;
+    cudaEvent_t stage_ev = nullptr;
     unsigned char *d_flagbuf = nullptr;
     size_t flagbuf_bytes = 0;
     double *d_fscratch = nullptr, *d_fout = nullptr;
@@ -178,14 +185,20 @@ void free_level(adjamr_ctx *c, Level &L)
     dfree(L.q[1], s);
     dfree(L.aux, s);
     dfree(L.med, s);
-    dfree(L.d_patches, s);
+    if (L.d_meta) {
+        dfree(L.d_meta, s);
+        L.d_patches = nullptr;
+        L.d_prefix = L.d_gprefix = L.d_sprefix = L.d_aprefix = nullptr;
+    } else {
+        dfree(L.d_patches, s);
+        dfree(L.d_prefix, s);
+        dfree(L.d_gprefix, s);
+        dfree(L.d_sprefix, s);
+        dfree(L.d_aprefix, s);
+    }
     dfree(L.d_work, s);
     dfree(L.d_ghost, s);
     dfree(L.d_avg, s);
-    dfree(L.d_prefix, s);
-    dfree(L.d_gprefix, s);
-    dfree(L.d_sprefix, s);
-    dfree(L.d_aprefix, s);
     dfree(L.d_owner, s);
     L.patches.clear();
     L.h_work.clear();
@@ -215,6 +228,47 @@ adjamr_status build_work(adjamr_ctx *c, int l, int tx, int ty)
     L.work_tx = tx;
     L.work_ty = ty;
     return ADJAMR_OK;
+}
+
+// Copy host chunks into one new device allocation through the pinned
+// staging buffer; returns the device base, chunk k at offs[k].
+cudaError_t upload_packed(adjamr_ctx *c, const std::vector<std::pair<const void *, size_t>> &chunks, char **dev,
+                          std::vector<size_t> &offs)
+{
+    size_t total = 0;
+    offs.clear();
+    for (auto &ch : chunks) {
+        offs.push_back(total);
+        total += (ch.second + 255) / 256 * 256;
+    }
+    *dev = nullptr;
+    if (total == 0) return cudaSuccess;
+    cudaError_t e;
+    if (c->stage_ev) {
+        e = cudaEventSynchronize(c->stage_ev);  // previous copy out of the staging buffer is done
+        if (e != cudaSuccess) return e;
+    } else {
+        e = cudaEventCreateWithFlags(&c->stage_ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) return e;
+    }
+    if (c->h_stage_bytes < total) {
+        if (c->h_stage) cudaFreeHost(c->h_stage);
+        c->h_stage = nullptr;
+        size_t want = std::max(total, (size_t)1 << 20);
+        e = cudaMallocHost((void **)&c->h_stage, want);
+        if (e != cudaSuccess) {
+            c->h_stage_bytes = 0;
+            return e;
+        }
+        c->h_stage_bytes = want;
+    }
+    for (size_t k = 0; k < chunks.size(); k++)
+        if (chunks[k].second) std::memcpy(c->h_stage + offs[k], chunks[k].first, chunks[k].second);
+    e = cudaMallocAsync((void **)dev, total, c->s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(*dev, c->h_stage, total, cudaMemcpyHostToDevice, c->s);
+    if (e != cudaSuccess) return e;
+    return cudaEventRecord(c->stage_ev, c->s);
 }
 
 LevelIdx idx_of(const adjamr_ctx *c, int l)
@@ -267,19 +321,24 @@ adjamr_status alloc_level(adjamr_ctx *c, int l, const std::vector<Box> &boxes)
         sprefix.push_back(L.nstore);
         aprefix.push_back(L.navg_cells);
     }
+    // (no clearing: every ghost cell is written by the ghost fill before it is
+    // read, every interior cell by the initialisation or the step)
     CKR(c, dalloc(&L.q[0], (size_t)c->m * L.ncell, c->s));
     CKR(c, dalloc(&L.q[1], (size_t)c->m * L.ncell, c->s));
     CKR(c, dalloc(&L.aux, (size_t)c->naux * L.ncell, c->s));
     CKR(c, dalloc(&L.med, (size_t)c->nmed * L.ncell, c->s));
-    if (L.ncell > 0) {
-        CKR(c, cudaMemsetAsync(L.q[0], 0, sizeof(double) * c->m * L.ncell, c->s));
-        CKR(c, cudaMemsetAsync(L.q[1], 0, sizeof(double) * c->m * L.ncell, c->s));
+    {
+        std::vector<size_t> offs;
+        const size_t pb = sizeof(long long) * prefix.size();
+        CKR(c, upload_packed(c, {{pd.data(), sizeof(PatchDesc) * pd.size()}, {prefix.data(), pb}, {gprefix.data(), pb},
+                                 {sprefix.data(), pb}, {aprefix.data(), pb}},
+                             &L.d_meta, offs));
+        L.d_patches = pd.empty() ? nullptr : (PatchDesc *)(L.d_meta + offs[0]);
+        L.d_prefix = (long long *)(L.d_meta + offs[1]);
+        L.d_gprefix = (long long *)(L.d_meta + offs[2]);
+        L.d_sprefix = (long long *)(L.d_meta + offs[3]);
+        L.d_aprefix = (long long *)(L.d_meta + offs[4]);
     }
-    CKR(c, upload(&L.d_patches, pd, c->s));
-    CKR(c, upload(&L.d_prefix, prefix, c->s));
-    CKR(c, upload(&L.d_gprefix, gprefix, c->s));
-    CKR(c, upload(&L.d_sprefix, sprefix, c->s));
-    CKR(c, upload(&L.d_aprefix, aprefix, c->s));
     CKR(c, dalloc(&L.d_owner, (size_t)L.N * L.M, c->s));
     CKR(c, cudaMemsetAsync(L.d_owner, 0xff, sizeof(int) * (size_t)L.N * L.M, c->s));
     if (!L.patches.empty()) {
@@ -356,6 +415,8 @@ struct Clusterer {
     double eff;
     std::vector<long long> SF, SB;  // integral images of flags and of non-nestable cells
     std::vector<Box> out;
+    std::vector<long long> cs, rs;  // signature scratch (split() is not recursive)
+    std::vector<Box> stack;
 
     long long sum(const std::vector<long long> &S, int i0, int i1, int j0, int j1) const
     {
@@ -383,7 +444,8 @@ struct Clusterer {
 
     void run(Box b)
     {
-        std::vector<Box> stack{b};
+        out.clear();
+        stack.assign(1, b);
         while (!stack.empty()) {
             Box x = stack.back();
             stack.pop_back();
@@ -400,7 +462,8 @@ struct Clusterer {
     bool split(Box x, Box &L, Box &R)
     {
         if (sum(SF, x.i0, x.i1, x.j0, x.j1) == 0) return false;
-        std::vector<long long> cs(x.i1 - x.i0 + 1), rs(x.j1 - x.j0 + 1);
+        cs.resize(x.i1 - x.i0 + 1);
+        rs.resize(x.j1 - x.j0 + 1);
         for (int i = x.i0; i <= x.i1; i++) cs[i - x.i0] = sum(SF, i, i, x.j0, x.j1);
         for (int j = x.j0; j <= x.j1; j++) rs[j - x.j0] = sum(SF, x.i0, x.i1, j, j);
         int a = 0, bb = (int)cs.size() - 1, c0 = 0, c1 = (int)rs.size() - 1;
@@ -409,9 +472,10 @@ struct Clusterer {
         while (rs[c0] == 0) c0++;
         while (rs[c1] == 0) c1--;
         Box b{x.i0 + a, x.i0 + bb, x.j0 + c0, x.j0 + c1};
-        std::vector<long long> sx(cs.begin() + a, cs.begin() + bb + 1), sy(rs.begin() + c0, rs.begin() + c1 + 1);
+        // signatures of the shrunk box: the removed rows and columns hold no flag
+        const long long *sxp = cs.data() + a, *syp = rs.data() + c0;
         long long nf = 0;
-        for (long long v : sx) nf += v;
+        for (int k = 0; k <= bb - a; k++) nf += sxp[k];
         int lx = b.i1 - b.i0 + 1, ly = b.j1 - b.j0 + 1;
         long long area = (long long)lx * ly;
         bool nestable = sum(SB, b.i0, b.i1, b.j0, b.j1) == 0;
@@ -421,12 +485,12 @@ struct Clusterer {
         }
         int m = nestable ? mc : 1;
         int ndim = (dim == 2) ? 2 : 1;
-        const std::vector<long long> *sig[2] = {&sx, &sy};
+        const long long *sig[2] = {sxp, syp};
         int los[2] = {b.i0, b.j0}, his[2] = {b.i1, b.j1};
         // (1) zero signature closest to the centre
         int bd = -1, bp = 0, bdist = 0;
         for (int d = 0; d < ndim; d++) {
-            const std::vector<long long> &s = *sig[d];
+            const long long *s = sig[d];
             for (int k = los[d] + 1; k < his[d]; k++) {
                 if (s[k - los[d]] != 0) continue;
                 int dist = std::abs(2 * k - (los[d] + his[d]));
@@ -442,7 +506,7 @@ struct Clusterer {
         // (2) strongest sign change of the second difference
         long long bstr = -1;
         for (int d = 0; d < ndim; d++) {
-            const std::vector<long long> &s = *sig[d];
+            const long long *s = sig[d];
             int lo = los[d], hi = his[d];
             for (int k = lo + 1; k <= hi - 2; k++) {
                 long long d0 = s[k - 1 - lo] - 2 * s[k - lo] + s[k + 1 - lo];
@@ -478,32 +542,37 @@ struct Clusterer {
     }
 };
 
-// separable Chebyshev dilation of a 0/1 field by w cells (wy in y), in place
-void dilate(std::vector<unsigned char> &f, int N, int M, int w, int wy)
+// separable Chebyshev dilation of a 0/1 field [M][N] by w cells in x and wy
+// in y, in place, with sliding window counts (t and cnt are scratch)
+void dilate(std::vector<unsigned char> &f, int N, int M, int w, int wy, std::vector<unsigned char> &t,
+            std::vector<int> &cnt)
 {
-    std::vector<unsigned char> t(f.size());
+    t.resize(f.size());
     for (int j = 0; j < M; j++) {
-        int run = -1;  // distance to the last set cell to the left is tracked by a sliding count
-        std::vector<int> pre(N + 1, 0);
-        for (int i = 0; i < N; i++) pre[i + 1] = pre[i] + f[(size_t)j * N + i];
+        const unsigned char *row = &f[(size_t)j * N];
+        unsigned char *out = &t[(size_t)j * N];
+        int c = 0;
+        for (int i = 0; i <= std::min(w, N - 1); i++) c += row[i];
         for (int i = 0; i < N; i++) {
-            int a = std::max(0, i - w), b = std::min(N - 1, i + w);
-            t[(size_t)j * N + i] = (pre[b + 1] - pre[a]) > 0;
+            out[i] = c > 0;
+            if (i + w + 1 < N) c += row[i + w + 1];
+            if (i - w >= 0) c -= row[i - w];
         }
-        (void)run;
     }
     if (wy == 0) {
         f.swap(t);
         return;
     }
-    std::vector<int> pre(M + 1);
-    for (int i = 0; i < N; i++) {
-        pre[0] = 0;
-        for (int j = 0; j < M; j++) pre[j + 1] = pre[j] + t[(size_t)j * N + i];
-        for (int j = 0; j < M; j++) {
-            int a = std::max(0, j - wy), b = std::min(M - 1, j + wy);
-            f[(size_t)j * N + i] = (pre[b + 1] - pre[a]) > 0;
-        }
+    cnt.assign((size_t)N, 0);
+    for (int j = 0; j <= std::min(wy, M - 1); j++)
+        for (int i = 0; i < N; i++) cnt[i] += t[(size_t)j * N + i];
+    for (int j = 0; j < M; j++) {
+        unsigned char *out = &f[(size_t)j * N];
+        for (int i = 0; i < N; i++) out[i] = cnt[i] > 0;
+        if (j + wy + 1 < M)
+            for (int i = 0; i < N; i++) cnt[i] += t[(size_t)(j + wy + 1) * N + i];
+        if (j - wy >= 0)
+            for (int i = 0; i < N; i++) cnt[i] -= t[(size_t)(j - wy) * N + i];
     }
 }
 
@@ -576,7 +645,7 @@ adjamr_status regrid_body(adjamr_ctx *c, int base, int init)
             c->st.regrid_phase_ms[1] += wcopy;
             c->st.cluster_host_ms -= wcopy;
             // buffer, nesting mask (every cell within 2 cells covered by this level)
-            dilate(fl, wN, wM, P.buffer, dim == 2 ? P.buffer : 0);
+            dilate(fl, wN, wM, P.buffer, dim == 2 ? P.buffer : 0, c->h_tmp, c->h_cnt);
             for (const HPatch &p : C.patches) {
                 int a0 = std::max(p.ilo, wi0), a1 = std::min(p.ilo + p.nx - 1, wi1);
                 int b0 = std::max(p.jlo, wj0), b1 = std::min(p.jlo + p.ny - 1, wj1);
@@ -586,12 +655,12 @@ adjamr_status regrid_body(adjamr_ctx *c, int base, int init)
             // cells beyond the window but inside the domain: the window reaches
             // 2 cells past every flag the buffer can create, so they never
             // decide a flagged cell's nesting
-            dilate(unc, wN, wM, 2, dim == 2 ? 2 : 0);
+            dilate(unc, wN, wM, 2, dim == 2 ? 2 : 0, c->h_tmp, c->h_cnt);
             for (size_t k = 0; k < wn; k++) {
                 nest[k] = !unc[k];
                 if (!nest[k]) fl[k] = 0;
             }
-            Clusterer cl;
+            static thread_local Clusterer cl;  // reused scratch (one context per host thread)
             cl.N = wN;
             cl.M = wM;
             cl.dim = dim;
@@ -637,6 +706,8 @@ adjamr_status regrid_body(adjamr_ctx *c, int base, int init)
         old.aux = F.aux; old.med = F.med; old.d_patches = F.d_patches; old.d_work = F.d_work;
         old.d_ghost = F.d_ghost; old.d_avg = F.d_avg; old.d_prefix = F.d_prefix;
         old.d_gprefix = F.d_gprefix; old.d_sprefix = F.d_sprefix; old.d_aprefix = F.d_aprefix; old.d_owner = F.d_owner;
+        old.d_meta = F.d_meta;
+        F.d_meta = nullptr;
         F.q[0] = F.q[1] = nullptr;
         F.aux = F.med = nullptr;
         F.d_patches = nullptr; F.d_work = nullptr; F.d_ghost = nullptr; F.d_avg = nullptr; F.d_prefix = nullptr;
@@ -737,6 +808,7 @@ adjamr_status flag_dense(adjamr_ctx *c, int l, double tol, unsigned char *d_dens
             if (P.t0 + (double)n * a.dts >= T) nhi = n;
         a.nlo = nlo;
         a.nhi = nhi;
+        a.bmax = c->adj->d_bmax;
     } else {
         a.S = 0;
         a.ax = a.ay = 1;
@@ -1099,6 +1171,20 @@ adjamr_status read_level_impl(adjamr_ctx *c, int l, double *dst, size_t cap, boo
 
 }  // namespace
 
+// culling table of a snapshot set (see k_flag)
+cudaError_t attach_block_max(adjamr_adjoint *a, cudaStream_t s)
+{
+    a->nblk = (a->S + kSnapBlock - 1) / kSnapBlock;
+    size_t n = (size_t)a->nblk * a->m * a->ax * a->ay;
+    cudaError_t e = cudaMalloc(&a->d_bmax, n * sizeof(double));
+    if (e != cudaSuccess) {
+        a->d_bmax = nullptr;
+        return e;
+    }
+    a->bytes += n * sizeof(double);
+    return launch_block_max(a->d_snaps, a->S, a->m, a->ax, a->ay, a->dim, a->d_bmax, s);
+}
+
 // ====================================================================== ABI
 extern "C" {
 
@@ -1147,6 +1233,7 @@ adjamr_status adjamr_load_adjoint_snapshots(adjamr_ctx *ctx, const double *snaps
         if (wet) e = cudaMemcpyAsync(a->d_wet, wet, (size_t)ax * ay, cudaMemcpyHostToDevice, ctx->s);
         else e = cudaMemsetAsync(a->d_wet, 1, (size_t)ax * ay, ctx->s);
     }
+    if (e == cudaSuccess) e = attach_block_max(a, ctx->s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->s);
     if (e != cudaSuccess) {
         ctx->err = cudaGetErrorString(e);
@@ -1186,6 +1273,7 @@ void adjamr_adjoint_release(adjamr_adjoint *adj)
     if (--adj->refs > 0) return;
     if (adj->d_snaps) cudaFree(adj->d_snaps);
     if (adj->d_wet) cudaFree(adj->d_wet);
+    if (adj->d_bmax) cudaFree(adj->d_bmax);
     delete adj;
 }
 
@@ -1273,6 +1361,7 @@ adjamr_status adjamr_solve_adjoint(adjamr_ctx *ctx, const adjamr_params *ap, con
             e = launch_gather_interior(m, d_map, (long long)nx * ny, L.q[L.cur], L.ncell,
                                        h->d_snaps + (size_t)(nsnap - 1 - sidx) * per, a->s);
         }
+        if (e == cudaSuccess && st == ADJAMR_OK) e = attach_block_max(h, a->s);
         if (e == cudaSuccess && st == ADJAMR_OK) e = cudaStreamSynchronize(a->s);
         dfree(d_map, a->s);
         long long adj_updates = a->st.cell_updates;
@@ -1557,6 +1646,8 @@ void adjamr_destroy(adjamr_ctx *ctx)
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     for (cudaEvent_t e : ctx->tev) cudaEventDestroy(e);
+    if (ctx->stage_ev) cudaEventDestroy(ctx->stage_ev);
+    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
     if (ctx->adj) adjamr_adjoint_release(ctx->adj);
     delete ctx;
 }

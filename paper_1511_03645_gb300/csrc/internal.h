@@ -18,6 +18,8 @@ struct adjamr_adjoint {
     int S = 0, m = 0, ax = 0, ay = 0, dim = 0;
     double *d_snaps = nullptr;
     unsigned char *d_wet = nullptr;
+    double *d_bmax = nullptr;  // [nblk][m][ay][ax]: max |q^| over a snapshot block and a bilinear stencil
+    int nblk = 0;
     size_t bytes = 0;
 };
 #endif
@@ -130,7 +132,13 @@ struct FlagArgs {
     int N;
     unsigned long long *count;
     int *bbox;                      // [4]: min I, max I, min J, max J of flagged cells (atomics)
+    const double *bmax;             // block maxima for culling (may be null)
 };
+constexpr int kSnapBlock = 8;       // snapshots per culling block
+// block maxima of a snapshot set: bmax[blk][f][b][a] = max over the block's
+// snapshots and the cells (a..a+1, b..b+1) of |snap|
+cudaError_t launch_block_max(const double *snaps, int S, int m, int ax, int ay, int dim, double *bmax,
+                             cudaStream_t s);
 cudaError_t launch_flag(const FlagArgs &a, cudaStream_t s);
 
 // terms weight*(q0*area) of the functional into out[0..n)

@@ -487,13 +487,28 @@ __global__ void k_flag(FlagArgs A)
             if (dry) {
                 hit = 0.0 > A.tol;
             } else if (A.mode == ADJAMR_FLAG_BRACKET_MAX) {
-                for (int n = A.nlo; n <= A.nhi && !hit; n++) {
-                    double d = 0.0;
-                    for (int f = 0; f < A.m; f++) {
-                        double av = adj_interp(A, n, f, a, wx, b, wy);
-                        d = (f == 0) ? av * Q[0] : d + av * Q[f];
+                // Blocks of snapshots whose bound sum_f |q_f| max_f |q^| cannot
+                // exceed tol are skipped: every computed |q^_n . q| of the block
+                // is at most the bound times (1 + 12 ulp), far inside the 1e-12
+                // margin, so the decision is that of the full scan.
+                const long long plane = (long long)A.ax * A.ay;
+                const long long cell = (long long)b * A.ax + a;
+                for (int blk = A.nlo / kSnapBlock; blk <= A.nhi / kSnapBlock && !hit; blk++) {
+                    if (A.bmax) {
+                        double B = 0.0;
+                        for (int f = 0; f < A.m; f++)
+                            B = fma(fabs(Q[f]), A.bmax[((long long)blk * A.m + f) * plane + cell], B);
+                        if (B * (1.0 + 1e-12) <= A.tol) continue;
                     }
-                    hit = fabs(d) > A.tol;
+                    int n0 = max(A.nlo, blk * kSnapBlock), n1 = min(A.nhi, blk * kSnapBlock + kSnapBlock - 1);
+                    for (int n = n0; n <= n1 && !hit; n++) {
+                        double d = 0.0;
+                        for (int f = 0; f < A.m; f++) {
+                            double av = adj_interp(A, n, f, a, wx, b, wy);
+                            d = (f == 0) ? av * Q[0] : d + av * Q[f];
+                        }
+                        hit = fabs(d) > A.tol;
+                    }
                 }
                 if (A.nlo > A.nhi) hit = 0.0 > A.tol;
             } else {
@@ -551,6 +566,28 @@ __global__ void k_flag(FlagArgs A)
     }
 }
 
+__global__ void k_block_max(const double *__restrict__ snaps, int S, int m, int ax, int ay, int dim, int nblk,
+                            double *bmax)
+{
+    long long plane = (long long)ax * ay;
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)nblk * m * plane) return;
+    long long cell = t % plane;
+    int f = (int)((t / plane) % m);
+    int blk = (int)(t / (plane * m));
+    int a = (int)(cell % ax), b = (int)(cell / ax);
+    int a1 = min(a + 1, ax - 1), b1 = (dim == 2) ? min(b + 1, ay - 1) : b;
+    double mx = 0.0;
+    for (int n = blk * kSnapBlock; n < min(S, blk * kSnapBlock + kSnapBlock); n++) {
+        const double *sp = snaps + ((long long)n * m + f) * plane;
+        mx = fmax(mx, fabs(sp[(long long)b * ax + a]));
+        mx = fmax(mx, fabs(sp[(long long)b * ax + a1]));
+        mx = fmax(mx, fabs(sp[(long long)b1 * ax + a]));
+        mx = fmax(mx, fabs(sp[(long long)b1 * ax + a1]));
+    }
+    bmax[t] = mx;
+}
+
 // ---------------------------------------------------------------- functional
 __global__ void k_func_terms(const long long *__restrict__ idx, const double *__restrict__ area, long long n,
                              const double *__restrict__ q, double weight, double *out)
@@ -592,6 +629,7 @@ __global__ void k_gather(int m, const long long *__restrict__ map, long long n, 
 }
 
 inline unsigned nblk(long long n) { return (unsigned)((n + kT - 1) / kT); }
+inline unsigned nblk_of(long long n) { return nblk(n); }
 
 }  // namespace
 
@@ -670,6 +708,15 @@ cudaError_t launch_aux_patches(int eqn, const PatchDesc *p, const long long *spr
 {
     if (nstore <= 0) return cudaSuccess;
     k_aux_patches<<<nblk(nstore), kT, 0, s>>>(eqn, p, sprefix, np, nstore, g, aux, med, stride, mdev, geom);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_max(const double *snaps, int S, int m, int ax, int ay, int dim, double *bmax, cudaStream_t s)
+{
+    int nblk = (S + kSnapBlock - 1) / kSnapBlock;
+    long long n = (long long)nblk * m * ax * ay;
+    if (n <= 0) return cudaSuccess;
+    k_block_max<<<nblk_of(n), kT, 0, s>>>(snaps, S, m, ax, ay, dim, nblk, bmax);
     return cudaGetLastError();
 }
 
