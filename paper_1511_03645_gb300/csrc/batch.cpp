@@ -222,6 +222,8 @@ adjamr_status adjamr_batch_create(int npatch, const int *nx, const int *ny, cons
             g.dx = p.dx;
             g.dy = p.dy;
             for (int q = 0; q < 4; q++) g.bc[q] = ADJAMR_BC_EXTRAP;
+            g.dtdx = p.dt / p.dx;
+            g.dtdy = p.dt / p.dy;
             chk(launch_aux_fill(0, 2, dad, (long long)ad.size(), b->aux, b->med, off, b->d_media + p.mid, g, b->s));
             chk(cudaFreeAsync(dad, b->s));
             if (q0)

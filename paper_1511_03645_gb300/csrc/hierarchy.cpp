@@ -362,6 +362,8 @@ LevelGeom geom_of(const adjamr_ctx *c, int l)
     g.dx = c->L[l].dx;
     g.dy = c->L[l].dy;
     for (int k = 0; k < 4; k++) g.bc[k] = c->P.bc[k];
+    g.dtdx = c->L[l].dt / c->L[l].dx;
+    g.dtdy = (c->P.dim == 2) ? c->L[l].dt / c->L[l].dy : 0.0;
     return g;
 }
 
@@ -967,6 +969,11 @@ adjamr_status set_medium_impl(adjamr_ctx *c, const adjamr_medium *m)
             }
             md.axis = m->axis;
             md.nl = m->nlayers;
+            for (int k = 0; k < m->nlayers; k++)
+                if (!(m->f0[k] > 0.0) || (c->nmed > 1 && !(m->f1[k] > 0.0))) {
+                    c->err = "medium must be positive (rho, K > 0; hbar > 0)";
+                    return ADJAMR_EINVAL;
+                }
             for (int k = 0; k < m->nlayers - 1; k++) md.iface[k] = m->iface[k];
             for (int k = 0; k < m->nlayers; k++) {
                 md.f0[k] = m->f0[k];
@@ -978,6 +985,11 @@ adjamr_status set_medium_impl(adjamr_ctx *c, const adjamr_medium *m)
                 return ADJAMR_EINVAL;
             }
             size_t n = (size_t)c->nmed * md.N * md.M;
+            for (size_t k = 0; k < n; k++)
+                if (!(m->dense[l][k] > 0.0)) {
+                    c->err = "medium must be positive (rho, K > 0; hbar > 0)";
+                    return ADJAMR_EINVAL;
+                }
             double *d = nullptr;
             CKR(c, dalloc(&d, n, c->s));
             CKR(c, cudaMemcpyAsync(d, m->dense[l], n * sizeof(double), cudaMemcpyHostToDevice, c->s));

@@ -35,7 +35,12 @@ constexpr double kGrav = 9.81;
 //  ACOUSTICS_ADJOINT:  c, Z, izs_x, izs_y, 1/rho, K
 //  SW:                 ce_x, 1/ce_x, g*he_x, ce_y, 1/ce_y, g*he_y
 //  SW_ADJOINT:         ce_x, 1/ce_x, ce_y, 1/ce_y, g*hbar
-__host__ __device__ constexpr int naux_of(int eqn) { return eqn == 0 ? 4 : (eqn == 3 ? 5 : 6); }
+// followed (at index kCfBase(eqn)) by the level's correction coefficients of
+// the two waves and the Courant number of each edge: cf1_x, cf2_x, cfl_x,
+// cf1_y, cf2_y, cfl_y (they depend on dt/dx of the level; the same operations
+// the step would perform per edge, done once when the patch is created).
+__host__ __device__ constexpr int kCfBase(int eqn) { return eqn == 0 ? 4 : (eqn == 3 ? 5 : 6); }
+__host__ __device__ constexpr int naux_of(int eqn) { return kCfBase(eqn) + 6; }
 __host__ __device__ constexpr int nmed_of(int eqn) { return (eqn == 2 || eqn == 3) ? 1 : 2; }
 
 // A patch in a level arena.  Storage cell (si, sj) (si in [0, sx), sj in
@@ -94,6 +99,7 @@ struct LevelGeom {
     int dim, N, M;
     double lo0, lo1, dx, dy;
     int bc[4];
+    double dtdx, dtdy;   // of the level (correction coefficients, Courant numbers)
 };
 
 // ---- kernel launchers (kernels_step.cu / kernels_amr.cu) ----

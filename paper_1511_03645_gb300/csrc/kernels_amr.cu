@@ -152,6 +152,16 @@ __device__ void medium_at(const MediumDev &md, const LevelGeom &g, int I, int J,
     }
 }
 
+// correction coefficient of a wave of speed s (canonical operations):
+// |s| (1 - dtdx |s|) for the wave form, sign(s) (1 - dtdx |s|) for f-waves
+__device__ __forceinline__ double cf_of(int eqn, double s, double dtd)
+{
+    double a = fabs(s);
+    if (eqn == 0) return a * fma(-dtd, a, 1.0);
+    double t = fma(-dtd, a, 1.0);
+    return (s < 0.0) ? -t : t;
+}
+
 __device__ void aux_cell(int eqn, int dim, const MediumDev &md, const LevelGeom &g, int I, int J, long long idx,
                          double *aux, double *med, long long stride)
 {
@@ -180,6 +190,16 @@ __device__ void aux_cell(int eqn, int dim, const MediumDev &md, const LevelGeom 
             aux[4 * stride + idx] = 1.0 / c0[0];
             aux[5 * stride + idx] = c0[1];
         }
+        // wave speeds of the x-edge (-c_{i-1}, c_i) and the y-edge (-c_{j-1}, c_j)
+        double ccb = (dim == 2) ? sqrt(cb[1] / cb[0]) : ccl;
+        double s1x = -ccl, s2x = c, s1y = -ccb, s2y = c;
+        int o = kCfBase(eqn);
+        aux[(o + 0) * stride + idx] = cf_of(eqn, s1x, g.dtdx);
+        aux[(o + 1) * stride + idx] = cf_of(eqn, s2x, g.dtdx);
+        aux[(o + 2) * stride + idx] = g.dtdx * fmax(fabs(s1x), fabs(s2x));
+        aux[(o + 3) * stride + idx] = (dim == 2) ? cf_of(eqn, s1y, g.dtdy) : 0.0;
+        aux[(o + 4) * stride + idx] = (dim == 2) ? cf_of(eqn, s2y, g.dtdy) : 0.0;
+        aux[(o + 5) * stride + idx] = (dim == 2) ? g.dtdy * fmax(fabs(s1y), fabs(s2y)) : 0.0;
     } else {
         double hx = 0.5 * (cl[0] + c0[0]);
         double ghx = kGrav * hx;
@@ -187,6 +207,13 @@ __device__ void aux_cell(int eqn, int dim, const MediumDev &md, const LevelGeom 
         double hy = (dim == 2) ? 0.5 * (cb[0] + c0[0]) : hx;
         double ghy = kGrav * hy;
         double cey = sqrt(ghy);
+        int o = kCfBase(eqn);
+        aux[(o + 0) * stride + idx] = cf_of(eqn, -cex, g.dtdx);
+        aux[(o + 1) * stride + idx] = cf_of(eqn, cex, g.dtdx);
+        aux[(o + 2) * stride + idx] = g.dtdx * fmax(fabs(-cex), fabs(cex));
+        aux[(o + 3) * stride + idx] = (dim == 2) ? cf_of(eqn, -cey, g.dtdy) : 0.0;
+        aux[(o + 4) * stride + idx] = (dim == 2) ? cf_of(eqn, cey, g.dtdy) : 0.0;
+        aux[(o + 5) * stride + idx] = (dim == 2) ? g.dtdy * fmax(fabs(-cey), fabs(cey)) : 0.0;
         if (eqn == 2) {
             aux[idx] = cex;
             aux[stride + idx] = 1.0 / cex;

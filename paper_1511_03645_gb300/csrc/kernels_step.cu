@@ -171,22 +171,23 @@ __device__ __forceinline__ double mc_phi(double w0, double w1, double u0, double
     return fmax(0.0, fmin(fmin(fma(0.5, th, 0.5), 2.0), 2.0 * th));
 }
 
-template <int EQN>
-__device__ __forceinline__ double corr_coef(double s, double dtd)
+// s > 0.0 decided on the integer pipe (identical for every non-NaN double)
+__device__ __forceinline__ bool positive(double s) { return __double_as_longlong(s) > 0; }
+
+// max of non-negative doubles through their bit patterns (integer pipe)
+__device__ __forceinline__ long long bmax(long long a, double v)
 {
-    double a = fabs(s);
-    if constexpr (EQN == 0) {
-        return a * fma(-dtd, a, 1.0);
-    } else {
-        double t = fma(-dtd, a, 1.0);
-        return (s < 0.0) ? -t : t;
-    }
+    long long b = __double_as_longlong(v);
+    return b > a ? b : a;
 }
 
-__device__ __forceinline__ void cfl_reduce(double c, unsigned long long *cfl_bits)
+__device__ __forceinline__ void cfl_reduce(long long c, unsigned long long *cfl_bits)
 {
-    for (int o = 16; o > 0; o >>= 1) c = fmax(c, __shfl_xor_sync(0xffffffffu, c, o));
-    if ((threadIdx.x & 31) == 0 && c > 0.0) atomicMax(cfl_bits, (unsigned long long)__double_as_longlong(c));
+    for (int o = 16; o > 0; o >>= 1) {
+        long long x = __shfl_xor_sync(0xffffffffu, c, o);
+        c = x > c ? x : c;
+    }
+    if ((threadIdx.x & 31) == 0 && c > 0) atomicMax(cfl_bits, (unsigned long long)c);
 }
 
 // ---------------------------------------------------------------- 2D
@@ -236,7 +237,8 @@ __global__ void __launch_bounds__(kThreads) k_step2d(const double *__restrict__ 
     constexpr int SXS = (TY + 2) * TX, FFS = TY * (TX + 1), SYS = TY * (TX + 2), GGS = (TY + 1) * TX;
 
     const int tid = threadIdx.x;
-    double cfl = 0.0;
+    constexpr int CF = kCfBase(EQN);
+    long long cfl = 0;
     for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
         const WorkItem wi = work[w];
         const PatchDesc P = patches[wi.patch];
@@ -303,12 +305,12 @@ __global__ void __launch_bounds__(kThreads) k_step2d(const double *__restrict__ 
                 int l = (er + 1) * PX + ec + 1, r = l + 1;
                 Edge e;
                 load_edge<EQN, 0>(sA, PS, l, r, e);
-                int u1 = (e.s1 > 0.0) ? o - 1 : o + 1;
-                int u2 = (e.s2 > 0.0) ? o - 1 : o + 1;
+                int u1 = positive(e.s1) ? o - 1 : o + 1;
+                int u2 = positive(e.s2) ? o - 1 : o + 1;
                 double w10 = XW[o], w1n = XW[XES + o], w20 = XW[2 * XES + o], w2n = XW[3 * XES + o];
                 double p1 = mc_phi(w10, w1n, XW[u1], XW[XES + u1]);
                 double p2 = mc_phi(w20, w2n, XW[2 * XES + u2], XW[3 * XES + u2]);
-                double cf1 = corr_coef<EQN>(e.s1, dtdx), cf2 = corr_coef<EQN>(e.s2, dtdx);
+                double cf1 = sA[CF * PS + r], cf2 = sA[(CF + 1) * PS + r];
                 int on = er * XNX + ec;
                 XN[on] = 0.5 * (cf1 * (p1 * w10) + cf2 * (p2 * w20));
                 XN[XNS + on] = 0.5 * (cf1 * (p1 * w1n) + cf2 * (p2 * w2n));
@@ -319,12 +321,12 @@ __global__ void __launch_bounds__(kThreads) k_step2d(const double *__restrict__ 
                 int l = (er + 1) * PX + ec + 1, r = l + PX;
                 Edge e;
                 load_edge<EQN, 1>(sA, PS, l, r, e);
-                int u1 = (e.s1 > 0.0) ? o - YEX : o + YEX;
-                int u2 = (e.s2 > 0.0) ? o - YEX : o + YEX;
+                int u1 = positive(e.s1) ? o - YEX : o + YEX;
+                int u2 = positive(e.s2) ? o - YEX : o + YEX;
                 double w10 = YW[o], w1n = YW[YES + o], w20 = YW[2 * YES + o], w2n = YW[3 * YES + o];
                 double p1 = mc_phi(w10, w1n, YW[u1], YW[YES + u1]);
                 double p2 = mc_phi(w20, w2n, YW[2 * YES + u2], YW[3 * YES + u2]);
-                double cf1 = corr_coef<EQN>(e.s1, dtdy), cf2 = corr_coef<EQN>(e.s2, dtdy);
+                double cf1 = sA[(CF + 3) * PS + r], cf2 = sA[(CF + 4) * PS + r];
                 int on = er * YNX + ec;
                 YN[on] = 0.5 * (cf1 * (p1 * w10) + cf2 * (p2 * w20));
                 YN[YNS + on] = 0.5 * (cf1 * (p1 * w1n) + cf2 * (p2 * w2n));
@@ -370,7 +372,7 @@ __global__ void __launch_bounds__(kThreads) k_step2d(const double *__restrict__ 
                 int on = (r + 1) * XNX + ec;
                 for (int kk = 0; kk < 2; kk++)
                     FF[kk * FFS + r * (TX + 1) + ec] = fma(-hy, am[kk] + bp[kk], XN[kk * XNS + on]);
-                cfl = fmax(cfl, dtdx * fmax(fabs(e.s1), fabs(e.s2)));
+                cfl = bmax(cfl, sA[(CF + 2) * PS + rr]);
             } else {
                 int kk0 = k - (tx + 1) * ty;
                 int er = kk0 / tx, c = kk0 - er * tx;              // y-edge ey = er, column c
@@ -385,7 +387,7 @@ __global__ void __launch_bounds__(kThreads) k_step2d(const double *__restrict__ 
                 int on = er * YNX + c + 1;
                 for (int kk = 0; kk < 2; kk++)
                     GG[kk * GGS + er * TX + c] = fma(-hx, am[kk] + bp[kk], YN[kk * YNS + on]);
-                cfl = fmax(cfl, dtdy * fmax(fabs(e.s1), fabs(e.s2)));
+                cfl = bmax(cfl, sA[(CF + 5) * PS + rr]);
             }
         }
         __syncthreads();
@@ -436,7 +438,8 @@ __global__ void __launch_bounds__(kThreads) k_step1d(const double *__restrict__ 
     double *XF = XW + 4 * XE;
     double *XN = XF + 4 * XE;
     const int tid = threadIdx.x;
-    double cfl = 0.0;
+    constexpr int CF = kCfBase(EQN);
+    long long cfl = 0;
     for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
         const WorkItem wi = work[w];
         const PatchDesc P = patches[wi.patch];
@@ -470,15 +473,15 @@ __global__ void __launch_bounds__(kThreads) k_step1d(const double *__restrict__ 
             int o = k + 1, l = k + 1, r = k + 2;
             Edge e;
             load_edge<EQN, 0>(sA, PX, l, r, e);
-            int u1 = (e.s1 > 0.0) ? o - 1 : o + 1;
-            int u2 = (e.s2 > 0.0) ? o - 1 : o + 1;
+            int u1 = positive(e.s1) ? o - 1 : o + 1;
+            int u2 = positive(e.s2) ? o - 1 : o + 1;
             double w10 = XW[o], w1n = XW[XE + o], w20 = XW[2 * XE + o], w2n = XW[3 * XE + o];
             double p1 = mc_phi(w10, w1n, XW[u1], XW[XE + u1]);
             double p2 = mc_phi(w20, w2n, XW[2 * XE + u2], XW[3 * XE + u2]);
-            double cf1 = corr_coef<EQN>(e.s1, dtdx), cf2 = corr_coef<EQN>(e.s2, dtdx);
+            double cf1 = sA[CF * PX + r], cf2 = sA[(CF + 1) * PX + r];
             XN[k] = 0.5 * (cf1 * (p1 * w10) + cf2 * (p2 * w20));
             XN[XNn + k] = 0.5 * (cf1 * (p1 * w1n) + cf2 * (p2 * w2n));
-            cfl = fmax(cfl, dtdx * fmax(fabs(e.s1), fabs(e.s2)));
+            cfl = bmax(cfl, sA[(CF + 2) * PX + r]);
         }
         __syncthreads();
         for (int c = tid; c < tx; c += kThreads) {
