@@ -182,10 +182,16 @@ def run_ours(args, rank, world):
 
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
 
+    # step-kernel tile per level (same bits for every tile; speed only)
+    from paper_1511_03645_gb300 import autotune as AT
+    tuned = AT.tune_amr(wl, adj, key="acoustics2d-100-r2r4", stream=s, use_cache=False)
+    log(f"tiles per level: {tuned['best_per_level']}")
+
     def make():
         h = A.Hierarchy(wl, stream=sp)
         h.set_adjoint(adj)
         h.set_timing(True)
+        AT.apply_amr(h, tuned)
         return h
 
     def solve(h):
@@ -214,6 +220,9 @@ def run_ours(args, rank, world):
     cluster_ms = 0.0
     rebuilds = 0
     phases = [0.0] * 6
+    lev_ms = [0.0] * wl.nlevels
+    lev_launch = [0] * wl.nlevels
+    lev_cells = [0] * wl.nlevels
     for h in hs:
         with torch.cuda.stream(s):
             flush.zero_()
@@ -233,6 +242,10 @@ def run_ours(args, rank, world):
         cluster_ms += st["cluster_host_ms"]
         rebuilds += st["level_rebuilds"]
         phases = [a + b for a, b in zip(phases, st["regrid_phase_ms"])]
+        for lev in range(wl.nlevels):
+            lev_ms[lev] += st["level_step_ms"][lev]
+            lev_launch[lev] += st["level_step_launches"][lev]
+            lev_cells[lev] += st["level_cell_updates"][lev]
         Js.append(J)
     torch.cuda.synchronize()
     if dist:
@@ -276,8 +289,32 @@ def run_ours(args, rank, world):
             e1.synchronize()
             res[name] = cells * nst / (e0.elapsed_time(e1) * 1e-3)
         b.close()
+        # autotuned: work-list order x tile x launch mode x ghost fusion, then
+        # the best configuration replayed from a CUDA graph
+        tb = AT.tune_batch(pb, key="config4-seed0", stream=s, use_cache=False)
+        best = tb["best"]
+        b = A.Batch(pb, stream=sp)
+        b.set_order(AT.batch_orders(pb)[best["order"]])
+        b.set_ghost_fusion(best["fuse_ghosts"])
+        tile = tuple(best["tile"])
+        b.step(2, mode=best["mode"], tile=tile, graph=True)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        nst = 20
+        e0.record(s)
+        b.step(nst, mode=best["mode"], tile=tile, graph=True)
+        e1.record(s)
+        e1.synchronize()
+        res["fused_tuned_graph"] = cells * nst / (e0.elapsed_time(e1) * 1e-3)
+        b.close()
+        tuned_batch = {k: best[k] for k in ("order", "tile", "mode", "fuse_ghosts")}
+        best_fused = max(v for k, v in res.items() if k != "per_patch")
         batched = {"patches": pb.npatch, "cells": cells, **{k: v for k, v in res.items()},
-                   "fused_over_per_patch": res["fused_worklist"] / res["per_patch"]}
+                   "tuned_config": tuned_batch,
+                   "fp64_roofline_frac_best": FLOPS_PER_CELL_2D * best_fused / peak_fma,
+                   "fused_over_per_patch": res["fused_worklist"] / res["per_patch"],
+                   "best_fused_over_per_patch": best_fused / res["per_patch"]}
 
     # end to end through the public API from pinned host buffers
     e2e = None
@@ -292,6 +329,7 @@ def run_ours(args, rank, world):
         cu_e = 0
         for _ in range(ne):
             h = A.Hierarchy(wl, stream=sp)
+            AT.apply_amr(h, tuned)
             h.load_adjoint(snaps_host.numpy())
             solve(h)
             cu_e += h.stats()["cell_updates"]
@@ -323,13 +361,21 @@ def run_ours(args, rank, world):
                                "snapshots (device-resident, solved once), tol 1e-3, time range [0, t_f]",
                    "step": "one full adjoint-flagged forward AMR solve to t_f plus J",
                    "l2": "flushed (256 MB write) between timed steps",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "step_kernel_per_level": tuned["best_per_level"]},
         "roofline": {"bound": "alu", "kernel": "k_step2d (fused wave-propagation step)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": None,
                      "peak_source": "project FP64 DFMA micro-benchmark (2 flops per instruction), measured live",
                      "flops_per_cell_update": FLOPS_PER_CELL_2D,
-                     "cells_per_launch": cells_per_launch, "avg_launch_us": avg_launch_s * 1e6},
+                     "cells_per_launch": cells_per_launch, "avg_launch_us": avg_launch_s * 1e6,
+                     "per_level": [{"level": lev, **tuned["best_per_level"][lev],
+                                    "launches_per_step": lev_launch[lev] / args.steps,
+                                    "cells_per_launch": lev_cells[lev] / max(lev_launch[lev], 1),
+                                    "avg_launch_us": lev_ms[lev] * 1e3 / max(lev_launch[lev], 1),
+                                    "tflops": (FLOPS_PER_CELL_2D * lev_cells[lev] / (lev_ms[lev] * 1e-3) / 1e12
+                                               if lev_ms[lev] > 0 else None)}
+                                   for lev in range(wl.nlevels)]},
         "fp64_peak": {"dfma_tflops": peak_fma / 1e12, "dadd_tflops": peak_add / 1e12},
         "batched": batched,
         "serving": serving,
@@ -343,6 +389,8 @@ def run_ours(args, rank, world):
                                   "regrid_phases": dict(zip(["flag_and_wait", "window_copy", "clustering",
                                                              "arena_alloc_upload", "builder_kernels", "release_old"],
                                                             [v / args.steps for v in phases]))},
+        "autotune_levels_ms": {f"{t['tile'][0]}x{t['tile'][1]}{'' if t['fuse_ghosts'] else '+fill'}":
+                               [round(x["ms"], 3) for x in t["levels"]] for t in tuned["candidates"]},
         "adjoint_solve_s": adj_s,
         "J": Js[0],
     }

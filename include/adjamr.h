@@ -141,6 +141,11 @@ typedef struct adjamr_stats {
      * [1] flag-window copy, [2] clustering, [3] arena allocation and descriptor upload,
      * [4] builder kernels (medium, init, ghost and average-down maps), [5] release of the old arena */
     double regrid_phase_ms[6];
+    /* per level: CUDA-event time of its step kernels (if timing enabled),
+     * their launches, and the cell updates they made */
+    double level_step_ms[ADJAMR_MAX_LEVELS];
+    long long level_step_launches[ADJAMR_MAX_LEVELS];
+    long long level_cell_updates[ADJAMR_MAX_LEVELS];
 } adjamr_stats;
 
 typedef struct adjamr_ctx adjamr_ctx;
@@ -181,7 +186,7 @@ adjamr_status adjamr_adjoint_read(adjamr_adjoint *adj, double *dst, size_t cap);
 /* Drop one reference; frees the device copy with the last one. */
 void adjamr_adjoint_release(adjamr_adjoint *adj);
 
-/* Rebuild levels base_level+1 .. nlevels-1 top-down (Sec. 3):
+/* Rebuild levels base_level+1 .. nlevels-1 top-down (Sec. 3, regridding):
  * adjoint flags on level l, buffered, properly nested, clustered by
  * Berger-Rigoutsos, split to max_patch, refined; new cells copied from old
  * patches of the same level or interpolated from level l (init != 0: sampled
@@ -228,6 +233,15 @@ adjamr_status adjamr_step_level_only(adjamr_ctx *ctx, int level);
 adjamr_status adjamr_get_stats(adjamr_ctx *ctx, adjamr_stats *out);
 /* Enable/disable CUDA-event timing of step kernels (adds events only). */
 adjamr_status adjamr_set_timing(adjamr_ctx *ctx, int enable);
+/* Step-kernel configuration of one level (level = -1: every level), used
+ * from the next step on: the tile shape, and whether the kernel computes the
+ * level's ghost ring (same-level copies and coarse space-time interpolation,
+ * Sec. 3) while staging its tiles (fuse_ghosts = 1, the default) or a
+ * separate ghost-fill kernel runs before it (0).  Every choice computes the
+ * same bits; it changes only speed (small levels fill the GPU better with
+ * small tiles).  2D tiles: 32x8, 16x8, 16x16, 32x16, 64x8, 8x8; 1D: 256 or
+ * 128 (tile_y ignored).  Errors: EINVAL for another shape or level. */
+adjamr_status adjamr_set_level_kernel(adjamr_ctx *ctx, int level, int tile_x, int tile_y, int fuse_ghosts);
 /* Level-0 step and number of level-0 steps to reach tf. */
 adjamr_status adjamr_time_info(adjamr_ctx *ctx, double *dt0, int *nsteps_to_tf);
 const char *adjamr_last_error(adjamr_ctx *ctx);
@@ -257,6 +271,10 @@ adjamr_status adjamr_batch_create(int npatch, const int *nx, const int *ny, cons
                                   adjamr_batch **out);
 /* Order of the tile work-list: patch order given here (a permutation). */
 adjamr_status adjamr_batch_set_order(adjamr_batch *b, const int *order);
+/* Ghost ring of the batch's patches computed inside the step kernel while
+ * it stages its tiles (1) or by a separate ghost-fill kernel launched before
+ * it (0, the default).  Same bits either way. */
+adjamr_status adjamr_batch_set_ghost_fusion(adjamr_batch *b, int fuse_ghosts);
 /* Advance all patches nsteps steps with the given launch mode and tile. */
 adjamr_status adjamr_batch_step(adjamr_batch *b, int nsteps, int launch_mode, int tile_x, int tile_y);
 /* Capture one step (ghost fill + fused step) in a CUDA graph and replay it

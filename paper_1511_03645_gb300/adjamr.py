@@ -83,7 +83,10 @@ class Stats(ctypes.Structure):
                 ("cfl_max_seen", ctypes.c_double), ("step_kernel_ms", ctypes.c_double),
                 ("step_kernel_launches", ctypes.c_longlong), ("regrid_host_ms", ctypes.c_double),
                 ("cluster_host_ms", ctypes.c_double), ("level_rebuilds", ctypes.c_longlong),
-                ("regrid_phase_ms", ctypes.c_double * 6)]
+                ("regrid_phase_ms", ctypes.c_double * 6),
+                ("level_step_ms", ctypes.c_double * MAXLEV),
+                ("level_step_launches", ctypes.c_longlong * MAXLEV),
+                ("level_cell_updates", ctypes.c_longlong * MAXLEV)]
 
 
 # every entry point declared in include/adjamr.h
@@ -92,8 +95,10 @@ SYMBOLS = [
     "adjamr_set_adjoint", "adjamr_adjoint_read", "adjamr_adjoint_release", "adjamr_regrid",
     "adjamr_advance_level", "adjamr_flag_cells", "adjamr_integrate_functional", "adjamr_get_patches",
     "adjamr_read_level", "adjamr_write_level", "adjamr_fill_ghosts", "adjamr_read_patch_ghosted",
-    "adjamr_step_level_only", "adjamr_get_stats", "adjamr_set_timing", "adjamr_time_info", "adjamr_last_error",
-    "adjamr_destroy", "adjamr_batch_create", "adjamr_batch_set_order", "adjamr_batch_step",
+    "adjamr_step_level_only", "adjamr_get_stats", "adjamr_set_timing", "adjamr_set_level_kernel", "adjamr_time_info",
+    "adjamr_last_error",
+    "adjamr_destroy", "adjamr_batch_create", "adjamr_batch_set_order", "adjamr_batch_set_ghost_fusion",
+    "adjamr_batch_step",
     "adjamr_batch_step_graph", "adjamr_batch_read", "adjamr_batch_cells", "adjamr_batch_destroy",
     "adjamr_fp64_peak", "adjamr_estimate_bytes", "adjamr_server_create", "adjamr_server_submit",
     "adjamr_server_poll", "adjamr_server_wait", "adjamr_server_info", "adjamr_server_now", "adjamr_server_destroy",
@@ -141,9 +146,11 @@ def load(build_if_missing: bool = True):
             "adjamr_step_level_only": [vp, i],
             "adjamr_get_stats": [vp, P(Stats)],
             "adjamr_set_timing": [vp, i],
+            "adjamr_set_level_kernel": [vp, i, i, i, i],
             "adjamr_time_info": [vp, dp, ip],
             "adjamr_batch_create": [i, ip, ip, dp, dp, dp, dp, dp, ip, P(Medium), i, dp, vp, P(vp)],
             "adjamr_batch_set_order": [vp, ip],
+            "adjamr_batch_set_ghost_fusion": [vp, i],
             "adjamr_batch_step": [vp, i, i, i, i],
             "adjamr_batch_step_graph": [vp, i, i, i, i],
             "adjamr_batch_read": [vp, dp, sz],
@@ -358,8 +365,15 @@ class Hierarchy:
         s = Stats()
         _check(load().adjamr_get_stats(self.h, ctypes.byref(s)), self.h, "get_stats")
         d = {k: getattr(s, k) for k, _ in Stats._fields_}
-        d["regrid_phase_ms"] = list(s.regrid_phase_ms)
+        for k in ("regrid_phase_ms", "level_step_ms", "level_step_launches", "level_cell_updates"):
+            d[k] = list(getattr(s, k))
         return d
+
+    def set_level_kernel(self, level: int, tile, fuse_ghosts: bool = True) -> None:
+        """Step-kernel tile (tx, ty) and ghost fusion of one level (-1: all
+        levels); results do not depend on either."""
+        _check(load().adjamr_set_level_kernel(self.h, level, int(tile[0]), int(tile[1]) if len(tile) > 1 else 1,
+                                              1 if fuse_ghosts else 0), self.h, "set_level_kernel")
 
     # ---- queries ----
     def patches(self, level: int) -> np.ndarray:
@@ -473,6 +487,9 @@ class Batch:
     def set_order(self, order):
         o = np.ascontiguousarray(order, dtype=np.int32)
         _check(load().adjamr_batch_set_order(self.h, _ip(o)), None, "batch_set_order")
+
+    def set_ghost_fusion(self, on: bool):
+        _check(load().adjamr_batch_set_ghost_fusion(self.h, 1 if on else 0), None, "batch_set_ghost_fusion")
 
     def step(self, nsteps=1, mode=LAUNCH_WORKLIST, tile=(32, 8), graph=False):
         f = load().adjamr_batch_step_graph if graph else load().adjamr_batch_step

@@ -70,8 +70,9 @@ def batch_orders(pb):
 
 
 def tune_batch(pb, key: str, stream=None, steps: int = 4, use_cache: bool = True) -> dict:
-    """Best (tile, order, launch mode, graph) for a batch; returns a dict with
-    the choice and the measured cell-updates/s of every candidate."""
+    """Best (work-list order, tile, launch mode, ghost fusion) for a batch;
+    returns a dict with the choice and the measured cell-updates/s of every
+    candidate."""
     import torch
     ck = f"{_gpu_key()}|batch|{key}"
     if use_cache:
@@ -86,10 +87,12 @@ def tune_batch(pb, key: str, stream=None, steps: int = 4, use_cache: bool = True
         b.set_order(order)
         for tile in TILES:
             for mode in (A.LAUNCH_WORKLIST, A.LAUNCH_PERSISTENT):
-                b.step(1, mode=mode, tile=tile)
-                ms = _time(s, lambda: b.step(steps, mode=mode, tile=tile)) / steps
-                results.append({"order": oname, "tile": list(tile), "mode": mode, "ms": ms,
-                                "cell_updates_per_s": cells / (ms * 1e-3)})
+                for fuse in (False, True):
+                    b.set_ghost_fusion(fuse)
+                    b.step(1, mode=mode, tile=tile)
+                    ms = _time(s, lambda: b.step(steps, mode=mode, tile=tile)) / steps
+                    results.append({"order": oname, "tile": list(tile), "mode": mode, "fuse_ghosts": fuse,
+                                    "ms": ms, "cell_updates_per_s": cells / (ms * 1e-3)})
     b.close()
     best = max(results, key=lambda r: r["cell_updates_per_s"])
     out = {"best": best, "candidates": results}
@@ -98,8 +101,15 @@ def tune_batch(pb, key: str, stream=None, steps: int = 4, use_cache: bool = True
 
 
 def tune_amr(wl, adj, key: str, stream=None, coarse_steps: int = 40, use_cache: bool = True) -> dict:
-    """Best tile shape for an AMR solve, timed on its first coarse steps
-    (regrids included)."""
+    """Best step-kernel configuration (tile shape, ghost ring fused into the
+    step or filled by its own kernel) of every level of an AMR solve.
+
+    Each candidate runs the solve's first coarse steps (regrids included) with
+    the same configuration on every level; the hierarchy evolves
+    bit-identically for every candidate, so the CUDA-event time of each
+    level's ghost fill + step kernels compares directly across candidates and
+    the best one is chosen per level (the coarse levels are too small to fill
+    the GPU with large tiles)."""
     import torch
     ck = f"{_gpu_key()}|amr|{key}"
     if use_cache:
@@ -109,15 +119,39 @@ def tune_amr(wl, adj, key: str, stream=None, coarse_steps: int = 40, use_cache: 
     s = torch.cuda.Stream() if stream is None else stream
     results = []
     for tile in TILES:
-        h = A.Hierarchy(wl, stream=s.cuda_stream, tile=tile)
-        h.set_adjoint(adj)
-        h.regrid(0, init=True)
-        h.advance(2)   # warm-up
-        torch.cuda.synchronize()
-        ms = _time(s, lambda: h.advance(coarse_steps))
-        results.append({"tile": list(tile), "ms": ms, "cell_updates": h.stats()["cell_updates"]})
-        h.close()
-    best = min(results, key=lambda r: r["ms"])
-    out = {"best": best, "candidates": results}
+        for fuse in (True, False):
+            h = A.Hierarchy(wl, stream=s.cuda_stream)
+            h.set_level_kernel(-1, tile, fuse)
+            h.set_adjoint(adj)
+            h.set_timing(True)
+            h.regrid(0, init=True)
+            h.advance(2)   # warm-up
+            torch.cuda.synchronize()
+            st0 = h.stats()
+            h.advance(coarse_steps)
+            torch.cuda.synchronize()
+            st1 = h.stats()
+            h.close()
+            per = []
+            for lev in range(wl.nlevels):
+                per.append({"launches": st1["level_step_launches"][lev] - st0["level_step_launches"][lev],
+                            "ms": st1["level_step_ms"][lev] - st0["level_step_ms"][lev],
+                            "cells": st1["level_cell_updates"][lev] - st0["level_cell_updates"][lev]})
+            results.append({"tile": list(tile), "fuse_ghosts": fuse, "levels": per})
+    best = []
+    for lev in range(wl.nlevels):
+        cand = [r for r in results if r["levels"][lev]["launches"] > 0]
+        if not cand:
+            best.append({"tile": list(TILES[0]), "fuse_ghosts": True})
+            continue
+        b = min(cand, key=lambda r: r["levels"][lev]["ms"])
+        best.append({"tile": b["tile"], "fuse_ghosts": b["fuse_ghosts"]})
+    out = {"best_per_level": best, "candidates": results, "coarse_steps": coarse_steps}
     _store(ck, out)
     return out
+
+
+def apply_amr(h, tuned: dict) -> None:
+    """Set the tuned per-level step-kernel configuration on a hierarchy."""
+    for lev, b in enumerate(tuned["best_per_level"]):
+        h.set_level_kernel(lev, b["tile"], b["fuse_ghosts"])

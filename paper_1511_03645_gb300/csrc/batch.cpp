@@ -37,6 +37,7 @@ struct adjamr_batch {
     PatchDesc *d_patches = nullptr;
     GhostDesc *d_ghost = nullptr;
     long long nghost = 0;
+    int fuse = 0;  // ghost ring computed inside the step kernel
     WorkItem *d_work = nullptr;
     int nwork = 0, wtx = 0, wty = 0;
     std::vector<WorkItem> h_work;
@@ -44,7 +45,7 @@ struct adjamr_batch {
     MediumDev *d_media = nullptr;
     unsigned long long *d_cfl = nullptr;
     int nsm = 0;
-    std::map<std::tuple<int, int, int, int>, cudaGraphExec_t> graphs;
+    std::map<std::tuple<int, int, int, int, int>, cudaGraphExec_t> graphs;
     std::string err;
 };
 
@@ -77,28 +78,36 @@ void drop_graphs(adjamr_batch *b)
     b->graphs.clear();
 }
 
-// one step: ghost fill, then the step kernel(s); swaps buffers
+// one step of every patch; swaps buffers.  The extrapolated ghost ring comes
+// from the ghost descriptors, either inside the step kernel while it stages
+// its tiles (b->fuse) or from the ghost-fill kernel launched first.
 cudaError_t one_step(adjamr_batch *b, int mode, int tx, int ty)
 {
     const double *q = b->q[b->cur];
     double *qn = b->q[1 - b->cur];
-    cudaError_t e = launch_ghost_fill(2, 3, b->d_ghost, b->nghost, b->q[b->cur], b->ncell, nullptr, nullptr, 0, 0, 1,
-                                      b->s);
-    if (e != cudaSuccess) return e;
+    GhostArgs ga{nullptr, nullptr, nullptr, 0, 0, 0.0};
+    cudaError_t e = cudaSuccess;
+    if (b->fuse) {
+        ga.gd = b->d_ghost;
+    } else {
+        e = launch_ghost_fill(2, 3, b->d_ghost, b->nghost, b->q[b->cur], b->ncell, nullptr, nullptr, 0, 0, 1, b->s);
+        if (e != cudaSuccess) return e;
+    }
     if (mode == ADJAMR_LAUNCH_PER_PATCH) {
         int w0 = 0;
         while (w0 < b->nwork) {
             int w1 = w0, k = b->h_work[w0].patch;
             while (w1 < b->nwork && b->h_work[w1].patch == k) w1++;
             e = launch_step(2, 0, tx, ty, q, qn, b->aux, b->ncell, b->d_patches, b->d_work + w0, w1 - w0, 0, b->d_cfl,
-                            b->s);
+                            b->s, ga);
             if (e != cudaSuccess) return e;
             w0 = w1;
         }
     } else {
         int grid = 0;
         if (mode == ADJAMR_LAUNCH_PERSISTENT) grid = std::min(b->nwork, b->nsm * std::max(1, step_occupancy(2, 0, tx, ty)));
-        e = launch_step(2, 0, tx, ty, q, qn, b->aux, b->ncell, b->d_patches, b->d_work, b->nwork, grid, b->d_cfl, b->s);
+        e = launch_step(2, 0, tx, ty, q, qn, b->aux, b->ncell, b->d_patches, b->d_work, b->nwork, grid, b->d_cfl, b->s,
+                        ga);
         if (e != cudaSuccess) return e;
     }
     b->cur = 1 - b->cur;
@@ -127,7 +136,7 @@ adjamr_status adjamr_batch_create(int npatch, const int *nx, const int *ny, cons
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
-        long long off = 0;
+        long long off = 0, gcount = 0;
         std::vector<PatchDesc> pd;
         for (int k = 0; k < npatch; k++) {
             if (nx[k] < 1 || ny[k] < 1 || medium_id[k] < 0 || medium_id[k] >= nmedia || !(x1[k] > x0[k]) ||
@@ -153,6 +162,8 @@ adjamr_status adjamr_batch_create(int npatch, const int *nx, const int *ny, cons
             PatchDesc d;
             d.ilo = 0; d.jlo = 0; d.nx = p.nx; d.ny = p.ny; d.sx = p.sx; d.sy = p.sy; d.base = p.base;
             d.dtdx = p.dt / p.dx; d.dtdy = p.dt / p.dy; d.hx = 0.5 * d.dtdx; d.hy = 0.5 * d.dtdy;
+            d.gbase = gcount;
+            gcount += (long long)p.sx * p.sy - (long long)p.nx * p.ny;
             pd.push_back(d);
             b->order.push_back(k);
         }
@@ -222,8 +233,6 @@ adjamr_status adjamr_batch_create(int npatch, const int *nx, const int *ny, cons
             g.dx = p.dx;
             g.dy = p.dy;
             for (int q = 0; q < 4; q++) g.bc[q] = ADJAMR_BC_EXTRAP;
-            g.dtdx = p.dt / p.dx;
-            g.dtdy = p.dt / p.dy;
             chk(launch_aux_fill(0, 2, dad, (long long)ad.size(), b->aux, b->med, off, b->d_media + p.mid, g, b->s));
             chk(cudaFreeAsync(dad, b->s));
             if (q0)
@@ -266,6 +275,13 @@ adjamr_status adjamr_batch_set_order(adjamr_batch *b, const int *order)
     return ADJAMR_OK;
 }
 
+adjamr_status adjamr_batch_set_ghost_fusion(adjamr_batch *b, int fuse_ghosts)
+{
+    if (!b) return ADJAMR_EINVAL;
+    b->fuse = fuse_ghosts != 0;
+    return ADJAMR_OK;
+}
+
 adjamr_status adjamr_batch_step(adjamr_batch *b, int nsteps, int mode, int tx, int ty)
 {
     if (!b || nsteps < 0) return ADJAMR_EINVAL;
@@ -287,7 +303,7 @@ adjamr_status adjamr_batch_step_graph(adjamr_batch *b, int nsteps, int mode, int
     if (build_work(b, tx, ty) != cudaSuccess) return ADJAMR_ECUDA;
     if (step_occupancy(2, 0, tx, ty) <= 0) return ADJAMR_EINVAL;
     if (b->s == nullptr) return ADJAMR_ESTATE;  // capture needs a non-default stream
-    auto key = std::make_tuple(mode, tx, ty, b->cur);
+    auto key = std::make_tuple(mode, tx, ty, b->cur, b->fuse);
     cudaGraphExec_t exec = nullptr;
     auto it = b->graphs.find(key);
     if (it == b->graphs.end()) {

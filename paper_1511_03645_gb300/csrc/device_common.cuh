@@ -1,0 +1,81 @@
+// Device helpers shared by the AMR kernels and the fused step kernel:
+// boundary signs and the coarse-to-fine space-time interpolation of a ghost
+// (or new) cell (Sec. 3: linear in time between the coarser level's old and
+// new states, minmod-limited linear in space), in the canonical order.
+#pragma once
+#include "internal.h"
+
+namespace adjamr {
+namespace {
+
+__device__ __forceinline__ double minmod(double a, double b)
+{
+    if (a > 0.0 && b > 0.0) return fmin(a, b);
+    if (a < 0.0 && b < 0.0) return fmax(a, b);
+    return 0.0;
+}
+
+__device__ __forceinline__ double sgn(double v, int signs, int comp, int ref)
+{
+    // comp 0 is never flipped; comps 1, 2 by bits (2*ref + comp - 1)
+    if (comp == 0) return v;
+    return ((signs >> (2 * ref + comp - 1)) & 1) ? -v : v;
+}
+
+// value of field f at coarse reference `ref` (cell index c), at time th = k/r
+// of the coarse step (k = 0: the old state alone)
+__device__ __forceinline__ double coarse_val(const double *__restrict__ qo, const double *__restrict__ qn_,
+                                             long long sc, long long c, int f, int k, double th, int signs, int ref)
+{
+    double v0 = qo[(long long)f * sc + c];
+    double v;
+    if (k == 0) {
+        v = v0;
+    } else {
+        double v1 = qn_[(long long)f * sc + c];
+        v = (1.0 - th) * v0 + th * v1;
+    }
+    return sgn(v, signs, f, ref + 1);
+}
+
+__device__ __forceinline__ double interp_field(const GhostDesc &g, const double *__restrict__ qo,
+                                               const double *__restrict__ qn_, long long sc, int f, int k, double th,
+                                               int dim)
+{
+    double q0 = coarse_val(qo, qn_, sc, g.src, f, k, th, g.signs, 0);
+    double qxm = coarse_val(qo, qn_, sc, g.cxm, f, k, th, g.signs, 1);
+    double qxp = coarse_val(qo, qn_, sc, g.cxp, f, k, th, g.signs, 2);
+    double sx = minmod(qxp - q0, q0 - qxm);
+    double v = q0 + sx * g.fx;
+    if (dim == 2) {
+        double qym = coarse_val(qo, qn_, sc, g.cym, f, k, th, g.signs, 3);
+        double qyp = coarse_val(qo, qn_, sc, g.cyp, f, k, th, g.signs, 4);
+        double sy = minmod(qyp - q0, q0 - qym);
+        v = v + sy * g.fy;
+    }
+    return v;
+}
+
+// value of field f of the ghost cell described by g (copy or interpolation),
+// with the boundary sign of the result
+__device__ __forceinline__ double ghost_value(const GhostDesc &g, const double *__restrict__ qf, long long sf,
+                                              const double *__restrict__ qo, const double *__restrict__ qn_,
+                                              long long sc, int f, int k, double th, int dim)
+{
+    double v;
+    if (g.kind == 0) v = qf[(long long)f * sf + g.src];
+    else v = interp_field(g, qo, qn_, sc, f, k, th, dim);
+    return sgn(v, g.signs, f, 0);
+}
+
+// index, within its patch, of the ghost cell at storage (si, sj): bottom rows,
+// then the 4 side cells of each interior row, then top rows
+__device__ __forceinline__ long long ghost_local_index(const PatchDesc &P, int si, int sj, int gy)
+{
+    if (sj < gy) return (long long)sj * P.sx + si;
+    if (sj < gy + P.ny) return (long long)gy * P.sx + (long long)(sj - gy) * 4 + (si < 2 ? si : si - P.nx);
+    return (long long)gy * P.sx + (long long)P.ny * 4 + (long long)(sj - gy - P.ny) * P.sx + si;
+}
+
+}  // namespace
+}  // namespace adjamr

@@ -92,12 +92,15 @@ struct adjamr_ctx {
     double *d_fscratch = nullptr, *d_fout = nullptr;
     size_t fscratch_n = 0;
     adjamr_stats st = {};
-    int tx = 32, ty = 8, launch_mode = 0, grid_persistent = 0;
+    int tx = 32, ty = 8, launch_mode = 0, grid_persistent = 0, nsm = 0;
+    int ltx[ADJAMR_MAX_LEVELS] = {}, lty[ADJAMR_MAX_LEVELS] = {}, lgrid[ADJAMR_MAX_LEVELS] = {};
+    int lfuse[ADJAMR_MAX_LEVELS] = {};  // ghost ring computed inside the step kernel
     bool timing = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // step-kernel timing without host synchronisation: event pairs recorded
     // around every step launch, read when the stream is synchronised
     std::vector<cudaEvent_t> tev;
+    std::vector<int> tev_level;
     size_t tev_used = 0;
 };
 
@@ -311,6 +314,7 @@ adjamr_status alloc_level(adjamr_ctx *c, int l, const std::vector<Box> &boxes)
         PatchDesc d;
         d.ilo = p.ilo; d.jlo = p.jlo; d.nx = p.nx; d.ny = p.ny; d.sx = p.sx; d.sy = p.sy; d.base = p.base;
         d.dtdx = dtdx; d.dtdy = dtdy; d.hx = 0.5 * dtdx; d.hy = 0.5 * dtdy;
+        d.gbase = L.nghost_cells;
         pd.push_back(d);
         L.ninterior += (long long)p.nx * p.ny;
         L.nstore += (long long)p.sx * p.sy;
@@ -348,7 +352,7 @@ adjamr_status alloc_level(adjamr_ctx *c, int l, const std::vector<Box> &boxes)
     }
     build_buckets(L);
     L.work_tx = L.work_ty = 0;
-    return build_work(c, l, c->tx, c->ty);
+    return build_work(c, l, c->ltx[l], c->lty[l]);
 }
 
 LevelGeom geom_of(const adjamr_ctx *c, int l)
@@ -362,8 +366,6 @@ LevelGeom geom_of(const adjamr_ctx *c, int l)
     g.dx = c->L[l].dx;
     g.dy = c->L[l].dy;
     for (int k = 0; k < 4; k++) g.bc[k] = c->P.bc[k];
-    g.dtdx = c->L[l].dt / c->L[l].dx;
-    g.dtdy = (c->P.dim == 2) ? c->L[l].dt / c->L[l].dy : 0.0;
     return g;
 }
 
@@ -581,7 +583,7 @@ void dilate(std::vector<unsigned char> &f, int N, int M, int w, int wy, std::vec
 adjamr_status flag_dense(adjamr_ctx *c, int l, double tol, unsigned char *d_dense, unsigned char *d_patchflags,
                          long long *nflag_out, int *bbox_out = nullptr);
 
-// Rebuild levels base+1 .. nlevels-1 top-down (Sec. 3).
+// Rebuild levels base+1 .. nlevels-1 top-down (Sec. 3, regridding).
 void harvest_timing(adjamr_ctx *c);
 
 adjamr_status regrid_body(adjamr_ctx *c, int base, int init);
@@ -850,23 +852,50 @@ adjamr_status ghost_fill(adjamr_ctx *c, int l, int k)
     return ADJAMR_OK;
 }
 
-adjamr_status step_patches(adjamr_ctx *c, int l)
+// Ghost arguments of a step that computes the level's ghost ring while it
+// stages its tiles (same descriptors and arithmetic as ghost_fill); k is the
+// fine substep within the coarser level's step.
+GhostArgs fused_ghosts(adjamr_ctx *c, int l, int k)
+{
+    Level &L = c->L[l];
+    GhostArgs ga{L.d_ghost, nullptr, nullptr, 0, k, 0.0};
+    if (l > 0) {
+        Level &C = c->L[l - 1];
+        ga.qco = C.q[C.cur];
+        ga.qcn = C.q[1 - C.cur];
+        ga.sc = C.ncell;
+        ga.th = (double)k / (double)c->P.ratio[l - 1];  // same division as the oracle's
+    }
+    return ga;
+}
+
+enum GhostMode { GHOST_READY = 0, GHOST_FUSED = 1, GHOST_FILL = 2 };
+
+// One step of every patch of level l at fine substep k: q[cur] -> q[1-cur].
+// GHOST_FUSED: the step kernel computes the ghost ring while staging;
+// GHOST_FILL: the ghost-fill kernel runs first; GHOST_READY: the ring of
+// q[cur] was filled beforehand.  Both ways give the same bits.
+adjamr_status step_patches(adjamr_ctx *c, int l, int k, GhostMode gm)
 {
     Level &L = c->L[l];
     if (L.patches.empty()) return ADJAMR_OK;
-    TRY(build_work(c, l, c->tx, c->ty));
+    const GhostArgs ga = (gm == GHOST_FUSED) ? fused_ghosts(c, l, k) : GhostArgs{nullptr, nullptr, nullptr, 0, 0, 0.0};
+    TRY(build_work(c, l, c->ltx[l], c->lty[l]));
     cudaEvent_t tb = nullptr, te = nullptr;
     if (c->timing) {
         while (c->tev.size() < c->tev_used + 2) {
             cudaEvent_t e;
             CKR(c, cudaEventCreate(&e));
             c->tev.push_back(e);
+            c->tev_level.push_back(0);
         }
         tb = c->tev[c->tev_used];
         te = c->tev[c->tev_used + 1];
+        c->tev_level[c->tev_used] = l;
         c->tev_used += 2;
         CKR(c, cudaEventRecord(tb, c->s));
     }
+    if (gm == GHOST_FILL) TRY(ghost_fill(c, l, k));
     const double *q = L.q[L.cur];
     double *qn = L.q[1 - L.cur];
     if (c->launch_mode == ADJAMR_LAUNCH_PER_PATCH) {
@@ -874,22 +903,25 @@ adjamr_status step_patches(adjamr_ctx *c, int l)
         for (int k = 0; k < (int)L.patches.size(); k++) {
             int w1 = w0;
             while (w1 < L.nwork && L.h_work[w1].patch == k) w1++;
-            CKR(c, launch_step(c->P.dim, c->P.eqn, c->tx, c->ty, q, qn, L.aux, L.ncell, L.d_patches, L.d_work + w0,
-                               w1 - w0, 0, c->d_cfl, c->s));
+            CKR(c, launch_step(c->P.dim, c->P.eqn, c->ltx[l], c->lty[l], q, qn, L.aux, L.ncell, L.d_patches,
+                               L.d_work + w0, w1 - w0, 0, c->d_cfl, c->s, ga));
             c->st.kernel_launches++;
             c->st.step_kernel_launches++;
+            c->st.level_step_launches[l]++;
             w0 = w1;
         }
     } else {
         int grid = 0;
-        if (c->launch_mode == ADJAMR_LAUNCH_PERSISTENT) grid = std::min(L.nwork, c->grid_persistent);
-        CKR(c, launch_step(c->P.dim, c->P.eqn, c->tx, c->ty, q, qn, L.aux, L.ncell, L.d_patches, L.d_work, L.nwork,
-                           grid, c->d_cfl, c->s));
+        if (c->launch_mode == ADJAMR_LAUNCH_PERSISTENT) grid = std::min(L.nwork, c->lgrid[l]);
+        CKR(c, launch_step(c->P.dim, c->P.eqn, c->ltx[l], c->lty[l], q, qn, L.aux, L.ncell, L.d_patches, L.d_work,
+                           L.nwork, grid, c->d_cfl, c->s, ga));
         c->st.kernel_launches++;
         c->st.step_kernel_launches++;
+        c->st.level_step_launches[l]++;
     }
     if (c->timing) CKR(c, cudaEventRecord(te, c->s));
     c->st.cell_updates += L.ninterior;
+    c->st.level_cell_updates[l] += L.ninterior;
     return ADJAMR_OK;
 }
 
@@ -922,12 +954,15 @@ void harvest_timing(adjamr_ctx *c)
 {
     for (size_t k = 0; k + 1 < c->tev_used; k += 2) {
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, c->tev[k], c->tev[k + 1]) == cudaSuccess) c->st.step_kernel_ms += ms;
+        if (cudaEventElapsedTime(&ms, c->tev[k], c->tev[k + 1]) == cudaSuccess) {
+            c->st.step_kernel_ms += ms;
+            c->st.level_step_ms[c->tev_level[k]] += ms;
+        }
     }
     c->tev_used = 0;
 }
 
-// Berger-Oliger recursion (Sec. 3)
+// Berger-Oliger recursion (Sec. 3, time stepping with subcycling)
 adjamr_status step_level(adjamr_ctx *c, int l)
 {
     Level &L = c->L[l];
@@ -937,8 +972,7 @@ adjamr_status step_level(adjamr_ctx *c, int l)
         TRY(regrid_from(c, l, 0));
     int sub = 0;
     if (l > 0) sub = (int)(L.nstep - c->L[l - 1].nstep * P.ratio[l - 1]);
-    TRY(ghost_fill(c, l, sub));
-    TRY(step_patches(c, l));
+    TRY(step_patches(c, l, sub, c->lfuse[l] ? GHOST_FUSED : GHOST_FILL));
     if (l < P.nlevels - 1 && !c->L[l + 1].patches.empty()) {
         int r = P.ratio[l];
         c->L[l + 1].nstep = L.nstep * r;
@@ -1057,6 +1091,13 @@ adjamr_status create_impl(const adjamr_params *p, adjamr_ctx **out)
         return ADJAMR_EINVAL;  // unsupported tile shape
     }
     c->grid_persistent = nsm * std::max(occ, 1);
+    c->nsm = nsm;
+    for (int l = 0; l < ADJAMR_MAX_LEVELS; l++) {
+        c->ltx[l] = c->tx;
+        c->lty[l] = c->ty;
+        c->lgrid[l] = c->grid_persistent;
+        c->lfuse[l] = 1;
+    }
     int N = p->n0[0], M = (p->dim == 2) ? p->n0[1] : 1;
     for (int l = 0; l < p->nlevels; l++) {
         Level &L = c->L[l];
@@ -1364,8 +1405,7 @@ adjamr_status adjamr_solve_adjoint(adjamr_ctx *ctx, const adjamr_params *ap, con
         for (int sidx = 0; sidx < nsnap && e == cudaSuccess; sidx++) {
             if (sidx > 0)
                 for (int k = 0; k < nsub && st == ADJAMR_OK; k++) {
-                    st = ghost_fill(a, 0, 0);
-                    if (st == ADJAMR_OK) st = step_patches(a, 0);
+                    st = step_patches(a, 0, 0, a->lfuse[0] ? GHOST_FUSED : GHOST_FILL);
                     L.cur = 1 - L.cur;
                     L.nstep++;
                 }
@@ -1607,10 +1647,32 @@ adjamr_status adjamr_step_level_only(adjamr_ctx *ctx, int level)
     if (!ctx || level < 0 || level >= ctx->P.nlevels) return ADJAMR_EINVAL;
     if (!ctx->have_medium) return ADJAMR_ESTATE;
     Level &L = ctx->L[level];
-    TRY(step_patches(ctx, level));
+    TRY(step_patches(ctx, level, 0, GHOST_READY));
     L.cur = 1 - L.cur;
     L.nstep++;
     CKR(ctx, cudaStreamSynchronize(ctx->s));
+    return ADJAMR_OK;
+}
+
+adjamr_status adjamr_set_level_kernel(adjamr_ctx *ctx, int level, int tile_x, int tile_y, int fuse_ghosts)
+{
+    if (!ctx || level < -1 || level >= ctx->P.nlevels) return ADJAMR_EINVAL;
+    int ty = (ctx->P.dim == 2) ? tile_y : 1;
+    int occ = 0;
+    if (ctx->P.dim == 2) {
+        occ = step_occupancy(2, ctx->P.eqn, tile_x, ty);
+        if (occ <= 0) return ADJAMR_EINVAL;
+    } else {
+        if (tile_x != 256 && tile_x != 128) return ADJAMR_EINVAL;
+        occ = step_occupancy(1, ctx->P.eqn, tile_x, 1);
+    }
+    for (int l = 0; l < ctx->P.nlevels; l++) {
+        if (level >= 0 && l != level) continue;
+        ctx->ltx[l] = tile_x;
+        ctx->lty[l] = ty;
+        ctx->lgrid[l] = ctx->nsm * std::max(occ, 1);
+        ctx->lfuse[l] = fuse_ghosts != 0;
+    }
     return ADJAMR_OK;
 }
 

@@ -35,12 +35,7 @@ constexpr double kGrav = 9.81;
 //  ACOUSTICS_ADJOINT:  c, Z, izs_x, izs_y, 1/rho, K
 //  SW:                 ce_x, 1/ce_x, g*he_x, ce_y, 1/ce_y, g*he_y
 //  SW_ADJOINT:         ce_x, 1/ce_x, ce_y, 1/ce_y, g*hbar
-// followed (at index kCfBase(eqn)) by the level's correction coefficients of
-// the two waves and the Courant number of each edge: cf1_x, cf2_x, cfl_x,
-// cf1_y, cf2_y, cfl_y (they depend on dt/dx of the level; the same operations
-// the step would perform per edge, done once when the patch is created).
-__host__ __device__ constexpr int kCfBase(int eqn) { return eqn == 0 ? 4 : (eqn == 3 ? 5 : 6); }
-__host__ __device__ constexpr int naux_of(int eqn) { return kCfBase(eqn) + 6; }
+__host__ __device__ constexpr int naux_of(int eqn) { return eqn == 0 ? 4 : (eqn == 3 ? 5 : 6); }
 __host__ __device__ constexpr int nmed_of(int eqn) { return (eqn == 2 || eqn == 3) ? 1 : 2; }
 
 // A patch in a level arena.  Storage cell (si, sj) (si in [0, sx), sj in
@@ -51,6 +46,7 @@ struct PatchDesc {
     int sx, sy;
     long long base;
     double dtdx, dtdy, hx, hy;
+    long long gbase;  // index of the patch's first ghost descriptor
 };
 
 // One tile of the step work-list.
@@ -70,7 +66,7 @@ struct GhostDesc {
     long long dst;
     long long src, cxm, cxp, cym, cyp;
     int kind, signs;
-    int mx, my;
+    double fx, fy;  // offsets (2m+1-r)/(2r) of the fine cell within its coarse cell
 };
 
 // Average-down of one coarse cell: dst in the coarse arena, src = fine child
@@ -99,21 +95,28 @@ struct LevelGeom {
     int dim, N, M;
     double lo0, lo1, dx, dy;
     int bc[4];
-    double dtdx, dtdy;   // of the level (correction coefficients, Courant numbers)
+};
+
+// Ghost cells computed inside the step kernel while staging a tile: the
+// ghost descriptors of the level and the coarser level's two time levels.
+// gd == nullptr: the ghost ring is read from q (filled beforehand).
+struct GhostArgs {
+    const GhostDesc *gd;
+    const double *qco, *qcn;
+    long long sc;
+    int k;      // fine substep within the coarse step (0: coarse old state only)
+    double th;  // k / r, divided on the host
 };
 
 // ---- kernel launchers (kernels_step.cu / kernels_amr.cu) ----
 cudaError_t launch_step(int dim, int eqn, int tx, int ty, const double *q, double *qn, const double *aux,
                         long long stride, const PatchDesc *patches, const WorkItem *work, int nwork, int grid,
-                        unsigned long long *cfl_bits, cudaStream_t s);
+                        unsigned long long *cfl_bits, cudaStream_t s, GhostArgs ga = GhostArgs{nullptr, nullptr, nullptr, 0, 0, 0.0});
 int step_occupancy(int dim, int eqn, int tx, int ty);
 
 cudaError_t launch_ghost_fill(int dim, int m, const GhostDesc *g, long long n, double *qf, long long sf,
                               const double *qc_old, const double *qc_new, long long sc, int k, int r,
                               cudaStream_t s);
-cudaError_t launch_regrid_init(int dim, int m, const GhostDesc *g, long long n, double *qf, long long sf,
-                               const double *qold, long long so, const double *qc, long long sc, int r,
-                               cudaStream_t s);
 cudaError_t launch_average_down(int dim, int m, const AvgDesc *a, long long n, const double *qf, long long sf,
                                 double *qc, long long sc, int r, cudaStream_t s);
 // Fill primary medium (med) and derived coefficients (aux) of the listed

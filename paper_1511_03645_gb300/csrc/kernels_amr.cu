@@ -14,90 +14,21 @@
 #include <cuda_runtime.h>
 
 #include "internal.h"
+#include "device_common.cuh"
 
 namespace adjamr {
 namespace {
 
 constexpr int kT = 256;
 
-__device__ __forceinline__ double minmod(double a, double b)
-{
-    if (a > 0.0 && b > 0.0) return fmin(a, b);
-    if (a < 0.0 && b < 0.0) return fmax(a, b);
-    return 0.0;
-}
-
-__device__ __forceinline__ double sgn(double v, int signs, int comp, int ref)
-{
-    // comp 0 is never flipped; comps 1, 2 by bits (2*ref + comp - 1)
-    if (comp == 0) return v;
-    return ((signs >> (2 * ref + comp - 1)) & 1) ? -v : v;
-}
-
-// value of field f at coarse reference `ref` (cell index c), at time k/r
-__device__ __forceinline__ double coarse_val(const double *__restrict__ qo, const double *__restrict__ qn_,
-                                             long long sc, long long c, int f, int k, int r, int signs, int ref)
-{
-    double v0 = qo[(long long)f * sc + c];
-    double v;
-    if (k == 0) {
-        v = v0;
-    } else {
-        double th = (double)k / (double)r;
-        double v1 = qn_[(long long)f * sc + c];
-        v = (1.0 - th) * v0 + th * v1;
-    }
-    return sgn(v, signs, f, ref + 1);
-}
-
-__device__ __forceinline__ double interp_field(const GhostDesc &g, const double *__restrict__ qo,
-                                               const double *__restrict__ qn_, long long sc, int f, int k, int r,
-                                               int dim)
-{
-    double fx = (double)(2 * g.mx + 1 - r) / (double)(2 * r);
-    double q0 = coarse_val(qo, qn_, sc, g.src, f, k, r, g.signs, 0);
-    double qxm = coarse_val(qo, qn_, sc, g.cxm, f, k, r, g.signs, 1);
-    double qxp = coarse_val(qo, qn_, sc, g.cxp, f, k, r, g.signs, 2);
-    double sx = minmod(qxp - q0, q0 - qxm);
-    double v = q0 + sx * fx;
-    if (dim == 2) {
-        double fy = (double)(2 * g.my + 1 - r) / (double)(2 * r);
-        double qym = coarse_val(qo, qn_, sc, g.cym, f, k, r, g.signs, 3);
-        double qyp = coarse_val(qo, qn_, sc, g.cyp, f, k, r, g.signs, 4);
-        double sy = minmod(qyp - q0, q0 - qym);
-        v = v + sy * fy;
-    }
-    return v;
-}
-
 __global__ void k_ghost_fill(int dim, int m, const GhostDesc *__restrict__ gd, long long n, double *qf, long long sf,
                              const double *__restrict__ qo, const double *__restrict__ qn_, long long sc, int k,
-                             int r)
+                             double th)
 {
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
     GhostDesc g = gd[t];
-    for (int f = 0; f < m; f++) {
-        double v;
-        if (g.kind == 0) v = qf[(long long)f * sf + g.src];
-        else v = interp_field(g, qo, qn_, sc, f, k, r, dim);
-        qf[(long long)f * sf + g.dst] = sgn(v, g.signs, f, 0);
-    }
-}
-
-__global__ void k_regrid_init(int dim, int m, const GhostDesc *__restrict__ gd, long long n, double *qf, long long sf,
-                              const double *__restrict__ qold, long long so, const double *__restrict__ qc,
-                              long long sc, int r)
-{
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    GhostDesc g = gd[t];
-    for (int f = 0; f < m; f++) {
-        double v;
-        if (g.kind == 2) v = qold[(long long)f * so + g.src];
-        else v = interp_field(g, qc, qc, sc, f, 0, r, dim);
-        qf[(long long)f * sf + g.dst] = v;
-    }
+    for (int f = 0; f < m; f++) qf[(long long)f * sf + g.dst] = ghost_value(g, qf, sf, qo, qn_, sc, f, k, th, dim);
 }
 
 __global__ void k_average_down(int dim, int m, const AvgDesc *__restrict__ ad, long long n,
@@ -152,16 +83,6 @@ __device__ void medium_at(const MediumDev &md, const LevelGeom &g, int I, int J,
     }
 }
 
-// correction coefficient of a wave of speed s (canonical operations):
-// |s| (1 - dtdx |s|) for the wave form, sign(s) (1 - dtdx |s|) for f-waves
-__device__ __forceinline__ double cf_of(int eqn, double s, double dtd)
-{
-    double a = fabs(s);
-    if (eqn == 0) return a * fma(-dtd, a, 1.0);
-    double t = fma(-dtd, a, 1.0);
-    return (s < 0.0) ? -t : t;
-}
-
 __device__ void aux_cell(int eqn, int dim, const MediumDev &md, const LevelGeom &g, int I, int J, long long idx,
                          double *aux, double *med, long long stride)
 {
@@ -190,16 +111,6 @@ __device__ void aux_cell(int eqn, int dim, const MediumDev &md, const LevelGeom 
             aux[4 * stride + idx] = 1.0 / c0[0];
             aux[5 * stride + idx] = c0[1];
         }
-        // wave speeds of the x-edge (-c_{i-1}, c_i) and the y-edge (-c_{j-1}, c_j)
-        double ccb = (dim == 2) ? sqrt(cb[1] / cb[0]) : ccl;
-        double s1x = -ccl, s2x = c, s1y = -ccb, s2y = c;
-        int o = kCfBase(eqn);
-        aux[(o + 0) * stride + idx] = cf_of(eqn, s1x, g.dtdx);
-        aux[(o + 1) * stride + idx] = cf_of(eqn, s2x, g.dtdx);
-        aux[(o + 2) * stride + idx] = g.dtdx * fmax(fabs(s1x), fabs(s2x));
-        aux[(o + 3) * stride + idx] = (dim == 2) ? cf_of(eqn, s1y, g.dtdy) : 0.0;
-        aux[(o + 4) * stride + idx] = (dim == 2) ? cf_of(eqn, s2y, g.dtdy) : 0.0;
-        aux[(o + 5) * stride + idx] = (dim == 2) ? g.dtdy * fmax(fabs(s1y), fabs(s2y)) : 0.0;
     } else {
         double hx = 0.5 * (cl[0] + c0[0]);
         double ghx = kGrav * hx;
@@ -207,13 +118,6 @@ __device__ void aux_cell(int eqn, int dim, const MediumDev &md, const LevelGeom 
         double hy = (dim == 2) ? 0.5 * (cb[0] + c0[0]) : hx;
         double ghy = kGrav * hy;
         double cey = sqrt(ghy);
-        int o = kCfBase(eqn);
-        aux[(o + 0) * stride + idx] = cf_of(eqn, -cex, g.dtdx);
-        aux[(o + 1) * stride + idx] = cf_of(eqn, cex, g.dtdx);
-        aux[(o + 2) * stride + idx] = g.dtdx * fmax(fabs(-cex), fabs(cex));
-        aux[(o + 3) * stride + idx] = (dim == 2) ? cf_of(eqn, -cey, g.dtdy) : 0.0;
-        aux[(o + 4) * stride + idx] = (dim == 2) ? cf_of(eqn, cey, g.dtdy) : 0.0;
-        aux[(o + 5) * stride + idx] = (dim == 2) ? g.dtdy * fmax(fabs(-cey), fabs(cey)) : 0.0;
         if (eqn == 2) {
             aux[idx] = cex;
             aux[stride + idx] = 1.0 / cex;
@@ -293,8 +197,8 @@ __device__ bool coarse_desc_dev(int I, int J, int r, const int *__restrict__ own
 {
     int ic = I / r, jc = (gc.dim == 2) ? J / r : 0;
     g.kind = 1;
-    g.mx = I - ic * r;
-    g.my = (gc.dim == 2) ? J - jc * r : 0;
+    g.fx = (double)(2 * (I - ic * r) + 1 - r) / (double)(2 * r);
+    g.fy = (gc.dim == 2) ? (double)(2 * (J - jc * r) + 1 - r) / (double)(2 * r) : 0.0;
     const int di[5] = {0, -1, 1, 0, 0}, dj[5] = {0, 0, 0, -1, 1};
     long long ref[5] = {0, 0, 0, 0, 0};
     int nref = (gc.dim == 2) ? 5 : 3;
@@ -362,7 +266,7 @@ __global__ void k_ghost_build(const PatchDesc *__restrict__ pd, const long long 
     d.src = d.cxm = d.cxp = d.cym = d.cyp = 0;
     d.kind = 0;
     d.signs = 0;
-    d.mx = d.my = 0;
+    d.fx = d.fy = 0.0;
     int o = owner_at(owner, g, I, J);
     if (o >= 0) {
         d.src = o;
@@ -425,7 +329,7 @@ __global__ void k_init_new(const PatchDesc *__restrict__ pd, const long long *__
     GhostDesc d;
     d.signs = 0;
     if (!coarse_desc_dev(I, J, r, owner_c, gc, d)) atomicOr(err, 8);
-    for (int f = 0; f < m; f++) qf[(long long)f * sf + dst] = interp_field(d, qc, qc, sc, f, 0, r, g.dim);
+    for (int f = 0; f < m; f++) qf[(long long)f * sf + dst] = interp_field(d, qc, qc, sc, f, 0, 0.0, g.dim);
 }
 
 __global__ void k_aux_patches(int eqn, const PatchDesc *__restrict__ pd, const long long *__restrict__ sprefix,
@@ -664,16 +568,8 @@ cudaError_t launch_ghost_fill(int dim, int m, const GhostDesc *g, long long n, d
                               const double *qc_old, const double *qc_new, long long sc, int k, int r, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    k_ghost_fill<<<nblk(n), kT, 0, s>>>(dim, m, g, n, qf, sf, qc_old, qc_new, sc, k, r);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_regrid_init(int dim, int m, const GhostDesc *g, long long n, double *qf, long long sf,
-                               const double *qold, long long so, const double *qc, long long sc, int r,
-                               cudaStream_t s)
-{
-    if (n <= 0) return cudaSuccess;
-    k_regrid_init<<<nblk(n), kT, 0, s>>>(dim, m, g, n, qf, sf, qold, so, qc, sc, r);
+    const double th = (double)k / (double)r;  // same division as the oracle's, on the host
+    k_ghost_fill<<<nblk(n), kT, 0, s>>>(dim, m, g, n, qf, sf, qc_old, qc_new, sc, k, th);
     return cudaGetLastError();
 }
 

@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include "internal.h"
+#include "device_common.cuh"
 
 namespace adjamr {
 namespace {
@@ -171,8 +172,36 @@ __device__ __forceinline__ double mc_phi(double w0, double w1, double u0, double
     return fmax(0.0, fmin(fmin(fma(0.5, th, 0.5), 2.0), 2.0 * th));
 }
 
-// s > 0.0 decided on the integer pipe (identical for every non-NaN double)
+// s > 0.0 and s < 0.0 decided on the integer pipe (identical to the FP64
+// comparisons for every non-NaN double, signed zeros included)
 __device__ __forceinline__ bool positive(double s) { return __double_as_longlong(s) > 0; }
+__device__ __forceinline__ bool negative(double s)
+{
+    long long b = __double_as_longlong(s);
+    return b < 0 && b != (long long)0x8000000000000000ull;
+}
+
+// correction coefficient of a wave of speed s: |s| fma(-dtd, |s|, 1) for the
+// wave form, sign(s) fma(-dtd, |s|, 1) for the f-wave forms
+template <int EQN>
+__device__ __forceinline__ double corr_coef(double s, double dtd)
+{
+    double a = fabs(s);
+    if constexpr (EQN == 0) {
+        return a * fma(-dtd, a, 1.0);
+    } else {
+        double t = fma(-dtd, a, 1.0);
+        return negative(s) ? -t : t;
+    }
+}
+
+// fmax(|a|, |b|) by comparing bit patterns on the integer pipe (non-NaN)
+__device__ __forceinline__ double maxabs(double a, double b)
+{
+    long long x = __double_as_longlong(a) & 0x7fffffffffffffffll;
+    long long y = __double_as_longlong(b) & 0x7fffffffffffffffll;
+    return __longlong_as_double(x > y ? x : y);
+}
 
 // max of non-negative doubles through their bit patterns (integer pipe)
 __device__ __forceinline__ long long bmax(long long a, double v)
@@ -212,7 +241,7 @@ __global__ void __launch_bounds__(kThreads) k_step2d(const double *__restrict__ 
                                                      const double *__restrict__ aux, long long stride,
                                                      const PatchDesc *__restrict__ patches,
                                                      const WorkItem *__restrict__ work, int nwork,
-                                                     unsigned long long *cfl_bits)
+                                                     unsigned long long *cfl_bits, GhostArgs ga)
 {
     using S = Smem2D<EQN, TX, TY>;
     extern __shared__ double sm[];
@@ -237,7 +266,6 @@ __global__ void __launch_bounds__(kThreads) k_step2d(const double *__restrict__ 
     constexpr int SXS = (TY + 2) * TX, FFS = TY * (TX + 1), SYS = TY * (TX + 2), GGS = (TY + 1) * TX;
 
     const int tid = threadIdx.x;
-    constexpr int CF = kCfBase(EQN);
     long long cfl = 0;
     for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
         const WorkItem wi = work[w];
@@ -247,15 +275,40 @@ __global__ void __launch_bounds__(kThreads) k_step2d(const double *__restrict__ 
         const int rx = tx + 4, ry = ty + 4;
         const double dtdx = P.dtdx, dtdy = P.dtdy, hx = P.hx, hy = P.hy;
         // ---- stage state and coefficients (tile + 2-cell halo) ----
+        // With ga.gd set, the ghost-ring cells of the state are not read from
+        // q but computed from their ghost descriptors (same-level copy or
+        // coarse space-time interpolation, Sec. 3) in a second pass over the
+        // staged region; without it the ring of q was filled beforehand.
         {
             const long long gb = P.base + (long long)y0 * P.sx + x0;
             const int nrow = rx;
+            // the staged storage columns [x0, x0+tx+4) reach the ghost ring when x0 < 2
+            // or x0 + tx + 3 >= nx + 2 (rows alike)
+            const bool ring = ga.gd && (x0 < 2 || y0 < 2 || x0 + tx + 1 >= P.nx || y0 + ty + 1 >= P.ny);
             for (int k = tid; k < (3 + S::NA) * ry * nrow; k += kThreads) {
                 int f = k / (ry * nrow), rem = k - f * ry * nrow;
                 int r = rem / nrow, c = rem - r * nrow;
                 long long g = gb + (long long)r * P.sx + c;
-                if (f < 3) sQ[f * PS + r * PX + c] = q[(long long)f * stride + g];
-                else sA[(f - 3) * PS + r * PX + c] = aux[(long long)(f - 3) * stride + g];
+                if (f < 3) {
+                    const int si = x0 + c, sj = y0 + r;
+                    if (!(ring && (si < 2 || si >= P.nx + 2 || sj < 2 || sj >= P.ny + 2)))
+                        sQ[f * PS + r * PX + c] = q[(long long)f * stride + g];
+                } else {
+                    sA[(f - 3) * PS + r * PX + c] = aux[(long long)(f - 3) * stride + g];
+                }
+            }
+            if (ring) {
+                for (int k = tid; k < ry * nrow; k += kThreads) {
+                    int r = k / nrow, c = k - r * nrow;
+                    const int si = x0 + c, sj = y0 + r;
+                    if (!(si < 2 || si >= P.nx + 2 || sj < 2 || sj >= P.ny + 2)) continue;
+                    const GhostDesc gdsc = ga.gd[P.gbase + ghost_local_index(P, si, sj, 2)];
+                    double v[3];
+#pragma unroll
+                    for (int f = 0; f < 3; f++) v[f] = ghost_value(gdsc, q, stride, ga.qco, ga.qcn, ga.sc, f, ga.k, ga.th, 2);
+#pragma unroll
+                    for (int f = 0; f < 3; f++) sQ[f * PS + r * PX + c] = v[f];
+                }
             }
         }
         __syncthreads();
@@ -310,7 +363,7 @@ __global__ void __launch_bounds__(kThreads) k_step2d(const double *__restrict__ 
                 double w10 = XW[o], w1n = XW[XES + o], w20 = XW[2 * XES + o], w2n = XW[3 * XES + o];
                 double p1 = mc_phi(w10, w1n, XW[u1], XW[XES + u1]);
                 double p2 = mc_phi(w20, w2n, XW[2 * XES + u2], XW[3 * XES + u2]);
-                double cf1 = sA[CF * PS + r], cf2 = sA[(CF + 1) * PS + r];
+                double cf1 = corr_coef<EQN>(e.s1, dtdx), cf2 = corr_coef<EQN>(e.s2, dtdx);
                 int on = er * XNX + ec;
                 XN[on] = 0.5 * (cf1 * (p1 * w10) + cf2 * (p2 * w20));
                 XN[XNS + on] = 0.5 * (cf1 * (p1 * w1n) + cf2 * (p2 * w2n));
@@ -326,7 +379,7 @@ __global__ void __launch_bounds__(kThreads) k_step2d(const double *__restrict__ 
                 double w10 = YW[o], w1n = YW[YES + o], w20 = YW[2 * YES + o], w2n = YW[3 * YES + o];
                 double p1 = mc_phi(w10, w1n, YW[u1], YW[YES + u1]);
                 double p2 = mc_phi(w20, w2n, YW[2 * YES + u2], YW[3 * YES + u2]);
-                double cf1 = sA[(CF + 3) * PS + r], cf2 = sA[(CF + 4) * PS + r];
+                double cf1 = corr_coef<EQN>(e.s1, dtdy), cf2 = corr_coef<EQN>(e.s2, dtdy);
                 int on = er * YNX + ec;
                 YN[on] = 0.5 * (cf1 * (p1 * w10) + cf2 * (p2 * w20));
                 YN[YNS + on] = 0.5 * (cf1 * (p1 * w1n) + cf2 * (p2 * w2n));
@@ -372,7 +425,7 @@ __global__ void __launch_bounds__(kThreads) k_step2d(const double *__restrict__ 
                 int on = (r + 1) * XNX + ec;
                 for (int kk = 0; kk < 2; kk++)
                     FF[kk * FFS + r * (TX + 1) + ec] = fma(-hy, am[kk] + bp[kk], XN[kk * XNS + on]);
-                cfl = bmax(cfl, sA[(CF + 2) * PS + rr]);
+                cfl = bmax(cfl, dtdx * maxabs(e.s1, e.s2));
             } else {
                 int kk0 = k - (tx + 1) * ty;
                 int er = kk0 / tx, c = kk0 - er * tx;              // y-edge ey = er, column c
@@ -387,7 +440,7 @@ __global__ void __launch_bounds__(kThreads) k_step2d(const double *__restrict__ 
                 int on = er * YNX + c + 1;
                 for (int kk = 0; kk < 2; kk++)
                     GG[kk * GGS + er * TX + c] = fma(-hx, am[kk] + bp[kk], YN[kk * YNS + on]);
-                cfl = bmax(cfl, sA[(CF + 5) * PS + rr]);
+                cfl = bmax(cfl, dtdy * maxabs(e.s1, e.s2));
             }
         }
         __syncthreads();
@@ -427,7 +480,7 @@ __global__ void __launch_bounds__(kThreads) k_step1d(const double *__restrict__ 
                                                      const double *__restrict__ aux, long long stride,
                                                      const PatchDesc *__restrict__ patches,
                                                      const WorkItem *__restrict__ work, int nwork,
-                                                     unsigned long long *cfl_bits)
+                                                     unsigned long long *cfl_bits, GhostArgs ga)
 {
     using S = Smem1D<EQN, TX>;
     extern __shared__ double sm[];
@@ -438,7 +491,6 @@ __global__ void __launch_bounds__(kThreads) k_step1d(const double *__restrict__ 
     double *XF = XW + 4 * XE;
     double *XN = XF + 4 * XE;
     const int tid = threadIdx.x;
-    constexpr int CF = kCfBase(EQN);
     long long cfl = 0;
     for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
         const WorkItem wi = work[w];
@@ -446,11 +498,26 @@ __global__ void __launch_bounds__(kThreads) k_step1d(const double *__restrict__ 
         const int x0 = wi.x0;
         const int tx = min(TX, P.nx - x0), rx = tx + 4;
         const double dtdx = P.dtdx;
+        const bool ring = ga.gd && (x0 < 2 || x0 + tx + 1 >= P.nx);  // staged [x0, x0+tx+4) meets the ring
         for (int k = tid; k < (2 + S::NA) * rx; k += kThreads) {
             int f = k / rx, c = k - f * rx;
             long long g = P.base + x0 + c;
-            if (f < 2) sQ[f * PX + c] = q[(long long)f * stride + g];
-            else sA[(f - 2) * PX + c] = aux[(long long)(f - 2) * stride + g];
+            if (f < 2) {
+                const int si = x0 + c;
+                if (!(ring && (si < 2 || si >= P.nx + 2))) sQ[f * PX + c] = q[(long long)f * stride + g];
+            } else {
+                sA[(f - 2) * PX + c] = aux[(long long)(f - 2) * stride + g];
+            }
+        }
+        for (int c = tid; ring && c < rx; c += kThreads) {
+            const int si = x0 + c;
+            if (si < 2 || si >= P.nx + 2) {
+                const GhostDesc gdsc = ga.gd[P.gbase + ghost_local_index(P, si, 0, 0)];
+                double v0 = ghost_value(gdsc, q, stride, ga.qco, ga.qcn, ga.sc, 0, ga.k, ga.th, 1);
+                double v1 = ghost_value(gdsc, q, stride, ga.qco, ga.qcn, ga.sc, 1, ga.k, ga.th, 1);
+                sQ[c] = v0;
+                sQ[PX + c] = v1;
+            }
         }
         __syncthreads();
         for (int k = tid; k < tx + 3; k += kThreads) {    // edge ex = k-1 between staged cells k, k+1
@@ -478,10 +545,10 @@ __global__ void __launch_bounds__(kThreads) k_step1d(const double *__restrict__ 
             double w10 = XW[o], w1n = XW[XE + o], w20 = XW[2 * XE + o], w2n = XW[3 * XE + o];
             double p1 = mc_phi(w10, w1n, XW[u1], XW[XE + u1]);
             double p2 = mc_phi(w20, w2n, XW[2 * XE + u2], XW[3 * XE + u2]);
-            double cf1 = sA[CF * PX + r], cf2 = sA[(CF + 1) * PX + r];
+            double cf1 = corr_coef<EQN>(e.s1, dtdx), cf2 = corr_coef<EQN>(e.s2, dtdx);
             XN[k] = 0.5 * (cf1 * (p1 * w10) + cf2 * (p2 * w20));
             XN[XNn + k] = 0.5 * (cf1 * (p1 * w1n) + cf2 * (p2 * w2n));
-            cfl = bmax(cfl, sA[(CF + 2) * PX + r]);
+            cfl = bmax(cfl, dtdx * maxabs(e.s1, e.s2));
         }
         __syncthreads();
         for (int c = tid; c < tx; c += kThreads) {
@@ -509,26 +576,26 @@ cudaError_t ensure_smem_attr(size_t smem)
 template <auto Kern>
 cudaError_t launch_kernel(size_t smem, int nwork, int grid, const double *q, double *qn, const double *aux,
                           long long stride, const PatchDesc *patches, const WorkItem *work,
-                          unsigned long long *cfl_bits, cudaStream_t s)
+                          unsigned long long *cfl_bits, cudaStream_t s, const GhostArgs &ga)
 {
     auto kern = Kern;
     cudaError_t e = ensure_smem_attr<Kern>(smem);
     if (e != cudaSuccess) return e;
     if (nwork <= 0) return cudaSuccess;
     int g = grid > 0 ? grid : nwork;
-    kern<<<g, kThreads, smem, s>>>(q, qn, aux, stride, patches, work, nwork, cfl_bits);
+    kern<<<g, kThreads, smem, s>>>(q, qn, aux, stride, patches, work, nwork, cfl_bits, ga);
     return cudaGetLastError();
 }
 
 template <int EQN>
 cudaError_t dispatch2d(int tx, int ty, int nwork, int grid, const double *q, double *qn, const double *aux,
                        long long stride, const PatchDesc *p, const WorkItem *w, unsigned long long *c,
-                       cudaStream_t s)
+                       cudaStream_t s, const GhostArgs &ga)
 {
 #define ADJ_TILE(X, Y)                                                                                    \
     if (tx == X && ty == Y)                                                                               \
         return launch_kernel<k_step2d<EQN, X, Y>>(Smem2D<EQN, X, Y>::bytes, nwork, grid, q, qn, aux, stride, p, w, \
-                                                  c, s);
+                                                  c, s, ga);
     ADJ_TILE(32, 8)
     ADJ_TILE(16, 8)
     ADJ_TILE(16, 16)
@@ -541,12 +608,15 @@ cudaError_t dispatch2d(int tx, int ty, int nwork, int grid, const double *q, dou
 
 template <int EQN>
 cudaError_t dispatch1d(int tx, int nwork, int grid, const double *q, double *qn, const double *aux, long long stride,
-                       const PatchDesc *p, const WorkItem *w, unsigned long long *c, cudaStream_t s)
+                       const PatchDesc *p, const WorkItem *w, unsigned long long *c, cudaStream_t s,
+                       const GhostArgs &ga)
 {
     if (tx == 256)
-        return launch_kernel<k_step1d<EQN, 256>>(Smem1D<EQN, 256>::bytes, nwork, grid, q, qn, aux, stride, p, w, c, s);
+        return launch_kernel<k_step1d<EQN, 256>>(Smem1D<EQN, 256>::bytes, nwork, grid, q, qn, aux, stride, p, w, c, s,
+                                                 ga);
     if (tx == 128)
-        return launch_kernel<k_step1d<EQN, 128>>(Smem1D<EQN, 128>::bytes, nwork, grid, q, qn, aux, stride, p, w, c, s);
+        return launch_kernel<k_step1d<EQN, 128>>(Smem1D<EQN, 128>::bytes, nwork, grid, q, qn, aux, stride, p, w, c, s,
+                                                 ga);
     return cudaErrorInvalidValue;
 }
 
@@ -574,20 +644,20 @@ int occ2d(int tx, int ty)
 
 cudaError_t launch_step(int dim, int eqn, int tx, int ty, const double *q, double *qn, const double *aux,
                         long long stride, const PatchDesc *patches, const WorkItem *work, int nwork, int grid,
-                        unsigned long long *cfl_bits, cudaStream_t s)
+                        unsigned long long *cfl_bits, cudaStream_t s, GhostArgs ga)
 {
     if (dim == 1) {
         switch (eqn) {
-        case 0: return dispatch1d<0>(tx, nwork, grid, q, qn, aux, stride, patches, work, cfl_bits, s);
-        case 1: return dispatch1d<1>(tx, nwork, grid, q, qn, aux, stride, patches, work, cfl_bits, s);
+        case 0: return dispatch1d<0>(tx, nwork, grid, q, qn, aux, stride, patches, work, cfl_bits, s, ga);
+        case 1: return dispatch1d<1>(tx, nwork, grid, q, qn, aux, stride, patches, work, cfl_bits, s, ga);
         default: return cudaErrorInvalidValue;
         }
     }
     switch (eqn) {
-    case 0: return dispatch2d<0>(tx, ty, nwork, grid, q, qn, aux, stride, patches, work, cfl_bits, s);
-    case 1: return dispatch2d<1>(tx, ty, nwork, grid, q, qn, aux, stride, patches, work, cfl_bits, s);
-    case 2: return dispatch2d<2>(tx, ty, nwork, grid, q, qn, aux, stride, patches, work, cfl_bits, s);
-    case 3: return dispatch2d<3>(tx, ty, nwork, grid, q, qn, aux, stride, patches, work, cfl_bits, s);
+    case 0: return dispatch2d<0>(tx, ty, nwork, grid, q, qn, aux, stride, patches, work, cfl_bits, s, ga);
+    case 1: return dispatch2d<1>(tx, ty, nwork, grid, q, qn, aux, stride, patches, work, cfl_bits, s, ga);
+    case 2: return dispatch2d<2>(tx, ty, nwork, grid, q, qn, aux, stride, patches, work, cfl_bits, s, ga);
+    case 3: return dispatch2d<3>(tx, ty, nwork, grid, q, qn, aux, stride, patches, work, cfl_bits, s, ga);
     default: return cudaErrorInvalidValue;
     }
 }

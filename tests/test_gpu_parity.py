@@ -198,6 +198,44 @@ def test_amr_run_matches_oracle(A, which):
     assert abs(Jg - Jo) <= RTOL * max(abs(Jo), 1e-300)
 
 
+def test_per_level_kernels_compute_the_same_bits(A):
+    """A different step-kernel tile on each level, with the ghost ring computed
+    inside the step kernel or by the separate fill kernel, changes nothing in
+    the results; the per-level statistics add up to the totals."""
+    wl = W.config2(seed=3, n0=32, ratios=(2, 4), tf=2.0, adj_n=64, nsnap=20, ts=0.0, tol=1e-4,
+                   min_patch=8, max_patch=32)
+    adj = A.solve_adjoint(wl)
+    runs = []
+    for cfg in (None, [((8, 8), False), ((16, 16), True), ((64, 8), False)],
+                [((32, 16), True), ((16, 8), False), ((8, 8), True)]):
+        h = A.Hierarchy(wl)
+        h.set_adjoint(adj)
+        h.set_timing(True)
+        if cfg:
+            for lev, (t, fuse) in enumerate(cfg):
+                h.set_level_kernel(lev, t, fuse)
+        h.regrid(0, init=True)
+        h.advance(h.nsteps_total())
+        st = h.stats()
+        assert sum(st["level_cell_updates"]) == st["cell_updates"]
+        assert sum(st["level_step_launches"]) == st["step_kernel_launches"]
+        assert abs(sum(st["level_step_ms"]) - st["step_kernel_ms"]) <= 1e-6 * max(st["step_kernel_ms"], 1.0)
+        assert sum(st["level_cell_updates"][1:]) > 0, "the case never refined"
+        runs.append((h.functional(), [h.read_level(lev) for lev in range(wl.nlevels)],
+                     [h.patches(lev) for lev in range(wl.nlevels)]))
+        h.close()
+    for J, lv, pt in runs[1:]:
+        assert J == runs[0][0]
+        assert all(np.array_equal(a, b) for a, b in zip(lv, runs[0][1]))
+        assert all(np.array_equal(a, b) for a, b in zip(pt, runs[0][2]))
+    h = A.Hierarchy(wl)
+    with pytest.raises(A.AdjamrError):
+        h.set_level_kernel(0, (24, 8))
+    with pytest.raises(A.AdjamrError):
+        h.set_level_kernel(wl.nlevels, (32, 8))
+    h.close()
+
+
 def _adj_medium(wl):
     nx = wl.adj_n[0]
     xa = wl.lo[0] + (np.arange(nx) + 0.5) * (wl.hi[0] - wl.lo[0]) / nx
@@ -250,14 +288,17 @@ def test_torch_stream_interop(A):
 def test_batched_patches_modes_agree_and_match_oracle(A):
     """4096 uneven patches (the batching stress configuration): the fused
     work-list launch, the persistent grid, one launch per patch, and the
-    CUDA-graph replay all produce the same bits; sampled patches (smallest,
+    CUDA-graph replay, each with the ghost ring filled by its own kernel or
+    inside the step kernel, all produce the same bits; sampled patches (smallest,
     largest, and random) match the oracle run of that patch alone."""
     pb = W.config4(seed=0)
     results = []
-    for mode, graph in ((0, False), (1, False), (2, False), (0, True), (1, True)):
+    for mode, graph, fuse in ((0, False, False), (1, False, False), (2, False, False), (0, True, False),
+                              (1, True, False), (0, False, True), (1, True, True), (2, False, True)):
         import torch
         s = torch.cuda.Stream()
         b = A.Batch(pb, stream=s.cuda_stream)
+        b.set_ghost_fusion(fuse)
         b.step(4, mode=mode, tile=(32, 8), graph=graph)
         results.append(b.read())
         b.close()
