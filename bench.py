@@ -492,6 +492,41 @@ def run_case_batch(args):
     b.close()
 
 
+def run_case_solve(args):
+    """Profiling case: one config-2 forward solve to --tf (adjoint solved
+    first), step-kernel tile and ghost mode of every level fixed
+    (8x8 fused, 8x8 fused, 16x8 fused); prints per-level step statistics."""
+    import torch
+    from paper_1511_03645_gb300 import adjamr as A
+    torch.cuda.set_device(0)
+    s = torch.cuda.Stream()
+    wl = workload()
+    if args.tf:
+        wl.tf = args.tf
+    adj = A.solve_adjoint(wl, stream=s.cuda_stream)
+    for rep in range(1 + args.warmup):
+        h = A.Hierarchy(wl, stream=s.cuda_stream)
+        for lev, t in enumerate([(8, 8), (8, 8), (16, 8)][:wl.nlevels]):
+            h.set_level_kernel(lev, t, True)
+        h.set_adjoint(adj)
+        h.set_timing(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h.regrid(0, init=True)
+        h.advance(h.nsteps_total())
+        J = h.functional()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        st = h.stats()
+        h.close()
+    print(json.dumps({"case": "solve", "tf": wl.tf, "s": el, "J": J, "cell_updates": st["cell_updates"],
+                      "kernel_launches": st["kernel_launches"], "step_kernel_ms": st["step_kernel_ms"],
+                      "level_step_ms": st["level_step_ms"][:wl.nlevels],
+                      "level_step_launches": st["level_step_launches"][:wl.nlevels],
+                      "level_cell_updates": st["level_cell_updates"][:wl.nlevels],
+                      "regrid_phase_ms": st["regrid_phase_ms"]}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -500,7 +535,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--case", default="main", choices=["main", "batch", "serve"])
+    ap.add_argument("--case", default="main", choices=["main", "batch", "serve", "solve"])
+    ap.add_argument("--tf", type=float, default=0.0, help="solve case: final time (0: the workload's)")
     ap.add_argument("--nreq", type=int, default=512)
     ap.add_argument("--slots", type=int, default=16)
     ap.add_argument("--serve-sample", type=int, default=32)
@@ -510,6 +546,9 @@ def main():
         return
     if args.case == "serve":
         run_case_serve(args)
+        return
+    if args.case == "solve":
+        run_case_solve(args)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

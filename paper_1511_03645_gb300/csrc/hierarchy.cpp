@@ -88,6 +88,10 @@ struct adjamr_ctx {
     size_t h_stage_bytes = 0;
     cudaEvent_t stage_ev = nullptr;
     unsigned char *d_flagbuf = nullptr;
+    // per-level bilinear tables of the adjoint grid for the dense flag kernel
+    char *d_ftab[ADJAMR_MAX_LEVELS] = {};
+    int ftab_ax[ADJAMR_MAX_LEVELS] = {}, ftab_ay[ADJAMR_MAX_LEVELS] = {};
+    size_t ftab_off[ADJAMR_MAX_LEVELS][6] = {};
     size_t flagbuf_bytes = 0;
     double *d_fscratch = nullptr, *d_fout = nullptr;
     size_t fscratch_n = 0;
@@ -611,7 +615,7 @@ adjamr_status regrid_body(adjamr_ctx *c, int base, int init)
         const int r = P.ratio[lev], N = C.N, M = C.M, dim = P.dim;
         const long long tick = C.nstep * c->T[lev];
         // ---- adjoint flags of level lev on its index space (device) ----
-        size_t nb = (size_t)N * M;
+        size_t nb = ((size_t)N * M + 255) / 256 * 256;  // padded: the dense flag kernel ORs whole words
         if (c->flagbuf_bytes < nb) {
             dfree(c->d_flagbuf, c->s);
             CKR(c, dalloc(&c->d_flagbuf, nb, c->s));
@@ -767,6 +771,59 @@ adjamr_status regrid_body(adjamr_ctx *c, int base, int init)
     return ADJAMR_OK;
 }
 
+constexpr int kFlagBlocksPerThread = 4;
+
+// Per-column and per-row bilinear tables of the attached adjoint grid for
+// level l (the same arithmetic as the flag kernel's per-cell setup: cell
+// centre x = lo + (I + 1/2) dx; u = (x - lo) / dxa; stencil index and
+// weight from u - 1/2 clamped to the outermost centres; containing cell
+// floor(u) clamped).  Rebuilt when the adjoint grid changes.
+adjamr_status flag_tables(adjamr_ctx *c, int l)
+{
+    const adjamr_params &P = c->P;
+    Level &L = c->L[l];
+    const int ax = c->adj->ax, ay = c->adj->ay;
+    if (c->d_ftab[l] && c->ftab_ax[l] == ax && c->ftab_ay[l] == ay) return ADJAMR_OK;
+    dfree(c->d_ftab[l], c->s);
+    const int N = L.N, M = (P.dim == 2) ? L.M : 1;
+    std::vector<int> ta(N), tac(N), tb(M), tbc(M);
+    std::vector<double> twx(N), twy(M);
+    auto axis = [](double x, double lo, double hi, int na, int &a, double &w, int &acell) {
+        double dxa = (hi - lo) / (double)na;
+        double u = (x - lo) / dxa;
+        double xi = u - 0.5;
+        xi = std::fmin(std::fmax(xi, 0.0), (double)(na - 1));
+        a = (int)std::floor(xi);
+        if (a > na - 2) a = na - 2;
+        if (a < 0) a = 0;
+        w = xi - (double)a;
+        acell = (int)std::floor(u);
+        if (acell < 0) acell = 0;
+        if (acell > na - 1) acell = na - 1;
+    };
+    for (int I = 0; I < N; I++) {
+        double x = P.lo[0] + ((double)I + 0.5) * L.dx;
+        axis(x, P.lo[0], P.hi[0], ax, ta[I], twx[I], tac[I]);
+    }
+    for (int J = 0; J < M; J++) {
+        if (P.dim == 2) {
+            double y = P.lo[1] + ((double)J + 0.5) * L.dy;
+            axis(y, P.lo[1], P.hi[1], ay, tb[J], twy[J], tbc[J]);
+        } else {
+            tb[J] = tbc[J] = 0;
+            twy[J] = 0.0;
+        }
+    }
+    std::vector<size_t> offs;
+    CKR(c, upload_packed(c, {{ta.data(), sizeof(int) * N}, {tac.data(), sizeof(int) * N}, {twx.data(), sizeof(double) * N},
+                             {tb.data(), sizeof(int) * M}, {tbc.data(), sizeof(int) * M}, {twy.data(), sizeof(double) * M}},
+                         &c->d_ftab[l], offs));
+    for (int k = 0; k < 6; k++) c->ftab_off[l][k] = offs[k];
+    c->ftab_ax[l] = ax;
+    c->ftab_ay[l] = ay;
+    return ADJAMR_OK;
+}
+
 adjamr_status flag_dense(adjamr_ctx *c, int l, double tol, unsigned char *d_dense, unsigned char *d_patchflags,
                          long long *nflag_out, int *bbox_out)
 {
@@ -821,7 +878,28 @@ adjamr_status flag_dense(adjamr_ctx *c, int l, double tol, unsigned char *d_dens
     a.bbox = c->d_bbox;
     CKR(c, cudaMemsetAsync(c->d_count, 0, sizeof(unsigned long long), c->s));
     CKR(c, cudaMemcpyAsync(c->d_bbox, bbox_init, sizeof bbox_init, cudaMemcpyHostToDevice, c->s));
-    CKR(c, launch_flag(a, c->s));
+    // regrid flags (dense only, bracket max, block maxima present): one thread
+    // per (cell, group of snapshot blocks) over the level's index space
+    const bool dense = d_dense && !d_patchflags && P.flag_mode == ADJAMR_FLAG_BRACKET_MAX && c->adj &&
+                       c->adj->d_bmax && a.S >= 2;
+    if (dense) {
+        TRY(flag_tables(c, l));
+        const size_t *off = c->ftab_off[l];
+        char *base = c->d_ftab[l];
+        a.owner = L.d_owner;
+        a.M = L.M;
+        a.tab_a = (const int *)(base + off[0]);
+        a.tab_ac = (const int *)(base + off[1]);
+        a.tab_wx = (const double *)(base + off[2]);
+        a.tab_b = (const int *)(base + off[3]);
+        a.tab_bc = (const int *)(base + off[4]);
+        a.tab_wy = (const double *)(base + off[5]);
+        a.gblk = kFlagBlocksPerThread;
+        const int nblk = (a.nlo <= a.nhi) ? a.nhi / kSnapBlock - a.nlo / kSnapBlock + 1 : 1;
+        CKR(c, launch_flag_dense(a, (nblk + a.gblk - 1) / a.gblk, c->s));
+    } else {
+        CKR(c, launch_flag(a, c->s));
+    }
     c->st.kernel_launches++;
     unsigned long long cnt = 0;
     int bb[4];
@@ -1710,6 +1788,7 @@ void adjamr_destroy(adjamr_ctx *ctx)
     }
     for (double *p : ctx->dense_dev) cudaFreeAsync(p, ctx->s);
     dfree(ctx->d_flagbuf, ctx->s);
+    for (int l = 0; l < ADJAMR_MAX_LEVELS; l++) dfree(ctx->d_ftab[l], ctx->s);
     dfree(ctx->d_fscratch, ctx->s);
     cudaStreamSynchronize(ctx->s);
     if (ctx->d_cfl) cudaFree(ctx->d_cfl);

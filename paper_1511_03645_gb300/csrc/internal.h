@@ -142,6 +142,14 @@ struct FlagArgs {
     unsigned long long *count;
     int *bbox;                      // [4]: min I, max I, min J, max J of flagged cells (atomics)
     const double *bmax;             // block maxima for culling (may be null)
+    // dense bracket-max variant: the level's owner map ([M][N] storage index
+    // or -1) and per-column / per-row bilinear tables of the adjoint grid
+    const int *owner;
+    int M, gblk;                    // index-space rows; snapshot blocks per thread
+    const int *tab_a, *tab_ac;      // [N]: stencil column, column of the containing cell
+    const double *tab_wx;           // [N]
+    const int *tab_b, *tab_bc;      // [M]
+    const double *tab_wy;           // [M]
 };
 constexpr int kSnapBlock = 8;       // snapshots per culling block
 // block maxima of a snapshot set: bmax[blk][f][b][a] = max over the block's
@@ -149,6 +157,9 @@ constexpr int kSnapBlock = 8;       // snapshots per culling block
 cudaError_t launch_block_max(const double *snaps, int S, int m, int ax, int ay, int dim, double *bmax,
                              cudaStream_t s);
 cudaError_t launch_flag(const FlagArgs &a, cudaStream_t s);
+// bracket-max flags over the level's index space, one thread per (cell, group
+// of a.gblk snapshot blocks); flags_dense (4-byte padded) must start zeroed
+cudaError_t launch_flag_dense(const FlagArgs &a, int ngroup, cudaStream_t s);
 
 // terms weight*(q0*area) of the functional into out[0..n)
 cudaError_t launch_func_terms(const long long *idx, const double *area, long long n, const double *q, double weight,

@@ -497,6 +497,80 @@ __global__ void k_flag(FlagArgs A)
     }
 }
 
+// Bracket-max flagging over the level's dense index space: thread (cell,
+// group) scans the group's snapshot blocks of the window.  A cell is flagged
+// iff some |q^_n . q| of the window exceeds tol (Sec. 4; the decision does not
+// depend on the order the snapshots are visited, so the window may be split
+// among threads); blocks whose bound cannot exceed tol are skipped as in
+// k_flag.  The first thread to set a cell's flag counts it; warp shuffles
+// reduce the count and the bounding box of the flags.
+__global__ void k_flag_dense(FlagArgs A)
+{
+    const long long NM = (long long)A.N * A.M;
+    const long long cidx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int grp = blockIdx.y;
+    bool hit = false, fresh = false;
+    int fI = 0x7fffffff, fJ = 0x7fffffff, gI = -1, gJ = -1;
+    if (cidx < NM) {
+        const int o = A.owner[cidx];
+        if (o >= 0) {
+            const int J = (int)(cidx / A.N), I = (int)(cidx - (long long)J * A.N);
+            const int ac = A.tab_ac[I], bc = (A.dim == 2) ? A.tab_bc[J] : 0;
+            const bool dry = A.wet && !A.wet[(long long)bc * A.ax + ac];
+            if (A.S < 2 || dry || A.nlo > A.nhi) {
+                hit = (grp == 0) && (0.0 > A.tol);
+            } else {
+                double Q[3];
+                for (int f = 0; f < A.m; f++) Q[f] = A.q[(long long)f * A.stride + o];
+                const int a = A.tab_a[I], b = (A.dim == 2) ? A.tab_b[J] : 0;
+                const double wx = A.tab_wx[I], wy = (A.dim == 2) ? A.tab_wy[J] : 0.0;
+                const long long plane = (long long)A.ax * A.ay;
+                const long long acell = (long long)b * A.ax + a;
+                const volatile unsigned char *done = A.flags_dense + cidx;
+                const int blo = A.nlo / kSnapBlock + grp * A.gblk;
+                const int bhi = min(A.nhi / kSnapBlock, blo + A.gblk - 1);
+                for (int blk = blo; blk <= bhi && !hit; blk++) {
+                    if (*done) break;  // set by another group: nothing left to decide
+                    double B = 0.0;
+                    for (int f = 0; f < A.m; f++)
+                        B = fma(fabs(Q[f]), A.bmax[((long long)blk * A.m + f) * plane + acell], B);
+                    if (B * (1.0 + 1e-12) <= A.tol) continue;
+                    const int n0 = max(A.nlo, blk * kSnapBlock), n1 = min(A.nhi, blk * kSnapBlock + kSnapBlock - 1);
+                    for (int n = n0; n <= n1 && !hit; n++) {
+                        double d = 0.0;
+                        for (int f = 0; f < A.m; f++) {
+                            double av = adj_interp(A, n, f, a, wx, b, wy);
+                            d = (f == 0) ? av * Q[0] : d + av * Q[f];
+                        }
+                        hit = fabs(d) > A.tol;
+                    }
+                }
+            }
+            if (hit) {
+                unsigned int *word = reinterpret_cast<unsigned int *>(A.flags_dense + (cidx & ~3LL));
+                const unsigned int bit = 1u << (8 * (int)(cidx & 3));
+                fresh = (atomicOr(word, bit) & bit) == 0;
+                fI = gI = I;
+                fJ = gJ = J;
+            }
+        }
+    }
+    const unsigned fr = __ballot_sync(0xffffffffu, fresh);
+    if (__any_sync(0xffffffffu, hit)) {
+        fI = __reduce_min_sync(0xffffffffu, fI);
+        fJ = __reduce_min_sync(0xffffffffu, fJ);
+        gI = __reduce_max_sync(0xffffffffu, gI);
+        gJ = __reduce_max_sync(0xffffffffu, gJ);
+        if ((threadIdx.x & 31) == 0) {
+            if (fr) atomicAdd(A.count, (unsigned long long)__popc(fr));
+            atomicMin(A.bbox + 0, fI);
+            atomicMax(A.bbox + 1, gI);
+            atomicMin(A.bbox + 2, fJ);
+            atomicMax(A.bbox + 3, gJ);
+        }
+    }
+}
+
 __global__ void k_block_max(const double *__restrict__ snaps, int S, int m, int ax, int ay, int dim, int nblk,
                             double *bmax)
 {
@@ -640,6 +714,15 @@ cudaError_t launch_block_max(const double *snaps, int S, int m, int ax, int ay, 
     long long n = (long long)nblk * m * ax * ay;
     if (n <= 0) return cudaSuccess;
     k_block_max<<<nblk_of(n), kT, 0, s>>>(snaps, S, m, ax, ay, dim, nblk, bmax);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flag_dense(const FlagArgs &a, int ngroup, cudaStream_t s)
+{
+    const long long nm = (long long)a.N * a.M;
+    if (nm <= 0 || ngroup <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((nm + kT - 1) / kT), (unsigned)ngroup);
+    k_flag_dense<<<grid, kT, 0, s>>>(a);
     return cudaGetLastError();
 }
 
