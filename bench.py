@@ -220,6 +220,7 @@ def run_ours(args, rank, world):
     cluster_ms = 0.0
     rebuilds = 0
     phases = [0.0] * 6
+    cphases = [0.0] * 4
     lev_ms = [0.0] * wl.nlevels
     lev_launch = [0] * wl.nlevels
     lev_cells = [0] * wl.nlevels
@@ -242,6 +243,7 @@ def run_ours(args, rank, world):
         cluster_ms += st["cluster_host_ms"]
         rebuilds += st["level_rebuilds"]
         phases = [a + b for a, b in zip(phases, st["regrid_phase_ms"])]
+        cphases = [a + b for a, b in zip(cphases, st["cluster_phase_ms"])]
         for lev in range(wl.nlevels):
             lev_ms[lev] += st["level_step_ms"][lev]
             lev_launch[lev] += st["level_step_launches"][lev]
@@ -388,7 +390,9 @@ def run_ours(args, rank, world):
                                   "level_rebuilds": rebuilds / args.steps,
                                   "regrid_phases": dict(zip(["flag_and_wait", "window_copy", "clustering",
                                                              "arena_alloc_upload", "builder_kernels", "release_old"],
-                                                            [v / args.steps for v in phases]))},
+                                                            [v / args.steps for v in phases])),
+                                  "clustering_phases": dict(zip(["dilate_nest", "integral_images", "bisection",
+                                                                 "split_sort"], [v / args.steps for v in cphases]))},
         "autotune_levels_ms": {f"{t['tile'][0]}x{t['tile'][1]}{'' if t['fuse_ghosts'] else '+fill'}":
                                [round(x["ms"], 3) for x in t["levels"]] for t in tuned["candidates"]},
         "adjoint_solve_s": adj_s,

@@ -146,6 +146,10 @@ typedef struct adjamr_stats {
     double level_step_ms[ADJAMR_MAX_LEVELS];
     long long level_step_launches[ADJAMR_MAX_LEVELS];
     long long level_cell_updates[ADJAMR_MAX_LEVELS];
+    /* host wall time inside clustering (regrid_phase_ms[2]): [0] buffer
+     * dilation and nesting mask, [1] integral images, [2] Berger-Rigoutsos
+     * bisection, [3] splitting to the maximum patch size and ordering */
+    double cluster_phase_ms[4];
 } adjamr_stats;
 
 typedef struct adjamr_ctx adjamr_ctx;

@@ -86,7 +86,8 @@ class Stats(ctypes.Structure):
                 ("regrid_phase_ms", ctypes.c_double * 6),
                 ("level_step_ms", ctypes.c_double * MAXLEV),
                 ("level_step_launches", ctypes.c_longlong * MAXLEV),
-                ("level_cell_updates", ctypes.c_longlong * MAXLEV)]
+                ("level_cell_updates", ctypes.c_longlong * MAXLEV),
+                ("cluster_phase_ms", ctypes.c_double * 4)]
 
 
 # every entry point declared in include/adjamr.h
@@ -365,7 +366,7 @@ class Hierarchy:
         s = Stats()
         _check(load().adjamr_get_stats(self.h, ctypes.byref(s)), self.h, "get_stats")
         d = {k: getattr(s, k) for k, _ in Stats._fields_}
-        for k in ("regrid_phase_ms", "level_step_ms", "level_step_launches", "level_cell_updates"):
+        for k in ("regrid_phase_ms", "level_step_ms", "level_step_launches", "level_cell_updates", "cluster_phase_ms"):
             d[k] = list(getattr(s, k))
         return d
 

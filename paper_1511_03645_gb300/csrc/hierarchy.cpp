@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -63,6 +64,23 @@ struct Level {
     std::vector<std::vector<int>> buckets;
 };
 
+// Row-major bitmap of a window of an index space: cell (i, j) is bit i & 63 of
+// word i >> 6 of row j.
+struct Bits {
+    int N = 0, M = 0, nw = 0;
+    std::vector<uint64_t> w;
+    void reset(int n, int m)
+    {
+        N = n;
+        M = m;
+        nw = (n + 63) >> 6;
+        w.assign((size_t)nw * m, 0);
+    }
+    uint64_t *row(int j) { return &w[(size_t)j * nw]; }
+    const uint64_t *row(int j) const { return &w[(size_t)j * nw]; }
+    uint64_t tail() const { return (N & 63) ? ((1ull << (N & 63)) - 1) : ~0ull; }
+};
+
 }  // namespace
 
 struct adjamr_ctx {
@@ -80,14 +98,15 @@ struct adjamr_ctx {
     unsigned long long *d_cfl = nullptr, *d_count = nullptr;
     int *d_err = nullptr;  // device-side invariant violations (nesting), checked after syncs
     int *d_bbox = nullptr; // bounding box of flagged cells of the last flag call
-    std::vector<unsigned char> h_fl, h_unc, h_nest, h_tmp;  // host clustering scratch (regrid window)
+    Bits h_fl, h_unc;               // host clustering scratch (regrid window)
+    std::vector<uint64_t> h_tmp;
     std::vector<int> h_cnt;
     // pinned staging for descriptor uploads; reused once the event of the
     // previous copy has completed
     char *h_stage = nullptr;
     size_t h_stage_bytes = 0;
     cudaEvent_t stage_ev = nullptr;
-    unsigned char *d_flagbuf = nullptr;
+    uint64_t *d_flagbuf = nullptr;  // flag bitmap of the level being regridded
     // per-level bilinear tables of the adjoint grid for the dense flag kernel
     char *d_ftab[ADJAMR_MAX_LEVELS] = {};
     int ftab_ax[ADJAMR_MAX_LEVELS] = {}, ftab_ay[ADJAMR_MAX_LEVELS] = {};
@@ -418,36 +437,136 @@ adjamr_status build_avg_map(adjamr_ctx *c, int l)
 // ---------------------------------------------------------------- clustering
 // Berger-Rigoutsos on a flag field [M][N] with a nesting mask, using
 // integral images for box counts and signatures.
+
+inline int popc(uint64_t x) { return __builtin_popcountll(x); }
+
+// number of set bits i0..i1 (inclusive) of a row
+inline int row_count(const uint64_t *r, int i0, int i1)
+{
+    const int k0 = i0 >> 6, k1 = i1 >> 6;
+    const uint64_t m0 = ~0ull << (i0 & 63), m1 = ~0ull >> (63 - (i1 & 63));
+    if (k0 == k1) return popc(r[k0] & m0 & m1);
+    int c = popc(r[k0] & m0);
+    for (int k = k0 + 1; k < k1; k++) c += popc(r[k]);
+    return c + popc(r[k1] & m1);
+}
+
+inline bool row_any(const uint64_t *r, int i0, int i1)
+{
+    const int k0 = i0 >> 6, k1 = i1 >> 6;
+    const uint64_t m0 = ~0ull << (i0 & 63), m1 = ~0ull >> (63 - (i1 & 63));
+    if (k0 == k1) return (r[k0] & m0 & m1) != 0;
+    if (r[k0] & m0) return true;
+    for (int k = k0 + 1; k < k1; k++)
+        if (r[k]) return true;
+    return (r[k1] & m1) != 0;
+}
+
+inline void row_clear(uint64_t *r, int i0, int i1)
+{
+    const int k0 = i0 >> 6, k1 = i1 >> 6;
+    const uint64_t m0 = ~0ull << (i0 & 63), m1 = ~0ull >> (63 - (i1 & 63));
+    if (k0 == k1) {
+        r[k0] &= ~(m0 & m1);
+        return;
+    }
+    r[k0] &= ~m0;
+    for (int k = k0 + 1; k < k1; k++) r[k] = 0;
+    r[k1] &= ~m1;
+}
+
+// Chebyshev dilation by w cells along rows and wy cells along columns; cells
+// outside the window count as clear.  t: scratch.
+void dilate_bits(Bits &f, int w, int wy, std::vector<uint64_t> &t)
+{
+    const int nw = f.nw;
+    const uint64_t tail = f.tail();
+    if (w > 0) {
+        t.resize((size_t)nw);
+        for (int j = 0; j < f.M; j++) {
+            uint64_t *r = f.row(j);
+            for (int pass = 0; pass < w; pass += 63) {  // shifts of at most 63 per pass
+                const int ws = std::min(63, w - pass);
+                std::copy(r, r + nw, t.begin());
+                for (int sft = 1; sft <= ws; sft++)
+                    for (int k = 0; k < nw; k++) {
+                        uint64_t up = (t[k] << sft) | (k > 0 ? t[k - 1] >> (64 - sft) : 0);
+                        uint64_t dn = (t[k] >> sft) | (k + 1 < nw ? t[k + 1] << (64 - sft) : 0);
+                        r[k] |= up | dn;
+                    }
+                r[nw - 1] &= tail;
+            }
+        }
+    }
+    if (wy > 0) {
+        t.assign(f.w.begin(), f.w.end());
+        for (int j = 0; j < f.M; j++) {
+            uint64_t *r = f.row(j);
+            for (int d = 1; d <= wy; d++) {
+                if (j - d >= 0) {
+                    const uint64_t *q = &t[(size_t)(j - d) * nw];
+                    for (int k = 0; k < nw; k++) r[k] |= q[k];
+                }
+                if (j + d < f.M) {
+                    const uint64_t *q = &t[(size_t)(j + d) * nw];
+                    for (int k = 0; k < nw; k++) r[k] |= q[k];
+                }
+            }
+        }
+    }
+}
+
+// 64x64 bit-matrix transpose in place: bit c of a[r] <-> bit r of a[c]
+// (swaps of the off-diagonal blocks of width 32, 16, ..., 1)
+void transpose64(uint64_t *a)
+{
+    uint64_t m = 0x00000000FFFFFFFFull;
+    for (int j = 32; j != 0; j >>= 1, m ^= (m << j)) {
+        for (int k = 0; k < 64; k = (k + j + 1) & ~j) {
+            uint64_t t = ((a[k] >> j) ^ a[k + j]) & m;
+            a[k + j] ^= t;
+            a[k] ^= t << j;
+        }
+    }
+}
+
+// T = transpose of f (T.N = f.M, T.M = f.N)
+void transpose_bits(const Bits &f, Bits &T)
+{
+    T.reset(f.M, f.N);
+    uint64_t blk[64];
+    const int nbj = (f.M + 63) >> 6;
+    for (int bj = 0; bj < nbj; bj++)
+        for (int bi = 0; bi < f.nw; bi++) {
+            for (int r = 0; r < 64; r++) {
+                int j = bj * 64 + r;
+                blk[r] = (j < f.M) ? f.row(j)[bi] : 0;
+            }
+            transpose64(blk);
+            for (int c = 0; c < 64; c++) {
+                int i = bi * 64 + c;
+                if (i < f.N) T.row(i)[bj] = blk[c];
+            }
+        }
+}
+
+// Berger-Rigoutsos clustering (Sec. 3, regridding) on a flag bitmap with the
+// non-nestable cells marked in U; row and column signatures of a box are bit
+// counts of the bitmap and of its transpose.
 struct Clusterer {
     int N, M, dim, mc;
     double eff;
-    std::vector<long long> SF, SB;  // integral images of flags and of non-nestable cells
+    const Bits *F = nullptr, *U = nullptr;
+    Bits T;                         // transpose of *F
     std::vector<Box> out;
     std::vector<long long> cs, rs;  // signature scratch (split() is not recursive)
     std::vector<Box> stack;
 
-    long long sum(const std::vector<long long> &S, int i0, int i1, int j0, int j1) const
+    void init(const Bits &flags, const Bits &unnest)
     {
-        // inclusive box, (N+1)-pitch integral image
-        long long W = N + 1;
-        return S[(long long)(j1 + 1) * W + (i1 + 1)] - S[(long long)j0 * W + (i1 + 1)] -
-               S[(long long)(j1 + 1) * W + i0] + S[(long long)j0 * W + i0];
-    }
-
-    void init(const std::vector<unsigned char> &flags, const std::vector<unsigned char> &nest)
-    {
-        long long W = N + 1;
-        SF.assign((size_t)(M + 1) * W, 0);
-        SB.assign((size_t)(M + 1) * W, 0);
-        for (int j = 0; j < M; j++) {
-            long long rf = 0, rb = 0;
-            for (int i = 0; i < N; i++) {
-                rf += flags[(size_t)j * N + i];
-                rb += nest[(size_t)j * N + i] ? 0 : 1;
-                SF[(size_t)(j + 1) * W + i + 1] = SF[(size_t)j * W + i + 1] + rf;
-                SB[(size_t)(j + 1) * W + i + 1] = SB[(size_t)j * W + i + 1] + rb;
-            }
-        }
+        F = &flags;
+        U = &unnest;
+        transpose_bits(flags, T);
     }
 
     void run(Box b)
@@ -469,11 +588,12 @@ struct Clusterer {
     // accepted (pushed to out) or holds no flag
     bool split(Box x, Box &L, Box &R)
     {
-        if (sum(SF, x.i0, x.i1, x.j0, x.j1) == 0) return false;
-        cs.resize(x.i1 - x.i0 + 1);
         rs.resize(x.j1 - x.j0 + 1);
-        for (int i = x.i0; i <= x.i1; i++) cs[i - x.i0] = sum(SF, i, i, x.j0, x.j1);
-        for (int j = x.j0; j <= x.j1; j++) rs[j - x.j0] = sum(SF, x.i0, x.i1, j, j);
+        long long tot = 0;
+        for (int j = x.j0; j <= x.j1; j++) tot += (rs[j - x.j0] = row_count(F->row(j), x.i0, x.i1));
+        if (tot == 0) return false;
+        cs.resize(x.i1 - x.i0 + 1);
+        for (int i = x.i0; i <= x.i1; i++) cs[i - x.i0] = row_count(T.row(i), x.j0, x.j1);
         int a = 0, bb = (int)cs.size() - 1, c0 = 0, c1 = (int)rs.size() - 1;
         while (cs[a] == 0) a++;
         while (cs[bb] == 0) bb--;
@@ -486,7 +606,8 @@ struct Clusterer {
         for (int k = 0; k <= bb - a; k++) nf += sxp[k];
         int lx = b.i1 - b.i0 + 1, ly = b.j1 - b.j0 + 1;
         long long area = (long long)lx * ly;
-        bool nestable = sum(SB, b.i0, b.i1, b.j0, b.j1) == 0;
+        bool nestable = true;
+        for (int j = b.j0; j <= b.j1 && nestable; j++) nestable = !row_any(U->row(j), b.i0, b.i1);
         if (nestable && (double)nf / (double)area >= eff) {
             out.push_back(b);
             return false;
@@ -552,39 +673,7 @@ struct Clusterer {
 
 // separable Chebyshev dilation of a 0/1 field [M][N] by w cells in x and wy
 // in y, in place, with sliding window counts (t and cnt are scratch)
-void dilate(std::vector<unsigned char> &f, int N, int M, int w, int wy, std::vector<unsigned char> &t,
-            std::vector<int> &cnt)
-{
-    t.resize(f.size());
-    for (int j = 0; j < M; j++) {
-        const unsigned char *row = &f[(size_t)j * N];
-        unsigned char *out = &t[(size_t)j * N];
-        int c = 0;
-        for (int i = 0; i <= std::min(w, N - 1); i++) c += row[i];
-        for (int i = 0; i < N; i++) {
-            out[i] = c > 0;
-            if (i + w + 1 < N) c += row[i + w + 1];
-            if (i - w >= 0) c -= row[i - w];
-        }
-    }
-    if (wy == 0) {
-        f.swap(t);
-        return;
-    }
-    cnt.assign((size_t)N, 0);
-    for (int j = 0; j <= std::min(wy, M - 1); j++)
-        for (int i = 0; i < N; i++) cnt[i] += t[(size_t)j * N + i];
-    for (int j = 0; j < M; j++) {
-        unsigned char *out = &f[(size_t)j * N];
-        for (int i = 0; i < N; i++) out[i] = cnt[i] > 0;
-        if (j + wy + 1 < M)
-            for (int i = 0; i < N; i++) cnt[i] += t[(size_t)(j + wy + 1) * N + i];
-        if (j - wy >= 0)
-            for (int i = 0; i < N; i++) cnt[i] -= t[(size_t)(j - wy) * N + i];
-    }
-}
-
-adjamr_status flag_dense(adjamr_ctx *c, int l, double tol, unsigned char *d_dense, unsigned char *d_patchflags,
+adjamr_status flag_dense(adjamr_ctx *c, int l, double tol, uint64_t *d_bits, int pitch64, unsigned char *d_patchflags,
                          long long *nflag_out, int *bbox_out = nullptr);
 
 // Rebuild levels base+1 .. nlevels-1 top-down (Sec. 3, regridding).
@@ -614,68 +703,79 @@ adjamr_status regrid_body(adjamr_ctx *c, int base, int init)
         Level &F = c->L[lev + 1];
         const int r = P.ratio[lev], N = C.N, M = C.M, dim = P.dim;
         const long long tick = C.nstep * c->T[lev];
-        // ---- adjoint flags of level lev on its index space (device) ----
-        size_t nb = ((size_t)N * M + 255) / 256 * 256;  // padded: the dense flag kernel ORs whole words
+        // ---- adjoint flags of level lev on its index space (device bitmap) ----
+        const int pitch64 = (N + 63) >> 6;
+        size_t nb = (size_t)pitch64 * M * sizeof(uint64_t);
         if (c->flagbuf_bytes < nb) {
             dfree(c->d_flagbuf, c->s);
-            CKR(c, dalloc(&c->d_flagbuf, nb, c->s));
+            CKR(c, dalloc(&c->d_flagbuf, nb / sizeof(uint64_t), c->s));
             c->flagbuf_bytes = nb;
         }
         CKR(c, cudaMemsetAsync(c->d_flagbuf, 0, nb, c->s));
         long long nf = 0;
         int bb[4];
         auto tp = std::chrono::steady_clock::now();
-        TRY(flag_dense(c, lev, P.tol, c->d_flagbuf, nullptr, &nf, bb));
+        TRY(flag_dense(c, lev, P.tol, c->d_flagbuf, pitch64, nullptr, &nf, bb));
         c->st.regrid_phase_ms[0] += ms_since(tp);
         harvest_timing(c);
         auto tc = std::chrono::steady_clock::now();
         std::vector<Box> fin;
         if (nf > 0) {
             // Window = bounding box of the flags grown by the buffer and the
-            // nesting distance, clipped to the domain.  Clustering starts by
-            // shrinking to the flags' bounding box, so the window gives the
-            // same boxes as the whole index space.
+            // nesting distance, clipped to the domain, its first column on a
+            // word boundary.  Clustering starts by shrinking to the flags'
+            // bounding box, so any such window gives the same boxes as the
+            // whole index space.
             const int grow = P.buffer + 2;
-            const int wi0 = std::max(0, bb[0] - grow), wi1 = std::min(N - 1, bb[1] + grow);
+            const int wi0 = std::max(0, bb[0] - grow) & ~63, wi1 = std::min(N - 1, bb[1] + grow);
             const int wj0 = (dim == 2) ? std::max(0, bb[2] - grow) : 0;
             const int wj1 = (dim == 2) ? std::min(M - 1, bb[3] + grow) : 0;
-            const int wN = wi1 - wi0 + 1, wM = wj1 - wj0 + 1;
-            const size_t wn = (size_t)wN * wM;
-            std::vector<unsigned char> &fl = c->h_fl, &unc = c->h_unc, &nest = c->h_nest;
-            fl.resize(wn);
-            unc.assign(wn, 1);
-            nest.resize(wn);
+            const int k0 = wi0 >> 6, nwords = (wi1 >> 6) - k0 + 1;
+            const int wN = std::min(N - wi0, 64 * nwords), wM = wj1 - wj0 + 1;
+            Bits &fl = c->h_fl, &unc = c->h_unc;
+            fl.reset(wN, wM);
             tp = std::chrono::steady_clock::now();
-            CKR(c, cudaMemcpy2DAsync(fl.data(), (size_t)wN, c->d_flagbuf + (size_t)wj0 * N + wi0, (size_t)N, (size_t)wN,
-                                     (size_t)wM, cudaMemcpyDeviceToHost, c->s));
+            CKR(c, cudaMemcpy2DAsync(fl.w.data(), (size_t)fl.nw * sizeof(uint64_t),
+                                     c->d_flagbuf + (size_t)wj0 * pitch64 + k0, (size_t)pitch64 * sizeof(uint64_t),
+                                     (size_t)fl.nw * sizeof(uint64_t), (size_t)wM, cudaMemcpyDeviceToHost, c->s));
             CKR(c, cudaStreamSynchronize(c->s));
             double wcopy = ms_since(tp);
             c->st.regrid_phase_ms[1] += wcopy;
             c->st.cluster_host_ms -= wcopy;
+            auto ts = std::chrono::steady_clock::now();
             // buffer, nesting mask (every cell within 2 cells covered by this level)
-            dilate(fl, wN, wM, P.buffer, dim == 2 ? P.buffer : 0, c->h_tmp, c->h_cnt);
+            dilate_bits(fl, P.buffer, dim == 2 ? P.buffer : 0, c->h_tmp);
+            unc.reset(wN, wM);
+            for (int j = 0; j < wM; j++) {
+                uint64_t *r = unc.row(j);
+                std::fill(r, r + unc.nw, ~0ull);
+                r[unc.nw - 1] &= unc.tail();
+            }
             for (const HPatch &p : C.patches) {
-                int a0 = std::max(p.ilo, wi0), a1 = std::min(p.ilo + p.nx - 1, wi1);
+                int a0 = std::max(p.ilo, wi0), a1 = std::min(p.ilo + p.nx - 1, wi0 + wN - 1);
                 int b0 = std::max(p.jlo, wj0), b1 = std::min(p.jlo + p.ny - 1, wj1);
                 if (a0 > a1 || b0 > b1) continue;
-                for (int j = b0; j <= b1; j++) std::memset(&unc[(size_t)(j - wj0) * wN + (a0 - wi0)], 0, (size_t)(a1 - a0 + 1));
+                for (int j = b0; j <= b1; j++) row_clear(unc.row(j - wj0), a0 - wi0, a1 - wi0);
             }
             // cells beyond the window but inside the domain: the window reaches
             // 2 cells past every flag the buffer can create, so they never
             // decide a flagged cell's nesting
-            dilate(unc, wN, wM, 2, dim == 2 ? 2 : 0, c->h_tmp, c->h_cnt);
-            for (size_t k = 0; k < wn; k++) {
-                nest[k] = !unc[k];
-                if (!nest[k]) fl[k] = 0;
-            }
+            dilate_bits(unc, 2, dim == 2 ? 2 : 0, c->h_tmp);
+            for (size_t k = 0; k < fl.w.size(); k++) fl.w[k] &= ~unc.w[k];
+            c->st.cluster_phase_ms[0] += ms_since(ts);
+            ts = std::chrono::steady_clock::now();
             static thread_local Clusterer cl;  // reused scratch (one context per host thread)
             cl.N = wN;
             cl.M = wM;
             cl.dim = dim;
             cl.mc = (P.min_patch + r - 1) / r;
             cl.eff = P.cluster_eff;
-            cl.init(fl, nest);
+            cl.init(fl, unc);
+            c->st.cluster_phase_ms[1] += ms_since(ts);
+            ts = std::chrono::steady_clock::now();
             cl.run(Box{0, wN - 1, 0, wM - 1});
+            c->st.cluster_phase_ms[2] += ms_since(ts);
+            ts = std::chrono::steady_clock::now();
             for (Box b : cl.out) {
                 b.i0 += wi0;
                 b.i1 += wi0;
@@ -699,6 +799,7 @@ adjamr_status regrid_body(adjamr_ctx *c, int base, int init)
             std::sort(fin.begin(), fin.end(), [](const Box &a, const Box &b) {
                 return a.j0 != b.j0 ? a.j0 < b.j0 : a.i0 < b.i0;
             });
+            c->st.cluster_phase_ms[3] += ms_since(ts);
         }
         c->st.cluster_host_ms += ms_since(tc);
         c->st.regrid_phase_ms[2] = c->st.cluster_host_ms;
@@ -771,7 +872,7 @@ adjamr_status regrid_body(adjamr_ctx *c, int base, int init)
     return ADJAMR_OK;
 }
 
-constexpr int kFlagBlocksPerThread = 4;
+constexpr int kFlagBlocksPerThread = 1;
 
 // Per-column and per-row bilinear tables of the attached adjoint grid for
 // level l (the same arithmetic as the flag kernel's per-cell setup: cell
@@ -824,7 +925,7 @@ adjamr_status flag_tables(adjamr_ctx *c, int l)
     return ADJAMR_OK;
 }
 
-adjamr_status flag_dense(adjamr_ctx *c, int l, double tol, unsigned char *d_dense, unsigned char *d_patchflags,
+adjamr_status flag_dense(adjamr_ctx *c, int l, double tol, uint64_t *d_bits, int pitch64, unsigned char *d_patchflags,
                          long long *nflag_out, int *bbox_out)
 {
     Level &L = c->L[l];
@@ -846,7 +947,8 @@ adjamr_status flag_dense(adjamr_ctx *c, int l, double tol, unsigned char *d_dens
     a.dx = L.dx; a.dy = L.dy;
     a.tol = tol;
     a.flags_patch = d_patchflags;
-    a.flags_dense = d_dense;
+    a.flags_bits = reinterpret_cast<unsigned long long *>(d_bits);
+    a.pitch64 = pitch64;
     a.N = L.N;
     a.count = c->d_count;
     double t = P.t0 + (double)L.nstep * L.dt;
@@ -880,7 +982,7 @@ adjamr_status flag_dense(adjamr_ctx *c, int l, double tol, unsigned char *d_dens
     CKR(c, cudaMemcpyAsync(c->d_bbox, bbox_init, sizeof bbox_init, cudaMemcpyHostToDevice, c->s));
     // regrid flags (dense only, bracket max, block maxima present): one thread
     // per (cell, group of snapshot blocks) over the level's index space
-    const bool dense = d_dense && !d_patchflags && P.flag_mode == ADJAMR_FLAG_BRACKET_MAX && c->adj &&
+    const bool dense = d_bits && !d_patchflags && P.flag_mode == ADJAMR_FLAG_BRACKET_MAX && c->adj &&
                        c->adj->d_bmax && a.S >= 2;
     if (dense) {
         TRY(flag_tables(c, l));
@@ -1567,7 +1669,7 @@ adjamr_status adjamr_flag_cells(adjamr_ctx *ctx, int level, double tol, unsigned
         unsigned char *d = nullptr;
         CKR(ctx, dalloc(&d, (size_t)std::max<long long>(L.ninterior, 1), ctx->s));
         long long n = 0;
-        adjamr_status st = flag_dense(ctx, level, tol, nullptr, d, &n);
+        adjamr_status st = flag_dense(ctx, level, tol, nullptr, 0, d, &n);
         if (st == ADJAMR_OK && flags_out && L.ninterior > 0) {
             CKR(ctx, cudaMemcpyAsync(flags_out, d, (size_t)L.ninterior, cudaMemcpyDeviceToHost, ctx->s));
             CKR(ctx, cudaStreamSynchronize(ctx->s));

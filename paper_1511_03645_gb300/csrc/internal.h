@@ -137,7 +137,8 @@ struct FlagArgs {
     int ax, ay, nlo, nhi, S;
     double t, T, t0, dts, tol;
     unsigned char *flags_patch;     // [ncells] (may be null)
-    unsigned char *flags_dense;     // [M][N] of the level (may be null)
+    unsigned long long *flags_bits; // [M][pitch64]: bit I & 63 of word I >> 6 of row J (may be null; zeroed)
+    int pitch64;
     int N;
     unsigned long long *count;
     int *bbox;                      // [4]: min I, max I, min J, max J of flagged cells (atomics)
@@ -158,7 +159,7 @@ cudaError_t launch_block_max(const double *snaps, int S, int m, int ax, int ay, 
                              cudaStream_t s);
 cudaError_t launch_flag(const FlagArgs &a, cudaStream_t s);
 // bracket-max flags over the level's index space, one thread per (cell, group
-// of a.gblk snapshot blocks); flags_dense (4-byte padded) must start zeroed
+// of a.gblk snapshot blocks), into the zeroed bitmap a.flags_bits
 cudaError_t launch_flag_dense(const FlagArgs &a, int ngroup, cudaStream_t s);
 
 // terms weight*(q0*area) of the functional into out[0..n)

@@ -473,7 +473,7 @@ __global__ void k_flag(FlagArgs A)
         }
         flagged = hit;
         if (A.flags_patch) A.flags_patch[t] = flagged ? 1 : 0;
-        if (A.flags_dense) A.flags_dense[(long long)J * A.N + I] = flagged ? 1 : 0;
+        if (A.flags_bits && flagged) atomicOr(A.flags_bits + (long long)J * A.pitch64 + (I >> 6), 1ull << (I & 63));
         if (flagged) {
             fI = gI = I;
             fJ = gJ = J;
@@ -504,6 +504,7 @@ __global__ void k_flag(FlagArgs A)
 // among threads); blocks whose bound cannot exceed tol are skipped as in
 // k_flag.  The first thread to set a cell's flag counts it; warp shuffles
 // reduce the count and the bounding box of the flags.
+template <int MF>
 __global__ void k_flag_dense(FlagArgs A)
 {
     const long long NM = (long long)A.N * A.M;
@@ -520,36 +521,44 @@ __global__ void k_flag_dense(FlagArgs A)
             if (A.S < 2 || dry || A.nlo > A.nhi) {
                 hit = (grp == 0) && (0.0 > A.tol);
             } else {
-                double Q[3];
-                for (int f = 0; f < A.m; f++) Q[f] = A.q[(long long)f * A.stride + o];
+                double Q[MF];
+#pragma unroll
+                for (int f = 0; f < MF; f++) Q[f] = A.q[(long long)f * A.stride + o];
                 const int a = A.tab_a[I], b = (A.dim == 2) ? A.tab_b[J] : 0;
                 const double wx = A.tab_wx[I], wy = (A.dim == 2) ? A.tab_wy[J] : 0.0;
                 const long long plane = (long long)A.ax * A.ay;
                 const long long acell = (long long)b * A.ax + a;
-                const volatile unsigned char *done = A.flags_dense + cidx;
+                const volatile unsigned long long *done = A.flags_bits + (long long)J * A.pitch64 + (I >> 6);
+                const unsigned long long bit = 1ull << (I & 63);
                 const int blo = A.nlo / kSnapBlock + grp * A.gblk;
                 const int bhi = min(A.nhi / kSnapBlock, blo + A.gblk - 1);
                 for (int blk = blo; blk <= bhi && !hit; blk++) {
-                    if (*done) break;  // set by another group: nothing left to decide
+                    if (*done & bit) break;  // set by another group: nothing left to decide
                     double B = 0.0;
-                    for (int f = 0; f < A.m; f++)
-                        B = fma(fabs(Q[f]), A.bmax[((long long)blk * A.m + f) * plane + acell], B);
+#pragma unroll
+                    for (int f = 0; f < MF; f++)
+                        B = fma(fabs(Q[f]), A.bmax[((long long)blk * MF + f) * plane + acell], B);
                     if (B * (1.0 + 1e-12) <= A.tol) continue;
-                    const int n0 = max(A.nlo, blk * kSnapBlock), n1 = min(A.nhi, blk * kSnapBlock + kSnapBlock - 1);
-                    for (int n = n0; n <= n1 && !hit; n++) {
+                    // the block's snapshots without an early exit, so that their
+                    // loads are in flight together
+                    const int n0 = blk * kSnapBlock;
+#pragma unroll
+                    for (int k = 0; k < kSnapBlock; k++) {
+                        const int n = n0 + k;
+                        if (n < A.nlo || n > A.nhi) continue;
                         double d = 0.0;
-                        for (int f = 0; f < A.m; f++) {
+#pragma unroll
+                        for (int f = 0; f < MF; f++) {
                             double av = adj_interp(A, n, f, a, wx, b, wy);
                             d = (f == 0) ? av * Q[0] : d + av * Q[f];
                         }
-                        hit = fabs(d) > A.tol;
+                        hit = hit || fabs(d) > A.tol;
                     }
                 }
             }
             if (hit) {
-                unsigned int *word = reinterpret_cast<unsigned int *>(A.flags_dense + (cidx & ~3LL));
-                const unsigned int bit = 1u << (8 * (int)(cidx & 3));
-                fresh = (atomicOr(word, bit) & bit) == 0;
+                const unsigned long long bit = 1ull << (I & 63);
+                fresh = (atomicOr(A.flags_bits + (long long)J * A.pitch64 + (I >> 6), bit) & bit) == 0;
                 fI = gI = I;
                 fJ = gJ = J;
             }
@@ -722,7 +731,9 @@ cudaError_t launch_flag_dense(const FlagArgs &a, int ngroup, cudaStream_t s)
     const long long nm = (long long)a.N * a.M;
     if (nm <= 0 || ngroup <= 0) return cudaSuccess;
     dim3 grid((unsigned)((nm + kT - 1) / kT), (unsigned)ngroup);
-    k_flag_dense<<<grid, kT, 0, s>>>(a);
+    if (a.m == 3) k_flag_dense<3><<<grid, kT, 0, s>>>(a);
+    else if (a.m == 2) k_flag_dense<2><<<grid, kT, 0, s>>>(a);
+    else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 
