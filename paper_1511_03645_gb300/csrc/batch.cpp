@@ -59,8 +59,11 @@ cudaError_t build_work(adjamr_batch *b, int tx, int ty)
     b->h_work.clear();
     for (int k : b->order) {
         const BPatch &p = b->patches[k];
-        for (int y0 = 0; y0 < p.ny; y0 += ty)
-            for (int x0 = 0; x0 < p.nx; x0 += tx) b->h_work.push_back({k, x0, y0, 0});
+        const int nx = tile_count(p.nx, tx), ny = tile_count(p.ny, ty);
+        for (int j = 0; j < ny; j++)
+            for (int i = 0; i < nx; i++)
+                b->h_work.push_back({k, tile_off(p.nx, nx, i), tile_off(p.ny, ny, j),
+                                     (unsigned short)tile_len(p.nx, nx, i), (unsigned short)tile_len(p.ny, ny, j)});
     }
     b->nwork = (int)b->h_work.size();
     cudaError_t e = cudaMallocAsync((void **)&b->d_work, sizeof(WorkItem) * b->h_work.size(), b->s);

@@ -242,13 +242,21 @@ adjamr_status build_work(adjamr_ctx *c, int l, int tx, int ty)
     if (L.work_tx == tx && L.work_ty == ty && L.d_work) return ADJAMR_OK;
     dfree(L.d_work, c->s);
     L.h_work.clear();
-    int txx = (c->P.dim == 1) ? tx : tx;
+    const int tyy = (c->P.dim == 2) ? ty : 1;
     for (int k = 0; k < (int)L.patches.size(); k++) {
         const HPatch &p = L.patches[k];
-        int tyy = (c->P.dim == 2) ? ty : 1;
-        for (int y0 = 0; y0 < p.ny; y0 += tyy)
-            for (int x0 = 0; x0 < p.nx; x0 += txx) L.h_work.push_back({k, x0, y0, 0});
+        const int nx = tile_count(p.nx, tx), ny = tile_count(p.ny, tyy);
+        for (int b = 0; b < ny; b++)
+            for (int a = 0; a < nx; a++)
+                L.h_work.push_back({k, tile_off(p.nx, nx, a), tile_off(p.ny, ny, b),
+                                    (unsigned short)tile_len(p.nx, nx, a), (unsigned short)tile_len(p.ny, ny, b)});
     }
+    // one launch over the level: largest tiles first, so that the last CTAs
+    // to start are the short ones (one launch per patch keeps patch order)
+    if (c->launch_mode != ADJAMR_LAUNCH_PER_PATCH)
+        std::stable_sort(L.h_work.begin(), L.h_work.end(), [](const WorkItem &a, const WorkItem &b) {
+            return (int)a.tx * a.ty > (int)b.tx * b.ty;
+        });
     L.nwork = (int)L.h_work.size();
     CKR(c, upload(&L.d_work, L.h_work, c->s));
     L.work_tx = tx;

@@ -50,9 +50,20 @@ struct PatchDesc {
 };
 
 // One tile of the step work-list.
+// One tile of a patch: interior cells [x0, x0+tx) x [y0, y0+ty), tx <= TX and
+// ty <= TY of the kernel.  A patch is cut into near-equal tiles (extents
+// differ by at most one cell per direction) so that the tiles of a level
+// carry near-equal work.
 struct WorkItem {
-    int patch, x0, y0, pad;
+    int patch, x0, y0;
+    unsigned short tx, ty;
 };
+
+// near-equal split of len cells into ceil(len / t) pieces: piece k's offset
+// and length
+inline int tile_count(int len, int t) { return (len + t - 1) / t; }
+inline int tile_off(int len, int n, int k) { return k * (len / n) + (k < len % n ? k : len % n); }
+inline int tile_len(int len, int n, int k) { return len / n + (k < len % n ? 1 : 0); }
 
 // One ghost cell (or one new cell at regrid).
 //  kind 0: copy the cell `src` of the same arena (with sign flips);

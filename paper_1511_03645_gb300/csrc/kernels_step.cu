@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(kThreads) k_step2d(const double *__restrict__ 
         const WorkItem wi = work[w];
         const PatchDesc P = patches[wi.patch];
         const int x0 = wi.x0, y0 = wi.y0;
-        const int tx = min(TX, P.nx - x0), ty = min(TY, P.ny - y0);
+        const int tx = wi.tx, ty = wi.ty;
         const int rx = tx + 4, ry = ty + 4;
         const double dtdx = P.dtdx, dtdy = P.dtdy, hx = P.hx, hy = P.hy;
         // ---- stage state and coefficients (tile + 2-cell halo) ----
@@ -496,7 +496,7 @@ __global__ void __launch_bounds__(kThreads) k_step1d(const double *__restrict__ 
         const WorkItem wi = work[w];
         const PatchDesc P = patches[wi.patch];
         const int x0 = wi.x0;
-        const int tx = min(TX, P.nx - x0), rx = tx + 4;
+        const int tx = wi.tx, rx = tx + 4;
         const double dtdx = P.dtdx;
         const bool ring = ga.gd && (x0 < 2 || x0 + tx + 1 >= P.nx);  // staged [x0, x0+tx+4) meets the ring
         for (int k = tid; k < (2 + S::NA) * rx; k += kThreads) {
