@@ -43,6 +43,7 @@ struct Level {
     long long ncell = 0, ninterior = 0;
     double *q[2] = {nullptr, nullptr};
     double *aux = nullptr, *med = nullptr;
+    double *d_arena = nullptr;  // the one allocation q[0], q[1], aux and med point into
     PatchDesc *d_patches = nullptr;
     WorkItem *d_work = nullptr;
     int nwork = 0, work_tx = 0, work_ty = 0;
@@ -103,9 +104,12 @@ struct adjamr_ctx {
     std::vector<int> h_cnt;
     // pinned staging for descriptor uploads; reused once the event of the
     // previous copy has completed
-    char *h_stage = nullptr;
-    size_t h_stage_bytes = 0;
-    cudaEvent_t stage_ev = nullptr;
+    // pinned staging for descriptor uploads: two slots used in turn, each
+    // reusable once the copy recorded by its event has completed
+    char *h_stage[2] = {nullptr, nullptr};
+    size_t h_stage_bytes[2] = {0, 0};
+    cudaEvent_t stage_ev[2] = {nullptr, nullptr};
+    int stage_slot = 0;
     uint64_t *d_flagbuf = nullptr;  // flag bitmap of the level being regridded
     // per-level bilinear tables of the adjoint grid for the dense flag kernel
     char *d_ftab[ADJAMR_MAX_LEVELS] = {};
@@ -193,8 +197,9 @@ void build_buckets(Level &L)
     }
 }
 
-int find_patch(const Level &L, int I, int J)
+int find_patch(Level &L, int I, int J)
 {
+    if (L.buckets.empty() && !L.patches.empty()) build_buckets(L);
     if (I < 0 || J < 0 || I >= L.N || J >= L.M || L.buckets.empty()) return -1;
     const std::vector<int> &b = L.buckets[(size_t)(J / L.bs) * L.nbx + I / L.bs];
     for (int k : b) {
@@ -207,10 +212,9 @@ int find_patch(const Level &L, int I, int J)
 void free_level(adjamr_ctx *c, Level &L)
 {
     cudaStream_t s = c->s;
-    dfree(L.q[0], s);
-    dfree(L.q[1], s);
-    dfree(L.aux, s);
-    dfree(L.med, s);
+    dfree(L.d_arena, s);
+    L.q[0] = L.q[1] = nullptr;
+    L.aux = L.med = nullptr;
     if (L.d_meta) {
         dfree(L.d_meta, s);
         L.d_patches = nullptr;
@@ -236,6 +240,9 @@ void free_level(adjamr_ctx *c, Level &L)
 }
 
 // (re)build the tile work-list of a level for tile (tx, ty)
+cudaError_t upload_packed(adjamr_ctx *c, const std::vector<std::pair<const void *, size_t>> &chunks, char **dev,
+                          std::vector<size_t> &offs);
+
 adjamr_status build_work(adjamr_ctx *c, int l, int tx, int ty)
 {
     Level &L = c->L[l];
@@ -258,7 +265,10 @@ adjamr_status build_work(adjamr_ctx *c, int l, int tx, int ty)
             return (int)a.tx * a.ty > (int)b.tx * b.ty;
         });
     L.nwork = (int)L.h_work.size();
-    CKR(c, upload(&L.d_work, L.h_work, c->s));
+    std::vector<size_t> offs;
+    char *dw = nullptr;
+    CKR(c, upload_packed(c, {{L.h_work.data(), sizeof(WorkItem) * L.h_work.size()}}, &dw, offs));
+    L.d_work = reinterpret_cast<WorkItem *>(dw);
     L.work_tx = tx;
     L.work_ty = ty;
     return ADJAMR_OK;
@@ -277,32 +287,34 @@ cudaError_t upload_packed(adjamr_ctx *c, const std::vector<std::pair<const void 
     }
     *dev = nullptr;
     if (total == 0) return cudaSuccess;
+    const int sl = c->stage_slot;
+    c->stage_slot = 1 - sl;
     cudaError_t e;
-    if (c->stage_ev) {
-        e = cudaEventSynchronize(c->stage_ev);  // previous copy out of the staging buffer is done
+    if (c->stage_ev[sl]) {
+        e = cudaEventSynchronize(c->stage_ev[sl]);  // the slot's previous copy is done
         if (e != cudaSuccess) return e;
     } else {
-        e = cudaEventCreateWithFlags(&c->stage_ev, cudaEventDisableTiming);
+        e = cudaEventCreateWithFlags(&c->stage_ev[sl], cudaEventDisableTiming);
         if (e != cudaSuccess) return e;
     }
-    if (c->h_stage_bytes < total) {
-        if (c->h_stage) cudaFreeHost(c->h_stage);
-        c->h_stage = nullptr;
+    if (c->h_stage_bytes[sl] < total) {
+        if (c->h_stage[sl]) cudaFreeHost(c->h_stage[sl]);
+        c->h_stage[sl] = nullptr;
         size_t want = std::max(total, (size_t)1 << 20);
-        e = cudaMallocHost((void **)&c->h_stage, want);
+        e = cudaMallocHost((void **)&c->h_stage[sl], want);
         if (e != cudaSuccess) {
-            c->h_stage_bytes = 0;
+            c->h_stage_bytes[sl] = 0;
             return e;
         }
-        c->h_stage_bytes = want;
+        c->h_stage_bytes[sl] = want;
     }
     for (size_t k = 0; k < chunks.size(); k++)
-        if (chunks[k].second) std::memcpy(c->h_stage + offs[k], chunks[k].first, chunks[k].second);
+        if (chunks[k].second) std::memcpy(c->h_stage[sl] + offs[k], chunks[k].first, chunks[k].second);
     e = cudaMallocAsync((void **)dev, total, c->s);
     if (e != cudaSuccess) return e;
-    e = cudaMemcpyAsync(*dev, c->h_stage, total, cudaMemcpyHostToDevice, c->s);
+    e = cudaMemcpyAsync(*dev, c->h_stage[sl], total, cudaMemcpyHostToDevice, c->s);
     if (e != cudaSuccess) return e;
-    return cudaEventRecord(c->stage_ev, c->s);
+    return cudaEventRecord(c->stage_ev[sl], c->s);
 }
 
 LevelIdx idx_of(const adjamr_ctx *c, int l)
@@ -358,10 +370,12 @@ adjamr_status alloc_level(adjamr_ctx *c, int l, const std::vector<Box> &boxes)
     }
     // (no clearing: every ghost cell is written by the ghost fill before it is
     // read, every interior cell by the initialisation or the step)
-    CKR(c, dalloc(&L.q[0], (size_t)c->m * L.ncell, c->s));
-    CKR(c, dalloc(&L.q[1], (size_t)c->m * L.ncell, c->s));
-    CKR(c, dalloc(&L.aux, (size_t)c->naux * L.ncell, c->s));
-    CKR(c, dalloc(&L.med, (size_t)c->nmed * L.ncell, c->s));
+    // one allocation: q[0] | q[1] | aux | med
+    CKR(c, dalloc(&L.d_arena, (size_t)(2 * c->m + c->naux + c->nmed) * L.ncell, c->s));
+    L.q[0] = L.d_arena;
+    L.q[1] = L.d_arena ? L.q[0] + (size_t)c->m * L.ncell : nullptr;
+    L.aux = L.d_arena ? L.q[1] + (size_t)c->m * L.ncell : nullptr;
+    L.med = L.d_arena ? L.aux + (size_t)c->naux * L.ncell : nullptr;
     {
         std::vector<size_t> offs;
         const size_t pb = sizeof(long long) * prefix.size();
@@ -381,7 +395,7 @@ adjamr_status alloc_level(adjamr_ctx *c, int l, const std::vector<Box> &boxes)
                                  c->s));
         c->st.kernel_launches++;
     }
-    build_buckets(L);
+    L.buckets.clear();  // rebuilt on demand by the host lookups
     L.work_tx = L.work_ty = 0;
     return build_work(c, l, c->ltx[l], c->lty[l]);
 }
@@ -819,7 +833,8 @@ adjamr_status regrid_body(adjamr_ctx *c, int base, int init)
         std::swap(old.patches, F.patches);
         std::swap(old.buckets, F.buckets);
         old.N = F.N; old.M = F.M; old.bs = F.bs; old.nbx = F.nbx; old.nby = F.nby;
-        old.q[0] = F.q[0]; old.q[1] = F.q[1]; old.ncell = F.ncell; old.cur = F.cur;
+        old.q[0] = F.q[0]; old.q[1] = F.q[1]; old.ncell = F.ncell; old.cur = F.cur; old.d_arena = F.d_arena;
+        F.d_arena = nullptr;
         old.aux = F.aux; old.med = F.med; old.d_patches = F.d_patches; old.d_work = F.d_work;
         old.d_ghost = F.d_ghost; old.d_avg = F.d_avg; old.d_prefix = F.d_prefix;
         old.d_gprefix = F.d_gprefix; old.d_sprefix = F.d_sprefix; old.d_aprefix = F.d_aprefix; old.d_owner = F.d_owner;
@@ -1702,7 +1717,7 @@ adjamr_status adjamr_integrate_functional(adjamr_ctx *ctx, const adjamr_target *
             const Level &L = ctx->L[l];
             if (L.patches.empty()) break;
             int r = (l < P.nlevels - 1) ? P.ratio[l] : 1;
-            const Level *F = (l < P.nlevels - 1 && !ctx->L[l + 1].patches.empty()) ? &ctx->L[l + 1] : nullptr;
+            Level *F = (l < P.nlevels - 1 && !ctx->L[l + 1].patches.empty()) ? &ctx->L[l + 1] : nullptr;
             for (const HPatch &p : L.patches)
                 for (int j = 0; j < p.ny; j++)
                     for (int i = 0; i < p.nx; i++) {
@@ -1909,8 +1924,10 @@ void adjamr_destroy(adjamr_ctx *ctx)
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     for (cudaEvent_t e : ctx->tev) cudaEventDestroy(e);
-    if (ctx->stage_ev) cudaEventDestroy(ctx->stage_ev);
-    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+    for (int k = 0; k < 2; k++) {
+        if (ctx->stage_ev[k]) cudaEventDestroy(ctx->stage_ev[k]);
+        if (ctx->h_stage[k]) cudaFreeHost(ctx->h_stage[k]);
+    }
     if (ctx->adj) adjamr_adjoint_release(ctx->adj);
     delete ctx;
 }
