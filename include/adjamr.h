@@ -55,10 +55,15 @@ enum {
 /* Physical boundary conditions (Sec. 5.1-5.2 walls; Sec. 5.2.3 outflow). */
 enum { ADJAMR_BC_EXTRAP = 0, ADJAMR_BC_WALL = 1, ADJAMR_BC_PERIODIC = 2 };
 
-/* Time combination of adjoint snapshots in the flag test (Sec. 4 "both
- * taken into account"): maximum over the bracketing snapshots, or q^
- * linear in time between snapshots. */
-enum { ADJAMR_FLAG_BRACKET_MAX = 0, ADJAMR_FLAG_LINEAR = 1 };
+/* Flag test.  Adjoint flagging (Sec. 4), with the time combination of the
+ * adjoint snapshots ("both taken into account"): maximum over the bracketing
+ * snapshots, or q^ linear in time between snapshots.  The standard flaggers
+ * the paper compares against: DIFFERENCE flags a cell when the undivided
+ * centred difference |q_f(i+1) - q_f(i-1)| of some component in some
+ * direction exceeds tol (Sec. 5.2.4, "pressure-flagging"; neighbours from the
+ * level's ghost cells at the current time); SURFACE when |q_0| exceeds tol
+ * (Sec. 5.3, "surface-flagging").  The standard flaggers need no adjoint. */
+enum { ADJAMR_FLAG_BRACKET_MAX = 0, ADJAMR_FLAG_LINEAR = 1, ADJAMR_FLAG_DIFFERENCE = 2, ADJAMR_FLAG_SURFACE = 3 };
 
 enum { ADJAMR_MEDIUM_LAYERED = 1, ADJAMR_MEDIUM_DENSE = 2 };
 
@@ -246,6 +251,17 @@ adjamr_status adjamr_set_timing(adjamr_ctx *ctx, int enable);
  * small tiles).  2D tiles: 32x8, 16x8, 16x16, 32x16, 64x8, 8x8; 1D: 256 or
  * 128 (tile_y ignored).  Errors: EINVAL for another shape or level. */
 adjamr_status adjamr_set_level_kernel(adjamr_ctx *ctx, int level, int tile_x, int tile_y, int fuse_ghosts);
+/* Gauges (time series at points, Sec. 5.2.4 and Sec. 5.3): n points (x[k],
+ * y[k]; y is ignored in 1D) recorded on the device after every level-0 step
+ * of adjamr_advance_level: the level-0 time, then the m values of the cell
+ * holding the point (index floor((x - lo)/dx), clamped to the level) on the
+ * finest level with a patch there.  Replaces earlier gauges and drops their
+ * records.  Errors: EINVAL (n < 0, or null points with n > 0), ENOMEM. */
+adjamr_status adjamr_set_gauges(adjamr_ctx *ctx, int n, const double *x, const double *y);
+/* Gauge records so far: out[r][k][1 + m] for r < min(*nrec, cap) (out may be
+ * null with cap = 0); *nrec = number of records held.  Synchronises the
+ * context's stream. */
+adjamr_status adjamr_read_gauges(adjamr_ctx *ctx, double *out, long long cap, long long *nrec);
 /* Level-0 step and number of level-0 steps to reach tf. */
 adjamr_status adjamr_time_info(adjamr_ctx *ctx, double *dt0, int *nsteps_to_tf);
 const char *adjamr_last_error(adjamr_ctx *ctx);

@@ -32,6 +32,9 @@
  *    intervals, bilinear interpolation in space, both bracketing snapshots
  *    in time; Sec. 5.1.2: maximum over the time window of interest.
  *  - Sec. 2, Eq. (eq:J_general): the functional J.
+ *  - Sec. 5.2.4 and Sec. 5.3: the standard flagging the paper compares
+ *    against (undivided differences of every component; surface elevation)
+ *    and gauges (time series at points, finest level covering the point).
  */
 #include <math.h>
 #include <stdint.h>
@@ -44,7 +47,7 @@
 
 enum { O_ACOU = 0, O_ACOU_ADJ = 1, O_SW = 2, O_SW_ADJ = 3 };
 enum { O_EXTRAP = 0, O_WALL = 1, O_PERIODIC = 2 };
-enum { O_BRACKET = 0, O_LINEAR = 1 };
+enum { O_BRACKET = 0, O_LINEAR = 1, O_DIFF = 2, O_SURFACE = 3 };
 enum { O_MED_NONE = 0, O_MED_LAYERED = 1, O_MED_DENSE = 2 };
 
 typedef void (*orc_qinit_fn)(int level, int n, const double *xc, const double *yc, double *q_out, void *user);
@@ -100,6 +103,12 @@ typedef struct {
     double *snaps;
     unsigned char *wet;
     long long cell_updates;
+    /* gauges: points recorded after every level-0 step, grec[n][g][1 + m] =
+       (t, q of the cell holding the point on the finest level covering it) */
+    int ngauge;
+    double *gxs, *gys;
+    long ngrec, gcap;
+    double *grec;
     char err[256];
 } OHier;
 
@@ -678,6 +687,9 @@ void orc_destroy(void *hv)
     }
     free(h->snaps);
     free(h->wet);
+    free(h->gxs);
+    free(h->gys);
+    free(h->grec);
     free(h);
 }
 
@@ -828,6 +840,12 @@ static int fill_ghosts(OHier *h, int l, int k)
             }
     }
     return 0;
+}
+
+/* substep of level l within the current step of level l-1 (0 on level 0) */
+static int level_sub(const OHier *h, int l)
+{
+    return l > 0 ? (int)(h->L[l].nstep - h->L[l - 1].nstep * h->P.ratio[l - 1]) : 0;
 }
 
 /* fine -> coarse: mean of the r^d children, summed row by row */
@@ -992,7 +1010,18 @@ static long flag_level(OHier *h, int l, double tol, unsigned char *flags)
                 double Q[3];
                 for (int f = 0; f < h->m; f++) Q[f] = p->q[L->cur][qidx(h, p, f, i, j)];
                 double val = 0.0;
-                if (S >= 2 && h->snaps) {
+                if (h->P.flag_mode == O_DIFF) {
+                    /* undivided centred difference of every component in
+                       every direction, from the ghost-filled patch */
+                    const double *qq = p->q[L->cur];
+                    for (int f = 0; f < h->m; f++) {
+                        val = fmax(val, fabs(qq[qidx(h, p, f, i + 1, j)] - qq[qidx(h, p, f, i - 1, j)]));
+                        if (h->P.dim == 2)
+                            val = fmax(val, fabs(qq[qidx(h, p, f, i, j + 1)] - qq[qidx(h, p, f, i, j - 1)]));
+                    }
+                } else if (h->P.flag_mode == O_SURFACE) {
+                    val = fabs(Q[0]);  /* perturbation of the surface (first component) */
+                } else if (S >= 2 && h->snaps) {
                     if (h->P.flag_mode == O_BRACKET) {
                         for (int n = nlo; n <= nhi; n++) val = fmax(val, adj_dot_snap(h, n, x, y, Q));
                     } else {
@@ -1016,6 +1045,7 @@ int orc_flag(void *hv, int level, double tol, unsigned char *flags, long *nflag)
 {
     OHier *h = hv;
     if (level < 0 || level >= h->P.nlevels) return 1;
+    if (h->P.flag_mode == O_DIFF && fill_ghosts(h, level, level_sub(h, level))) return 1;
     long c = flag_level(h, level, tol, flags);
     if (nflag) *nflag = c;
     return 0;
@@ -1207,6 +1237,10 @@ static int regrid_from(OHier *h, int l, int init)
         long ncell = 0;
         for (int k = 0; k < C->np; k++) ncell += (long)C->p[k].nx * C->p[k].ny;
         unsigned char *pf = xcalloc(ncell, 1);
+        if (h->P.flag_mode == O_DIFF && fill_ghosts(h, lev, level_sub(h, lev))) {
+            free(pf);
+            return 1;
+        }
         flag_level(h, lev, h->P.tol, pf);
         unsigned char *fl = xcalloc((size_t)N * M, 1);
         unsigned char *cov = xcalloc((size_t)N * M, 1);
@@ -1349,12 +1383,80 @@ static int step_level(OHier *h, int l, double *cflmax)
 
 /* advance the hierarchy by nsteps coarse steps; returns 0, or 1 on error,
    or 2 if the CFL number exceeded cfl_max */
+/* gauge record at the current level-0 time: for every gauge, the cell that
+   holds the point on the finest level covering it (cell index floor((x -
+   lo)/dx), clamped to the level) */
+static void record_gauges(OHier *h)
+{
+    if (h->ngauge == 0) return;
+    const int w = 1 + h->m;
+    if (h->ngrec == h->gcap) {
+        h->gcap = h->gcap ? 2 * h->gcap : 64;
+        h->grec = realloc(h->grec, (size_t)h->gcap * h->ngauge * w * sizeof(double));
+    }
+    double *rec = h->grec + (size_t)h->ngrec * h->ngauge * w;
+    for (int g = 0; g < h->ngauge; g++) {
+        double *o = rec + (size_t)g * w;
+        o[0] = level_time(h, 0);
+        for (int f = 0; f < h->m; f++) o[1 + f] = 0.0;
+        for (int l = h->P.nlevels - 1; l >= 0; l--) {
+            const OLevel *L = &h->L[l];
+            if (L->np == 0) continue;
+            int I = (int)floor((h->gxs[g] - h->P.lo[0]) / L->dx);
+            if (I < 0) I = 0;
+            if (I > L->N - 1) I = L->N - 1;
+            int J = 0;
+            if (h->P.dim == 2) {
+                J = (int)floor((h->gys[g] - h->P.lo[1]) / L->dy);
+                if (J < 0) J = 0;
+                if (J > L->M - 1) J = L->M - 1;
+            }
+            int k = find_patch(h, l, I, J);
+            if (k < 0) continue;
+            const OPatch *p = &L->p[k];
+            for (int f = 0; f < h->m; f++) o[1 + f] = p->q[L->cur][qidx(h, p, f, I - p->ilo, J - p->jlo)];
+            break;
+        }
+    }
+    h->ngrec++;
+}
+
+int orc_set_gauges(void *hv, int n, const double *x, const double *y)
+{
+    OHier *h = hv;
+    if (n < 0) return 1;
+    free(h->gxs);
+    free(h->gys);
+    free(h->grec);
+    h->gxs = n ? xcalloc((size_t)n, sizeof(double)) : NULL;
+    h->gys = n ? xcalloc((size_t)n, sizeof(double)) : NULL;
+    for (int g = 0; g < n; g++) {
+        h->gxs[g] = x[g];
+        h->gys[g] = (h->P.dim == 2) ? y[g] : 0.0;
+    }
+    h->ngauge = n;
+    h->grec = NULL;
+    h->ngrec = h->gcap = 0;
+    return 0;
+}
+
+/* records so far (each ngauge x (1 + m) doubles); copies at most cap */
+long orc_read_gauges(void *hv, double *out, long cap)
+{
+    OHier *h = hv;
+    long n = h->ngrec < cap ? h->ngrec : cap;
+    if (n > 0) memcpy(out, h->grec, (size_t)n * h->ngauge * (1 + h->m) * sizeof(double));
+    return h->ngrec;
+}
+
 int orc_advance(void *hv, int nsteps, double *cfl_out)
 {
     OHier *h = hv;
     double cfl = 0.0;
-    for (int s = 0; s < nsteps; s++)
+    for (int s = 0; s < nsteps; s++) {
         if (step_level(h, 0, &cfl)) return 1;
+        record_gauges(h);
+    }
     if (cfl_out) *cfl_out = cfl;
     return cfl > h->P.cfl_max ? 2 : 0;
 }

@@ -91,6 +91,9 @@ def lib():
             L.orc_step_patch.argtypes = [i, i, i, i, dp, dp, d, d, d, dp, dp]
             L.orc_adjoint_solve.argtypes = [P(OrcParams), i, i, dp, dp, dp, dp, dp, i, dp]
             L.orc_cluster.argtypes = [P(ctypes.c_ubyte), P(ctypes.c_ubyte), i, i, i, i, d, P(ctypes.c_int), i]
+            L.orc_set_gauges.argtypes = [vp, i, dp, dp]
+            L.orc_read_gauges.restype = ctypes.c_long
+            L.orc_read_gauges.argtypes = [vp, dp, ctypes.c_long]
             _lib = L
     return _lib
 
@@ -216,6 +219,24 @@ class OracleHierarchy:
         cnt = ctypes.c_long(0)
         lib().orc_flag(self.h, level, tol, out.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)), ctypes.byref(cnt))
         return out[:n], cnt.value
+
+    def set_gauges(self, xs, ys=None):
+        """Points recorded after every level-0 step."""
+        xs = np.ascontiguousarray(xs, dtype=np.float64)
+        ys = np.ascontiguousarray(np.zeros_like(xs) if ys is None else ys, dtype=np.float64)
+        self._keep += [xs, ys]
+        if lib().orc_set_gauges(self.h, xs.size, _dp(xs), _dp(ys)):
+            raise RuntimeError("orc_set_gauges failed")
+        self._ng = xs.size
+
+    def gauges(self) -> np.ndarray:
+        """Records [nrec, ngauge, 1 + m]: time and the values of the cell holding
+        each point on the finest level covering it."""
+        ng = getattr(self, "_ng", 0)
+        n = lib().orc_read_gauges(self.h, None, 0)
+        out = np.zeros((max(n, 1), max(ng, 1), 1 + self.m))
+        lib().orc_read_gauges(self.h, _dp(out), n)
+        return out[:n, :ng]
 
     def read_level(self, level: int) -> np.ndarray:
         b = self.patches(level)

@@ -96,7 +96,8 @@ SYMBOLS = [
     "adjamr_set_adjoint", "adjamr_adjoint_read", "adjamr_adjoint_release", "adjamr_regrid",
     "adjamr_advance_level", "adjamr_flag_cells", "adjamr_integrate_functional", "adjamr_get_patches",
     "adjamr_read_level", "adjamr_write_level", "adjamr_fill_ghosts", "adjamr_read_patch_ghosted",
-    "adjamr_step_level_only", "adjamr_get_stats", "adjamr_set_timing", "adjamr_set_level_kernel", "adjamr_time_info",
+    "adjamr_step_level_only", "adjamr_get_stats", "adjamr_set_timing", "adjamr_set_level_kernel", "adjamr_set_gauges",
+    "adjamr_read_gauges", "adjamr_time_info",
     "adjamr_last_error",
     "adjamr_destroy", "adjamr_batch_create", "adjamr_batch_set_order", "adjamr_batch_set_ghost_fusion",
     "adjamr_batch_step",
@@ -148,6 +149,8 @@ def load(build_if_missing: bool = True):
             "adjamr_get_stats": [vp, P(Stats)],
             "adjamr_set_timing": [vp, i],
             "adjamr_set_level_kernel": [vp, i, i, i, i],
+            "adjamr_set_gauges": [vp, i, dp, dp],
+            "adjamr_read_gauges": [vp, dp, ll, ctypes.POINTER(ll)],
             "adjamr_time_info": [vp, dp, ip],
             "adjamr_batch_create": [i, ip, ip, dp, dp, dp, dp, dp, ip, P(Medium), i, dp, vp, P(vp)],
             "adjamr_batch_set_order": [vp, ip],
@@ -369,6 +372,23 @@ class Hierarchy:
         for k in ("regrid_phase_ms", "level_step_ms", "level_step_launches", "level_cell_updates", "cluster_phase_ms"):
             d[k] = list(getattr(s, k))
         return d
+
+    def set_gauges(self, xs, ys=None) -> None:
+        """Points recorded on the device after every level-0 step."""
+        xs = np.ascontiguousarray(xs, dtype=np.float64)
+        ys = np.ascontiguousarray(np.zeros_like(xs) if ys is None else ys, dtype=np.float64)
+        _check(load().adjamr_set_gauges(self.h, xs.size, _dp(xs), _dp(ys)), self.h, "set_gauges")
+        self._ng = xs.size
+
+    def gauges(self) -> np.ndarray:
+        """Records [nrec, ngauge, 1 + m]: time and the values of the cell holding
+        each point on the finest level covering it."""
+        ng = getattr(self, "_ng", 0)
+        n = ctypes.c_longlong(0)
+        _check(load().adjamr_read_gauges(self.h, None, 0, ctypes.byref(n)), self.h, "read_gauges")
+        out = np.zeros((max(n.value, 1), max(ng, 1), 1 + self.m))
+        _check(load().adjamr_read_gauges(self.h, _dp(out), n.value, ctypes.byref(n)), self.h, "read_gauges")
+        return out[:n.value, :ng]
 
     def set_level_kernel(self, level: int, tile, fuse_ghosts: bool = True) -> None:
         """Step-kernel tile (tx, ty) and ghost fusion of one level (-1: all

@@ -123,6 +123,11 @@ struct adjamr_ctx {
     int ltx[ADJAMR_MAX_LEVELS] = {}, lty[ADJAMR_MAX_LEVELS] = {}, lgrid[ADJAMR_MAX_LEVELS] = {};
     int lfuse[ADJAMR_MAX_LEVELS] = {};  // ghost ring computed inside the step kernel
     bool timing = false;
+    // gauges: cell indices per level (device), records on the device
+    int ngauge = 0;
+    int *d_gij = nullptr;           // [2][nlevels][ngauge]: I then J
+    double *d_grec = nullptr;       // [gcap][ngauge][1 + m]
+    long long ngrec = 0, gcap = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // step-kernel timing without host synchronisation: event pairs recorded
     // around every step launch, read when the stream is synchronised
@@ -948,6 +953,8 @@ adjamr_status flag_tables(adjamr_ctx *c, int l)
     return ADJAMR_OK;
 }
 
+adjamr_status ghost_fill(adjamr_ctx *c, int l, int k);
+
 adjamr_status flag_dense(adjamr_ctx *c, int l, double tol, uint64_t *d_bits, int pitch64, unsigned char *d_patchflags,
                          long long *nflag_out, int *bbox_out)
 {
@@ -1005,6 +1012,11 @@ adjamr_status flag_dense(adjamr_ctx *c, int l, double tol, uint64_t *d_bits, int
     CKR(c, cudaMemcpyAsync(c->d_bbox, bbox_init, sizeof bbox_init, cudaMemcpyHostToDevice, c->s));
     // regrid flags (dense only, bracket max, block maxima present): one thread
     // per (cell, group of snapshot blocks) over the level's index space
+    if (P.flag_mode == ADJAMR_FLAG_DIFFERENCE) {
+        // centred differences read the ghost ring of the current state
+        const int sub = l > 0 ? (int)(L.nstep - c->L[l - 1].nstep * P.ratio[l - 1]) : 0;
+        TRY(ghost_fill(c, l, sub));
+    }
     const bool dense = d_bits && !d_patchflags && P.flag_mode == ADJAMR_FLAG_BRACKET_MAX && c->adj &&
                        c->adj->d_bmax && a.S >= 2;
     if (dense) {
@@ -1260,6 +1272,7 @@ adjamr_status create_impl(const adjamr_params *p, adjamr_ctx **out)
         if (p->ratio[l] < 2) return ADJAMR_EINVAL;
     for (int k = 0; k < 4; k++)
         if (p->bc[k] < 0 || p->bc[k] > 2) return ADJAMR_EINVAL;
+    if (p->flag_mode < ADJAMR_FLAG_BRACKET_MAX || p->flag_mode > ADJAMR_FLAG_SURFACE) return ADJAMR_EINVAL;
     adjamr_ctx *c = new (std::nothrow) adjamr_ctx();
     if (!c) return ADJAMR_ENOMEM;
     c->P = *p;
@@ -1659,13 +1672,102 @@ adjamr_status adjamr_regrid(adjamr_ctx *ctx, int base_level, int init)
     }
 }
 
+// one gauge record at the current level-0 time (device, stream-ordered)
+adjamr_status record_gauges(adjamr_ctx *c)
+{
+    if (c->ngauge == 0) return ADJAMR_OK;
+    const int w = 1 + c->m;
+    if (c->ngrec == c->gcap) {
+        long long ncap = c->gcap ? 2 * c->gcap : 256;
+        double *nb = nullptr;
+        CKR(c, dalloc(&nb, (size_t)ncap * c->ngauge * w, c->s));
+        if (c->ngrec) CKR(c, cudaMemcpyAsync(nb, c->d_grec, sizeof(double) * (size_t)c->ngrec * c->ngauge * w,
+                                              cudaMemcpyDeviceToDevice, c->s));
+        dfree(c->d_grec, c->s);
+        c->d_grec = nb;
+        c->gcap = ncap;
+    }
+    GaugeArgs g;
+    std::memset(&g, 0, sizeof g);
+    g.n = c->ngauge;
+    g.m = c->m;
+    g.nlev = c->P.nlevels;
+    g.gi = c->d_gij;
+    g.gj = c->d_gij + (size_t)c->P.nlevels * c->ngauge;
+    for (int l = 0; l < c->P.nlevels; l++) {
+        const Level &L = c->L[l];
+        g.owner[l] = L.patches.empty() ? nullptr : L.d_owner;
+        g.q[l] = L.q[L.cur];
+        g.stride[l] = L.ncell;
+        g.N[l] = L.N;
+    }
+    g.t = c->P.t0 + (double)c->L[0].nstep * c->L[0].dt;
+    g.out = c->d_grec + (size_t)c->ngrec * c->ngauge * w;
+    CKR(c, launch_gauges(g, c->s));
+    c->st.kernel_launches++;
+    c->ngrec++;
+    return ADJAMR_OK;
+}
+
+adjamr_status adjamr_set_gauges(adjamr_ctx *ctx, int n, const double *x, const double *y)
+{
+    if (!ctx || n < 0 || (n > 0 && (!x || (ctx->P.dim == 2 && !y)))) return ADJAMR_EINVAL;
+    try {
+        const adjamr_params &P = ctx->P;
+        const int nl = P.nlevels;
+        std::vector<int> ij((size_t)2 * nl * n);
+        for (int l = 0; l < nl; l++) {
+            const Level &L = ctx->L[l];
+            for (int g = 0; g < n; g++) {
+                int I = (int)std::floor((x[g] - P.lo[0]) / L.dx);
+                I = std::min(std::max(I, 0), L.N - 1);
+                int J = 0;
+                if (P.dim == 2) {
+                    J = (int)std::floor((y[g] - P.lo[1]) / L.dy);
+                    J = std::min(std::max(J, 0), L.M - 1);
+                }
+                ij[(size_t)l * n + g] = I;
+                ij[(size_t)(nl + l) * n + g] = J;
+            }
+        }
+        dfree(ctx->d_gij, ctx->s);
+        dfree(ctx->d_grec, ctx->s);
+        ctx->ngrec = ctx->gcap = 0;
+        ctx->ngauge = n;
+        if (n > 0) {
+            std::vector<size_t> offs;
+            char *d = nullptr;
+            CKR(ctx, upload_packed(ctx, {{ij.data(), sizeof(int) * ij.size()}}, &d, offs));
+            ctx->d_gij = reinterpret_cast<int *>(d);
+        }
+        return ADJAMR_OK;
+    } catch (...) {
+        return ADJAMR_ENOMEM;
+    }
+}
+
+adjamr_status adjamr_read_gauges(adjamr_ctx *ctx, double *out, long long cap, long long *nrec)
+{
+    if (!ctx || cap < 0 || (cap > 0 && !out)) return ADJAMR_EINVAL;
+    const long long n = std::min(cap, ctx->ngrec);
+    if (n > 0)
+        CKR(ctx, cudaMemcpyAsync(out, ctx->d_grec, sizeof(double) * (size_t)n * ctx->ngauge * (1 + ctx->m),
+                                 cudaMemcpyDeviceToHost, ctx->s));
+    CKR(ctx, cudaStreamSynchronize(ctx->s));
+    if (nrec) *nrec = ctx->ngrec;
+    return ADJAMR_OK;
+}
+
 adjamr_status adjamr_advance_level(adjamr_ctx *ctx, int level, int nsteps)
 {
     if (!ctx || level != 0 || nsteps < 0) return ADJAMR_EINVAL;
     if (!ctx->have_medium) return ADJAMR_ESTATE;
     try {
         CKR(ctx, cudaMemsetAsync(ctx->d_cfl, 0, sizeof(unsigned long long), ctx->s));
-        for (int s = 0; s < nsteps; s++) TRY(step_level(ctx, 0));
+        for (int s = 0; s < nsteps; s++) {
+            TRY(step_level(ctx, 0));
+            TRY(record_gauges(ctx));
+        }
         unsigned long long bits = 0;
         CKR(ctx, cudaMemcpyAsync(&bits, ctx->d_cfl, sizeof bits, cudaMemcpyDeviceToHost, ctx->s));
         CKR(ctx, cudaStreamSynchronize(ctx->s));
@@ -1914,6 +2016,8 @@ void adjamr_destroy(adjamr_ctx *ctx)
     for (double *p : ctx->dense_dev) cudaFreeAsync(p, ctx->s);
     dfree(ctx->d_flagbuf, ctx->s);
     for (int l = 0; l < ADJAMR_MAX_LEVELS; l++) dfree(ctx->d_ftab[l], ctx->s);
+    dfree(ctx->d_gij, ctx->s);
+    dfree(ctx->d_grec, ctx->s);
     dfree(ctx->d_fscratch, ctx->s);
     cudaStreamSynchronize(ctx->s);
     if (ctx->d_cfl) cudaFree(ctx->d_cfl);

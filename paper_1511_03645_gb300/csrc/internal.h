@@ -169,6 +169,19 @@ constexpr int kSnapBlock = 8;       // snapshots per culling block
 cudaError_t launch_block_max(const double *snaps, int S, int m, int ax, int ay, int dim, double *bmax,
                              cudaStream_t s);
 cudaError_t launch_flag(const FlagArgs &a, cudaStream_t s);
+// gauge record: out[g][1 + m] for every gauge (see k_gauges)
+struct GaugeArgs {
+    int n, m, nlev;
+    const int *gi, *gj;             // [nlev][n]: cell index of every gauge on every level
+    const int *owner[ADJAMR_MAX_LEVELS];
+    const double *q[ADJAMR_MAX_LEVELS];
+    long long stride[ADJAMR_MAX_LEVELS];
+    int N[ADJAMR_MAX_LEVELS];
+    double t;
+    double *out;
+};
+cudaError_t launch_gauges(const GaugeArgs &g, cudaStream_t s);
+
 // bracket-max flags over the level's index space, one thread per (cell, group
 // of a.gblk snapshot blocks), into the zeroed bitmap a.flags_bits
 cudaError_t launch_flag_dense(const FlagArgs &a, int ngroup, cudaStream_t s);

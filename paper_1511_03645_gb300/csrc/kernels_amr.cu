@@ -400,7 +400,18 @@ __global__ void k_flag(FlagArgs A)
         // at the first term above tol (the decision is that of the full max);
         // a dry adjoint cell sets the inner product to zero (Sec. 5.3)
         bool hit = false;
-        if (A.S >= 2) {
+        if (A.mode == ADJAMR_FLAG_DIFFERENCE) {
+            // undivided centred differences from the ghost-filled arena
+            double val = 0.0;
+            for (int f = 0; f < A.m; f++) {
+                const double *qf = A.q + (long long)f * A.stride;
+                val = fmax(val, fabs(qf[cell + 1] - qf[cell - 1]));
+                if (A.dim == 2) val = fmax(val, fabs(qf[cell + P.sx] - qf[cell - P.sx]));
+            }
+            hit = val > A.tol;
+        } else if (A.mode == ADJAMR_FLAG_SURFACE) {
+            hit = fabs(Q[0]) > A.tol;
+        } else if (A.S >= 2) {
             double dxa = (A.hi0 - A.lo0) / (double)A.ax;
             int ac = (int)floor((x - A.lo0) / dxa);
             ac = min(max(ac, 0), A.ax - 1);
@@ -504,6 +515,25 @@ __global__ void k_flag(FlagArgs A)
 // among threads); blocks whose bound cannot exceed tol are skipped as in
 // k_flag.  The first thread to set a cell's flag counts it; warp shuffles
 // reduce the count and the bounding box of the flags.
+// Gauge record: for every gauge, the level-0 time and the values of the cell
+// holding the point on the finest level with a patch there.
+__global__ void k_gauges(GaugeArgs G)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= G.n) return;
+    double *o = G.out + (long long)g * (1 + G.m);
+    o[0] = G.t;
+    for (int f = 0; f < G.m; f++) o[1 + f] = 0.0;
+    for (int l = G.nlev - 1; l >= 0; l--) {
+        if (!G.owner[l]) continue;
+        const int I = G.gi[l * G.n + g], J = G.gj[l * G.n + g];
+        const int c = G.owner[l][(long long)J * G.N[l] + I];
+        if (c < 0) continue;
+        for (int f = 0; f < G.m; f++) o[1 + f] = G.q[l][(long long)f * G.stride[l] + c];
+        break;
+    }
+}
+
 template <int MF>
 __global__ void k_flag_dense(FlagArgs A)
 {
@@ -723,6 +753,13 @@ cudaError_t launch_block_max(const double *snaps, int S, int m, int ax, int ay, 
     long long n = (long long)nblk * m * ax * ay;
     if (n <= 0) return cudaSuccess;
     k_block_max<<<nblk_of(n), kT, 0, s>>>(snaps, S, m, ax, ay, dim, nblk, bmax);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gauges(const GaugeArgs &g, cudaStream_t s)
+{
+    if (g.n <= 0) return cudaSuccess;
+    k_gauges<<<(g.n + kT - 1) / kT, kT, 0, s>>>(g);
     return cudaGetLastError();
 }
 

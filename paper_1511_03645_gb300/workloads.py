@@ -38,6 +38,8 @@ BC_PERIODIC = 2
 
 FLAG_BRACKET_MAX = 0
 FLAG_LINEAR = 1
+FLAG_DIFFERENCE = 2   # standard flagging: undivided differences of every component
+FLAG_SURFACE = 3      # standard flagging: |first component| (surface elevation)
 
 GRAV = 9.81
 

@@ -158,13 +158,15 @@ def _compare_all(o, g, nlev):
         close(a, b)
 
 
-@pytest.mark.parametrize("which", ["c1", "c2", "c2_linear", "c2_walls", "c3"])
+@pytest.mark.parametrize("which", ["c1", "c2", "c2_linear", "c2_walls", "c3", "c1_diff", "c2_diff", "c3_surface"])
 def test_amr_run_matches_oracle(A, which):
     """Adjoint-guided AMR runs (reduced sizes of the workloads): layouts of
     every level bit-exact after every regrid, states within 1e-12, flags
     bit-exact, J within 1e-12."""
-    if which == "c1":
+    if which.startswith("c1"):
         wl = W.config1(n0=100, tf=6.0, adj_n=400, nsnap=30)
+        if which == "c1_diff":
+            wl.flag_mode, wl.tol = W.FLAG_DIFFERENCE, 0.02
         chunks = 6
     elif which.startswith("c2"):
         bc = (W.BC_WALL,) * 4 if which == "c2_walls" else (W.BC_EXTRAP,) * 4
@@ -172,10 +174,14 @@ def test_amr_run_matches_oracle(A, which):
                        min_patch=8, max_patch=32)
         if which == "c2_linear":
             wl.flag_mode = W.FLAG_LINEAR
+        if which == "c2_diff":
+            wl.flag_mode, wl.tol = W.FLAG_DIFFERENCE, 0.05
         chunks = 4
     else:
         wl = W.config3(seed=2, n0=24, ratios=(2, 2), tf=4 * 3600.0, adj_n=48, nsnap=20, tol=1e-5, L=2.0e6,
                        dense_levels=3)
+        if which == "c3_surface":
+            wl.flag_mode, wl.tol = W.FLAG_SURFACE, 0.02
         chunks = 4
     snaps = O.adjoint_solve(wl, medium_dense=None if wl.medium.kind != "dense" else _adj_medium(wl))
     o, g = _amr_pair(A, wl, snaps=snaps)
@@ -234,6 +240,29 @@ def test_per_level_kernels_compute_the_same_bits(A):
     with pytest.raises(A.AdjamrError):
         h.set_level_kernel(wl.nlevels, (32, 8))
     h.close()
+
+
+def test_gauges_match_oracle_bitwise(A):
+    """Gauge series (finest level covering each point, after every coarse
+    step) of an adjoint-flagged run and of a difference-flagged run equal the
+    oracle's bit for bit."""
+    for mode, tol in ((W.FLAG_BRACKET_MAX, 1e-4), (W.FLAG_DIFFERENCE, 0.05)):
+        wl = W.config2(seed=3, n0=32, ratios=(2, 4), tf=2.0, adj_n=64, nsnap=20, ts=0.0, tol=tol,
+                       min_patch=8, max_patch=32)
+        wl.flag_mode = mode
+        o, g = _amr_pair(A, wl)
+        xs, ys = [2.25, 0.0, -3.9, 1.3], [2.25, 0.0, 3.9, -0.7]
+        o.set_gauges(xs, ys)
+        g.set_gauges(xs, ys)
+        n = o.nsteps_total()
+        o.advance(n // 2)
+        g.advance(n // 2)
+        o.advance(n - n // 2)
+        g.advance(n - n // 2)
+        go, gg = o.gauges(), g.gauges()
+        assert go.shape == gg.shape == (n, 4, 4)
+        assert np.array_equal(go, gg)
+        assert np.any(go[:, 0, 1] != 0.0)
 
 
 def _adj_medium(wl):
