@@ -34,12 +34,21 @@ METRIC = "FP64 cell-updates/s (fused batched vs per-patch, same GPU); serve p50/
 UNIT = "cell-updates/s"
 
 # FP64 operations per 2D acoustics cell-update in the canonical operation
-# order (a cell owns one x-edge and one y-edge): per edge 14 (normal solve),
-# 44 (two MC limiters, correction coefficients, Fn), 18 (two transverse
-# splits into F or G), 3 (CFL); per cell 12 (entering sums Sx, Sy) and 22
-# (update); a fused multiply-add counts 2, divisions and min/max 1 each.
-# 2*79 + 34 = 192.
-FLOPS_PER_CELL_2D = 192
+# order, one per IEEE operation (fma, division, min and max count one each;
+# a cell owns one x-edge and one y-edge).  Per edge: jump 2, decomposition 6,
+# fluctuations 4, two MC limiters 20, correction coefficients 4, second-order
+# flux 12, CFL 2, two transverse splits 16 and their accumulation 4 = 70; per
+# cell: entering sums 12, update 18.  2*70 + 30 = 170.  The FP64 pipe issues
+# one such operation per instruction, so the roofline peak is the pipe's
+# instruction rate (the DFMA micro-benchmark's flop rate / 2).
+OPS_PER_CELL_2D = 170
+# DRAM bytes per cell-update of a finest-level step launch, from the ncu
+# capture summarised in profiles/k_step2d_amr_level2_config2.md (4.59 MB read,
+# 0 written, in a launch of the --case solve --tf 1 run, whose level-2
+# launches average 40,920 cells): 1.4x the 80 algorithmic bytes per
+# cell-update (tile halos, descriptors, coarse reads for the ghost ring);
+# written lines stay in L2 within the launch.
+TRAFFIC_PER_CELL_L2 = 4.594688e6 / 40920.0
 
 
 def log(*a):
@@ -265,11 +274,10 @@ def run_ours(args, rank, world):
     # roofline of the step kernel (FP64-pipe bound)
     cells_per_launch = cu / max(step_launches, 1)
     avg_launch_s = step_ms * 1e-3 / max(step_launches, 1)
-    achieved = FLOPS_PER_CELL_2D * cells_per_launch / avg_launch_s / 1e12
-    # peak: the FP64 pipe's flop rate measured with DFMA chains (2 flops per
-    # instruction); the step's operations are only partly fusable, so this
-    # bounds it from above
-    peak = peak_fma / 1e12
+    achieved = OPS_PER_CELL_2D * cells_per_launch / avg_launch_s / 1e12
+    # peak: FP64 instructions per second of the pipe, measured live with DFMA
+    # chains (flop rate / 2: one operation per instruction)
+    peak = peak_fma / 2 / 1e12
 
     # batched patches: fused work-list vs one launch per patch (same GPU)
     batched = None
@@ -314,7 +322,7 @@ def run_ours(args, rank, world):
         best_fused = max(v for k, v in res.items() if k != "per_patch")
         batched = {"patches": pb.npatch, "cells": cells, **{k: v for k, v in res.items()},
                    "tuned_config": tuned_batch,
-                   "fp64_roofline_frac_best": FLOPS_PER_CELL_2D * best_fused / peak_fma,
+                   "fp64_roofline_frac_best": OPS_PER_CELL_2D * best_fused / (peak_fma / 2),
                    "fused_over_per_patch": res["fused_worklist"] / res["per_patch"],
                    "best_fused_over_per_patch": best_fused / res["per_patch"]}
 
@@ -370,16 +378,17 @@ def run_ours(args, rank, world):
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "step_kernel_per_level": tuned["best_per_level"]},
         "roofline": {"bound": "alu", "kernel": "k_step2d (fused wave-propagation step)",
-                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": None,
-                     "peak_source": "project FP64 DFMA micro-benchmark (2 flops per instruction), measured live",
-                     "flops_per_cell_update": FLOPS_PER_CELL_2D,
+                     "achieved": achieved, "peak": peak, "unit": "TOP/s (FP64 operations)",
+                     "frac": achieved / peak, "traffic": TRAFFIC_PER_CELL_L2 * cells_per_launch,
+                     "peak_source": "FP64 instruction rate of the project DFMA micro-benchmark, measured live "
+                                    "(its flop rate / 2)",
+                     "ops_per_cell_update": OPS_PER_CELL_2D,
                      "cells_per_launch": cells_per_launch, "avg_launch_us": avg_launch_s * 1e6,
                      "per_level": [{"level": lev, **tuned["best_per_level"][lev],
                                     "launches_per_step": lev_launch[lev] / args.steps,
                                     "cells_per_launch": lev_cells[lev] / max(lev_launch[lev], 1),
                                     "avg_launch_us": lev_ms[lev] * 1e3 / max(lev_launch[lev], 1),
-                                    "tflops": (FLOPS_PER_CELL_2D * lev_cells[lev] / (lev_ms[lev] * 1e-3) / 1e12
+                                    "tops": (OPS_PER_CELL_2D * lev_cells[lev] / (lev_ms[lev] * 1e-3) / 1e12
                                                if lev_ms[lev] > 0 else None)}
                                    for lev in range(wl.nlevels)]},
         "fp64_peak": {"dfma_tflops": peak_fma / 1e12, "dadd_tflops": peak_add / 1e12},
@@ -398,7 +407,8 @@ def run_ours(args, rank, world):
                                                             [v / args.steps for v in phases])),
                                   "clustering_phases": dict(zip(["dilate_nest", "integral_images", "bisection",
                                                                  "split_sort"], [v / args.steps for v in cphases]))},
-        "autotune_levels_ms": {f"{t['tile'][0]}x{t['tile'][1]}{'' if t['fuse_ghosts'] else '+fill'}":
+        "autotune_levels_ms": {f"{t['tile'][0]}x{t['tile'][1]}{'' if t['fuse_ghosts'] else '+fill'}"
+                               f"{'+dyn' if t['mode'] == A.LAUNCH_DYNAMIC else ''}":
                                [round(x["ms"], 3) for x in t["levels"]] for t in tuned["candidates"]},
         "adjoint_solve_s": adj_s,
         "J": Js[0],
@@ -501,50 +511,75 @@ def run_case_batch(args):
     b.close()
 
 
-def compare_flaggers(A, W, wl, adj, adj_s, s, tuned=None, diff_tol=0.1, reps=2):
+def compare_flaggers(A, W, wl, adj, adj_s, s, tuned=None, diff_tols=(0.1, 0.03, 0.01, 0.003)):
     """The paper's comparison (Sec. 5.2.4): the same forward solve refined by
-    adjoint flagging and by the standard undivided-difference
-    ("pressure") flagging; wall time per solve on this GPU, cell-updates, and
-    the gauge at the centre of the target region from both runs."""
+    adjoint flagging and by the standard undivided-difference ("pressure")
+    flagging over a range of tolerances (0.1 is the paper's); GPU time per
+    solve, cell-updates, and the error of J and of the gauge at the centre of
+    the target region against the uniform run on the finest grid."""
     import copy
     import torch
     from paper_1511_03645_gb300 import autotune as AT
     gx = [0.5 * (wl.target.x0 + wl.target.x1)]
     gy = [0.5 * (wl.target.y0 + wl.target.y1)]
-    out = {}
-    series = {}
-    for name, mode, tol in (("adjoint", wl.flag_mode, wl.tol), ("difference", W.FLAG_DIFFERENCE, diff_tol)):
+
+    def one(mode, tol):
         w = copy.copy(wl)
         w.flag_mode, w.tol = mode, tol
-        best = None
-        for _ in range(reps):
-            h = A.Hierarchy(w, stream=s.cuda_stream)
-            if tuned:
-                AT.apply_amr(h, tuned)
-            h.set_adjoint(adj)
-            h.set_gauges(gx, gy)
-            torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(s)
-            h.regrid(0, init=True)
-            h.advance(h.nsteps_total())
-            J = h.functional()
-            e1.record(s)
-            e1.synchronize()
-            ms = e0.elapsed_time(e1)
-            st = h.stats()
-            g = h.gauges()
-            h.close()
-            if best is None or ms < best[0]:
-                best = (ms, st["cell_updates"], J, g)
-        out[name] = {"tol": tol, "ms_per_solve": best[0], "cell_updates": best[1], "J": best[2]}
-        series[name] = best[3]
-    out["adjoint"]["adjoint_solve_ms"] = adj_s * 1e3
-    ga, gd = series["adjoint"][:, 0, 1], series["difference"][:, 0, 1]
-    out["gauge"] = {"x": gx[0], "y": gy[0], "records": int(ga.size), "peak_abs_p": float(np.max(np.abs(gd))),
-                    "max_abs_diff_p": float(np.max(np.abs(ga - gd)))}
-    out["difference_over_adjoint_time"] = out["difference"]["ms_per_solve"] / out["adjoint"]["ms_per_solve"]
+        h = A.Hierarchy(w, stream=s.cuda_stream)
+        if tuned:
+            AT.apply_amr(h, tuned)
+        h.set_adjoint(adj)
+        h.set_gauges(gx, gy)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        h.regrid(0, init=True)
+        h.advance(h.nsteps_total())
+        J = h.functional()
+        e1.record(s)
+        e1.synchronize()
+        res = {"tol": tol, "ms_per_solve": e0.elapsed_time(e1), "cell_updates": h.stats()["cell_updates"], "J": J}
+        g = h.gauges()[:, 0, 1]
+        h.close()
+        return res, g
+
+    # reference: the uniform run on the finest grid (every cell refined)
+    h0 = A.Hierarchy(wl, stream=s.cuda_stream)
+    dt0, n0 = h0.time_info()
+    h0.close()
+    rf = int(np.prod(wl.ratios))
+    fine = A.Hierarchy(wl, nlevels=1, n0=wl.level_shape(wl.nlevels - 1), dt0=dt0 / rf, stream=s.cuda_stream)
+    fine.set_gauges(gx, gy)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    fine.advance(n0 * rf)
+    J_fine = fine.functional()
+    e1.record(s)
+    e1.synchronize()
+    g_fine = fine.gauges()[rf - 1::rf, 0, 1]
+    ref = {"ms_per_solve": e0.elapsed_time(e1), "cell_updates": fine.stats()["cell_updates"], "J": J_fine}
+    fine.close()
+
+    def accuracy(res, g):
+        res["J_rel_err_vs_uniform_fine"] = abs(res["J"] - J_fine) / max(abs(J_fine), 1e-300)
+        res["gauge_max_abs_err_vs_uniform_fine"] = float(np.max(np.abs(g - g_fine)))
+
+    adj_runs = [one(wl.flag_mode, wl.tol) for _ in range(2)]
+    ra, ga = min(adj_runs, key=lambda r: r[0]["ms_per_solve"])
+    ra["adjoint_solve_ms"] = adj_s * 1e3
+    accuracy(ra, ga)
+    out = {"uniform_fine": ref, "adjoint": ra,
+           "gauge": {"x": gx[0], "y": gy[0], "records": int(ga.size), "peak_abs_p_fine": float(np.max(np.abs(g_fine)))},
+           "difference": []}
+    for tol in diff_tols:
+        rd, gd = one(W.FLAG_DIFFERENCE, tol)
+        accuracy(rd, gd)
+        rd["time_over_adjoint_forward"] = rd["ms_per_solve"] / ra["ms_per_solve"]
+        out["difference"].append(rd)
     out["paper_context"] = ("Sec. 5.2.4 (laptop): pressure-flagging 3.1-15.7 s vs adjoint-flagging forward "
                             "1.3-6.9 s + adjoint 0.47-0.68 s")
     return out
@@ -552,8 +587,10 @@ def compare_flaggers(A, W, wl, adj, adj_s, s, tuned=None, diff_tol=0.1, reps=2):
 
 def run_case_solve(args):
     """Profiling case: one config-2 forward solve to --tf (adjoint solved
-    first), step-kernel tile and ghost mode of every level fixed
-    (8x8 fused, 8x8 fused, 16x8 fused); prints per-level step statistics."""
+    first) with the step-kernel tile and ghost mode of every level given by
+    --kernels (default: the configuration the autotuner picks on a GB300,
+    8x8 fused, 8x8 fused, 16x8 with a separate ghost fill); prints per-level
+    step statistics."""
     import torch
     from paper_1511_03645_gb300 import adjamr as A
     torch.cuda.set_device(0)
@@ -564,8 +601,10 @@ def run_case_solve(args):
     adj = A.solve_adjoint(wl, stream=s.cuda_stream)
     for rep in range(1 + args.warmup):
         h = A.Hierarchy(wl, stream=s.cuda_stream)
-        for lev, t in enumerate([(8, 8), (8, 8), (16, 8)][:wl.nlevels]):
-            h.set_level_kernel(lev, t, True)
+        for lev, spec in enumerate(args.kernels.split(",")[:wl.nlevels]):
+            fused = spec.endswith("f")
+            tx, ty = (int(v) for v in spec.rstrip("f").split("x"))
+            h.set_level_kernel(lev, (tx, ty), fused)
         h.set_adjoint(adj)
         h.set_timing(True)
         torch.cuda.synchronize()
@@ -595,6 +634,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--case", default="main", choices=["main", "batch", "serve", "solve"])
     ap.add_argument("--tf", type=float, default=0.0, help="solve case: final time (0: the workload's)")
+    ap.add_argument("--kernels", default="8x8f,8x8f,16x8",
+                    help="solve case: per-level step tile, suffix f = ghost ring computed in the step kernel")
     ap.add_argument("--nreq", type=int, default=512)
     ap.add_argument("--slots", type=int, default=16)
     ap.add_argument("--serve-sample", type=int, default=32)

@@ -68,9 +68,11 @@ enum { ADJAMR_FLAG_BRACKET_MAX = 0, ADJAMR_FLAG_LINEAR = 1, ADJAMR_FLAG_DIFFEREN
 enum { ADJAMR_MEDIUM_LAYERED = 1, ADJAMR_MEDIUM_DENSE = 2 };
 
 /* Step launch modes: one launch per level over the whole tile work-list
- * (the default), a persistent grid of (#SMs x occupancy) CTAs over the
- * work-list, or one launch per patch (the comparison baseline). */
-enum { ADJAMR_LAUNCH_WORKLIST = 0, ADJAMR_LAUNCH_PERSISTENT = 1, ADJAMR_LAUNCH_PER_PATCH = 2 };
+ * (the default), a persistent grid of (#SMs x occupancy) CTAs striding over
+ * the work-list, one launch per patch (the comparison baseline), or a
+ * persistent grid whose CTAs take the next tile from an atomic counter
+ * (dynamic balancing).  Every mode computes the same bits. */
+enum { ADJAMR_LAUNCH_WORKLIST = 0, ADJAMR_LAUNCH_PERSISTENT = 1, ADJAMR_LAUNCH_PER_PATCH = 2, ADJAMR_LAUNCH_DYNAMIC = 3 };
 
 /* Initial condition callback: fills q_out[f*n + k] for the n cell centres
  * (xc[k], yc[k]) of level `level` (yc = 0 in 1D).  Called on the host by
@@ -243,14 +245,17 @@ adjamr_status adjamr_get_stats(adjamr_ctx *ctx, adjamr_stats *out);
 /* Enable/disable CUDA-event timing of step kernels (adds events only). */
 adjamr_status adjamr_set_timing(adjamr_ctx *ctx, int enable);
 /* Step-kernel configuration of one level (level = -1: every level), used
- * from the next step on: the tile shape, and whether the kernel computes the
+ * from the next step on: the tile shape, whether the kernel computes the
  * level's ghost ring (same-level copies and coarse space-time interpolation,
  * Sec. 3) while staging its tiles (fuse_ghosts = 1, the default) or a
- * separate ghost-fill kernel runs before it (0).  Every choice computes the
- * same bits; it changes only speed (small levels fill the GPU better with
- * small tiles).  2D tiles: 32x8, 16x8, 16x16, 32x16, 64x8, 8x8; 1D: 256 or
- * 128 (tile_y ignored).  Errors: EINVAL for another shape or level. */
-adjamr_status adjamr_set_level_kernel(adjamr_ctx *ctx, int level, int tile_x, int tile_y, int fuse_ghosts);
+ * separate ghost-fill kernel runs before it (0), and the launch mode
+ * (ADJAMR_LAUNCH_*; -1 keeps the level's current one).  Every choice
+ * computes the same bits; it changes only speed (small levels fill the GPU
+ * better with small tiles).  2D tiles: 32x8, 16x8, 16x16, 32x16, 64x8, 8x8;
+ * 1D: 256 or 128 (tile_y ignored).  Errors: EINVAL for another shape, mode
+ * or level. */
+adjamr_status adjamr_set_level_kernel(adjamr_ctx *ctx, int level, int tile_x, int tile_y, int fuse_ghosts,
+                                      int launch_mode);
 /* Gauges (time series at points, Sec. 5.2.4 and Sec. 5.3): n points (x[k],
  * y[k]; y is ignored in 1D) recorded on the device after every level-0 step
  * of adjamr_advance_level: the level-0 time, then the m values of the cell

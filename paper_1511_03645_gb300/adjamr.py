@@ -17,7 +17,7 @@ _lock = threading.Lock()
 _lib = None
 
 OK, EINVAL, ENOMEM, EBUDGET, ECFL, ETIMEOUT, ECUDA, ESTATE, ENEST = range(9)
-LAUNCH_WORKLIST, LAUNCH_PERSISTENT, LAUNCH_PER_PATCH = 0, 1, 2
+LAUNCH_WORKLIST, LAUNCH_PERSISTENT, LAUNCH_PER_PATCH, LAUNCH_DYNAMIC = 0, 1, 2, 3
 MEDIUM_LAYERED, MEDIUM_DENSE = 1, 2
 _NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "EBUDGET", 4: "ECFL", 5: "ETIMEOUT", 6: "ECUDA", 7: "ESTATE",
           8: "ENEST"}
@@ -148,7 +148,7 @@ def load(build_if_missing: bool = True):
             "adjamr_step_level_only": [vp, i],
             "adjamr_get_stats": [vp, P(Stats)],
             "adjamr_set_timing": [vp, i],
-            "adjamr_set_level_kernel": [vp, i, i, i, i],
+            "adjamr_set_level_kernel": [vp, i, i, i, i, i],
             "adjamr_set_gauges": [vp, i, dp, dp],
             "adjamr_read_gauges": [vp, dp, ll, ctypes.POINTER(ll)],
             "adjamr_time_info": [vp, dp, ip],
@@ -390,11 +390,11 @@ class Hierarchy:
         _check(load().adjamr_read_gauges(self.h, _dp(out), n.value, ctypes.byref(n)), self.h, "read_gauges")
         return out[:n.value, :ng]
 
-    def set_level_kernel(self, level: int, tile, fuse_ghosts: bool = True) -> None:
-        """Step-kernel tile (tx, ty) and ghost fusion of one level (-1: all
-        levels); results do not depend on either."""
+    def set_level_kernel(self, level: int, tile, fuse_ghosts: bool = True, mode: int = -1) -> None:
+        """Step-kernel tile (tx, ty), ghost fusion and launch mode (-1: keep)
+        of one level (-1: all levels); results do not depend on them."""
         _check(load().adjamr_set_level_kernel(self.h, level, int(tile[0]), int(tile[1]) if len(tile) > 1 else 1,
-                                              1 if fuse_ghosts else 0), self.h, "set_level_kernel")
+                                              1 if fuse_ghosts else 0, int(mode)), self.h, "set_level_kernel")
 
     # ---- queries ----
     def patches(self, level: int) -> np.ndarray:

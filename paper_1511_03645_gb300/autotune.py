@@ -7,6 +7,7 @@ a tile does not depend on the schedule), so tuning changes speed only.
 """
 from __future__ import annotations
 
+import itertools
 import json
 import os
 import threading
@@ -86,7 +87,7 @@ def tune_batch(pb, key: str, stream=None, steps: int = 4, use_cache: bool = True
     for oname, order in batch_orders(pb).items():
         b.set_order(order)
         for tile in TILES:
-            for mode in (A.LAUNCH_WORKLIST, A.LAUNCH_PERSISTENT):
+            for mode in (A.LAUNCH_WORKLIST, A.LAUNCH_PERSISTENT, A.LAUNCH_DYNAMIC):
                 for fuse in (False, True):
                     b.set_ghost_fusion(fuse)
                     b.step(1, mode=mode, tile=tile)
@@ -102,7 +103,8 @@ def tune_batch(pb, key: str, stream=None, steps: int = 4, use_cache: bool = True
 
 def tune_amr(wl, adj, key: str, stream=None, coarse_steps: int = 40, use_cache: bool = True) -> dict:
     """Best step-kernel configuration (tile shape, ghost ring fused into the
-    step or filled by its own kernel) of every level of an AMR solve.
+    step or filled by its own kernel, one work-list launch or a persistent
+    grid with dynamic tile fetching) of every level of an AMR solve.
 
     Each candidate runs the solve's first coarse steps (regrids included) with
     the same configuration on every level; the hierarchy evolves
@@ -118,34 +120,33 @@ def tune_amr(wl, adj, key: str, stream=None, coarse_steps: int = 40, use_cache: 
             return hit
     s = torch.cuda.Stream() if stream is None else stream
     results = []
-    for tile in TILES:
-        for fuse in (True, False):
-            h = A.Hierarchy(wl, stream=s.cuda_stream)
-            h.set_level_kernel(-1, tile, fuse)
-            h.set_adjoint(adj)
-            h.set_timing(True)
-            h.regrid(0, init=True)
-            h.advance(2)   # warm-up
-            torch.cuda.synchronize()
-            st0 = h.stats()
-            h.advance(coarse_steps)
-            torch.cuda.synchronize()
-            st1 = h.stats()
-            h.close()
-            per = []
-            for lev in range(wl.nlevels):
-                per.append({"launches": st1["level_step_launches"][lev] - st0["level_step_launches"][lev],
-                            "ms": st1["level_step_ms"][lev] - st0["level_step_ms"][lev],
-                            "cells": st1["level_cell_updates"][lev] - st0["level_cell_updates"][lev]})
-            results.append({"tile": list(tile), "fuse_ghosts": fuse, "levels": per})
+    for tile, fuse, mode in itertools.product(TILES, (True, False), (A.LAUNCH_WORKLIST, A.LAUNCH_DYNAMIC)):
+        h = A.Hierarchy(wl, stream=s.cuda_stream)
+        h.set_level_kernel(-1, tile, fuse, mode)
+        h.set_adjoint(adj)
+        h.set_timing(True)
+        h.regrid(0, init=True)
+        h.advance(2)   # warm-up
+        torch.cuda.synchronize()
+        st0 = h.stats()
+        h.advance(coarse_steps)
+        torch.cuda.synchronize()
+        st1 = h.stats()
+        h.close()
+        per = []
+        for lev in range(wl.nlevels):
+            per.append({"launches": st1["level_step_launches"][lev] - st0["level_step_launches"][lev],
+                        "ms": st1["level_step_ms"][lev] - st0["level_step_ms"][lev],
+                        "cells": st1["level_cell_updates"][lev] - st0["level_cell_updates"][lev]})
+        results.append({"tile": list(tile), "fuse_ghosts": fuse, "mode": mode, "levels": per})
     best = []
     for lev in range(wl.nlevels):
         cand = [r for r in results if r["levels"][lev]["launches"] > 0]
         if not cand:
-            best.append({"tile": list(TILES[0]), "fuse_ghosts": True})
+            best.append({"tile": list(TILES[0]), "fuse_ghosts": True, "mode": A.LAUNCH_WORKLIST})
             continue
         b = min(cand, key=lambda r: r["levels"][lev]["ms"])
-        best.append({"tile": b["tile"], "fuse_ghosts": b["fuse_ghosts"]})
+        best.append({"tile": b["tile"], "fuse_ghosts": b["fuse_ghosts"], "mode": b["mode"]})
     out = {"best_per_level": best, "candidates": results, "coarse_steps": coarse_steps}
     _store(ck, out)
     return out
@@ -154,4 +155,4 @@ def tune_amr(wl, adj, key: str, stream=None, coarse_steps: int = 40, use_cache: 
 def apply_amr(h, tuned: dict) -> None:
     """Set the tuned per-level step-kernel configuration on a hierarchy."""
     for lev, b in enumerate(tuned["best_per_level"]):
-        h.set_level_kernel(lev, b["tile"], b["fuse_ghosts"])
+        h.set_level_kernel(lev, b["tile"], b["fuse_ghosts"], b.get("mode", -1))

@@ -44,6 +44,7 @@ struct adjamr_batch {
     std::vector<int> order;
     MediumDev *d_media = nullptr;
     unsigned long long *d_cfl = nullptr;
+    unsigned long long *d_wctr = nullptr;  // tile counter of the dynamic launch mode
     int nsm = 0;
     std::map<std::tuple<int, int, int, int, int>, cudaGraphExec_t> graphs;
     std::string err;
@@ -108,9 +109,17 @@ cudaError_t one_step(adjamr_batch *b, int mode, int tx, int ty)
         }
     } else {
         int grid = 0;
-        if (mode == ADJAMR_LAUNCH_PERSISTENT) grid = std::min(b->nwork, b->nsm * std::max(1, step_occupancy(2, 0, tx, ty)));
+        if (mode == ADJAMR_LAUNCH_PERSISTENT || mode == ADJAMR_LAUNCH_DYNAMIC)
+            grid = std::min(b->nwork, b->nsm * std::max(1, step_occupancy(2, 0, tx, ty)));
+        TileSched sc{nullptr, 0};
+        if (mode == ADJAMR_LAUNCH_DYNAMIC) {
+            // counter reset in the stream, so that a captured step replays as is
+            e = cudaMemsetAsync(b->d_wctr, 0, sizeof(unsigned long long), b->s);
+            if (e != cudaSuccess) return e;
+            sc.ctr = b->d_wctr;
+        }
         e = launch_step(2, 0, tx, ty, q, qn, b->aux, b->ncell, b->d_patches, b->d_work, b->nwork, grid, b->d_cfl, b->s,
-                        ga);
+                        ga, sc);
         if (e != cudaSuccess) return e;
     }
     b->cur = 1 - b->cur;
@@ -180,6 +189,7 @@ adjamr_status adjamr_batch_create(int npatch, const int *nx, const int *ny, cons
         chk(cudaMallocAsync((void **)&b->d_patches, sizeof(PatchDesc) * pd.size(), b->s));
         chk(cudaMallocAsync((void **)&b->d_media, sizeof(MediumDev) * nmedia, b->s));
         chk(cudaMallocAsync((void **)&b->d_cfl, sizeof(unsigned long long), b->s));
+        chk(cudaMallocAsync((void **)&b->d_wctr, sizeof(unsigned long long), b->s));
         if (e != cudaSuccess) {
             adjamr_batch_destroy(b);
             return ADJAMR_ENOMEM;
@@ -287,7 +297,7 @@ adjamr_status adjamr_batch_set_ghost_fusion(adjamr_batch *b, int fuse_ghosts)
 
 adjamr_status adjamr_batch_step(adjamr_batch *b, int nsteps, int mode, int tx, int ty)
 {
-    if (!b || nsteps < 0) return ADJAMR_EINVAL;
+    if (!b || nsteps < 0 || mode < ADJAMR_LAUNCH_WORKLIST || mode > ADJAMR_LAUNCH_DYNAMIC) return ADJAMR_EINVAL;
     if (build_work(b, tx, ty) != cudaSuccess) return ADJAMR_ECUDA;
     if (step_occupancy(2, 0, tx, ty) <= 0) return ADJAMR_EINVAL;
     for (int s = 0; s < nsteps; s++) {
@@ -302,7 +312,7 @@ adjamr_status adjamr_batch_step(adjamr_batch *b, int nsteps, int mode, int tx, i
 
 adjamr_status adjamr_batch_step_graph(adjamr_batch *b, int nsteps, int mode, int tx, int ty)
 {
-    if (!b || nsteps < 0) return ADJAMR_EINVAL;
+    if (!b || nsteps < 0 || mode < ADJAMR_LAUNCH_WORKLIST || mode > ADJAMR_LAUNCH_DYNAMIC) return ADJAMR_EINVAL;
     if (build_work(b, tx, ty) != cudaSuccess) return ADJAMR_ECUDA;
     if (step_occupancy(2, 0, tx, ty) <= 0) return ADJAMR_EINVAL;
     if (b->s == nullptr) return ADJAMR_ESTATE;  // capture needs a non-default stream
@@ -375,7 +385,8 @@ void adjamr_batch_destroy(adjamr_batch *b)
     if (!b) return;
     drop_graphs(b);
     cudaStream_t s = b->s;
-    void *ptrs[] = {b->q[0], b->q[1], b->aux, b->med, b->d_patches, b->d_ghost, b->d_work, b->d_media, b->d_cfl};
+    void *ptrs[] = {b->q[0], b->q[1], b->aux, b->med, b->d_patches, b->d_ghost, b->d_work, b->d_media, b->d_cfl,
+                    b->d_wctr};
     for (void *p : ptrs)
         if (p) cudaFreeAsync(p, s);
     cudaStreamSynchronize(s);

@@ -47,6 +47,7 @@ struct Level {
     PatchDesc *d_patches = nullptr;
     WorkItem *d_work = nullptr;
     int nwork = 0, work_tx = 0, work_ty = 0;
+    bool work_lpt = false;
     std::vector<WorkItem> h_work;
     GhostDesc *d_ghost = nullptr;
     long long nghost = 0;
@@ -122,6 +123,9 @@ struct adjamr_ctx {
     int tx = 32, ty = 8, launch_mode = 0, grid_persistent = 0, nsm = 0;
     int ltx[ADJAMR_MAX_LEVELS] = {}, lty[ADJAMR_MAX_LEVELS] = {}, lgrid[ADJAMR_MAX_LEVELS] = {};
     int lfuse[ADJAMR_MAX_LEVELS] = {};  // ghost ring computed inside the step kernel
+    int lmode[ADJAMR_MAX_LEVELS] = {};  // ADJAMR_LAUNCH_* per level
+    unsigned long long *d_wctr = nullptr;  // tile counter of the dynamic launch mode
+    unsigned long long wbase = 0;          // its value at the start of the next dynamic launch
     bool timing = false;
     // gauges: cell indices per level (device), records on the device
     int ngauge = 0;
@@ -251,7 +255,8 @@ cudaError_t upload_packed(adjamr_ctx *c, const std::vector<std::pair<const void 
 adjamr_status build_work(adjamr_ctx *c, int l, int tx, int ty)
 {
     Level &L = c->L[l];
-    if (L.work_tx == tx && L.work_ty == ty && L.d_work) return ADJAMR_OK;
+    const bool lpt = c->lmode[l] != ADJAMR_LAUNCH_PER_PATCH;
+    if (L.work_tx == tx && L.work_ty == ty && L.d_work && L.work_lpt == lpt) return ADJAMR_OK;
     dfree(L.d_work, c->s);
     L.h_work.clear();
     const int tyy = (c->P.dim == 2) ? ty : 1;
@@ -265,7 +270,7 @@ adjamr_status build_work(adjamr_ctx *c, int l, int tx, int ty)
     }
     // one launch over the level: largest tiles first, so that the last CTAs
     // to start are the short ones (one launch per patch keeps patch order)
-    if (c->launch_mode != ADJAMR_LAUNCH_PER_PATCH)
+    if (lpt)
         std::stable_sort(L.h_work.begin(), L.h_work.end(), [](const WorkItem &a, const WorkItem &b) {
             return (int)a.tx * a.ty > (int)b.tx * b.ty;
         });
@@ -276,6 +281,7 @@ adjamr_status build_work(adjamr_ctx *c, int l, int tx, int ty)
     L.d_work = reinterpret_cast<WorkItem *>(dw);
     L.work_tx = tx;
     L.work_ty = ty;
+    L.work_lpt = lpt;
     return ADJAMR_OK;
 }
 
@@ -1113,7 +1119,8 @@ adjamr_status step_patches(adjamr_ctx *c, int l, int k, GhostMode gm)
     if (gm == GHOST_FILL) TRY(ghost_fill(c, l, k));
     const double *q = L.q[L.cur];
     double *qn = L.q[1 - L.cur];
-    if (c->launch_mode == ADJAMR_LAUNCH_PER_PATCH) {
+    const int mode = c->lmode[l];
+    if (mode == ADJAMR_LAUNCH_PER_PATCH) {
         int w0 = 0;
         for (int k = 0; k < (int)L.patches.size(); k++) {
             int w1 = w0;
@@ -1127,9 +1134,15 @@ adjamr_status step_patches(adjamr_ctx *c, int l, int k, GhostMode gm)
         }
     } else {
         int grid = 0;
-        if (c->launch_mode == ADJAMR_LAUNCH_PERSISTENT) grid = std::min(L.nwork, c->lgrid[l]);
+        TileSched sc{nullptr, 0};
+        if (mode == ADJAMR_LAUNCH_PERSISTENT || mode == ADJAMR_LAUNCH_DYNAMIC) grid = std::min(L.nwork, c->lgrid[l]);
+        if (mode == ADJAMR_LAUNCH_DYNAMIC) {
+            sc.ctr = c->d_wctr;
+            sc.base = c->wbase;
+            c->wbase += (unsigned long long)L.nwork + (unsigned long long)grid;
+        }
         CKR(c, launch_step(c->P.dim, c->P.eqn, c->ltx[l], c->lty[l], q, qn, L.aux, L.ncell, L.d_patches, L.d_work,
-                           L.nwork, grid, c->d_cfl, c->s, ga));
+                           L.nwork, grid, c->d_cfl, c->s, ga, sc));
         c->st.kernel_launches++;
         c->st.step_kernel_launches++;
         c->st.level_step_launches[l]++;
@@ -1273,6 +1286,7 @@ adjamr_status create_impl(const adjamr_params *p, adjamr_ctx **out)
     for (int k = 0; k < 4; k++)
         if (p->bc[k] < 0 || p->bc[k] > 2) return ADJAMR_EINVAL;
     if (p->flag_mode < ADJAMR_FLAG_BRACKET_MAX || p->flag_mode > ADJAMR_FLAG_SURFACE) return ADJAMR_EINVAL;
+    if (p->launch_mode < ADJAMR_LAUNCH_WORKLIST || p->launch_mode > ADJAMR_LAUNCH_DYNAMIC) return ADJAMR_EINVAL;
     adjamr_ctx *c = new (std::nothrow) adjamr_ctx();
     if (!c) return ADJAMR_ENOMEM;
     c->P = *p;
@@ -1313,6 +1327,7 @@ adjamr_status create_impl(const adjamr_params *p, adjamr_ctx **out)
         c->lty[l] = c->ty;
         c->lgrid[l] = c->grid_persistent;
         c->lfuse[l] = 1;
+        c->lmode[l] = p->launch_mode;
     }
     int N = p->n0[0], M = (p->dim == 2) ? p->n0[1] : 1;
     for (int l = 0; l < p->nlevels; l++) {
@@ -1352,11 +1367,13 @@ adjamr_status create_impl(const adjamr_params *p, adjamr_ctx **out)
     if (cudaMalloc(&c->d_cfl, sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc(&c->d_count, sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc(&c->d_fout, sizeof(double)) != cudaSuccess || cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&c->d_bbox, 4 * sizeof(int)) != cudaSuccess) {
+        cudaMalloc(&c->d_bbox, 4 * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&c->d_wctr, sizeof(unsigned long long)) != cudaSuccess) {
         adjamr_destroy(c);
         return ADJAMR_ENOMEM;
     }
     cudaMemsetAsync(c->d_cfl, 0, sizeof(unsigned long long), c->s);
+    cudaMemsetAsync(c->d_wctr, 0, sizeof(unsigned long long), c->s);
     cudaMemsetAsync(c->d_err, 0, sizeof(int), c->s);
     cudaEventCreate(&c->ev0);
     cudaEventCreate(&c->ev1);
@@ -1959,9 +1976,11 @@ adjamr_status adjamr_step_level_only(adjamr_ctx *ctx, int level)
     return ADJAMR_OK;
 }
 
-adjamr_status adjamr_set_level_kernel(adjamr_ctx *ctx, int level, int tile_x, int tile_y, int fuse_ghosts)
+adjamr_status adjamr_set_level_kernel(adjamr_ctx *ctx, int level, int tile_x, int tile_y, int fuse_ghosts,
+                                      int launch_mode)
 {
     if (!ctx || level < -1 || level >= ctx->P.nlevels) return ADJAMR_EINVAL;
+    if (launch_mode < -1 || launch_mode > ADJAMR_LAUNCH_DYNAMIC) return ADJAMR_EINVAL;
     int ty = (ctx->P.dim == 2) ? tile_y : 1;
     int occ = 0;
     if (ctx->P.dim == 2) {
@@ -1977,6 +1996,7 @@ adjamr_status adjamr_set_level_kernel(adjamr_ctx *ctx, int level, int tile_x, in
         ctx->lty[l] = ty;
         ctx->lgrid[l] = ctx->nsm * std::max(occ, 1);
         ctx->lfuse[l] = fuse_ghosts != 0;
+        if (launch_mode >= 0) ctx->lmode[l] = launch_mode;
     }
     return ADJAMR_OK;
 }
@@ -2025,6 +2045,7 @@ void adjamr_destroy(adjamr_ctx *ctx)
     if (ctx->d_fout) cudaFree(ctx->d_fout);
     if (ctx->d_err) cudaFree(ctx->d_err);
     if (ctx->d_bbox) cudaFree(ctx->d_bbox);
+    if (ctx->d_wctr) cudaFree(ctx->d_wctr);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     for (cudaEvent_t e : ctx->tev) cudaEventDestroy(e);

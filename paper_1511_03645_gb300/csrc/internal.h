@@ -119,10 +119,21 @@ struct GhostArgs {
     double th;  // k / r, divided on the host
 };
 
+// Tile schedule of a step launch.  ctr == nullptr: CTA b takes tiles b,
+// b + grid, ...  Otherwise every CTA takes the next tile from the counter
+// (dynamic balancing); tile = counter - base, and the launch advances the
+// counter by exactly nwork + grid (its tiles plus one fetch past the end per
+// CTA), so consecutive launches on a stream chain their bases.
+struct TileSched {
+    unsigned long long *ctr;
+    unsigned long long base;
+};
+
 // ---- kernel launchers (kernels_step.cu / kernels_amr.cu) ----
 cudaError_t launch_step(int dim, int eqn, int tx, int ty, const double *q, double *qn, const double *aux,
                         long long stride, const PatchDesc *patches, const WorkItem *work, int nwork, int grid,
-                        unsigned long long *cfl_bits, cudaStream_t s, GhostArgs ga = GhostArgs{nullptr, nullptr, nullptr, 0, 0, 0.0});
+                        unsigned long long *cfl_bits, cudaStream_t s, GhostArgs ga = GhostArgs{nullptr, nullptr, nullptr, 0, 0, 0.0},
+                        TileSched sc = TileSched{nullptr, 0});
 int step_occupancy(int dim, int eqn, int tx, int ty);
 
 cudaError_t launch_ghost_fill(int dim, int m, const GhostDesc *g, long long n, double *qf, long long sf,

@@ -219,6 +219,15 @@ __device__ __forceinline__ void cfl_reduce(long long c, unsigned long long *cfl_
     if ((threadIdx.x & 31) == 0 && c > 0) atomicMax(cfl_bits, (unsigned long long)c);
 }
 
+// next tile of this CTA (see TileSched); w_static = the strided choice
+__device__ __forceinline__ int fetch_tile(const TileSched &sc, int *slot, int w_static)
+{
+    if (!sc.ctr) return w_static;
+    if (threadIdx.x == 0) *slot = (int)(atomicAdd(sc.ctr, 1ull) - sc.base);
+    __syncthreads();
+    return *slot;
+}
+
 // ---------------------------------------------------------------- 2D
 template <int EQN, int TX, int TY>
 struct Smem2D {
@@ -241,7 +250,7 @@ __global__ void __launch_bounds__(kThreads) k_step2d(const double *__restrict__ 
                                                      const double *__restrict__ aux, long long stride,
                                                      const PatchDesc *__restrict__ patches,
                                                      const WorkItem *__restrict__ work, int nwork,
-                                                     unsigned long long *cfl_bits, GhostArgs ga)
+                                                     unsigned long long *cfl_bits, GhostArgs ga, TileSched sc)
 {
     using S = Smem2D<EQN, TX, TY>;
     extern __shared__ double sm[];
@@ -267,7 +276,8 @@ __global__ void __launch_bounds__(kThreads) k_step2d(const double *__restrict__ 
 
     const int tid = threadIdx.x;
     long long cfl = 0;
-    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+    __shared__ int s_next;
+    for (int w = fetch_tile(sc, &s_next, blockIdx.x); w < nwork; w = fetch_tile(sc, &s_next, w + gridDim.x)) {
         const WorkItem wi = work[w];
         const PatchDesc P = patches[wi.patch];
         const int x0 = wi.x0, y0 = wi.y0;
@@ -480,7 +490,7 @@ __global__ void __launch_bounds__(kThreads) k_step1d(const double *__restrict__ 
                                                      const double *__restrict__ aux, long long stride,
                                                      const PatchDesc *__restrict__ patches,
                                                      const WorkItem *__restrict__ work, int nwork,
-                                                     unsigned long long *cfl_bits, GhostArgs ga)
+                                                     unsigned long long *cfl_bits, GhostArgs ga, TileSched sc)
 {
     using S = Smem1D<EQN, TX>;
     extern __shared__ double sm[];
@@ -492,7 +502,8 @@ __global__ void __launch_bounds__(kThreads) k_step1d(const double *__restrict__ 
     double *XN = XF + 4 * XE;
     const int tid = threadIdx.x;
     long long cfl = 0;
-    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+    __shared__ int s_next;
+    for (int w = fetch_tile(sc, &s_next, blockIdx.x); w < nwork; w = fetch_tile(sc, &s_next, w + gridDim.x)) {
         const WorkItem wi = work[w];
         const PatchDesc P = patches[wi.patch];
         const int x0 = wi.x0;
@@ -576,26 +587,26 @@ cudaError_t ensure_smem_attr(size_t smem)
 template <auto Kern>
 cudaError_t launch_kernel(size_t smem, int nwork, int grid, const double *q, double *qn, const double *aux,
                           long long stride, const PatchDesc *patches, const WorkItem *work,
-                          unsigned long long *cfl_bits, cudaStream_t s, const GhostArgs &ga)
+                          unsigned long long *cfl_bits, cudaStream_t s, const GhostArgs &ga, const TileSched &sc)
 {
     auto kern = Kern;
     cudaError_t e = ensure_smem_attr<Kern>(smem);
     if (e != cudaSuccess) return e;
     if (nwork <= 0) return cudaSuccess;
     int g = grid > 0 ? grid : nwork;
-    kern<<<g, kThreads, smem, s>>>(q, qn, aux, stride, patches, work, nwork, cfl_bits, ga);
+    kern<<<g, kThreads, smem, s>>>(q, qn, aux, stride, patches, work, nwork, cfl_bits, ga, sc);
     return cudaGetLastError();
 }
 
 template <int EQN>
 cudaError_t dispatch2d(int tx, int ty, int nwork, int grid, const double *q, double *qn, const double *aux,
                        long long stride, const PatchDesc *p, const WorkItem *w, unsigned long long *c,
-                       cudaStream_t s, const GhostArgs &ga)
+                       cudaStream_t s, const GhostArgs &ga, const TileSched &sc)
 {
 #define ADJ_TILE(X, Y)                                                                                    \
     if (tx == X && ty == Y)                                                                               \
         return launch_kernel<k_step2d<EQN, X, Y>>(Smem2D<EQN, X, Y>::bytes, nwork, grid, q, qn, aux, stride, p, w, \
-                                                  c, s, ga);
+                                                  c, s, ga, sc);
     ADJ_TILE(32, 8)
     ADJ_TILE(16, 8)
     ADJ_TILE(16, 16)
@@ -609,14 +620,14 @@ cudaError_t dispatch2d(int tx, int ty, int nwork, int grid, const double *q, dou
 template <int EQN>
 cudaError_t dispatch1d(int tx, int nwork, int grid, const double *q, double *qn, const double *aux, long long stride,
                        const PatchDesc *p, const WorkItem *w, unsigned long long *c, cudaStream_t s,
-                       const GhostArgs &ga)
+                       const GhostArgs &ga, const TileSched &sc)
 {
     if (tx == 256)
         return launch_kernel<k_step1d<EQN, 256>>(Smem1D<EQN, 256>::bytes, nwork, grid, q, qn, aux, stride, p, w, c, s,
-                                                 ga);
+                                                 ga, sc);
     if (tx == 128)
         return launch_kernel<k_step1d<EQN, 128>>(Smem1D<EQN, 128>::bytes, nwork, grid, q, qn, aux, stride, p, w, c, s,
-                                                 ga);
+                                                 ga, sc);
     return cudaErrorInvalidValue;
 }
 
@@ -644,20 +655,20 @@ int occ2d(int tx, int ty)
 
 cudaError_t launch_step(int dim, int eqn, int tx, int ty, const double *q, double *qn, const double *aux,
                         long long stride, const PatchDesc *patches, const WorkItem *work, int nwork, int grid,
-                        unsigned long long *cfl_bits, cudaStream_t s, GhostArgs ga)
+                        unsigned long long *cfl_bits, cudaStream_t s, GhostArgs ga, TileSched sc)
 {
     if (dim == 1) {
         switch (eqn) {
-        case 0: return dispatch1d<0>(tx, nwork, grid, q, qn, aux, stride, patches, work, cfl_bits, s, ga);
-        case 1: return dispatch1d<1>(tx, nwork, grid, q, qn, aux, stride, patches, work, cfl_bits, s, ga);
+        case 0: return dispatch1d<0>(tx, nwork, grid, q, qn, aux, stride, patches, work, cfl_bits, s, ga, sc);
+        case 1: return dispatch1d<1>(tx, nwork, grid, q, qn, aux, stride, patches, work, cfl_bits, s, ga, sc);
         default: return cudaErrorInvalidValue;
         }
     }
     switch (eqn) {
-    case 0: return dispatch2d<0>(tx, ty, nwork, grid, q, qn, aux, stride, patches, work, cfl_bits, s, ga);
-    case 1: return dispatch2d<1>(tx, ty, nwork, grid, q, qn, aux, stride, patches, work, cfl_bits, s, ga);
-    case 2: return dispatch2d<2>(tx, ty, nwork, grid, q, qn, aux, stride, patches, work, cfl_bits, s, ga);
-    case 3: return dispatch2d<3>(tx, ty, nwork, grid, q, qn, aux, stride, patches, work, cfl_bits, s, ga);
+    case 0: return dispatch2d<0>(tx, ty, nwork, grid, q, qn, aux, stride, patches, work, cfl_bits, s, ga, sc);
+    case 1: return dispatch2d<1>(tx, ty, nwork, grid, q, qn, aux, stride, patches, work, cfl_bits, s, ga, sc);
+    case 2: return dispatch2d<2>(tx, ty, nwork, grid, q, qn, aux, stride, patches, work, cfl_bits, s, ga, sc);
+    case 3: return dispatch2d<3>(tx, ty, nwork, grid, q, qn, aux, stride, patches, work, cfl_bits, s, ga, sc);
     default: return cudaErrorInvalidValue;
     }
 }

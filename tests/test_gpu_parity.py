@@ -97,7 +97,7 @@ def test_uniform_grid_steps_match_oracle_bitwise(A, dim, eqn, bc):
 
 
 @pytest.mark.parametrize("tile", [(16, 8), (16, 16), (32, 16), (64, 8), (8, 8)])
-@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
 def test_tile_shapes_and_launch_modes_agree_bitwise(A, tile, mode):
     """Every tile shape and launch mode (work-list, persistent, per patch)
     computes the same bits as the default configuration."""
@@ -206,20 +206,21 @@ def test_amr_run_matches_oracle(A, which):
 
 def test_per_level_kernels_compute_the_same_bits(A):
     """A different step-kernel tile on each level, with the ghost ring computed
-    inside the step kernel or by the separate fill kernel, changes nothing in
-    the results; the per-level statistics add up to the totals."""
+    inside the step kernel or by the separate fill kernel, and with strided,
+    per-patch or dynamically fetched tiles, changes nothing in the results;
+    the per-level statistics add up to the totals."""
     wl = W.config2(seed=3, n0=32, ratios=(2, 4), tf=2.0, adj_n=64, nsnap=20, ts=0.0, tol=1e-4,
                    min_patch=8, max_patch=32)
     adj = A.solve_adjoint(wl)
     runs = []
-    for cfg in (None, [((8, 8), False), ((16, 16), True), ((64, 8), False)],
-                [((32, 16), True), ((16, 8), False), ((8, 8), True)]):
+    for cfg in (None, [((8, 8), False, 3), ((16, 16), True, 0), ((64, 8), False, 3)],
+                [((32, 16), True, 3), ((16, 8), False, 1), ((8, 8), True, 3)]):
         h = A.Hierarchy(wl)
         h.set_adjoint(adj)
         h.set_timing(True)
         if cfg:
-            for lev, (t, fuse) in enumerate(cfg):
-                h.set_level_kernel(lev, t, fuse)
+            for lev, (t, fuse, mode) in enumerate(cfg):
+                h.set_level_kernel(lev, t, fuse, mode)
         h.regrid(0, init=True)
         h.advance(h.nsteps_total())
         st = h.stats()
@@ -239,6 +240,8 @@ def test_per_level_kernels_compute_the_same_bits(A):
         h.set_level_kernel(0, (24, 8))
     with pytest.raises(A.AdjamrError):
         h.set_level_kernel(wl.nlevels, (32, 8))
+    with pytest.raises(A.AdjamrError):
+        h.set_level_kernel(0, (32, 8), True, 4)
     h.close()
 
 
@@ -323,7 +326,8 @@ def test_batched_patches_modes_agree_and_match_oracle(A):
     pb = W.config4(seed=0)
     results = []
     for mode, graph, fuse in ((0, False, False), (1, False, False), (2, False, False), (0, True, False),
-                              (1, True, False), (0, False, True), (1, True, True), (2, False, True)):
+                              (1, True, False), (0, False, True), (1, True, True), (2, False, True),
+                              (3, False, False), (3, True, True)):
         import torch
         s = torch.cuda.Stream()
         b = A.Batch(pb, stream=s.cuda_stream)
