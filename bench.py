@@ -351,8 +351,10 @@ def run_ours(args, rank, world):
                        "regrid flag bitmaps also cross (internal)"}
 
     flaggers = None
+    paper = None
     if rank == 0:
         flaggers = compare_flaggers(A, W, wl, adj, adj_s, s, tuned)
+        paper = paper_table(A, W, s)
 
     serving = None
     if rank == 0 and args.serve_sample > 0:
@@ -394,6 +396,7 @@ def run_ours(args, rank, world):
         "fp64_peak": {"dfma_tflops": peak_fma / 1e12, "dadd_tflops": peak_add / 1e12},
         "batched": batched,
         "flaggers": flaggers,
+        "paper_sec_5_2": paper,
         "serving": serving,
         "e2e": e2e,
         "cpu_baseline": cpu,
@@ -484,7 +487,7 @@ def run_case_serve(args):
     from paper_1511_03645_gb300 import workloads as W
     torch.cuda.set_device(0)
     A.load()
-    res = serve_stream(A, W, args.nreq, [0.5, 0.8, 1.0], args.slots)
+    res = serve_stream(A, W, args.nreq, [float(v) for v in args.rates.split(",")], args.slots)
     print(json.dumps({"case": "serve", **res}), flush=True)
 
 
@@ -585,6 +588,76 @@ def compare_flaggers(A, W, wl, adj, adj_s, s, tuned=None, diff_tols=(0.1, 0.03, 
     return out
 
 
+PAPER_TABLE_5_2_4 = {  # Sec. 5.2.4 (a laptop): pressure-flagging; adjoint-flagging forward, adjoint solve (s)
+    "timepoint_walls": (3.137, 1.325, 0.465),
+    "range_walls": (15.664, 6.866, 0.683),
+    "range_mixed": (13.504, 5.492, 0.666),
+}
+
+
+def paper_table(A, W, s, reps=3):
+    """The Sec. 5.2 examples at the paper's sizes on this GPU: adjoint solve,
+    adjoint-flagged forward solve (tol 0.02) and pressure-flagged forward solve
+    (undivided differences, tol 0.1), best of `reps` wall times each, and the
+    gauge at (3.5, 0.5) from both forward runs."""
+    import copy
+    import torch
+    out = {}
+    for v in W.PAPER_5_2_VARIANTS:
+        wl = W.paper_5_2(v)
+        gx, gy = wl.extra["gauge"]
+        best_adj = None
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            adj = A.solve_adjoint(wl, stream=s.cuda_stream)
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t
+            if best_adj is None or el < best_adj[0]:
+                best_adj = (el, adj)
+        res = {"adjoint_solve_s": best_adj[0]}
+        gauges = {}
+        for name, mode, tol in (("adjoint_flagging", W.FLAG_BRACKET_MAX, wl.tol), ("pressure_flagging",
+                                                                                   W.FLAG_DIFFERENCE, 0.1)):
+            w = copy.copy(wl)
+            w.flag_mode, w.tol = mode, tol
+            best = None
+            for _ in range(reps):
+                h = A.Hierarchy(w, stream=s.cuda_stream)
+                h.set_adjoint(best_adj[1])
+                h.set_gauges([gx], [gy])
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                h.regrid(0, init=True)
+                h.advance(h.nsteps_total())
+                J = h.functional()
+                torch.cuda.synchronize()
+                el = time.perf_counter() - t
+                if best is None or el < best[0]:
+                    best = (el, h.stats()["cell_updates"], J, h.gauges()[:, 0, 1])
+                h.close()
+            res[name] = {"tol": tol, "forward_s": best[0], "cell_updates": best[1], "J": best[2]}
+            gauges[name] = best[3]
+        res["gauge_max_abs_diff"] = float(np.max(np.abs(gauges["adjoint_flagging"] - gauges["pressure_flagging"])))
+        res["gauge_peak_abs"] = float(np.max(np.abs(gauges["pressure_flagging"])))
+        pp, pf, pa = PAPER_TABLE_5_2_4[v]
+        res["paper_laptop_s"] = {"pressure_flagging": pp, "adjoint_flagging_forward": pf, "adjoint_solve": pa}
+        best_adj[1].release()
+        out[v] = res
+    return out
+
+
+def run_case_paper(args):
+    """The paper's Sec. 5.2.4 timing table, reproduced on this GPU."""
+    import torch
+    from paper_1511_03645_gb300 import adjamr as A
+    from paper_1511_03645_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    A.load()
+    s = torch.cuda.Stream()
+    print(json.dumps({"case": "paper", "sec_5_2": paper_table(A, W, s)}), flush=True)
+
+
 def run_case_solve(args):
     """Profiling case: one config-2 forward solve to --tf (adjoint solved
     first) with the step-kernel tile and ghost mode of every level given by
@@ -632,11 +705,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--case", default="main", choices=["main", "batch", "serve", "solve"])
+    ap.add_argument("--case", default="main", choices=["main", "batch", "serve", "solve", "paper"])
     ap.add_argument("--tf", type=float, default=0.0, help="solve case: final time (0: the workload's)")
     ap.add_argument("--kernels", default="8x8f,8x8f,16x8",
                     help="solve case: per-level step tile, suffix f = ghost ring computed in the step kernel")
     ap.add_argument("--nreq", type=int, default=512)
+    ap.add_argument("--rates", default="0.5,0.8,1.0", help="serve case: offered rates as fractions of saturation")
     ap.add_argument("--slots", type=int, default=16)
     ap.add_argument("--serve-sample", type=int, default=32)
     args = ap.parse_args()
@@ -648,6 +722,9 @@ def main():
         return
     if args.case == "solve":
         run_case_solve(args)
+        return
+    if args.case == "paper":
+        run_case_paper(args)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

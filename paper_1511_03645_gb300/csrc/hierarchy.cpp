@@ -17,6 +17,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "internal.h"
@@ -111,7 +112,19 @@ struct adjamr_ctx {
     size_t h_stage_bytes[2] = {0, 0};
     cudaEvent_t stage_ev[2] = {nullptr, nullptr};
     int stage_slot = 0;
+    // device blocks released by regrids, reused by later ones (the stream
+    // orders every use, as with cudaFreeAsync): sizes of every block handed
+    // out, and the cached ones
+    std::unordered_map<void *, size_t> blk_size;
+    std::vector<std::pair<size_t, void *>> blk_free;
+    size_t blk_free_bytes = 0;
+    size_t blk_cache_cap = (size_t)512 << 20;  // bytes the cache may hold (0: no caching)
     uint64_t *d_flagbuf = nullptr;  // flag bitmap of the level being regridded
+    // pinned readback of the flag count, bounding box and (when small) the
+    // whole bitmap: one synchronisation per flagged level
+    char *h_pin = nullptr;
+    size_t h_pin_bytes = 0;
+    bool pin_has_bits = false;
     // per-level bilinear tables of the adjoint grid for the dense flag kernel
     char *d_ftab[ADJAMR_MAX_LEVELS] = {};
     int ftab_ax[ADJAMR_MAX_LEVELS] = {}, ftab_ay[ADJAMR_MAX_LEVELS] = {};
@@ -141,6 +154,76 @@ struct adjamr_ctx {
 };
 
 namespace {
+
+// device block from the context's cache (best fit up to twice the size),
+// else a new stream-ordered allocation
+template <typename T>
+cudaError_t cget(adjamr_ctx *c, T **p, size_t n)
+{
+    *p = nullptr;
+    if (n == 0) return cudaSuccess;
+    const size_t bytes = (n * sizeof(T) + 255) / 256 * 256;
+    int best = -1;
+    for (int k = 0; k < (int)c->blk_free.size(); k++) {
+        const size_t b = c->blk_free[k].first;
+        if (b >= bytes && b <= 2 * bytes + 65536 && (best < 0 || b < c->blk_free[best].first)) best = k;
+    }
+    if (best >= 0) {
+        *p = static_cast<T *>(c->blk_free[best].second);
+        c->blk_free_bytes -= c->blk_free[best].first;
+        c->blk_free.erase(c->blk_free.begin() + best);
+        return cudaSuccess;
+    }
+    void *q = nullptr;
+    cudaError_t e = cudaMallocAsync(&q, bytes, c->s);
+    if (e != cudaSuccess) return e;
+    c->blk_size[q] = bytes;
+    *p = static_cast<T *>(q);
+    return cudaSuccess;
+}
+
+// return a block to the cache (blocks not from cget are freed)
+constexpr size_t kBlockCacheMax = 48;
+template <typename T>
+void cput(adjamr_ctx *c, T *&p)
+{
+    if (!p) return;
+    void *q = (void *)p;
+    p = nullptr;
+    auto it = c->blk_size.find(q);
+    if (it == c->blk_size.end()) {
+        cudaFreeAsync(q, c->s);
+        return;
+    }
+    c->blk_free.push_back({it->second, q});
+    c->blk_free_bytes += it->second;
+    while (!c->blk_free.empty() && (c->blk_free.size() > kBlockCacheMax || c->blk_free_bytes > c->blk_cache_cap)) {
+        void *old = c->blk_free.front().second;
+        c->blk_free_bytes -= c->blk_free.front().first;
+        c->blk_free.erase(c->blk_free.begin());
+        c->blk_size.erase(old);
+        cudaFreeAsync(old, c->s);
+    }
+}
+
+}  // namespace
+
+namespace adjamr {
+void ctx_set_block_cache(adjamr_ctx *c, size_t cap_bytes) { c->blk_cache_cap = cap_bytes; }
+}  // namespace adjamr
+
+namespace {
+
+void cache_drain(adjamr_ctx *c)
+{
+    for (auto &b : c->blk_free) {
+        c->blk_size.erase(b.second);
+        cudaFreeAsync(b.second, c->s);
+    }
+    c->blk_free.clear();
+    c->blk_free_bytes = 0;
+}
+
 
 #define CKR(ctx, x)                                                                                   \
     do {                                                                                              \
@@ -221,11 +304,11 @@ int find_patch(Level &L, int I, int J)
 void free_level(adjamr_ctx *c, Level &L)
 {
     cudaStream_t s = c->s;
-    dfree(L.d_arena, s);
+    cput(c, L.d_arena);
     L.q[0] = L.q[1] = nullptr;
     L.aux = L.med = nullptr;
     if (L.d_meta) {
-        dfree(L.d_meta, s);
+        cput(c, L.d_meta);
         L.d_patches = nullptr;
         L.d_prefix = L.d_gprefix = L.d_sprefix = L.d_aprefix = nullptr;
     } else {
@@ -235,10 +318,10 @@ void free_level(adjamr_ctx *c, Level &L)
         dfree(L.d_sprefix, s);
         dfree(L.d_aprefix, s);
     }
-    dfree(L.d_work, s);
-    dfree(L.d_ghost, s);
-    dfree(L.d_avg, s);
-    dfree(L.d_owner, s);
+    cput(c, L.d_work);
+    cput(c, L.d_ghost);
+    cput(c, L.d_avg);
+    cput(c, L.d_owner);
     L.patches.clear();
     L.h_work.clear();
     L.buckets.clear();
@@ -249,6 +332,7 @@ void free_level(adjamr_ctx *c, Level &L)
 }
 
 // (re)build the tile work-list of a level for tile (tx, ty)
+
 cudaError_t upload_packed(adjamr_ctx *c, const std::vector<std::pair<const void *, size_t>> &chunks, char **dev,
                           std::vector<size_t> &offs);
 
@@ -257,7 +341,7 @@ adjamr_status build_work(adjamr_ctx *c, int l, int tx, int ty)
     Level &L = c->L[l];
     const bool lpt = c->lmode[l] != ADJAMR_LAUNCH_PER_PATCH;
     if (L.work_tx == tx && L.work_ty == ty && L.d_work && L.work_lpt == lpt) return ADJAMR_OK;
-    dfree(L.d_work, c->s);
+    cput(c, L.d_work);
     L.h_work.clear();
     const int tyy = (c->P.dim == 2) ? ty : 1;
     for (int k = 0; k < (int)L.patches.size(); k++) {
@@ -321,7 +405,7 @@ cudaError_t upload_packed(adjamr_ctx *c, const std::vector<std::pair<const void 
     }
     for (size_t k = 0; k < chunks.size(); k++)
         if (chunks[k].second) std::memcpy(c->h_stage[sl] + offs[k], chunks[k].first, chunks[k].second);
-    e = cudaMallocAsync((void **)dev, total, c->s);
+    e = cget(c, dev, total);
     if (e != cudaSuccess) return e;
     e = cudaMemcpyAsync(*dev, c->h_stage[sl], total, cudaMemcpyHostToDevice, c->s);
     if (e != cudaSuccess) return e;
@@ -382,7 +466,7 @@ adjamr_status alloc_level(adjamr_ctx *c, int l, const std::vector<Box> &boxes)
     // (no clearing: every ghost cell is written by the ghost fill before it is
     // read, every interior cell by the initialisation or the step)
     // one allocation: q[0] | q[1] | aux | med
-    CKR(c, dalloc(&L.d_arena, (size_t)(2 * c->m + c->naux + c->nmed) * L.ncell, c->s));
+    CKR(c, cget(c, &L.d_arena, (size_t)(2 * c->m + c->naux + c->nmed) * L.ncell));
     L.q[0] = L.d_arena;
     L.q[1] = L.d_arena ? L.q[0] + (size_t)c->m * L.ncell : nullptr;
     L.aux = L.d_arena ? L.q[1] + (size_t)c->m * L.ncell : nullptr;
@@ -399,7 +483,7 @@ adjamr_status alloc_level(adjamr_ctx *c, int l, const std::vector<Box> &boxes)
         L.d_sprefix = (long long *)(L.d_meta + offs[3]);
         L.d_aprefix = (long long *)(L.d_meta + offs[4]);
     }
-    CKR(c, dalloc(&L.d_owner, (size_t)L.N * L.M, c->s));
+    CKR(c, cget(c, &L.d_owner, (size_t)L.N * L.M));
     CKR(c, cudaMemsetAsync(L.d_owner, 0xff, sizeof(int) * (size_t)L.N * L.M, c->s));
     if (!L.patches.empty()) {
         CKR(c, launch_owner_fill(L.d_patches, L.d_prefix, (int)L.patches.size(), L.ninterior, idx_of(c, l), L.d_owner,
@@ -440,10 +524,10 @@ adjamr_status fill_aux(adjamr_ctx *c, int l)
 adjamr_status build_ghost_map(adjamr_ctx *c, int l)
 {
     Level &L = c->L[l];
-    dfree(L.d_ghost, c->s);
+    cput(c, L.d_ghost);
     L.nghost = L.nghost_cells;
     if (L.nghost == 0) return ADJAMR_OK;
-    CKR(c, dalloc(&L.d_ghost, (size_t)L.nghost, c->s));
+    CKR(c, cget(c, &L.d_ghost, (size_t)L.nghost));
     const int *oc = (l > 0) ? c->L[l - 1].d_owner : nullptr;
     LevelIdx gc = (l > 0) ? idx_of(c, l - 1) : idx_of(c, l);
     int r = (l > 0) ? c->P.ratio[l - 1] : 1;
@@ -457,10 +541,10 @@ adjamr_status build_ghost_map(adjamr_ctx *c, int l)
 adjamr_status build_avg_map(adjamr_ctx *c, int l)
 {
     Level &F = c->L[l];
-    dfree(F.d_avg, c->s);
+    cput(c, F.d_avg);
     F.navg = F.navg_cells;
     if (F.navg == 0) return ADJAMR_OK;
-    CKR(c, dalloc(&F.d_avg, (size_t)F.navg, c->s));
+    CKR(c, cget(c, &F.d_avg, (size_t)F.navg));
     CKR(c, launch_avg_build(F.d_patches, F.d_aprefix, (int)F.patches.size(), F.navg, c->P.dim, c->P.ratio[l - 1],
                             c->L[l - 1].d_owner, idx_of(c, l - 1), F.d_avg, c->d_err, c->s));
     c->st.kernel_launches++;
@@ -706,6 +790,9 @@ struct Clusterer {
 
 // separable Chebyshev dilation of a 0/1 field [M][N] by w cells in x and wy
 // in y, in place, with sliding window counts (t and cnt are scratch)
+constexpr size_t kPinHead = 64;          // count and bounding box ahead of the bitmap
+constexpr size_t kPinBits = 256 << 10;   // bitmaps up to this size come back with the count
+
 adjamr_status flag_dense(adjamr_ctx *c, int l, double tol, uint64_t *d_bits, int pitch64, unsigned char *d_patchflags,
                          long long *nflag_out, int *bbox_out = nullptr);
 
@@ -768,10 +855,16 @@ adjamr_status regrid_body(adjamr_ctx *c, int base, int init)
             Bits &fl = c->h_fl, &unc = c->h_unc;
             fl.reset(wN, wM);
             tp = std::chrono::steady_clock::now();
-            CKR(c, cudaMemcpy2DAsync(fl.w.data(), (size_t)fl.nw * sizeof(uint64_t),
-                                     c->d_flagbuf + (size_t)wj0 * pitch64 + k0, (size_t)pitch64 * sizeof(uint64_t),
-                                     (size_t)fl.nw * sizeof(uint64_t), (size_t)wM, cudaMemcpyDeviceToHost, c->s));
-            CKR(c, cudaStreamSynchronize(c->s));
+            if (c->pin_has_bits) {
+                const uint64_t *all = reinterpret_cast<const uint64_t *>(c->h_pin + kPinHead);
+                for (int j = 0; j < wM; j++)
+                    std::memcpy(fl.row(j), all + (size_t)(wj0 + j) * pitch64 + k0, (size_t)fl.nw * sizeof(uint64_t));
+            } else {
+                CKR(c, cudaMemcpy2DAsync(fl.w.data(), (size_t)fl.nw * sizeof(uint64_t),
+                                         c->d_flagbuf + (size_t)wj0 * pitch64 + k0, (size_t)pitch64 * sizeof(uint64_t),
+                                         (size_t)fl.nw * sizeof(uint64_t), (size_t)wM, cudaMemcpyDeviceToHost, c->s));
+                CKR(c, cudaStreamSynchronize(c->s));
+            }
             double wcopy = ms_since(tp);
             c->st.regrid_phase_ms[1] += wcopy;
             c->st.cluster_host_ms -= wcopy;
@@ -919,7 +1012,7 @@ adjamr_status flag_tables(adjamr_ctx *c, int l)
     Level &L = c->L[l];
     const int ax = c->adj->ax, ay = c->adj->ay;
     if (c->d_ftab[l] && c->ftab_ax[l] == ax && c->ftab_ay[l] == ay) return ADJAMR_OK;
-    dfree(c->d_ftab[l], c->s);
+    cput(c, c->d_ftab[l]);
     const int N = L.N, M = (P.dim == 2) ? L.M : 1;
     std::vector<int> ta(N), tac(N), tb(M), tbc(M);
     std::vector<double> twx(N), twy(M);
@@ -1044,13 +1137,27 @@ adjamr_status flag_dense(adjamr_ctx *c, int l, double tol, uint64_t *d_bits, int
         CKR(c, launch_flag(a, c->s));
     }
     c->st.kernel_launches++;
-    unsigned long long cnt = 0;
-    int bb[4];
-    CKR(c, cudaMemcpyAsync(&cnt, c->d_count, sizeof cnt, cudaMemcpyDeviceToHost, c->s));
-    CKR(c, cudaMemcpyAsync(bb, c->d_bbox, sizeof bb, cudaMemcpyDeviceToHost, c->s));
+    // count, box and (up to kPinBits bytes) the bitmap into pinned memory,
+    // then one synchronisation
+    const size_t bits_bytes = d_bits ? (size_t)pitch64 * (size_t)L.M * sizeof(uint64_t) : 0;
+    const bool with_bits = d_bits && bits_bytes <= kPinBits;
+    const size_t need = kPinHead + (with_bits ? bits_bytes : 0);
+    if (c->h_pin_bytes < need) {
+        if (c->h_pin) cudaFreeHost(c->h_pin);
+        c->h_pin = nullptr;
+        c->h_pin_bytes = 0;
+        CKR(c, cudaMallocHost((void **)&c->h_pin, std::max(need, (size_t)kPinHead + 4096)));
+        c->h_pin_bytes = std::max(need, (size_t)kPinHead + 4096);
+    }
+    CKR(c, cudaMemcpyAsync(c->h_pin, c->d_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->s));
+    CKR(c, cudaMemcpyAsync(c->h_pin + 8, c->d_bbox, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->s));
+    if (with_bits) CKR(c, cudaMemcpyAsync(c->h_pin + kPinHead, d_bits, bits_bytes, cudaMemcpyDeviceToHost, c->s));
+    c->pin_has_bits = with_bits;
     CKR(c, cudaStreamSynchronize(c->s));
+    unsigned long long cnt = 0;
+    std::memcpy(&cnt, c->h_pin, sizeof cnt);
     *nflag_out = (long long)cnt;
-    if (bbox_out) std::memcpy(bbox_out, bb, sizeof bb);
+    if (bbox_out) std::memcpy(bbox_out, c->h_pin + 8, 4 * sizeof(int));
     return ADJAMR_OK;
 }
 
@@ -1747,7 +1854,7 @@ adjamr_status adjamr_set_gauges(adjamr_ctx *ctx, int n, const double *x, const d
                 ij[(size_t)(nl + l) * n + g] = J;
             }
         }
-        dfree(ctx->d_gij, ctx->s);
+        cput(ctx, ctx->d_gij);
         dfree(ctx->d_grec, ctx->s);
         ctx->ngrec = ctx->gcap = 0;
         ctx->ngauge = n;
@@ -2035,10 +2142,11 @@ void adjamr_destroy(adjamr_ctx *ctx)
     }
     for (double *p : ctx->dense_dev) cudaFreeAsync(p, ctx->s);
     dfree(ctx->d_flagbuf, ctx->s);
-    for (int l = 0; l < ADJAMR_MAX_LEVELS; l++) dfree(ctx->d_ftab[l], ctx->s);
-    dfree(ctx->d_gij, ctx->s);
+    for (int l = 0; l < ADJAMR_MAX_LEVELS; l++) cput(ctx, ctx->d_ftab[l]);
+    cput(ctx, ctx->d_gij);
     dfree(ctx->d_grec, ctx->s);
     dfree(ctx->d_fscratch, ctx->s);
+    cache_drain(ctx);
     cudaStreamSynchronize(ctx->s);
     if (ctx->d_cfl) cudaFree(ctx->d_cfl);
     if (ctx->d_count) cudaFree(ctx->d_count);
@@ -2053,6 +2161,7 @@ void adjamr_destroy(adjamr_ctx *ctx)
         if (ctx->stage_ev[k]) cudaEventDestroy(ctx->stage_ev[k]);
         if (ctx->h_stage[k]) cudaFreeHost(ctx->h_stage[k]);
     }
+    if (ctx->h_pin) cudaFreeHost(ctx->h_pin);
     if (ctx->adj) adjamr_adjoint_release(ctx->adj);
     delete ctx;
 }

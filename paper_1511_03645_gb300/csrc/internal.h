@@ -193,6 +193,11 @@ struct GaugeArgs {
 };
 cudaError_t launch_gauges(const GaugeArgs &g, cudaStream_t s);
 
+// bytes of released device blocks a context keeps for reuse by later regrids
+// (0: every block is freed at once; the serving loop, which admits requests by
+// their projected bytes, uses 0)
+void ctx_set_block_cache(adjamr_ctx *c, size_t cap_bytes);
+
 // bracket-max flags over the level's index space, one thread per (cell, group
 // of a.gblk snapshot blocks), into the zeroed bitmap a.flags_bits
 cudaError_t launch_flag_dense(const FlagArgs &a, int ngroup, cudaStream_t s);

@@ -314,6 +314,54 @@ def config3(seed: int = 0, n0: int = 200, ratios=(4, 4, 2), tf: float = 4.0 * 36
 
 
 # --------------------------------------------------------------------------
+# the paper's two-dimensional acoustics examples (Sec. 5.2)
+# --------------------------------------------------------------------------
+PAPER_5_2_VARIANTS = ("timepoint_walls", "range_walls", "range_mixed")
+
+
+def paper_5_2(variant: str = "range_walls", n0: int = 50, nsnap: Optional[int] = None,
+              tol: float = 0.02) -> Workload:
+    """Sec. 5.2: homogeneous acoustics (K = 4, rho = 1) on [-4,8] x [-1,11],
+    a radially symmetric pressure hump at (0.5, 1), the pressure over
+    [3.32,3.8] x [0.32,0.8] with weight 2 (Eq. eq:phi_2d) as the quantity of
+    interest, 3 levels with ratio 2, coarse and adjoint grids 50 x 50,
+    tolerance 0.02.
+
+    Variants: "timepoint_walls" (Sec. 5.2.1: walls, t_s = t_f = 1.5),
+    "range_walls" (Sec. 5.2.2: walls, t_f = 6, t_s = 1), "range_mixed"
+    (Sec. 5.2.3: walls at x = 8 and y = -1, outflow at x = -4 and y = 11).
+    The hump is read as p = 1 + cos(pi (r - 0.3)/w) for |r - 0.3| <= w,
+    w = 0.15 (the printed formula is garbled: its centre differs between the
+    two expressions and "3 + cos" does not vanish at the edge).  Snapshots:
+    one every 0.05 in time (the paper does not say how many)."""
+    if variant not in PAPER_5_2_VARIANTS:
+        raise ValueError(variant)
+    tf, ts = (1.5, 1.5) if variant == "timepoint_walls" else (6.0, 1.0)
+    if variant == "range_mixed":
+        bc = (BC_EXTRAP, BC_WALL, BC_WALL, BC_EXTRAP)   # x = a outflow, x = b wall, y = alpha wall, y = beta outflow
+    else:
+        bc = (BC_WALL,) * 4
+    rho = np.array([1.0])
+    K = np.array([4.0])
+    med = Medium(kind="layered", axis=0, iface=np.zeros(0), rho=rho, K=K, cmax=_layered_cmax(rho, K))
+    w = 0.15
+
+    def qinit(x, y):
+        r = np.sqrt((x - 0.5) ** 2 + (y - 1.0) ** 2)
+        p = np.where(np.abs(r - 0.3) <= w, 1.0 + np.cos(np.pi * (r - 0.3) / w), 0.0)
+        z = np.zeros_like(p)
+        return np.stack([p, z, z])
+
+    if nsnap is None:
+        nsnap = int(round(tf / 0.05)) + 1
+    return Workload(name="acoustics2d-sec5.2-" + variant, dim=2, eqn=EQ_ACOUSTICS, lo=(-4.0, -1.0),
+                    hi=(8.0, 11.0), n0=(n0, n0), ratios=(2, 2), bc=bc, cfl=0.9, cfl_max=1.0, t0=0.0, tf=tf,
+                    ts=ts, tol=tol, medium=med, qinit=qinit, target=Target(3.32, 3.8, 0.32, 0.8, weight=2.0),
+                    adj_n=(n0, n0), nsnap=nsnap, min_patch=8, max_patch=64, max_patch0=64,
+                    extra={"gauge": (3.5, 0.5)})
+
+
+# --------------------------------------------------------------------------
 # config 4: batching stress test, 4096 independent patches
 # --------------------------------------------------------------------------
 @dataclass

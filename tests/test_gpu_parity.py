@@ -158,12 +158,19 @@ def _compare_all(o, g, nlev):
         close(a, b)
 
 
-@pytest.mark.parametrize("which", ["c1", "c2", "c2_linear", "c2_walls", "c3", "c1_diff", "c2_diff", "c3_surface"])
+@pytest.mark.parametrize("which", ["c1", "c2", "c2_linear", "c2_walls", "c3", "c1_diff", "c2_diff", "c3_surface",
+                                   "p521", "p522", "p523", "p523_diff"])
 def test_amr_run_matches_oracle(A, which):
     """Adjoint-guided AMR runs (reduced sizes of the workloads): layouts of
     every level bit-exact after every regrid, states within 1e-12, flags
     bit-exact, J within 1e-12."""
-    if which.startswith("c1"):
+    if which.startswith("p52"):
+        # the paper's Sec. 5.2 examples at their own sizes
+        wl = W.paper_5_2({"p521": "timepoint_walls", "p522": "range_walls"}.get(which[:4], "range_mixed"))
+        if which.endswith("_diff"):
+            wl.flag_mode, wl.tol = W.FLAG_DIFFERENCE, 0.1
+        chunks = 4
+    elif which.startswith("c1"):
         wl = W.config1(n0=100, tf=6.0, adj_n=400, nsnap=30)
         if which == "c1_diff":
             wl.flag_mode, wl.tol = W.FLAG_DIFFERENCE, 0.02
