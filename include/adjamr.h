@@ -56,7 +56,7 @@ enum {
 enum { ADJAMR_BC_EXTRAP = 0, ADJAMR_BC_WALL = 1, ADJAMR_BC_PERIODIC = 2 };
 
 /* Flag test.  Adjoint flagging (Sec. 4), with the time combination of the
- * adjoint snapshots ("both taken into account"): maximum over the bracketing
+ * adjoint snapshots (both bracketing snapshots count): maximum over the bracketing
  * snapshots, or q^ linear in time between snapshots.  The standard flaggers
  * the paper compares against: DIFFERENCE flags a cell when the undivided
  * centred difference |q_f(i+1) - q_f(i-1)| of some component in some

@@ -200,7 +200,7 @@ def test_flag_linear_mode_equals_dense_time_sampling(t_s):
 
 @pytest.mark.parametrize("t_s", [1.0, 0.55, 0.0])
 def test_flag_bracket_mode_is_max_over_bracketing_snapshots(t_s):
-    """BRACKET-MAX (default; Sec. 4 "both taken into account"): the maximum
+    """BRACKET-MAX (default; Sec. 4, both bracketing snapshots count): the maximum
     of |qhat_n . q| over the snapshots from the last one at or before t to
     the first one at or after T = min(t + t_f - t_s, t_f)."""
     rng = np.random.default_rng(6)
