@@ -158,18 +158,51 @@ __device__ __forceinline__ void trans_split(const Edge &e, double d0, double *am
     }
 }
 
-// MC limiter of the canonical operations.  Two exact shortcuts skip the
-// division: dot <= 0 gives theta <= 0 and phi = 0 (up to the sign of zero);
-// dot >= 4 wn gives a rounded theta >= 4 and phi = 2.
+// MC limiter phi(theta), theta = (W_upwind . W)/(W . W), in the canonical
+// form  wn == 0 ? 0 : fmax(0, fmin(fmin(fma(0.5, th, 0.5), 2), 2*th)).
+// Exact shortcuts skip the division: dot <= 0 gives theta <= 0 and phi = 0
+// (up to the sign of zero); dot >= 4 wn gives a rounded theta >= 4 and
+// phi = 2.  The tests and the min run on the integer pipe: a sum of squares
+// is never -0, and past the early exits every value compared (dot, 4 wn,
+// fma(0.5, th, 0.5), 2, 2 th) is a non-negative double, which orders like its
+// bit pattern (products by 2 and 4 are exponent increments); the outer
+// fmax(0, .) is the identity on those values.
+// bits of x * 2^k for a positive double x: an exponent increment when x is
+// normal and stays finite (exact), else the multiplication
+template <int K>
+__device__ __forceinline__ long long scaled_bits(double x)
+{
+    const long long b = __double_as_longlong(x);
+    const long long e = b >> 52;
+    if (e >= 1 && e <= 2046 - K) return b + ((long long)K << 52);
+    return __double_as_longlong(x * (double)(1 << K));
+}
+
+// 0.5 * x: an exponent decrement when x and x/2 are normal (exact), else the
+// multiplication
+__device__ __forceinline__ double half(double x)
+{
+    const long long b = __double_as_longlong(x);
+    const long long e = (b >> 52) & 0x7ff;
+    if (e >= 2 && e <= 2046) return __longlong_as_double(b - (1ll << 52));
+    return 0.5 * x;
+}
+
 __device__ __forceinline__ double mc_phi(double w0, double w1, double u0, double u1)
 {
-    double wn = fma(w0, w0, w1 * w1);
-    if (wn == 0.0) return 0.0;
-    double dot = fma(u0, w0, u1 * w1);
-    if (dot <= 0.0) return 0.0;
-    if (dot >= 4.0 * wn) return 2.0;
-    double th = dot / wn;
-    return fmax(0.0, fmin(fmin(fma(0.5, th, 0.5), 2.0), 2.0 * th));
+    const double wn = fma(w0, w0, w1 * w1);
+    if (__double_as_longlong(wn) == 0) return 0.0;
+    const double dot = fma(u0, w0, u1 * w1);
+    const long long idot = __double_as_longlong(dot);
+    if (idot <= 0) return 0.0;
+    if (idot >= scaled_bits<2>(wn)) return 2.0;
+    const double th = dot / wn;
+    const long long ia = __double_as_longlong(fma(0.5, th, 0.5));
+    const long long ib = scaled_bits<1>(th);
+    const long long i2 = 0x4000000000000000ll;  // 2.0
+    long long m = ia < i2 ? ia : i2;
+    m = m < ib ? m : ib;
+    return __longlong_as_double(m);
 }
 
 // s > 0.0 and s < 0.0 decided on the integer pipe (identical to the FP64
@@ -375,8 +408,8 @@ __global__ void __launch_bounds__(kThreads) k_step2d(const double *__restrict__ 
                 double p2 = mc_phi(w20, w2n, XW[2 * XES + u2], XW[3 * XES + u2]);
                 double cf1 = corr_coef<EQN>(e.s1, dtdx), cf2 = corr_coef<EQN>(e.s2, dtdx);
                 int on = er * XNX + ec;
-                XN[on] = 0.5 * (cf1 * (p1 * w10) + cf2 * (p2 * w20));
-                XN[XNS + on] = 0.5 * (cf1 * (p1 * w1n) + cf2 * (p2 * w2n));
+                XN[on] = half(cf1 * (p1 * w10) + cf2 * (p2 * w20));
+                XN[XNS + on] = half(cf1 * (p1 * w1n) + cf2 * (p2 * w2n));
             } else {
                 int kk = k - (tx + 1) * (ty + 2);
                 int er = kk / (tx + 2), ec = kk - er * (tx + 2);   // y-edge ey = er, column cx = ec-1
@@ -391,8 +424,8 @@ __global__ void __launch_bounds__(kThreads) k_step2d(const double *__restrict__ 
                 double p2 = mc_phi(w20, w2n, YW[2 * YES + u2], YW[3 * YES + u2]);
                 double cf1 = corr_coef<EQN>(e.s1, dtdy), cf2 = corr_coef<EQN>(e.s2, dtdy);
                 int on = er * YNX + ec;
-                YN[on] = 0.5 * (cf1 * (p1 * w10) + cf2 * (p2 * w20));
-                YN[YNS + on] = 0.5 * (cf1 * (p1 * w1n) + cf2 * (p2 * w2n));
+                YN[on] = half(cf1 * (p1 * w10) + cf2 * (p2 * w20));
+                YN[YNS + on] = half(cf1 * (p1 * w1n) + cf2 * (p2 * w2n));
             }
         }
         __syncthreads();
@@ -557,8 +590,8 @@ __global__ void __launch_bounds__(kThreads) k_step1d(const double *__restrict__ 
             double p1 = mc_phi(w10, w1n, XW[u1], XW[XE + u1]);
             double p2 = mc_phi(w20, w2n, XW[2 * XE + u2], XW[3 * XE + u2]);
             double cf1 = corr_coef<EQN>(e.s1, dtdx), cf2 = corr_coef<EQN>(e.s2, dtdx);
-            XN[k] = 0.5 * (cf1 * (p1 * w10) + cf2 * (p2 * w20));
-            XN[XNn + k] = 0.5 * (cf1 * (p1 * w1n) + cf2 * (p2 * w2n));
+            XN[k] = half(cf1 * (p1 * w10) + cf2 * (p2 * w20));
+            XN[XNn + k] = half(cf1 * (p1 * w1n) + cf2 * (p2 * w2n));
             cfl = bmax(cfl, dtdx * maxabs(e.s1, e.s2));
         }
         __syncthreads();
