@@ -43,12 +43,12 @@ UNIT = "cell-updates/s"
 # instruction rate (the DFMA micro-benchmark's flop rate / 2).
 OPS_PER_CELL_2D = 170
 # DRAM bytes per cell-update of a finest-level step launch, from the ncu
-# capture summarised in profiles/k_step2d_amr_level2_config2.md (4.59 MB read,
+# capture summarised in profiles/k_step2d_amr_level2_config2.md (3.98 MB read,
 # 0 written, in a launch of the --case solve --tf 1 run, whose level-2
-# launches average 40,920 cells): 1.4x the 80 algorithmic bytes per
-# cell-update (tile halos, descriptors, coarse reads for the ghost ring);
-# written lines stay in L2 within the launch.
-TRAFFIC_PER_CELL_L2 = 4.594688e6 / 40920.0
+# launches average 40,920 cells): 1.2x the 80 algorithmic bytes per
+# cell-update (tile halos and descriptors); written lines stay in L2 within
+# the launch.
+TRAFFIC_PER_CELL_L2 = 3.978496e6 / 40920.0
 
 
 def log(*a):

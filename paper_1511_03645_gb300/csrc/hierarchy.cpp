@@ -510,12 +510,21 @@ LevelGeom geom_of(const adjamr_ctx *c, int l)
 }
 
 // medium coefficients of every storage cell of a level
-adjamr_status fill_aux(adjamr_ctx *c, int l)
+// (old: the level's previous arena during a rebuild, whose interior cells
+// give their coefficients to the new storage cells at the same (I, J))
+adjamr_status fill_aux(adjamr_ctx *c, int l, const Level *old = nullptr)
 {
     Level &L = c->L[l];
     if (!c->have_medium || L.patches.empty()) return ADJAMR_OK;
+    AuxReuse ru{nullptr, nullptr, nullptr, 0, c->naux, c->nmed};
+    if (old && !old->patches.empty() && old->d_owner && old->aux) {
+        ru.owner = old->d_owner;
+        ru.aux = old->aux;
+        ru.med = old->med;
+        ru.stride = old->ncell;
+    }
     CKR(c, launch_aux_patches(c->P.eqn, L.d_patches, L.d_sprefix, (int)L.patches.size(), L.nstore, idx_of(c, l),
-                              L.aux, L.med, L.ncell, L.d_med, geom_of(c, l), c->s));
+                              L.aux, L.med, L.ncell, L.d_med, geom_of(c, l), c->s, ru));
     c->st.kernel_launches++;
     return ADJAMR_OK;
 }
@@ -955,7 +964,7 @@ adjamr_status regrid_body(adjamr_ctx *c, int base, int init)
         tp = std::chrono::steady_clock::now();
         F.cur = 0;
         F.nstep = C.nstep * r;
-        TRY(fill_aux(c, lev + 1));
+        TRY(fill_aux(c, lev + 1, &old));
         if (!F.patches.empty()) {
             if (init && P.qinit) {
                 long long n = F.ninterior;

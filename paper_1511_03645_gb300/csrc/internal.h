@@ -240,8 +240,17 @@ cudaError_t launch_init_new(const PatchDesc *p, const long long *prefix, int np,
                             const int *owner_c, LevelIdx gc, const double *qc, long long sc, int r, int *err,
                             cudaStream_t s);
 // medium coefficients of every storage cell; sprefix = storage-cell prefix
+// coefficients a rebuilt level may copy from its previous arena: a storage
+// cell whose (I, J) was an interior cell of the previous patches takes that
+// cell's values (they depend on (I, J) only); owner == nullptr: compute all
+struct AuxReuse {
+    const int *owner;
+    const double *aux, *med;
+    long long stride;
+    int naux, nmed;
+};
 cudaError_t launch_aux_patches(int eqn, const PatchDesc *p, const long long *sprefix, int np, long long nstore,
                                LevelIdx g, double *aux, double *med, long long stride, const MediumDev *mdev,
-                               LevelGeom geom, cudaStream_t s);
+                               LevelGeom geom, cudaStream_t s, AuxReuse ru = AuxReuse{nullptr, nullptr, nullptr, 0, 0, 0});
 
 }  // namespace adjamr

@@ -334,7 +334,7 @@ __global__ void k_init_new(const PatchDesc *__restrict__ pd, const long long *__
 
 __global__ void k_aux_patches(int eqn, const PatchDesc *__restrict__ pd, const long long *__restrict__ sprefix,
                               int np, long long nstore, LevelIdx g, double *aux, double *med, long long stride,
-                              const MediumDev *__restrict__ mdp, LevelGeom geom)
+                              const MediumDev *__restrict__ mdp, LevelGeom geom, AuxReuse ru)
 {
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nstore) return;
@@ -342,7 +342,17 @@ __global__ void k_aux_patches(int eqn, const PatchDesc *__restrict__ pd, const l
     const PatchDesc P = pd[p];
     long long k = t - sprefix[p];
     int sj = (int)(k / P.sx), si = (int)(k - (long long)sj * P.sx);
-    aux_cell(eqn, g.dim, *mdp, geom, P.ilo + si - 2, P.jlo + sj - g.gy, P.base + k, aux, med, stride);
+    const int I = P.ilo + si - 2, J = P.jlo + sj - g.gy;
+    const long long idx = P.base + k;
+    if (ru.owner) {
+        const int o = owner_at(ru.owner, g, I, J);
+        if (o >= 0) {
+            for (int f = 0; f < ru.naux; f++) aux[(long long)f * stride + idx] = ru.aux[(long long)f * ru.stride + o];
+            for (int f = 0; f < ru.nmed; f++) med[(long long)f * stride + idx] = ru.med[(long long)f * ru.stride + o];
+            return;
+        }
+    }
+    aux_cell(eqn, g.dim, *mdp, geom, I, J, idx, aux, med, stride);
 }
 
 // ---------------------------------------------------------------- flagging
@@ -740,10 +750,10 @@ cudaError_t launch_init_new(const PatchDesc *p, const long long *prefix, int np,
 
 cudaError_t launch_aux_patches(int eqn, const PatchDesc *p, const long long *sprefix, int np, long long nstore,
                                LevelIdx g, double *aux, double *med, long long stride, const MediumDev *mdev,
-                               LevelGeom geom, cudaStream_t s)
+                               LevelGeom geom, cudaStream_t s, AuxReuse ru)
 {
     if (nstore <= 0) return cudaSuccess;
-    k_aux_patches<<<nblk(nstore), kT, 0, s>>>(eqn, p, sprefix, np, nstore, g, aux, med, stride, mdev, geom);
+    k_aux_patches<<<nblk(nstore), kT, 0, s>>>(eqn, p, sprefix, np, nstore, g, aux, med, stride, mdev, geom, ru);
     return cudaGetLastError();
 }
 
