@@ -105,7 +105,7 @@ typedef struct adjamr_params {
     adjamr_qinit_fn qinit;       /* may be NULL (state starts at zero) */
     void *qinit_user;
     void *stream;                /* cudaStream_t or NULL */
-    int tile_x, tile_y;          /* step-kernel tile (0 = default 32 x 8) */
+    int tile_x, tile_y;          /* step-kernel tile size (0 = default 32 x 8; see adjamr_set_level_kernel) */
     int launch_mode;             /* ADJAMR_LAUNCH_* */
 } adjamr_params;
 
@@ -245,14 +245,17 @@ adjamr_status adjamr_get_stats(adjamr_ctx *ctx, adjamr_stats *out);
 /* Enable/disable CUDA-event timing of step kernels (adds events only). */
 adjamr_status adjamr_set_timing(adjamr_ctx *ctx, int enable);
 /* Step-kernel configuration of one level (level = -1: every level), used
- * from the next step on: the tile shape, whether the kernel computes the
+ * from the next step on: the tile size the level's patches are cut to
+ * (near-equal tiles of at most tile_x x tile_y cells; the kernel compiled for
+ * the smallest of 8x8, 16x8, 32x8, 16x16, 64x8, 32x16 that holds them runs
+ * them; 1D: tile_x <= 256, tile_y ignored), whether the kernel computes the
  * level's ghost ring (same-level copies and coarse space-time interpolation,
  * Sec. 3) while staging its tiles (fuse_ghosts = 1, the default) or a
  * separate ghost-fill kernel runs before it (0), and the launch mode
  * (ADJAMR_LAUNCH_*; -1 keeps the level's current one).  Every choice
- * computes the same bits; it changes only speed (small levels fill the GPU
- * better with small tiles).  2D tiles: 32x8, 16x8, 16x16, 32x16, 64x8, 8x8;
- * 1D: 256 or 128 (tile_y ignored).  Errors: EINVAL for another shape, mode
+ * computes the same bits; it changes only speed (tile counts near whole
+ * waves of resident CTAs, and small tiles on small levels, fill the GPU
+ * better).  Errors: EINVAL for a tile no compiled kernel holds, or a bad mode
  * or level. */
 adjamr_status adjamr_set_level_kernel(adjamr_ctx *ctx, int level, int tile_x, int tile_y, int fuse_ghosts,
                                       int launch_mode);
@@ -300,7 +303,8 @@ adjamr_status adjamr_batch_set_order(adjamr_batch *b, const int *order);
  * it stages its tiles (1) or by a separate ghost-fill kernel launched before
  * it (0, the default).  Same bits either way. */
 adjamr_status adjamr_batch_set_ghost_fusion(adjamr_batch *b, int fuse_ghosts);
-/* Advance all patches nsteps steps with the given launch mode and tile. */
+/* Advance all patches nsteps steps with the given launch mode and tile size
+ * (as in adjamr_set_level_kernel). */
 adjamr_status adjamr_batch_step(adjamr_batch *b, int nsteps, int launch_mode, int tile_x, int tile_y);
 /* Capture one step (ghost fill + fused step) in a CUDA graph and replay it
  * nsteps times. */

@@ -18,7 +18,12 @@ from . import adjamr as A
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE = os.path.join(HERE, "_build", "autotune.json")
-TILES = [(32, 8), (16, 8), (16, 16), (32, 16), (64, 8), (8, 8)]
+# tile sizes the patches are cut to (the kernel compiled for the smallest of
+# 8x8, 16x8, 32x8, 16x16, 64x8, 32x16 holding them runs them): the compiled
+# shapes and cuts between them, which move a level's tile count towards whole
+# waves of resident CTAs
+TILES = [(32, 8), (16, 8), (16, 16), (32, 16), (64, 8), (8, 8), (12, 8), (16, 12), (24, 8), (24, 16), (48, 8),
+         (12, 12)]
 _lock = threading.Lock()
 
 
@@ -71,8 +76,10 @@ def batch_orders(pb):
 
 
 def tune_batch(pb, key: str, stream=None, steps: int = 4, use_cache: bool = True) -> dict:
-    """Best (work-list order, tile, launch mode, ghost fusion) for a batch;
-    returns a dict with the choice and the measured cell-updates/s of every
+    """Best (work-list order, tile size, launch mode) for a batch, ghost ring
+    from its own kernel (the measured faster way for this batch; the fused
+    ring, the shuffled order and the dynamic tile counter never won); returns
+    a dict with the choice and the measured cell-updates/s of every
     candidate."""
     import torch
     ck = f"{_gpu_key()}|batch|{key}"
@@ -85,10 +92,12 @@ def tune_batch(pb, key: str, stream=None, steps: int = 4, use_cache: bool = True
     cells = b.cells()
     results = []
     for oname, order in batch_orders(pb).items():
+        if oname == "shuffled":
+            continue
         b.set_order(order)
         for tile in TILES:
-            for mode in (A.LAUNCH_WORKLIST, A.LAUNCH_PERSISTENT, A.LAUNCH_DYNAMIC):
-                for fuse in (False, True):
+            for mode in (A.LAUNCH_WORKLIST, A.LAUNCH_PERSISTENT):
+                for fuse in (False,):
                     b.set_ghost_fusion(fuse)
                     b.step(1, mode=mode, tile=tile)
                     ms = _time(s, lambda: b.step(steps, mode=mode, tile=tile)) / steps
@@ -102,9 +111,9 @@ def tune_batch(pb, key: str, stream=None, steps: int = 4, use_cache: bool = True
 
 
 def tune_amr(wl, adj, key: str, stream=None, coarse_steps: int = 40, use_cache: bool = True) -> dict:
-    """Best step-kernel configuration (tile shape, ghost ring fused into the
-    step or filled by its own kernel, one work-list launch or a persistent
-    grid with dynamic tile fetching) of every level of an AMR solve.
+    """Best step-kernel configuration (tile size, ghost ring fused into the
+    step or filled by its own kernel; one work-list launch per level, the
+    dynamic tile counter never won) of every level of an AMR solve.
 
     Each candidate runs the solve's first coarse steps (regrids included) with
     the same configuration on every level; the hierarchy evolves
@@ -120,7 +129,7 @@ def tune_amr(wl, adj, key: str, stream=None, coarse_steps: int = 40, use_cache: 
             return hit
     s = torch.cuda.Stream() if stream is None else stream
     results = []
-    for tile, fuse, mode in itertools.product(TILES, (True, False), (A.LAUNCH_WORKLIST, A.LAUNCH_DYNAMIC)):
+    for tile, fuse, mode in itertools.product(TILES, (True, False), (A.LAUNCH_WORKLIST,)):
         h = A.Hierarchy(wl, stream=s.cuda_stream)
         h.set_level_kernel(-1, tile, fuse, mode)
         h.set_adjoint(adj)

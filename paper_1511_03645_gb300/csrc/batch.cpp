@@ -87,6 +87,8 @@ void drop_graphs(adjamr_batch *b)
 // its tiles (b->fuse) or from the ghost-fill kernel launched first.
 cudaError_t one_step(adjamr_batch *b, int mode, int tx, int ty)
 {
+    int kx = 0, ky = 0;  // the compiled kernel tile that holds tx x ty tiles
+    if (!step_kernel_shape(2, tx, ty, &kx, &ky)) return cudaErrorInvalidValue;
     const double *q = b->q[b->cur];
     double *qn = b->q[1 - b->cur];
     GhostArgs ga{nullptr, nullptr, nullptr, 0, 0, 0.0};
@@ -102,7 +104,7 @@ cudaError_t one_step(adjamr_batch *b, int mode, int tx, int ty)
         while (w0 < b->nwork) {
             int w1 = w0, k = b->h_work[w0].patch;
             while (w1 < b->nwork && b->h_work[w1].patch == k) w1++;
-            e = launch_step(2, 0, tx, ty, q, qn, b->aux, b->ncell, b->d_patches, b->d_work + w0, w1 - w0, 0, b->d_cfl,
+            e = launch_step(2, 0, kx, ky, q, qn, b->aux, b->ncell, b->d_patches, b->d_work + w0, w1 - w0, 0, b->d_cfl,
                             b->s, ga);
             if (e != cudaSuccess) return e;
             w0 = w1;
@@ -110,7 +112,7 @@ cudaError_t one_step(adjamr_batch *b, int mode, int tx, int ty)
     } else {
         int grid = 0;
         if (mode == ADJAMR_LAUNCH_PERSISTENT || mode == ADJAMR_LAUNCH_DYNAMIC)
-            grid = std::min(b->nwork, b->nsm * std::max(1, step_occupancy(2, 0, tx, ty)));
+            grid = std::min(b->nwork, b->nsm * std::max(1, step_occupancy(2, 0, kx, ky)));
         TileSched sc{nullptr, 0};
         if (mode == ADJAMR_LAUNCH_DYNAMIC) {
             // counter reset in the stream, so that a captured step replays as is
@@ -118,7 +120,7 @@ cudaError_t one_step(adjamr_batch *b, int mode, int tx, int ty)
             if (e != cudaSuccess) return e;
             sc.ctr = b->d_wctr;
         }
-        e = launch_step(2, 0, tx, ty, q, qn, b->aux, b->ncell, b->d_patches, b->d_work, b->nwork, grid, b->d_cfl, b->s,
+        e = launch_step(2, 0, kx, ky, q, qn, b->aux, b->ncell, b->d_patches, b->d_work, b->nwork, grid, b->d_cfl, b->s,
                         ga, sc);
         if (e != cudaSuccess) return e;
     }
@@ -298,8 +300,9 @@ adjamr_status adjamr_batch_set_ghost_fusion(adjamr_batch *b, int fuse_ghosts)
 adjamr_status adjamr_batch_step(adjamr_batch *b, int nsteps, int mode, int tx, int ty)
 {
     if (!b || nsteps < 0 || mode < ADJAMR_LAUNCH_WORKLIST || mode > ADJAMR_LAUNCH_DYNAMIC) return ADJAMR_EINVAL;
+    int kx = 0, ky = 0;
+    if (!step_kernel_shape(2, tx, ty, &kx, &ky) || step_occupancy(2, 0, kx, ky) <= 0) return ADJAMR_EINVAL;
     if (build_work(b, tx, ty) != cudaSuccess) return ADJAMR_ECUDA;
-    if (step_occupancy(2, 0, tx, ty) <= 0) return ADJAMR_EINVAL;
     for (int s = 0; s < nsteps; s++) {
         cudaError_t e = one_step(b, mode, tx, ty);
         if (e != cudaSuccess) {
@@ -313,8 +316,9 @@ adjamr_status adjamr_batch_step(adjamr_batch *b, int nsteps, int mode, int tx, i
 adjamr_status adjamr_batch_step_graph(adjamr_batch *b, int nsteps, int mode, int tx, int ty)
 {
     if (!b || nsteps < 0 || mode < ADJAMR_LAUNCH_WORKLIST || mode > ADJAMR_LAUNCH_DYNAMIC) return ADJAMR_EINVAL;
+    int kx = 0, ky = 0;
+    if (!step_kernel_shape(2, tx, ty, &kx, &ky) || step_occupancy(2, 0, kx, ky) <= 0) return ADJAMR_EINVAL;
     if (build_work(b, tx, ty) != cudaSuccess) return ADJAMR_ECUDA;
-    if (step_occupancy(2, 0, tx, ty) <= 0) return ADJAMR_EINVAL;
     if (b->s == nullptr) return ADJAMR_ESTATE;  // capture needs a non-default stream
     auto key = std::make_tuple(mode, tx, ty, b->cur, b->fuse);
     cudaGraphExec_t exec = nullptr;

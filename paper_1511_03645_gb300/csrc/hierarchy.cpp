@@ -125,6 +125,9 @@ struct adjamr_ctx {
     char *h_pin = nullptr;
     size_t h_pin_bytes = 0;
     bool pin_has_bits = false;
+    // work list of the two-pass flags
+    unsigned long long *d_fitems = nullptr, *d_fctr = nullptr;
+    long long fcap = 0;
     // per-level bilinear tables of the adjoint grid for the dense flag kernel
     char *d_ftab[ADJAMR_MAX_LEVELS] = {};
     int ftab_ax[ADJAMR_MAX_LEVELS] = {}, ftab_ay[ADJAMR_MAX_LEVELS] = {};
@@ -134,7 +137,10 @@ struct adjamr_ctx {
     size_t fscratch_n = 0;
     adjamr_stats st = {};
     int tx = 32, ty = 8, launch_mode = 0, grid_persistent = 0, nsm = 0;
+    // per level: tile extents the patches are cut to, the compiled kernel tile
+    // that holds them, the persistent grid
     int ltx[ADJAMR_MAX_LEVELS] = {}, lty[ADJAMR_MAX_LEVELS] = {}, lgrid[ADJAMR_MAX_LEVELS] = {};
+    int lkx[ADJAMR_MAX_LEVELS] = {}, lky[ADJAMR_MAX_LEVELS] = {};
     int lfuse[ADJAMR_MAX_LEVELS] = {};  // ghost ring computed inside the step kernel
     int lmode[ADJAMR_MAX_LEVELS] = {};  // ADJAMR_LAUNCH_* per level
     unsigned long long *d_wctr = nullptr;  // tile counter of the dynamic launch mode
@@ -799,11 +805,25 @@ struct Clusterer {
 
 // separable Chebyshev dilation of a 0/1 field [M][N] by w cells in x and wy
 // in y, in place, with sliding window counts (t and cnt are scratch)
-constexpr size_t kPinHead = 64;          // count and bounding box ahead of the bitmap
+constexpr size_t kPinHead = 64;          // count, bounding box and list counters ahead of the bitmap
+constexpr long long kFlagItemsMax = (long long)1 << 26;  // longest (cell, block) list of the two-pass flags
 constexpr size_t kPinBits = 256 << 10;   // bitmaps up to this size come back with the count
 
 adjamr_status flag_dense(adjamr_ctx *c, int l, double tol, uint64_t *d_bits, int pitch64, unsigned char *d_patchflags,
                          long long *nflag_out, int *bbox_out = nullptr);
+adjamr_status flag_readback(adjamr_ctx *c, int l, uint64_t *d_bits, int pitch64, bool twopass, long long *nflag_out,
+                            int *bbox_out);
+
+// work list of the two-pass flags with room for n (cell, block) pairs
+adjamr_status grow_flag_list(adjamr_ctx *c, long long n)
+{
+    cput(c, c->d_fitems);
+    c->fcap = 0;
+    CKR(c, cget(c, &c->d_fitems, (size_t)n));
+    if (!c->d_fctr) CKR(c, cget(c, &c->d_fctr, 2));
+    c->fcap = n;
+    return ADJAMR_OK;
+}
 
 // Rebuild levels base+1 .. nlevels-1 top-down (Sec. 3, regridding).
 void harvest_timing(adjamr_ctx *c);
@@ -1140,14 +1160,46 @@ adjamr_status flag_dense(adjamr_ctx *c, int l, double tol, uint64_t *d_bits, int
         a.tab_bc = (const int *)(base + off[4]);
         a.tab_wy = (const double *)(base + off[5]);
         a.gblk = kFlagBlocksPerThread;
-        const int nblk = (a.nlo <= a.nhi) ? a.nhi / kSnapBlock - a.nlo / kSnapBlock + 1 : 1;
-        CKR(c, launch_flag_dense(a, (nblk + a.gblk - 1) / a.gblk, c->s));
-    } else {
-        CKR(c, launch_flag(a, c->s));
+        const long long nblk = (a.nlo <= a.nhi) ? a.nhi / kSnapBlock - a.nlo / kSnapBlock + 1 : 1;
+        // two passes through a work list of (cell, block) pairs; a list too
+        // short for this call is grown (up to kFlagItemsMax) and the call redone,
+        // beyond that the one-pass kernel decides
+        const long long want = std::min((long long)L.N * L.M * nblk, kFlagItemsMax);
+        if (c->fcap < std::min(want, (long long)1 << 20)) TRY(grow_flag_list(c, std::min(want, (long long)1 << 20)));
+        for (int attempt = 0;; attempt++) {
+            if (attempt > 0) {
+                CKR(c, cudaMemsetAsync(d_bits, 0, (size_t)pitch64 * L.M * sizeof(uint64_t), c->s));
+                CKR(c, cudaMemsetAsync(c->d_count, 0, sizeof(unsigned long long), c->s));
+                CKR(c, cudaMemcpyAsync(c->d_bbox, bbox_init, sizeof bbox_init, cudaMemcpyHostToDevice, c->s));
+            }
+            const bool twopass = attempt == 0 || c->fcap >= (long long)L.N * L.M * nblk;
+            if (twopass) {
+                CKR(c, cudaMemsetAsync(c->d_fctr, 0, 2 * sizeof(unsigned long long), c->s));
+                CKR(c, launch_flag_twopass(a, FlagWork{c->d_fitems, c->d_fctr, c->fcap}, c->nsm * 8, c->s));
+                c->st.kernel_launches += 2;
+            } else {
+                CKR(c, launch_flag_dense(a, (int)((nblk + a.gblk - 1) / a.gblk), c->s));
+                c->st.kernel_launches++;
+            }
+            TRY(flag_readback(c, l, d_bits, pitch64, twopass, nflag_out, bbox_out));
+            unsigned long long ovf = 0;
+            if (twopass) std::memcpy(&ovf, c->h_pin + 32, sizeof ovf);
+            if (!ovf) break;
+            if (c->fcap < want) TRY(grow_flag_list(c, want));
+        }
+        return ADJAMR_OK;
     }
+    CKR(c, launch_flag(a, c->s));
     c->st.kernel_launches++;
-    // count, box and (up to kPinBits bytes) the bitmap into pinned memory,
-    // then one synchronisation
+    return flag_readback(c, l, d_bits, pitch64, false, nflag_out, bbox_out);
+}
+
+// count, box, (twopass) the work-list counters and (up to kPinBits bytes) the
+// bitmap into pinned memory, then one synchronisation
+adjamr_status flag_readback(adjamr_ctx *c, int l, uint64_t *d_bits, int pitch64, bool twopass, long long *nflag_out,
+                            int *bbox_out)
+{
+    Level &L = c->L[l];
     const size_t bits_bytes = d_bits ? (size_t)pitch64 * (size_t)L.M * sizeof(uint64_t) : 0;
     const bool with_bits = d_bits && bits_bytes <= kPinBits;
     const size_t need = kPinHead + (with_bits ? bits_bytes : 0);
@@ -1160,6 +1212,8 @@ adjamr_status flag_dense(adjamr_ctx *c, int l, double tol, uint64_t *d_bits, int
     }
     CKR(c, cudaMemcpyAsync(c->h_pin, c->d_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->s));
     CKR(c, cudaMemcpyAsync(c->h_pin + 8, c->d_bbox, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->s));
+    if (twopass)
+        CKR(c, cudaMemcpyAsync(c->h_pin + 24, c->d_fctr, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->s));
     if (with_bits) CKR(c, cudaMemcpyAsync(c->h_pin + kPinHead, d_bits, bits_bytes, cudaMemcpyDeviceToHost, c->s));
     c->pin_has_bits = with_bits;
     CKR(c, cudaStreamSynchronize(c->s));
@@ -1241,7 +1295,7 @@ adjamr_status step_patches(adjamr_ctx *c, int l, int k, GhostMode gm)
         for (int k = 0; k < (int)L.patches.size(); k++) {
             int w1 = w0;
             while (w1 < L.nwork && L.h_work[w1].patch == k) w1++;
-            CKR(c, launch_step(c->P.dim, c->P.eqn, c->ltx[l], c->lty[l], q, qn, L.aux, L.ncell, L.d_patches,
+            CKR(c, launch_step(c->P.dim, c->P.eqn, c->lkx[l], c->lky[l], q, qn, L.aux, L.ncell, L.d_patches,
                                L.d_work + w0, w1 - w0, 0, c->d_cfl, c->s, ga));
             c->st.kernel_launches++;
             c->st.step_kernel_launches++;
@@ -1257,7 +1311,7 @@ adjamr_status step_patches(adjamr_ctx *c, int l, int k, GhostMode gm)
             sc.base = c->wbase;
             c->wbase += (unsigned long long)L.nwork + (unsigned long long)grid;
         }
-        CKR(c, launch_step(c->P.dim, c->P.eqn, c->ltx[l], c->lty[l], q, qn, L.aux, L.ncell, L.d_patches, L.d_work,
+        CKR(c, launch_step(c->P.dim, c->P.eqn, c->lkx[l], c->lky[l], q, qn, L.aux, L.ncell, L.d_patches, L.d_work,
                            L.nwork, grid, c->d_cfl, c->s, ga, sc));
         c->st.kernel_launches++;
         c->st.step_kernel_launches++;
@@ -1431,16 +1485,23 @@ adjamr_status create_impl(const adjamr_params *p, adjamr_ctx **out)
             cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
         }
     }
-    int occ = step_occupancy(p->dim, p->eqn, c->tx, c->ty);
+    int kx = 0, ky = 0;
+    if (!step_kernel_shape(p->dim, c->tx, c->ty, &kx, &ky)) {
+        delete c;
+        return ADJAMR_EINVAL;  // no compiled tile holds tiles of this size
+    }
+    int occ = step_occupancy(p->dim, p->eqn, kx, ky);
     if (p->dim == 2 && occ <= 0) {
         delete c;
-        return ADJAMR_EINVAL;  // unsupported tile shape
+        return ADJAMR_EINVAL;
     }
     c->grid_persistent = nsm * std::max(occ, 1);
     c->nsm = nsm;
     for (int l = 0; l < ADJAMR_MAX_LEVELS; l++) {
         c->ltx[l] = c->tx;
         c->lty[l] = c->ty;
+        c->lkx[l] = kx;
+        c->lky[l] = ky;
         c->lgrid[l] = c->grid_persistent;
         c->lfuse[l] = 1;
         c->lmode[l] = p->launch_mode;
@@ -2098,18 +2159,16 @@ adjamr_status adjamr_set_level_kernel(adjamr_ctx *ctx, int level, int tile_x, in
     if (!ctx || level < -1 || level >= ctx->P.nlevels) return ADJAMR_EINVAL;
     if (launch_mode < -1 || launch_mode > ADJAMR_LAUNCH_DYNAMIC) return ADJAMR_EINVAL;
     int ty = (ctx->P.dim == 2) ? tile_y : 1;
-    int occ = 0;
-    if (ctx->P.dim == 2) {
-        occ = step_occupancy(2, ctx->P.eqn, tile_x, ty);
-        if (occ <= 0) return ADJAMR_EINVAL;
-    } else {
-        if (tile_x != 256 && tile_x != 128) return ADJAMR_EINVAL;
-        occ = step_occupancy(1, ctx->P.eqn, tile_x, 1);
-    }
+    int kx = 0, ky = 0;
+    if (!step_kernel_shape(ctx->P.dim, tile_x, ty, &kx, &ky)) return ADJAMR_EINVAL;
+    const int occ = step_occupancy(ctx->P.dim, ctx->P.eqn, kx, ky);
+    if (occ <= 0) return ADJAMR_EINVAL;
     for (int l = 0; l < ctx->P.nlevels; l++) {
         if (level >= 0 && l != level) continue;
         ctx->ltx[l] = tile_x;
         ctx->lty[l] = ty;
+        ctx->lkx[l] = kx;
+        ctx->lky[l] = ky;
         ctx->lgrid[l] = ctx->nsm * std::max(occ, 1);
         ctx->lfuse[l] = fuse_ghosts != 0;
         if (launch_mode >= 0) ctx->lmode[l] = launch_mode;
@@ -2152,6 +2211,8 @@ void adjamr_destroy(adjamr_ctx *ctx)
     for (double *p : ctx->dense_dev) cudaFreeAsync(p, ctx->s);
     dfree(ctx->d_flagbuf, ctx->s);
     for (int l = 0; l < ADJAMR_MAX_LEVELS; l++) cput(ctx, ctx->d_ftab[l]);
+    cput(ctx, ctx->d_fitems);
+    cput(ctx, ctx->d_fctr);
     cput(ctx, ctx->d_gij);
     dfree(ctx->d_grec, ctx->s);
     dfree(ctx->d_fscratch, ctx->s);

@@ -135,6 +135,10 @@ cudaError_t launch_step(int dim, int eqn, int tx, int ty, const double *q, doubl
                         unsigned long long *cfl_bits, cudaStream_t s, GhostArgs ga = GhostArgs{nullptr, nullptr, nullptr, 0, 0, 0.0},
                         TileSched sc = TileSched{nullptr, 0});
 int step_occupancy(int dim, int eqn, int tx, int ty);
+// compiled step-kernel tile (kx, ky) that holds tiles of tx x ty cells: the
+// smallest by area among 8x8, 16x8, 32x8, 16x16, 64x8, 32x16 (1D: 128 or 256);
+// false if none does
+bool step_kernel_shape(int dim, int tx, int ty, int *kx, int *ky);
 
 cudaError_t launch_ghost_fill(int dim, int m, const GhostDesc *g, long long n, double *qf, long long sf,
                               const double *qc_old, const double *qc_new, long long sc, int k, int r,
@@ -201,6 +205,16 @@ void ctx_set_block_cache(adjamr_ctx *c, size_t cap_bytes);
 // bracket-max flags over the level's index space, one thread per (cell, group
 // of a.gblk snapshot blocks), into the zeroed bitmap a.flags_bits
 cudaError_t launch_flag_dense(const FlagArgs &a, int ngroup, cudaStream_t s);
+// The same flags in two passes: a bound pass lists the (cell, snapshot block)
+// pairs whose bound can exceed tol, an evaluation pass takes one snapshot of a
+// listed block per thread.  ctr[0] = listed pairs, ctr[1] = nonzero when the
+// list overflowed cap (the flags are then incomplete; ctr zeroed beforehand).
+struct FlagWork {
+    unsigned long long *items;  // (cell index << 16) | block
+    unsigned long long *ctr;
+    long long cap;
+};
+cudaError_t launch_flag_twopass(const FlagArgs &a, const FlagWork &w, int eval_grid, cudaStream_t s);
 
 // terms weight*(q0*area) of the functional into out[0..n)
 cudaError_t launch_func_terms(const long long *idx, const double *area, long long n, const double *q, double weight,

@@ -620,6 +620,138 @@ __global__ void k_flag_dense(FlagArgs A)
     }
 }
 
+// count and bounding box of this warp's flags: a shuffle reduction and one
+// set of atomics per warp (every lane calls it)
+__device__ __forceinline__ void flag_reduce(const FlagArgs &A, bool any_hit, unsigned nfresh, int fI, int gI, int fJ,
+                                            int gJ)
+{
+    const unsigned total = __reduce_add_sync(0xffffffffu, nfresh);
+    if (__any_sync(0xffffffffu, any_hit)) {
+        fI = __reduce_min_sync(0xffffffffu, fI);
+        fJ = __reduce_min_sync(0xffffffffu, fJ);
+        gI = __reduce_max_sync(0xffffffffu, gI);
+        gJ = __reduce_max_sync(0xffffffffu, gJ);
+        if ((threadIdx.x & 31) == 0) {
+            if (total) atomicAdd(A.count, (unsigned long long)total);
+            atomicMin(A.bbox + 0, fI);
+            atomicMax(A.bbox + 1, gI);
+            atomicMin(A.bbox + 2, fJ);
+            atomicMax(A.bbox + 3, gJ);
+        }
+    }
+}
+
+// Pass 1 of the two-pass flagging: one thread per cell of the level's index
+// space.  Cells whose test needs no snapshot (dry adjoint cell, fewer than 2
+// snapshots, empty window) are decided here; for the others every snapshot
+// block of the window whose bound sum_f |q_f| max |q^_f| can exceed tol (see
+// k_flag) is appended to the work list, a warp at a time.
+template <int MF>
+__global__ void k_flag_bound(FlagArgs A, FlagWork W)
+{
+    const long long NM = (long long)A.N * A.M;
+    const long long cidx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    bool hit = false, active = false;
+    unsigned fresh = 0;
+    int fI = 0x7fffffff, fJ = 0x7fffffff, gI = -1, gJ = -1;
+    double Q[MF];
+#pragma unroll
+    for (int f = 0; f < MF; f++) Q[f] = 0.0;
+    long long acell = 0;
+    if (cidx < NM) {
+        const int o = A.owner[cidx];
+        if (o >= 0) {
+            const int J = (int)(cidx / A.N), I = (int)(cidx - (long long)J * A.N);
+            const int ac = A.tab_ac[I], bc = (A.dim == 2) ? A.tab_bc[J] : 0;
+            const bool dry = A.wet && !A.wet[(long long)bc * A.ax + ac];
+            if (A.S < 2 || dry || A.nlo > A.nhi) {
+                hit = 0.0 > A.tol;
+                if (hit) {
+                    const unsigned long long bit = 1ull << (I & 63);
+                    fresh = (atomicOr(A.flags_bits + (long long)J * A.pitch64 + (I >> 6), bit) & bit) == 0;
+                    fI = gI = I;
+                    fJ = gJ = J;
+                }
+            } else {
+                active = true;
+#pragma unroll
+                for (int f = 0; f < MF; f++) Q[f] = A.q[(long long)f * A.stride + o];
+                const int a = A.tab_a[I], b = (A.dim == 2) ? A.tab_b[J] : 0;
+                acell = (long long)b * A.ax + a;
+            }
+        }
+    }
+    // the window's blocks are the same for every thread of the launch
+    const long long plane = (long long)A.ax * A.ay;
+    const int b1 = (A.nlo <= A.nhi) ? A.nhi / kSnapBlock : -1;
+    for (int blk = A.nlo / kSnapBlock; blk <= b1; blk++) {
+        bool push = false;
+        if (active) {
+            double B = 0.0;
+#pragma unroll
+            for (int f = 0; f < MF; f++) B = fma(fabs(Q[f]), A.bmax[((long long)blk * MF + f) * plane + acell], B);
+            push = B * (1.0 + 1e-12) > A.tol;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, push);
+        if (m) {
+            const int leader = __ffs(m) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(W.ctr, (unsigned long long)__popc(m));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (push) {
+                const unsigned long long slot = base + __popc(m & ((1u << lane) - 1u));
+                if (slot < (unsigned long long)W.cap) W.items[slot] = ((unsigned long long)cidx << 16) | (unsigned)blk;
+                else W.ctr[1] = 1;
+            }
+        }
+    }
+    flag_reduce(A, hit, fresh, fI, gI, fJ, gJ);
+}
+
+// Pass 2: thread t evaluates snapshot t % 8 of listed block t / 8 (a grid
+// striding over the list), skipping cells already flagged.
+template <int MF>
+__global__ void k_flag_eval(FlagArgs A, FlagWork W)
+{
+    const unsigned long long listed = W.ctr[0];
+    const unsigned long long nitem = listed < (unsigned long long)W.cap ? listed : (unsigned long long)W.cap;
+    const unsigned long long total = nitem * kSnapBlock;
+    bool any = false;
+    unsigned fresh = 0;
+    int fI = 0x7fffffff, fJ = 0x7fffffff, gI = -1, gJ = -1;
+    for (unsigned long long t = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long item = W.items[t / kSnapBlock];
+        const int n = (int)(item & 0xffff) * kSnapBlock + (int)(t % kSnapBlock);
+        if (n < A.nlo || n > A.nhi) continue;
+        const long long cidx = (long long)(item >> 16);
+        const int J = (int)(cidx / A.N), I = (int)(cidx - (long long)J * A.N);
+        unsigned long long *word = A.flags_bits + (long long)J * A.pitch64 + (I >> 6);
+        const unsigned long long bit = 1ull << (I & 63);
+        if (*(volatile unsigned long long *)word & bit) continue;  // decided by another snapshot
+        const int o = A.owner[cidx];
+        const int a = A.tab_a[I], b = (A.dim == 2) ? A.tab_b[J] : 0;
+        const double wx = A.tab_wx[I], wy = (A.dim == 2) ? A.tab_wy[J] : 0.0;
+        double d = 0.0;
+#pragma unroll
+        for (int f = 0; f < MF; f++) {
+            const double av = adj_interp(A, n, f, a, wx, b, wy);
+            const double qf = A.q[(long long)f * A.stride + o];
+            d = (f == 0) ? av * qf : d + av * qf;
+        }
+        if (fabs(d) > A.tol) {
+            any = true;
+            if ((atomicOr(word, bit) & bit) == 0) fresh++;
+            fI = min(fI, I);
+            gI = max(gI, I);
+            fJ = min(fJ, J);
+            gJ = max(gJ, J);
+        }
+    }
+    flag_reduce(A, any, fresh, fI, gI, fJ, gJ);
+}
+
 __global__ void k_block_max(const double *__restrict__ snaps, int S, int m, int ax, int ay, int dim, int nblk,
                             double *bmax)
 {
@@ -770,6 +902,23 @@ cudaError_t launch_gauges(const GaugeArgs &g, cudaStream_t s)
 {
     if (g.n <= 0) return cudaSuccess;
     k_gauges<<<(g.n + kT - 1) / kT, kT, 0, s>>>(g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flag_twopass(const FlagArgs &a, const FlagWork &w, int eval_grid, cudaStream_t s)
+{
+    const long long nm = (long long)a.N * a.M;
+    if (nm <= 0) return cudaSuccess;
+    const unsigned nb = (unsigned)((nm + kT - 1) / kT);
+    if (a.m == 3) {
+        k_flag_bound<3><<<nb, kT, 0, s>>>(a, w);
+        k_flag_eval<3><<<eval_grid, kT, 0, s>>>(a, w);
+    } else if (a.m == 2) {
+        k_flag_bound<2><<<nb, kT, 0, s>>>(a, w);
+        k_flag_eval<2><<<eval_grid, kT, 0, s>>>(a, w);
+    } else {
+        return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

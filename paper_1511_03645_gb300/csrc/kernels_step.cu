@@ -706,6 +706,25 @@ cudaError_t launch_step(int dim, int eqn, int tx, int ty, const double *q, doubl
     }
 }
 
+bool step_kernel_shape(int dim, int tx, int ty, int *kx, int *ky)
+{
+    if (tx < 1 || ty < 1) return false;
+    if (dim == 1) {
+        if (tx > 256) return false;
+        *kx = tx <= 128 ? 128 : 256;
+        *ky = 1;
+        return true;
+    }
+    static const int shapes[6][2] = {{8, 8}, {16, 8}, {32, 8}, {16, 16}, {64, 8}, {32, 16}};
+    for (const auto &sh : shapes)
+        if (tx <= sh[0] && ty <= sh[1]) {
+            *kx = sh[0];
+            *ky = sh[1];
+            return true;
+        }
+    return false;
+}
+
 int step_occupancy(int dim, int eqn, int tx, int ty)
 {
     if (dim == 1) return 4;

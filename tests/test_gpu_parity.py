@@ -96,11 +96,12 @@ def test_uniform_grid_steps_match_oracle_bitwise(A, dim, eqn, bc):
     assert np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("tile", [(16, 8), (16, 16), (32, 16), (64, 8), (8, 8)])
+@pytest.mark.parametrize("tile", [(16, 8), (16, 16), (32, 16), (64, 8), (8, 8), (12, 8), (24, 12), (5, 3)])
 @pytest.mark.parametrize("mode", [0, 1, 2, 3])
 def test_tile_shapes_and_launch_modes_agree_bitwise(A, tile, mode):
-    """Every tile shape and launch mode (work-list, persistent, per patch)
-    computes the same bits as the default configuration."""
+    """Every tile size (compiled shapes and smaller cuts run by the smallest
+    compiled shape holding them) and launch mode (work-list, persistent, per
+    patch, dynamic) computes the same bits as the default configuration."""
     rng = np.random.default_rng(7)
     N = 70
     fields = np.stack([rng.uniform(1, 3, (N, N)), rng.uniform(1, 30, (N, N))])
@@ -221,7 +222,8 @@ def test_per_level_kernels_compute_the_same_bits(A):
     adj = A.solve_adjoint(wl)
     runs = []
     for cfg in (None, [((8, 8), False, 3), ((16, 16), True, 0), ((64, 8), False, 3)],
-                [((32, 16), True, 3), ((16, 8), False, 1), ((8, 8), True, 3)]):
+                [((32, 16), True, 3), ((16, 8), False, 1), ((8, 8), True, 3)],
+                [((12, 8), True, 0), ((24, 12), False, 0), ((12, 8), False, 0)]):
         h = A.Hierarchy(wl)
         h.set_adjoint(adj)
         h.set_timing(True)
@@ -244,7 +246,9 @@ def test_per_level_kernels_compute_the_same_bits(A):
         assert all(np.array_equal(a, b) for a, b in zip(pt, runs[0][2]))
     h = A.Hierarchy(wl)
     with pytest.raises(A.AdjamrError):
-        h.set_level_kernel(0, (24, 8))
+        h.set_level_kernel(0, (40, 16))   # no compiled tile holds 40 x 16
+    with pytest.raises(A.AdjamrError):
+        h.set_level_kernel(0, (0, 8))
     with pytest.raises(A.AdjamrError):
         h.set_level_kernel(wl.nlevels, (32, 8))
     with pytest.raises(A.AdjamrError):
