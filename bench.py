@@ -196,10 +196,10 @@ def run_ours(args, rank, world):
     tuned = AT.tune_amr(wl, adj, key="acoustics2d-100-r2r4", stream=s, use_cache=False)
     log(f"tiles per level: {tuned['best_per_level']}")
 
-    def make():
+    def make(timing=False):
         h = A.Hierarchy(wl, stream=sp)
         h.set_adjoint(adj)
-        h.set_timing(True)
+        h.set_timing(timing)
         AT.apply_amr(h, tuned)
         return h
 
@@ -246,22 +246,30 @@ def run_ours(args, rank, world):
         st = h.stats()
         cu += st["cell_updates"]
         launches += st["kernel_launches"]
-        step_ms += st["step_kernel_ms"]
-        step_launches += st["step_kernel_launches"]
         regrid_ms += st["regrid_host_ms"]
         cluster_ms += st["cluster_host_ms"]
         rebuilds += st["level_rebuilds"]
         phases = [a + b for a, b in zip(phases, st["regrid_phase_ms"])]
         cphases = [a + b for a, b in zip(cphases, st["cluster_phase_ms"])]
-        for lev in range(wl.nlevels):
-            lev_ms[lev] += st["level_step_ms"][lev]
-            lev_launch[lev] += st["level_step_launches"][lev]
-            lev_cells[lev] += st["level_cell_updates"][lev]
         Js.append(J)
     torch.cuda.synchronize()
     if dist:
         td.barrier()
     ck = clocks.stop()
+    # step-kernel times from one more solve with CUDA events around every
+    # level's launches (kept out of the timed solves: an event between two
+    # kernels also stops the next one from launching early)
+    hi = make(timing=True)
+    solve(hi)
+    torch.cuda.synchronize()
+    st = hi.stats()
+    hi.close()
+    step_ms = st["step_kernel_ms"] * args.steps
+    step_launches = st["step_kernel_launches"] * args.steps
+    for lev in range(wl.nlevels):
+        lev_ms[lev] = st["level_step_ms"][lev] * args.steps
+        lev_launch[lev] = st["level_step_launches"][lev] * args.steps
+        lev_cells[lev] = st["level_cell_updates"][lev] * args.steps
     total_ms = sum(times)
     if dist:
         total_ms, cu_all = aggregate(td, total_ms, cu, "cuda")

@@ -8,6 +8,16 @@
 namespace adjamr {
 namespace {
 
+// Programmatic dependent launch (sm_90 and later): a kernel launched with the
+// programmatic-serialization attribute may start before the kernel ahead of it
+// in the stream has finished; pdl_wait() returns once that kernel has
+// completed and its writes are visible (at once for a normal launch).  Every
+// kernel launched that way calls it before its first global memory access, so
+// completions stay in stream order.  pdl_launch_dependents() lets the next
+// such kernel launch as soon as every CTA of this grid has started.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ double minmod(double a, double b)
 {
     if (a > 0.0 && b > 0.0) return fmin(a, b);

@@ -13,6 +13,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdint>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -216,6 +217,15 @@ void cput(adjamr_ctx *c, T *&p)
 
 namespace adjamr {
 void ctx_set_block_cache(adjamr_ctx *c, size_t cap_bytes) { c->blk_cache_cap = cap_bytes; }
+
+bool pdl_enabled()
+{
+    static const bool on = [] {
+        const char *v = std::getenv("ADJAMR_PDL");
+        return !(v && v[0] == '0');
+    }();
+    return on;
+}
 }  // namespace adjamr
 
 namespace {

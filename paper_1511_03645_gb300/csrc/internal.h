@@ -129,6 +129,28 @@ struct TileSched {
     unsigned long long base;
 };
 
+// Programmatic dependent launch of the kernels of the stepping sequence (step,
+// ghost fill, average-down, gauges): on unless the environment sets
+// ADJAMR_PDL=0 (read once).  Results are the same either way.
+bool pdl_enabled();
+#ifdef __CUDACC__
+template <typename... P, typename... A>
+cudaError_t launch_pdl(void (*kern)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<A &&>(args)...);
+}
+#endif
+
 // ---- kernel launchers (kernels_step.cu / kernels_amr.cu) ----
 cudaError_t launch_step(int dim, int eqn, int tx, int ty, const double *q, double *qn, const double *aux,
                         long long stride, const PatchDesc *patches, const WorkItem *work, int nwork, int grid,

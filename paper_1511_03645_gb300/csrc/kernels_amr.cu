@@ -25,6 +25,8 @@ __global__ void k_ghost_fill(int dim, int m, const GhostDesc *__restrict__ gd, l
                              const double *__restrict__ qo, const double *__restrict__ qn_, long long sc, int k,
                              double th)
 {
+    pdl_wait();
+    pdl_launch_dependents();
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
     GhostDesc g = gd[t];
@@ -34,6 +36,8 @@ __global__ void k_ghost_fill(int dim, int m, const GhostDesc *__restrict__ gd, l
 __global__ void k_average_down(int dim, int m, const AvgDesc *__restrict__ ad, long long n,
                                const double *__restrict__ qf, long long sf, double *qc, long long sc, int r)
 {
+    pdl_wait();
+    pdl_launch_dependents();
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
     AvgDesc a = ad[t];
@@ -529,6 +533,8 @@ __global__ void k_flag(FlagArgs A)
 // holding the point on the finest level with a patch there.
 __global__ void k_gauges(GaugeArgs G)
 {
+    pdl_wait();
+    pdl_launch_dependents();
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= G.n) return;
     double *o = G.out + (long long)g * (1 + G.m);
@@ -824,16 +830,14 @@ cudaError_t launch_ghost_fill(int dim, int m, const GhostDesc *g, long long n, d
 {
     if (n <= 0) return cudaSuccess;
     const double th = (double)k / (double)r;  // same division as the oracle's, on the host
-    k_ghost_fill<<<nblk(n), kT, 0, s>>>(dim, m, g, n, qf, sf, qc_old, qc_new, sc, k, th);
-    return cudaGetLastError();
+    return launch_pdl(k_ghost_fill, dim3(nblk(n)), dim3(kT), 0, s, dim, m, g, n, qf, sf, qc_old, qc_new, sc, k, th);
 }
 
 cudaError_t launch_average_down(int dim, int m, const AvgDesc *a, long long n, const double *qf, long long sf,
                                 double *qc, long long sc, int r, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    k_average_down<<<nblk(n), kT, 0, s>>>(dim, m, a, n, qf, sf, qc, sc, r);
-    return cudaGetLastError();
+    return launch_pdl(k_average_down, dim3(nblk(n)), dim3(kT), 0, s, dim, m, a, n, qf, sf, qc, sc, r);
 }
 
 cudaError_t launch_aux_fill(int eqn, int dim, const AuxDesc *d, long long n, double *aux, double *med,
@@ -901,8 +905,7 @@ cudaError_t launch_block_max(const double *snaps, int S, int m, int ax, int ay, 
 cudaError_t launch_gauges(const GaugeArgs &g, cudaStream_t s)
 {
     if (g.n <= 0) return cudaSuccess;
-    k_gauges<<<(g.n + kT - 1) / kT, kT, 0, s>>>(g);
-    return cudaGetLastError();
+    return launch_pdl(k_gauges, dim3((g.n + kT - 1) / kT), dim3(kT), 0, s, g);
 }
 
 cudaError_t launch_flag_twopass(const FlagArgs &a, const FlagWork &w, int eval_grid, cudaStream_t s)

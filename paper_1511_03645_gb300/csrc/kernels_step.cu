@@ -286,6 +286,8 @@ __global__ void __launch_bounds__(kThreads) k_step2d(const double *__restrict__ 
                                                      unsigned long long *cfl_bits, GhostArgs ga, TileSched sc)
 {
     using S = Smem2D<EQN, TX, TY>;
+    pdl_wait();
+    pdl_launch_dependents();
     extern __shared__ double sm[];
     double *sQ = sm;
     double *sA = sQ + S::nQ;
@@ -526,6 +528,8 @@ __global__ void __launch_bounds__(kThreads) k_step1d(const double *__restrict__ 
                                                      unsigned long long *cfl_bits, GhostArgs ga, TileSched sc)
 {
     using S = Smem1D<EQN, TX>;
+    pdl_wait();
+    pdl_launch_dependents();
     extern __shared__ double sm[];
     constexpr int PX = S::PX, XE = S::XE, XNn = S::XN;
     double *sQ = sm;
@@ -627,8 +631,8 @@ cudaError_t launch_kernel(size_t smem, int nwork, int grid, const double *q, dou
     if (e != cudaSuccess) return e;
     if (nwork <= 0) return cudaSuccess;
     int g = grid > 0 ? grid : nwork;
-    kern<<<g, kThreads, smem, s>>>(q, qn, aux, stride, patches, work, nwork, cfl_bits, ga, sc);
-    return cudaGetLastError();
+    return launch_pdl(kern, dim3(g), dim3(kThreads), smem, s, q, qn, aux, stride, patches, work, nwork, cfl_bits, ga,
+                      sc);
 }
 
 template <int EQN>
