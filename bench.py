@@ -670,8 +670,8 @@ def run_case_solve(args):
     """Profiling case: one config-2 forward solve to --tf (adjoint solved
     first) with the step-kernel tile and ghost mode of every level given by
     --kernels (default: the configuration the autotuner picks on a GB300,
-    8x8 fused, 8x8 fused, 16x8 with a separate ghost fill); prints per-level
-    step statistics."""
+    12x8 fused, 8x8 fused, 16x12 with a separate ghost fill); prints
+    per-level step statistics."""
     import torch
     from paper_1511_03645_gb300 import adjamr as A
     torch.cuda.set_device(0)
@@ -715,7 +715,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--case", default="main", choices=["main", "batch", "serve", "solve", "paper"])
     ap.add_argument("--tf", type=float, default=0.0, help="solve case: final time (0: the workload's)")
-    ap.add_argument("--kernels", default="8x8f,8x8f,16x8",
+    ap.add_argument("--kernels", default="12x8f,8x8f,16x12",
                     help="solve case: per-level step tile, suffix f = ghost ring computed in the step kernel")
     ap.add_argument("--nreq", type=int, default=512)
     ap.add_argument("--rates", default="0.5,0.8,1.0", help="serve case: offered rates as fractions of saturation")
