@@ -270,6 +270,17 @@ adjamr_status adjamr_set_gauges(adjamr_ctx *ctx, int n, const double *x, const d
  * null with cap = 0); *nrec = number of records held.  Synchronises the
  * context's stream. */
 adjamr_status adjamr_read_gauges(adjamr_ctx *ctx, double *out, long long cap, long long *nrec);
+/* Berger-Rigoutsos clustering (Sec. 3, regridding) as the regrid runs it, on
+ * the host: flags[M][N] (0/1; the regrid clears flags where no patch may lie
+ * before it clusters) and nestable[M][N] (nonzero where a patch may cover the
+ * cell: a box over another cell is split; NULL: everywhere) in, boxes out as
+ * (i0, i1, j0, j1)
+ * inclusive, sorted by (j0, i0), for at most cap boxes; *nboxes = the number
+ * of boxes (more than cap: only cap written).  min_cells = smallest side a
+ * split may leave, efficiency = flagged fraction a box must reach.  No GPU is
+ * involved.  Errors: EINVAL. */
+adjamr_status adjamr_cluster_boxes(const unsigned char *flags, const unsigned char *nestable, int N, int M, int dim,
+                                   int min_cells, double efficiency, int *boxes, int cap, int *nboxes);
 /* Level-0 step and number of level-0 steps to reach tf. */
 adjamr_status adjamr_time_info(adjamr_ctx *ctx, double *dt0, int *nsteps_to_tf);
 const char *adjamr_last_error(adjamr_ctx *ctx);

@@ -97,7 +97,7 @@ SYMBOLS = [
     "adjamr_advance_level", "adjamr_flag_cells", "adjamr_integrate_functional", "adjamr_get_patches",
     "adjamr_read_level", "adjamr_write_level", "adjamr_fill_ghosts", "adjamr_read_patch_ghosted",
     "adjamr_step_level_only", "adjamr_get_stats", "adjamr_set_timing", "adjamr_set_level_kernel", "adjamr_set_gauges",
-    "adjamr_read_gauges", "adjamr_time_info",
+    "adjamr_read_gauges", "adjamr_cluster_boxes", "adjamr_time_info",
     "adjamr_last_error",
     "adjamr_destroy", "adjamr_batch_create", "adjamr_batch_set_order", "adjamr_batch_set_ghost_fusion",
     "adjamr_batch_step",
@@ -150,6 +150,7 @@ def load(build_if_missing: bool = True):
             "adjamr_set_timing": [vp, i],
             "adjamr_set_level_kernel": [vp, i, i, i, i, i],
             "adjamr_set_gauges": [vp, i, dp, dp],
+            "adjamr_cluster_boxes": [ucp, ucp, i, i, i, i, d, ip, i, ip],
             "adjamr_read_gauges": [vp, dp, ll, ctypes.POINTER(ll)],
             "adjamr_time_info": [vp, dp, ip],
             "adjamr_batch_create": [i, ip, ip, dp, dp, dp, dp, dp, ip, P(Medium), i, dp, vp, P(vp)],
@@ -627,3 +628,22 @@ def weighted_sum_noalloc(q_ptr: int, w_ptr: int, n: int, weight: float, out_ptr:
     rc = load().adjamr_weighted_sum_noalloc(ctypes.c_void_p(q_ptr), ctypes.c_void_p(w_ptr), int(n), float(weight),
                                             ctypes.c_void_p(out_ptr), ctypes.c_void_p(stream) if stream else None)
     _check(rc, None, "weighted_sum_noalloc")
+
+
+def cluster_boxes(flags: np.ndarray, mc: int = 1, eff: float = 0.7, nest: np.ndarray | None = None) -> np.ndarray:
+    """Boxes (i0, i1, j0, j1) of the library's Berger-Rigoutsos clustering of a
+    flag field [M, N] (host code, no GPU)."""
+    flags = np.ascontiguousarray(flags, dtype=np.uint8)
+    M, N = flags.shape
+    dim = 2 if M > 1 else 1
+    cap = N * M + 1
+    out = np.zeros((cap, 4), dtype=np.int32)
+    n = ctypes.c_int(0)
+    npt = None
+    if nest is not None:
+        nest = np.ascontiguousarray(nest, dtype=np.uint8)
+        npt = nest.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))
+    _check(load().adjamr_cluster_boxes(flags.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)), npt, N, M, dim, mc, eff,
+                                       out.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), cap, ctypes.byref(n)),
+           None, "cluster_boxes")
+    return out[:n.value].copy()

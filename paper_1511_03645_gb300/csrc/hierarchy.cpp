@@ -103,6 +103,8 @@ struct adjamr_ctx {
     int *d_err = nullptr;  // device-side invariant violations (nesting), checked after syncs
     int *d_bbox = nullptr; // bounding box of flagged cells of the last flag call
     Bits h_fl, h_unc;               // host clustering scratch (regrid window)
+    std::vector<int> h_sort_cnt;    // work-list ordering scratch
+    std::vector<WorkItem> h_sort_tmp;
     std::vector<uint64_t> h_tmp;
     std::vector<int> h_cnt;
     // pinned staging for descriptor uploads; reused once the event of the
@@ -370,10 +372,19 @@ adjamr_status build_work(adjamr_ctx *c, int l, int tx, int ty)
     }
     // one launch over the level: largest tiles first, so that the last CTAs
     // to start are the short ones (one launch per patch keeps patch order)
-    if (lpt)
-        std::stable_sort(L.h_work.begin(), L.h_work.end(), [](const WorkItem &a, const WorkItem &b) {
-            return (int)a.tx * a.ty > (int)b.tx * b.ty;
-        });
+    if (lpt && L.h_work.size() > 1) {
+        // stable counting sort by tile area, largest first (areas <= 64 x 16)
+        int amax = 0;
+        for (const WorkItem &w : L.h_work) amax = std::max(amax, (int)w.tx * w.ty);
+        std::vector<int> &start = c->h_sort_cnt;
+        start.assign((size_t)amax + 2, 0);
+        for (const WorkItem &w : L.h_work) start[(size_t)(amax - (int)w.tx * w.ty) + 1]++;
+        for (size_t k = 1; k < start.size(); k++) start[k] += start[k - 1];
+        std::vector<WorkItem> &out = c->h_sort_tmp;
+        out.resize(L.h_work.size());
+        for (const WorkItem &w : L.h_work) out[(size_t)start[(size_t)(amax - (int)w.tx * w.ty)]++] = w;
+        L.h_work.swap(out);
+    }
     L.nwork = (int)L.h_work.size();
     std::vector<size_t> offs;
     char *dw = nullptr;
@@ -2161,6 +2172,46 @@ adjamr_status adjamr_step_level_only(adjamr_ctx *ctx, int level)
     L.nstep++;
     CKR(ctx, cudaStreamSynchronize(ctx->s));
     return ADJAMR_OK;
+}
+
+adjamr_status adjamr_cluster_boxes(const unsigned char *flags, const unsigned char *nestable, int N, int M, int dim,
+                                   int min_cells, double efficiency, int *boxes, int cap, int *nboxes)
+{
+    if (!flags || N < 1 || M < 1 || (dim != 1 && dim != 2) || (dim == 1 && M != 1) || min_cells < 1 || cap < 0 ||
+        (cap > 0 && !boxes) || !nboxes)
+        return ADJAMR_EINVAL;
+    try {
+        Bits fl, un;
+        fl.reset(N, M);
+        un.reset(N, M);
+        for (int j = 0; j < M; j++)
+            for (int i = 0; i < N; i++) {
+                const size_t k = (size_t)j * N + i;
+                if (flags[k]) fl.row(j)[i >> 6] |= 1ull << (i & 63);
+                if (nestable && !nestable[k]) un.row(j)[i >> 6] |= 1ull << (i & 63);
+            }
+        Clusterer cl;
+        cl.N = N;
+        cl.M = M;
+        cl.dim = dim;
+        cl.mc = min_cells;
+        cl.eff = efficiency;
+        cl.init(fl, un);
+        cl.run(Box{0, N - 1, 0, M - 1});
+        std::vector<Box> out = cl.out;
+        std::sort(out.begin(), out.end(),
+                  [](const Box &a, const Box &b) { return a.j0 != b.j0 ? a.j0 < b.j0 : a.i0 < b.i0; });
+        *nboxes = (int)out.size();
+        for (int k = 0; k < (int)out.size() && k < cap; k++) {
+            boxes[4 * k + 0] = out[k].i0;
+            boxes[4 * k + 1] = out[k].i1;
+            boxes[4 * k + 2] = out[k].j0;
+            boxes[4 * k + 3] = out[k].j1;
+        }
+        return ADJAMR_OK;
+    } catch (...) {
+        return ADJAMR_ENOMEM;
+    }
 }
 
 adjamr_status adjamr_set_level_kernel(adjamr_ctx *ctx, int level, int tile_x, int tile_y, int fuse_ghosts,
