@@ -48,7 +48,7 @@ OPS_PER_CELL_2D = 170
 # launches average 40,920 cells): 1.2x the 80 algorithmic bytes per
 # cell-update (tile halos and descriptors); written lines stay in L2 within
 # the launch.
-TRAFFIC_PER_CELL_L2 = 3.978496e6 / 40920.0
+TRAFFIC_PER_CELL_L2 = 3.975936e6 / 40920.0
 
 
 def log(*a):
