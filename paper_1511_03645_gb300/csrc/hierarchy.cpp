@@ -1102,7 +1102,7 @@ adjamr_status flag_tables(adjamr_ctx *c, int l)
     return ADJAMR_OK;
 }
 
-adjamr_status ghost_fill(adjamr_ctx *c, int l, int k);
+adjamr_status ghost_fill(adjamr_ctx *c, int l, int k, bool early = false);
 
 adjamr_status flag_dense(adjamr_ctx *c, int l, double tol, uint64_t *d_bits, int pitch64, unsigned char *d_patchflags,
                          long long *nflag_out, int *bbox_out)
@@ -1245,7 +1245,10 @@ adjamr_status flag_readback(adjamr_ctx *c, int l, uint64_t *d_bits, int pitch64,
     return ADJAMR_OK;
 }
 
-adjamr_status ghost_fill(adjamr_ctx *c, int l, int k)
+// early: the caller knows that the kernel ahead in the stream writes only
+// interior cells of level l or cells of finer levels, and that level l - 1 is
+// final for this substep (see k_ghost_fill)
+adjamr_status ghost_fill(adjamr_ctx *c, int l, int k, bool early)
 {
     Level &L = c->L[l];
     if (L.nghost == 0) return ADJAMR_OK;
@@ -1259,7 +1262,8 @@ adjamr_status ghost_fill(adjamr_ctx *c, int l, int k)
         sc = C.ncell;
         r = c->P.ratio[l - 1];
     }
-    CKR(c, launch_ghost_fill(c->P.dim, c->m, L.d_ghost, L.nghost, L.q[L.cur], L.ncell, qo, qn, sc, k, r, c->s));
+    CKR(c, launch_ghost_fill(c->P.dim, c->m, L.d_ghost, L.nghost, L.q[L.cur], L.ncell, qo, qn, sc, k, r, c->s,
+                             early && l > 0 && k > 0));
     c->st.kernel_launches++;
     return ADJAMR_OK;
 }
@@ -1287,7 +1291,7 @@ enum GhostMode { GHOST_READY = 0, GHOST_FUSED = 1, GHOST_FILL = 2 };
 // GHOST_FUSED: the step kernel computes the ghost ring while staging;
 // GHOST_FILL: the ghost-fill kernel runs first; GHOST_READY: the ring of
 // q[cur] was filled beforehand.  Both ways give the same bits.
-adjamr_status step_patches(adjamr_ctx *c, int l, int k, GhostMode gm)
+adjamr_status step_patches(adjamr_ctx *c, int l, int k, GhostMode gm, bool early_ghosts = false)
 {
     Level &L = c->L[l];
     if (L.patches.empty()) return ADJAMR_OK;
@@ -1307,7 +1311,7 @@ adjamr_status step_patches(adjamr_ctx *c, int l, int k, GhostMode gm)
         c->tev_used += 2;
         CKR(c, cudaEventRecord(tb, c->s));
     }
-    if (gm == GHOST_FILL) TRY(ghost_fill(c, l, k));
+    if (gm == GHOST_FILL) TRY(ghost_fill(c, l, k, early_ghosts));
     const double *q = L.q[L.cur];
     double *qn = L.q[1 - L.cur];
     const int mode = c->lmode[l];
@@ -1387,11 +1391,17 @@ adjamr_status step_level(adjamr_ctx *c, int l)
     Level &L = c->L[l];
     const adjamr_params &P = c->P;
     int k = P.regrid_interval;
-    if (l < P.nlevels - 1 && k > 0 && L.nstep > 0 && L.nstep % k == 0 && c->rebuilt_tick[l + 1] != L.nstep * c->T[l])
+    bool regridded = false;
+    if (l < P.nlevels - 1 && k > 0 && L.nstep > 0 && L.nstep % k == 0 && c->rebuilt_tick[l + 1] != L.nstep * c->T[l]) {
         TRY(regrid_from(c, l, 0));
+        regridded = true;
+    }
     int sub = 0;
     if (l > 0) sub = (int)(L.nstep - c->L[l - 1].nstep * P.ratio[l - 1]);
-    TRY(step_patches(c, l, sub, c->lfuse[l] ? GHOST_FUSED : GHOST_FILL));
+    // After the first substep and without a rebuild in between, the kernel
+    // ahead is this level's previous step, the average-down into it or a
+    // finer level's kernel; none of them touches this level's ghost cells.
+    TRY(step_patches(c, l, sub, c->lfuse[l] ? GHOST_FUSED : GHOST_FILL, sub > 0 && !regridded));
     if (l < P.nlevels - 1 && !c->L[l + 1].patches.empty()) {
         int r = P.ratio[l];
         c->L[l + 1].nstep = L.nstep * r;

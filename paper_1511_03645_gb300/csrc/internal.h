@@ -129,6 +129,22 @@ struct TileSched {
     unsigned long long base;
 };
 
+// Several substeps of one level in one launch (k_step2d_sub).  dep_off /
+// dep_idx (CSR over the work list): the tiles whose interior cells a tile's
+// staged region reads, itself included.  done[w] = base + substeps tile w has
+// completed in this launch (values from earlier launches are <= base).
+constexpr int kMaxSubsteps = 16;
+constexpr unsigned long long kSubstepWaitNs = 1000000000ull;  // a wait gives up after 1 s
+constexpr unsigned int kSubstepWaitSpins = 1u << 24;
+struct SubstepArgs {
+    const int *dep_off, *dep_idx;
+    unsigned long long *done;
+    unsigned long long base;
+    int nsub;
+    int *err;                  // set to 1 when a wait gave up
+    double th[kMaxSubsteps];   // ghost-ring time fraction (k0 + s) / r per substep, divided on the host
+};
+
 // Programmatic dependent launch of the kernels of the stepping sequence (step,
 // ghost fill, average-down, gauges): on unless the environment sets
 // ADJAMR_PDL=0 (read once).  Results are the same either way.
@@ -157,14 +173,25 @@ cudaError_t launch_step(int dim, int eqn, int tx, int ty, const double *q, doubl
                         unsigned long long *cfl_bits, cudaStream_t s, GhostArgs ga = GhostArgs{nullptr, nullptr, nullptr, 0, 0, 0.0},
                         TileSched sc = TileSched{nullptr, 0});
 int step_occupancy(int dim, int eqn, int tx, int ty);
+// sa.nsub steps of a 2D level in one launch of `grid` CTAs that take items
+// from sc (sc.ctr required; the counter advances by nsub * nwork + grid).
+// Kernel tiles 8x8, 16x8 and 16x16 only; ga.gd required (the ghost ring is
+// computed in the kernel), ga.k = the first substep.
+cudaError_t launch_step_substeps(int eqn, int tx, int ty, double *qa, double *qb, const double *aux, long long stride,
+                                 const PatchDesc *patches, const WorkItem *work, int nwork, int grid,
+                                 unsigned long long *cfl_bits, cudaStream_t s, const GhostArgs &ga,
+                                 const TileSched &sc, const SubstepArgs &sa);
+int substep_occupancy(int eqn, int tx, int ty);  // 0: no such kernel
 // compiled step-kernel tile (kx, ky) that holds tiles of tx x ty cells: the
 // smallest by area among 8x8, 16x8, 32x8, 16x16, 64x8, 32x16 (1D: 128 or 256);
 // false if none does
 bool step_kernel_shape(int dim, int tx, int ty, int *kx, int *ky);
 
+// early: the kernel ahead in the stream is a step of this level and the
+// coarser level's states are final (see k_ghost_fill)
 cudaError_t launch_ghost_fill(int dim, int m, const GhostDesc *g, long long n, double *qf, long long sf,
                               const double *qc_old, const double *qc_new, long long sc, int k, int r,
-                              cudaStream_t s);
+                              cudaStream_t s, bool early = false);
 cudaError_t launch_average_down(int dim, int m, const AvgDesc *a, long long n, const double *qf, long long sf,
                                 double *qc, long long sc, int r, cudaStream_t s);
 // Fill primary medium (med) and derived coefficients (aux) of the listed

@@ -21,16 +21,31 @@ namespace {
 
 constexpr int kT = 256;
 
+// One thread per (ghost cell, field): short load chains, more of them in
+// flight.  early != 0 (a fine substep after the first, so the coarser level's
+// states are final and the kernel ahead in the stream is a step of this level,
+// which writes only interior cells): the coarse interpolations are written
+// before waiting for that step, so they overlap its tail; the same-level copies
+// read its output and come after the wait.
 __global__ void k_ghost_fill(int dim, int m, const GhostDesc *__restrict__ gd, long long n, double *qf, long long sf,
                              const double *__restrict__ qo, const double *__restrict__ qn_, long long sc, int k,
-                             double th)
+                             double th, int early)
 {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = t < n * m;
+    const long long gi = valid ? t / m : 0;
+    const int f = (int)(t - gi * m);
+    bool done = false;
+    if (early && valid && gd[gi].kind != 0) {
+        const GhostDesc &g = gd[gi];
+        qf[(long long)f * sf + g.dst] = ghost_value(g, qf, sf, qo, qn_, sc, f, k, th, dim);
+        done = true;
+    }
     pdl_wait();
     pdl_launch_dependents();
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    GhostDesc g = gd[t];
-    for (int f = 0; f < m; f++) qf[(long long)f * sf + g.dst] = ghost_value(g, qf, sf, qo, qn_, sc, f, k, th, dim);
+    if (!valid || done) return;
+    const GhostDesc &g = gd[gi];
+    qf[(long long)f * sf + g.dst] = ghost_value(g, qf, sf, qo, qn_, sc, f, k, th, dim);
 }
 
 __global__ void k_average_down(int dim, int m, const AvgDesc *__restrict__ ad, long long n,
@@ -826,11 +841,13 @@ inline unsigned nblk_of(long long n) { return nblk(n); }
 }  // namespace
 
 cudaError_t launch_ghost_fill(int dim, int m, const GhostDesc *g, long long n, double *qf, long long sf,
-                              const double *qc_old, const double *qc_new, long long sc, int k, int r, cudaStream_t s)
+                              const double *qc_old, const double *qc_new, long long sc, int k, int r, cudaStream_t s,
+                              bool early)
 {
     if (n <= 0) return cudaSuccess;
     const double th = (double)k / (double)r;  // same division as the oracle's, on the host
-    return launch_pdl(k_ghost_fill, dim3(nblk(n)), dim3(kT), 0, s, dim, m, g, n, qf, sf, qc_old, qc_new, sc, k, th);
+    return launch_pdl(k_ghost_fill, dim3(nblk(n * m)), dim3(kT), 0, s, dim, m, g, n, qf, sf, qc_old, qc_new, sc, k, th,
+                      early && pdl_enabled() ? 1 : 0);
 }
 
 cudaError_t launch_average_down(int dim, int m, const AvgDesc *a, long long n, const double *qf, long long sf,
