@@ -419,7 +419,8 @@ def run_ours(args, rank, world):
                                   "clustering_phases": dict(zip(["dilate_nest", "integral_images", "bisection",
                                                                  "split_sort"], [v / args.steps for v in cphases]))},
         "autotune_levels_ms": {f"{t['tile'][0]}x{t['tile'][1]}{'' if t['fuse_ghosts'] else '+fill'}"
-                               f"{'+dyn' if t['mode'] == A.LAUNCH_DYNAMIC else ''}":
+                               f"{'+dyn' if t['mode'] == A.LAUNCH_DYNAMIC else ''}"
+                               f"{'+sub' if t['mode'] == A.LAUNCH_SUBSTEPS else ''}":
                                [round(x["ms"], 3) for x in t["levels"]] for t in tuned["candidates"]},
         "adjoint_solve_s": adj_s,
         "J": Js[0],
@@ -683,9 +684,10 @@ def run_case_solve(args):
     for rep in range(1 + args.warmup):
         h = A.Hierarchy(wl, stream=s.cuda_stream)
         for lev, spec in enumerate(args.kernels.split(",")[:wl.nlevels]):
-            fused = spec.endswith("f")
-            tx, ty = (int(v) for v in spec.rstrip("f").split("x"))
-            h.set_level_kernel(lev, (tx, ty), fused)
+            # suffix f: ghost ring in the step kernel; s: substep launches (finest level)
+            fused, sub = spec.endswith("f"), spec.endswith("s")
+            tx, ty = (int(v) for v in spec.rstrip("fs").split("x"))
+            h.set_level_kernel(lev, (tx, ty), fused or sub, A.LAUNCH_SUBSTEPS if sub else A.LAUNCH_WORKLIST)
         h.set_adjoint(adj)
         h.set_timing(True)
         torch.cuda.synchronize()

@@ -71,8 +71,18 @@ enum { ADJAMR_MEDIUM_LAYERED = 1, ADJAMR_MEDIUM_DENSE = 2 };
  * (the default), a persistent grid of (#SMs x occupancy) CTAs striding over
  * the work-list, one launch per patch (the comparison baseline), or a
  * persistent grid whose CTAs take the next tile from an atomic counter
- * (dynamic balancing).  Every mode computes the same bits. */
-enum { ADJAMR_LAUNCH_WORKLIST = 0, ADJAMR_LAUNCH_PERSISTENT = 1, ADJAMR_LAUNCH_PER_PATCH = 2, ADJAMR_LAUNCH_DYNAMIC = 3 };
+ * (dynamic balancing).  SUBSTEPS, on the finest level of a 2D hierarchy with
+ * 8x8, 16x8 or 16x16 kernel tiles: all r substeps of one coarser step in one
+ * launch, each tile starting a substep as soon as the tiles its halo reads
+ * have finished the previous one (ghost ring computed in the kernel); on any
+ * other level it acts as DYNAMIC.  Every mode computes the same bits. */
+enum {
+    ADJAMR_LAUNCH_WORKLIST = 0,
+    ADJAMR_LAUNCH_PERSISTENT = 1,
+    ADJAMR_LAUNCH_PER_PATCH = 2,
+    ADJAMR_LAUNCH_DYNAMIC = 3,
+    ADJAMR_LAUNCH_SUBSTEPS = 4
+};
 
 /* Initial condition callback: fills q_out[f*n + k] for the n cell centres
  * (xc[k], yc[k]) of level `level` (yc = 0 in 1D).  Called on the host by
@@ -259,6 +269,14 @@ adjamr_status adjamr_set_timing(adjamr_ctx *ctx, int enable);
  * or level. */
 adjamr_status adjamr_set_level_kernel(adjamr_ctx *ctx, int level, int tile_x, int tile_y, int fuse_ghosts,
                                       int launch_mode);
+/* Check of the bounded waits of ADJAMR_LAUNCH_SUBSTEPS: one substep launch
+ * (2 substeps) of the finest level in which every tile's second substep
+ * waits on a completion counter that nothing advances.  The waits give up
+ * after about 1 s; the call returns ADJAMR_ETIMEOUT and the elapsed device
+ * time in *wait_ms, and clears the failure, so the context stays usable.  The
+ * level's current state (q[cur]) is not changed.  ESTATE when the finest
+ * level cannot run substep launches or has no patches. */
+adjamr_status adjamr_substep_wait_selftest(adjamr_ctx *ctx, double *wait_ms);
 /* Gauges (time series at points, Sec. 5.2.4 and Sec. 5.3): n points (x[k],
  * y[k]; y is ignored in 1D) recorded on the device after every level-0 step
  * of adjamr_advance_level: the level-0 time, then the m values of the cell

@@ -17,7 +17,7 @@ _lock = threading.Lock()
 _lib = None
 
 OK, EINVAL, ENOMEM, EBUDGET, ECFL, ETIMEOUT, ECUDA, ESTATE, ENEST = range(9)
-LAUNCH_WORKLIST, LAUNCH_PERSISTENT, LAUNCH_PER_PATCH, LAUNCH_DYNAMIC = 0, 1, 2, 3
+LAUNCH_WORKLIST, LAUNCH_PERSISTENT, LAUNCH_PER_PATCH, LAUNCH_DYNAMIC, LAUNCH_SUBSTEPS = 0, 1, 2, 3, 4
 MEDIUM_LAYERED, MEDIUM_DENSE = 1, 2
 _NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "EBUDGET", 4: "ECFL", 5: "ETIMEOUT", 6: "ECUDA", 7: "ESTATE",
           8: "ENEST"}
@@ -96,7 +96,8 @@ SYMBOLS = [
     "adjamr_set_adjoint", "adjamr_adjoint_read", "adjamr_adjoint_release", "adjamr_regrid",
     "adjamr_advance_level", "adjamr_flag_cells", "adjamr_integrate_functional", "adjamr_get_patches",
     "adjamr_read_level", "adjamr_write_level", "adjamr_fill_ghosts", "adjamr_read_patch_ghosted",
-    "adjamr_step_level_only", "adjamr_get_stats", "adjamr_set_timing", "adjamr_set_level_kernel", "adjamr_set_gauges",
+    "adjamr_step_level_only", "adjamr_get_stats", "adjamr_set_timing", "adjamr_set_level_kernel",
+    "adjamr_substep_wait_selftest", "adjamr_set_gauges",
     "adjamr_read_gauges", "adjamr_cluster_boxes", "adjamr_time_info",
     "adjamr_last_error",
     "adjamr_destroy", "adjamr_batch_create", "adjamr_batch_set_order", "adjamr_batch_set_ghost_fusion",
@@ -149,6 +150,7 @@ def load(build_if_missing: bool = True):
             "adjamr_get_stats": [vp, P(Stats)],
             "adjamr_set_timing": [vp, i],
             "adjamr_set_level_kernel": [vp, i, i, i, i, i],
+            "adjamr_substep_wait_selftest": [vp, dp],
             "adjamr_set_gauges": [vp, i, dp, dp],
             "adjamr_cluster_boxes": [ucp, ucp, i, i, i, i, d, ip, i, ip],
             "adjamr_read_gauges": [vp, dp, ll, ctypes.POINTER(ll)],
@@ -396,6 +398,13 @@ class Hierarchy:
         of one level (-1: all levels); results do not depend on them."""
         _check(load().adjamr_set_level_kernel(self.h, level, int(tile[0]), int(tile[1]) if len(tile) > 1 else 1,
                                               1 if fuse_ghosts else 0, int(mode)), self.h, "set_level_kernel")
+
+    def substep_wait_selftest(self):
+        """(status, ms): a substep launch of the finest level whose waits
+        can never be satisfied; expected status ETIMEOUT after about 1 s."""
+        ms = ctypes.c_double()
+        rc = load().adjamr_substep_wait_selftest(self.h, ctypes.byref(ms))
+        return rc, ms.value
 
     # ---- queries ----
     def patches(self, level: int) -> np.ndarray:

@@ -112,8 +112,10 @@ def tune_batch(pb, key: str, stream=None, steps: int = 4, use_cache: bool = True
 
 def tune_amr(wl, adj, key: str, stream=None, coarse_steps: int = 40, use_cache: bool = True) -> dict:
     """Best step-kernel configuration (tile size, ghost ring fused into the
-    step or filled by its own kernel; one work-list launch per level, the
-    dynamic tile counter never won) of every level of an AMR solve.
+    step or filled by its own kernel; one work-list launch per level: the
+    dynamic tile counter never won, and substep launches save less kernel
+    time than their host-side dependency lists cost) of every level of an
+    AMR solve.
 
     Each candidate runs the solve's first coarse steps (regrids included) with
     the same configuration on every level; the hierarchy evolves

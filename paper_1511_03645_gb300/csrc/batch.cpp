@@ -91,7 +91,7 @@ cudaError_t one_step(adjamr_batch *b, int mode, int tx, int ty)
     if (!step_kernel_shape(2, tx, ty, &kx, &ky)) return cudaErrorInvalidValue;
     const double *q = b->q[b->cur];
     double *qn = b->q[1 - b->cur];
-    GhostArgs ga{nullptr, nullptr, nullptr, 0, 0, 0.0};
+    GhostArgs ga{};
     cudaError_t e = cudaSuccess;
     if (b->fuse) {
         ga.gd = b->d_ghost;

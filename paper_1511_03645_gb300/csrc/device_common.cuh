@@ -66,11 +66,62 @@ __device__ __forceinline__ double interp_field(const GhostDesc &g, const double 
     return v;
 }
 
-// value of field f of the ghost cell described by g (copy or interpolation),
-// with the boundary sign of the result
+// load of the level's state; CG: through L2 only, for state written by other
+// CTAs of the running launch
+template <bool CG>
+__device__ __forceinline__ double ldq(const double *p)
+{
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
+}
+
+// The coarse stencil values of interp_field (q0 and the minmod slopes sx, sy
+// of field f at time fraction th), stored for reuse by every fine cell of
+// the coarse cell: p[0..2].
+__device__ __forceinline__ void coarse_stencil(const GhostDesc &g, const double *__restrict__ qo,
+                                               const double *__restrict__ qn_, long long sc, int f, int k, double th,
+                                               int dim, double *p)
+{
+    double q0 = coarse_val(qo, qn_, sc, g.src, f, k, th, g.signs, 0);
+    double qxm = coarse_val(qo, qn_, sc, g.cxm, f, k, th, g.signs, 1);
+    double qxp = coarse_val(qo, qn_, sc, g.cxp, f, k, th, g.signs, 2);
+    p[0] = q0;
+    p[1] = minmod(qxp - q0, q0 - qxm);
+    p[2] = 0.0;
+    if (dim == 2) {
+        double qym = coarse_val(qo, qn_, sc, g.cym, f, k, th, g.signs, 3);
+        double qyp = coarse_val(qo, qn_, sc, g.cyp, f, k, th, g.signs, 4);
+        p[2] = minmod(qyp - q0, q0 - qym);
+    }
+}
+
+// interp_field from stored coarse stencil values (same operations, same bits)
+__device__ __forceinline__ double pre_field(const GhostDesc &g, const double *__restrict__ pre, long long sc, int f,
+                                            int dim)
+{
+    const double *p = pre + ((long long)f * sc + g.src) * 3;
+    double v = p[0] + p[1] * g.fx;
+    if (dim == 2) v = v + p[2] * g.fy;
+    return v;
+}
+
+// value of field f of the ghost cell described by g (same-level copy, or the
+// coarse space-time interpolation from the stored stencil values pre_k of
+// its substep), with the boundary sign of the result
+template <bool CG = false>
 __device__ __forceinline__ double ghost_value(const GhostDesc &g, const double *__restrict__ qf, long long sf,
-                                              const double *__restrict__ qo, const double *__restrict__ qn_,
-                                              long long sc, int f, int k, double th, int dim)
+                                              const double *__restrict__ pre_k, long long sc, int f, int dim)
+{
+    double v;
+    if (g.kind == 0) v = ldq<CG>(qf + (long long)f * sf + g.src);
+    else v = pre_field(g, pre_k, sc, f, dim);
+    return sgn(v, g.signs, f, 0);
+}
+
+// the same, interpolating directly from the coarse states
+__device__ __forceinline__ double ghost_value_direct(const GhostDesc &g, const double *__restrict__ qf, long long sf,
+                                                     const double *__restrict__ qo, const double *__restrict__ qn_,
+                                                     long long sc, int f, int k, double th, int dim)
 {
     double v;
     if (g.kind == 0) v = qf[(long long)f * sf + g.src];

@@ -49,10 +49,21 @@ struct Level {
     PatchDesc *d_patches = nullptr;
     WorkItem *d_work = nullptr;
     int nwork = 0, work_tx = 0, work_ty = 0;
-    bool work_lpt = false;
+    bool work_lpt = false, work_deps = false;
+    // substep launches: CSR of the tiles each tile's staged region reads (in
+    // d_work's allocation)
+    const int *d_dep_off = nullptr, *d_dep_idx = nullptr;
     std::vector<WorkItem> h_work;
     GhostDesc *d_ghost = nullptr;
     long long nghost = 0;
+    // coarse stencil values of the kind-1 ghost cells (k_cpre), recomputed
+    // after every step of level l - 1: d_cpre[((k * m + f) * cpre_sc + src) * 3 + j]
+    // for substep k; d_clist lists one ghost cell per distinct coarse cell
+    int *d_cmark = nullptr;
+    size_t cmark_cap = 0;
+    unsigned long long *d_clist = nullptr;
+    double *d_cpre = nullptr;
+    long long cpre_sc = 0;
     AvgDesc *d_avg = nullptr;
     long long navg = 0;
     long long *d_prefix = nullptr;   // interior cells per patch (prefix)
@@ -148,6 +159,14 @@ struct adjamr_ctx {
     int lmode[ADJAMR_MAX_LEVELS] = {};  // ADJAMR_LAUNCH_* per level
     unsigned long long *d_wctr = nullptr;  // tile counter of the dynamic launch mode
     unsigned long long wbase = 0;          // its value at the start of the next dynamic launch
+    // substep launches: grid per level (0: the level's kernel tile has no
+    // substep kernel), per-tile completion counters and their epoch
+    int lgrid_sub[ADJAMR_MAX_LEVELS] = {};
+    unsigned long long *d_done = nullptr;
+    size_t done_cap = 0;
+    unsigned long long done_base = 0;
+    std::vector<int> h_dep_off, h_dep_idx, h_tbox, h_bcnt, h_btile, h_dtmp;
+    int cgen = 0;  // generation of the coarse-stencil marks
     bool timing = false;
     // gauges: cell indices per level (device), records on the device
     int ngauge = 0;
@@ -338,6 +357,10 @@ void free_level(adjamr_ctx *c, Level &L)
     }
     cput(c, L.d_work);
     cput(c, L.d_ghost);
+    cput(c, L.d_cmark);
+    L.cmark_cap = 0;
+    cput(c, L.d_clist);
+    cput(c, L.d_cpre);
     cput(c, L.d_avg);
     cput(c, L.d_owner);
     L.patches.clear();
@@ -354,11 +377,85 @@ void free_level(adjamr_ctx *c, Level &L)
 cudaError_t upload_packed(adjamr_ctx *c, const std::vector<std::pair<const void *, size_t>> &chunks, char **dev,
                           std::vector<size_t> &offs);
 
+// Dependencies of the tiles of a substep launch (CSR into c->h_dep_off /
+// h_dep_idx): tile u is on tile w's list when u's cells meet w's staged region
+// (w's cells and a 2-cell halo).  Halo cells beyond a periodic boundary stand
+// for their images on the other side; beyond the other boundaries the ghost
+// values come from cells that lie in the halo itself.  Tiles are found
+// through 16 x 16-cell buckets of the level's index space.
+void build_deps(adjamr_ctx *c, const Level &L)
+{
+    constexpr int B = 16;
+    const int N = L.N, M = L.M, nbx = (N + B - 1) / B, nby = (M + B - 1) / B;
+    const int nw = (int)L.h_work.size();
+    std::vector<int> &box = c->h_tbox, &cnt = c->h_bcnt, &bt = c->h_btile, &tmp = c->h_dtmp;
+    box.resize((size_t)4 * nw);
+    for (int w = 0; w < nw; w++) {
+        const WorkItem &wi = L.h_work[w];
+        const HPatch &p = L.patches[wi.patch];
+        box[4 * w + 0] = p.ilo + wi.x0;
+        box[4 * w + 1] = p.ilo + wi.x0 + wi.tx - 1;
+        box[4 * w + 2] = p.jlo + wi.y0;
+        box[4 * w + 3] = p.jlo + wi.y0 + wi.ty - 1;
+    }
+    cnt.assign((size_t)nbx * nby + 1, 0);
+    for (int pass = 0; pass < 2; pass++) {
+        for (int w = 0; w < nw; w++)
+            for (int b = box[4 * w + 2] / B; b <= box[4 * w + 3] / B; b++)
+                for (int a = box[4 * w] / B; a <= box[4 * w + 1] / B; a++) {
+                    if (pass == 0) cnt[(size_t)b * nbx + a + 1]++;
+                    else bt[(size_t)cnt[(size_t)b * nbx + a]++] = w;
+                }
+        if (pass == 0) {
+            for (size_t k = 1; k < cnt.size(); k++) cnt[k] += cnt[k - 1];
+            bt.resize((size_t)cnt.back());
+        } else {
+            for (size_t k = cnt.size() - 1; k > 0; k--) cnt[k] = cnt[k - 1];  // back to bucket starts
+            cnt[0] = 0;
+        }
+    }
+    auto query = [&](int i0, int i1, int j0, int j1) {
+        i0 = std::max(i0, 0);
+        j0 = std::max(j0, 0);
+        i1 = std::min(i1, N - 1);
+        j1 = std::min(j1, M - 1);
+        if (i0 > i1 || j0 > j1) return;
+        for (int b = j0 / B; b <= j1 / B; b++)
+            for (int a = i0 / B; a <= i1 / B; a++)
+                for (int k = cnt[(size_t)b * nbx + a]; k < cnt[(size_t)b * nbx + a + 1]; k++) {
+                    const int u = bt[(size_t)k];
+                    if (box[4 * u] <= i1 && box[4 * u + 1] >= i0 && box[4 * u + 2] <= j1 && box[4 * u + 3] >= j0)
+                        tmp.push_back(u);
+                }
+    };
+    const int *bc = c->P.bc;
+    c->h_dep_off.assign((size_t)nw + 1, 0);
+    c->h_dep_idx.clear();
+    for (int w = 0; w < nw; w++) {
+        tmp.clear();
+        const int i0 = box[4 * w] - 2, i1 = box[4 * w + 1] + 2, j0 = box[4 * w + 2] - 2, j1 = box[4 * w + 3] + 2;
+        int sx[3] = {0, 0, 0}, sy[3] = {0, 0, 0}, nsx = 1, nsy = 1;
+        if (i0 < 0 && bc[0] == ADJAMR_BC_PERIODIC) sx[nsx++] = N;
+        if (i1 >= N && bc[1] == ADJAMR_BC_PERIODIC) sx[nsx++] = -N;
+        if (j0 < 0 && bc[2] == ADJAMR_BC_PERIODIC) sy[nsy++] = M;
+        if (j1 >= M && bc[3] == ADJAMR_BC_PERIODIC) sy[nsy++] = -M;
+        for (int a = 0; a < nsx; a++)
+            for (int b = 0; b < nsy; b++) query(i0 + sx[a], i1 + sx[a], j0 + sy[b], j1 + sy[b]);
+        std::sort(tmp.begin(), tmp.end());
+        tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
+        c->h_dep_idx.insert(c->h_dep_idx.end(), tmp.begin(), tmp.end());
+        c->h_dep_off[(size_t)w + 1] = (int)c->h_dep_idx.size();
+    }
+}
+
 adjamr_status build_work(adjamr_ctx *c, int l, int tx, int ty)
 {
     Level &L = c->L[l];
-    const bool lpt = c->lmode[l] != ADJAMR_LAUNCH_PER_PATCH;
-    if (L.work_tx == tx && L.work_ty == ty && L.d_work && L.work_lpt == lpt) return ADJAMR_OK;
+    const bool deps = c->lmode[l] == ADJAMR_LAUNCH_SUBSTEPS && c->P.dim == 2;
+    // substep launches keep the spatial (patch, row) order: a tile's
+    // neighbours are then taken close to it in the previous substep
+    const bool lpt = c->lmode[l] != ADJAMR_LAUNCH_PER_PATCH && !deps;
+    if (L.work_tx == tx && L.work_ty == ty && L.d_work && L.work_lpt == lpt && L.work_deps == deps) return ADJAMR_OK;
     cput(c, L.d_work);
     L.h_work.clear();
     const int tyy = (c->P.dim == 2) ? ty : 1;
@@ -388,11 +485,24 @@ adjamr_status build_work(adjamr_ctx *c, int l, int tx, int ty)
     L.nwork = (int)L.h_work.size();
     std::vector<size_t> offs;
     char *dw = nullptr;
-    CKR(c, upload_packed(c, {{L.h_work.data(), sizeof(WorkItem) * L.h_work.size()}}, &dw, offs));
+    if (deps) {
+        build_deps(c, L);
+        CKR(c, upload_packed(c,
+                             {{L.h_work.data(), sizeof(WorkItem) * L.h_work.size()},
+                              {c->h_dep_off.data(), sizeof(int) * c->h_dep_off.size()},
+                              {c->h_dep_idx.data(), sizeof(int) * c->h_dep_idx.size()}},
+                             &dw, offs));
+        L.d_dep_off = reinterpret_cast<const int *>(dw + offs[1]);
+        L.d_dep_idx = reinterpret_cast<const int *>(dw + offs[2]);
+    } else {
+        CKR(c, upload_packed(c, {{L.h_work.data(), sizeof(WorkItem) * L.h_work.size()}}, &dw, offs));
+        L.d_dep_off = L.d_dep_idx = nullptr;
+    }
     L.d_work = reinterpret_cast<WorkItem *>(dw);
     L.work_tx = tx;
     L.work_ty = ty;
     L.work_lpt = lpt;
+    L.work_deps = deps;
     return ADJAMR_OK;
 }
 
@@ -567,8 +677,47 @@ adjamr_status build_ghost_map(adjamr_ctx *c, int l)
     const int *oc = (l > 0) ? c->L[l - 1].d_owner : nullptr;
     LevelIdx gc = (l > 0) ? idx_of(c, l - 1) : idx_of(c, l);
     int r = (l > 0) ? c->P.ratio[l - 1] : 1;
+    // the coarse stencil list and values (levels > 0): the marks persist with
+    // the level (zeroed when allocated) and are compared with a fresh
+    // generation number, so they need no clearing per build
+    cput(c, L.d_clist);
+    cput(c, L.d_cpre);
+    L.cpre_sc = 0;
+    int gen = 0;
+    if (l > 0) {
+        const Level &C = c->L[l - 1];
+        if (L.cmark_cap < (size_t)C.ncell) {
+            cput(c, L.d_cmark);
+            L.cmark_cap = 0;
+            const size_t want = std::max((size_t)C.ncell, 2 * L.cmark_cap);
+            CKR(c, cget(c, &L.d_cmark, want));
+            CKR(c, cudaMemsetAsync(L.d_cmark, 0, sizeof(int) * want, c->s));
+            L.cmark_cap = want;
+        }
+        CKR(c, cget(c, &L.d_clist, (size_t)L.nghost + 1));
+        CKR(c, cget(c, &L.d_cpre, (size_t)r * c->m * C.ncell * 3));
+        CKR(c, cudaMemsetAsync(L.d_clist, 0, sizeof(unsigned long long), c->s));
+        if (++c->cgen <= 0) c->cgen = 1;  // (2^31 builds)
+        gen = c->cgen;
+        L.cpre_sc = C.ncell;
+    }
     CKR(c, launch_ghost_build(L.d_patches, L.d_gprefix, (int)L.patches.size(), L.nghost, idx_of(c, l), L.d_owner, oc,
-                              gc, r, L.d_ghost, c->d_err, c->s));
+                              gc, r, L.d_ghost, c->d_err, c->s, l > 0 ? L.d_cmark : nullptr, gen,
+                              l > 0 ? L.d_clist : nullptr));
+    c->st.kernel_launches++;
+    return ADJAMR_OK;
+}
+
+// Coarse stencil values of level l's kind-1 ghost cells for all substeps of
+// the step level l - 1 has just taken (its old and new states final until the
+// average-down); the substeps' ghost fills and ghost rings read them.
+adjamr_status coarse_pre(adjamr_ctx *c, int l)
+{
+    Level &L = c->L[l];
+    const Level &C = c->L[l - 1];
+    if (!L.d_cpre || L.nghost == 0) return ADJAMR_OK;
+    CKR(c, launch_cpre(L.d_ghost, L.d_clist, L.nghost, c->m, c->P.ratio[l - 1], c->P.dim, C.q[C.cur],
+                       C.q[1 - C.cur], L.cpre_sc, L.d_cpre, c->nsm * 8, c->s));
     c->st.kernel_launches++;
     return ADJAMR_OK;
 }
@@ -1102,7 +1251,7 @@ adjamr_status flag_tables(adjamr_ctx *c, int l)
     return ADJAMR_OK;
 }
 
-adjamr_status ghost_fill(adjamr_ctx *c, int l, int k, bool early = false);
+adjamr_status ghost_fill(adjamr_ctx *c, int l, int k, bool early = false, bool stored = false);
 
 adjamr_status flag_dense(adjamr_ctx *c, int l, double tol, uint64_t *d_bits, int pitch64, unsigned char *d_patchflags,
                          long long *nflag_out, int *bbox_out)
@@ -1247,8 +1396,10 @@ adjamr_status flag_readback(adjamr_ctx *c, int l, uint64_t *d_bits, int pitch64,
 
 // early: the caller knows that the kernel ahead in the stream writes only
 // interior cells of level l or cells of finer levels, and that level l - 1 is
-// final for this substep (see k_ghost_fill)
-adjamr_status ghost_fill(adjamr_ctx *c, int l, int k, bool early)
+// final for this substep (see k_ghost_fill).  stored: the coarse stencil
+// values of this coarse step are current (coarse_pre ran after the step of
+// level l - 1); otherwise the fill interpolates from the coarse states.
+adjamr_status ghost_fill(adjamr_ctx *c, int l, int k, bool early, bool stored)
 {
     Level &L = c->L[l];
     if (L.nghost == 0) return ADJAMR_OK;
@@ -1262,8 +1413,11 @@ adjamr_status ghost_fill(adjamr_ctx *c, int l, int k, bool early)
         sc = C.ncell;
         r = c->P.ratio[l - 1];
     }
+    const double *pre_k =
+        (stored && l > 0 && L.d_cpre) ? L.d_cpre + (long long)k * c->m * L.cpre_sc * 3 : nullptr;
+    if (pre_k) sc = L.cpre_sc;
     CKR(c, launch_ghost_fill(c->P.dim, c->m, L.d_ghost, L.nghost, L.q[L.cur], L.ncell, qo, qn, sc, k, r, c->s,
-                             early && l > 0 && k > 0));
+                             early && l > 0 && k > 0, pre_k));
     c->st.kernel_launches++;
     return ADJAMR_OK;
 }
@@ -1274,13 +1428,11 @@ adjamr_status ghost_fill(adjamr_ctx *c, int l, int k, bool early)
 GhostArgs fused_ghosts(adjamr_ctx *c, int l, int k)
 {
     Level &L = c->L[l];
-    GhostArgs ga{L.d_ghost, nullptr, nullptr, 0, k, 0.0};
+    GhostArgs ga{L.d_ghost, nullptr, 0, 0, k};
     if (l > 0) {
-        Level &C = c->L[l - 1];
-        ga.qco = C.q[C.cur];
-        ga.qcn = C.q[1 - C.cur];
-        ga.sc = C.ncell;
-        ga.th = (double)k / (double)c->P.ratio[l - 1];  // same division as the oracle's
+        ga.pre = L.d_cpre;
+        ga.sc = L.cpre_sc;
+        ga.pstride = (long long)c->m * L.cpre_sc * 3;
     }
     return ga;
 }
@@ -1295,7 +1447,7 @@ adjamr_status step_patches(adjamr_ctx *c, int l, int k, GhostMode gm, bool early
 {
     Level &L = c->L[l];
     if (L.patches.empty()) return ADJAMR_OK;
-    const GhostArgs ga = (gm == GHOST_FUSED) ? fused_ghosts(c, l, k) : GhostArgs{nullptr, nullptr, nullptr, 0, 0, 0.0};
+    const GhostArgs ga = (gm == GHOST_FUSED) ? fused_ghosts(c, l, k) : GhostArgs{};
     TRY(build_work(c, l, c->ltx[l], c->lty[l]));
     cudaEvent_t tb = nullptr, te = nullptr;
     if (c->timing) {
@@ -1311,7 +1463,7 @@ adjamr_status step_patches(adjamr_ctx *c, int l, int k, GhostMode gm, bool early
         c->tev_used += 2;
         CKR(c, cudaEventRecord(tb, c->s));
     }
-    if (gm == GHOST_FILL) TRY(ghost_fill(c, l, k, early_ghosts));
+    if (gm == GHOST_FILL) TRY(ghost_fill(c, l, k, early_ghosts, true));
     const double *q = L.q[L.cur];
     double *qn = L.q[1 - L.cur];
     const int mode = c->lmode[l];
@@ -1330,8 +1482,10 @@ adjamr_status step_patches(adjamr_ctx *c, int l, int k, GhostMode gm, bool early
     } else {
         int grid = 0;
         TileSched sc{nullptr, 0};
-        if (mode == ADJAMR_LAUNCH_PERSISTENT || mode == ADJAMR_LAUNCH_DYNAMIC) grid = std::min(L.nwork, c->lgrid[l]);
-        if (mode == ADJAMR_LAUNCH_DYNAMIC) {
+        // SUBSTEPS on a level that cannot take substep launches runs as DYNAMIC
+        const bool dyn = mode == ADJAMR_LAUNCH_DYNAMIC || mode == ADJAMR_LAUNCH_SUBSTEPS;
+        if (mode == ADJAMR_LAUNCH_PERSISTENT || dyn) grid = std::min(L.nwork, c->lgrid[l]);
+        if (dyn) {
             sc.ctr = c->d_wctr;
             sc.base = c->wbase;
             c->wbase += (unsigned long long)L.nwork + (unsigned long long)grid;
@@ -1345,6 +1499,83 @@ adjamr_status step_patches(adjamr_ctx *c, int l, int k, GhostMode gm, bool early
     if (c->timing) CKR(c, cudaEventRecord(te, c->s));
     c->st.cell_updates += L.ninterior;
     c->st.level_cell_updates[l] += L.ninterior;
+    return ADJAMR_OK;
+}
+
+// Whether the r substeps of level l within one step of level l - 1 run as one
+// substep launch: the finest level of a 2D hierarchy whose kernel tile has a
+// substep kernel (no regrid and no finer level come between its substeps).
+bool substeps_ok(const adjamr_ctx *c, int l)
+{
+    return l > 0 && l == c->P.nlevels - 1 && c->P.dim == 2 && c->lmode[l] == ADJAMR_LAUNCH_SUBSTEPS &&
+           c->lgrid_sub[l] > 0 && c->P.ratio[l - 1] <= kMaxSubsteps;
+}
+
+// One substep launch of r substeps of level l (work list already built)
+// with the given dependency lists; r * ninterior cell updates.
+adjamr_status launch_substeps(adjamr_ctx *c, int l, int r, const int *dep_off, const int *dep_idx)
+{
+    Level &L = c->L[l];
+    {
+        if (c->done_cap < (size_t)L.nwork + 1) {
+            const size_t want = std::max((size_t)L.nwork + 1, 2 * c->done_cap);
+            if (c->d_done) CKR(c, cudaFreeAsync(c->d_done, c->s));
+            c->d_done = nullptr;
+            c->done_cap = 0;
+            CKR(c, cudaMallocAsync((void **)&c->d_done, want * sizeof(unsigned long long), c->s));
+            CKR(c, cudaMemsetAsync(c->d_done, 0, want * sizeof(unsigned long long), c->s));
+            c->done_cap = want;
+        }
+        GhostArgs ga = fused_ghosts(c, l, 0);
+        SubstepArgs sa{};
+        sa.dep_off = dep_off;
+        sa.dep_idx = dep_idx;
+        sa.done = c->d_done;
+        sa.base = c->done_base;
+        sa.nsub = r;
+        sa.err = c->d_err;
+        c->done_base += (unsigned long long)r;
+        const int nitems = r * L.nwork;
+        const int grid = std::min(nitems, c->lgrid_sub[l]);
+        TileSched sc{c->d_wctr, c->wbase};
+        c->wbase += (unsigned long long)nitems + (unsigned long long)grid;
+        cudaEvent_t tb = nullptr, te = nullptr;
+        if (c->timing) {
+            while (c->tev.size() < c->tev_used + 2) {
+                cudaEvent_t e;
+                CKR(c, cudaEventCreate(&e));
+                c->tev.push_back(e);
+                c->tev_level.push_back(0);
+            }
+            tb = c->tev[c->tev_used];
+            te = c->tev[c->tev_used + 1];
+            c->tev_level[c->tev_used] = l;
+            c->tev_used += 2;
+            CKR(c, cudaEventRecord(tb, c->s));
+        }
+        CKR(c, launch_step_substeps(c->P.eqn, c->lkx[l], c->lky[l], L.q[L.cur], L.q[1 - L.cur], L.aux, L.ncell,
+                                    L.d_patches, L.d_work, L.nwork, grid, c->d_cfl, c->s, ga, sc, sa));
+        if (c->timing) CKR(c, cudaEventRecord(te, c->s));
+        c->st.kernel_launches++;
+        c->st.step_kernel_launches++;
+        c->st.level_step_launches[l]++;
+        c->st.cell_updates += (long long)r * L.ninterior;
+        c->st.level_cell_updates[l] += (long long)r * L.ninterior;
+    }
+    return ADJAMR_OK;
+}
+
+// All r substeps of level l (Sec. 3 subcycling) in one launch of
+// k_step2d_sub: q[cur] -> ... -> the final state, in q[cur] again for even r.
+adjamr_status step_level_substeps(adjamr_ctx *c, int l, int r)
+{
+    Level &L = c->L[l];
+    if (!L.patches.empty()) {
+        TRY(build_work(c, l, c->ltx[l], c->lty[l]));
+        TRY(launch_substeps(c, l, r, L.d_dep_off, L.d_dep_idx));
+    }
+    if (r & 1) L.cur = 1 - L.cur;
+    L.nstep += r;
     return ADJAMR_OK;
 }
 
@@ -1365,6 +1596,10 @@ adjamr_status check_err(adjamr_ctx *c)
     int e = 0;
     CKR(c, cudaMemcpyAsync(&e, c->d_err, sizeof e, cudaMemcpyDeviceToHost, c->s));
     CKR(c, cudaStreamSynchronize(c->s));
+    if (e & kSubstepErrBit) {
+        c->err = "a substep launch gave up waiting for a neighbouring tile";
+        return ADJAMR_ETIMEOUT;
+    }
     if (e) {
         c->err = "hierarchy not properly nested (device check " + std::to_string(e) + ")";
         return ADJAMR_ENEST;
@@ -1404,8 +1639,11 @@ adjamr_status step_level(adjamr_ctx *c, int l)
     TRY(step_patches(c, l, sub, c->lfuse[l] ? GHOST_FUSED : GHOST_FILL, sub > 0 && !regridded));
     if (l < P.nlevels - 1 && !c->L[l + 1].patches.empty()) {
         int r = P.ratio[l];
+        TRY(coarse_pre(c, l + 1));
         c->L[l + 1].nstep = L.nstep * r;
-        for (int s = 0; s < r; s++) TRY(step_level(c, l + 1));
+        if (substeps_ok(c, l + 1)) TRY(step_level_substeps(c, l + 1, r));
+        else
+            for (int s = 0; s < r; s++) TRY(step_level(c, l + 1));
         TRY(average_down(c, l + 1));
     }
     L.cur = 1 - L.cur;
@@ -1487,7 +1725,7 @@ adjamr_status create_impl(const adjamr_params *p, adjamr_ctx **out)
     for (int k = 0; k < 4; k++)
         if (p->bc[k] < 0 || p->bc[k] > 2) return ADJAMR_EINVAL;
     if (p->flag_mode < ADJAMR_FLAG_BRACKET_MAX || p->flag_mode > ADJAMR_FLAG_SURFACE) return ADJAMR_EINVAL;
-    if (p->launch_mode < ADJAMR_LAUNCH_WORKLIST || p->launch_mode > ADJAMR_LAUNCH_DYNAMIC) return ADJAMR_EINVAL;
+    if (p->launch_mode < ADJAMR_LAUNCH_WORKLIST || p->launch_mode > ADJAMR_LAUNCH_SUBSTEPS) return ADJAMR_EINVAL;
     adjamr_ctx *c = new (std::nothrow) adjamr_ctx();
     if (!c) return ADJAMR_ENOMEM;
     c->P = *p;
@@ -1534,6 +1772,7 @@ adjamr_status create_impl(const adjamr_params *p, adjamr_ctx **out)
         c->lkx[l] = kx;
         c->lky[l] = ky;
         c->lgrid[l] = c->grid_persistent;
+        c->lgrid_sub[l] = p->dim == 2 ? nsm * substep_occupancy(p->eqn, kx, ky) : 0;
         c->lfuse[l] = 1;
         c->lmode[l] = p->launch_mode;
     }
@@ -2228,7 +2467,7 @@ adjamr_status adjamr_set_level_kernel(adjamr_ctx *ctx, int level, int tile_x, in
                                       int launch_mode)
 {
     if (!ctx || level < -1 || level >= ctx->P.nlevels) return ADJAMR_EINVAL;
-    if (launch_mode < -1 || launch_mode > ADJAMR_LAUNCH_DYNAMIC) return ADJAMR_EINVAL;
+    if (launch_mode < -1 || launch_mode > ADJAMR_LAUNCH_SUBSTEPS) return ADJAMR_EINVAL;
     int ty = (ctx->P.dim == 2) ? tile_y : 1;
     int kx = 0, ky = 0;
     if (!step_kernel_shape(ctx->P.dim, tile_x, ty, &kx, &ky)) return ADJAMR_EINVAL;
@@ -2241,10 +2480,51 @@ adjamr_status adjamr_set_level_kernel(adjamr_ctx *ctx, int level, int tile_x, in
         ctx->lkx[l] = kx;
         ctx->lky[l] = ky;
         ctx->lgrid[l] = ctx->nsm * std::max(occ, 1);
+        ctx->lgrid_sub[l] = ctx->P.dim == 2 ? ctx->nsm * substep_occupancy(ctx->P.eqn, kx, ky) : 0;
         ctx->lfuse[l] = fuse_ghosts != 0;
         if (launch_mode >= 0) ctx->lmode[l] = launch_mode;
     }
     return ADJAMR_OK;
+}
+
+adjamr_status adjamr_substep_wait_selftest(adjamr_ctx *ctx, double *wait_ms)
+{
+    if (!ctx) return ADJAMR_EINVAL;
+    const int l = ctx->P.nlevels - 1;
+    if (!substeps_ok(ctx, l) || ctx->L[l].patches.empty() || !ctx->have_medium) return ADJAMR_ESTATE;
+    try {
+        Level &L = ctx->L[l];
+        TRY(build_work(ctx, l, ctx->ltx[l], ctx->lty[l]));
+        // every tile waits for counter nwork, which no tile advances
+        std::vector<int> off((size_t)L.nwork + 1), idx((size_t)L.nwork, L.nwork);
+        for (int w = 0; w <= L.nwork; w++) off[(size_t)w] = w;
+        std::vector<size_t> offs;
+        char *d = nullptr;
+        CKR(ctx, upload_packed(ctx, {{off.data(), sizeof(int) * off.size()}, {idx.data(), sizeof(int) * idx.size()}},
+                               &d, offs));
+        const adjamr_stats keep = ctx->st;
+        CKR(ctx, cudaEventRecord(ctx->ev0, ctx->s));
+        adjamr_status st = launch_substeps(ctx, l, 2, reinterpret_cast<const int *>(d + offs[0]),
+                                           reinterpret_cast<const int *>(d + offs[1]));
+        ctx->st = keep;
+        if (st != ADJAMR_OK) return st;
+        CKR(ctx, cudaEventRecord(ctx->ev1, ctx->s));
+        int e = 0;
+        CKR(ctx, cudaMemcpyAsync(&e, ctx->d_err, sizeof e, cudaMemcpyDeviceToHost, ctx->s));
+        CKR(ctx, cudaStreamSynchronize(ctx->s));
+        float ms = 0.f;
+        CKR(ctx, cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+        if (wait_ms) *wait_ms = ms;
+        cput(ctx, d);
+        if (!(e & kSubstepErrBit)) return ADJAMR_OK;
+        const int rest = e & ~kSubstepErrBit;
+        CKR(ctx, cudaMemcpyAsync(ctx->d_err, &rest, sizeof rest, cudaMemcpyHostToDevice, ctx->s));
+        CKR(ctx, cudaStreamSynchronize(ctx->s));
+        ctx->err = "a substep launch gave up waiting for a neighbouring tile (self test)";
+        return ADJAMR_ETIMEOUT;
+    } catch (...) {
+        return ADJAMR_ENOMEM;
+    }
 }
 
 adjamr_status adjamr_get_stats(adjamr_ctx *ctx, adjamr_stats *out)
@@ -2287,6 +2567,7 @@ void adjamr_destroy(adjamr_ctx *ctx)
     cput(ctx, ctx->d_gij);
     dfree(ctx->d_grec, ctx->s);
     dfree(ctx->d_fscratch, ctx->s);
+    dfree(ctx->d_done, ctx->s);
     cache_drain(ctx);
     cudaStreamSynchronize(ctx->s);
     if (ctx->d_cfl) cudaFree(ctx->d_cfl);

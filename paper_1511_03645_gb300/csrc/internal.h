@@ -113,10 +113,11 @@ struct LevelGeom {
 // gd == nullptr: the ghost ring is read from q (filled beforehand).
 struct GhostArgs {
     const GhostDesc *gd;
-    const double *qco, *qcn;
-    long long sc;
-    int k;      // fine substep within the coarse step (0: coarse old state only)
-    double th;  // k / r, divided on the host
+    // coarse stencil values of the level's kind-1 ghost cells (k_cpre) for
+    // substep 0; substep k at pre + k * pstride; sc = the coarse arena stride
+    const double *pre;
+    long long sc, pstride;
+    int k;  // fine substep within the coarse step
 };
 
 // Tile schedule of a step launch.  ctr == nullptr: CTA b takes tiles b,
@@ -136,13 +137,18 @@ struct TileSched {
 constexpr int kMaxSubsteps = 16;
 constexpr unsigned long long kSubstepWaitNs = 1000000000ull;  // a wait gives up after 1 s
 constexpr unsigned int kSubstepWaitSpins = 1u << 24;
+constexpr int kSubstepErrBit = 1 << 30;  // recorded in the context's device error word
 struct SubstepArgs {
     const int *dep_off, *dep_idx;
     unsigned long long *done;
     unsigned long long base;
     int nsub;
-    int *err;                  // set to 1 when a wait gave up
-    double th[kMaxSubsteps];   // ghost-ring time fraction (k0 + s) / r per substep, divided on the host
+    int *err;                  // kSubstepErrBit is or-ed in when a wait gave up
+};
+
+// time fractions k / r of the substeps of a coarse step, divided on the host
+struct SubstepTimes {
+    double th[kMaxSubsteps];
 };
 
 // Programmatic dependent launch of the kernels of the stepping sequence (step,
@@ -170,7 +176,7 @@ cudaError_t launch_pdl(void (*kern)(P...), dim3 grid, dim3 block, size_t smem, c
 // ---- kernel launchers (kernels_step.cu / kernels_amr.cu) ----
 cudaError_t launch_step(int dim, int eqn, int tx, int ty, const double *q, double *qn, const double *aux,
                         long long stride, const PatchDesc *patches, const WorkItem *work, int nwork, int grid,
-                        unsigned long long *cfl_bits, cudaStream_t s, GhostArgs ga = GhostArgs{nullptr, nullptr, nullptr, 0, 0, 0.0},
+                        unsigned long long *cfl_bits, cudaStream_t s, GhostArgs ga = GhostArgs{},
                         TileSched sc = TileSched{nullptr, 0});
 int step_occupancy(int dim, int eqn, int tx, int ty);
 // sa.nsub steps of a 2D level in one launch of `grid` CTAs that take items
@@ -188,10 +194,17 @@ int substep_occupancy(int eqn, int tx, int ty);  // 0: no such kernel
 bool step_kernel_shape(int dim, int tx, int ty, int *kx, int *ky);
 
 // early: the kernel ahead in the stream is a step of this level and the
-// coarser level's states are final (see k_ghost_fill)
+// coarser level's states are final (see k_ghost_fill).  pre_k != nullptr: the
+// kind-1 ghost cells take the precomputed coarse stencil values of substep k
+// (k_cpre) instead of interpolating from qc_old / qc_new.
 cudaError_t launch_ghost_fill(int dim, int m, const GhostDesc *g, long long n, double *qf, long long sf,
                               const double *qc_old, const double *qc_new, long long sc, int k, int r,
-                              cudaStream_t s, bool early = false);
+                              cudaStream_t s, bool early = false, const double *pre_k = nullptr);
+// coarse stencil values (q0, sx, sy) of every listed coarse cell, field and
+// substep s < r: pre[((s * m + f) * sc + src) * 3 + {0, 1, 2}]
+cudaError_t launch_cpre(const GhostDesc *g, const unsigned long long *list, long long nmax, int m, int r, int dim,
+                        const double *qc_old, const double *qc_new, long long sc, double *pre, int grid,
+                        cudaStream_t s);
 cudaError_t launch_average_down(int dim, int m, const AvgDesc *a, long long n, const double *qf, long long sf,
                                 double *qc, long long sc, int r, cudaStream_t s);
 // Fill primary medium (med) and derived coefficients (aux) of the listed
@@ -290,9 +303,13 @@ cudaError_t launch_owner_fill(const PatchDesc *p, const long long *prefix, int n
                               int *owner, cudaStream_t s);
 // ghost descriptors of every patch of a level; gprefix = ghost-cell prefix.
 // owner_c / gc describe the coarser level (owner_c null on level 0).
+// cmark / clist (levels > 0): also lists one kind-1 ghost cell per distinct
+// coarse cell, clist[0] = count (zeroed beforehand), clist[1 + e] = ghost
+// index; a coarse cell is taken when its mark was not yet cgen (> 0)
 cudaError_t launch_ghost_build(const PatchDesc *p, const long long *gprefix, int np, long long nghost, LevelIdx g,
                                const int *owner, const int *owner_c, LevelIdx gc, int r, GhostDesc *out, int *err,
-                               cudaStream_t s);
+                               cudaStream_t s, int *cmark = nullptr, int cgen = 0,
+                               unsigned long long *clist = nullptr);
 // average-down descriptors; aprefix = prefix of coarse-footprint cells per fine patch
 cudaError_t launch_avg_build(const PatchDesc *p, const long long *aprefix, int np, long long navg, int dim, int r,
                              const int *owner_c, LevelIdx gc, AvgDesc *out, int *err, cudaStream_t s);

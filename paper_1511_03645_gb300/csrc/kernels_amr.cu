@@ -11,6 +11,8 @@
 //  - the functional J with a fixed pairwise summation tree.
 // Operation order follows the canonical operations (compiled with
 // --fmad=false), as does the CPU oracle.
+#include <algorithm>
+
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -26,10 +28,19 @@ constexpr int kT = 256;
 // states are final and the kernel ahead in the stream is a step of this level,
 // which writes only interior cells): the coarse interpolations are written
 // before waiting for that step, so they overlap its tail; the same-level copies
-// read its output and come after the wait.
+// read its output and come after the wait.  pre_k != nullptr: coarse
+// interpolations from the stored stencil values of this substep.
+__device__ __forceinline__ double fill_value(const GhostDesc &g, const double *qf, long long sf,
+                                             const double *__restrict__ qo, const double *__restrict__ qn_,
+                                             long long sc, int f, int k, double th, int dim,
+                                             const double *__restrict__ pre_k)
+{
+    return pre_k ? ghost_value(g, qf, sf, pre_k, sc, f, dim) : ghost_value_direct(g, qf, sf, qo, qn_, sc, f, k, th, dim);
+}
+
 __global__ void k_ghost_fill(int dim, int m, const GhostDesc *__restrict__ gd, long long n, double *qf, long long sf,
                              const double *__restrict__ qo, const double *__restrict__ qn_, long long sc, int k,
-                             double th, int early)
+                             double th, int early, const double *__restrict__ pre_k)
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = t < n * m;
@@ -38,14 +49,38 @@ __global__ void k_ghost_fill(int dim, int m, const GhostDesc *__restrict__ gd, l
     bool done = false;
     if (early && valid && gd[gi].kind != 0) {
         const GhostDesc &g = gd[gi];
-        qf[(long long)f * sf + g.dst] = ghost_value(g, qf, sf, qo, qn_, sc, f, k, th, dim);
+        qf[(long long)f * sf + g.dst] = fill_value(g, qf, sf, qo, qn_, sc, f, k, th, dim, pre_k);
         done = true;
     }
     pdl_wait();
     pdl_launch_dependents();
     if (!valid || done) return;
     const GhostDesc &g = gd[gi];
-    qf[(long long)f * sf + g.dst] = ghost_value(g, qf, sf, qo, qn_, sc, f, k, th, dim);
+    qf[(long long)f * sf + g.dst] = fill_value(g, qf, sf, qo, qn_, sc, f, k, th, dim, pre_k);
+}
+
+// Coarse stencil values of the listed coarse cells for every substep s < r of
+// the coarse step (time fraction th[s]) and field: computed once per coarse
+// cell instead of once per fine ghost cell.
+__global__ void k_cpre(const GhostDesc *__restrict__ gd, const unsigned long long *__restrict__ list, int m, int r,
+                       int dim, const double *__restrict__ qo, const double *__restrict__ qn_, long long sc,
+                       double *pre, SubstepTimes tt)
+{
+    pdl_wait();
+    pdl_launch_dependents();
+    const long long per = (long long)r * m;
+    const long long n = (long long)list[0] * per;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const long long e = t / per;
+        const int rest = (int)(t - e * per), s = rest / m, f = rest - s * m;
+        const GhostDesc g = gd[list[1 + e]];
+        double v[3];
+        coarse_stencil(g, qo, qn_, sc, f, s, tt.th[s], dim, v);
+        double *p = pre + (((long long)s * m + f) * sc + g.src) * 3;
+        p[0] = v[0];
+        p[1] = v[1];
+        p[2] = v[2];
+    }
 }
 
 __global__ void k_average_down(int dim, int m, const AvgDesc *__restrict__ ad, long long n,
@@ -255,7 +290,8 @@ __global__ void k_owner_fill(const PatchDesc *__restrict__ pd, const long long *
 
 __global__ void k_ghost_build(const PatchDesc *__restrict__ pd, const long long *__restrict__ gprefix, int np,
                               long long nghost, LevelIdx g, const int *__restrict__ owner,
-                              const int *__restrict__ owner_c, LevelIdx gc, int r, GhostDesc *out, int *err)
+                              const int *__restrict__ owner_c, LevelIdx gc, int r, GhostDesc *out, int *err,
+                              int *cmark, int cgen, unsigned long long *clist)
 {
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nghost) return;
@@ -297,6 +333,9 @@ __global__ void k_ghost_build(const PatchDesc *__restrict__ pd, const long long 
     }
     d.signs |= f1 | (f2 << 1);
     out[t] = d;
+    // list the coarse cell once (which of its ghost cells is listed is immaterial)
+    if (d.kind != 0 && cmark && atomicExch(&cmark[d.src], cgen) != cgen)
+        clist[1 + atomicAdd(&clist[0], 1ull)] = (unsigned long long)t;
 }
 
 __global__ void k_avg_build(const PatchDesc *__restrict__ pd, const long long *__restrict__ aprefix, int np,
@@ -842,12 +881,25 @@ inline unsigned nblk_of(long long n) { return nblk(n); }
 
 cudaError_t launch_ghost_fill(int dim, int m, const GhostDesc *g, long long n, double *qf, long long sf,
                               const double *qc_old, const double *qc_new, long long sc, int k, int r, cudaStream_t s,
-                              bool early)
+                              bool early, const double *pre_k)
 {
     if (n <= 0) return cudaSuccess;
     const double th = (double)k / (double)r;  // same division as the oracle's, on the host
     return launch_pdl(k_ghost_fill, dim3(nblk(n * m)), dim3(kT), 0, s, dim, m, g, n, qf, sf, qc_old, qc_new, sc, k, th,
-                      early && pdl_enabled() ? 1 : 0);
+                      early && pdl_enabled() ? 1 : 0, pre_k);
+}
+
+cudaError_t launch_cpre(const GhostDesc *g, const unsigned long long *list, long long nmax, int m, int r, int dim,
+                        const double *qc_old, const double *qc_new, long long sc, double *pre, int grid,
+                        cudaStream_t s)
+{
+    if (nmax <= 0) return cudaSuccess;
+    if (r < 1 || r > kMaxSubsteps) return cudaErrorInvalidValue;
+    SubstepTimes tt{};
+    for (int k = 0; k < r; k++) tt.th[k] = (double)k / (double)r;  // same division as the oracle's, on the host
+    const long long need = nblk(nmax * r * m);
+    const int g_ = (int)std::max(1ll, std::min(need, (long long)grid));
+    return launch_pdl(k_cpre, dim3(g_), dim3(kT), 0, s, g, list, m, r, dim, qc_old, qc_new, sc, pre, tt);
 }
 
 cudaError_t launch_average_down(int dim, int m, const AvgDesc *a, long long n, const double *qf, long long sf,
@@ -875,10 +927,12 @@ cudaError_t launch_owner_fill(const PatchDesc *p, const long long *prefix, int n
 
 cudaError_t launch_ghost_build(const PatchDesc *p, const long long *gprefix, int np, long long nghost, LevelIdx g,
                                const int *owner, const int *owner_c, LevelIdx gc, int r, GhostDesc *out, int *err,
-                               cudaStream_t s)
+                               cudaStream_t s, int *cmark, int cgen, unsigned long long *clist)
 {
     if (nghost <= 0) return cudaSuccess;
-    k_ghost_build<<<nblk(nghost), kT, 0, s>>>(p, gprefix, np, nghost, g, owner, owner_c, gc, r, out, err);
+    if (cmark && (cgen <= 0 || !clist)) return cudaErrorInvalidValue;
+    k_ghost_build<<<nblk(nghost), kT, 0, s>>>(p, gprefix, np, nghost, g, owner, owner_c, gc, r, out, err, cmark, cgen,
+                                              clist);
     return cudaGetLastError();
 }
 

@@ -278,17 +278,15 @@ struct Smem2D {
     static constexpr size_t bytes = sizeof(double) * (size_t)total;
 };
 
-template <int EQN, int TX, int TY>
-__global__ void __launch_bounds__(kThreads) k_step2d(const double *__restrict__ q, double *__restrict__ qn,
-                                                     const double *__restrict__ aux, long long stride,
-                                                     const PatchDesc *__restrict__ patches,
-                                                     const WorkItem *__restrict__ work, int nwork,
-                                                     unsigned long long *cfl_bits, GhostArgs ga, TileSched sc)
+// One tile of one step: stage, Riemann problems, limiter, transverse
+// corrections, update of the tile's cells in qn.  CG: the state is read
+// through L2 only (it was written by other CTAs of the same launch).
+template <int EQN, int TX, int TY, bool CG>
+__device__ __forceinline__ void step2d_tile(const double *__restrict__ q, double *__restrict__ qn,
+                                            const double *__restrict__ aux, long long stride, const PatchDesc P,
+                                            const WorkItem wi, const GhostArgs &ga, double *sm, long long &cfl)
 {
     using S = Smem2D<EQN, TX, TY>;
-    pdl_wait();
-    pdl_launch_dependents();
-    extern __shared__ double sm[];
     double *sQ = sm;
     double *sA = sQ + S::nQ;
     double *XW = sA + S::nA;   // waves w1_0, w1_n, w2_0, w2_n at x-edges; later SX + FF
@@ -310,11 +308,7 @@ __global__ void __launch_bounds__(kThreads) k_step2d(const double *__restrict__ 
     constexpr int SXS = (TY + 2) * TX, FFS = TY * (TX + 1), SYS = TY * (TX + 2), GGS = (TY + 1) * TX;
 
     const int tid = threadIdx.x;
-    long long cfl = 0;
-    __shared__ int s_next;
-    for (int w = fetch_tile(sc, &s_next, blockIdx.x); w < nwork; w = fetch_tile(sc, &s_next, w + gridDim.x)) {
-        const WorkItem wi = work[w];
-        const PatchDesc P = patches[wi.patch];
+    {
         const int x0 = wi.x0, y0 = wi.y0;
         const int tx = wi.tx, ty = wi.ty;
         const int rx = tx + 4, ry = ty + 4;
@@ -337,7 +331,7 @@ __global__ void __launch_bounds__(kThreads) k_step2d(const double *__restrict__ 
                 if (f < 3) {
                     const int si = x0 + c, sj = y0 + r;
                     if (!(ring && (si < 2 || si >= P.nx + 2 || sj < 2 || sj >= P.ny + 2)))
-                        sQ[f * PS + r * PX + c] = q[(long long)f * stride + g];
+                        sQ[f * PS + r * PX + c] = ldq<CG>(q + (long long)f * stride + g);
                 } else {
                     sA[(f - 3) * PS + r * PX + c] = aux[(long long)(f - 3) * stride + g];
                 }
@@ -350,7 +344,8 @@ __global__ void __launch_bounds__(kThreads) k_step2d(const double *__restrict__ 
                     const GhostDesc gdsc = ga.gd[P.gbase + ghost_local_index(P, si, sj, 2)];
                     double v[3];
 #pragma unroll
-                    for (int f = 0; f < 3; f++) v[f] = ghost_value(gdsc, q, stride, ga.qco, ga.qcn, ga.sc, f, ga.k, ga.th, 2);
+                    for (int f = 0; f < 3; f++)
+                        v[f] = ghost_value<CG>(gdsc, q, stride, ga.pre + ga.k * ga.pstride, ga.sc, f, 2);
 #pragma unroll
                     for (int f = 0; f < 3; f++) sQ[f * PS + r * PX + c] = v[f];
                 }
@@ -508,6 +503,128 @@ __global__ void __launch_bounds__(kThreads) k_step2d(const double *__restrict__ 
         }
         __syncthreads();
     }
+}
+
+template <int EQN, int TX, int TY>
+__global__ void __launch_bounds__(kThreads) k_step2d(const double *__restrict__ q, double *__restrict__ qn,
+                                                     const double *__restrict__ aux, long long stride,
+                                                     const PatchDesc *__restrict__ patches,
+                                                     const WorkItem *__restrict__ work, int nwork,
+                                                     unsigned long long *cfl_bits, GhostArgs ga, TileSched sc)
+{
+    pdl_wait();
+    pdl_launch_dependents();
+    extern __shared__ double sm[];
+    long long cfl = 0;
+    __shared__ int s_next;
+    for (int w = fetch_tile(sc, &s_next, blockIdx.x); w < nwork; w = fetch_tile(sc, &s_next, w + gridDim.x)) {
+        const WorkItem wi = work[w];
+        step2d_tile<EQN, TX, TY, false>(q, qn, aux, stride, patches[wi.patch], wi, ga, sm, cfl);
+    }
+    cfl_reduce(cfl, cfl_bits);
+}
+
+// ---------------------------------------------------------------- substeps
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Warp 0 waits until every tile on w's dependency list has completed `target`
+// substeps.  Each wait is bounded (time and spins); it gives up early when
+// another CTA has already reported a failure.  Uniform over the CTA.
+__device__ __forceinline__ bool wait_deps(const SubstepArgs &sa, int w, unsigned long long target, int *s_ok)
+{
+    if (threadIdx.x < 32) {
+        bool ok = true;
+        const int e = sa.dep_off[w + 1];
+        unsigned long long t0 = 0;
+        unsigned int spins = 0;
+        for (int j = sa.dep_off[w] + (int)threadIdx.x; ok && j < e; j += 32) {
+            const unsigned long long *f = sa.done + sa.dep_idx[j];
+            while (ld_acquire(f) < target) {
+                if (spins == 0) t0 = global_ns();
+                if ((++spins & 255u) == 0 &&
+                    (global_ns() - t0 > kSubstepWaitNs || spins > kSubstepWaitSpins ||
+                     (*(volatile const int *)sa.err & kSubstepErrBit) != 0)) {
+                    ok = false;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        ok = __all_sync(0xffffffffu, ok);
+        if (threadIdx.x == 0) {
+            if (!ok) atomicOr(sa.err, kSubstepErrBit);
+            *s_ok = ok ? 1 : 0;
+        }
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+// nsub consecutive steps of one level in one launch (the substeps of the
+// finest level within a coarser step, Sec. 3 time stepping with
+// subcycling).  Work item i is tile w = i mod nwork of substep s = i / nwork;
+// CTAs take items in increasing order from the atomic counter, and item
+// (s, w) first waits until the tiles whose cells its staged region reads
+// (2-cell halo and ghost-ring sources) have completed substep s - 1.  Every
+// such tile has a smaller item index, so the smallest unfinished item can
+// always proceed.  Substep s reads buffer (s & 1 ? qb : qa) and writes the
+// other; its ghost ring takes the stored coarse stencil values of substep s.
+template <int EQN, int TX, int TY>
+__global__ void __launch_bounds__(kThreads) k_step2d_sub(double *qa, double *qb, const double *__restrict__ aux,
+                                                         long long stride, const PatchDesc *__restrict__ patches,
+                                                         const WorkItem *__restrict__ work, int nwork,
+                                                         unsigned long long *cfl_bits, GhostArgs ga, TileSched sc,
+                                                         SubstepArgs sa)
+{
+    pdl_wait();
+    pdl_launch_dependents();
+    extern __shared__ double sm[];
+    long long cfl = 0;
+    __shared__ int s_next, s_ok;
+    const int nitems = sa.nsub * nwork;
+    // After a failed wait the CTA keeps taking items without working on them,
+    // so that the counter advances by exactly nitems + gridDim.x.
+    bool failed = false;
+    for (int i = fetch_tile(sc, &s_next, 0); i < nitems; i = fetch_tile(sc, &s_next, 0)) {
+        if (failed || i < 0) {
+            if (!failed && threadIdx.x == 0) atomicOr(sa.err, kSubstepErrBit);
+            failed = true;
+            __syncthreads();  // every thread has read s_next before it is written again
+            continue;
+        }
+        const int s = i / nwork, w = i - s * nwork;
+        if (s > 0 && !wait_deps(sa, w, sa.base + (unsigned long long)s, &s_ok)) {
+            failed = true;
+            continue;
+        }
+        GhostArgs g = ga;
+        g.k = ga.k + s;
+        const WorkItem wi = work[w];
+        step2d_tile<EQN, TX, TY, true>((s & 1) ? qb : qa, (s & 1) ? qa : qb, aux, stride, patches[wi.patch], wi, g,
+                                       sm, cfl);
+        // the tile's stores precede the barrier that ends step2d_tile
+        if (threadIdx.x == 0) {
+            __threadfence();
+            st_release(sa.done + w, sa.base + (unsigned long long)s + 1);
+        }
+    }
     cfl_reduce(cfl, cfl_bits);
 }
 
@@ -561,8 +678,8 @@ __global__ void __launch_bounds__(kThreads) k_step1d(const double *__restrict__ 
             const int si = x0 + c;
             if (si < 2 || si >= P.nx + 2) {
                 const GhostDesc gdsc = ga.gd[P.gbase + ghost_local_index(P, si, 0, 0)];
-                double v0 = ghost_value(gdsc, q, stride, ga.qco, ga.qcn, ga.sc, 0, ga.k, ga.th, 1);
-                double v1 = ghost_value(gdsc, q, stride, ga.qco, ga.qcn, ga.sc, 1, ga.k, ga.th, 1);
+                double v0 = ghost_value(gdsc, q, stride, ga.pre + ga.k * ga.pstride, ga.sc, 0, 1);
+                double v1 = ghost_value(gdsc, q, stride, ga.pre + ga.k * ga.pstride, ga.sc, 1, 1);
                 sQ[c] = v0;
                 sQ[PX + c] = v1;
             }
@@ -688,7 +805,64 @@ int occ2d(int tx, int ty)
     return n;
 }
 
+template <int EQN>
+cudaError_t dispatch_sub(int tx, int ty, int nwork, int grid, double *qa, double *qb, const double *aux,
+                         long long stride, const PatchDesc *p, const WorkItem *w, unsigned long long *c, cudaStream_t s,
+                         const GhostArgs &ga, const TileSched &sc, const SubstepArgs &sa, int *occ)
+{
+#define ADJ_SUB(X, Y)                                                                                          \
+    if (tx == X && ty == Y) {                                                                                  \
+        constexpr size_t smem = Smem2D<EQN, X, Y>::bytes;                                                      \
+        cudaError_t e = ensure_smem_attr<k_step2d_sub<EQN, X, Y>>(smem);                                      \
+        if (e != cudaSuccess) return e;                                                                        \
+        if (occ) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_step2d_sub<EQN, X, Y>, kThreads, \
+                                                                      smem);                                   \
+        return launch_pdl(k_step2d_sub<EQN, X, Y>, dim3(grid), dim3(kThreads), smem, s, qa, qb, aux, stride, p, \
+                          w, nwork, c, ga, sc, sa);                                                            \
+    }
+    ADJ_SUB(16, 16)
+    ADJ_SUB(16, 8)
+    ADJ_SUB(8, 8)
+#undef ADJ_SUB
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t sub_switch(int eqn, int tx, int ty, int nwork, int grid, double *qa, double *qb, const double *aux,
+                       long long stride, const PatchDesc *p, const WorkItem *w, unsigned long long *c, cudaStream_t s,
+                       const GhostArgs &ga, const TileSched &sc, const SubstepArgs &sa, int *occ)
+{
+    switch (eqn) {
+    case 0: return dispatch_sub<0>(tx, ty, nwork, grid, qa, qb, aux, stride, p, w, c, s, ga, sc, sa, occ);
+    case 1: return dispatch_sub<1>(tx, ty, nwork, grid, qa, qb, aux, stride, p, w, c, s, ga, sc, sa, occ);
+    case 2: return dispatch_sub<2>(tx, ty, nwork, grid, qa, qb, aux, stride, p, w, c, s, ga, sc, sa, occ);
+    case 3: return dispatch_sub<3>(tx, ty, nwork, grid, qa, qb, aux, stride, p, w, c, s, ga, sc, sa, occ);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_step_substeps(int eqn, int tx, int ty, double *qa, double *qb, const double *aux, long long stride,
+                                 const PatchDesc *patches, const WorkItem *work, int nwork, int grid,
+                                 unsigned long long *cfl_bits, cudaStream_t s, const GhostArgs &ga,
+                                 const TileSched &sc, const SubstepArgs &sa)
+{
+    if (!sc.ctr || !ga.gd || sa.nsub < 1 || sa.nsub > kMaxSubsteps || grid < 1) return cudaErrorInvalidValue;
+    if (nwork <= 0) return cudaSuccess;
+    return sub_switch(eqn, tx, ty, nwork, grid, qa, qb, aux, stride, patches, work, cfl_bits, s, ga, sc, sa, nullptr);
+}
+
+int substep_occupancy(int eqn, int tx, int ty)
+{
+    int n = 0;
+    const GhostArgs ga{};
+    const TileSched sc{};
+    const SubstepArgs sa{};
+    if (sub_switch(eqn, tx, ty, 0, 0, nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, ga, sc, sa,
+                   &n) != cudaSuccess)
+        return 0;
+    return n;
+}
 
 cudaError_t launch_step(int dim, int eqn, int tx, int ty, const double *q, double *qn, const double *aux,
                         long long stride, const PatchDesc *patches, const WorkItem *work, int nwork, int grid,

@@ -160,11 +160,15 @@ def _compare_all(o, g, nlev):
 
 
 @pytest.mark.parametrize("which", ["c1", "c2", "c2_linear", "c2_walls", "c3", "c1_diff", "c2_diff", "c3_surface",
-                                   "p521", "p522", "p523", "p523_diff"])
+                                   "p521", "p522", "p523", "p523_diff", "c2_sub", "c2_walls_sub",
+                                   "c3_sub", "p523_sub"])
 def test_amr_run_matches_oracle(A, which):
     """Adjoint-guided AMR runs (reduced sizes of the workloads): layouts of
     every level bit-exact after every regrid, states within 1e-12, flags
-    bit-exact, J within 1e-12."""
+    bit-exact, J within 1e-12.  The _sub variants run the finest level's
+    substeps as single substep launches."""
+    sub = which.endswith("_sub")
+    which = which[:-4] if sub else which
     if which.startswith("p52"):
         # the paper's Sec. 5.2 examples at their own sizes
         wl = W.paper_5_2({"p521": "timepoint_walls", "p522": "range_walls"}.get(which[:4], "range_mixed"))
@@ -193,6 +197,8 @@ def test_amr_run_matches_oracle(A, which):
         chunks = 4
     snaps = O.adjoint_solve(wl, medium_dense=None if wl.medium.kind != "dense" else _adj_medium(wl))
     o, g = _amr_pair(A, wl, snaps=snaps)
+    if sub:
+        g.set_level_kernel(-1, (16, 12), True, A.LAUNCH_SUBSTEPS)
     _compare_all(o, g, wl.nlevels)
     n = o.nsteps_total()
     assert g.nsteps_total() == n
@@ -208,6 +214,12 @@ def test_amr_run_matches_oracle(A, which):
             fg, cg = g.flag(lev, wl.tol)
             assert co == cg and np.array_equal(fo, fg)
     assert refined > 0, "the case never refined"
+    if sub:
+        st = g.stats()
+        fine = wl.nlevels - 1
+        assert st["level_cell_updates"][fine] > 0
+        # one launch per coarser step (r substeps each would exceed it)
+        assert st["level_step_launches"][fine] <= st["level_step_launches"][fine - 1]
     Jo, Jg = o.functional(), g.functional()
     assert abs(Jg - Jo) <= RTOL * max(abs(Jo), 1e-300)
 
@@ -223,7 +235,11 @@ def test_per_level_kernels_compute_the_same_bits(A):
     runs = []
     for cfg in (None, [((8, 8), False, 3), ((16, 16), True, 0), ((64, 8), False, 3)],
                 [((32, 16), True, 3), ((16, 8), False, 1), ((8, 8), True, 3)],
-                [((12, 8), True, 0), ((24, 12), False, 0), ((12, 8), False, 0)]):
+                [((12, 8), True, 0), ((24, 12), False, 0), ((12, 8), False, 0)],
+                # substep launches on the finest level; on the others mode 4 acts as mode 3
+                [((12, 8), True, 4), ((8, 8), False, 4), ((16, 12), False, 4)],
+                [((16, 8), False, 0), ((12, 8), True, 0), ((5, 3), True, 4)],
+                [((32, 8), True, 0), ((16, 16), True, 1), ((16, 8), True, 4)]):
         h = A.Hierarchy(wl)
         h.set_adjoint(adj)
         h.set_timing(True)
@@ -252,8 +268,31 @@ def test_per_level_kernels_compute_the_same_bits(A):
     with pytest.raises(A.AdjamrError):
         h.set_level_kernel(wl.nlevels, (32, 8))
     with pytest.raises(A.AdjamrError):
-        h.set_level_kernel(0, (32, 8), True, 4)
+        h.set_level_kernel(0, (32, 8), True, 5)
     h.close()
+
+
+def test_substep_waits_give_up_and_the_context_stays_usable(A):
+    """A substep launch whose tiles wait on a counter nothing advances: the
+    bounded waits give up after about a second, the call reports ETIMEOUT,
+    and the run then goes on to the oracle's results."""
+    wl = W.config2(seed=3, n0=32, ratios=(2, 4), tf=2.0, adj_n=64, nsnap=20, ts=0.0, tol=1e-4,
+                   min_patch=8, max_patch=32)
+    o, g = _amr_pair(A, wl)
+    g.set_level_kernel(-1, (16, 12), True, A.LAUNCH_SUBSTEPS)
+    n = o.nsteps_total()
+    k = n // 2
+    o.advance(k)
+    g.advance(k)
+    assert len(g.patches(wl.nlevels - 1)) > 0
+    rc, ms = g.substep_wait_selftest()
+    assert rc == A.ETIMEOUT
+    assert 500.0 <= ms <= 10000.0
+    _compare_all(o, g, wl.nlevels)
+    o.advance(n - k)
+    g.advance(n - k)
+    _compare_all(o, g, wl.nlevels)
+    assert abs(g.functional() - o.functional()) <= RTOL * max(abs(o.functional()), 1e-300)
 
 
 def test_gauges_match_oracle_bitwise(A):
