@@ -42,13 +42,12 @@ UNIT = "cell-updates/s"
 # one such operation per instruction, so the roofline peak is the pipe's
 # instruction rate (the DFMA micro-benchmark's flop rate / 2).
 OPS_PER_CELL_2D = 170
-# DRAM bytes per cell-update of a finest-level step launch, from the ncu
-# capture summarised in profiles/k_step2d_amr_level2_config2.md (3.98 MB read,
-# 0 written, in a launch of the --case solve --tf 1 run, whose level-2
-# launches average 40,920 cells): 1.2x the 80 algorithmic bytes per
-# cell-update (tile halos and descriptors); written lines stay in L2 within
-# the launch.
-TRAFFIC_PER_CELL_L2 = 3.975936e6 / 40920.0
+# DRAM bytes per cell-update of a finest-level step launch, from an ncu
+# capture of one such launch (the 601st finest-level launch of the config-2
+# solve to t = 2: 53,424 cells, 3.67 MB read, 0 written): 69 B, 1.2x the 56
+# algorithmic bytes read (tile halos and descriptors); written lines stay in
+# L2 within the launch.
+TRAFFIC_PER_CELL_L2 = 3.665152e6 / 53424.0
 
 
 def log(*a):

@@ -50,9 +50,9 @@ struct Level {
     WorkItem *d_work = nullptr;
     int nwork = 0, work_tx = 0, work_ty = 0;
     bool work_lpt = false, work_deps = false;
-    // substep launches: CSR of the tiles each tile's staged region reads (in
-    // d_work's allocation)
-    const int *d_dep_off = nullptr, *d_dep_idx = nullptr;
+    // substep launches: dependency rows of the work list ([nwork][kDepRow]
+    // tile indices, then nwork counts) and the tile of every arena cell
+    int *d_dep = nullptr, *d_tile_of = nullptr;
     std::vector<WorkItem> h_work;
     GhostDesc *d_ghost = nullptr;
     long long nghost = 0;
@@ -165,7 +165,6 @@ struct adjamr_ctx {
     unsigned long long *d_done = nullptr;
     size_t done_cap = 0;
     unsigned long long done_base = 0;
-    std::vector<int> h_dep_off, h_dep_idx, h_tbox, h_bcnt, h_btile, h_dtmp;
     int cgen = 0;  // generation of the coarse-stencil marks
     bool timing = false;
     // gauges: cell indices per level (device), records on the device
@@ -356,6 +355,8 @@ void free_level(adjamr_ctx *c, Level &L)
         dfree(L.d_aprefix, s);
     }
     cput(c, L.d_work);
+    cput(c, L.d_dep);
+    cput(c, L.d_tile_of);
     cput(c, L.d_ghost);
     cput(c, L.d_cmark);
     L.cmark_cap = 0;
@@ -376,77 +377,6 @@ void free_level(adjamr_ctx *c, Level &L)
 
 cudaError_t upload_packed(adjamr_ctx *c, const std::vector<std::pair<const void *, size_t>> &chunks, char **dev,
                           std::vector<size_t> &offs);
-
-// Dependencies of the tiles of a substep launch (CSR into c->h_dep_off /
-// h_dep_idx): tile u is on tile w's list when u's cells meet w's staged region
-// (w's cells and a 2-cell halo).  Halo cells beyond a periodic boundary stand
-// for their images on the other side; beyond the other boundaries the ghost
-// values come from cells that lie in the halo itself.  Tiles are found
-// through 16 x 16-cell buckets of the level's index space.
-void build_deps(adjamr_ctx *c, const Level &L)
-{
-    constexpr int B = 16;
-    const int N = L.N, M = L.M, nbx = (N + B - 1) / B, nby = (M + B - 1) / B;
-    const int nw = (int)L.h_work.size();
-    std::vector<int> &box = c->h_tbox, &cnt = c->h_bcnt, &bt = c->h_btile, &tmp = c->h_dtmp;
-    box.resize((size_t)4 * nw);
-    for (int w = 0; w < nw; w++) {
-        const WorkItem &wi = L.h_work[w];
-        const HPatch &p = L.patches[wi.patch];
-        box[4 * w + 0] = p.ilo + wi.x0;
-        box[4 * w + 1] = p.ilo + wi.x0 + wi.tx - 1;
-        box[4 * w + 2] = p.jlo + wi.y0;
-        box[4 * w + 3] = p.jlo + wi.y0 + wi.ty - 1;
-    }
-    cnt.assign((size_t)nbx * nby + 1, 0);
-    for (int pass = 0; pass < 2; pass++) {
-        for (int w = 0; w < nw; w++)
-            for (int b = box[4 * w + 2] / B; b <= box[4 * w + 3] / B; b++)
-                for (int a = box[4 * w] / B; a <= box[4 * w + 1] / B; a++) {
-                    if (pass == 0) cnt[(size_t)b * nbx + a + 1]++;
-                    else bt[(size_t)cnt[(size_t)b * nbx + a]++] = w;
-                }
-        if (pass == 0) {
-            for (size_t k = 1; k < cnt.size(); k++) cnt[k] += cnt[k - 1];
-            bt.resize((size_t)cnt.back());
-        } else {
-            for (size_t k = cnt.size() - 1; k > 0; k--) cnt[k] = cnt[k - 1];  // back to bucket starts
-            cnt[0] = 0;
-        }
-    }
-    auto query = [&](int i0, int i1, int j0, int j1) {
-        i0 = std::max(i0, 0);
-        j0 = std::max(j0, 0);
-        i1 = std::min(i1, N - 1);
-        j1 = std::min(j1, M - 1);
-        if (i0 > i1 || j0 > j1) return;
-        for (int b = j0 / B; b <= j1 / B; b++)
-            for (int a = i0 / B; a <= i1 / B; a++)
-                for (int k = cnt[(size_t)b * nbx + a]; k < cnt[(size_t)b * nbx + a + 1]; k++) {
-                    const int u = bt[(size_t)k];
-                    if (box[4 * u] <= i1 && box[4 * u + 1] >= i0 && box[4 * u + 2] <= j1 && box[4 * u + 3] >= j0)
-                        tmp.push_back(u);
-                }
-    };
-    const int *bc = c->P.bc;
-    c->h_dep_off.assign((size_t)nw + 1, 0);
-    c->h_dep_idx.clear();
-    for (int w = 0; w < nw; w++) {
-        tmp.clear();
-        const int i0 = box[4 * w] - 2, i1 = box[4 * w + 1] + 2, j0 = box[4 * w + 2] - 2, j1 = box[4 * w + 3] + 2;
-        int sx[3] = {0, 0, 0}, sy[3] = {0, 0, 0}, nsx = 1, nsy = 1;
-        if (i0 < 0 && bc[0] == ADJAMR_BC_PERIODIC) sx[nsx++] = N;
-        if (i1 >= N && bc[1] == ADJAMR_BC_PERIODIC) sx[nsx++] = -N;
-        if (j0 < 0 && bc[2] == ADJAMR_BC_PERIODIC) sy[nsy++] = M;
-        if (j1 >= M && bc[3] == ADJAMR_BC_PERIODIC) sy[nsy++] = -M;
-        for (int a = 0; a < nsx; a++)
-            for (int b = 0; b < nsy; b++) query(i0 + sx[a], i1 + sx[a], j0 + sy[b], j1 + sy[b]);
-        std::sort(tmp.begin(), tmp.end());
-        tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
-        c->h_dep_idx.insert(c->h_dep_idx.end(), tmp.begin(), tmp.end());
-        c->h_dep_off[(size_t)w + 1] = (int)c->h_dep_idx.size();
-    }
-}
 
 adjamr_status build_work(adjamr_ctx *c, int l, int tx, int ty)
 {
@@ -485,20 +415,18 @@ adjamr_status build_work(adjamr_ctx *c, int l, int tx, int ty)
     L.nwork = (int)L.h_work.size();
     std::vector<size_t> offs;
     char *dw = nullptr;
-    if (deps) {
-        build_deps(c, L);
-        CKR(c, upload_packed(c,
-                             {{L.h_work.data(), sizeof(WorkItem) * L.h_work.size()},
-                              {c->h_dep_off.data(), sizeof(int) * c->h_dep_off.size()},
-                              {c->h_dep_idx.data(), sizeof(int) * c->h_dep_idx.size()}},
-                             &dw, offs));
-        L.d_dep_off = reinterpret_cast<const int *>(dw + offs[1]);
-        L.d_dep_idx = reinterpret_cast<const int *>(dw + offs[2]);
-    } else {
-        CKR(c, upload_packed(c, {{L.h_work.data(), sizeof(WorkItem) * L.h_work.size()}}, &dw, offs));
-        L.d_dep_off = L.d_dep_idx = nullptr;
-    }
+    CKR(c, upload_packed(c, {{L.h_work.data(), sizeof(WorkItem) * L.h_work.size()}}, &dw, offs));
     L.d_work = reinterpret_cast<WorkItem *>(dw);
+    cput(c, L.d_dep);
+    cput(c, L.d_tile_of);
+    if (deps && L.nwork > 0) {
+        // dependency rows built on the device from the level's owner map
+        CKR(c, cget(c, &L.d_dep, (size_t)L.nwork * (kDepRow + 1)));
+        CKR(c, cget(c, &L.d_tile_of, (size_t)L.ncell));
+        CKR(c, launch_tile_deps(L.d_patches, L.d_work, L.nwork, L.d_owner, L.N, L.M, c->P.bc, L.d_tile_of, L.d_dep,
+                                L.d_dep + (size_t)L.nwork * kDepRow, c->s));
+        c->st.kernel_launches += 2;
+    }
     L.work_tx = tx;
     L.work_ty = ty;
     L.work_lpt = lpt;
@@ -1513,7 +1441,7 @@ bool substeps_ok(const adjamr_ctx *c, int l)
 
 // One substep launch of r substeps of level l (work list already built)
 // with the given dependency lists; r * ninterior cell updates.
-adjamr_status launch_substeps(adjamr_ctx *c, int l, int r, const int *dep_off, const int *dep_idx)
+adjamr_status launch_substeps(adjamr_ctx *c, int l, int r, const int *dep_idx, const int *dep_cnt)
 {
     Level &L = c->L[l];
     {
@@ -1528,8 +1456,8 @@ adjamr_status launch_substeps(adjamr_ctx *c, int l, int r, const int *dep_off, c
         }
         GhostArgs ga = fused_ghosts(c, l, 0);
         SubstepArgs sa{};
-        sa.dep_off = dep_off;
         sa.dep_idx = dep_idx;
+        sa.dep_cnt = dep_cnt;
         sa.done = c->d_done;
         sa.base = c->done_base;
         sa.nsub = r;
@@ -1572,7 +1500,7 @@ adjamr_status step_level_substeps(adjamr_ctx *c, int l, int r)
     Level &L = c->L[l];
     if (!L.patches.empty()) {
         TRY(build_work(c, l, c->ltx[l], c->lty[l]));
-        TRY(launch_substeps(c, l, r, L.d_dep_off, L.d_dep_idx));
+        TRY(launch_substeps(c, l, r, L.d_dep, L.d_dep + (size_t)L.nwork * kDepRow));
     }
     if (r & 1) L.cur = 1 - L.cur;
     L.nstep += r;
@@ -2496,11 +2424,10 @@ adjamr_status adjamr_substep_wait_selftest(adjamr_ctx *ctx, double *wait_ms)
         Level &L = ctx->L[l];
         TRY(build_work(ctx, l, ctx->ltx[l], ctx->lty[l]));
         // every tile waits for counter nwork, which no tile advances
-        std::vector<int> off((size_t)L.nwork + 1), idx((size_t)L.nwork, L.nwork);
-        for (int w = 0; w <= L.nwork; w++) off[(size_t)w] = w;
+        std::vector<int> idx((size_t)L.nwork * kDepRow, L.nwork), cnt((size_t)L.nwork, 1);
         std::vector<size_t> offs;
         char *d = nullptr;
-        CKR(ctx, upload_packed(ctx, {{off.data(), sizeof(int) * off.size()}, {idx.data(), sizeof(int) * idx.size()}},
+        CKR(ctx, upload_packed(ctx, {{idx.data(), sizeof(int) * idx.size()}, {cnt.data(), sizeof(int) * cnt.size()}},
                                &d, offs));
         const adjamr_stats keep = ctx->st;
         CKR(ctx, cudaEventRecord(ctx->ev0, ctx->s));

@@ -130,16 +130,19 @@ struct TileSched {
     unsigned long long base;
 };
 
-// Several substeps of one level in one launch (k_step2d_sub).  dep_off /
-// dep_idx (CSR over the work list): the tiles whose interior cells a tile's
-// staged region reads, itself included.  done[w] = base + substeps tile w has
-// completed in this launch (values from earlier launches are <= base).
+// Several substeps of one level in one launch (k_step2d_sub).  Row w of
+// dep_idx (stride kDepRow) lists the tiles whose interior cells tile w's
+// staged region reads, itself included; dep_cnt[w] entries, or more than
+// kDepRow when the row overflowed (then the tile waits for every tile).
+// done[w] = base + substeps tile w has completed in this launch (values from
+// earlier launches are <= base).
 constexpr int kMaxSubsteps = 16;
+constexpr int kDepRow = 48;
 constexpr unsigned long long kSubstepWaitNs = 1000000000ull;  // a wait gives up after 1 s
 constexpr unsigned int kSubstepWaitSpins = 1u << 24;
 constexpr int kSubstepErrBit = 1 << 30;  // recorded in the context's device error word
 struct SubstepArgs {
-    const int *dep_off, *dep_idx;
+    const int *dep_idx, *dep_cnt;
     unsigned long long *done;
     unsigned long long base;
     int nsub;
@@ -188,6 +191,12 @@ cudaError_t launch_step_substeps(int eqn, int tx, int ty, double *qa, double *qb
                                  unsigned long long *cfl_bits, cudaStream_t s, const GhostArgs &ga,
                                  const TileSched &sc, const SubstepArgs &sa);
 int substep_occupancy(int eqn, int tx, int ty);  // 0: no such kernel
+// dependency rows of a 2D level's work list for substep launches: tile_of
+// (one int per arena cell) receives the tile of every interior cell, then
+// each tile lists the tiles met by its cells and 2-cell halo (periodic
+// images across periodic boundaries; owner = the level's [M][N] owner map)
+cudaError_t launch_tile_deps(const PatchDesc *patches, const WorkItem *work, int nwork, const int *owner, int N, int M,
+                             const int *bc, int *tile_of, int *dep_idx, int *dep_cnt, cudaStream_t s);
 // compiled step-kernel tile (kx, ky) that holds tiles of tx x ty cells: the
 // smallest by area among 8x8, 16x8, 32x8, 16x16, 64x8, 32x16 (1D: 128 or 256);
 // false if none does

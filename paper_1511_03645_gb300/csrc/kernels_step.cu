@@ -544,18 +544,23 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
-// Warp 0 waits until every tile on w's dependency list has completed `target`
-// substeps.  Each wait is bounded (time and spins); it gives up early when
-// another CTA has already reported a failure.  Uniform over the CTA.
-__device__ __forceinline__ bool wait_deps(const SubstepArgs &sa, int w, unsigned long long target, int *s_ok)
+// Warp 0 waits until every tile on w's dependency row (all nwork tiles when
+// the row overflowed) has completed `target` substeps.  Each wait is bounded
+// (time and polls); it gives up early when another CTA has already reported
+// a failure.  Uniform over the CTA.
+__device__ __forceinline__ bool wait_deps(const SubstepArgs &sa, int w, int nwork, unsigned long long target,
+                                          int *s_ok)
 {
     if (threadIdx.x < 32) {
         bool ok = true;
-        const int e = sa.dep_off[w + 1];
+        const int n = sa.dep_cnt[w];
+        const bool all = n > kDepRow;
+        const int cnt = all ? nwork : n;
         unsigned long long t0 = 0;
         unsigned int spins = 0;
-        for (int j = sa.dep_off[w] + (int)threadIdx.x; ok && j < e; j += 32) {
-            const unsigned long long *f = sa.done + sa.dep_idx[j];
+        for (int j = (int)threadIdx.x; ok && j < cnt; j += 32) {
+            const int u = all ? j : sa.dep_idx[(long long)w * kDepRow + j];
+            const unsigned long long *f = sa.done + u;
             while (ld_acquire(f) < target) {
                 if (spins == 0) t0 = global_ns();
                 if ((++spins & 255u) == 0 &&
@@ -575,6 +580,11 @@ __device__ __forceinline__ bool wait_deps(const SubstepArgs &sa, int w, unsigned
     }
     __syncthreads();
     return *s_ok != 0;
+}
+
+__device__ __forceinline__ int claim_item(const TileSched &sc)
+{
+    return (int)(atomicAdd(sc.ctr, 1ull) - sc.base);
 }
 
 // nsub consecutive steps of one level in one launch (the substeps of the
@@ -597,33 +607,43 @@ __global__ void __launch_bounds__(kThreads) k_step2d_sub(double *qa, double *qb,
     pdl_launch_dependents();
     extern __shared__ double sm[];
     long long cfl = 0;
-    __shared__ int s_next, s_ok;
+    // s_next[it & 1]: the item taken during iteration it - 1 (a thread of
+    // warp 1 takes the next item while the CTA works on the current one, off
+    // the path of warp 0, which runs the dependency waits)
+    constexpr int kClaimer = 32;
+    __shared__ int s_next[2], s_ok;
     const int nitems = sa.nsub * nwork;
+    if (threadIdx.x == kClaimer) s_next[0] = claim_item(sc);
+    __syncthreads();
+    int i = s_next[0];
     // After a failed wait the CTA keeps taking items without working on them,
     // so that the counter advances by exactly nitems + gridDim.x.
     bool failed = false;
-    for (int i = fetch_tile(sc, &s_next, 0); i < nitems; i = fetch_tile(sc, &s_next, 0)) {
+    for (int it = 0; i < nitems; it++) {
+        const int nb = (it + 1) & 1;
+        if (threadIdx.x == kClaimer) s_next[nb] = claim_item(sc);
         if (failed || i < 0) {
             if (!failed && threadIdx.x == 0) atomicOr(sa.err, kSubstepErrBit);
             failed = true;
-            __syncthreads();  // every thread has read s_next before it is written again
-            continue;
+        } else {
+            const int s = i / nwork, w = i - s * nwork;
+            if (s > 0 && !wait_deps(sa, w, nwork, sa.base + (unsigned long long)s, &s_ok)) {
+                failed = true;
+            } else {
+                GhostArgs g = ga;
+                g.k = ga.k + s;
+                const WorkItem wi = work[w];
+                step2d_tile<EQN, TX, TY, true>((s & 1) ? qb : qa, (s & 1) ? qa : qb, aux, stride,
+                                               patches[wi.patch], wi, g, sm, cfl);
+                // the tile's stores precede the barrier that ends step2d_tile
+                if (threadIdx.x == 0) {
+                    __threadfence();
+                    st_release(sa.done + w, sa.base + (unsigned long long)s + 1);
+                }
+            }
         }
-        const int s = i / nwork, w = i - s * nwork;
-        if (s > 0 && !wait_deps(sa, w, sa.base + (unsigned long long)s, &s_ok)) {
-            failed = true;
-            continue;
-        }
-        GhostArgs g = ga;
-        g.k = ga.k + s;
-        const WorkItem wi = work[w];
-        step2d_tile<EQN, TX, TY, true>((s & 1) ? qb : qa, (s & 1) ? qa : qb, aux, stride, patches[wi.patch], wi, g,
-                                       sm, cfl);
-        // the tile's stores precede the barrier that ends step2d_tile
-        if (threadIdx.x == 0) {
-            __threadfence();
-            st_release(sa.done + w, sa.base + (unsigned long long)s + 1);
-        }
+        __syncthreads();  // s_next[nb] is written
+        i = s_next[nb];
     }
     cfl_reduce(cfl, cfl_bits);
 }
@@ -805,6 +825,73 @@ int occ2d(int tx, int ty)
     return n;
 }
 
+// tile of every interior cell of the level (one CTA per tile)
+__global__ void k_tile_map(const PatchDesc *__restrict__ patches, const WorkItem *__restrict__ work, int nwork,
+                           int *tile_of)
+{
+    const int w = blockIdx.x;
+    if (w >= nwork) return;
+    const WorkItem wi = work[w];
+    const PatchDesc P = patches[wi.patch];
+    for (int k = threadIdx.x; k < (int)wi.tx * wi.ty; k += blockDim.x) {
+        const int j = k / wi.tx, i = k - j * wi.tx;
+        tile_of[P.base + (long long)(wi.y0 + j + 2) * P.sx + (wi.x0 + i + 2)] = w;
+    }
+}
+
+// Dependency row of each tile (one CTA per tile): the distinct tiles owning
+// a cell of its cells + 2-cell halo, collected in a shared open-addressing
+// set with bounded probing.  Halo cells beyond a periodic boundary are taken
+// at their images; beyond the other boundaries the ghost values come from
+// cells inside the halo, so those cells are skipped.
+constexpr int kDepSet = 128;
+__global__ void k_tile_deps(const PatchDesc *__restrict__ patches, const WorkItem *__restrict__ work, int nwork,
+                            const int *__restrict__ owner, int N, int M, int4 bc, const int *__restrict__ tile_of,
+                            int *dep_idx, int *dep_cnt)
+{
+    __shared__ int set[kDepSet];
+    __shared__ int s_over;
+    const int w = blockIdx.x;
+    if (w >= nwork) return;
+    for (int k = threadIdx.x; k < kDepSet; k += blockDim.x) set[k] = -1;
+    if (threadIdx.x == 0) s_over = 0;
+    __syncthreads();
+    const WorkItem wi = work[w];
+    const PatchDesc P = patches[wi.patch];
+    const int W = wi.tx + 4, H = wi.ty + 4, i0 = P.ilo + wi.x0 - 2, j0 = P.jlo + wi.y0 - 2;
+    for (int k = threadIdx.x; k < W * H; k += blockDim.x) {
+        int J = j0 + k / W, I = i0 + k % W;
+        if (I < 0) { if (bc.x != ADJAMR_BC_PERIODIC) continue; I += N; }
+        if (I >= N) { if (bc.y != ADJAMR_BC_PERIODIC) continue; I -= N; }
+        if (J < 0) { if (bc.z != ADJAMR_BC_PERIODIC) continue; J += M; }
+        if (J >= M) { if (bc.w != ADJAMR_BC_PERIODIC) continue; J -= M; }
+        const int o = owner[(long long)J * N + I];
+        if (o < 0) continue;
+        const int u = tile_of[o];
+        int h = (int)(((unsigned)u * 2654435761u) >> 25);  // 7 bits
+        bool in = false;
+        for (int p = 0; p < kDepSet; p++) {
+            const int prev = atomicCAS(&set[h], -1, u);
+            if (prev == -1 || prev == u) {
+                in = true;
+                break;
+            }
+            h = (h + 1) & (kDepSet - 1);
+        }
+        if (!in) s_over = 1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int n = 0;
+        for (int k = 0; k < kDepSet; k++)
+            if (set[k] >= 0) {
+                if (n < kDepRow) dep_idx[(long long)w * kDepRow + n] = set[k];
+                n++;
+            }
+        dep_cnt[w] = (s_over || n > kDepRow) ? kDepRow + 1 : n;
+    }
+}
+
 template <int EQN>
 cudaError_t dispatch_sub(int tx, int ty, int nwork, int grid, double *qa, double *qb, const double *aux,
                          long long stride, const PatchDesc *p, const WorkItem *w, unsigned long long *c, cudaStream_t s,
@@ -850,6 +937,18 @@ cudaError_t launch_step_substeps(int eqn, int tx, int ty, double *qa, double *qb
     if (!sc.ctr || !ga.gd || sa.nsub < 1 || sa.nsub > kMaxSubsteps || grid < 1) return cudaErrorInvalidValue;
     if (nwork <= 0) return cudaSuccess;
     return sub_switch(eqn, tx, ty, nwork, grid, qa, qb, aux, stride, patches, work, cfl_bits, s, ga, sc, sa, nullptr);
+}
+
+cudaError_t launch_tile_deps(const PatchDesc *patches, const WorkItem *work, int nwork, const int *owner, int N, int M,
+                             const int *bc, int *tile_of, int *dep_idx, int *dep_cnt, cudaStream_t s)
+{
+    if (nwork <= 0) return cudaSuccess;
+    k_tile_map<<<nwork, 256, 0, s>>>(patches, work, nwork, tile_of);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_tile_deps<<<nwork, 256, 0, s>>>(patches, work, nwork, owner, N, M, make_int4(bc[0], bc[1], bc[2], bc[3]),
+                                      tile_of, dep_idx, dep_cnt);
+    return cudaGetLastError();
 }
 
 int substep_occupancy(int eqn, int tx, int ty)
