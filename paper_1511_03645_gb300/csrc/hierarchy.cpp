@@ -105,6 +105,11 @@ struct adjamr_ctx {
     long long T[ADJAMR_MAX_LEVELS] = {};
     long long rebuilt_tick[ADJAMR_MAX_LEVELS];
     cudaStream_t s = nullptr;
+    // side stream of the adjoint flags that overlap the step of their level
+    // (high priority: the host waits for them), and the event that orders
+    // them after the work already queued on s
+    cudaStream_t s_flag = nullptr;
+    cudaEvent_t ev_flag = nullptr;
     std::string err;
     bool have_medium = false;
     MediumDev mh[ADJAMR_MAX_LEVELS];
@@ -926,23 +931,38 @@ adjamr_status grow_flag_list(adjamr_ctx *c, long long n)
 // Rebuild levels base+1 .. nlevels-1 top-down (Sec. 3, regridding).
 void harvest_timing(adjamr_ctx *c);
 
-adjamr_status regrid_body(adjamr_ctx *c, int base, int init);
+adjamr_status regrid_body(adjamr_ctx *c, int base, int init, bool side_flags = false);
 
 double ms_since(std::chrono::steady_clock::time_point t)
 {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t).count();
 }
 
-adjamr_status regrid_from(adjamr_ctx *c, int base, int init)
+adjamr_status regrid_from(adjamr_ctx *c, int base, int init, bool side_flags = false)
 {
     c->st.regrids++;
     auto t0 = std::chrono::steady_clock::now();
-    adjamr_status st = regrid_body(c, base, init);
+    adjamr_status st = regrid_body(c, base, init, side_flags);
     c->st.regrid_host_ms += ms_since(t0);
     return st;
 }
 
-adjamr_status regrid_body(adjamr_ctx *c, int base, int init)
+// flags of level lev into d_flagbuf (count, bounding box and bitmap read back)
+adjamr_status regrid_flags(adjamr_ctx *c, int lev, long long *nf, int *bb)
+{
+    const Level &C = c->L[lev];
+    const int pitch64 = (C.N + 63) >> 6;
+    size_t nb = (size_t)pitch64 * C.M * sizeof(uint64_t);
+    if (c->flagbuf_bytes < nb) {
+        dfree(c->d_flagbuf, c->s);
+        CKR(c, dalloc(&c->d_flagbuf, nb / sizeof(uint64_t), c->s));
+        c->flagbuf_bytes = nb;
+    }
+    CKR(c, cudaMemsetAsync(c->d_flagbuf, 0, nb, c->s));
+    return flag_dense(c, lev, c->P.tol, c->d_flagbuf, pitch64, nullptr, nf, bb);
+}
+
+adjamr_status regrid_body(adjamr_ctx *c, int base, int init, bool side_flags)
 {
     const adjamr_params &P = c->P;
     for (int lev = base; lev < P.nlevels - 1; lev++) {
@@ -952,17 +972,22 @@ adjamr_status regrid_body(adjamr_ctx *c, int base, int init)
         const long long tick = C.nstep * c->T[lev];
         // ---- adjoint flags of level lev on its index space (device bitmap) ----
         const int pitch64 = (N + 63) >> 6;
-        size_t nb = (size_t)pitch64 * M * sizeof(uint64_t);
-        if (c->flagbuf_bytes < nb) {
-            dfree(c->d_flagbuf, c->s);
-            CKR(c, dalloc(&c->d_flagbuf, nb / sizeof(uint64_t), c->s));
-            c->flagbuf_bytes = nb;
-        }
-        CKR(c, cudaMemsetAsync(c->d_flagbuf, 0, nb, c->s));
         long long nf = 0;
         int bb[4];
         auto tp = std::chrono::steady_clock::now();
-        TRY(flag_dense(c, lev, P.tol, c->d_flagbuf, pitch64, nullptr, &nf, bb));
+        if (lev == base && side_flags) {
+            // on the side stream, after the work queued before ev_flag
+            CKR(c, cudaStreamWaitEvent(c->s_flag, c->ev_flag, 0));
+            std::swap(c->s, c->s_flag);
+            const adjamr_status fs = regrid_flags(c, lev, &nf, bb);
+            std::swap(c->s, c->s_flag);
+            TRY(fs);
+            // later work on s that reuses the flag buffers comes after them
+            CKR(c, cudaEventRecord(c->ev_flag, c->s_flag));
+            CKR(c, cudaStreamWaitEvent(c->s, c->ev_flag, 0));
+        } else {
+            TRY(regrid_flags(c, lev, &nf, bb));
+        }
         c->st.regrid_phase_ms[0] += ms_since(tp);
         harvest_timing(c);
         auto tc = std::chrono::steady_clock::now();
@@ -1536,16 +1561,24 @@ adjamr_status check_err(adjamr_ctx *c)
 }
 
 // sum the recorded step-kernel event pairs (stream already synchronised)
+// (pairs whose end event has not completed yet stay for a later harvest)
 void harvest_timing(adjamr_ctx *c)
 {
-    for (size_t k = 0; k + 1 < c->tev_used; k += 2) {
+    size_t k = 0;
+    for (; k + 1 < c->tev_used; k += 2) {
+        if (cudaEventQuery(c->tev[k + 1]) == cudaErrorNotReady) break;
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, c->tev[k], c->tev[k + 1]) == cudaSuccess) {
             c->st.step_kernel_ms += ms;
             c->st.level_step_ms[c->tev_level[k]] += ms;
         }
     }
-    c->tev_used = 0;
+    (void)cudaGetLastError();
+    for (size_t j = k; j < c->tev_used; j++) {
+        std::swap(c->tev[j - k], c->tev[j]);
+        std::swap(c->tev_level[j - k], c->tev_level[j]);
+    }
+    c->tev_used -= k;
 }
 
 // Berger-Oliger recursion (Sec. 3, time stepping with subcycling)
@@ -1554,17 +1587,27 @@ adjamr_status step_level(adjamr_ctx *c, int l)
     Level &L = c->L[l];
     const adjamr_params &P = c->P;
     int k = P.regrid_interval;
-    bool regridded = false;
-    if (l < P.nlevels - 1 && k > 0 && L.nstep > 0 && L.nstep % k == 0 && c->rebuilt_tick[l + 1] != L.nstep * c->T[l]) {
-        TRY(regrid_from(c, l, 0));
-        regridded = true;
-    }
+    const bool regrid =
+        l < P.nlevels - 1 && k > 0 && L.nstep > 0 && L.nstep % k == 0 && c->rebuilt_tick[l + 1] != L.nstep * c->T[l];
     int sub = 0;
     if (l > 0) sub = (int)(L.nstep - c->L[l - 1].nstep * P.ratio[l - 1]);
-    // After the first substep and without a rebuild in between, the kernel
-    // ahead is this level's previous step, the average-down into it or a
-    // finer level's kernel; none of them touches this level's ghost cells.
-    TRY(step_patches(c, l, sub, c->lfuse[l] ? GHOST_FUSED : GHOST_FILL, sub > 0 && !regridded));
+    const GhostMode gm = c->lfuse[l] ? GHOST_FUSED : GHOST_FILL;
+    if (regrid && c->s_flag && (P.flag_mode == ADJAMR_FLAG_BRACKET_MAX || P.flag_mode == ADJAMR_FLAG_LINEAR)) {
+        // The adjoint flags of level l read its current interior state, which
+        // its step leaves alone (it writes the other buffer): the flags run on
+        // the side stream while the step runs, so the host clusters and builds
+        // level l + 1 during the step.  The rebuilt levels come after the step
+        // in stream order, as their first use does.
+        CKR(c, cudaEventRecord(c->ev_flag, c->s));
+        TRY(step_patches(c, l, sub, gm, false));
+        TRY(regrid_from(c, l, 0, true));
+    } else {
+        if (regrid) TRY(regrid_from(c, l, 0));
+        // After the first substep and without a rebuild in between, the kernel
+        // ahead is this level's previous step, the average-down into it or a
+        // finer level's kernel; none of them touches this level's ghost cells.
+        TRY(step_patches(c, l, sub, gm, sub > 0 && !regrid));
+    }
     if (l < P.nlevels - 1 && !c->L[l + 1].patches.empty()) {
         int r = P.ratio[l];
         TRY(coarse_pre(c, l + 1));
@@ -1746,6 +1789,15 @@ adjamr_status create_impl(const adjamr_params *p, adjamr_ctx **out)
         cudaMalloc(&c->d_wctr, sizeof(unsigned long long)) != cudaSuccess) {
         adjamr_destroy(c);
         return ADJAMR_ENOMEM;
+    }
+    {
+        int lo = 0, hi = 0;
+        if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&c->s_flag, cudaStreamNonBlocking, hi) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_flag, cudaEventDisableTiming) != cudaSuccess) {
+            adjamr_destroy(c);
+            return ADJAMR_ECUDA;
+        }
     }
     cudaMemsetAsync(c->d_cfl, 0, sizeof(unsigned long long), c->s);
     cudaMemsetAsync(c->d_wctr, 0, sizeof(unsigned long long), c->s);
@@ -2497,6 +2549,11 @@ void adjamr_destroy(adjamr_ctx *ctx)
     dfree(ctx->d_done, ctx->s);
     cache_drain(ctx);
     cudaStreamSynchronize(ctx->s);
+    if (ctx->s_flag) {
+        cudaStreamSynchronize(ctx->s_flag);
+        cudaStreamDestroy(ctx->s_flag);
+    }
+    if (ctx->ev_flag) cudaEventDestroy(ctx->ev_flag);
     if (ctx->d_cfl) cudaFree(ctx->d_cfl);
     if (ctx->d_count) cudaFree(ctx->d_count);
     if (ctx->d_fout) cudaFree(ctx->d_fout);

@@ -83,23 +83,25 @@ __global__ void k_cpre(const GhostDesc *__restrict__ gd, const unsigned long lon
     }
 }
 
+// one thread per (coarse cell, field): the sum of its r^d fine values in row
+// order, times 1/r^d
 __global__ void k_average_down(int dim, int m, const AvgDesc *__restrict__ ad, long long n,
                                const double *__restrict__ qf, long long sf, double *qc, long long sc, int r)
 {
     pdl_wait();
     pdl_launch_dependents();
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    AvgDesc a = ad[t];
-    int rr = (dim == 2) ? r : 1;
-    double inv = 1.0 / (double)(r * rr);
-    for (int f = 0; f < m; f++) {
-        const double *src = qf + (long long)f * sf + a.src;
-        double s = 0.0;
-        for (int jj = 0; jj < rr; jj++)
-            for (int ii = 0; ii < r; ii++) s = s + src[(long long)jj * a.fsx + ii];
-        qc[(long long)f * sc + a.dst] = s * inv;
-    }
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * m) return;
+    const long long e = t / m;
+    const int f = (int)(t - e * m);
+    const AvgDesc a = ad[e];
+    const int rr = (dim == 2) ? r : 1;
+    const double inv = 1.0 / (double)(r * rr);
+    const double *src = qf + (long long)f * sf + a.src;
+    double s = 0.0;
+    for (int jj = 0; jj < rr; jj++)
+        for (int ii = 0; ii < r; ii++) s = s + src[(long long)jj * a.fsx + ii];
+    qc[(long long)f * sc + a.dst] = s * inv;
 }
 
 // boundary map of a level index (no signs: the medium is even)
@@ -906,7 +908,7 @@ cudaError_t launch_average_down(int dim, int m, const AvgDesc *a, long long n, c
                                 double *qc, long long sc, int r, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    return launch_pdl(k_average_down, dim3(nblk(n)), dim3(kT), 0, s, dim, m, a, n, qf, sf, qc, sc, r);
+    return launch_pdl(k_average_down, dim3(nblk(n * m)), dim3(kT), 0, s, dim, m, a, n, qf, sf, qc, sc, r);
 }
 
 cudaError_t launch_aux_fill(int eqn, int dim, const AuxDesc *d, long long n, double *aux, double *med,
