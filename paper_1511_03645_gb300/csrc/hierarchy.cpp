@@ -53,6 +53,8 @@ struct Level {
     // substep launches: dependency rows of the work list ([nwork][kDepRow]
     // tile indices, then nwork counts) and the tile of every arena cell
     int *d_dep = nullptr, *d_tile_of = nullptr;
+    // coefficient table of the whole index space (AuxTable), kept across rebuilds
+    double *d_auxtab = nullptr;
     std::vector<WorkItem> h_work;
     GhostDesc *d_ghost = nullptr;
     long long nghost = 0;
@@ -171,6 +173,7 @@ struct adjamr_ctx {
     size_t done_cap = 0;
     unsigned long long done_base = 0;
     int cgen = 0;  // generation of the coarse-stencil marks
+    bool aux_tables = true;  // per-level coefficient tables (off in the serving loop)
     bool timing = false;
     // gauges: cell indices per level (device), records on the device
     int ngauge = 0;
@@ -242,6 +245,15 @@ void cput(adjamr_ctx *c, T *&p)
 
 namespace adjamr {
 void ctx_set_block_cache(adjamr_ctx *c, size_t cap_bytes) { c->blk_cache_cap = cap_bytes; }
+void ctx_set_aux_tables(adjamr_ctx *c, bool on) { c->aux_tables = on; }
+
+// index-space cells of level l's coefficient table (0: none is kept)
+long long aux_table_cells(const adjamr_ctx *c, int l)
+{
+    constexpr long long kMaxCells = 1ll << 23;  // <= 8.4 M cells (400 MB at 6 fields)
+    const long long n = (long long)(c->L[l].N + 4) * (c->P.dim == 2 ? c->L[l].M + 4 : 1);
+    return (c->aux_tables && n <= kMaxCells) ? n : 0;
+}
 
 bool pdl_enabled()
 {
@@ -587,14 +599,16 @@ adjamr_status fill_aux(adjamr_ctx *c, int l, const Level *old = nullptr)
     Level &L = c->L[l];
     if (!c->have_medium || L.patches.empty()) return ADJAMR_OK;
     AuxReuse ru{nullptr, nullptr, nullptr, 0, c->naux, c->nmed};
-    if (old && !old->patches.empty() && old->d_owner && old->aux) {
+    const long long tn = aux_table_cells(c, l);
+    const AuxTable tb{L.d_auxtab, tn, L.N + 4};
+    if (!tb.tab && old && !old->patches.empty() && old->d_owner && old->aux) {
         ru.owner = old->d_owner;
         ru.aux = old->aux;
         ru.med = old->med;
         ru.stride = old->ncell;
     }
     CKR(c, launch_aux_patches(c->P.eqn, L.d_patches, L.d_sprefix, (int)L.patches.size(), L.nstore, idx_of(c, l),
-                              L.aux, L.med, L.ncell, L.d_med, geom_of(c, l), c->s, ru));
+                              L.aux, L.med, L.ncell, L.d_med, geom_of(c, l), c->s, ru, tb));
     c->st.kernel_launches++;
     return ADJAMR_OK;
 }
@@ -1676,6 +1690,17 @@ adjamr_status set_medium_impl(adjamr_ctx *c, const adjamr_medium *m)
         CKR(c, dalloc(&L.d_med, 1, c->s));
         CKR(c, cudaMemcpyAsync(L.d_med, &md, sizeof md, cudaMemcpyHostToDevice, c->s));
     }
+    // coefficient tables: the medium does not change in time, so the
+    // coefficients of a cell depend on (level, I, J) only
+    for (int l = 0; l < c->P.nlevels; l++) {
+        Level &L = c->L[l];
+        dfree(L.d_auxtab, c->s);
+        const long long tn = aux_table_cells(c, l);
+        if (tn == 0) continue;
+        CKR(c, dalloc(&L.d_auxtab, (size_t)(c->naux + c->nmed) * tn, c->s));
+        CKR(c, launch_aux_table(c->P.eqn, L.d_med, geom_of(c, l), L.d_auxtab, c->s));
+        c->st.kernel_launches++;
+    }
     CKR(c, cudaStreamSynchronize(c->s));
     c->have_medium = true;
     for (int l = 0; l < c->P.nlevels; l++) TRY(fill_aux(c, l));
@@ -2537,6 +2562,7 @@ void adjamr_destroy(adjamr_ctx *ctx)
     for (int l = 0; l < ADJAMR_MAX_LEVELS; l++) {
         free_level(ctx, ctx->L[l]);
         dfree(ctx->L[l].d_med, ctx->s);
+        dfree(ctx->L[l].d_auxtab, ctx->s);
     }
     for (double *p : ctx->dense_dev) cudaFreeAsync(p, ctx->s);
     dfree(ctx->d_flagbuf, ctx->s);

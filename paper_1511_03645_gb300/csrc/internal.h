@@ -272,6 +272,8 @@ cudaError_t launch_gauges(const GaugeArgs &g, cudaStream_t s);
 // (0: every block is freed at once; the serving loop, which admits requests by
 // their projected bytes, uses 0)
 void ctx_set_block_cache(adjamr_ctx *c, size_t cap_bytes);
+// per-level coefficient tables on (default) or off; set before adjamr_set_medium
+void ctx_set_aux_tables(adjamr_ctx *c, bool on);
 
 // bracket-max flags over the level's index space, one thread per (cell, group
 // of a.gblk snapshot blocks), into the zeroed bitmap a.flags_bits
@@ -338,8 +340,19 @@ struct AuxReuse {
     long long stride;
     int naux, nmed;
 };
+// Coefficient table of a level: aux then med fields of every cell of the
+// index space with a 2-cell border ([naux + nmed][rows][N + 4], rows = M + 4
+// in 2D, 1 in 1D), computed once per medium by launch_aux_table.
+struct AuxTable {
+    const double *tab;
+    long long stride;  // cells per field
+    int width;         // N + 4
+};
+cudaError_t launch_aux_table(int eqn, const MediumDev *mdev, LevelGeom geom, double *tab, cudaStream_t s);
+// tab.tab != nullptr: the storage cells copy their coefficients from the table
 cudaError_t launch_aux_patches(int eqn, const PatchDesc *p, const long long *sprefix, int np, long long nstore,
                                LevelIdx g, double *aux, double *med, long long stride, const MediumDev *mdev,
-                               LevelGeom geom, cudaStream_t s, AuxReuse ru = AuxReuse{nullptr, nullptr, nullptr, 0, 0, 0});
+                               LevelGeom geom, cudaStream_t s, AuxReuse ru = AuxReuse{nullptr, nullptr, nullptr, 0, 0, 0},
+                               AuxTable tab = AuxTable{nullptr, 0, 0});
 
 }  // namespace adjamr

@@ -191,6 +191,18 @@ __device__ void aux_cell(int eqn, int dim, const MediumDev &md, const LevelGeom 
     }
 }
 
+// the coefficients of every cell of the bordered index space (aux_cell's
+// arithmetic, so the table holds the bits the per-cell path computes)
+__global__ void k_aux_table(int eqn, const MediumDev *__restrict__ mdp, LevelGeom g, double *tab, long long n, int W,
+                            int naux)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int j = (int)(t / W), i = (int)(t - (long long)j * W);
+    const int I = i - 2, J = (g.dim == 2) ? j - 2 : 0;
+    aux_cell(eqn, g.dim, *mdp, g, I, J, t, tab, tab + (long long)naux * n, n);
+}
+
 __global__ void k_aux_fill(int eqn, int dim, const AuxDesc *__restrict__ ad, long long n, double *aux, double *med,
                            long long stride, const MediumDev *__restrict__ mdp, LevelGeom g)
 {
@@ -394,7 +406,7 @@ __global__ void k_init_new(const PatchDesc *__restrict__ pd, const long long *__
 
 __global__ void k_aux_patches(int eqn, const PatchDesc *__restrict__ pd, const long long *__restrict__ sprefix,
                               int np, long long nstore, LevelIdx g, double *aux, double *med, long long stride,
-                              const MediumDev *__restrict__ mdp, LevelGeom geom, AuxReuse ru)
+                              const MediumDev *__restrict__ mdp, LevelGeom geom, AuxReuse ru, AuxTable tb)
 {
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nstore) return;
@@ -404,6 +416,13 @@ __global__ void k_aux_patches(int eqn, const PatchDesc *__restrict__ pd, const l
     int sj = (int)(k / P.sx), si = (int)(k - (long long)sj * P.sx);
     const int I = P.ilo + si - 2, J = P.jlo + sj - g.gy;
     const long long idx = P.base + k;
+    if (tb.tab) {
+        const long long ti = (long long)(J + g.gy) * tb.width + (I + 2);
+        for (int f = 0; f < ru.naux; f++) aux[(long long)f * stride + idx] = tb.tab[(long long)f * tb.stride + ti];
+        for (int f = 0; f < ru.nmed; f++)
+            med[(long long)f * stride + idx] = tb.tab[(long long)(ru.naux + f) * tb.stride + ti];
+        return;
+    }
     if (ru.owner) {
         const int o = owner_at(ru.owner, g, I, J);
         if (o >= 0) {
@@ -959,10 +978,18 @@ cudaError_t launch_init_new(const PatchDesc *p, const long long *prefix, int np,
 
 cudaError_t launch_aux_patches(int eqn, const PatchDesc *p, const long long *sprefix, int np, long long nstore,
                                LevelIdx g, double *aux, double *med, long long stride, const MediumDev *mdev,
-                               LevelGeom geom, cudaStream_t s, AuxReuse ru)
+                               LevelGeom geom, cudaStream_t s, AuxReuse ru, AuxTable tb)
 {
     if (nstore <= 0) return cudaSuccess;
-    k_aux_patches<<<nblk(nstore), kT, 0, s>>>(eqn, p, sprefix, np, nstore, g, aux, med, stride, mdev, geom, ru);
+    k_aux_patches<<<nblk(nstore), kT, 0, s>>>(eqn, p, sprefix, np, nstore, g, aux, med, stride, mdev, geom, ru, tb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_aux_table(int eqn, const MediumDev *mdev, LevelGeom geom, double *tab, cudaStream_t s)
+{
+    const int W = geom.N + 4, H = (geom.dim == 2) ? geom.M + 4 : 1;
+    const long long n = (long long)W * H;
+    k_aux_table<<<nblk(n), kT, 0, s>>>(eqn, mdev, geom, tab, n, W, naux_of(eqn));
     return cudaGetLastError();
 }
 

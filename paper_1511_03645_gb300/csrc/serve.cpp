@@ -80,7 +80,11 @@ void run_request(adjamr_server *srv, Req *r, cudaStream_t s)
     p.stream = (void *)s;
     adjamr_ctx *ctx = nullptr;
     adjamr_status st = adjamr_init_grid_hierarchy(&p, &ctx);
-    if (st == ADJAMR_OK) adjamr::ctx_set_block_cache(ctx, 0);  // admitted bytes stay the projected bytes
+    if (st == ADJAMR_OK) {
+        // admitted bytes stay the projected bytes: no block cache, no coefficient tables
+        adjamr::ctx_set_block_cache(ctx, 0);
+        adjamr::ctx_set_aux_tables(ctx, false);
+    }
     if (st == ADJAMR_OK) st = adjamr_set_medium(ctx, &r->m);
     if (st == ADJAMR_OK) st = adjamr_set_adjoint(ctx, r->adj);
     if (st == ADJAMR_OK) st = adjamr_regrid(ctx, 0, 1);
