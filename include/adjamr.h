@@ -72,7 +72,7 @@ enum { ADJAMR_MEDIUM_LAYERED = 1, ADJAMR_MEDIUM_DENSE = 2 };
  * the work-list, one launch per patch (the comparison baseline), or a
  * persistent grid whose CTAs take the next tile from an atomic counter
  * (dynamic balancing).  SUBSTEPS, on the finest level of a 2D hierarchy with
- * 8x8, 16x8 or 16x16 kernel tiles: all r substeps of one coarser step in one
+ * 8x8, 16x8, 16x12 or 16x16 kernel tiles: all r substeps of one coarser step in one
  * launch, each tile starting a substep as soon as the tiles its halo reads
  * have finished the previous one (ghost ring computed in the kernel); on any
  * other level it acts as DYNAMIC.  Every mode computes the same bits. */
@@ -257,7 +257,7 @@ adjamr_status adjamr_set_timing(adjamr_ctx *ctx, int enable);
 /* Step-kernel configuration of one level (level = -1: every level), used
  * from the next step on: the tile size the level's patches are cut to
  * (near-equal tiles of at most tile_x x tile_y cells; the kernel compiled for
- * the smallest of 8x8, 16x8, 32x8, 16x16, 64x8, 32x16 that holds them runs
+ * the smallest of 8x8, 16x8, 16x12, 32x8, 16x16, 64x8, 32x16 that holds them runs
  * them; 1D: tile_x <= 256, tile_y ignored), whether the kernel computes the
  * level's ghost ring (same-level copies and coarse space-time interpolation,
  * Sec. 3) while staging its tiles (fuse_ghosts = 1, the default) or a

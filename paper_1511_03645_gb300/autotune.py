@@ -19,7 +19,7 @@ from . import adjamr as A
 HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE = os.path.join(HERE, "_build", "autotune.json")
 # tile sizes the patches are cut to (the kernel compiled for the smallest of
-# 8x8, 16x8, 32x8, 16x16, 64x8, 32x16 holding them runs them): the compiled
+# 8x8, 16x8, 16x12, 32x8, 16x16, 64x8, 32x16 holding them runs them): the compiled
 # shapes and cuts between them, which move a level's tile count towards whole
 # waves of resident CTAs
 TILES = [(32, 8), (16, 8), (16, 16), (32, 16), (64, 8), (8, 8), (12, 8), (16, 12), (24, 8), (24, 16), (48, 8),

@@ -184,7 +184,7 @@ cudaError_t launch_step(int dim, int eqn, int tx, int ty, const double *q, doubl
 int step_occupancy(int dim, int eqn, int tx, int ty);
 // sa.nsub steps of a 2D level in one launch of `grid` CTAs that take items
 // from sc (sc.ctr required; the counter advances by nsub * nwork + grid).
-// Kernel tiles 8x8, 16x8 and 16x16 only; ga.gd required (the ghost ring is
+// Kernel tiles 8x8, 16x8, 16x12 and 16x16 only; ga.gd required (the ghost ring is
 // computed in the kernel), ga.k = the first substep.
 cudaError_t launch_step_substeps(int eqn, int tx, int ty, double *qa, double *qb, const double *aux, long long stride,
                                  const PatchDesc *patches, const WorkItem *work, int nwork, int grid,
@@ -198,7 +198,7 @@ int substep_occupancy(int eqn, int tx, int ty);  // 0: no such kernel
 cudaError_t launch_tile_deps(const PatchDesc *patches, const WorkItem *work, int nwork, const int *owner, int N, int M,
                              const int *bc, int *tile_of, int *dep_idx, int *dep_cnt, cudaStream_t s);
 // compiled step-kernel tile (kx, ky) that holds tiles of tx x ty cells: the
-// smallest by area among 8x8, 16x8, 32x8, 16x16, 64x8, 32x16 (1D: 128 or 256);
+// smallest by area among 8x8, 16x8, 16x12, 32x8, 16x16, 64x8, 32x16 (1D: 128 or 256);
 // false if none does
 bool step_kernel_shape(int dim, int tx, int ty, int *kx, int *ky);
 

@@ -274,7 +274,11 @@ struct Smem2D {
     static constexpr int nXW = 4 * XEX * XEY, nXF = 4 * XEX * XEY;
     static constexpr int nYW = 4 * YEX * YEY, nYF = 4 * YEX * YEY;
     static constexpr int nXN = 2 * XNX * XNY, nYN = 2 * YNX * YNY;
-    static constexpr int total = nQ + nA + nXW + nXF + nYW + nYF + nXN + nYN;
+    // the second-order fluxes Fn, Gn live from the limiter to the transverse
+    // phase, when the staged state is not read: they take its place where
+    // they fit (the update then reads the tile's cells from global memory)
+    static constexpr bool kAlias = nXN + nYN <= nQ;
+    static constexpr int total = nQ + nA + nXW + nXF + nYW + nYF + (kAlias ? 0 : nXN + nYN);
     static constexpr size_t bytes = sizeof(double) * (size_t)total;
 };
 
@@ -293,8 +297,8 @@ __device__ __forceinline__ void step2d_tile(const double *__restrict__ q, double
     double *XF = XW + S::nXW;  // fluctuations am_0, am_n, ap_0, ap_n at x-edges
     double *YW = XF + S::nXF;  // same at y-edges; later SY + GG
     double *YF = YW + S::nYW;
-    double *XN = YF + S::nYF;  // Fn (2 comps)
-    double *YN = XN + S::nXN;  // Gn (2 comps)
+    double *XN = S::kAlias ? sQ : YF + S::nYF;  // Fn (2 comps)
+    double *YN = XN + S::nXN;                   // Gn (2 comps)
     constexpr int PX = S::PX, PY = S::PY, PS = PX * PY;
     constexpr int XEX = S::XEX, XEY = S::XEY, XES = XEX * XEY;
     constexpr int YEX = S::YEX, YEY = S::YEY, YES = YEX * YEY;
@@ -497,9 +501,12 @@ __device__ __forceinline__ void step2d_tile(const double *__restrict__ q, double
             double B1 = (YF[3 * YES + oB] + YF[YES + oT]) + (GG[GGS + gT] - GG[GGS + gB]);
             int s = (r + 2) * PX + c + 2;
             long long g = P.base + (long long)(y0 + r + 2) * P.sx + (x0 + c + 2);
-            qn[g] = sQ[s] - (dtdx * A0 + dtdy * B0);
-            qn[stride + g] = fma(-dtdx, A1, sQ[PS + s]);        // u sees the x-edges only
-            qn[2 * stride + g] = fma(-dtdy, B1, sQ[2 * PS + s]); // v sees the y-edges only
+            const double p0 = S::kAlias ? ldq<CG>(q + g) : sQ[s];
+            const double u0 = S::kAlias ? ldq<CG>(q + stride + g) : sQ[PS + s];
+            const double v0 = S::kAlias ? ldq<CG>(q + 2 * stride + g) : sQ[2 * PS + s];
+            qn[g] = p0 - (dtdx * A0 + dtdy * B0);
+            qn[stride + g] = fma(-dtdx, A1, u0);        // u sees the x-edges only
+            qn[2 * stride + g] = fma(-dtdy, B1, v0);    // v sees the y-edges only
         }
         __syncthreads();
     }
@@ -783,6 +790,7 @@ cudaError_t dispatch2d(int tx, int ty, int nwork, int grid, const double *q, dou
                                                   c, s, ga, sc);
     ADJ_TILE(32, 8)
     ADJ_TILE(16, 8)
+    ADJ_TILE(16, 12)
     ADJ_TILE(16, 16)
     ADJ_TILE(32, 16)
     ADJ_TILE(64, 8)
@@ -817,6 +825,7 @@ int occ2d(int tx, int ty)
     }
     ADJ_OCC(32, 8)
     ADJ_OCC(16, 8)
+    ADJ_OCC(16, 12)
     ADJ_OCC(16, 16)
     ADJ_OCC(32, 16)
     ADJ_OCC(64, 8)
@@ -908,6 +917,7 @@ cudaError_t dispatch_sub(int tx, int ty, int nwork, int grid, double *qa, double
                           w, nwork, c, ga, sc, sa);                                                            \
     }
     ADJ_SUB(16, 16)
+    ADJ_SUB(16, 12)
     ADJ_SUB(16, 8)
     ADJ_SUB(8, 8)
 #undef ADJ_SUB
@@ -992,7 +1002,7 @@ bool step_kernel_shape(int dim, int tx, int ty, int *kx, int *ky)
         *ky = 1;
         return true;
     }
-    static const int shapes[6][2] = {{8, 8}, {16, 8}, {32, 8}, {16, 16}, {64, 8}, {32, 16}};
+    static const int shapes[7][2] = {{8, 8}, {16, 8}, {16, 12}, {32, 8}, {16, 16}, {64, 8}, {32, 16}};
     for (const auto &sh : shapes)
         if (tx <= sh[0] && ty <= sh[1]) {
             *kx = sh[0];
