@@ -658,13 +658,36 @@ adjamr_status build_ghost_map(adjamr_ctx *c, int l)
 // Coarse stencil values of level l's kind-1 ghost cells for all substeps of
 // the step level l - 1 has just taken (its old and new states final until the
 // average-down); the substeps' ghost fills and ghost rings read them.
+bool substeps_ok(const adjamr_ctx *c, int l);
+
+// Whether level l's first ghost fill of a coarse step also computes the
+// stored stencil values of the later substeps (separate fill, one launch per
+// substep): then coarse_pre does nothing for it.
+bool fill_makes_pre(const adjamr_ctx *c, int l) { return l > 0 && !c->lfuse[l] && !substeps_ok(c, l); }
+
 adjamr_status coarse_pre(adjamr_ctx *c, int l)
 {
     Level &L = c->L[l];
     const Level &C = c->L[l - 1];
-    if (!L.d_cpre || L.nghost == 0) return ADJAMR_OK;
+    if (!L.d_cpre || L.nghost == 0 || fill_makes_pre(c, l)) return ADJAMR_OK;
+    // timed with level l's steps (a fill at substep 0 computes the same values
+    // inside the level's timing otherwise)
+    cudaEvent_t te = nullptr;
+    if (c->timing) {
+        while (c->tev.size() < c->tev_used + 2) {
+            cudaEvent_t e;
+            CKR(c, cudaEventCreate(&e));
+            c->tev.push_back(e);
+            c->tev_level.push_back(0);
+        }
+        c->tev_level[c->tev_used] = l;
+        te = c->tev[c->tev_used + 1];
+        CKR(c, cudaEventRecord(c->tev[c->tev_used], c->s));
+        c->tev_used += 2;
+    }
     CKR(c, launch_cpre(L.d_ghost, L.d_clist, L.nghost, c->m, c->P.ratio[l - 1], c->P.dim, C.q[C.cur],
                        C.q[1 - C.cur], L.cpre_sc, L.d_cpre, c->nsm * 8, c->s));
+    if (te) CKR(c, cudaEventRecord(te, c->s));
     c->st.kernel_launches++;
     return ADJAMR_OK;
 }
@@ -1380,11 +1403,21 @@ adjamr_status ghost_fill(adjamr_ctx *c, int l, int k, bool early, bool stored)
         sc = C.ncell;
         r = c->P.ratio[l - 1];
     }
-    const double *pre_k =
-        (stored && l > 0 && L.d_cpre) ? L.d_cpre + (long long)k * c->m * L.cpre_sc * 3 : nullptr;
-    if (pre_k) sc = L.cpre_sc;
+    const bool stored_ok = stored && l > 0 && L.d_cpre;
+    CpreArgs cp{};
+    const double *pre_k = nullptr;
+    if (stored_ok && k == 0 && fill_makes_pre(c, l)) {
+        // substep 0 interpolates directly and computes the later substeps' values
+        cp.list = L.d_clist;
+        cp.pre = L.d_cpre;
+        cp.sc = L.cpre_sc;
+        cp.r = r;
+    } else if (stored_ok) {
+        pre_k = L.d_cpre + (long long)k * c->m * L.cpre_sc * 3;
+        sc = L.cpre_sc;
+    }
     CKR(c, launch_ghost_fill(c->P.dim, c->m, L.d_ghost, L.nghost, L.q[L.cur], L.ncell, qo, qn, sc, k, r, c->s,
-                             early && l > 0 && k > 0, pre_k));
+                             early && l > 0 && k > 0, pre_k, cp, c->nsm * 2));
     c->st.kernel_launches++;
     return ADJAMR_OK;
 }

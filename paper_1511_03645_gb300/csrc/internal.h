@@ -206,9 +206,20 @@ bool step_kernel_shape(int dim, int tx, int ty, int *kx, int *ky);
 // coarser level's states are final (see k_ghost_fill).  pre_k != nullptr: the
 // kind-1 ghost cells take the precomputed coarse stencil values of substep k
 // (k_cpre) instead of interpolating from qc_old / qc_new.
+// cp.list != nullptr: cp_blocks extra CTAs also compute the stored stencil
+// values of substeps 1 .. cp.r - 1 into cp.pre (as launch_cpre; the fill
+// itself then interpolates directly, pre_k = nullptr)
+struct CpreArgs {
+    const unsigned long long *list;
+    double *pre;
+    long long sc;
+    int r;
+    SubstepTimes tt;  // filled by the launcher
+};
 cudaError_t launch_ghost_fill(int dim, int m, const GhostDesc *g, long long n, double *qf, long long sf,
                               const double *qc_old, const double *qc_new, long long sc, int k, int r,
-                              cudaStream_t s, bool early = false, const double *pre_k = nullptr);
+                              cudaStream_t s, bool early = false, const double *pre_k = nullptr,
+                              CpreArgs cp = CpreArgs{}, int cp_blocks = 0);
 // coarse stencil values (q0, sx, sy) of every listed coarse cell, field and
 // substep s < r: pre[((s * m + f) * sc + src) * 3 + {0, 1, 2}]
 cudaError_t launch_cpre(const GhostDesc *g, const unsigned long long *list, long long nmax, int m, int r, int dim,

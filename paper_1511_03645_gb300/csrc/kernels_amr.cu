@@ -38,10 +38,33 @@ __device__ __forceinline__ double fill_value(const GhostDesc &g, const double *q
     return pre_k ? ghost_value(g, qf, sf, pre_k, sc, f, dim) : ghost_value_direct(g, qf, sf, qo, qn_, sc, f, k, th, dim);
 }
 
+// cp.list != nullptr (substep 0): the CTAs past the fill's also compute the
+// coarse stencil values of substeps 1 .. r - 1 (k_cpre's work) for the later
+// substeps' fills
 __global__ void k_ghost_fill(int dim, int m, const GhostDesc *__restrict__ gd, long long n, double *qf, long long sf,
                              const double *__restrict__ qo, const double *__restrict__ qn_, long long sc, int k,
-                             double th, int early, const double *__restrict__ pre_k)
+                             double th, int early, const double *__restrict__ pre_k, CpreArgs cp)
 {
+    const unsigned fill_blocks = (unsigned)((n * m + kT - 1) / kT);
+    if (cp.list && blockIdx.x >= fill_blocks) {
+        pdl_wait();
+        pdl_launch_dependents();
+        const long long per = (long long)(cp.r - 1) * m;
+        const long long total = (long long)cp.list[0] * per;
+        const long long stride = (long long)(gridDim.x - fill_blocks) * blockDim.x;
+        for (long long t = (long long)(blockIdx.x - fill_blocks) * blockDim.x + threadIdx.x; t < total; t += stride) {
+            const long long e = t / per;
+            const int rest = (int)(t - e * per), s = 1 + rest / m, f = rest - (s - 1) * m;
+            const GhostDesc g = gd[cp.list[1 + e]];
+            double v[3];
+            coarse_stencil(g, qo, qn_, sc, f, s, cp.tt.th[s], dim, v);
+            double *p = cp.pre + (((long long)s * m + f) * cp.sc + g.src) * 3;
+            p[0] = v[0];
+            p[1] = v[1];
+            p[2] = v[2];
+        }
+        return;
+    }
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = t < n * m;
     const long long gi = valid ? t / m : 0;
@@ -902,12 +925,18 @@ inline unsigned nblk_of(long long n) { return nblk(n); }
 
 cudaError_t launch_ghost_fill(int dim, int m, const GhostDesc *g, long long n, double *qf, long long sf,
                               const double *qc_old, const double *qc_new, long long sc, int k, int r, cudaStream_t s,
-                              bool early, const double *pre_k)
+                              bool early, const double *pre_k, CpreArgs cp, int cp_blocks)
 {
     if (n <= 0) return cudaSuccess;
     const double th = (double)k / (double)r;  // same division as the oracle's, on the host
-    return launch_pdl(k_ghost_fill, dim3(nblk(n * m)), dim3(kT), 0, s, dim, m, g, n, qf, sf, qc_old, qc_new, sc, k, th,
-                      early && pdl_enabled() ? 1 : 0, pre_k);
+    unsigned grid = nblk(n * m);
+    if (cp.list) {
+        if (cp.r < 2 || cp.r > kMaxSubsteps || cp_blocks < 1) return cudaErrorInvalidValue;
+        for (int j = 0; j < cp.r; j++) cp.tt.th[j] = (double)j / (double)cp.r;  // as the oracle's, on the host
+        grid += (unsigned)cp_blocks;
+    }
+    return launch_pdl(k_ghost_fill, dim3(grid), dim3(kT), 0, s, dim, m, g, n, qf, sf, qc_old, qc_new, sc, k, th,
+                      early && pdl_enabled() ? 1 : 0, pre_k, cp);
 }
 
 cudaError_t launch_cpre(const GhostDesc *g, const unsigned long long *list, long long nmax, int m, int r, int dim,
