@@ -112,6 +112,7 @@ struct adjamr_ctx {
     // them after the work already queued on s
     cudaStream_t s_flag = nullptr;
     cudaEvent_t ev_flag = nullptr;
+    bool on_side = false;  // s is the side stream (inside the overlapped flags)
     std::string err;
     bool have_medium = false;
     MediumDev mh[ADJAMR_MAX_LEVELS];
@@ -199,7 +200,9 @@ cudaError_t cget(adjamr_ctx *c, T **p, size_t n)
     if (n == 0) return cudaSuccess;
     const size_t bytes = (n * sizeof(T) + 255) / 256 * 256;
     int best = -1;
-    for (int k = 0; k < (int)c->blk_free.size(); k++) {
+    // (a cached block was released in the order of the main stream: work on
+    // the side stream takes fresh stream-ordered memory instead)
+    for (int k = 0; k < (int)c->blk_free.size() && !c->on_side; k++) {
         const size_t b = c->blk_free[k].first;
         if (b >= bytes && b <= 2 * bytes + 65536 && (best < 0 || b < c->blk_free[best].first)) best = k;
     }
@@ -237,7 +240,7 @@ void cput(adjamr_ctx *c, T *&p)
         c->blk_free_bytes -= c->blk_free.front().first;
         c->blk_free.erase(c->blk_free.begin());
         c->blk_size.erase(old);
-        cudaFreeAsync(old, c->s);
+        cudaFreeAsync(old, c->on_side ? c->s_flag : c->s);  // in the main stream's order
     }
 }
 
@@ -1016,7 +1019,9 @@ adjamr_status regrid_body(adjamr_ctx *c, int base, int init, bool side_flags)
             // on the side stream, after the work queued before ev_flag
             CKR(c, cudaStreamWaitEvent(c->s_flag, c->ev_flag, 0));
             std::swap(c->s, c->s_flag);
+            c->on_side = true;
             const adjamr_status fs = regrid_flags(c, lev, &nf, bb);
+            c->on_side = false;
             std::swap(c->s, c->s_flag);
             TRY(fs);
             // later work on s that reuses the flag buffers comes after them
