@@ -115,7 +115,7 @@ typedef struct adjamr_params {
     adjamr_qinit_fn qinit;       /* may be NULL (state starts at zero) */
     void *qinit_user;
     void *stream;                /* cudaStream_t or NULL */
-    int tile_x, tile_y;          /* step-kernel tile size (0 = default 32 x 8; see adjamr_set_level_kernel) */
+    int tile_x, tile_y;          /* step-kernel tile size (0 = default 16 x 12; see adjamr_set_level_kernel) */
     int launch_mode;             /* ADJAMR_LAUNCH_* */
 } adjamr_params;
 

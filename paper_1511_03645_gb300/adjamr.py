@@ -466,12 +466,13 @@ class Hierarchy:
 
 
 def solve_adjoint(wl, *, nsnap=None, n=None, phi=None, medium_dense=None, stream=None, ctx: Hierarchy = None,
-                  tf=None) -> Adjoint:
-    """Adjoint snapshots computed on the GPU (device-resident handle)."""
+                  tf=None, tile=(0, 0)) -> Adjoint:
+    """Adjoint snapshots computed on the GPU (device-resident handle);
+    tile: the step-kernel tile of the adjoint grid (0: default)."""
     L = load()
     nn = wl.adj_n if n is None else n
     S = wl.nsnap if nsnap is None else nsnap
-    p = make_params(wl, eqn=wl.adj_eqn, nlevels=1, n0=nn, stream=stream, tf=tf)
+    p = make_params(wl, eqn=wl.adj_eqn, nlevels=1, n0=nn, stream=stream, tf=tf, tile=tile)
     if phi is None:
         import copy
         w2 = copy.copy(wl)
