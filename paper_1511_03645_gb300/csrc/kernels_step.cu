@@ -128,10 +128,11 @@ template <int EQN>
 __device__ __forceinline__ void trans_split(const Edge &e, double d0, double *am, double *ap)
 {
     if constexpr (EQN == 0) {
-        double a1 = (-d0) * e.izs;
+        // a1 = (-d0) izs = -a2 exactly (rounding is sign-symmetric), so
+        // -(Zl a1) = Zl a2 and s1 a1 = -(s1 a2): one product fewer, same bits
         double a2 = d0 * e.izs;
-        am[0] = e.s1 * (-(e.Zl * a1));
-        am[1] = e.s1 * a1;
+        am[0] = e.s1 * (e.Zl * a2);
+        am[1] = -(e.s1 * a2);
         ap[0] = e.s2 * (e.Zr * a2);
         ap[1] = e.s2 * a2;
     } else if constexpr (EQN == 1) {
