@@ -272,6 +272,51 @@ def test_per_level_kernels_compute_the_same_bits(A):
     h.close()
 
 
+def test_dry_adjoint_cells_match_oracle(A):
+    """Adjoint cells marked dry (Sec. 5.3: no flag where the adjoint grid is
+    dry) over the part of the grid where this run flags (x >= 1.5): flags,
+    layouts and states of the AMR run agree with the oracle's, no flag lies
+    in a dry adjoint cell, and without the mask some would."""
+    wl = W.config2(seed=3, n0=32, ratios=(2, 4), tf=1.5, adj_n=64, nsnap=20, ts=0.0, tol=1e-6,
+                   min_patch=8, max_patch=32)
+    snaps = O.adjoint_solve(wl)
+    wet = np.ones((64, 64), np.uint8)
+    wet[:, 44:] = 0   # adjoint columns with x >= 1.5
+
+    def flagged_x(h, lev, fl):
+        dx = (wl.hi[0] - wl.lo[0]) / (wl.n0[0] * int(np.prod(wl.ratios[:lev])))
+        xs, off = [], 0
+        for ilo, jlo, nx, ny in h.patches(lev):
+            ff = fl[off:off + nx * ny].reshape(ny, nx)
+            off += nx * ny
+            xs.extend((wl.lo[0] + (ilo + np.nonzero(ff)[1] + 0.5) * dx).tolist())
+        return np.array(xs)
+
+    plain = O.OracleHierarchy(wl)
+    plain.set_adjoint(snaps)
+    plain.regrid(0, init=True)
+    assert (flagged_x(plain, 0, plain.flag(0, wl.tol)[0]) >= 1.5).any()
+    o = O.OracleHierarchy(wl)
+    o.set_adjoint(snaps, wet=wet)
+    o.regrid(0, init=True)
+    g = A.Hierarchy(wl)
+    g.load_adjoint(snaps, wet=wet)
+    g.regrid(0, init=True)
+    _compare_all(o, g, wl.nlevels)
+    n = o.nsteps_total()
+    for c in range(3):
+        k = n // 3 if c < 2 else n - 2 * (n // 3)
+        o.advance(k)
+        g.advance(k)
+        _compare_all(o, g, wl.nlevels)
+        for lev in range(wl.nlevels - 1):
+            fo, co = o.flag(lev, wl.tol)
+            fg, cg = g.flag(lev, wl.tol)
+            assert co == cg and np.array_equal(fo, fg)
+            assert not (flagged_x(g, lev, fg) >= 1.5).any()
+    assert abs(g.functional() - o.functional()) <= RTOL * max(abs(o.functional()), 1e-300)
+
+
 def test_substep_waits_give_up_and_the_context_stays_usable(A):
     """A substep launch whose tiles wait on a counter nothing advances: the
     bounded waits give up after about a second, the call reports ETIMEOUT,
