@@ -126,13 +126,14 @@ struct adjamr_ctx {
     std::vector<WorkItem> h_sort_tmp;
     std::vector<uint64_t> h_tmp;
     std::vector<int> h_cnt;
-    // pinned staging for descriptor uploads; reused once the event of the
-    // previous copy has completed
-    // pinned staging for descriptor uploads: two slots used in turn, each
-    // reusable once the copy recorded by its event has completed
-    char *h_stage[2] = {nullptr, nullptr};
-    size_t h_stage_bytes[2] = {0, 0};
-    cudaEvent_t stage_ev[2] = {nullptr, nullptr};
+    // pinned staging ring of the descriptor uploads: slots used in turn, each
+    // reused once the copy recorded by its event has completed; 4 slots cover
+    // the uploads of one regrid of two levels, so the host does not wait for
+    // the stream in the middle of a regrid
+    static constexpr int kStageSlots = 4;
+    char *h_stage[kStageSlots] = {};
+    size_t h_stage_bytes[kStageSlots] = {};
+    cudaEvent_t stage_ev[kStageSlots] = {};
     int stage_slot = 0;
     // device blocks released by regrids, reused by later ones (the stream
     // orders every use, as with cudaFreeAsync): sizes of every block handed
@@ -468,7 +469,7 @@ cudaError_t upload_packed(adjamr_ctx *c, const std::vector<std::pair<const void 
     *dev = nullptr;
     if (total == 0) return cudaSuccess;
     const int sl = c->stage_slot;
-    c->stage_slot = 1 - sl;
+    c->stage_slot = (sl + 1) % adjamr_ctx::kStageSlots;
     cudaError_t e;
     if (c->stage_ev[sl]) {
         e = cudaEventSynchronize(c->stage_ev[sl]);  // the slot's previous copy is done
@@ -2629,7 +2630,7 @@ void adjamr_destroy(adjamr_ctx *ctx)
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     for (cudaEvent_t e : ctx->tev) cudaEventDestroy(e);
-    for (int k = 0; k < 2; k++) {
+    for (int k = 0; k < adjamr_ctx::kStageSlots; k++) {
         if (ctx->stage_ev[k]) cudaEventDestroy(ctx->stage_ev[k]);
         if (ctx->h_stage[k]) cudaFreeHost(ctx->h_stage[k]);
     }
