@@ -98,7 +98,7 @@ typedef struct adjamr_params {
     double lo[2], hi[2];         /* domain [lo, hi] (y ignored in 1D) */
     int n0[2];                   /* level-0 cells per direction */
     int nlevels;                 /* 1 .. ADJAMR_MAX_LEVELS */
-    int ratio[ADJAMR_MAX_LEVELS];/* ratio[l]: refinement from level l to l+1, space and time */
+    int ratio[ADJAMR_MAX_LEVELS];/* ratio[l]: refinement from level l to l+1, space and time (2..16) */
     int bc[4];                   /* x-lo, x-hi, y-lo, y-hi */
     double cfl;                  /* desired Courant number: sets dt_0 */
     double cfl_max;              /* ADJAMR_ECFL if exceeded */

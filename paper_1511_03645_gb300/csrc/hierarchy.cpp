@@ -1756,7 +1756,7 @@ adjamr_status create_impl(const adjamr_params *p, adjamr_ctx **out)
         p->max_patch < 1 || (p->dt0 <= 0.0 && !(p->cmax > 0.0)) || !(p->tf > p->t0))
         return ADJAMR_EINVAL;
     for (int l = 0; l < p->nlevels - 1; l++)
-        if (p->ratio[l] < 2) return ADJAMR_EINVAL;
+        if (p->ratio[l] < 2 || p->ratio[l] > kMaxSubsteps) return ADJAMR_EINVAL;
     for (int k = 0; k < 4; k++)
         if (p->bc[k] < 0 || p->bc[k] > 2) return ADJAMR_EINVAL;
     if (p->flag_mode < ADJAMR_FLAG_BRACKET_MAX || p->flag_mode > ADJAMR_FLAG_SURFACE) return ADJAMR_EINVAL;

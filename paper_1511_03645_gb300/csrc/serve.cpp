@@ -45,12 +45,17 @@ extern "C" size_t adjamr_estimate_bytes(const adjamr_params *p)
     const int per = 2 * m + adjamr::naux_of(p->eqn) + adjamr::nmed_of(p->eqn);
     long long N = p->n0[0], M = (p->dim == 2) ? p->n0[1] : 1;
     size_t total = 0;
+    long long prev = 0;  // storage cells of the coarser level
     for (int l = 0; l < p->nlevels; l++) {
         // upper bound: every level fully refined, ghost rings included
         long long cells = (N + 4 * (N / 8 + 1)) * (p->dim == 2 ? (M + 4 * (M / 8 + 1)) : 1);
         total += (size_t)cells * per * sizeof(double);
         // descriptors (ghost maps, average-down maps, work-lists), generous
         total += (size_t)cells * 24;
+        // coarse stencil values of the ghost cells (3 per coarse cell, field
+        // and substep), their marks, and the list of coarse cells
+        if (l > 0) total += (size_t)prev * (3 * sizeof(double) * m * p->ratio[l - 1] + sizeof(int)) + (size_t)cells * 8;
+        prev = cells;
         if (l < p->nlevels - 1) {
             N *= p->ratio[l];
             if (p->dim == 2) M *= p->ratio[l];

@@ -50,3 +50,24 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(A, "lib_path", lambda: str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError):
         A.load(build_if_missing=False)
+
+
+def test_parameters_are_validated_before_any_device_call():
+    """Invalid parameters (here refinement ratios outside 2..16) are refused
+    with EINVAL before any CUDA call; the serving byte estimate grows with
+    the ratio."""
+    from paper_1511_03645_gb300 import adjamr as A, workloads as W
+    L = A.load()
+    wl = W.config2(seed=1, n0=16, ratios=(2, 4), tf=0.5, adj_n=32, nsnap=4)
+    out = ctypes.c_void_p()
+    est = {}
+    for r, want in ((1, A.EINVAL), (17, A.EINVAL)):
+        p = A.make_params(wl)
+        p.ratio[1] = r
+        assert L.adjamr_init_grid_hierarchy(ctypes.byref(p), ctypes.byref(out)) == want
+        assert not out.value
+    for r in (2, 4, 16):
+        p = A.make_params(wl)
+        p.ratio[1] = r
+        est[r] = L.adjamr_estimate_bytes(ctypes.byref(p))
+    assert 0 < est[2] < est[4] < est[16]
