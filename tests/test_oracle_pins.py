@@ -221,21 +221,155 @@ def test_conservation_periodic_2d(case):
 
 
 def test_well_balanced_lake_at_rest_bitwise():
-    """Shallow water at rest (eta = mu = gamma = 0) over seamount bathymetry:
-    the f-wave flux difference (d mu, g hbar_edge d eta) is exactly zero, so
-    the state stays bitwise zero (Sec. 3, f-wave formulation)."""
-    rng = np.random.default_rng(3)
+    """Shallow water at rest over seamount bathymetry, with a flat surface
+    that is not sea level (eta = 0.37 everywhere, mu = gamma = 0): the state
+    is eta, the surface, not the depth, so every jump of eta is zero; the
+    f-wave flux difference (d mu, g hbar_edge d eta) of the forward system
+    and (-(g hbar mu), -eta) of the adjoint then cancel exactly at every
+    edge, and the state stays bitwise as it is (Sec. 3, f-wave formulation;
+    Sec. 5.3, the equations written for the surface elevation).  A scheme
+    that carried the depth h + eta, or put the bathymetry gradient into the
+    flux difference, would move this state."""
     N = 20
     hb = W.bathymetry(*np.meshgrid(np.linspace(0, 2e6, N), np.linspace(0, 2e6, N)),
                       mounts=np.array([[2000.0, 3e5, 1e6, 1e6], [1500.0, 2e5, 5e5, 1.5e6]]))[None]
+    assert hb.max() / hb.min() > 3.0
     for eqn in (W.EQ_SW, W.EQ_SW_ADJ):
-        wl = _dense_workload(2, eqn, N, hb, bc=W.BC_WALL, L=2e6)
-        wl.lo, wl.hi = (0.0, 0.0), (2e6, 2e6)
+        for eta in (0.0, 0.37):
+            wl = _dense_workload(2, eqn, N, hb, bc=W.BC_WALL, L=2e6)
+            wl.lo, wl.hi = (0.0, 0.0), (2e6, 2e6)
+            h = O.OracleHierarchy(wl, nlevels=1, with_qinit=False)
+            q0 = np.zeros((3, N, N))
+            q0[0] = eta
+            _scatter_write(h, 0, q0)
+            h.advance(10)
+            assert np.array_equal(h.level_dense(0), q0)
+
+
+def _sw_dalembert(eqn, N, hbar, t, L=8.0e5, beta=20.0):
+    """One-dimensional linearised shallow water of constant depth hbar on
+    [-L/2, L/2] from eta = f(x) = exp(-beta (x/s)^2) (s = L/8, exact cell
+    averages) at rest; returns (dx, computed [2, N], exact [2, N])."""
+    s = L / 8.0
+    fields = np.full((1, 1, N), hbar)
+    wl = _dense_workload(1, eqn, N, fields, bc=W.BC_EXTRAP, L=L, tf=t)
+    h = O.OracleHierarchy(wl, nlevels=1, with_qinit=False)
+    dx = L / N
+    xl = -L / 2 + np.arange(N) * dx
+    avg = lambda a: np.array([_gauss_avg(v / s, (v + dx) / s, beta) for v in a])
+    f0 = avg(xl)
+    _scatter_write(h, 0, np.stack([f0, np.zeros(N)])[:, None, :])
+    h.advance(h.nsteps_total())
+    c = math.sqrt(W.GRAV * hbar)
+    fm, fp = avg(xl - c * t), avg(xl + c * t)
+    eta = 0.5 * (fm + fp)
+    # forward: mu = c (f(x-ct) - f(x+ct))/2; adjoint (eta~_t = g h mu~_x,
+    # mu~_t = eta~_x): mu~ = (f(x+ct) - f(x-ct))/(2c)
+    mu = 0.5 * c * (fm - fp) if eqn == W.EQ_SW else 0.5 * (fp - fm) / c
+    return dx, h.level_dense(0)[:, 0, :], np.stack([eta, mu])
+
+
+@pytest.mark.parametrize("eqn", [W.EQ_SW, W.EQ_SW_ADJ])
+def test_shallow_water_dalembert_speed_and_convergence(eqn):
+    """Constant depth hbar = 2500 m: the linearised system of Sec. 5.3 is the
+    wave equation with speed c = sqrt(g hbar) = 156.6 m/s, so a surface hump
+    at rest splits into two halves travelling at +-c, with momentum
+    +-c eta / 2 (forward) and the adjoint's mu~ = -+eta~/c.  L1 errors
+    against the exact cell averages converge at order >= 1.5 over three grids,
+    and the peaks sit where x = +-c t puts them (a wrong g hbar factor moves
+    them and the error stops converging; a wrong eigenvector sign puts the
+    momentum on the wrong half)."""
+    hbar, t = 2500.0, 1.5e5 / math.sqrt(W.GRAV * 2500.0)
+    errs = []
+    for N in (200, 400, 800):
+        dx, q, ex = _sw_dalembert(eqn, N, hbar, t)
+        scale = np.abs(ex).sum(axis=1)
+        errs.append(float(sum(np.abs(q[k] - ex[k]).sum() / scale[k] for k in range(2))))
+        if N == 800:
+            x = -4.0e5 + (np.arange(N) + 0.5) * dx
+            assert abs(x[np.argmax(q[0] * (x > 0))] - 1.5e5) <= 2 * dx
+            assert abs(x[np.argmax(q[0] * (x < 0))] + 1.5e5) <= 2 * dx
+            assert abs(q[0].max() - 0.5) < 5e-3
+            sgn = 1.0 if eqn == W.EQ_SW else -1.0
+            assert sgn * q[1][x > 0].sum() > 0 and sgn * q[1][x < 0].sum() < 0
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(orders) >= 1.5, (errs, orders)
+
+
+def test_shallow_water_standing_wave_convergence_2d_diagonal():
+    """Two-dimensional constant-depth shallow water on a periodic box with
+    the diagonal standing wave eta = cos(k (x + y)) cos(c |k| t), c =
+    sqrt(g hbar): exercises the transverse terms and the gamma row of the
+    Sec. 5.3 system.  L1 errors converge at order >= 1.5."""
+    hbar, L = 1000.0, 4.0e5
+    c = math.sqrt(W.GRAV * hbar)
+    k = 2.0 * math.pi / L
+    t = 0.4 * L / c
+    errs = []
+    for N in (32, 64, 128):
+        fields = np.full((1, N, N), hbar)
+        wl = _dense_workload(2, W.EQ_SW, N, fields, bc=W.BC_PERIODIC, L=L, tf=t)
         h = O.OracleHierarchy(wl, nlevels=1, with_qinit=False)
-        _scatter_write(h, 0, np.zeros((3, N, N)))
-        h.advance(10)
-        assert np.all(h.level_dense(0) == 0.0)
-    del rng
+        dx = L / N
+        xc = -L / 2 + (np.arange(N) + 0.5) * dx
+        X, Y = np.meshgrid(xc, xc)
+        # cell averages of cos(k(x + y)): cos(k(xc + yc)) * sinc(k dx / 2)^2
+        sinc2 = (math.sin(k * dx / 2) / (k * dx / 2)) ** 2
+        e0 = np.cos(k * (X + Y)) * sinc2
+        _scatter_write(h, 0, np.stack([e0, 0 * e0, 0 * e0]))
+        h.advance(h.nsteps_total())
+        q = h.level_dense(0)
+        ee = e0 * math.cos(c * math.sqrt(2.0) * k * t)
+        errs.append(dx * dx * np.abs(q[0] - ee).sum())
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(orders) >= 1.5, (errs, orders)
+
+
+def test_shallow_water_forward_adjoint_inner_product_time_invariance():
+    """Eq. eq:q_equality for the linearised shallow water of Sec. 5.3 over
+    variable bathymetry (two seamounts on a sloping floor) with walls: the
+    forward state q = (eta, mu, gamma) and the adjoint qhat, which solves
+    qhat_t + (A^T qhat)_x + (B^T qhat)_y = 0 backward from phi (f-wave form
+    of -A^T, Sec. 3), keep int qhat^T q dx constant in time; discretised
+    independently, the identity holds to discretisation error, which shrinks
+    under refinement.  A wrong g hbar factor or eigenvector sign in either
+    system breaks the identity at every resolution."""
+    L = 4.0e5
+    devs = []
+    for N in (24, 48, 96):
+        dx = L / N
+        xc = (np.arange(N) + 0.5) * dx
+        X, Y = np.meshgrid(xc, xc)
+        hb = (1500.0 + 2000.0 * X / L - 900.0 * np.exp(-((X - 0.3 * L) ** 2 + (Y - 0.6 * L) ** 2) / (0.1 * L) ** 2)
+              - 700.0 * np.exp(-((X - 0.7 * L) ** 2 + (Y - 0.3 * L) ** 2) / (0.08 * L) ** 2))[None]
+        cmax = float(np.sqrt(W.GRAV * hb.max()))
+        tf = 0.5 * L / cmax
+        wl = _dense_workload(2, W.EQ_SW, N, hb, bc=W.BC_WALL, L=L, tf=tf, cmax=cmax)
+        wl.lo, wl.hi = (0.0, 0.0), (L, L)
+        wl.adj_n, wl.nsnap = (N, N), 5
+        phi = np.zeros((3, N, N))
+        phi[0] = np.exp(-((X - 0.55 * L) ** 2 + (Y - 0.5 * L) ** 2) / (0.12 * L) ** 2)
+        snaps = O.adjoint_solve(wl, phi=phi, medium_dense=hb)
+        S = snaps.shape[0]
+        dts = tf / (S - 1)
+        nsub = int(math.ceil(dts / (wl.cfl * dx / cmax)))
+        h = O.OracleHierarchy(wl, nlevels=1, dt0=dts / nsub, with_qinit=False)
+        q0 = np.zeros((3, N, N))
+        q0[0] = np.exp(-((X - 0.35 * L) ** 2 + (Y - 0.45 * L) ** 2) / (0.1 * L) ** 2)
+        q0[1] = 30.0 * np.exp(-((X - 0.5 * L) ** 2 + (Y - 0.5 * L) ** 2) / (0.15 * L) ** 2)
+        _scatter_write(h, 0, q0)
+        Js = []
+        for n in range(S):
+            if n:
+                h.advance(nsub)
+            q = h.level_dense(0)
+            Js.append(float(np.sum(snaps[n] * q) * dx * dx))
+        Jf = float(np.sum(phi[0] * q[0]) * dx * dx)
+        assert abs(Js[-1] - Jf) <= 1e-12 * abs(Jf)
+        devs.append(max(abs(j - Jf) for j in Js) / abs(Jf))
+    for a, b in zip(devs, devs[1:]):
+        assert b < 0.75 * a, devs
+    assert devs[-1] < 0.05, devs
 
 
 # --------------------------------------------------------------- symmetry
