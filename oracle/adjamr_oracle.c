@@ -67,6 +67,7 @@ typedef struct {
     int flag_mode;
     orc_qinit_fn qinit;
     void *qinit_user;
+    int reflux;   /* conservation fix-up at coarse-fine interfaces (Sec. 3; Berger-LeVeque) */
 } orc_params;
 
 typedef struct {
@@ -91,9 +92,25 @@ typedef struct {
     int dn[OMAXLEV][2];
 } OMedium;
 
+/* conservation fix-up register of one coarse level l: one entry per
+   (uncovered level-l cell C, side of C that faces a level-(l+1) patch) */
+typedef struct {
+    int pk, i, j, side; /* coarse patch, local cell, side 0..3 = x-left, x-right, y-bottom, y-top */
+    double Lc[2];       /* what the coarse step put into C through that side */
+    double *Lf;         /* [substep][segment][2]: the fine-side values L* */
+} OReg;
+
+typedef struct {
+    int active, n, cap, N, M;
+    OReg *e;
+    int *idx;           /* [4][M][N]: entry of (cell, side), -1 if none */
+    unsigned char *cov; /* [M][N]: cell covered by level l+1 */
+} ORegs;
+
 typedef struct {
     orc_params P;
     int m, nmed, gx, gy;
+    ORegs reg[OMAXLEV];
     OLevel L[OMAXLEV];
     OMedium med;
     long T[OMAXLEV];
@@ -111,6 +128,8 @@ typedef struct {
     double *grec;
     char err[256];
 } OHier;
+
+static void reg_clear(ORegs *R);
 
 /* ------------------------------------------------------------------ */
 /* storage helpers                                                     */
@@ -395,7 +414,7 @@ static void limit_edge(int eqn, double dtdx, OEdgeRes *r, const OEdgeRes *rm, co
 /* sx = nx + 4 and sy; qout: interior only, field-major [f][j][i].     */
 /* ------------------------------------------------------------------ */
 static double step_patch(int dim, int eqn, int nx, int ny, const double *q, const double *med, double dt,
-                         double dx, double dy, double *qout)
+                         double dx, double dy, double *qout, double *side)
 {
     const int gx = 2, gy = (dim == 2) ? 2 : 0;
     const int sx = nx + 2 * gx, sy = ny + 2 * gy;
@@ -430,6 +449,11 @@ static double step_patch(int dim, int eqn, int nx, int ny, const double *q, cons
             double A1 = (L->ap[1] + R->am[1]) + (R->Fn[1] - L->Fn[1]);
             qout[i] = Q(0, i, 0) - dtdx * A0;
             qout[(long)nx + i] = fma(-dtdx, A1, Q(1, i, 0));
+            if (side)
+                for (int k = 0; k < 2; k++) {
+                    side[(long)(0 * 2 + k) * nx + i] = L->ap[k] - L->Fn[k];
+                    side[(long)(1 * 2 + k) * nx + i] = R->am[k] + R->Fn[k];
+                }
         }
         free(X);
         return cfl;
@@ -532,6 +556,15 @@ static double step_patch(int dim, int eqn, int nx, int ny, const double *q, cons
             qout[((long)0 * ny + j) * nx + i] = Q(0, i, j) - (dtdx * Ax[0] + dtdy * By[0]);
             qout[((long)1 * ny + j) * nx + i] = fma(-dtdx, Ax[1], Q(1, i, j));
             qout[((long)2 * ny + j) * nx + i] = fma(-dtdy, By[1], Q(2, i, j));
+            if (side) {
+                long nc = (long)nx * ny, c = (long)j * nx + i;
+                for (int k = 0; k < 2; k++) {
+                    side[(0 * 2 + k) * nc + c] = L->ap[k] - FF(k, i, j);
+                    side[(1 * 2 + k) * nc + c] = R->am[k] + FF(k, i + 1, j);
+                    side[(2 * 2 + k) * nc + c] = B->ap[k] - GG(k, i, j);
+                    side[(3 * 2 + k) * nc + c] = T->am[k] + GG(k, i, j + 1);
+                }
+            }
         }
     free(X);
     free(Y);
@@ -557,7 +590,7 @@ int orc_step_patch(int dim, int eqn, int nx, int ny, const double *q, const doub
                    double dy, double *qout, double *cfl)
 {
     if (dim == 1) ny = 1;
-    double c = step_patch(dim, eqn, nx, ny, q, med, dt, dx, dy, qout);
+    double c = step_patch(dim, eqn, nx, ny, q, med, dt, dx, dy, qout, NULL);
     if (cfl) *cfl = c;
     return 0;
 }
@@ -684,6 +717,10 @@ void orc_destroy(void *hv)
         for (int k = 0; k < h->L[l].np; k++) free_patch(&h->L[l].p[k]);
         free(h->L[l].p);
         for (int f = 0; f < 2; f++) free(h->med.dense[l][f]);
+        reg_clear(&h->reg[l]);
+        free(h->reg[l].e);
+        free(h->reg[l].idx);
+        free(h->reg[l].cov);
     }
     free(h->snaps);
     free(h->wet);
@@ -882,22 +919,207 @@ static int average_down(OHier *h, int lf)
     return 0;
 }
 
-static double step_level_patches(OHier *h, int l)
+/* ------------------------------------------------------------------ */
+/* conservation fix-up at coarse-fine interfaces (refluxing).           */
+/*                                                                      */
+/* The coarse step updates an uncovered coarse cell C beside a fine     */
+/* patch with what it computes at the shared edge (Lc: the fluctuation */
+/* plus correction flux entering C from that side).  The fine patch     */
+/* meanwhile advances with ghost values interpolated from the coarse    */
+/* level, so what leaves the fine side through the edge is not what C   */
+/* received.  Written as fluxes of a linear conservative system f = Aq: */
+/* the fine cell f beside the edge receives F_fine - f(Q_f) (its side   */
+/* value "fin"), so the flux through the edge seen from the fine side   */
+/* is f(Q_f) -/+ fin; C should have received the time and edge average  */
+/* of that flux less f(Q_C), i.e.                                       */
+/*   L* = (A-dQ + A+dQ)(Riemann problem between C and f) - fin,         */
+/* with C on its own side of the problem and Q_C its value at the start */
+/* of the coarse step (C's other edges telescope with that value).      */
+/* After the fine substeps and the average-down,                        */
+/*   Q_C <- Q_C - (dt/dx)_coarse * (mean(L*) - Lc)                      */
+/* for every such side of C.  For homogeneous acoustics and for the     */
+/* f-wave systems (adjoints, the surface row of shallow water) this     */
+/* makes the composite sums of the conserved fields change only through */
+/* the physical boundary; elsewhere it is the same consistent           */
+/* correction.  Sec. 3 (AMR following Berger and LeVeque).              */
+/* ------------------------------------------------------------------ */
+static int opposite_side(int s) { return s ^ 1; }
+
+static void side_neighbour(int s, int I, int J, int *nI, int *nJ)
+{
+    *nI = I + (s == 0 ? -1 : s == 1 ? 1 : 0);
+    *nJ = J + (s == 2 ? -1 : s == 3 ? 1 : 0);
+}
+
+static void reg_clear(ORegs *R)
+{
+    for (int q = 0; q < R->n; q++) free(R->e[q].Lf);
+    R->n = 0;
+    R->active = 0;
+}
+
+static void reg_begin(OHier *h, int l)
+{
+    ORegs *R = &h->reg[l];
+    reg_clear(R);
+    int N = h->L[l].N, M = h->L[l].M, r = h->P.ratio[l];
+    if (R->N != N || R->M != M) {
+        free(R->idx);
+        free(R->cov);
+        R->idx = xcalloc((size_t)4 * N * M, sizeof(int));
+        R->cov = xcalloc((size_t)N * M, 1);
+        R->N = N;
+        R->M = M;
+    }
+    for (long q = 0; q < 4L * N * M; q++) R->idx[q] = -1;
+    memset(R->cov, 0, (size_t)N * M);
+    const OLevel *F = &h->L[l + 1];
+    for (int k = 0; k < F->np; k++) {
+        const OPatch *p = &F->p[k];
+        int a0 = p->ilo / r, a1 = (p->ilo + p->nx) / r;
+        int b0 = (h->P.dim == 2) ? p->jlo / r : 0, b1 = (h->P.dim == 2) ? (p->jlo + p->ny) / r : 1;
+        for (int b = b0; b < b1; b++)
+            for (int a = a0; a < a1; a++) R->cov[(long)b * N + a] = 1;
+    }
+    R->active = 1;
+}
+
+/* coarse side: every uncovered cell of patch pk with a covered neighbour */
+static void reg_coarse(OHier *h, int l, int pk, const double *side)
+{
+    ORegs *R = &h->reg[l];
+    const OPatch *p = &h->L[l].p[pk];
+    int N = R->N, M = R->M, ns = (h->P.dim == 2) ? 4 : 2;
+    int r = h->P.ratio[l], nseg = (h->P.dim == 2) ? r : 1;
+    long nc = (long)p->nx * p->ny;
+    for (int j = 0; j < p->ny; j++)
+        for (int i = 0; i < p->nx; i++) {
+            int I = p->ilo + i, J = p->jlo + j;
+            if (R->cov[(long)J * N + I]) continue;
+            for (int s = 0; s < ns; s++) {
+                int nI, nJ;
+                side_neighbour(s, I, J, &nI, &nJ);
+                if (nI < 0 || nI >= N || nJ < 0 || nJ >= M) continue;
+                if (!R->cov[(long)nJ * N + nI]) continue;
+                if (R->n == R->cap) {
+                    R->cap = R->cap ? 2 * R->cap : 256;
+                    R->e = realloc(R->e, (size_t)R->cap * sizeof(OReg));
+                }
+                OReg *e = &R->e[R->n];
+                e->pk = pk;
+                e->i = i;
+                e->j = j;
+                e->side = s;
+                for (int k = 0; k < 2; k++) e->Lc[k] = side[(long)(s * 2 + k) * nc + (long)j * p->nx + i];
+                e->Lf = xcalloc((size_t)r * nseg * 2, sizeof(double));
+                R->idx[((long)s * M + J) * N + I] = R->n;
+                R->n++;
+            }
+        }
+}
+
+/* fine side: patch pk of level l (fine) at its current substep; the cells
+   whose neighbour across a side is a coarse-interpolated ghost cell */
+static int reg_fine(OHier *h, int l, int pk, const double *side)
+{
+    int c = l - 1, r = h->P.ratio[c];
+    ORegs *R = &h->reg[c];
+    const OLevel *L = &h->L[l], *C = &h->L[c];
+    const OPatch *p = &L->p[pk];
+    int ns = (h->P.dim == 2) ? 4 : 2, nseg = (h->P.dim == 2) ? r : 1;
+    int sub = level_sub(h, l);
+    long nc = (long)p->nx * p->ny;
+    for (int j = 0; j < p->ny; j++)
+        for (int i = 0; i < p->nx; i++) {
+            if (i > 0 && i < p->nx - 1 && (h->P.dim == 1 || (j > 0 && j < p->ny - 1))) continue;
+            int I = p->ilo + i, J = p->jlo + j;
+            for (int s = 0; s < ns; s++) {
+                int nI, nJ;
+                side_neighbour(s, I, J, &nI, &nJ);
+                int li = nI - p->ilo, lj = nJ - p->jlo;
+                if (li >= 0 && li < p->nx && lj >= 0 && lj < p->ny) continue;    /* inside the patch */
+                if (nI < 0 || nI >= L->N || nJ < 0 || nJ >= L->M) continue;   /* physical boundary */
+                if (find_patch(h, l, nI, nJ) >= 0) continue;                     /* same-level neighbour */
+                int Ci = nI / r, Cj = (h->P.dim == 2) ? nJ / r : 0;
+                int cs = opposite_side(s);
+                int q = R->idx[((long)cs * R->M + Cj) * R->N + Ci];
+                int ck = find_patch(h, c, Ci, Cj);
+                if (q < 0 || ck < 0) {
+                    snprintf(h->err, sizeof h->err, "reflux: no register for coarse cell (%d,%d) side %d", Ci, Cj, cs);
+                    return 1;
+                }
+                const OPatch *cp = &C->p[ck];
+                int n = (s < 2) ? 1 : 2;
+                double QC0 = cp->q[C->cur][qidx(h, cp, 0, Ci - cp->ilo, Cj - cp->jlo)];
+                double QCn = cp->q[C->cur][qidx(h, cp, n, Ci - cp->ilo, Cj - cp->jlo)];
+                double Qf0 = p->q[L->cur][qidx(h, p, 0, i, j)];
+                double Qfn = p->q[L->cur][qidx(h, p, n, i, j)];
+                double mC[2], mf[2];
+                for (int f = 0; f < h->nmed; f++) {
+                    mC[f] = cp->med[qidx(h, cp, f, Ci - cp->ilo, Cj - cp->jlo)];
+                    mf[f] = p->med[qidx(h, p, f, i, j)];
+                }
+                OEdgeRes er;
+                if (s == 0 || s == 2) normal_solve(h->P.eqn, mC, mf, QC0, QCn, Qf0, Qfn, &er);   /* C below/left of f */
+                else normal_solve(h->P.eqn, mf, mC, Qf0, Qfn, QC0, QCn, &er);                  /* C above/right of f */
+                int kseg = (h->P.dim == 1) ? 0 : (s < 2 ? J - Cj * r : I - Ci * r);
+                double *o = R->e[q].Lf + ((long)sub * nseg + kseg) * 2;
+                for (int k = 0; k < 2; k++) {
+                    double tot = er.am[k] + er.ap[k];
+                    o[k] = tot - side[(long)(s * 2 + k) * nc + (long)j * p->nx + i];
+                }
+            }
+        }
+    return 0;
+}
+
+/* apply the fix-up to the new state of coarse level l (after average-down) */
+static void reg_apply(OHier *h, int l)
+{
+    ORegs *R = &h->reg[l];
+    OLevel *L = &h->L[l];
+    int r = h->P.ratio[l], nseg = (h->P.dim == 2) ? r : 1;
+    double w = 1.0 / (double)(r * nseg);
+    double dtdx = L->dt / L->dx, dtdy = (h->P.dim == 2) ? L->dt / L->dy : 0.0;
+    for (int q = 0; q < R->n; q++) {
+        const OReg *e = &R->e[q];
+        OPatch *p = &L->p[e->pk];
+        int n = (e->side < 2) ? 1 : 2;
+        double dtd = (e->side < 2) ? dtdx : dtdy;
+        for (int k = 0; k < 2; k++) {
+            double acc = 0.0;
+            for (int sb = 0; sb < r; sb++)
+                for (int g = 0; g < nseg; g++) acc = acc + e->Lf[((long)sb * nseg + g) * 2 + k];
+            double *v = &p->q[1 - L->cur][qidx(h, p, k == 0 ? 0 : n, e->i, e->j)];
+            *v = *v - dtd * (acc * w - e->Lc[k]);
+        }
+    }
+    reg_clear(R);
+}
+
+static double step_level_patches(OHier *h, int l, int *err)
 {
     OLevel *L = &h->L[l];
     int cur = L->cur;
     double cfl = 0.0;
+    int coarse_reg = h->P.reflux && l < h->P.nlevels - 1 && h->L[l + 1].np > 0;
+    int fine_reg = h->P.reflux && l > 0 && h->reg[l - 1].active;
+    if (coarse_reg) reg_begin(h, l);
     for (int pk = 0; pk < L->np; pk++) {
         OPatch *p = &L->p[pk];
         double *qo = xcalloc((size_t)h->m * p->nx * p->ny, sizeof(double));
-        double c = step_patch(h->P.dim, h->P.eqn, p->nx, p->ny, p->q[cur], p->med, L->dt, L->dx, L->dy, qo);
+        double *side = (coarse_reg || fine_reg) ? xcalloc((size_t)8 * p->nx * p->ny, sizeof(double)) : NULL;
+        double c = step_patch(h->P.dim, h->P.eqn, p->nx, p->ny, p->q[cur], p->med, L->dt, L->dx, L->dy, qo, side);
         cfl = fmax(cfl, c);
         h->cell_updates += (long long)p->nx * p->ny;
+        if (coarse_reg) reg_coarse(h, l, pk, side);
+        if (fine_reg && reg_fine(h, l, pk, side)) *err = 1;
         for (int f = 0; f < h->m; f++)
             for (int j = 0; j < p->ny; j++)
                 for (int i = 0; i < p->nx; i++)
                     p->q[1 - cur][qidx(h, p, f, i, j)] = qo[((long)f * p->ny + j) * p->nx + i];
         free(qo);
+        free(side);
     }
     return cfl;
 }
@@ -1367,7 +1589,9 @@ static int step_level(OHier *h, int l, double *cflmax)
     int sub = 0;
     if (l > 0) sub = (int)(L->nstep - h->L[l - 1].nstep * h->P.ratio[l - 1]);
     if (fill_ghosts(h, l, sub)) return 1;
-    double c = step_level_patches(h, l);
+    int err = 0;
+    double c = step_level_patches(h, l, &err);
+    if (err) return 1;
     *cflmax = fmax(*cflmax, c);
     if (l < h->P.nlevels - 1 && h->L[l + 1].np > 0) {
         int r = h->P.ratio[l];
@@ -1375,6 +1599,7 @@ static int step_level(OHier *h, int l, double *cflmax)
         for (int s = 0; s < r; s++)
             if (step_level(h, l + 1, cflmax)) return 1;
         if (average_down(h, l + 1)) return 1;
+        if (h->reg[l].active) reg_apply(h, l);
     }
     L->cur = 1 - L->cur;
     L->nstep++;
@@ -1635,8 +1860,9 @@ int orc_adjoint_solve(const orc_params *P, int axis, int nl, const double *iface
     for (int s = 0; s < nsnap; s++) {
         if (s > 0)
             for (int q = 0; q < nsub; q++) {
+                int err = 0;
                 if (fill_ghosts(h, 0, 0)) { orc_destroy(h); return 1; }
-                step_level_patches(h, 0);
+                step_level_patches(h, 0, &err);
                 L->cur = 1 - L->cur;
                 L->nstep++;
             }

@@ -38,6 +38,7 @@ class OrcParams(ctypes.Structure):
         ("min_patch", ctypes.c_int), ("max_patch", ctypes.c_int), ("max_patch0", ctypes.c_int),
         ("flag_mode", ctypes.c_int),
         ("qinit", ctypes.c_void_p), ("qinit_user", ctypes.c_void_p),
+        ("reflux", ctypes.c_int),
     ]
 
 
@@ -121,6 +122,7 @@ def params_from_workload(wl, eqn=None, nlevels=None, n0=None, tol=None, dt0=0.0,
     P.regrid_interval, P.buffer, P.cluster_eff = wl.regrid_interval, wl.buffer, wl.cluster_eff
     P.min_patch, P.max_patch, P.max_patch0 = wl.min_patch, wl.max_patch, wl.max_patch0
     P.flag_mode = wl.flag_mode
+    P.reflux = int(getattr(wl, "reflux", 0))
     if qinit is not None:
         P.qinit = ctypes.cast(qinit, ctypes.c_void_p)
     return P

@@ -129,6 +129,7 @@ class Workload:
     max_patch: int = 64
     max_patch0: int = 64
     flag_mode: int = FLAG_BRACKET_MAX
+    reflux: int = 0
     extra: dict = field(default_factory=dict)
 
     @property
