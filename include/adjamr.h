@@ -117,6 +117,13 @@ typedef struct adjamr_params {
     void *stream;                /* cudaStream_t or NULL */
     int tile_x, tile_y;          /* step-kernel tile size (0 = default 16 x 12; see adjamr_set_level_kernel) */
     int launch_mode;             /* ADJAMR_LAUNCH_* */
+    int reflux;                  /* 1: conservation fix-up at coarse-fine interfaces (Sec. 3, AMR after
+                                    Berger and LeVeque): after the fine substeps and the average-down,
+                                    every uncovered coarse cell beside a fine patch is corrected so that
+                                    it receives, through that side, the mean over the substeps and fine
+                                    edges of (A-dQ + A+dQ of the Riemann problem between it and the fine
+                                    cell) minus what the fine cell received there, in place of what the
+                                    coarse step gave it; 0: off (the default) */
 } adjamr_params;
 
 /* Medium (Sec. 5.1/5.2 piecewise-constant layers; Sec. 5.3 bathymetry).
@@ -216,14 +223,22 @@ adjamr_status adjamr_regrid(adjamr_ctx *ctx, int base_level, int init);
 
 /* Advance the hierarchy by nsteps level-0 steps (Berger-Oliger recursion,
  * Sec. 3: coarse step, r fine steps with time-interpolated ghost cells,
- * average down; regrid every regrid_interval steps).  level must be 0.
+ * average down; regrid every regrid_interval steps).  level must be 0 (EINVAL
+ * otherwise): a finer level advances only inside a step of the coarser one,
+ * whose old and new states its ghost cells interpolate between, so every
+ * advance starts at level 0 and recurses below it.
  * Returns ECFL if the Courant number exceeded cfl_max. */
 adjamr_status adjamr_advance_level(adjamr_ctx *ctx, int level, int nsteps);
 
-/* Adjoint flags of the interior cells of `level` at its current time (Sec.
- * 4, Sec. 5.1.2): flags_out[k] in patch order, row-major per patch (may be
- * NULL); *nflag = number flagged.  Synchronises. */
-adjamr_status adjamr_flag_cells(adjamr_ctx *ctx, int level, double tol, unsigned char *flags_out,
+/* Adjoint flags of the interior cells of `level` at its current time t for
+ * the time range of interest [t_s, tf] (Sec. 4, Sec. 5.1.2: flag iff the
+ * maximum of |q^(tau) . q| over tau in [t, min(t + tf - t_s, tf)] exceeds
+ * tol; t_s = tf is a time point of interest): flags_out[k] in patch order,
+ * row-major per patch (may be NULL); *nflag = number flagged.  The standard
+ * flaggers (params.flag_mode DIFFERENCE / SURFACE) ignore t_s.  The regrids
+ * of adjamr_advance_level use params.ts.  EINVAL unless t0 <= t_s <= tf.
+ * Synchronises. */
+adjamr_status adjamr_flag_cells(adjamr_ctx *ctx, int level, double tol, double t_s, unsigned char *flags_out,
                                 long long *nflag);
 
 /* J = sum over the composite grid of weight * q0 * |cell ∩ box| (Sec. 2 Eq.
@@ -363,9 +378,12 @@ void adjamr_batch_destroy(adjamr_batch *b);
  * Allocates nothing: its scratch is a static device array of
  * ADJAMR_NOALLOC_MAX_TERMS doubles (8 MiB) that every GPU loading the
  * library holds until the process exits.  n > ADJAMR_NOALLOC_MAX_TERMS is
- * rejected with ADJAMR_EBUDGET before any work is issued.  The first call on
- * a device looks up the array's device address (cudaGetSymbolAddress) and
- * caches it: make that first call before any stream capture.  All calls share
+ * rejected with ADJAMR_EBUDGET before any work is issued.  Every call whose
+ * stream is not being captured looks up the array's device address on the
+ * current device (cudaGetSymbolAddress), so a device reset in between does
+ * no harm; a call made during a stream capture uses the address found by the
+ * last such call on that device: make the first call on a device before any
+ * stream capture (otherwise ADJAMR_ESTATE, with nothing issued).  All calls share
  * the one array, so calls whose work overlaps on the GPU (different streams,
  * no ordering between them) race and give wrong results; calls ordered on
  * one stream are safe.  Nothing in the array needs clearing: each call writes
@@ -401,11 +419,14 @@ typedef struct adjamr_result {
 } adjamr_result;
 
 /* Projected device bytes of one solve (upper bound: every level fully
- * refined), used for admission. */
+ * refined), used for admission.  0 for parameters no hierarchy accepts
+ * (nlevels outside 1 .. ADJAMR_MAX_LEVELS, a refinement ratio outside
+ * 2 .. 16); adjamr_server_submit refuses those requests with EINVAL. */
 size_t adjamr_estimate_bytes(const adjamr_params *p);
 /* max_slots worker threads on the current device; budget in bytes. */
 adjamr_status adjamr_server_create(size_t budget_bytes, int max_slots, adjamr_server **out);
-/* Queue a request; EBUDGET if it can never fit the budget. */
+/* Queue a request; EBUDGET if it can never fit the budget, EINVAL if its
+ * parameters are refused (adjamr_estimate_bytes gives 0). */
 adjamr_status adjamr_server_submit(adjamr_server *srv, const adjamr_request *rq, long long *ticket);
 /* Non-blocking status of a ticket (res.done = 0 while queued or running). */
 adjamr_status adjamr_server_poll(adjamr_server *srv, long long ticket, adjamr_result *out);

@@ -46,6 +46,7 @@ class Params(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
         ("launch_mode", ctypes.c_int),
+        ("reflux", ctypes.c_int),
     ]
 
 
@@ -139,7 +140,7 @@ def load(build_if_missing: bool = True):
             "adjamr_adjoint_read": [vp, dp, sz],
             "adjamr_regrid": [vp, i, i],
             "adjamr_advance_level": [vp, i, i],
-            "adjamr_flag_cells": [vp, i, d, ucp, P(ll)],
+            "adjamr_flag_cells": [vp, i, d, d, ucp, P(ll)],
             "adjamr_integrate_functional": [vp, P(Target), dp],
             "adjamr_get_patches": [vp, i, P(Patch), i, ip],
             "adjamr_read_level": [vp, i, dp, sz],
@@ -225,6 +226,7 @@ def make_params(wl, *, eqn=None, nlevels=None, n0=None, tol=None, dt0=0.0, qinit
     p.stream = stream
     p.tile_x, p.tile_y = tile
     p.launch_mode = launch_mode
+    p.reflux = int(getattr(wl, "reflux", 0))
     return p
 
 
@@ -437,12 +439,15 @@ class Hierarchy:
             o += sz
         return arr
 
-    def flag(self, level: int, tol: float):
+    def flag(self, level: int, tol: float, ts: float | None = None):
+        """Flags of the level's interior cells for the range of interest
+        [ts, tf] (default: the workload's ts)."""
         b = self.patches(level)
         n = int(np.sum(b[:, 2].astype(np.int64) * b[:, 3])) if len(b) else 0
         out = np.zeros(max(n, 1), dtype=np.uint8)
         cnt = ctypes.c_longlong()
-        _check(load().adjamr_flag_cells(self.h, level, tol, out.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)),
+        t_s = self.wl.ts if ts is None else ts
+        _check(load().adjamr_flag_cells(self.h, level, tol, t_s, out.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)),
                                         ctypes.byref(cnt)), self.h, "flag_cells")
         return out[:n], cnt.value
 

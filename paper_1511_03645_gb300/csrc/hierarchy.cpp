@@ -79,6 +79,18 @@ struct Level {
     // lookup buckets (cells per bucket side)
     int bs = 16, nbx = 0, nby = 0;
     std::vector<std::vector<int>> buckets;
+    // conservation fix-up (refluxing), rebuilt after every regrid: the table
+    // of the level's taking-part cells (coarse-role entries first) and its
+    // arena map, keyed on the host by J * N + I; for the pair (l, l + 1) the
+    // coarse-role records, the fine records of every substep and the fine
+    // cell each fine record belongs to
+    std::unordered_map<long long, int> rkey;
+    int nrcell = 0, nrcoarse = 0;
+    RefluxCell *d_rcells = nullptr;
+    int *d_rmap = nullptr;
+    double *d_lc = nullptr, *d_lf = nullptr;
+    long long nfrec = 0;
+    long long *d_fidx = nullptr;
 };
 
 // Row-major bitmap of a window of an index space: cell (i, j) is bit i & 63 of
@@ -358,6 +370,18 @@ int find_patch(Level &L, int I, int J)
     return -1;
 }
 
+void reflux_release(adjamr_ctx *c, Level &L)
+{
+    cput(c, L.d_rcells);
+    cput(c, L.d_rmap);
+    cput(c, L.d_lc);
+    cput(c, L.d_lf);
+    cput(c, L.d_fidx);
+    L.rkey.clear();
+    L.nrcell = L.nrcoarse = 0;
+    L.nfrec = 0;
+}
+
 void free_level(adjamr_ctx *c, Level &L)
 {
     cudaStream_t s = c->s;
@@ -385,6 +409,7 @@ void free_level(adjamr_ctx *c, Level &L)
     cput(c, L.d_cpre);
     cput(c, L.d_avg);
     cput(c, L.d_owner);
+    reflux_release(c, L);
     L.patches.clear();
     L.h_work.clear();
     L.buckets.clear();
@@ -494,6 +519,40 @@ cudaError_t upload_packed(adjamr_ctx *c, const std::vector<std::pair<const void 
     e = cget(c, dev, total);
     if (e != cudaSuccess) return e;
     e = cudaMemcpyAsync(*dev, c->h_stage[sl], total, cudaMemcpyHostToDevice, c->s);
+    if (e != cudaSuccess) return e;
+    return cudaEventRecord(c->stage_ev[sl], c->s);
+}
+
+// Copy a host vector into an existing device block through the pinned
+// staging ring (no host wait for the stream unless the slot is still busy).
+template <typename T>
+cudaError_t upload_now(adjamr_ctx *c, T *dst, const std::vector<T> &v)
+{
+    const size_t total = v.size() * sizeof(T);
+    if (total == 0) return cudaSuccess;
+    const int sl = c->stage_slot;
+    c->stage_slot = (sl + 1) % adjamr_ctx::kStageSlots;
+    cudaError_t e;
+    if (c->stage_ev[sl]) {
+        e = cudaEventSynchronize(c->stage_ev[sl]);
+        if (e != cudaSuccess) return e;
+    } else {
+        e = cudaEventCreateWithFlags(&c->stage_ev[sl], cudaEventDisableTiming);
+        if (e != cudaSuccess) return e;
+    }
+    if (c->h_stage_bytes[sl] < total) {
+        if (c->h_stage[sl]) cudaFreeHost(c->h_stage[sl]);
+        c->h_stage[sl] = nullptr;
+        const size_t want = std::max(total, (size_t)1 << 20);
+        e = cudaMallocHost((void **)&c->h_stage[sl], want);
+        if (e != cudaSuccess) {
+            c->h_stage_bytes[sl] = 0;
+            return e;
+        }
+        c->h_stage_bytes[sl] = want;
+    }
+    std::memcpy(c->h_stage[sl], v.data(), total);
+    e = cudaMemcpyAsync(dst, c->h_stage[sl], total, cudaMemcpyHostToDevice, c->s);
     if (e != cudaSuccess) return e;
     return cudaEventRecord(c->stage_ev[sl], c->s);
 }
@@ -979,13 +1038,178 @@ double ms_since(std::chrono::steady_clock::time_point t)
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t).count();
 }
 
+adjamr_status build_reflux(adjamr_ctx *c, int base);
+
 adjamr_status regrid_from(adjamr_ctx *c, int base, int init, bool side_flags = false)
 {
     c->st.regrids++;
     auto t0 = std::chrono::steady_clock::now();
     adjamr_status st = regrid_body(c, base, init, side_flags);
+    if (st == ADJAMR_OK) st = build_reflux(c, base);
     c->st.regrid_host_ms += ms_since(t0);
     return st;
+}
+
+// Conservation fix-up tables of levels base .. nlevels - 1 (their layouts
+// or the layouts of the next finer levels changed).  Coarse role of level
+// l: every uncovered cell beside a level-(l + 1) patch, found by walking the
+// ring of cells around each fine patch's footprint; side s of that cell
+// faces the patch and gets record id 4 e + s.  Fine role of level l: every
+// patch-edge cell whose neighbour across side s is inside the domain and in
+// no patch of the level; its coarse cell C (the neighbour divided by r) is a
+// coarse-role entry e_C of level l - 1 with side s ^ 1 facing this patch,
+// and the fine record id is (4 e_C + (s ^ 1)) nseg + (the cell's offset
+// along that side inside C).
+adjamr_status build_reflux(adjamr_ctx *c, int base)
+{
+    const adjamr_params &P = c->P;
+    if (!P.reflux) return ADJAMR_OK;
+    const int nl = P.nlevels, dim = P.dim, ns = dim == 2 ? 4 : 2;
+    for (int l = base; l < nl; l++) reflux_release(c, c->L[l]);
+    std::vector<std::vector<RefluxCell>> ent(nl);
+    auto entry_of = [&](int l, int I, int J) -> int {
+        Level &L = c->L[l];
+        const long long key = (long long)J * L.N + I;
+        auto it = L.rkey.find(key);
+        if (it != L.rkey.end()) return it->second;
+        const int k = find_patch(L, I, J);
+        if (k < 0) return -1;
+        RefluxCell rc;
+        rc.idx = cell_of(c, L.patches[k], I - L.patches[k].ilo, J - L.patches[k].jlo);
+        for (int q = 0; q < 4; q++) rc.c[q] = rc.f[q] = -1;
+        const int e = (int)ent[l].size();
+        ent[l].push_back(rc);
+        L.rkey.emplace(key, e);
+        return e;
+    };
+    for (int l = base; l + 1 < nl; l++) {
+        Level &L = c->L[l], &F = c->L[l + 1];
+        if (L.patches.empty() || F.patches.empty()) continue;
+        const int r = P.ratio[l];
+        auto visit = [&](int I, int J, int side) -> bool {
+            if (I < 0 || I >= L.N || J < 0 || J >= L.M) return true;
+            if (find_patch(F, I * r, J * r) >= 0) return true;  // covered: not an interface
+            const int e = entry_of(l, I, J);
+            if (e < 0) return false;
+            ent[l][e].c[side] = 4 * e + side;
+            return true;
+        };
+        bool ok = true;
+        for (const HPatch &fp : F.patches) {
+            const int a0 = fp.ilo / r, a1 = (fp.ilo + fp.nx) / r - 1;
+            const int b0 = dim == 2 ? fp.jlo / r : 0, b1 = dim == 2 ? (fp.jlo + fp.ny) / r - 1 : 0;
+            for (int J = b0; J <= b1; J++) ok = visit(a0 - 1, J, 1) && visit(a1 + 1, J, 0) && ok;
+            if (dim == 2)
+                for (int I = a0; I <= a1; I++) ok = visit(I, b0 - 1, 3) && visit(I, b1 + 1, 2) && ok;
+        }
+        if (!ok) {
+            c->err = "refluxing: a cell beside a level-" + std::to_string(l + 1) + " patch is not a level-" +
+                     std::to_string(l) + " cell";
+            return ADJAMR_ENEST;
+        }
+        L.nrcoarse = (int)ent[l].size();
+    }
+    for (int l = std::max(base, 1); l < nl; l++) {
+        Level &L = c->L[l], &C = c->L[l - 1];
+        if (L.patches.empty() || C.nrcoarse == 0) continue;
+        const int r = P.ratio[l - 1], nseg = dim == 2 ? r : 1;
+        const long long nfrec = (long long)C.nrcoarse * 4 * nseg;
+        std::vector<long long> fidx((size_t)nfrec, -1);
+        for (const HPatch &p : L.patches)
+            for (int j = 0; j < p.ny; j++)
+                for (int i = 0; i < p.nx; i++) {
+                    if (i > 0 && i < p.nx - 1 && (dim == 1 || (j > 0 && j < p.ny - 1))) continue;
+                    const int I = p.ilo + i, J = p.jlo + j;
+                    for (int sd = 0; sd < ns; sd++) {
+                        const int nI = I + (sd == 0 ? -1 : sd == 1 ? 1 : 0);
+                        const int nJ = J + (sd == 2 ? -1 : sd == 3 ? 1 : 0);
+                        const int li = nI - p.ilo, lj = nJ - p.jlo;
+                        if (li >= 0 && li < p.nx && lj >= 0 && lj < p.ny) continue;
+                        if (nI < 0 || nI >= L.N || nJ < 0 || nJ >= L.M) continue;
+                        if (find_patch(L, nI, nJ) >= 0) continue;
+                        const int Ci = nI / r, Cj = dim == 2 ? nJ / r : 0, cs = sd ^ 1;
+                        auto it = C.rkey.find((long long)Cj * C.N + Ci);
+                        const int ec = it == C.rkey.end() ? -1 : it->second;
+                        if (ec < 0 || ec >= C.nrcoarse) {
+                            c->err = "refluxing: no coarse record beside a level-" + std::to_string(l) + " patch";
+                            return ADJAMR_ENEST;
+                        }
+                        const int seg = dim == 1 ? 0 : (sd < 2 ? J - Cj * r : I - Ci * r);
+                        const long long fr = ((long long)ec * 4 + cs) * nseg + seg;
+                        fidx[(size_t)fr] = cell_of(c, p, i, j);
+                        const int e = entry_of(l, I, J);
+                        ent[l][e].f[sd] = (int)fr;
+                    }
+                }
+        if (C.nfrec != nfrec || !C.d_fidx) {
+            cput(c, C.d_fidx);
+            cput(c, C.d_lf);
+            cput(c, C.d_lc);
+            CKR(c, cget(c, &C.d_fidx, (size_t)nfrec));
+            CKR(c, cget(c, &C.d_lf, (size_t)r * nfrec * 4));
+            CKR(c, cget(c, &C.d_lc, (size_t)C.nrcoarse * 8));
+            C.nfrec = nfrec;
+        }
+        CKR(c, upload_now(c, C.d_fidx, fidx));
+    }
+    for (int l = base; l < nl; l++) {
+        Level &L = c->L[l];
+        L.nrcell = (int)ent[l].size();
+        if (L.nrcell == 0) continue;
+        CKR(c, cget(c, &L.d_rcells, ent[l].size()));
+        CKR(c, upload_now(c, L.d_rcells, ent[l]));
+        CKR(c, cget(c, &L.d_rmap, (size_t)L.ncell));
+        CKR(c, cudaMemsetAsync(L.d_rmap, 0xff, (size_t)L.ncell * sizeof(int), c->s));
+        CKR(c, launch_reflux_map(L.d_rcells, L.nrcell, L.d_rmap, c->s));
+        c->st.kernel_launches++;
+    }
+    return ADJAMR_OK;
+}
+
+// fix-up records of a step of level l at substep `sub` of the coarser step
+RefluxArgs reflux_args(adjamr_ctx *c, int l, int sub)
+{
+    RefluxArgs rx{};
+    Level &L = c->L[l];
+    if (!c->P.reflux || L.nrcell == 0) return rx;
+    rx.rmap = L.d_rmap;
+    rx.cells = L.d_rcells;
+    rx.lc = L.d_lc;
+    if (l > 0) {
+        rx.lf = c->L[l - 1].d_lf;
+        rx.nfrec = c->L[l - 1].nfrec;
+    }
+    rx.sub = sub;
+    return rx;
+}
+
+// the fix-up of level l's coarse-role cells after its finer level's substeps
+// and average-down (Sec. 3, AMR after Berger and LeVeque)
+adjamr_status reflux_apply(adjamr_ctx *c, int l)
+{
+    Level &L = c->L[l], &F = c->L[l + 1];
+    if (!c->P.reflux || L.nrcoarse == 0) return ADJAMR_OK;
+    RefluxApply a{};
+    a.cells = L.d_rcells;
+    a.ncoarse = L.nrcoarse;
+    a.qc_old = L.q[L.cur];
+    a.qc_new = L.q[1 - L.cur];
+    a.medc = L.med;
+    a.sc = L.ncell;
+    a.lc = L.d_lc;
+    a.lf = L.d_lf;
+    a.nfrec = L.nfrec;
+    a.fidx = L.d_fidx;
+    a.medf = F.med;
+    a.sf = F.ncell;
+    a.r = c->P.ratio[l];
+    a.nseg = c->P.dim == 2 ? a.r : 1;
+    a.w = 1.0 / (double)(a.r * a.nseg);
+    a.dtdx = L.dt / L.dx;
+    a.dtdy = c->P.dim == 2 ? L.dt / L.dy : 0.0;
+    CKR(c, launch_reflux_apply(c->P.dim, c->P.eqn, a, c->s));
+    c->st.kernel_launches++;
+    return ADJAMR_OK;
 }
 
 // flags of level lev into d_flagbuf (count, bounding box and bitmap read back)
@@ -1453,7 +1677,8 @@ adjamr_status step_patches(adjamr_ctx *c, int l, int k, GhostMode gm, bool early
 {
     Level &L = c->L[l];
     if (L.patches.empty()) return ADJAMR_OK;
-    const GhostArgs ga = (gm == GHOST_FUSED) ? fused_ghosts(c, l, k) : GhostArgs{};
+    GhostArgs ga = (gm == GHOST_FUSED) ? fused_ghosts(c, l, k) : GhostArgs{};
+    ga.rx = reflux_args(c, l, k);
     TRY(build_work(c, l, c->ltx[l], c->lty[l]));
     cudaEvent_t tb = nullptr, te = nullptr;
     if (c->timing) {
@@ -1533,6 +1758,7 @@ adjamr_status launch_substeps(adjamr_ctx *c, int l, int r, const int *dep_idx, c
             c->done_cap = want;
         }
         GhostArgs ga = fused_ghosts(c, l, 0);
+        ga.rx = reflux_args(c, l, 0);
         SubstepArgs sa{};
         sa.dep_idx = dep_idx;
         sa.dep_cnt = dep_cnt;
@@ -1645,7 +1871,9 @@ adjamr_status step_level(adjamr_ctx *c, int l)
     int sub = 0;
     if (l > 0) sub = (int)(L.nstep - c->L[l - 1].nstep * P.ratio[l - 1]);
     const GhostMode gm = c->lfuse[l] ? GHOST_FUSED : GHOST_FILL;
-    if (regrid && c->s_flag && (P.flag_mode == ADJAMR_FLAG_BRACKET_MAX || P.flag_mode == ADJAMR_FLAG_LINEAR)) {
+    // (with the fix-up the step records for the new finer level: regrid first)
+    if (regrid && c->s_flag && !P.reflux &&
+        (P.flag_mode == ADJAMR_FLAG_BRACKET_MAX || P.flag_mode == ADJAMR_FLAG_LINEAR)) {
         // The adjoint flags of level l read its current interior state, which
         // its step leaves alone (it writes the other buffer): the flags run on
         // the side stream while the step runs, so the host clusters and builds
@@ -1669,6 +1897,7 @@ adjamr_status step_level(adjamr_ctx *c, int l)
         else
             for (int s = 0; s < r; s++) TRY(step_level(c, l + 1));
         TRY(average_down(c, l + 1));
+        TRY(reflux_apply(c, l));
     }
     L.cur = 1 - L.cur;
     L.nstep++;
@@ -1761,6 +1990,7 @@ adjamr_status create_impl(const adjamr_params *p, adjamr_ctx **out)
         if (p->bc[k] < 0 || p->bc[k] > 2) return ADJAMR_EINVAL;
     if (p->flag_mode < ADJAMR_FLAG_BRACKET_MAX || p->flag_mode > ADJAMR_FLAG_SURFACE) return ADJAMR_EINVAL;
     if (p->launch_mode < ADJAMR_LAUNCH_WORKLIST || p->launch_mode > ADJAMR_LAUNCH_SUBSTEPS) return ADJAMR_EINVAL;
+    if (p->reflux != 0 && p->reflux != 1) return ADJAMR_EINVAL;
     adjamr_ctx *c = new (std::nothrow) adjamr_ctx();
     if (!c) return ADJAMR_ENOMEM;
     c->P = *p;
@@ -2296,15 +2526,22 @@ adjamr_status adjamr_advance_level(adjamr_ctx *ctx, int level, int nsteps)
     }
 }
 
-adjamr_status adjamr_flag_cells(adjamr_ctx *ctx, int level, double tol, unsigned char *flags_out, long long *nflag)
+adjamr_status adjamr_flag_cells(adjamr_ctx *ctx, int level, double tol, double t_s, unsigned char *flags_out,
+                                long long *nflag)
 {
     if (!ctx || level < 0 || level >= ctx->P.nlevels) return ADJAMR_EINVAL;
+    if (!(t_s >= ctx->P.t0 && t_s <= ctx->P.tf)) return ADJAMR_EINVAL;
     try {
         Level &L = ctx->L[level];
         unsigned char *d = nullptr;
         CKR(ctx, dalloc(&d, (size_t)std::max<long long>(L.ninterior, 1), ctx->s));
         long long n = 0;
+        // the window of this call starts at t_s; the run's own ts (the
+        // regrids' window) is put back afterwards
+        const double ts_run = ctx->P.ts;
+        ctx->P.ts = t_s;
         adjamr_status st = flag_dense(ctx, level, tol, nullptr, 0, d, &n);
+        ctx->P.ts = ts_run;
         if (st == ADJAMR_OK && flags_out && L.ninterior > 0) {
             CKR(ctx, cudaMemcpyAsync(flags_out, d, (size_t)L.ninterior, cudaMemcpyDeviceToHost, ctx->s));
             CKR(ctx, cudaStreamSynchronize(ctx->s));

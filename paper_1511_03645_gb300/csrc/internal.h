@@ -108,9 +108,37 @@ struct LevelGeom {
     int bc[4];
 };
 
+// Conservation fix-up at coarse-fine interfaces (refluxing).  A cell of a
+// level that takes part has an entry in the level's table: its arena index,
+// for each side s (0 x-low, 1 x-high, 2 y-low, 3 y-high) the coarse-role
+// record c[s] (the cell is an uncovered cell and its neighbour across s is
+// covered by the finer level) and the fine-role record f[s] (the cell is on
+// a patch edge and its neighbour across s is a ghost cell interpolated from
+// the coarser level), -1 where none.
+struct RefluxCell {
+    long long idx;
+    int c[4], f[4];
+};
+
+// What a step launch records for the fix-up (rmap == nullptr: nothing).
+// rmap[arena cell] = entry of the level's table or -1.  A coarse-role record
+// c receives lc[2c + k] = the value side s put into the cell (component 0,
+// then the normal component); a fine-role record f of substep `sub`
+// receives lf[(sub * nfrec + f) * 4 + {0, 1, 2, 3}] = those two values and
+// the cell's state (component 0, normal component) at the start of the step.
+struct RefluxArgs {
+    const int *rmap;
+    const RefluxCell *cells;
+    double *lc, *lf;
+    long long nfrec;
+    int sub;
+};
+
 // Ghost cells computed inside the step kernel while staging a tile: the
 // ghost descriptors of the level and the coarser level's two time levels.
-// gd == nullptr: the ghost ring is read from q (filled beforehand).
+// gd == nullptr: the ghost ring is read from q (filled beforehand).  rx: the
+// fix-up records of the launch (they travel with the ghost arguments, which
+// every step launch carries).
 struct GhostArgs {
     const GhostDesc *gd;
     // coarse stencil values of the level's kind-1 ghost cells (k_cpre) for
@@ -118,7 +146,33 @@ struct GhostArgs {
     const double *pre;
     long long sc, pstride;
     int k;  // fine substep within the coarse step
+    RefluxArgs rx;
 };
+
+// The fix-up of the coarse-role cells of level l after the fine substeps and
+// the average-down: for every side s with c[s] >= 0, the mean over the r
+// substeps and nseg fine edges of L* = (A-dQ + A+dQ)(Riemann problem between
+// the cell, at its old state, and the fine cell) - (what the fine cell
+// received through the edge), and qc_new -= dtd * (mean L* - lc).
+struct RefluxApply {
+    const RefluxCell *cells;
+    int ncoarse;
+    const double *qc_old;
+    double *qc_new;
+    const double *medc;     // primary medium of level l
+    long long sc;
+    const double *lc, *lf;
+    long long nfrec;
+    const long long *fidx;  // [nfrec]: arena index of the fine cell of a fine record
+    const double *medf;     // primary medium of level l + 1
+    long long sf;
+    int r, nseg;
+    double w;               // 1 / (r * nseg)
+    double dtdx, dtdy;
+};
+cudaError_t launch_reflux_apply(int dim, int eqn, const RefluxApply &a, cudaStream_t s);
+// rmap[cells[e].idx] = e for every entry (rmap set to -1 beforehand)
+cudaError_t launch_reflux_map(const RefluxCell *cells, int n, int *rmap, cudaStream_t s);
 
 // Tile schedule of a step launch.  ctr == nullptr: CTA b takes tiles b,
 // b + grid, ...  Otherwise every CTA takes the next tile from the counter

@@ -508,6 +508,44 @@ __device__ __forceinline__ void step2d_tile(const double *__restrict__ q, double
             qn[g] = p0 - (dtdx * A0 + dtdy * B0);
             qn[stride + g] = fma(-dtdx, A1, u0);        // u sees the x-edges only
             qn[2 * stride + g] = fma(-dtdy, B1, v0);    // v sees the y-edges only
+            if (ga.rx.rmap) {
+                const int e = ga.rx.rmap[g];
+                if (e >= 0) {
+                    // what each side puts into the cell: the fluctuation
+                    // entering through it with the full (transverse-
+                    // corrected) flux of that edge
+                    const RefluxCell rc = ga.rx.cells[e];
+#pragma unroll
+                    for (int sd = 0; sd < 4; sd++) {
+                        if (rc.c[sd] < 0 && rc.f[sd] < 0) continue;
+                        double a, b;
+                        if (sd == 0) {
+                            a = XF[2 * XES + oL] - FF[fL];
+                            b = XF[3 * XES + oL] - FF[FFS + fL];
+                        } else if (sd == 1) {
+                            a = XF[oR] + FF[fR];
+                            b = XF[XES + oR] + FF[FFS + fR];
+                        } else if (sd == 2) {
+                            a = YF[2 * YES + oB] - GG[gB];
+                            b = YF[3 * YES + oB] - GG[GGS + gB];
+                        } else {
+                            a = YF[oT] + GG[gT];
+                            b = YF[YES + oT] + GG[GGS + gT];
+                        }
+                        if (rc.c[sd] >= 0) {
+                            ga.rx.lc[2 * (long long)rc.c[sd]] = a;
+                            ga.rx.lc[2 * (long long)rc.c[sd] + 1] = b;
+                        }
+                        if (rc.f[sd] >= 0) {
+                            double *o = ga.rx.lf + ((long long)ga.rx.sub * ga.rx.nfrec + rc.f[sd]) * 4;
+                            o[0] = a;
+                            o[1] = b;
+                            o[2] = p0;
+                            o[3] = sd < 2 ? u0 : v0;
+                        }
+                    }
+                }
+            }
         }
         __syncthreads();
     }
@@ -640,6 +678,7 @@ __global__ void __launch_bounds__(kThreads) k_step2d_sub(double *qa, double *qb,
             } else {
                 GhostArgs g = ga;
                 g.k = ga.k + s;
+                g.rx.sub = ga.rx.sub + s;
                 const WorkItem wi = work[w];
                 step2d_tile<EQN, TX, TY, true>((s & 1) ? qb : qa, (s & 1) ? qa : qb, aux, stride,
                                                patches[wi.patch], wi, g, sm, cfl);
@@ -751,6 +790,28 @@ __global__ void __launch_bounds__(kThreads) k_step1d(const double *__restrict__ 
             long long g = P.base + x0 + c + 2;
             qn[g] = sQ[c + 2] - dtdx * A0;
             qn[stride + g] = fma(-dtdx, A1, sQ[PX + c + 2]);
+            if (ga.rx.rmap) {
+                const int e = ga.rx.rmap[g];
+                if (e >= 0) {
+                    const RefluxCell rc = ga.rx.cells[e];
+                    for (int sd = 0; sd < 2; sd++) {
+                        if (rc.c[sd] < 0 && rc.f[sd] < 0) continue;
+                        const double a = sd == 0 ? XF[2 * XE + oL] - XN[c] : XF[oR] + XN[c + 1];
+                        const double b = sd == 0 ? XF[3 * XE + oL] - XN[XNn + c] : XF[XE + oR] + XN[XNn + c + 1];
+                        if (rc.c[sd] >= 0) {
+                            ga.rx.lc[2 * (long long)rc.c[sd]] = a;
+                            ga.rx.lc[2 * (long long)rc.c[sd] + 1] = b;
+                        }
+                        if (rc.f[sd] >= 0) {
+                            double *o = ga.rx.lf + ((long long)ga.rx.sub * ga.rx.nfrec + rc.f[sd]) * 4;
+                            o[0] = a;
+                            o[1] = b;
+                            o[2] = sQ[c + 2];
+                            o[3] = sQ[PX + c + 2];
+                        }
+                    }
+                }
+            }
         }
         __syncthreads();
     }
@@ -938,7 +999,138 @@ cudaError_t sub_switch(int eqn, int tx, int ty, int nwork, int grid, double *qa,
     }
 }
 
+// ---------------------------------------------------------------- refluxing
+// (A-dQ + A+dQ) of the Riemann problem between a left cell (primary medium
+// ml, state (l0, ln)) and a right cell (mr, (r0, rn)): the edge coefficients
+// from the primary media as the per-cell coefficient fill computes them
+// (c = sqrt(K / rho), Z = rho c, 1 / (Z_l + Z_r); shallow water: the edge
+// depth 0.5 (h_l + h_r), c_e = sqrt(g h_e), 1 / c_e), then the jump or flux
+// difference, the decomposition and the fluctuations of the step kernel.
+template <int EQN>
+__device__ __forceinline__ void riemann_total(const double *ml, const double *mr, double l0, double ln, double r0,
+                                              double rn, double *tot)
+{
+    Edge e;
+    if constexpr (EQN == 0 || EQN == 1) {
+        const double cl = sqrt(ml[1] / ml[0]), cr = sqrt(mr[1] / mr[0]);
+        e.Zl = ml[0] * cl;
+        e.Zr = mr[0] * cr;
+        e.izs = 1.0 / (e.Zl + e.Zr);
+        e.s1 = -cl;
+        e.s2 = cr;
+    } else {
+        const double he = 0.5 * (ml[0] + mr[0]);
+        e.ghe = kGrav * he;
+        e.ce = sqrt(e.ghe);
+        e.ice = 1.0 / e.ce;
+        e.s1 = -e.ce;
+        e.s2 = e.ce;
+    }
+    double d0, dn;
+    if constexpr (EQN == 0) {
+        d0 = r0 - l0;
+        dn = rn - ln;
+    } else if constexpr (EQN == 2) {
+        d0 = rn - ln;
+        dn = e.ghe * (r0 - l0);
+    } else if constexpr (EQN == 1) {
+        const double irl = 1.0 / ml[0], irr = 1.0 / mr[0];
+        const double fl0 = -(irl * ln), fln = -(ml[1] * l0);
+        const double fr0 = -(irr * rn), frn = -(mr[1] * r0);
+        d0 = fr0 - fl0;
+        dn = frn - fln;
+    } else {
+        const double gl = kGrav * ml[0], gr = kGrav * mr[0];
+        const double fl0 = -(gl * ln), fln = -l0;
+        const double fr0 = -(gr * rn), frn = -r0;
+        d0 = fr0 - fl0;
+        dn = frn - fln;
+    }
+    double w1[2], w2[2];
+    decompose<EQN>(e, d0, dn, w1, w2);
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        if constexpr (EQN == 0) tot[k] = e.s1 * w1[k] + e.s2 * w2[k];
+        else tot[k] = w1[k] + w2[k];
+    }
+}
+
+// One thread per coarse-role cell: its sides in the order 0..3, each summing
+// L* over the substeps (outer) and the fine edges along the side (inner).
+template <int EQN, int DIM>
+__global__ void __launch_bounds__(256) k_reflux_apply(RefluxApply a)
+{
+    pdl_wait();
+    pdl_launch_dependents();
+    constexpr int NM = nmed_of(EQN);
+    constexpr int NS = DIM == 2 ? 4 : 2;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < a.ncoarse; e += gridDim.x * blockDim.x) {
+        const RefluxCell rc = a.cells[e];
+        const long long ic = rc.idx;
+        double mC[2] = {0.0, 0.0};
+#pragma unroll
+        for (int f = 0; f < NM; f++) mC[f] = a.medc[f * a.sc + ic];
+        for (int sd = 0; sd < NS; sd++) {
+            if (rc.c[sd] < 0) continue;
+            const int n = sd < 2 ? 1 : 2;
+            const double c0 = a.qc_old[ic], cn = a.qc_old[n * a.sc + ic];
+            double acc0 = 0.0, acc1 = 0.0;
+            for (int sb = 0; sb < a.r; sb++)
+                for (int g = 0; g < a.nseg; g++) {
+                    const long long fr = (long long)rc.c[sd] * a.nseg + g;
+                    const double *rec = a.lf + ((long long)sb * a.nfrec + fr) * 4;
+                    const long long fi = a.fidx[fr];
+                    if (fi < 0) continue;  // (every fine edge of a recorded side has a record)
+                    double mf[2] = {0.0, 0.0};
+#pragma unroll
+                    for (int f = 0; f < NM; f++) mf[f] = a.medf[f * a.sf + fi];
+                    double tot[2];
+                    if (sd == 1 || sd == 3) riemann_total<EQN>(mC, mf, c0, cn, rec[2], rec[3], tot);  // C below/left
+                    else riemann_total<EQN>(mf, mC, rec[2], rec[3], c0, cn, tot);                  // C above/right
+                    acc0 = acc0 + (tot[0] - rec[0]);
+                    acc1 = acc1 + (tot[1] - rec[1]);
+                }
+            const double dtd = sd < 2 ? a.dtdx : a.dtdy;
+            const long long lcr = 2 * (long long)rc.c[sd];
+            a.qc_new[ic] = a.qc_new[ic] - dtd * (acc0 * a.w - a.lc[lcr]);
+            a.qc_new[n * a.sc + ic] = a.qc_new[n * a.sc + ic] - dtd * (acc1 * a.w - a.lc[lcr + 1]);
+        }
+    }
+}
+
+__global__ void k_reflux_map(const RefluxCell *__restrict__ cells, int n, int *rmap)
+{
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) rmap[cells[e].idx] = e;
+}
+
 }  // namespace
+
+cudaError_t launch_reflux_apply(int dim, int eqn, const RefluxApply &a, cudaStream_t s)
+{
+    if (a.ncoarse <= 0) return cudaSuccess;
+    const dim3 grid((a.ncoarse + 255) / 256), block(256);
+    if (dim == 1) {
+        switch (eqn) {
+        case 0: return launch_pdl(k_reflux_apply<0, 1>, grid, block, 0, s, a);
+        case 1: return launch_pdl(k_reflux_apply<1, 1>, grid, block, 0, s, a);
+        default: return cudaErrorInvalidValue;
+        }
+    }
+    switch (eqn) {
+    case 0: return launch_pdl(k_reflux_apply<0, 2>, grid, block, 0, s, a);
+    case 1: return launch_pdl(k_reflux_apply<1, 2>, grid, block, 0, s, a);
+    case 2: return launch_pdl(k_reflux_apply<2, 2>, grid, block, 0, s, a);
+    case 3: return launch_pdl(k_reflux_apply<3, 2>, grid, block, 0, s, a);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_reflux_map(const RefluxCell *cells, int n, int *rmap, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_reflux_map<<<(n + 255) / 256, 256, 0, s>>>(cells, n, rmap);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_step_substeps(int eqn, int tx, int ty, double *qa, double *qb, const double *aux, long long stride,
                                  const PatchDesc *patches, const WorkItem *work, int nwork, int grid,

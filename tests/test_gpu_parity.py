@@ -161,14 +161,19 @@ def _compare_all(o, g, nlev):
 
 @pytest.mark.parametrize("which", ["c1", "c2", "c2_linear", "c2_walls", "c3", "c1_diff", "c2_diff", "c3_surface",
                                    "p521", "p522", "p523", "p523_diff", "c2_sub", "c2_walls_sub",
-                                   "c3_sub", "p523_sub"])
+                                   "c3_sub", "p523_sub",
+                                   "c1_rx", "c2_rx", "c2_walls_rx", "c3_rx", "c3_surface_rx", "p521_rx",
+                                   "p523_diff_rx", "c2_rx_sub", "c3_rx_sub"])
 def test_amr_run_matches_oracle(A, which):
     """Adjoint-guided AMR runs (reduced sizes of the workloads): layouts of
     every level bit-exact after every regrid, states within 1e-12, flags
     bit-exact, J within 1e-12.  The _sub variants run the finest level's
-    substeps as single substep launches."""
+    substeps as single substep launches; the _rx variants add the
+    conservation fix-up at coarse-fine interfaces."""
     sub = which.endswith("_sub")
     which = which[:-4] if sub else which
+    rx = which.endswith("_rx")
+    which = which[:-3] if rx else which
     if which.startswith("p52"):
         # the paper's Sec. 5.2 examples at their own sizes
         wl = W.paper_5_2({"p521": "timepoint_walls", "p522": "range_walls"}.get(which[:4], "range_mixed"))
@@ -195,6 +200,7 @@ def test_amr_run_matches_oracle(A, which):
         if which == "c3_surface":
             wl.flag_mode, wl.tol = W.FLAG_SURFACE, 0.02
         chunks = 4
+    wl.reflux = 1 if rx else 0
     snaps = O.adjoint_solve(wl, medium_dense=None if wl.medium.kind != "dense" else _adj_medium(wl))
     o, g = _amr_pair(A, wl, snaps=snaps)
     if sub:
@@ -224,13 +230,16 @@ def test_amr_run_matches_oracle(A, which):
     assert abs(Jg - Jo) <= RTOL * max(abs(Jo), 1e-300)
 
 
-def test_per_level_kernels_compute_the_same_bits(A):
+@pytest.mark.parametrize("reflux", [0, 1])
+def test_per_level_kernels_compute_the_same_bits(A, reflux):
     """A different step-kernel tile on each level, with the ghost ring computed
     inside the step kernel or by the separate fill kernel, and with strided,
-    per-patch or dynamically fetched tiles, changes nothing in the results;
-    the per-level statistics add up to the totals."""
+    per-patch or dynamically fetched tiles, changes nothing in the results
+    (with and without the conservation fix-up); the per-level statistics add
+    up to the totals."""
     wl = W.config2(seed=3, n0=32, ratios=(2, 4), tf=2.0, adj_n=64, nsnap=20, ts=0.0, tol=1e-4,
                    min_patch=8, max_patch=32)
+    wl.reflux = reflux
     adj = A.solve_adjoint(wl)
     runs = []
     for cfg in (None, [((8, 8), False, 3), ((16, 16), True, 0), ((64, 8), False, 3)],
@@ -560,3 +569,62 @@ def test_full_size_config3_sampled_step_parity(A):
             checked += 1
         assert flat_before.shape == flat.shape
     assert checked > 0
+
+
+def test_reflux_conserves_on_the_gpu_with_walls(A):
+    """The conservation fix-up on the GPU: homogeneous acoustics with walls on
+    three levels whose patches follow the wave keeps the composite sum of p
+    constant to 1e-13 (as the oracle's pin shows for the same run), and the
+    run without the fix-up does not."""
+    import test_oracle_amr as T
+    drift = {}
+    for reflux in (1, 0):
+        wl = T._reflux_workload("acoustics_homog", reflux)
+        g = A.Hierarchy(wl)
+        g.regrid(0, init=True)
+        g.advance(1)
+        s1 = T._composite_sum(g, wl)
+        q = g.level_dense(0)[0]
+        scale = float(np.abs(q).sum()) * np.prod(wl.level_dx(0))
+        g.advance(g.nsteps_total() - 1)
+        drift[reflux] = abs(T._composite_sum(g, wl) - s1) / scale
+        g.close()
+    assert drift[1] <= 1e-13 and drift[0] >= 1e-6, drift
+
+
+def test_flag_time_range_per_call_and_level0_only_advance(A):
+    """adjamr_flag_cells takes the start t_s of the range of interest per call
+    (Sec. 5.1.2): flags for a t_s other than the run's equal the oracle's
+    flags for a run with that t_s, bit for bit.  adjamr_advance_level starts
+    every advance at level 0 (finer levels advance only inside a coarser
+    step), so any other level is refused with EINVAL, and so is a t_s outside
+    [t0, tf]; neither changes the hierarchy."""
+    import ctypes
+    wl = W.config2(seed=3, n0=32, ratios=(2, 4), tf=2.0, adj_n=64, nsnap=20, ts=0.0, tol=1e-4,
+                   min_patch=8, max_patch=32)
+    snaps = O.adjoint_solve(wl)
+    o, g = _amr_pair(A, wl, snaps=snaps)
+    n = o.nsteps_total()
+    o.advance(n // 3)
+    g.advance(n // 3)
+    for ts in (0.0, 0.7, 1.3, wl.tf):
+        wt = W.config2(seed=3, n0=32, ratios=(2, 4), tf=2.0, adj_n=64, nsnap=20, ts=ts, tol=1e-4,
+                       min_patch=8, max_patch=32)
+        ot = O.OracleHierarchy(wt)
+        ot.set_adjoint(snaps)
+        ot.regrid(0, init=True)
+        ot.advance(n // 3)
+        for lev in range(wl.nlevels - 1):
+            fo, co = ot.flag(lev, wl.tol)
+            fg, cg = g.flag(lev, wl.tol, ts=ts)
+            assert np.array_equal(ot.patches(lev), g.patches(lev))
+            assert co == cg and np.array_equal(fo, fg), (ts, lev)
+    L = A.load()
+    before = [g.read_level(lev) for lev in range(wl.nlevels)]
+    assert L.adjamr_advance_level(g.h, 1, 1) == A.EINVAL
+    cnt = ctypes.c_longlong()
+    assert L.adjamr_flag_cells(g.h, 0, wl.tol, -0.5, None, ctypes.byref(cnt)) == A.EINVAL
+    assert L.adjamr_flag_cells(g.h, 0, wl.tol, wl.tf + 1.0, None, ctypes.byref(cnt)) == A.EINVAL
+    for lev in range(wl.nlevels):
+        assert np.array_equal(before[lev], g.read_level(lev))
+    g.close()
