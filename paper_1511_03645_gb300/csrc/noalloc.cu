@@ -21,20 +21,31 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 double *g_scratch_dev[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device, looked up once
-// per device (the name g_sum_scratch is only a host-side stand-in).
-cudaError_t scratch_address(double **out)
+// Device address of the scratch array on the current device (the name
+// g_sum_scratch is only a host-side stand-in).  Looked up afresh on every
+// call whose stream is not being captured -- after a device reset or a
+// re-created primary context the array has a new address -- and remembered
+// per device for calls made during a stream capture, when the lookup is not
+// made (the first call on a device must therefore come before any capture).
+cudaError_t scratch_address(cudaStream_t s, double **out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        (void)cudaGetLastError();
+        cs = cudaStreamCaptureStatusActive;  // treat an unanswerable query as a capture
+    }
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_dev[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_sum_scratch);
         if (e != cudaSuccess) return e;
         g_scratch_dev[dev] = static_cast<double *>(p);
+    } else if (!g_scratch_dev[dev]) {
+        return cudaErrorStreamCaptureUnsupported;
     }
     *out = g_scratch_dev[dev];
     return cudaSuccess;
@@ -54,9 +65,11 @@ extern "C" adjamr_status adjamr_weighted_sum_noalloc(const double *q, const doub
 {
     if (n > ADJAMR_NOALLOC_MAX_TERMS) return ADJAMR_EBUDGET;
     if (n < 0 || !out || (n > 0 && (!q || !w))) return ADJAMR_EINVAL;
-    double *terms = nullptr;
-    if (scratch_address(&terms) != cudaSuccess) return ADJAMR_ECUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double *terms = nullptr;
+    const cudaError_t ea = scratch_address(s, &terms);
+    if (ea == cudaErrorStreamCaptureUnsupported) return ADJAMR_ESTATE;  // first call on this device under capture
+    if (ea != cudaSuccess) return ADJAMR_ECUDA;
     if (n > 0) {
         const int threads = 256;
         k_weighted_terms<<<(unsigned)((n + threads - 1) / threads), threads, 0, s>>>(q, w, n, weight, terms);

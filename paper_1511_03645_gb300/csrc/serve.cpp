@@ -41,6 +41,8 @@ double now_s(std::chrono::steady_clock::time_point t0)
 extern "C" size_t adjamr_estimate_bytes(const adjamr_params *p)
 {
     if (!p || p->nlevels < 1 || p->nlevels > ADJAMR_MAX_LEVELS) return 0;
+    for (int l = 0; l < p->nlevels - 1; l++)
+        if (p->ratio[l] < 2 || p->ratio[l] > adjamr::kMaxSubsteps) return 0;  // as hierarchy creation refuses them
     const int m = (p->dim == 2) ? 3 : 2;
     const int per = 2 * m + adjamr::naux_of(p->eqn) + adjamr::nmed_of(p->eqn);
     long long N = p->n0[0], M = (p->dim == 2) ? p->n0[1] : 1;
@@ -55,6 +57,8 @@ extern "C" size_t adjamr_estimate_bytes(const adjamr_params *p)
         // coarse stencil values of the ghost cells (3 per coarse cell, field
         // and substep), their marks, and the list of coarse cells
         if (l > 0) total += (size_t)prev * (3 * sizeof(double) * m * p->ratio[l - 1] + sizeof(int)) + (size_t)cells * 8;
+        // conservation fix-up: arena map and records (refluxing runs only)
+        if (p->reflux) total += (size_t)cells * 8;
         prev = cells;
         if (l < p->nlevels - 1) {
             N *= p->ratio[l];
@@ -191,6 +195,10 @@ adjamr_status adjamr_server_submit(adjamr_server *srv, const adjamr_request *rq,
     r->t = rq->target;
     r->bytes = adjamr_estimate_bytes(&rq->params);
     std::memset(&r->res, 0, sizeof r->res);
+    if (r->bytes == 0) {  // parameters the estimate (and the hierarchy) refuse
+        delete r;
+        return ADJAMR_EINVAL;
+    }
     if (r->bytes > srv->budget) {
         delete r;
         return ADJAMR_EBUDGET;

@@ -71,3 +71,15 @@ def test_parameters_are_validated_before_any_device_call():
         p.ratio[1] = r
         est[r] = L.adjamr_estimate_bytes(ctypes.byref(p))
     assert 0 < est[2] < est[4] < est[16]
+    # the serving admission estimate refuses the same ratios (0 bytes; the
+    # server then refuses the request with EINVAL), and the fix-up flag must be 0 or 1
+    for r in (0, 1, 17):
+        p = A.make_params(wl)
+        p.ratio[1] = r
+        assert L.adjamr_estimate_bytes(ctypes.byref(p)) == 0
+    p = A.make_params(wl)
+    p.reflux = 2
+    assert L.adjamr_init_grid_hierarchy(ctypes.byref(p), ctypes.byref(out)) == A.EINVAL
+    assert not out.value
+    p.reflux = 1
+    assert L.adjamr_estimate_bytes(ctypes.byref(p)) > est[4]
