@@ -156,7 +156,7 @@ typedef struct adjamr_stats {
     long long kernel_launches;
     long long regrids;
     double cfl_max_seen;
-    double step_kernel_ms;       /* CUDA-event time of step kernels, if timing enabled */
+    double step_kernel_ms;       /* CUDA-event time of the step kernels alone, if timing enabled */
     long long step_kernel_launches;
     double regrid_host_ms;       /* host wall time inside regrids (includes their synchronisations) */
     double cluster_host_ms;      /* of which: buffering, nesting and Berger-Rigoutsos on the host */
@@ -174,6 +174,10 @@ typedef struct adjamr_stats {
      * dilation and nesting mask, [1] integral images, [2] Berger-Rigoutsos
      * bisection, [3] splitting to the maximum patch size and ordering */
     double cluster_phase_ms[4];
+    /* per level: CUDA-event time of its ghost work outside the step kernels
+     * (the separate ghost fill and the coarse stencil values), if timing
+     * enabled; level_step_ms counts the step kernels alone */
+    double level_ghost_ms[ADJAMR_MAX_LEVELS];
 } adjamr_stats;
 
 typedef struct adjamr_ctx adjamr_ctx;

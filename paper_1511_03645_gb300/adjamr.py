@@ -88,7 +88,8 @@ class Stats(ctypes.Structure):
                 ("level_step_ms", ctypes.c_double * MAXLEV),
                 ("level_step_launches", ctypes.c_longlong * MAXLEV),
                 ("level_cell_updates", ctypes.c_longlong * MAXLEV),
-                ("cluster_phase_ms", ctypes.c_double * 4)]
+                ("cluster_phase_ms", ctypes.c_double * 4),
+                ("level_ghost_ms", ctypes.c_double * MAXLEV)]
 
 
 # every entry point declared in include/adjamr.h
@@ -374,7 +375,8 @@ class Hierarchy:
         s = Stats()
         _check(load().adjamr_get_stats(self.h, ctypes.byref(s)), self.h, "get_stats")
         d = {k: getattr(s, k) for k, _ in Stats._fields_}
-        for k in ("regrid_phase_ms", "level_step_ms", "level_step_launches", "level_cell_updates", "cluster_phase_ms"):
+        for k in ("regrid_phase_ms", "level_step_ms", "level_step_launches", "level_cell_updates", "cluster_phase_ms",
+                  "level_ghost_ms"):
             d[k] = list(getattr(s, k))
         return d
 

@@ -146,8 +146,12 @@ def tune_amr(wl, adj, key: str, stream=None, coarse_steps: int = 40, use_cache: 
         h.close()
         per = []
         for lev in range(wl.nlevels):
+            # step kernels plus the level's separate ghost work: the fused and
+            # the separate ghost ring compare with the same work inside
             per.append({"launches": st1["level_step_launches"][lev] - st0["level_step_launches"][lev],
-                        "ms": st1["level_step_ms"][lev] - st0["level_step_ms"][lev],
+                        "ms": (st1["level_step_ms"][lev] - st0["level_step_ms"][lev]
+                               + st1["level_ghost_ms"][lev] - st0["level_ghost_ms"][lev]),
+                        "step_ms": st1["level_step_ms"][lev] - st0["level_step_ms"][lev],
                         "cells": st1["level_cell_updates"][lev] - st0["level_cell_updates"][lev]})
         results.append({"tile": list(tile), "fuse_ghosts": fuse, "mode": mode, "levels": per})
     best = []

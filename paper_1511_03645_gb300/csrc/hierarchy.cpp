@@ -728,26 +728,37 @@ bool substeps_ok(const adjamr_ctx *c, int l);
 // substep): then coarse_pre does nothing for it.
 bool fill_makes_pre(const adjamr_ctx *c, int l) { return l > 0 && !c->lfuse[l] && !substeps_ok(c, l); }
 
+// Step-kernel timing without host synchronisation: an event pair around a
+// launch, tagged with its level and kind (0: step kernel; 1: ghost work of the
+// level -- its separate ghost fill or coarse stencil values), harvested once
+// the stream has passed them.  Records the first event; returns the second.
+cudaError_t time_begin(adjamr_ctx *c, int l, int kind, cudaEvent_t *end)
+{
+    *end = nullptr;
+    if (!c->timing) return cudaSuccess;
+    while (c->tev.size() < c->tev_used + 2) {
+        cudaEvent_t e;
+        cudaError_t err = cudaEventCreate(&e);
+        if (err != cudaSuccess) return err;
+        c->tev.push_back(e);
+        c->tev_level.push_back(0);
+    }
+    c->tev_level[c->tev_used] = l + kind * ADJAMR_MAX_LEVELS;
+    *end = c->tev[c->tev_used + 1];
+    cudaError_t err = cudaEventRecord(c->tev[c->tev_used], c->s);
+    c->tev_used += 2;
+    return err;
+}
+
 adjamr_status coarse_pre(adjamr_ctx *c, int l)
 {
     Level &L = c->L[l];
     const Level &C = c->L[l - 1];
     if (!L.d_cpre || L.nghost == 0 || fill_makes_pre(c, l)) return ADJAMR_OK;
-    // timed with level l's steps (a fill at substep 0 computes the same values
-    // inside the level's timing otherwise)
+    // timed as level l's ghost work (a fill at substep 0 computes the same
+    // values there otherwise)
     cudaEvent_t te = nullptr;
-    if (c->timing) {
-        while (c->tev.size() < c->tev_used + 2) {
-            cudaEvent_t e;
-            CKR(c, cudaEventCreate(&e));
-            c->tev.push_back(e);
-            c->tev_level.push_back(0);
-        }
-        c->tev_level[c->tev_used] = l;
-        te = c->tev[c->tev_used + 1];
-        CKR(c, cudaEventRecord(c->tev[c->tev_used], c->s));
-        c->tev_used += 2;
-    }
+    CKR(c, time_begin(c, l, 1, &te));
     CKR(c, launch_cpre(L.d_ghost, L.d_clist, L.nghost, c->m, c->P.ratio[l - 1], c->P.dim, C.q[C.cur],
                        C.q[1 - C.cur], L.cpre_sc, L.d_cpre, c->nsm * 8, c->s));
     if (te) CKR(c, cudaEventRecord(te, c->s));
@@ -1680,21 +1691,13 @@ adjamr_status step_patches(adjamr_ctx *c, int l, int k, GhostMode gm, bool early
     GhostArgs ga = (gm == GHOST_FUSED) ? fused_ghosts(c, l, k) : GhostArgs{};
     ga.rx = reflux_args(c, l, k);
     TRY(build_work(c, l, c->ltx[l], c->lty[l]));
-    cudaEvent_t tb = nullptr, te = nullptr;
-    if (c->timing) {
-        while (c->tev.size() < c->tev_used + 2) {
-            cudaEvent_t e;
-            CKR(c, cudaEventCreate(&e));
-            c->tev.push_back(e);
-            c->tev_level.push_back(0);
-        }
-        tb = c->tev[c->tev_used];
-        te = c->tev[c->tev_used + 1];
-        c->tev_level[c->tev_used] = l;
-        c->tev_used += 2;
-        CKR(c, cudaEventRecord(tb, c->s));
+    cudaEvent_t te = nullptr;
+    if (gm == GHOST_FILL) {
+        CKR(c, time_begin(c, l, 1, &te));
+        TRY(ghost_fill(c, l, k, early_ghosts, true));
+        if (te) CKR(c, cudaEventRecord(te, c->s));
     }
-    if (gm == GHOST_FILL) TRY(ghost_fill(c, l, k, early_ghosts, true));
+    CKR(c, time_begin(c, l, 0, &te));
     const double *q = L.q[L.cur];
     double *qn = L.q[1 - L.cur];
     const int mode = c->lmode[l];
@@ -1771,20 +1774,8 @@ adjamr_status launch_substeps(adjamr_ctx *c, int l, int r, const int *dep_idx, c
         const int grid = std::min(nitems, c->lgrid_sub[l]);
         TileSched sc{c->d_wctr, c->wbase};
         c->wbase += (unsigned long long)nitems + (unsigned long long)grid;
-        cudaEvent_t tb = nullptr, te = nullptr;
-        if (c->timing) {
-            while (c->tev.size() < c->tev_used + 2) {
-                cudaEvent_t e;
-                CKR(c, cudaEventCreate(&e));
-                c->tev.push_back(e);
-                c->tev_level.push_back(0);
-            }
-            tb = c->tev[c->tev_used];
-            te = c->tev[c->tev_used + 1];
-            c->tev_level[c->tev_used] = l;
-            c->tev_used += 2;
-            CKR(c, cudaEventRecord(tb, c->s));
-        }
+        cudaEvent_t te = nullptr;
+        CKR(c, time_begin(c, l, 0, &te));
         CKR(c, launch_step_substeps(c->P.eqn, c->lkx[l], c->lky[l], L.q[L.cur], L.q[1 - L.cur], L.aux, L.ncell,
                                     L.d_patches, L.d_work, L.nwork, grid, c->d_cfl, c->s, ga, sc, sa));
         if (c->timing) CKR(c, cudaEventRecord(te, c->s));
@@ -1848,8 +1839,13 @@ void harvest_timing(adjamr_ctx *c)
         if (cudaEventQuery(c->tev[k + 1]) == cudaErrorNotReady) break;
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, c->tev[k], c->tev[k + 1]) == cudaSuccess) {
-            c->st.step_kernel_ms += ms;
-            c->st.level_step_ms[c->tev_level[k]] += ms;
+            const int lev = c->tev_level[k] % ADJAMR_MAX_LEVELS;
+            if (c->tev_level[k] < ADJAMR_MAX_LEVELS) {
+                c->st.step_kernel_ms += ms;
+                c->st.level_step_ms[lev] += ms;
+            } else {
+                c->st.level_ghost_ms[lev] += ms;
+            }
         }
     }
     (void)cudaGetLastError();

@@ -437,25 +437,27 @@ __device__ __forceinline__ void step2d_tile(const double *__restrict__ q, double
                 int er = k / tx, c = k - er * tx;                  // cell (c, ry = er-1)
                 int oL = er * XEX + c + 1, oR = oL + 1;            // x-edges c and c+1
                 int nL = er * XNX + c, nR = nL + 1;
-                for (int kk = 0; kk < 2; kk++) {
-                    double apT = XF[(2 + kk) * XES + oL] - XN[kk * XNS + nL];
-                    double amT = XF[kk * XES + oR] + XN[kk * XNS + nR];
-                    SX[kk * SXS + er * TX + c] = apT + amT;
-                }
+                // component 0 only: the transverse split of this fluctuation
+                // takes (Sx_0, 0) (the y-direction sees no x-velocity jump)
+                const double apT = XF[2 * XES + oL] - XN[nL];
+                const double amT = XF[oR] + XN[nR];
+                SX[er * TX + c] = apT + amT;
             } else {
                 int kk0 = k - tx * (ty + 2);
                 int r = kk0 / (tx + 2), ec = kk0 - r * (tx + 2);  // cell (cx = ec-1, r)
                 int oB = (r + 1) * YEX + ec, oT = oB + YEX;        // y-edges r and r+1
                 int nB = r * YNX + ec, nT = nB + YNX;
-                for (int kk = 0; kk < 2; kk++) {
-                    double bpT = YF[(2 + kk) * YES + oB] - YN[kk * YNS + nB];
-                    double bmT = YF[kk * YES + oT] + YN[kk * YNS + nT];
-                    SY[kk * SYS + r * (TX + 2) + ec] = bpT + bmT;
-                }
+                const double bpT = YF[2 * YES + oB] - YN[nB];
+                const double bmT = YF[oT] + YN[nT];
+                SY[r * (TX + 2) + ec] = bpT + bmT;
             }
         }
         __syncthreads();
         // ---- transverse corrections: full edge fluxes F and G, and CFL ----
+        // (the CFL number max_e (dtd |s|_e) is dtd * max_e |s|_e exactly: a
+        // product by a positive constant is monotone, so the maxima of |s| are
+        // taken on the integer pipe and multiplied once per direction)
+        long long smx = 0, smy = 0;
         for (int k = tid; k < (tx + 1) * ty + tx * (ty + 1); k += kThreads) {
             if (k < (tx + 1) * ty) {
                 int r = k / (tx + 1), ec = k - r * (tx + 1);       // x-edge ex = ec, row r
@@ -470,7 +472,7 @@ __device__ __forceinline__ void step2d_tile(const double *__restrict__ q, double
                 int on = (r + 1) * XNX + ec;
                 for (int kk = 0; kk < 2; kk++)
                     FF[kk * FFS + r * (TX + 1) + ec] = fma(-hy, am[kk] + bp[kk], XN[kk * XNS + on]);
-                cfl = bmax(cfl, dtdx * maxabs(e.s1, e.s2));
+                smx = bmax(smx, maxabs(e.s1, e.s2));
             } else {
                 int kk0 = k - (tx + 1) * ty;
                 int er = kk0 / tx, c = kk0 - er * tx;              // y-edge ey = er, column c
@@ -485,9 +487,11 @@ __device__ __forceinline__ void step2d_tile(const double *__restrict__ q, double
                 int on = er * YNX + c + 1;
                 for (int kk = 0; kk < 2; kk++)
                     GG[kk * GGS + er * TX + c] = fma(-hx, am[kk] + bp[kk], YN[kk * YNS + on]);
-                cfl = bmax(cfl, dtdy * maxabs(e.s1, e.s2));
+                smy = bmax(smy, maxabs(e.s1, e.s2));
             }
         }
+        if (smx > 0) cfl = bmax(cfl, dtdx * __longlong_as_double(smx));
+        if (smy > 0) cfl = bmax(cfl, dtdy * __longlong_as_double(smy));
         __syncthreads();
         // ---- cell update q - (X + Y) ----
         for (int k = tid; k < tx * ty; k += kThreads) {
@@ -768,6 +772,7 @@ __global__ void __launch_bounds__(kThreads) k_step1d(const double *__restrict__ 
             }
         }
         __syncthreads();
+        long long smx = 0;  // max |s| over this thread's edges (see the 2D kernel)
         for (int k = tid; k < tx + 1; k += kThreads) {    // edge ex = k
             int o = k + 1, l = k + 1, r = k + 2;
             Edge e;
@@ -780,8 +785,9 @@ __global__ void __launch_bounds__(kThreads) k_step1d(const double *__restrict__ 
             double cf1 = corr_coef<EQN>(e.s1, dtdx), cf2 = corr_coef<EQN>(e.s2, dtdx);
             XN[k] = half(cf1 * (p1 * w10) + cf2 * (p2 * w20));
             XN[XNn + k] = half(cf1 * (p1 * w1n) + cf2 * (p2 * w2n));
-            cfl = bmax(cfl, dtdx * maxabs(e.s1, e.s2));
+            smx = bmax(smx, maxabs(e.s1, e.s2));
         }
+        if (smx > 0) cfl = bmax(cfl, dtdx * __longlong_as_double(smx));
         __syncthreads();
         for (int c = tid; c < tx; c += kThreads) {
             int oL = c + 1, oR = c + 2;
