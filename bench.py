@@ -33,15 +33,26 @@ import numpy as np  # noqa: E402
 METRIC = "FP64 cell-updates/s (fused batched vs per-patch, same GPU); serve p50/p99 latency"
 UNIT = "cell-updates/s"
 
-# FP64 operations per 2D acoustics cell-update in the canonical operation
-# order, one per IEEE operation (fma, division, min and max count one each;
-# a cell owns one x-edge and one y-edge).  Per edge: jump 2, decomposition 6,
-# fluctuations 4, two MC limiters 20, correction coefficients 4, second-order
-# flux 12, CFL 2, two transverse splits 16 and their accumulation 4 = 70; per
-# cell: entering sums 12, update 18.  2*70 + 30 = 170.  The FP64 pipe issues
-# one such operation per instruction, so the roofline peak is the pipe's
-# instruction rate (the DFMA micro-benchmark's flop rate / 2).
-OPS_PER_CELL_2D = 170
+# FP64 operations per cell-update in the canonical operation order, one per
+# IEEE operation (fma, division, min and max count one each; negation and
+# absolute value are free; a cell owns one x-edge and one y-edge); counted by
+# running that sequence on a counting number type (tests/test_op_count.py).
+#  2D acoustics, per edge: jump 2, decomposition 6, fluctuations 4, two MC
+#   limiters 20, correction coefficients 4, second-order flux 12, CFL 3
+#   (max |s|, product, running max), two transverse splits 16 and their
+#   accumulation 4 = 71; per cell: entering sums 6 (component 0, the one the
+#   transverse splits take), update 18.  2*71 + 24 = 166.
+#  2D linearised shallow water (f-wave): jump 3, decomposition 6, no
+#   fluctuation products, limiters 20, coefficients 2, flux 12, CFL 3,
+#   transverse 16 + 4 = 66 per edge; 2*66 + 24 = 156.
+#  1D acoustics: per edge 2 + 6 + 4 + 20 + 4 + 12 + 3 = 51; update 9; 60.
+# The FP64 pipe issues one such operation per instruction, so the roofline
+# peak is the pipe's instruction rate (the DFMA micro-benchmark's flop rate / 2).
+OPS_PER_CELL = {"acoustics2d": 166, "shallow_water2d": 156, "acoustics1d": 60}
+OPS_PER_CELL_2D = OPS_PER_CELL["acoustics2d"]
+# algorithmic bytes per cell-update: read q (m doubles) and the cell's
+# coefficients (aux), write q
+BYTES_PER_CELL = {"acoustics2d": 24 + 32 + 24, "shallow_water2d": 24 + 48 + 24, "acoustics1d": 16 + 24 + 16}
 # DRAM bytes per cell-update of a finest-level step launch, from an ncu
 # capture of one such launch (the 601st finest-level launch of the config-2
 # solve to t = 2: 53,424 cells, 3.67 MB read, 0 written): 69 B, 1.2x the 56
@@ -161,6 +172,64 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ configs 1 and 3
+def measure_config(A, W, wl, s, peak_ops, cpu_budget, adj_medium=None, label=""):
+    """One more BASELINE configuration measured whole: its adjoint solved on
+    the GPU (untimed), one warm-up and one timed forward solve (CUDA events on
+    the solve's stream, inputs resident), one instrumented solve for the
+    step-kernel roofline, and the CPU oracle on a bounded sample of the same
+    solve (its first coarse steps)."""
+    import torch
+    sp = s.cuda_stream
+    t = time.perf_counter()
+    adj = A.solve_adjoint(wl, stream=sp, medium_dense=adj_medium)
+    torch.cuda.synchronize()
+    adj_s = time.perf_counter() - t
+
+    def run(timing):
+        h = A.Hierarchy(wl, stream=sp)
+        h.set_adjoint(adj)
+        h.set_timing(timing)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s)
+        h.regrid(0, init=True)
+        h.advance(h.nsteps_total())
+        J = h.functional()
+        e1.record(s)
+        e1.synchronize()
+        st = h.stats()
+        h.close()
+        return e0.elapsed_time(e1), st, J
+
+    run(False)
+    ms, st, J = run(False)
+    _, sti, _ = run(True)
+    ops = OPS_PER_CELL[wl.name]
+    nbytes = BYTES_PER_CELL[wl.name]
+    step_s = sti["step_kernel_ms"] * 1e-3
+    achieved = ops * sti["cell_updates"] / step_s / 1e12 if step_s > 0 else None
+    out = {"workload": label, "value": st["cell_updates"] / (ms * 1e-3), "unit": UNIT, "ms_per_solve": ms,
+           "cell_updates": st["cell_updates"], "J": J, "adjoint_solve_s": adj_s,
+           "roofline": {"bound": "alu", "kernel": "k_step1d" if wl.dim == 1 else "k_step2d", "achieved": achieved,
+                        "peak": peak_ops, "unit": "TOP/s (FP64 operations)",
+                        "frac": achieved / peak_ops if achieved else None, "ops_per_cell_update": ops,
+                        "algorithmic_bytes_per_cell_update": nbytes,
+                        "step_kernel_ms": sti["step_kernel_ms"], "step_launches": sti["step_kernel_launches"],
+                        "per_level_tops": [ops * c / (m * 1e-3) / 1e12 if m > 0 else None
+                                           for c, m in zip(sti["level_cell_updates"][:wl.nlevels],
+                                                           sti["level_step_ms"][:wl.nlevels])]}}
+    if cpu_budget > 0:
+        snaps = adj.read()
+        v, desc = oracle_sample(wl, snaps, budget_s=cpu_budget)
+        del snaps
+        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
+                               "sample": desc}
+    adj.release()
+    return out
+
+
 # ------------------------------------------------------------------ ours
 def run_ours(args, rank, world):
     import torch
@@ -232,6 +301,7 @@ def run_ours(args, rank, world):
     lev_ms = [0.0] * wl.nlevels
     lev_launch = [0] * wl.nlevels
     lev_cells = [0] * wl.nlevels
+    lev_ghost = [0.0] * wl.nlevels
     for h in hs:
         with torch.cuda.stream(s):
             flush.zero_()
@@ -269,6 +339,7 @@ def run_ours(args, rank, world):
         lev_ms[lev] = st["level_step_ms"][lev] * args.steps
         lev_launch[lev] = st["level_step_launches"][lev] * args.steps
         lev_cells[lev] = st["level_cell_updates"][lev] * args.steps
+        lev_ghost[lev] = st["level_ghost_ms"][lev] * args.steps
     total_ms = sum(times)
     if dist:
         total_ms, cu_all = aggregate(td, total_ms, cu, "cuda")
@@ -359,9 +430,24 @@ def run_ours(args, rank, world):
 
     flaggers = None
     paper = None
+    configs = None
     if rank == 0:
         flaggers = compare_flaggers(A, W, wl, adj, adj_s, s, tuned)
         paper = paper_table(A, W, s)
+        configs = {}
+        if not args.no_configs:
+            w1 = W.config1()
+            configs["config1"] = measure_config(
+                A, W, w1, s, peak, args.cpu_budget / 3,
+                label="acoustics1d config 1: 200 cells, ratio 4, t_f=20, adjoint 800 x 100 snapshots, tol 1e-3, "
+                      "time range [0, t_f]")
+            w3 = W.config3(seed=0)
+            configs["config3"] = measure_config(
+                A, W, w3, s, peak, args.cpu_budget / 3, adj_medium=W.config3_adjoint_medium(w3),
+                label="shallow_water2d config 3: 2000 km square, coarse 200^2, ratios 4,4,2, t_f=4 h, adjoint "
+                      "1000^2 x 300 snapshots, tol 4e-3, time range [t_f/2, t_f]")
+            for k, v in configs.items():
+                log(f"{k}: {v['value']:.3e} cell-updates/s, frac {v['roofline']['frac']}")
 
     serving = None
     if rank == 0 and args.serve_sample > 0:
@@ -375,7 +461,7 @@ def run_ours(args, rank, world):
     cpu = None
     if not args.no_cpu:
         v, desc = oracle_sample(wl, adj.read(), budget_s=args.cpu_budget)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle", "sample": desc}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -397,11 +483,13 @@ def run_ours(args, rank, world):
                                     "launches_per_step": lev_launch[lev] / args.steps,
                                     "cells_per_launch": lev_cells[lev] / max(lev_launch[lev], 1),
                                     "avg_launch_us": lev_ms[lev] * 1e3 / max(lev_launch[lev], 1),
+                                    "ghost_ms_per_step": lev_ghost[lev] / args.steps,
                                     "tops": (OPS_PER_CELL_2D * lev_cells[lev] / (lev_ms[lev] * 1e-3) / 1e12
                                                if lev_ms[lev] > 0 else None)}
                                    for lev in range(wl.nlevels)]},
         "fp64_peak": {"dfma_tflops": peak_fma / 1e12, "dadd_tflops": peak_add / 1e12},
         "batched": batched,
+        "configs": configs,
         "flaggers": flaggers,
         "paper_sec_5_2": paper,
         "serving": serving,
@@ -417,13 +505,12 @@ def run_ours(args, rank, world):
                                                             [v / args.steps for v in phases])),
                                   "clustering_phases": dict(zip(["dilate_nest", "integral_images", "bisection",
                                                                  "split_sort"], [v / args.steps for v in cphases]))},
-        "autotune_levels_ms": {f"{t['tile'][0]}x{t['tile'][1]}{'' if t['fuse_ghosts'] else '+fill'}"
-                               f"{'+dyn' if t['mode'] == A.LAUNCH_DYNAMIC else ''}"
-                               f"{'+sub' if t['mode'] == A.LAUNCH_SUBSTEPS else ''}":
-                               [round(x["ms"], 3) for x in t["levels"]] for t in tuned["candidates"]},
         "adjoint_solve_s": adj_s,
         "J": Js[0],
     }
+    log("autotune (ms of the timed coarse steps per candidate, by level): " + json.dumps(
+        {f"level{r['level']}": {f"{c['tile'][0]}x{c['tile'][1]}{'' if c['fuse_ghosts'] else '+fill'}": round(c["ms"], 2)
+                                for c in r["candidates"]} for r in tuned["candidates"]}))
     print(json.dumps(line), flush=True)
 
 
@@ -605,9 +692,11 @@ PAPER_TABLE_5_2_4 = {  # Sec. 5.2.4 (a laptop): pressure-flagging; adjoint-flagg
 
 def paper_table(A, W, s, reps=3):
     """The Sec. 5.2 examples at the paper's sizes on this GPU: adjoint solve,
-    adjoint-flagged forward solve (tol 0.02) and pressure-flagged forward solve
-    (undivided differences, tol 0.1), best of `reps` wall times each, and the
-    gauge at (3.5, 0.5) from both forward runs."""
+    adjoint-flagged forward solve (tol 0.02; also with the conservation
+    fix-up) and pressure-flagged forward solve (undivided differences, tol
+    0.1), best of `reps` wall times each; J and the gauge at (3.5, 0.5) of
+    every run against the uniform run on the finest grid (200^2 with the
+    finest time step)."""
     import copy
     import torch
     out = {}
@@ -622,13 +711,30 @@ def paper_table(A, W, s, reps=3):
             torch.cuda.synchronize()
             el = time.perf_counter() - t
             if best_adj is None or el < best_adj[0]:
+                if best_adj is not None:
+                    best_adj[1].release()
                 best_adj = (el, adj)
+            else:
+                adj.release()
         res = {"adjoint_solve_s": best_adj[0]}
+        # reference: every cell refined, i.e. the uniform finest grid
+        h0 = A.Hierarchy(wl, stream=s.cuda_stream)
+        dt0, n0 = h0.time_info()
+        h0.close()
+        rf = int(np.prod(wl.ratios))
+        fine = A.Hierarchy(wl, nlevels=1, n0=wl.level_shape(wl.nlevels - 1), dt0=dt0 / rf, stream=s.cuda_stream)
+        fine.set_gauges([gx], [gy])
+        fine.advance(n0 * rf)
+        J_fine = fine.functional()
+        g_fine = fine.gauges()[rf - 1::rf, 0, 1]
+        fine.close()
+        res["uniform_fine"] = {"J": J_fine, "gauge_peak_abs": float(np.max(np.abs(g_fine)))}
         gauges = {}
-        for name, mode, tol in (("adjoint_flagging", W.FLAG_BRACKET_MAX, wl.tol), ("pressure_flagging",
-                                                                                   W.FLAG_DIFFERENCE, 0.1)):
+        for name, mode, tol, reflux in (("adjoint_flagging", W.FLAG_BRACKET_MAX, wl.tol, 0),
+                                        ("adjoint_flagging_reflux", W.FLAG_BRACKET_MAX, wl.tol, 1),
+                                        ("pressure_flagging", W.FLAG_DIFFERENCE, 0.1, 0)):
             w = copy.copy(wl)
-            w.flag_mode, w.tol = mode, tol
+            w.flag_mode, w.tol, w.reflux = mode, tol, reflux
             best = None
             for _ in range(reps):
                 h = A.Hierarchy(w, stream=s.cuda_stream)
@@ -644,10 +750,14 @@ def paper_table(A, W, s, reps=3):
                 if best is None or el < best[0]:
                     best = (el, h.stats()["cell_updates"], J, h.gauges()[:, 0, 1])
                 h.close()
-            res[name] = {"tol": tol, "forward_s": best[0], "cell_updates": best[1], "J": best[2]}
-            gauges[name] = best[3]
-        res["gauge_max_abs_diff"] = float(np.max(np.abs(gauges["adjoint_flagging"] - gauges["pressure_flagging"])))
-        res["gauge_peak_abs"] = float(np.max(np.abs(gauges["pressure_flagging"])))
+            g = best[3]
+            res[name] = {"tol": tol, "forward_s": best[0], "cell_updates": best[1], "J": best[2],
+                         "J_rel_err_vs_uniform_fine": abs(best[2] - J_fine) / max(abs(J_fine), 1e-300),
+                         "gauge_max_abs_err_vs_uniform_fine": float(np.max(np.abs(g - g_fine))),
+                         "gauge_peak_abs": float(np.max(np.abs(g)))}
+            gauges[name] = g
+        res["gauge_max_abs_diff_adjoint_vs_pressure"] = float(
+            np.max(np.abs(gauges["adjoint_flagging"] - gauges["pressure_flagging"])))
         pp, pf, pa = PAPER_TABLE_5_2_4[v]
         res["paper_laptop_s"] = {"pressure_flagging": pp, "adjoint_flagging_forward": pf, "adjoint_solve": pa}
         best_adj[1].release()
@@ -722,6 +832,7 @@ def main():
     ap.add_argument("--rates", default="0.5,0.8,1.0", help="serve case: offered rates as fractions of saturation")
     ap.add_argument("--slots", type=int, default=16)
     ap.add_argument("--serve-sample", type=int, default=32)
+    ap.add_argument("--no-configs", action="store_true", help="skip the config-1 and config-3 solves")
     args = ap.parse_args()
     if args.case == "batch":
         run_case_batch(args)

@@ -1567,6 +1567,34 @@ static int regrid_from(OHier *h, int l, int init)
     return 0;
 }
 
+/* exported for tests: replace the patches of `level` by the given boxes
+   ([np][4] = ilo, jlo, nx, ny on the level's index space), state zero,
+   medium filled as a regrid fills it (checks of another implementation's
+   ghost cells and coefficients on its own layout) */
+int orc_set_layout(void *hv, int level, int np, const int *boxes)
+{
+    OHier *h = hv;
+    if (level < 0 || level >= h->P.nlevels || np < 0) return 1;
+    OLevel *L = &h->L[level];
+    for (int k = 0; k < L->np; k++) free_patch(&L->p[k]);
+    free(L->p);
+    L->p = xcalloc(np ? np : 1, sizeof(OPatch));
+    L->np = np;
+    L->cur = 0;
+    for (int k = 0; k < np; k++) {
+        OPatch *p = &L->p[k];
+        p->ilo = boxes[4 * k + 0];
+        p->jlo = boxes[4 * k + 1];
+        p->nx = boxes[4 * k + 2];
+        p->ny = boxes[4 * k + 3];
+        if (p->nx < 1 || p->ny < 1 || p->ilo < 0 || p->jlo < 0 || p->ilo + p->nx > L->N || p->jlo + p->ny > L->M)
+            return 1;
+        alloc_patch(h, p);
+        fill_patch_medium(h, level, p);
+    }
+    return 0;
+}
+
 int orc_regrid(void *hv, int level, int init)
 {
     OHier *h = hv;

@@ -93,6 +93,7 @@ def lib():
             L.orc_adjoint_solve.argtypes = [P(OrcParams), i, i, dp, dp, dp, dp, dp, i, dp]
             L.orc_cluster.argtypes = [P(ctypes.c_ubyte), P(ctypes.c_ubyte), i, i, i, i, d, P(ctypes.c_int), i]
             L.orc_set_gauges.argtypes = [vp, i, dp, dp]
+            L.orc_set_layout.argtypes = [vp, i, i, P(ctypes.c_int)]
             L.orc_read_gauges.restype = ctypes.c_long
             L.orc_read_gauges.argtypes = [vp, dp, ctypes.c_long]
             _lib = L
@@ -269,6 +270,13 @@ class OracleHierarchy:
         for (ilo, jlo, nx, ny), q in self.level_patch_arrays(level):
             arr[:, jlo:jlo + ny, ilo:ilo + nx] = q
         return arr
+
+    def set_layout(self, level: int, boxes):
+        """Replace the patches of a level by boxes [n, 4] = (ilo, jlo, nx, ny);
+        state zero, medium filled."""
+        b = np.ascontiguousarray(np.asarray(boxes, dtype=np.int32).reshape(-1, 4))
+        if lib().orc_set_layout(self.h, level, b.shape[0], b.ctypes.data_as(ctypes.POINTER(ctypes.c_int))):
+            raise RuntimeError("orc_set_layout failed")
 
     def fill_ghosts(self, level: int):
         rc = lib().orc_fill_ghosts(self.h, level)

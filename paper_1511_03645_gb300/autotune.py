@@ -110,19 +110,22 @@ def tune_batch(pb, key: str, stream=None, steps: int = 4, use_cache: bool = True
     return out
 
 
-def tune_amr(wl, adj, key: str, stream=None, coarse_steps: int = 40, use_cache: bool = True) -> dict:
+def tune_amr(wl, adj, key: str, stream=None, coarse_steps: int = 60, skip_steps: int = 40,
+             use_cache: bool = True) -> dict:
     """Best step-kernel configuration (tile size, ghost ring fused into the
     step or filled by its own kernel; one work-list launch per level: the
     dynamic tile counter never won, and substep launches save less kernel
     time than their host-side dependency lists cost) of every level of an
     AMR solve.
 
-    Each candidate runs the solve's first coarse steps (regrids included) with
-    the same configuration on every level; the hierarchy evolves
-    bit-identically for every candidate, so the CUDA-event time of each
-    level's ghost fill + step kernels compares directly across candidates and
-    the best one is chosen per level (the coarse levels are too small to fill
-    the GPU with large tiles)."""
+    Each candidate runs part of the solve (after `skip_steps` coarse steps,
+    so that the finest levels have grown) with the candidate on one level and
+    the best configuration found so far on the others, finest level first;
+    the whole run is timed with one pair of CUDA events and no events between
+    launches, which would stop a launch from starting early behind the one
+    before it (the separate ghost fill overlaps the previous step's tail that
+    way).  The hierarchy evolves bit-identically under every candidate, so the
+    times compare directly."""
     import torch
     ck = f"{_gpu_key()}|amr|{key}"
     if use_cache:
@@ -130,39 +133,34 @@ def tune_amr(wl, adj, key: str, stream=None, coarse_steps: int = 40, use_cache: 
         if hit:
             return hit
     s = torch.cuda.Stream() if stream is None else stream
-    results = []
-    for tile, fuse, mode in itertools.product(TILES, (True, False), (A.LAUNCH_WORKLIST,)):
+    cands = list(itertools.product(TILES, (True, False)))
+    best = [((16, 12), False) for _ in range(wl.nlevels)]
+
+    def run(cfg):
         h = A.Hierarchy(wl, stream=s.cuda_stream)
-        h.set_level_kernel(-1, tile, fuse, mode)
+        for lev, (tile, fuse) in enumerate(cfg):
+            h.set_level_kernel(lev, tile, fuse, A.LAUNCH_WORKLIST)
         h.set_adjoint(adj)
-        h.set_timing(True)
         h.regrid(0, init=True)
-        h.advance(2)   # warm-up
+        h.advance(skip_steps)
         torch.cuda.synchronize()
-        st0 = h.stats()
-        h.advance(coarse_steps)
-        torch.cuda.synchronize()
-        st1 = h.stats()
+        ms = _time(s, lambda: h.advance(coarse_steps))
         h.close()
+        return ms
+
+    results = []
+    for lev in reversed(range(wl.nlevels)):
         per = []
-        for lev in range(wl.nlevels):
-            # step kernels plus the level's separate ghost work: the fused and
-            # the separate ghost ring compare with the same work inside
-            per.append({"launches": st1["level_step_launches"][lev] - st0["level_step_launches"][lev],
-                        "ms": (st1["level_step_ms"][lev] - st0["level_step_ms"][lev]
-                               + st1["level_ghost_ms"][lev] - st0["level_ghost_ms"][lev]),
-                        "step_ms": st1["level_step_ms"][lev] - st0["level_step_ms"][lev],
-                        "cells": st1["level_cell_updates"][lev] - st0["level_cell_updates"][lev]})
-        results.append({"tile": list(tile), "fuse_ghosts": fuse, "mode": mode, "levels": per})
-    best = []
-    for lev in range(wl.nlevels):
-        cand = [r for r in results if r["levels"][lev]["launches"] > 0]
-        if not cand:
-            best.append({"tile": list(TILES[0]), "fuse_ghosts": True, "mode": A.LAUNCH_WORKLIST})
-            continue
-        b = min(cand, key=lambda r: r["levels"][lev]["ms"])
-        best.append({"tile": b["tile"], "fuse_ghosts": b["fuse_ghosts"], "mode": b["mode"]})
-    out = {"best_per_level": best, "candidates": results, "coarse_steps": coarse_steps}
+        for tile, fuse in cands:
+            cfg = list(best)
+            cfg[lev] = (tile, fuse)
+            ms = run(cfg)
+            per.append({"tile": list(tile), "fuse_ghosts": fuse, "ms": ms})
+        b = min(per, key=lambda r: r["ms"])
+        best[lev] = (tuple(b["tile"]), b["fuse_ghosts"])
+        results.append({"level": lev, "candidates": per})
+    out = {"best_per_level": [{"tile": list(t), "fuse_ghosts": f, "mode": A.LAUNCH_WORKLIST} for t, f in best],
+           "candidates": results, "coarse_steps": coarse_steps, "skip_steps": skip_steps}
     _store(ck, out)
     return out
 

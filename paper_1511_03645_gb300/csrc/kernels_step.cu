@@ -512,41 +512,54 @@ __device__ __forceinline__ void step2d_tile(const double *__restrict__ q, double
             qn[g] = p0 - (dtdx * A0 + dtdy * B0);
             qn[stride + g] = fma(-dtdx, A1, u0);        // u sees the x-edges only
             qn[2 * stride + g] = fma(-dtdy, B1, v0);    // v sees the y-edges only
-            if (ga.rx.rmap) {
+        }
+        // ---- fix-up records (coarse-fine sides of the listed cells) ----
+        // A loop of its own after the update: the edge arrays are intact until
+        // the barrier, and the update keeps its registers.
+        if (ga.rx.rmap) {
+            for (int k = tid; k < tx * ty; k += kThreads) {
+                const int r = k / tx, c = k - r * tx;
+                const long long g = P.base + (long long)(y0 + r + 2) * P.sx + (x0 + c + 2);
                 const int e = ga.rx.rmap[g];
-                if (e >= 0) {
-                    // what each side puts into the cell: the fluctuation
-                    // entering through it with the full (transverse-
-                    // corrected) flux of that edge
-                    const RefluxCell rc = ga.rx.cells[e];
+                if (e < 0) continue;
+                const int oL = (r + 1) * XEX + c + 1, oR = oL + 1;
+                const int oB = (r + 1) * YEX + c + 1, oT = oB + YEX;
+                const int fL = r * (TX + 1) + c, fR = fL + 1;
+                const int gB = r * TX + c, gT = gB + TX;
+                const RefluxCell rc = ga.rx.cells[e];
+                // what each side puts into the cell: the fluctuation entering
+                // through it with the full (transverse-corrected) flux of that edge
 #pragma unroll
-                    for (int sd = 0; sd < 4; sd++) {
-                        if (rc.c[sd] < 0 && rc.f[sd] < 0) continue;
-                        double a, b;
-                        if (sd == 0) {
-                            a = XF[2 * XES + oL] - FF[fL];
-                            b = XF[3 * XES + oL] - FF[FFS + fL];
-                        } else if (sd == 1) {
-                            a = XF[oR] + FF[fR];
-                            b = XF[XES + oR] + FF[FFS + fR];
-                        } else if (sd == 2) {
-                            a = YF[2 * YES + oB] - GG[gB];
-                            b = YF[3 * YES + oB] - GG[GGS + gB];
-                        } else {
-                            a = YF[oT] + GG[gT];
-                            b = YF[YES + oT] + GG[GGS + gT];
-                        }
-                        if (rc.c[sd] >= 0) {
-                            ga.rx.lc[2 * (long long)rc.c[sd]] = a;
-                            ga.rx.lc[2 * (long long)rc.c[sd] + 1] = b;
-                        }
-                        if (rc.f[sd] >= 0) {
-                            double *o = ga.rx.lf + ((long long)ga.rx.sub * ga.rx.nfrec + rc.f[sd]) * 4;
-                            o[0] = a;
-                            o[1] = b;
-                            o[2] = p0;
-                            o[3] = sd < 2 ? u0 : v0;
-                        }
+                for (int sd = 0; sd < 4; sd++) {
+                    if (rc.c[sd] < 0 && rc.f[sd] < 0) continue;
+                    double a, b;
+                    if (sd == 0) {
+                        a = XF[2 * XES + oL] - FF[fL];
+                        b = XF[3 * XES + oL] - FF[FFS + fL];
+                    } else if (sd == 1) {
+                        a = XF[oR] + FF[fR];
+                        b = XF[XES + oR] + FF[FFS + fR];
+                    } else if (sd == 2) {
+                        a = YF[2 * YES + oB] - GG[gB];
+                        b = YF[3 * YES + oB] - GG[GGS + gB];
+                    } else {
+                        a = YF[oT] + GG[gT];
+                        b = YF[YES + oT] + GG[GGS + gT];
+                    }
+                    if (rc.c[sd] >= 0) {
+                        ga.rx.lc[2 * (long long)rc.c[sd]] = a;
+                        ga.rx.lc[2 * (long long)rc.c[sd] + 1] = b;
+                    }
+                    if (rc.f[sd] >= 0) {
+                        // the cell's state at the start of the step (not yet
+                        // overwritten: q and qn are different buffers)
+                        const int s = (r + 2) * PX + c + 2;
+                        double *o = ga.rx.lf + ((long long)ga.rx.sub * ga.rx.nfrec + rc.f[sd]) * 4;
+                        o[0] = a;
+                        o[1] = b;
+                        o[2] = S::kAlias ? ldq<CG>(q + g) : sQ[s];
+                        o[3] = sd < 2 ? (S::kAlias ? ldq<CG>(q + stride + g) : sQ[PS + s])
+                                      : (S::kAlias ? ldq<CG>(q + 2 * stride + g) : sQ[2 * PS + s]);
                     }
                 }
             }

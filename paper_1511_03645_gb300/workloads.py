@@ -314,6 +314,16 @@ def config3(seed: int = 0, n0: int = 200, ratios=(4, 4, 2), tf: float = 4.0 * 36
     return wl
 
 
+def config3_adjoint_medium(wl: Workload) -> np.ndarray:
+    """Bathymetry of a config-3 workload at the cell centres of its adjoint
+    grid, shape (1, ay, ax) (the adjoint solve's dense medium)."""
+    nx, ny = wl.adj_n
+    xa = wl.lo[0] + (np.arange(nx) + 0.5) * (wl.hi[0] - wl.lo[0]) / nx
+    ya = wl.lo[1] + (np.arange(ny) + 0.5) * (wl.hi[1] - wl.lo[1]) / ny
+    X, Y = np.meshgrid(xa, ya)
+    return bathymetry(X, Y, wl.extra["mounts"], wl.hi[0])[None]
+
+
 # --------------------------------------------------------------------------
 # the paper's two-dimensional acoustics examples (Sec. 5.2)
 # --------------------------------------------------------------------------

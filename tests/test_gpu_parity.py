@@ -462,24 +462,59 @@ def test_batched_patches_modes_agree_and_match_oracle(A):
 
 
 # ---------------------------------------------------------- full size, sampled
+def _ghosts_match_oracle_on_gpu_layout(g, wl, picks):
+    """The ghost rings and medium of sampled patches, checked independently
+    of the GPU's ghost fill: the oracle takes the GPU's patch layouts and
+    interior states of every level, fills the ghost cells itself (same-level
+    copies, boundary maps, coarse space interpolation, Sec. 3) and computes
+    the medium of every storage cell; both must equal the GPU's bit for bit.
+    picks: {level: [patch indices]}."""
+    o = O.OracleHierarchy(wl, with_qinit=False)
+    for lev in range(wl.nlevels):
+        P = g.patches(lev)
+        if len(P) == 0:
+            break
+        o.set_layout(lev, P)
+        o.write_level(lev, g.read_level(lev))
+    n = 0
+    for lev, ks in picks.items():
+        g.fill_ghosts(lev)
+        o.fill_ghosts(lev)
+        for k in ks:
+            qg, mg = g.patch_ghosted(lev, k)
+            qo, mo = o.patch_ghosted(lev, k)
+            assert np.array_equal(qg, qo), f"ghost ring, level {lev} patch {k}"
+            assert np.array_equal(mg, mo), f"medium, level {lev} patch {k}"
+            n += 1
+    o.close()
+    return n
+
+
 def test_full_size_config2_sampled_step_parity(A):
     """Config 2 at full size (100^2 coarse, ratios 2 and 4, adjoint 400^2 x
     200 snapshots) in the benchmark's launch configuration: after an adjoint-
-    guided run of 40 coarse steps, one step of sampled finest-level patches is
-    recomputed by the oracle from the GPU's own ghosted input and must match
-    bit for bit; layouts satisfy the nesting and size invariants."""
+    guided run of 40 coarse steps, the ghost rings and medium of sampled
+    patches of every refined level equal the oracle's own fill from the GPU's
+    interior states, and one step of sampled finest-level patches is
+    recomputed by the oracle from that ghosted input and must match bit for
+    bit; layouts satisfy the size invariants."""
     wl = W.config2(seed=0, ts=0.0, tol=1e-3)
     adj = A.solve_adjoint(wl)
     g = A.Hierarchy(wl)
     g.set_adjoint(adj)
+    for lev, (t, fuse) in enumerate((((16, 8), True), ((8, 8), True), ((16, 12), False))):
+        g.set_level_kernel(lev, t, fuse, A.LAUNCH_WORKLIST)   # the benchmark's usual per-level choice
     g.regrid(0, init=True)
     g.advance(40)
     L = wl.nlevels - 1
     P = g.patches(L)
     assert len(P) > 0
-    g.fill_ghosts(L)
     rng = np.random.default_rng(0)
-    ks = sorted(set(rng.choice(len(P), min(6, len(P)), replace=False).tolist()))
+    picks = {lev: sorted(set(rng.choice(len(g.patches(lev)), min(12, len(g.patches(lev))), replace=False).tolist()))
+             for lev in range(1, wl.nlevels) if len(g.patches(lev))}
+    assert _ghosts_match_oracle_on_gpu_layout(g, wl, picks) >= 12
+    g.fill_ghosts(L)
+    ks = sorted(set(rng.choice(len(P), min(12, len(P)), replace=False).tolist()))
     inputs = [g.patch_ghosted(L, k) for k in ks]
     dt = g.time_info()[0] / (wl.ratios[0] * wl.ratios[1])
     dx, dy = wl.level_dx(L)
@@ -529,10 +564,13 @@ def test_full_size_config1_matches_oracle_everywhere(A):
 def test_full_size_config3_sampled_step_parity(A):
     """Config 3 at full size (coarse 200^2 over 2000 km, ratios 4, 4, 2 --
     finest 6400^2 index space -- adjoint 1000^2 x 300 snapshots solved on the
-    GPU): after an adjoint-guided run of 4 coarse steps, one step of sampled
-    patches of every refined level is recomputed by the oracle from the GPU's
-    own ghosted input (f-wave shallow water over the bathymetry) and must
-    match bit for bit."""
+    GPU): after an adjoint-guided run until the finest level is refined (at
+    least 8 coarse steps, regrids every 2 steps of each level), the ghost rings and
+    medium of sampled patches of every refined level equal the oracle's own
+    fill from the GPU's interior states and its own bathymetry, and one step
+    of sampled patches of every refined level is recomputed by the oracle
+    from that ghosted input (f-wave shallow water over the bathymetry) and
+    must match bit for bit."""
     wl = W.config3(seed=0)
     nx = wl.adj_n[0]
     xa = wl.lo[0] + (np.arange(nx) + 0.5) * (wl.hi[0] - wl.lo[0]) / nx
@@ -544,9 +582,18 @@ def test_full_size_config3_sampled_step_parity(A):
     g = A.Hierarchy(wl)
     g.set_adjoint(adj)
     g.regrid(0, init=True)
-    g.advance(4)
+    # advance (regrids every 2 steps of each level) until the finest level
+    # holds patches, at most 200 of the 320 coarse steps
+    steps = 0
+    while steps < 200 and (steps < 8 or len(g.patches(wl.nlevels - 1)) == 0):
+        g.advance(8)
+        steps += 8
     dt0 = g.time_info()[0]
     rng = np.random.default_rng(3)
+    picks = {lev: sorted(set(rng.choice(len(g.patches(lev)), min(6, len(g.patches(lev))), replace=False).tolist()))
+             for lev in range(1, wl.nlevels) if len(g.patches(lev))}
+    assert len(picks) >= 2, f"only levels {sorted(picks)} refined after {steps} coarse steps"
+    assert _ghosts_match_oracle_on_gpu_layout(g, wl, picks) >= 6
     checked = 0
     for L in range(1, wl.nlevels):
         P = g.patches(L)

@@ -568,3 +568,26 @@ def test_adjoint_flagged_functional_converges_to_the_uniform_fine_one():
     assert errs[0] < 0.05, errs
     assert errs[0] > errs[1] > errs[2], errs
     assert errs[2] < 5e-3, errs
+
+
+def test_set_layout_reproduces_a_hierarchy():
+    """The oracle's layout entry (used to check another implementation's ghost
+    cells on that implementation's own layout): a hierarchy copied level by
+    level (patches, then interior states) fills its ghost cells and medium
+    exactly like the original."""
+    wl = _reflux_workload("acoustics_adj_layered", 0)   # layered medium, surface flags, walls
+    a = O.OracleHierarchy(wl)
+    a.regrid(0, init=True)
+    a.advance(7)
+    b = O.OracleHierarchy(wl, with_qinit=False)
+    for lev in range(wl.nlevels):
+        b.set_layout(lev, a.patches(lev))
+        b.write_level(lev, a.read_level(lev))
+    assert len(a.patches(2)) > 0
+    for lev in range(1, wl.nlevels):
+        a.fill_ghosts(lev)
+        b.fill_ghosts(lev)
+        for k in range(len(a.patches(lev))):
+            qa, ma = a.patch_ghosted(lev, k)
+            qb, mb = b.patch_ghosted(lev, k)
+            assert np.array_equal(qa, qb) and np.array_equal(ma, mb)
