@@ -253,6 +253,21 @@ __device__ __forceinline__ void cfl_reduce(long long c, unsigned long long *cfl_
     if ((threadIdx.x & 31) == 0 && c > 0) atomicMax(cfl_bits, (unsigned long long)c);
 }
 
+// Asynchronous 8-byte global -> shared copies for the tile staging: all of a
+// thread's copies are in flight at once instead of one load-store round trip
+// each (cp.async.ca: through L1; used only for data no other CTA of the launch
+// writes).
+__device__ __forceinline__ void cp_async8(double *smem, const double *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 // next tile of this CTA (see TileSched); w_static = the strided choice
 __device__ __forceinline__ int fetch_tile(const TileSched &sc, int *slot, int w_static)
 {
@@ -335,12 +350,17 @@ __device__ __forceinline__ void step2d_tile(const double *__restrict__ q, double
                 long long g = gb + (long long)r * P.sx + c;
                 if (f < 3) {
                     const int si = x0 + c, sj = y0 + r;
-                    if (!(ring && (si < 2 || si >= P.nx + 2 || sj < 2 || sj >= P.ny + 2)))
-                        sQ[f * PS + r * PX + c] = ldq<CG>(q + (long long)f * stride + g);
+                    if (!(ring && (si < 2 || si >= P.nx + 2 || sj < 2 || sj >= P.ny + 2))) {
+                        // the state of a substep launch was written by other CTAs
+                        // of the launch: read it through L2 only
+                        if constexpr (CG) sQ[f * PS + r * PX + c] = ldq<CG>(q + (long long)f * stride + g);
+                        else cp_async8(&sQ[f * PS + r * PX + c], q + (long long)f * stride + g);
+                    }
                 } else {
-                    sA[(f - 3) * PS + r * PX + c] = aux[(long long)(f - 3) * stride + g];
+                    cp_async8(&sA[(f - 3) * PS + r * PX + c], aux + (long long)(f - 3) * stride + g);
                 }
             }
+            cp_async_wait_all();
             if (ring) {
                 for (int k = tid; k < ry * nrow; k += kThreads) {
                     int r = k / nrow, c = k - r * nrow;

@@ -397,6 +397,44 @@ def test_edge_cases_no_refinement_and_full_refinement(A):
             assert cov == 40 * 40
 
 
+@pytest.mark.parametrize("case", ["ratio16", "odd_ratio3_1d", "two_snapshots", "ragged_n0_37", "ratios_3_5"])
+def test_degenerate_parameters_match_oracle(A, case):
+    """Limits the method admits, each against the oracle bit for bit: the
+    largest refinement ratio (16: the time-fraction table is full), odd
+    ratios (fine cells straddle no coarse centre symmetrically: offsets
+    (2m + 1 - r)/(2r) with r odd), the fewest adjoint snapshots (2: every
+    window brackets the whole run), a coarse grid whose size no tile divides,
+    and an advance by zero steps (a no-op)."""
+    if case == "ratio16":
+        wl = W.config2(seed=4, n0=12, ratios=(16,), tf=0.4, adj_n=48, nsnap=8, ts=0.0, tol=1e-3,
+                       min_patch=16, max_patch=64)
+    elif case == "odd_ratio3_1d":
+        wl = W.config1(n0=60, ratio=3, tf=3.0, adj_n=180, nsnap=12)
+    elif case == "two_snapshots":
+        wl = W.config2(seed=6, n0=20, ratios=(2,), tf=0.6, adj_n=40, nsnap=2, ts=0.0, tol=1e-6)
+    elif case == "ragged_n0_37":
+        wl = W.config2(seed=7, n0=37, ratios=(2, 2), tf=0.5, adj_n=74, nsnap=10, ts=0.0, tol=0.02)
+    else:
+        wl = W.config2(seed=8, n0=18, ratios=(3, 5), tf=0.4, adj_n=54, nsnap=10, ts=0.0, tol=0.02,
+                       min_patch=15, max_patch=60)
+    if case in ("ragged_n0_37", "ratios_3_5"):
+        wl.flag_mode = W.FLAG_DIFFERENCE   # layouts from the undivided differences of the state
+    snaps = O.adjoint_solve(wl)
+    o, g = _amr_pair(A, wl, snaps=snaps)
+    g.advance(0)
+    _compare_all(o, g, wl.nlevels)
+    n = o.nsteps_total()
+    refined = 0
+    for c in range(3):
+        k = n // 3 if c < 2 else n - 2 * (n // 3)
+        o.advance(k)
+        g.advance(k)
+        _compare_all(o, g, wl.nlevels)
+        refined += sum(len(o.patches(lev)) for lev in range(1, wl.nlevels))
+    assert refined > 0, "the case never refined"
+    assert abs(g.functional() - o.functional()) <= RTOL * max(abs(o.functional()), 1e-300)
+
+
 def test_cfl_violation_is_reported(A):
     """Courant number above cfl_max returns ADJAMR_ECFL, not a crash."""
     wl = W.config2(seed=5, n0=16, ratios=(2,), tf=0.5)
