@@ -203,11 +203,19 @@ adjamr_status adjamr_load_adjoint_snapshots(adjamr_ctx *ctx, const double *snaps
                                             const unsigned char *wet, int snaps_on_device,
                                             adjamr_adjoint **out);
 
-/* Solve the adjoint on the fixed grid described by ap (nlevels = 1, eqn =
- * adjoint system) from q~(x, 0) = phi (host [m][ay][ax]) and store nsnap
- * snapshots on the device (Sec. 4: q^(x, tf - t_n) = q~(x, t_n)).  The step
- * is dt = dT/ceil(dT/dt_cfl), dT = (tf - t0)/(nsnap - 1).  The handle is
- * attached to ctx (ctx may be NULL: then it is only returned). */
+/* Solve the adjoint (eqn = adjoint system) on the grid described by ap from
+ * q~(x, 0) = phi (host [m][ay][ax] on the level-0 grid of ap) and store
+ * nsnap snapshots of that grid on the device (Sec. 4: q^(x, tf - t_n) =
+ * q~(x, t_n)).  The level-0 step is dt = dT/ceil(dT/dt_cfl), dT = (tf -
+ * t0)/(nsnap - 1).  ap->nlevels = 1: a fixed grid, as in the paper.
+ * ap->nlevels > 1: the adjoint solved with AMR (Sec. 6 proposes it for a
+ * more accurate inner product): finer levels by ap->ratio, flagged by the
+ * standard flagger ap->flag_mode (DIFFERENCE or SURFACE; EINVAL otherwise)
+ * at ap->tol and regridded every ap->regrid_interval steps as in a forward
+ * run; their initial cells are interpolated from phi on level 0; each
+ * level-0 step is a full Berger-Oliger step, so the snapshot is level 0
+ * holding the composite solution averaged onto it.  The handle is attached
+ * to ctx (ctx may be NULL: then it is only returned). */
 adjamr_status adjamr_solve_adjoint(adjamr_ctx *ctx, const adjamr_params *ap, const adjamr_medium *am,
                                    const double *phi, int nsnap, adjamr_adjoint **out);
 

@@ -1907,6 +1907,86 @@ int orc_adjoint_solve(const orc_params *P, int axis, int nl, const double *iface
     return 0;
 }
 
+/* The adjoint solved on an AMR hierarchy of its own (Sec. 6 names this as a
+   way to a more accurate inner product): P describes the adjoint hierarchy
+   (eqn = adjoint system, nlevels >= 1, ratios, a standard flag mode and its
+   tolerance, regrid interval and buffer); its level 0 is the snapshot grid.
+   q~(x, 0) = phi on level 0 and, on the finer levels the initial regrid
+   creates, the coarse-fine interpolation of it (a target box aligned to
+   level-0 cell edges is reproduced exactly).  Level-0 steps of dt = dT /
+   ceil(dT / dt_cfl), dT = (tf - t0)/(nsnap - 1), each a full Berger-Oliger
+   step (regrids, substeps, average-down: level 0 holds the composite
+   solution averaged onto it); snapshot s is level 0 at tau_s, stored at
+   index nsnap - 1 - s (forward time order).  medium: dense [nmed][ny][nx]
+   per level in `dense` (nlevels arrays back to back) or layered. */
+int orc_adjoint_solve_amr(const orc_params *P, int axis, int nl, const double *iface, const double *f0,
+                          const double *f1, const double *dense, const double *phi, int nsnap, double *snaps)
+{
+    if (nsnap < 2 || P->nlevels < 1) return 1;
+    orc_params Q = *P;
+    Q.qinit = NULL;
+    double dmin0;
+    {
+        int N = P->n0[0], M = (P->dim == 2) ? P->n0[1] : 1;
+        double dx = (P->hi[0] - P->lo[0]) / (double)N;
+        double dy = (P->dim == 2) ? (P->hi[1] - P->lo[1]) / (double)M : dx;
+        dmin0 = (P->dim == 2) ? fmin(dx, dy) : dx;
+    }
+    double dts = (P->tf - P->t0) / (double)(nsnap - 1);
+    double dtc = P->cfl * dmin0 / P->cmax;
+    int nsub = (int)ceil(dts / dtc);
+    Q.dt0 = dts / (double)nsub;
+    OHier *h = orc_create(&Q);
+    if (!h) return 1;
+    if (dense) {
+        long off = 0;
+        int N = P->n0[0], M = (P->dim == 2) ? P->n0[1] : 1;
+        for (int l = 0; l < P->nlevels; l++) {
+            orc_set_medium_dense(h, l, dense + off);
+            off += (long)h->nmed * N * M;
+            if (l < P->nlevels - 1) {
+                N *= P->ratio[l];
+                if (P->dim == 2) M *= P->ratio[l];
+            }
+        }
+    } else {
+        orc_set_medium_layered(h, axis, nl, iface, f0, f1);
+    }
+    OLevel *L = &h->L[0];
+    int nx = L->N, ny = L->M;
+    for (int k = 0; k < L->np; k++) {
+        OPatch *p = &L->p[k];
+        for (int f = 0; f < h->m; f++)
+            for (int j = 0; j < p->ny; j++)
+                for (int i = 0; i < p->nx; i++)
+                    p->q[L->cur][qidx(h, p, f, i, j)] = phi[((long)f * ny + p->jlo + j) * nx + p->ilo + i];
+    }
+    if (P->nlevels > 1 && regrid_from(h, 0, 0)) {
+        orc_destroy(h);
+        return 1;
+    }
+    long per = (long)h->m * nx * ny;
+    double cfl = 0.0;
+    for (int s = 0; s < nsnap; s++) {
+        if (s > 0)
+            for (int q = 0; q < nsub; q++)
+                if (step_level(h, 0, &cfl)) {
+                    orc_destroy(h);
+                    return 1;
+                }
+        double *dst = snaps + (long)(nsnap - 1 - s) * per;
+        for (int k = 0; k < L->np; k++) {
+            const OPatch *p = &L->p[k];
+            for (int f = 0; f < h->m; f++)
+                for (int j = 0; j < p->ny; j++)
+                    for (int i = 0; i < p->nx; i++)
+                        dst[((long)f * ny + p->jlo + j) * nx + p->ilo + i] = p->q[L->cur][qidx(h, p, f, i, j)];
+        }
+    }
+    orc_destroy(h);
+    return 0;
+}
+
 /* exported for tests: Berger-Rigoutsos clustering of a dense flag field
    [M][N] with nesting mask (NULL = everything nestable); boxes out as
    [n][4] = (i0, i1, j0, j1), inclusive, sorted by (j0, i0).  Returns the

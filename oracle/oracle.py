@@ -94,6 +94,7 @@ def lib():
             L.orc_cluster.argtypes = [P(ctypes.c_ubyte), P(ctypes.c_ubyte), i, i, i, i, d, P(ctypes.c_int), i]
             L.orc_set_gauges.argtypes = [vp, i, dp, dp]
             L.orc_set_layout.argtypes = [vp, i, i, P(ctypes.c_int)]
+            L.orc_adjoint_solve_amr.argtypes = [P(OrcParams), i, i, dp, dp, dp, dp, dp, i, dp]
             L.orc_read_gauges.restype = ctypes.c_long
             L.orc_read_gauges.argtypes = [vp, dp, ctypes.c_long]
             _lib = L
@@ -336,6 +337,42 @@ def adjoint_solve(wl, nsnap=None, n=None, medium_dense=None, tf=None, phi=None):
                                      None, _dp(phi), S, _dp(out))
     if rc:
         raise RuntimeError("orc_adjoint_solve failed")
+    return out
+
+
+def adjoint_solve_amr(wl, ratios, flag_mode, tol, nsnap=None, n=None, phi=None, medium_dense_levels=None,
+                      reflux=0):
+    """Adjoint snapshots [nsnap, m, ny, nx] (forward-time order) from an AMR
+    solve of the adjoint whose level 0 is the snapshot grid (n, default
+    wl.adj_n), refined by `ratios` under a standard flagger (flag_mode,
+    tol); medium_dense_levels: dense media [nmed][M_l][N_l] per level (dense
+    workloads)."""
+    import copy
+    nn = tuple(wl.adj_n if n is None else n)
+    S = wl.nsnap if nsnap is None else nsnap
+    w2 = copy.copy(wl)
+    w2.n0, w2.ratios, w2.flag_mode, w2.tol, w2.reflux = nn, tuple(ratios), flag_mode, tol, reflux
+    P = params_from_workload(w2, eqn=wl.adj_eqn, nlevels=len(ratios) + 1, n0=nn)
+    if phi is None:
+        phi = _phi_for(wl, nn)
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    nx = nn[0]
+    ny = nn[1] if wl.dim == 2 else 1
+    out = np.zeros((S, wl.m, ny, nx))
+    med = wl.medium
+    z = np.zeros(1)
+    if medium_dense_levels is not None or med.kind == "dense":
+        dense = np.concatenate([np.ascontiguousarray(a, dtype=np.float64).reshape(-1) for a in medium_dense_levels])
+        rc = lib().orc_adjoint_solve_amr(ctypes.byref(P), 0, 1, _dp(z), _dp(z), _dp(z), _dp(dense), _dp(phi), S,
+                                         _dp(out))
+    else:
+        iface = np.ascontiguousarray(med.iface if med.iface.size else np.zeros(1), dtype=np.float64)
+        f0 = np.ascontiguousarray(med.rho, dtype=np.float64)
+        f1 = np.ascontiguousarray(med.K, dtype=np.float64)
+        rc = lib().orc_adjoint_solve_amr(ctypes.byref(P), med.axis, f0.size, _dp(iface), _dp(f0), _dp(f1),
+                                         None, _dp(phi), S, _dp(out))
+    if rc:
+        raise RuntimeError("orc_adjoint_solve_amr failed")
     return out
 
 

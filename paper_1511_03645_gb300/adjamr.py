@@ -473,20 +473,34 @@ class Hierarchy:
 
 
 def solve_adjoint(wl, *, nsnap=None, n=None, phi=None, medium_dense=None, stream=None, ctx: Hierarchy = None,
-                  tf=None, tile=(0, 0)) -> Adjoint:
+                  tf=None, tile=(0, 0), amr=None) -> Adjoint:
     """Adjoint snapshots computed on the GPU (device-resident handle);
-    tile: the step-kernel tile of the adjoint grid (0: default)."""
+    tile: the step-kernel tile of the adjoint grid (0: default).
+    amr = (ratios, flag_mode, tol[, reflux]): the adjoint solved with AMR on a
+    hierarchy whose level 0 is the snapshot grid; medium_dense is then the
+    list of the levels' dense media (dense workloads)."""
+    import copy
     L = load()
     nn = wl.adj_n if n is None else n
     S = wl.nsnap if nsnap is None else nsnap
-    p = make_params(wl, eqn=wl.adj_eqn, nlevels=1, n0=nn, stream=stream, tf=tf, tile=tile)
+    wa = wl
+    nlev = 1
+    if amr is not None:
+        wa = copy.copy(wl)
+        wa.ratios, wa.flag_mode, wa.tol = tuple(amr[0]), amr[1], amr[2]
+        wa.reflux = amr[3] if len(amr) > 3 else 0
+        nlev = len(wa.ratios) + 1
+    p = make_params(wa, eqn=wl.adj_eqn, nlevels=nlev, n0=nn, stream=stream, tf=tf, tile=tile)
     if phi is None:
         import copy
         w2 = copy.copy(wl)
         w2.adj_n = tuple(nn)
         phi = w2.adjoint_phi()
     phi = np.ascontiguousarray(phi, dtype=np.float64)
-    mh = _MediumHolder(wl.medium, dense_fields=None if medium_dense is None else [medium_dense])
+    dense = None
+    if medium_dense is not None:
+        dense = list(medium_dense) if amr is not None else [medium_dense]
+    mh = _MediumHolder(wl.medium, dense_fields=dense)
     out = ctypes.c_void_p()
     rc = L.adjamr_solve_adjoint(ctx.h if ctx is not None else None, ctypes.byref(p), ctypes.byref(mh.m), _dp(phi), S,
                                 ctypes.byref(out))

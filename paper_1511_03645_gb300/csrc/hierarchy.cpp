@@ -2285,13 +2285,24 @@ void adjamr_adjoint_release(adjamr_adjoint *adj)
 adjamr_status adjamr_solve_adjoint(adjamr_ctx *ctx, const adjamr_params *ap, const adjamr_medium *am,
                                    const double *phi, int nsnap, adjamr_adjoint **out)
 {
-    if (!ap || !am || !phi || nsnap < 2 || ap->nlevels != 1 || (ap->eqn != ADJAMR_ACOUSTICS_ADJOINT &&
-                                                                 ap->eqn != ADJAMR_SW_ADJOINT))
+    if (!ap || !am || !phi || nsnap < 2 || ap->nlevels < 1 || (ap->eqn != ADJAMR_ACOUSTICS_ADJOINT &&
+                                                                ap->eqn != ADJAMR_SW_ADJOINT))
+        return ADJAMR_EINVAL;
+    const bool amr = ap->nlevels > 1;
+    if (amr && ap->flag_mode != ADJAMR_FLAG_DIFFERENCE && ap->flag_mode != ADJAMR_FLAG_SURFACE) return ADJAMR_EINVAL;
+    if (!(ap->cmax > 0.0) || ap->n0[0] < 1 || (ap->dim == 2 && ap->n0[1] < 1) || !(ap->tf > ap->t0))
         return ADJAMR_EINVAL;
     try {
+        // level-0 step dT / ceil(dT / dt_cfl), dT = the snapshot interval, so
+        // that steps land on the snapshots (finer levels: dt_0 / prod r)
+        const double dx0 = (ap->hi[0] - ap->lo[0]) / (double)ap->n0[0];
+        const double dmin = (ap->dim == 2) ? std::fmin(dx0, (ap->hi[1] - ap->lo[1]) / (double)ap->n0[1]) : dx0;
+        const double dts = (ap->tf - ap->t0) / (double)(nsnap - 1);
+        const double dtc = ap->cfl * dmin / ap->cmax;
+        const int nsub = (int)std::ceil(dts / dtc);
         adjamr_params q = *ap;
         q.qinit = nullptr;
-        q.dt0 = 1.0;  // replaced below
+        q.dt0 = dts / (double)nsub;
         q.stream = ctx ? (void *)ctx->s : ap->stream;
         adjamr_ctx *a = nullptr;
         TRY(create_impl(&q, &a));
@@ -2303,25 +2314,6 @@ adjamr_status adjamr_solve_adjoint(adjamr_ctx *ctx, const adjamr_params *ap, con
         }
         Level &L = a->L[0];
         int nx = L.N, ny = L.M, m = a->m;
-        double dmin = (ap->dim == 2) ? std::fmin(L.dx, L.dy) : L.dx;
-        double dts = (ap->tf - ap->t0) / (double)(nsnap - 1);
-        double dtc = ap->cfl * dmin / ap->cmax;
-        int nsub = (int)std::ceil(dts / dtc);
-        L.dt = dts / (double)nsub;
-        // patch descriptors carry dt/dx: rebuild them with the final step
-        {
-            std::vector<Box> boxes;
-            for (const HPatch &p : L.patches) boxes.push_back(Box{p.ilo, p.ilo + p.nx - 1, p.jlo, p.jlo + p.ny - 1});
-            free_level(a, L);
-            st = alloc_level(a, 0, boxes);
-            if (st == ADJAMR_OK) st = build_ghost_map(a, 0);
-            if (st == ADJAMR_OK) st = fill_aux(a, 0);
-            if (st != ADJAMR_OK) {
-                if (ctx) ctx->err = a->err;
-                adjamr_destroy(a);
-                return st;
-            }
-        }
         // phi into the interior (patch order)
         {
             std::vector<double> pv((size_t)m * L.ninterior);
@@ -2331,7 +2323,11 @@ adjamr_status adjamr_solve_adjoint(adjamr_ctx *ctx, const adjamr_params *ap, con
                     for (int j = 0; j < p.ny; j++)
                         for (int i = 0; i < p.nx; i++) pv[o++] = phi[((size_t)f * ny + p.jlo + j) * nx + p.ilo + i];
             st = read_level_impl(a, 0, nullptr, pv.size(), true, pv.data());
+            // adjoint with AMR: the finer levels flagged by the standard
+            // flagger from phi, their cells interpolated from level 0
+            if (st == ADJAMR_OK && amr) st = regrid_from(a, 0, 0);
             if (st != ADJAMR_OK) {
+                if (ctx) ctx->err = a->err;
                 adjamr_destroy(a);
                 return st;
             }
@@ -2357,9 +2353,15 @@ adjamr_status adjamr_solve_adjoint(adjamr_ctx *ctx, const adjamr_params *ap, con
         for (int sidx = 0; sidx < nsnap && e == cudaSuccess; sidx++) {
             if (sidx > 0)
                 for (int k = 0; k < nsub && st == ADJAMR_OK; k++) {
-                    st = step_patches(a, 0, 0, a->lfuse[0] ? GHOST_FUSED : GHOST_FILL);
-                    L.cur = 1 - L.cur;
-                    L.nstep++;
+                    if (amr) {
+                        // a Berger-Oliger step: level 0 then holds the composite
+                        // solution averaged onto the snapshot grid
+                        st = step_level(a, 0);
+                    } else {
+                        st = step_patches(a, 0, 0, a->lfuse[0] ? GHOST_FUSED : GHOST_FILL);
+                        L.cur = 1 - L.cur;
+                        L.nstep++;
+                    }
                 }
             if (st != ADJAMR_OK) break;
             e = launch_gather_interior(m, d_map, (long long)nx * ny, L.q[L.cur], L.ncell,

@@ -314,14 +314,20 @@ def config3(seed: int = 0, n0: int = 200, ratios=(4, 4, 2), tf: float = 4.0 * 36
     return wl
 
 
-def config3_adjoint_medium(wl: Workload) -> np.ndarray:
+def config3_adjoint_medium(wl: Workload, ratios=None):
     """Bathymetry of a config-3 workload at the cell centres of its adjoint
-    grid, shape (1, ay, ax) (the adjoint solve's dense medium)."""
+    grid, shape (1, ay, ax) (the adjoint solve's dense medium); with ratios,
+    the list of those arrays for every level of an adjoint hierarchy whose
+    level 0 is the adjoint grid."""
+    out = []
     nx, ny = wl.adj_n
-    xa = wl.lo[0] + (np.arange(nx) + 0.5) * (wl.hi[0] - wl.lo[0]) / nx
-    ya = wl.lo[1] + (np.arange(ny) + 0.5) * (wl.hi[1] - wl.lo[1]) / ny
-    X, Y = np.meshgrid(xa, ya)
-    return bathymetry(X, Y, wl.extra["mounts"], wl.hi[0])[None]
+    for r in [1] + list(ratios or []):
+        nx, ny = nx * r, ny * r
+        xa = wl.lo[0] + (np.arange(nx) + 0.5) * (wl.hi[0] - wl.lo[0]) / nx
+        ya = wl.lo[1] + (np.arange(ny) + 0.5) * (wl.hi[1] - wl.lo[1]) / ny
+        X, Y = np.meshgrid(xa, ya)
+        out.append(bathymetry(X, Y, wl.extra["mounts"], wl.hi[0])[None])
+    return out if ratios is not None else out[0]
 
 
 # --------------------------------------------------------------------------

@@ -591,3 +591,67 @@ def test_set_layout_reproduces_a_hierarchy():
             qa, ma = a.patch_ghosted(lev, k)
             qb, mb = b.patch_ghosted(lev, k)
             assert np.array_equal(qa, qb) and np.array_equal(ma, mb)
+
+
+# ------------------------------------------------------ adjoint with AMR
+def _two_stage_average(q, rs):
+    """Average a fine field [m, M, N] down level by level (ratios rs from
+    the finest), each cell the sum of its children row by row times 1/r^2,
+    as the hierarchy's average-down does."""
+    for r in rs:
+        m, M, N = q.shape
+        out = np.zeros((m, M // r, N // r))
+        inv = 1.0 / (r * r)
+        for f in range(m):
+            for b in range(M // r):
+                for a in range(N // r):
+                    s = 0.0
+                    for jj in range(r):
+                        for ii in range(r):
+                            s = s + q[f, b * r + jj, a * r + ii]
+                    out[f, b, a] = s * inv
+        q = out
+    return q
+
+
+def _adjoint_fine_reference(wl, N, ratios, S):
+    """Uniform adjoint on the finest grid with the hierarchy's finest step,
+    averaged onto the snapshot grid in the hierarchy's order."""
+    import copy
+    rf = int(np.prod(ratios))
+    dts = (wl.tf - wl.t0) / (S - 1)
+    nsub = int(math.ceil(dts / (wl.cfl * (8.0 / N) / wl.medium.cmax)))
+    wf = copy.copy(wl)
+    wf.eqn, wf.n0, wf.ratios = wl.adj_eqn, (N * rf, N * rf), ()
+    hf = O.OracleHierarchy(wf, nlevels=1, with_qinit=False, dt0=dts / nsub / rf)
+    phif = O._phi_for(wl, (N * rf, N * rf))
+    hf.write_level(0, np.concatenate([phif[:, jlo:jlo + ny, ilo:ilo + nx].reshape(-1)
+                                      for ilo, jlo, nx, ny in hf.patches(0)]))
+    out = []
+    for s in range(S):
+        if s:
+            hf.advance(nsub * rf)
+        out.append(_two_stage_average(hf.level_dense(0), list(reversed(ratios))))
+    return np.array(out[::-1])
+
+
+def test_adjoint_with_amr_limits_and_accuracy():
+    """The adjoint solved with AMR (Sec. 6 proposes it for a more accurate
+    inner product), snapshots from its level 0 after each Berger-Oliger step.
+    Limits: tol = +inf refines nothing and gives the fixed-grid adjoint bit
+    for bit; tol < 0 refines everything and gives the uniform finest-grid
+    adjoint averaged onto the snapshot grid, bit for bit (target box on
+    level-0 cell edges, so the interpolated initial data is the finest
+    grid's).  Between them the snapshots approach that finest-grid adjoint as
+    the tolerance falls, far closer than the fixed grid of the same size."""
+    N, S, ratios = 16, 5, (2, 2)
+    wl = W.config2(seed=3, n0=N, adj_n=N, tf=2.0, nsnap=S, bc=(W.BC_WALL,) * 4)
+    uni = O.adjoint_solve(wl)
+    assert np.array_equal(O.adjoint_solve_amr(wl, ratios, W.FLAG_DIFFERENCE, math.inf), uni)
+    ref = _adjoint_fine_reference(wl, N, ratios, S)
+    assert np.array_equal(O.adjoint_solve_amr(wl, ratios, W.FLAG_DIFFERENCE, -1.0), ref)
+    e_uni = float(np.abs(uni - ref).max())
+    errs = [float(np.abs(O.adjoint_solve_amr(wl, ratios, W.FLAG_DIFFERENCE, tol) - ref).max())
+            for tol in (0.1, 0.03, 0.01)]
+    assert errs[0] > errs[1] > errs[2], errs
+    assert errs[2] < 1e-3 * e_uni, (errs, e_uni)
