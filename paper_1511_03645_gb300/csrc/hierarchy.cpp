@@ -434,10 +434,32 @@ adjamr_status build_work(adjamr_ctx *c, int l, int tx, int ty)
     if (L.work_tx == tx && L.work_ty == ty && L.d_work && L.work_lpt == lpt && L.work_deps == deps) return ADJAMR_OK;
     cput(c, L.d_work);
     L.h_work.clear();
-    const int tyy = (c->P.dim == 2) ? ty : 1;
+    const int tyy0 = (c->P.dim == 2) ? ty : 1;
+    int txx = tx, tyy = tyy0;
+    if (c->P.dim == 2 && c->lmode[l] == ADJAMR_LAUNCH_WORKLIST && c->nsm > 0) {
+        // A small layout cut at the level's tile size leaves SMs with one or
+        // two CTAs (or none), which cannot keep the FP64 pipe busy: cut it
+        // finer, down to 8x8, until every SM has about three tiles.  The
+        // kernel is the level's (it runs any tile up to its shape), and every
+        // cut gives the same bits.
+        auto count = [&](int a, int b) {
+            long long n = 0;
+            for (const HPatch &p : L.patches) n += (long long)tile_count(p.nx, a) * tile_count(p.ny, b);
+            return n;
+        };
+        const long long want = 3LL * c->nsm;
+        static const int cuts[3][2] = {{12, 12}, {12, 8}, {8, 8}};
+        if (count(txx, tyy) < want)
+            for (const auto &cu : cuts) {
+                if (cu[0] * cu[1] >= txx * tyy) continue;
+                txx = std::min(txx, cu[0]);
+                tyy = std::min(tyy, cu[1]);
+                if (count(txx, tyy) >= want) break;
+            }
+    }
     for (int k = 0; k < (int)L.patches.size(); k++) {
         const HPatch &p = L.patches[k];
-        const int nx = tile_count(p.nx, tx), ny = tile_count(p.ny, tyy);
+        const int nx = tile_count(p.nx, txx), ny = tile_count(p.ny, tyy);
         for (int b = 0; b < ny; b++)
             for (int a = 0; a < nx; a++)
                 L.h_work.push_back({k, tile_off(p.nx, nx, a), tile_off(p.ny, ny, b),
