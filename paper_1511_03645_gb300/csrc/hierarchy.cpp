@@ -1240,6 +1240,7 @@ adjamr_status reflux_apply(adjamr_ctx *c, int l)
     a.w = 1.0 / (double)(a.r * a.nseg);
     a.dtdx = L.dt / L.dx;
     a.dtdy = c->P.dim == 2 ? L.dt / L.dy : 0.0;
+    a.err = c->d_err;
     CKR(c, launch_reflux_apply(c->P.dim, c->P.eqn, a, c->s));
     c->st.kernel_launches++;
     return ADJAMR_OK;
@@ -1844,6 +1845,10 @@ adjamr_status check_err(adjamr_ctx *c)
     if (e & kSubstepErrBit) {
         c->err = "a substep launch gave up waiting for a neighbouring tile";
         return ADJAMR_ETIMEOUT;
+    }
+    if (e & kRefluxErrBit) {
+        c->err = "conservation fix-up: a coarse-fine side without its fine records";
+        return ADJAMR_ENEST;
     }
     if (e) {
         c->err = "hierarchy not properly nested (device check " + std::to_string(e) + ")";

@@ -169,7 +169,9 @@ struct RefluxApply {
     int r, nseg;
     double w;               // 1 / (r * nseg)
     double dtdx, dtdy;
+    int *err;               // kRefluxErrBit or-ed in if a fine edge of a recorded side has no record
 };
+constexpr int kRefluxErrBit = 1 << 29;
 cudaError_t launch_reflux_apply(int dim, int eqn, const RefluxApply &a, cudaStream_t s);
 // rmap[cells[e].idx] = e for every entry (rmap set to -1 beforehand)
 cudaError_t launch_reflux_map(const RefluxCell *cells, int n, int *rmap, cudaStream_t s);

@@ -1119,7 +1119,10 @@ __global__ void __launch_bounds__(256) k_reflux_apply(RefluxApply a)
                     const long long fr = (long long)rc.c[sd] * a.nseg + g;
                     const double *rec = a.lf + ((long long)sb * a.nfrec + fr) * 4;
                     const long long fi = a.fidx[fr];
-                    if (fi < 0) continue;  // (every fine edge of a recorded side has a record)
+                    if (fi < 0) {  // every fine edge of a recorded side has a record: a broken table
+                        atomicOr(a.err, kRefluxErrBit);
+                        continue;
+                    }
                     double mf[2] = {0.0, 0.0};
 #pragma unroll
                     for (int f = 0; f < NM; f++) mf[f] = a.medf[f * a.sf + fi];
