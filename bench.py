@@ -546,6 +546,34 @@ def run_ours(args, rank, world):
         "adjoint_solve_s": adj_s,
         "J": Js[0],
     }
+    # the headline figures of every measured configuration in a few hundred
+    # characters, last in the line so that a truncated record still holds them
+    def rnd(x, n=4):
+        return float(f"{x:.{n}g}") if isinstance(x, (int, float)) else x
+
+    summ = {"config2_cell_updates_per_s": rnd(value), "config2_step_frac": rnd(achieved / peak, 3),
+            "config2_e2e": rnd(e2e["value"]) if e2e else None}
+    if batched:
+        summ["config4_batched_cell_updates_per_s"] = rnd(max(
+            batched[k] for k in ("fused_worklist", "fused_persistent", "fused_graph", "fused_tuned_graph")))
+        summ["config4_batched_frac"] = rnd(batched.get("fp64_roofline_frac_best"), 3)
+        summ["config4_fused_over_per_patch"] = rnd(batched.get("fused_over_per_patch"), 3)
+    for k in ("config1", "config3"):
+        if configs and k in configs:
+            c = configs[k]
+            summ[k] = {"value": rnd(c["value"]), "step_frac": rnd(c["roofline"]["frac"], 3),
+                       "cpu_oracle": rnd(c["cpu_baseline"]["value"]) if "cpu_baseline" in c else None}
+    if configs and "adjoint_amr" in configs:
+        summ["adjoint_amr_cell_updates_per_s"] = rnd(configs["adjoint_amr"]["value"])
+    if serving and serving.get("runs"):
+        summ["serve_sample_p50_s"] = rnd(serving["runs"][0]["p50_latency_s"], 3)
+        summ["serve_sample_p99_s"] = rnd(serving["runs"][0]["p99_latency_s"], 3)
+    if paper:
+        summ["sec_5_2_gauge_err_adjoint_vs_fine"] = [
+            rnd(r["adjoint_flagging"]["gauge_max_abs_err_vs_uniform_fine"], 3) for r in paper.values()]
+        summ["sec_5_2_gauge_err_pressure_vs_fine"] = [
+            rnd(r["pressure_flagging"]["gauge_max_abs_err_vs_uniform_fine"], 3) for r in paper.values()]
+    line["summary"] = summ
     log("autotune (ms of the timed coarse steps per candidate, by level): " + json.dumps(
         {f"level{r['level']}": {f"{c['tile'][0]}x{c['tile'][1]}{'' if c['fuse_ghosts'] else '+fill'}": round(c["ms"], 2)
                                 for c in r["candidates"]} for r in tuned["candidates"]}))
