@@ -47,7 +47,7 @@
 
 enum { O_ACOU = 0, O_ACOU_ADJ = 1, O_SW = 2, O_SW_ADJ = 3 };
 enum { O_EXTRAP = 0, O_WALL = 1, O_PERIODIC = 2 };
-enum { O_BRACKET = 0, O_LINEAR = 1, O_DIFF = 2, O_SURFACE = 3 };
+enum { O_BRACKET = 0, O_LINEAR = 1, O_DIFF = 2, O_SURFACE = 3, O_ERROR = 4 };
 enum { O_MED_NONE = 0, O_MED_LAYERED = 1, O_MED_DENSE = 2 };
 
 typedef void (*orc_qinit_fn)(int level, int n, const double *xc, const double *yc, double *q_out, void *user);
@@ -126,6 +126,10 @@ typedef struct {
     double *gxs, *gys;
     long ngrec, gcap;
     double *grec;
+    /* adjoint-weighted error flagging: the error estimate of the level being
+       flagged, [cell in patch order, row-major within a patch][m] */
+    double *tau;
+    long ntau;
     char err[256];
 } OHier;
 
@@ -727,6 +731,7 @@ void orc_destroy(void *hv)
     free(h->gxs);
     free(h->gys);
     free(h->grec);
+    free(h->tau);
     free(h);
 }
 
@@ -1208,6 +1213,163 @@ static double adj_dot_time(const OHier *h, double tau, double x, double y, const
     return fabs(d);
 }
 
+/* ------------------------------------------------------------------ */
+/* adjoint-weighted error estimate (Sec. 7: the forward solution's      */
+/* pointwise error estimated by Richardson extrapolation, its effect on */
+/* J by the adjoint).                                                   */
+/*                                                                      */
+/* For every patch of level l at the level's current time t: take the   */
+/* patch extended to an even size (ne x me) with a ring of 4 cells, the */
+/* values outside the patch filled as ghost cells are (same level where */
+/* it has a patch, else the interpolation from level l-1 at the same    */
+/* substep, boundary-mapped); advance it two steps of dt (the first     */
+/* over the region widened by 2 cells, the second over the even patch); */
+/* coarsen the extended patch by 2 in every direction (mean of the      */
+/* children, medium included) and advance it one step of 2 dt.  With a  */
+/* second-order method one fine step's local error is C dx^3 and the    */
+/* coarse step's 8 C dx^3, so coarse minus (coarsened) fine after the   */
+/* two is 6 C dx^3 and                                                  */
+/*   tau = (coarsen(fine) - coarse) / 6 = -(local error of one step),   */
+/* per component, on every 2 x 2 (1D: 2) block of the patch.  A cell   */
+/* is flagged where max over the flagging window's snapshots of         */
+/* |qhat . tau| exceeds the tolerance (the bracket rule of Sec. 4 with  */
+/* tau in place of q).                                                  */
+/* ------------------------------------------------------------------ */
+/* value of level l at index (I, J) (boundary-mapped) at substep k of the
+   coarser step: the level's own patch where it has one, else the
+   interpolation from level l - 1, as a ghost cell gets it */
+static int level_value(OHier *h, int l, int I, int J, int k, double *v)
+{
+    double sg[3], w[3];
+    map_bc(h, l, &I, &J, sg);
+    int sk = find_patch(h, l, I, J);
+    if (sk >= 0) {
+        const OPatch *s = &h->L[l].p[sk];
+        for (int f = 0; f < h->m; f++) w[f] = s->q[h->L[l].cur][qidx(h, s, f, I - s->ilo, J - s->jlo)];
+    } else {
+        if (l == 0) {
+            snprintf(h->err, sizeof h->err, "level 0 does not cover cell (%d,%d)", I, J);
+            return 1;
+        }
+        if (coarse_interp(h, l, I, J, k, w)) return 1;
+    }
+    for (int f = 0; f < h->m; f++) v[f] = sg[f] < 0.0 ? -w[f] : w[f];
+    return 0;
+}
+
+/* mean of the 2 x 2 (1D: 2) children of every cell of a coarsened array:
+   src [nf][sy][sx] -> dst [nf][sy/2][sx/2] (1D: sy = 1 stays 1), children
+   summed row by row */
+static void coarsen2(int dim, int nf, int sx, int sy, const double *src, double *dst)
+{
+    int cx = sx / 2, cy = (dim == 2) ? sy / 2 : 1, rr = (dim == 2) ? 2 : 1;
+    double inv = 1.0 / (double)(2 * rr);
+    for (int f = 0; f < nf; f++)
+        for (int b = 0; b < cy; b++)
+            for (int a = 0; a < cx; a++) {
+                double s = 0.0;
+                for (int jj = 0; jj < rr; jj++)
+                    for (int ii = 0; ii < 2; ii++) s = s + src[((long)f * sy + b * rr + jj) * sx + 2 * a + ii];
+                dst[((long)f * cy + b) * cx + a] = s * inv;
+            }
+}
+
+static int error_estimate(OHier *h, int l)
+{
+    OLevel *L = &h->L[l];
+    const int dim = h->P.dim, eqn = h->P.eqn, m = h->m, nmed = h->nmed;
+    const int k = level_sub(h, l);
+    long n = 0;
+    for (int pk = 0; pk < L->np; pk++) n += (long)L->p[pk].nx * L->p[pk].ny;
+    free(h->tau);
+    h->tau = xcalloc((size_t)(n > 0 ? n : 1) * m, sizeof(double));
+    h->ntau = n;
+    long o = 0;
+    for (int pk = 0; pk < L->np; pk++) {
+        const OPatch *p = &L->p[pk];
+        const int ne = p->nx + (p->nx & 1), me = (dim == 2) ? p->ny + (p->ny & 1) : 1;
+        const int g = (dim == 2) ? 4 : 0;
+        const int ex = ne + 8, ey = me + 2 * g;
+        double *E = xcalloc((size_t)m * ex * ey, sizeof(double));
+        double *EM = xcalloc((size_t)nmed * ex * ey, sizeof(double));
+        for (int sj = 0; sj < ey; sj++)
+            for (int si = 0; si < ex; si++) {
+                int I = p->ilo + si - 4, J = p->jlo + sj - g;
+                double v[3], sg[3], md[2];
+                if (level_value(h, l, I, J, k, v)) {
+                    free(E);
+                    free(EM);
+                    return 1;
+                }
+                for (int f = 0; f < m; f++) E[((long)f * ey + sj) * ex + si] = v[f];
+                map_bc(h, l, &I, &J, sg);
+                medium_at(h, l, I, J, md);
+                for (int f = 0; f < nmed; f++) EM[((long)f * ey + sj) * ex + si] = md[f];
+            }
+        /* fine: two steps of dt */
+        const int f1x = ne + 4, f1y = (dim == 2) ? me + 4 : 1;
+        double *F1 = xcalloc((size_t)m * f1x * f1y, sizeof(double));
+        step_patch(dim, eqn, f1x, f1y, E, EM, L->dt, L->dx, L->dy, F1, NULL);
+        double *M1 = xcalloc((size_t)nmed * f1x * f1y, sizeof(double));
+        for (int f = 0; f < nmed; f++)
+            for (int j = 0; j < f1y; j++)
+                for (int i = 0; i < f1x; i++)
+                    M1[((long)f * f1y + j) * f1x + i] = EM[((long)f * ey + j + (g ? 2 : 0)) * ex + i + 2];
+        double *F2 = xcalloc((size_t)m * ne * me, sizeof(double));
+        step_patch(dim, eqn, ne, me, F1, M1, L->dt, L->dx, L->dy, F2, NULL);
+        /* coarse: one step of 2 dt on the extended patch coarsened by 2 */
+        const int cx = ex / 2, cy = (dim == 2) ? ey / 2 : 1;
+        double *C = xcalloc((size_t)m * cx * cy, sizeof(double));
+        double *CM = xcalloc((size_t)nmed * cx * cy, sizeof(double));
+        coarsen2(dim, m, ex, ey, E, C);
+        coarsen2(dim, nmed, ex, ey, EM, CM);
+        const int nc = ne / 2, mc = (dim == 2) ? me / 2 : 1;
+        double *C1 = xcalloc((size_t)m * nc * mc, sizeof(double));
+        step_patch(dim, eqn, nc, mc, C, CM, 2.0 * L->dt, 2.0 * L->dx, 2.0 * L->dy, C1, NULL);
+        double *FC = xcalloc((size_t)m * nc * mc, sizeof(double));
+        coarsen2(dim, m, ne, me, F2, FC);
+        for (int j = 0; j < p->ny; j++)
+            for (int i = 0; i < p->nx; i++) {
+                int a = i / 2, b = (dim == 2) ? j / 2 : 0;
+                for (int f = 0; f < m; f++) {
+                    long c = ((long)f * mc + b) * nc + a;
+                    h->tau[(o + (long)j * p->nx + i) * m + f] = (FC[c] - C1[c]) / 6.0;
+                }
+            }
+        o += (long)p->nx * p->ny;
+        free(E);
+        free(EM);
+        free(F1);
+        free(M1);
+        free(F2);
+        free(C);
+        free(CM);
+        free(C1);
+        free(FC);
+    }
+    return 0;
+}
+
+/* exported: the error estimate of level l at its current time, laid out as
+   orc_read_level lays out the state (per patch [m][ny][nx], patches in
+   order); n = capacity in doubles; returns 0, or 1 on error */
+int orc_error_estimate(void *hv, int level, double *tau_out, long n)
+{
+    OHier *h = hv;
+    if (level < 0 || level >= h->P.nlevels) return 1;
+    if (error_estimate(h, level)) return 1;
+    if (n < h->ntau * h->m) return 1;
+    long o = 0, c = 0;
+    for (int pk = 0; pk < h->L[level].np; pk++) {
+        const OPatch *p = &h->L[level].p[pk];
+        long np = (long)p->nx * p->ny;
+        for (int f = 0; f < h->m; f++)
+            for (long e = 0; e < np; e++) tau_out[o++] = h->tau[(c + e) * h->m + f];
+        c += np;
+    }
+    return 0;
+}
+
 /* flags of the interior cells of level l at its current time, in patch
    order, row-major within a patch.  Window: tau in [t, T],
    T = min(t + tf - ts, tf); value = max over the window of |qhat . q|. */
@@ -1244,7 +1406,10 @@ static long flag_level(OHier *h, int l, double tol, unsigned char *flags)
                 } else if (h->P.flag_mode == O_SURFACE) {
                     val = fabs(Q[0]);  /* perturbation of the surface (first component) */
                 } else if (S >= 2 && h->snaps) {
-                    if (h->P.flag_mode == O_BRACKET) {
+                    if (h->P.flag_mode == O_ERROR) {
+                        const double *tq = &h->tau[o * h->m];
+                        for (int n = nlo; n <= nhi; n++) val = fmax(val, adj_dot_snap(h, n, x, y, tq));
+                    } else if (h->P.flag_mode == O_BRACKET) {
                         for (int n = nlo; n <= nhi; n++) val = fmax(val, adj_dot_snap(h, n, x, y, Q));
                     } else {
                         val = fmax(adj_dot_time(h, t, x, y, Q), adj_dot_time(h, T, x, y, Q));
@@ -1268,6 +1433,7 @@ int orc_flag(void *hv, int level, double tol, unsigned char *flags, long *nflag)
     OHier *h = hv;
     if (level < 0 || level >= h->P.nlevels) return 1;
     if (h->P.flag_mode == O_DIFF && fill_ghosts(h, level, level_sub(h, level))) return 1;
+    if (h->P.flag_mode == O_ERROR && error_estimate(h, level)) return 1;
     long c = flag_level(h, level, tol, flags);
     if (nflag) *nflag = c;
     return 0;
@@ -1459,7 +1625,8 @@ static int regrid_from(OHier *h, int l, int init)
         long ncell = 0;
         for (int k = 0; k < C->np; k++) ncell += (long)C->p[k].nx * C->p[k].ny;
         unsigned char *pf = xcalloc(ncell, 1);
-        if (h->P.flag_mode == O_DIFF && fill_ghosts(h, lev, level_sub(h, lev))) {
+        if ((h->P.flag_mode == O_DIFF && fill_ghosts(h, lev, level_sub(h, lev))) ||
+            (h->P.flag_mode == O_ERROR && error_estimate(h, lev))) {
             free(pf);
             return 1;
         }
@@ -1487,10 +1654,14 @@ static int regrid_from(OHier *h, int l, int init)
                         if (ii >= 0 && ii < N && jj >= 0 && jj < M) fb[(long)jj * N + ii] = 1;
             }
         /* proper nesting: a cell may be refined only if every cell within
-           2 cells of it is covered by this level (outside the domain counts
-           as covered) */
+           nw cells of it is covered by this level (outside the domain counts
+           as covered): nw = 2 for the ghost ring of 2 fine cells; the error
+           estimate's ring of 4 fine cells takes nw = ceil(4 / r) + 1 (3 for
+           r = 2, 3), so that its interpolation stencils stay on this level */
         unsigned char *nest = xcalloc((size_t)N * M, 1);
-        int nw = 2, nwy = (dim == 2) ? 2 : 0;
+        int nw = 2;
+        if (h->P.flag_mode == O_ERROR && (4 + r - 1) / r + 1 > nw) nw = (4 + r - 1) / r + 1;
+        int nwy = (dim == 2) ? nw : 0;
         for (int j = 0; j < M; j++)
             for (int i = 0; i < N; i++) {
                 int ok = 1;
@@ -1592,6 +1763,15 @@ int orc_set_layout(void *hv, int level, int np, const int *boxes)
         alloc_patch(h, p);
         fill_patch_medium(h, level, p);
     }
+    return 0;
+}
+
+/* exported: set the step counter of a level (its time t0 + nstep * dt) */
+int orc_set_nstep(void *hv, int level, long nstep)
+{
+    OHier *h = hv;
+    if (level < 0 || level >= h->P.nlevels || nstep < 0) return 1;
+    h->L[level].nstep = nstep;
     return 0;
 }
 

@@ -70,6 +70,8 @@ def lib():
             L.orc_regrid.argtypes = [vp, i, i]
             L.orc_advance.argtypes = [vp, i, dp]
             L.orc_flag.argtypes = [vp, i, d, P(ctypes.c_ubyte), P(ctypes.c_long)]
+            L.orc_error_estimate.argtypes = [vp, i, dp, ctypes.c_long]
+            L.orc_set_nstep.argtypes = [vp, i, ctypes.c_long]
             L.orc_npatches.argtypes = [vp, i]
             L.orc_get_patches.argtypes = [vp, i, P(ctypes.c_int)]
             L.orc_level_dt.restype = d
@@ -224,6 +226,17 @@ class OracleHierarchy:
         lib().orc_flag(self.h, level, tol, out.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)), ctypes.byref(cnt))
         return out[:n], cnt.value
 
+    def error_estimate(self, level: int) -> np.ndarray:
+        """Richardson estimate tau of one step's local error on level
+        `level` at its current time, laid out as read_level (per patch
+        [m][ny][nx])."""
+        b = self.patches(level)
+        n = int(np.sum(b[:, 2].astype(np.int64) * b[:, 3])) * self.m if len(b) else 0
+        out = np.zeros(max(n, 1))
+        if lib().orc_error_estimate(self.h, level, _dp(out), out.size):
+            raise RuntimeError("orc_error_estimate failed: " + self.error())
+        return out[:n]
+
     def set_gauges(self, xs, ys=None):
         """Points recorded after every level-0 step."""
         xs = np.ascontiguousarray(xs, dtype=np.float64)
@@ -278,6 +291,11 @@ class OracleHierarchy:
         b = np.ascontiguousarray(np.asarray(boxes, dtype=np.int32).reshape(-1, 4))
         if lib().orc_set_layout(self.h, level, b.shape[0], b.ctypes.data_as(ctypes.POINTER(ctypes.c_int))):
             raise RuntimeError("orc_set_layout failed")
+
+    def set_level_time(self, level: int, nstep: int):
+        """Set the step counter of a level (its time is t0 + nstep * dt)."""
+        if lib().orc_set_nstep(self.h, level, int(nstep)):
+            raise RuntimeError("orc_set_nstep failed")
 
     def fill_ghosts(self, level: int):
         rc = lib().orc_fill_ghosts(self.h, level)
