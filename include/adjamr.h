@@ -62,8 +62,21 @@ enum { ADJAMR_BC_EXTRAP = 0, ADJAMR_BC_WALL = 1, ADJAMR_BC_PERIODIC = 2 };
  * centred difference |q_f(i+1) - q_f(i-1)| of some component in some
  * direction exceeds tol (Sec. 5.2.4, "pressure-flagging"; neighbours from the
  * level's ghost cells at the current time); SURFACE when |q_0| exceeds tol
- * (Sec. 5.3, "surface-flagging").  The standard flaggers need no adjoint. */
-enum { ADJAMR_FLAG_BRACKET_MAX = 0, ADJAMR_FLAG_LINEAR = 1, ADJAMR_FLAG_DIFFERENCE = 2, ADJAMR_FLAG_SURFACE = 3 };
+ * (Sec. 5.3, "surface-flagging").  The standard flaggers need no adjoint.
+ * ERROR (Sec. 7, the refinement the paper proposes as future work: the
+ * forward solution's error estimated by Richardson extrapolation, its effect
+ * on J by the adjoint) flags a cell when the maximum over the bracketing
+ * snapshots of |q^ . tau| exceeds tol, tau being the cell's estimate of one
+ * step's local error (adjamr_error_estimate).  It needs the adjoint, and it
+ * nests refined levels ceil(4/r) + 1 cells of the coarser level deep (3 for
+ * r = 2, 3) instead of 2, so that the estimate's ring stays on that level. */
+enum {
+    ADJAMR_FLAG_BRACKET_MAX = 0,
+    ADJAMR_FLAG_LINEAR = 1,
+    ADJAMR_FLAG_DIFFERENCE = 2,
+    ADJAMR_FLAG_SURFACE = 3,
+    ADJAMR_FLAG_ERROR = 4
+};
 
 enum { ADJAMR_MEDIUM_LAYERED = 1, ADJAMR_MEDIUM_DENSE = 2 };
 
@@ -266,6 +279,21 @@ adjamr_status adjamr_get_patches(adjamr_ctx *ctx, int level, adjamr_patch *out, 
 adjamr_status adjamr_read_level(adjamr_ctx *ctx, int level, double *dst, size_t cap);
 /* Overwrite the interior state of a level (same layout). */
 adjamr_status adjamr_write_level(adjamr_ctx *ctx, int level, const double *src, size_t count);
+
+/* Richardson estimate tau of one step's local error on `level` at its current
+ * time (Sec. 7, future work: the error estimate that adjoint-weighted flagging
+ * would weigh; ADJAMR_FLAG_ERROR flags with it).  Every patch is extended to
+ * even extents with a ring of 4 cells (filled as ghost cells are: the level's
+ * own cells, else the coarse space-time interpolation, boundary-mapped),
+ * advanced two steps of dt, and, coarsened by 2 in every direction (mean of
+ * the children, medium included), one step of 2 dt;
+ *   tau = (coarsened two-step state - coarse step) / 6
+ * on every 2 x 2 (1D: 2) block, the local error of one step of a
+ * second-order method being C dx^3 and that of the coarse step 8 C dx^3.
+ * Layout as adjamr_read_level; cap in doubles.  A level above level 0 must be
+ * nested as ADJAMR_FLAG_ERROR nests it (else ADJAMR_ENEST).  The step
+ * counters and the CFL record are unchanged.  Synchronises. */
+adjamr_status adjamr_error_estimate(adjamr_ctx *ctx, int level, double *dst, size_t cap);
 
 /* Fill the ghost cells of `level` for its current time (as a step would). */
 adjamr_status adjamr_fill_ghosts(adjamr_ctx *ctx, int level);

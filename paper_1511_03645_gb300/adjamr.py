@@ -97,7 +97,8 @@ SYMBOLS = [
     "adjamr_init_grid_hierarchy", "adjamr_set_medium", "adjamr_load_adjoint_snapshots", "adjamr_solve_adjoint",
     "adjamr_set_adjoint", "adjamr_adjoint_read", "adjamr_adjoint_release", "adjamr_regrid",
     "adjamr_advance_level", "adjamr_flag_cells", "adjamr_integrate_functional", "adjamr_get_patches",
-    "adjamr_read_level", "adjamr_write_level", "adjamr_fill_ghosts", "adjamr_read_patch_ghosted",
+    "adjamr_read_level", "adjamr_write_level", "adjamr_error_estimate", "adjamr_fill_ghosts",
+    "adjamr_read_patch_ghosted",
     "adjamr_step_level_only", "adjamr_get_stats", "adjamr_set_timing", "adjamr_set_level_kernel",
     "adjamr_substep_wait_selftest", "adjamr_set_gauges",
     "adjamr_read_gauges", "adjamr_cluster_boxes", "adjamr_time_info",
@@ -145,6 +146,7 @@ def load(build_if_missing: bool = True):
             "adjamr_integrate_functional": [vp, P(Target), dp],
             "adjamr_get_patches": [vp, i, P(Patch), i, ip],
             "adjamr_read_level": [vp, i, dp, sz],
+            "adjamr_error_estimate": [vp, i, dp, sz],
             "adjamr_write_level": [vp, i, dp, sz],
             "adjamr_fill_ghosts": [vp, i],
             "adjamr_read_patch_ghosted": [vp, i, i, dp, dp],
@@ -424,6 +426,15 @@ class Hierarchy:
         n = int(np.sum(b[:, 2].astype(np.int64) * b[:, 3])) * self.m if len(b) else 0
         out = np.zeros(max(n, 1))
         _check(load().adjamr_read_level(self.h, level, _dp(out), out.size), self.h, "read_level")
+        return out[:n]
+
+    def error_estimate(self, level: int) -> np.ndarray:
+        """Richardson estimate of one step's local error on the level at its
+        current time, laid out as read_level."""
+        b = self.patches(level)
+        n = int(np.sum(b[:, 2].astype(np.int64) * b[:, 3])) * self.m if len(b) else 0
+        out = np.zeros(max(n, 1))
+        _check(load().adjamr_error_estimate(self.h, level, _dp(out), out.size), self.h, "error_estimate")
         return out[:n]
 
     def write_level(self, level: int, data):

@@ -1045,6 +1045,169 @@ constexpr size_t kPinHead = 64;          // count, bounding box and list counter
 constexpr long long kFlagItemsMax = (long long)1 << 26;  // longest (cell, block) list of the two-pass flags
 constexpr size_t kPinBits = 256 << 10;   // bitmaps up to this size come back with the count
 
+// Richardson error estimate of level l at its current time (flag mode
+// ADJAMR_FLAG_ERROR): into *tau (the level's arena layout, m fields, taken
+// from the block cache; the caller returns it with cput).  Every patch is
+// extended to even extents with a ring of 4 cells (values as ghost cells get
+// them), advanced two steps of dt by the step kernel (the first over the
+// region widened by 2, the second over the even patch), coarsened by 2 and
+// advanced one step of 2 dt (dt/dx unchanged), and tau = (coarsened two-step
+// state - coarse step) / 6 on every 2^d block.
+adjamr_status error_estimate(adjamr_ctx *c, int l, double **tau)
+{
+    Level &L = c->L[l];
+    const adjamr_params &P = c->P;
+    const int dim = P.dim, m = c->m;
+    *tau = nullptr;
+    if (L.patches.empty()) return ADJAMR_OK;
+    const int kx = (dim == 2) ? 16 : 128, ky = (dim == 2) ? 8 : 1;
+    std::vector<ErrEstPatch> ep;
+    std::vector<long long> epre{0}, cpre{0};
+    std::vector<PatchDesc> p1, p2, pc;
+    std::vector<WorkItem> w1, w2, wc;
+    const double dtdx = L.dt / L.dx, dtdy = (dim == 2) ? L.dt / L.dy : 0.0;
+    auto tiles = [&](std::vector<WorkItem> &w, int k, int nx, int ny) {
+        const int tx = tile_count(nx, kx), ty = tile_count(ny, ky);
+        for (int b = 0; b < ty; b++)
+            for (int a = 0; a < tx; a++)
+                w.push_back({k, tile_off(nx, tx, a), tile_off(ny, ty, b), (unsigned short)tile_len(nx, tx, a),
+                             (unsigned short)tile_len(ny, ty, b)});
+    };
+    long long nE = 0, nC = 0;
+    for (const HPatch &h : L.patches) {
+        ErrEstPatch e{};
+        e.ilo = h.ilo;
+        e.jlo = h.jlo;
+        e.nx = h.nx;
+        e.ny = h.ny;
+        e.ne = h.nx + (h.nx & 1);
+        e.me = (dim == 2) ? h.ny + (h.ny & 1) : 1;
+        e.asx = h.sx;
+        e.abase = h.base;
+        const int ex = e.ne + 8, ey = (dim == 2) ? e.me + 8 : 1;
+        const int cx = e.ne / 2 + 4, cy = (dim == 2) ? e.me / 2 + 4 : 1;
+        e.ebase = nE;
+        e.cbase = nC;
+        PatchDesc d{};
+        d.dtdx = dtdx;
+        d.dtdy = dtdy;
+        d.hx = 0.5 * dtdx;
+        d.hy = 0.5 * dtdy;
+        // first fine step: the even patch widened by 2 cells, ring = E's outer 2
+        d.ilo = h.ilo - 2;
+        d.jlo = (dim == 2) ? h.jlo - 2 : 0;
+        d.nx = e.ne + 4;
+        d.ny = (dim == 2) ? e.me + 4 : 1;
+        d.sx = ex;
+        d.sy = ey;
+        d.base = e.ebase;
+        tiles(w1, (int)p1.size(), d.nx, d.ny);
+        p1.push_back(d);
+        // second fine step: the even patch, its ring = the first step's border
+        d.ilo = h.ilo;
+        d.jlo = h.jlo;
+        d.nx = e.ne;
+        d.ny = e.me;
+        d.sy = (dim == 2) ? e.me + 4 : 1;
+        d.base = e.ebase + ((dim == 2) ? 2LL * ex : 0LL) + 2;
+        tiles(w2, (int)p2.size(), d.nx, d.ny);
+        p2.push_back(d);
+        // coarse step (2 dt over 2 dx: the same dt/dx)
+        d.nx = e.ne / 2;
+        d.ny = (dim == 2) ? e.me / 2 : 1;
+        d.sx = cx;
+        d.sy = cy;
+        d.base = e.cbase;
+        tiles(wc, (int)pc.size(), d.nx, d.ny);
+        pc.push_back(d);
+        ep.push_back(e);
+        nE += (long long)ex * ey;
+        nC += (long long)cx * cy;
+        epre.push_back(nE);
+        cpre.push_back(nC);
+    }
+    std::vector<size_t> offs;
+    char *meta = nullptr;
+    CKR(c, upload_packed(c,
+                         {{ep.data(), sizeof(ErrEstPatch) * ep.size()},
+                          {epre.data(), sizeof(long long) * epre.size()},
+                          {cpre.data(), sizeof(long long) * cpre.size()},
+                          {p1.data(), sizeof(PatchDesc) * p1.size()},
+                          {p2.data(), sizeof(PatchDesc) * p2.size()},
+                          {pc.data(), sizeof(PatchDesc) * pc.size()},
+                          {w1.data(), sizeof(WorkItem) * w1.size()},
+                          {w2.data(), sizeof(WorkItem) * w2.size()},
+                          {wc.data(), sizeof(WorkItem) * wc.size()}},
+                         &meta, offs));
+    const int per = 2 * m + c->naux + c->nmed;
+    double *buf = nullptr;
+    unsigned long long *cfl = nullptr;
+    double *t = nullptr;
+    CKR(c, cget(c, &buf, (size_t)per * (nE + nC)));
+    CKR(c, cget(c, &cfl, 1));
+    CKR(c, cget(c, &t, (size_t)m * L.ncell));
+    ErrEstArgs a{};
+    a.ep = reinterpret_cast<const ErrEstPatch *>(meta + offs[0]);
+    a.eprefix = reinterpret_cast<const long long *>(meta + offs[1]);
+    a.cprefix = reinterpret_cast<const long long *>(meta + offs[2]);
+    a.np = (int)ep.size();
+    a.dim = dim;
+    a.m = m;
+    a.eqn = P.eqn;
+    a.nE = nE;
+    a.nC = nC;
+    a.E = buf;
+    a.F = a.E + (size_t)m * nE;
+    a.auxE = a.F + (size_t)m * nE;
+    a.medE = a.auxE + (size_t)c->naux * nE;
+    a.C = a.medE + (size_t)c->nmed * nE;
+    a.C1 = a.C + (size_t)m * nC;
+    a.auxC = a.C1 + (size_t)m * nC;
+    a.medC = a.auxC + (size_t)c->naux * nC;
+    const int *oc = nullptr;
+    const double *qo = nullptr, *qn = nullptr;
+    long long sc = 0;
+    int r = 1, k = 0;
+    LevelIdx gc = idx_of(c, l);
+    if (l > 0) {
+        Level &C = c->L[l - 1];
+        oc = C.d_owner;
+        gc = idx_of(c, l - 1);
+        qo = C.q[C.cur];
+        qn = C.q[1 - C.cur];
+        sc = C.ncell;
+        r = P.ratio[l - 1];
+        k = (int)(L.nstep - C.nstep * r);
+    }
+    adjamr_status st = ADJAMR_OK;
+    cudaError_t e = launch_errest_fill(a, idx_of(c, l), L.d_owner, L.q[L.cur], L.ncell, oc, gc, r, qo, qn, sc, k,
+                                       L.d_med, geom_of(c, l), c->d_err, c->s);
+    const PatchDesc *d1 = reinterpret_cast<const PatchDesc *>(meta + offs[3]);
+    const PatchDesc *d2 = reinterpret_cast<const PatchDesc *>(meta + offs[4]);
+    const PatchDesc *dc = reinterpret_cast<const PatchDesc *>(meta + offs[5]);
+    if (e == cudaSuccess)
+        e = launch_step(dim, P.eqn, kx, ky, a.E, a.F, a.auxE, nE, d1,
+                        reinterpret_cast<const WorkItem *>(meta + offs[6]), (int)w1.size(), 0, cfl, c->s);
+    if (e == cudaSuccess)
+        e = launch_step(dim, P.eqn, kx, ky, a.F, a.E, a.auxE, nE, d2,
+                        reinterpret_cast<const WorkItem *>(meta + offs[7]), (int)w2.size(), 0, cfl, c->s);
+    if (e == cudaSuccess)
+        e = launch_step(dim, P.eqn, kx, ky, a.C, a.C1, a.auxC, nC, dc,
+                        reinterpret_cast<const WorkItem *>(meta + offs[8]), (int)wc.size(), 0, cfl, c->s);
+    if (e == cudaSuccess) e = launch_errest_tau(a, L.d_prefix, L.ninterior, t, L.ncell, c->s);
+    c->st.kernel_launches += 6;
+    cput(c, buf);
+    cput(c, cfl);
+    cput(c, meta);
+    if (e != cudaSuccess) {
+        cput(c, t);
+        c->err = std::string("error estimate: ") + cudaGetErrorString(e);
+        return ADJAMR_ECUDA;
+    }
+    *tau = t;
+    return st;
+}
+
 adjamr_status flag_dense(adjamr_ctx *c, int l, double tol, uint64_t *d_bits, int pitch64, unsigned char *d_patchflags,
                          long long *nflag_out, int *bbox_out = nullptr);
 adjamr_status flag_readback(adjamr_ctx *c, int l, uint64_t *d_bits, int pitch64, bool twopass, long long *nflag_out,
@@ -1063,6 +1226,17 @@ adjamr_status grow_flag_list(adjamr_ctx *c, long long n)
 
 // Rebuild levels base+1 .. nlevels-1 top-down (Sec. 3, regridding).
 void harvest_timing(adjamr_ctx *c);
+
+// Proper-nesting distance of a refinement by r, in cells of the coarser
+// level: the ghost ring of 2 fine cells needs 2; the error estimate's ring of
+// 4 fine cells (flag mode ADJAMR_FLAG_ERROR) ceil(4 / r) + 1, so that its
+// interpolation stencils stay on the coarser level.
+int nest_width(const adjamr_ctx *c, int r)
+{
+    int nw = 2;
+    if (c->P.flag_mode == ADJAMR_FLAG_ERROR && r > 0) nw = std::max(nw, (4 + r - 1) / r + 1);
+    return nw;
+}
 
 adjamr_status regrid_body(adjamr_ctx *c, int base, int init, bool side_flags = false);
 
@@ -1299,7 +1473,8 @@ adjamr_status regrid_body(adjamr_ctx *c, int base, int init, bool side_flags)
             // word boundary.  Clustering starts by shrinking to the flags'
             // bounding box, so any such window gives the same boxes as the
             // whole index space.
-            const int grow = P.buffer + 2;
+            const int nw = nest_width(c, r);
+            const int grow = P.buffer + nw;
             const int wi0 = std::max(0, bb[0] - grow) & ~63, wi1 = std::min(N - 1, bb[1] + grow);
             const int wj0 = (dim == 2) ? std::max(0, bb[2] - grow) : 0;
             const int wj1 = (dim == 2) ? std::min(M - 1, bb[3] + grow) : 0;
@@ -1322,7 +1497,7 @@ adjamr_status regrid_body(adjamr_ctx *c, int base, int init, bool side_flags)
             c->st.regrid_phase_ms[1] += wcopy;
             c->st.cluster_host_ms -= wcopy;
             auto ts = std::chrono::steady_clock::now();
-            // buffer, nesting mask (every cell within 2 cells covered by this level)
+            // buffer, nesting mask (every cell within nw cells covered by this level)
             dilate_bits(fl, P.buffer, dim == 2 ? P.buffer : 0, c->h_tmp);
             unc.reset(wN, wM);
             for (int j = 0; j < wM; j++) {
@@ -1337,9 +1512,9 @@ adjamr_status regrid_body(adjamr_ctx *c, int base, int init, bool side_flags)
                 for (int j = b0; j <= b1; j++) row_clear(unc.row(j - wj0), a0 - wi0, a1 - wi0);
             }
             // cells beyond the window but inside the domain: the window reaches
-            // 2 cells past every flag the buffer can create, so they never
+            // nw cells past every flag the buffer can create, so they never
             // decide a flagged cell's nesting
-            dilate_bits(unc, 2, dim == 2 ? 2 : 0, c->h_tmp);
+            dilate_bits(unc, nw, dim == 2 ? nw : 0, c->h_tmp);
             for (size_t k = 0; k < fl.w.size(); k++) fl.w[k] &= ~unc.w[k];
             c->st.cluster_phase_ms[0] += ms_since(ts);
             ts = std::chrono::steady_clock::now();
@@ -1569,7 +1744,19 @@ adjamr_status flag_dense(adjamr_ctx *c, int l, double tol, uint64_t *d_bits, int
         const int sub = l > 0 ? (int)(L.nstep - c->L[l - 1].nstep * P.ratio[l - 1]) : 0;
         TRY(ghost_fill(c, l, sub));
     }
-    const bool dense = d_bits && !d_patchflags && P.flag_mode == ADJAMR_FLAG_BRACKET_MAX && c->adj &&
+    // error flagging: the bracket rule on the error estimate instead of the state
+    double *tau = nullptr;
+    struct TauRelease {
+        adjamr_ctx *c;
+        double *&t;
+        ~TauRelease() { if (t) cput(c, t); }
+    } tau_release{c, tau};
+    if (P.flag_mode == ADJAMR_FLAG_ERROR) {
+        TRY(error_estimate(c, l, &tau));
+        a.q = tau;
+        a.mode = ADJAMR_FLAG_BRACKET_MAX;
+    }
+    const bool dense = d_bits && !d_patchflags && a.mode == ADJAMR_FLAG_BRACKET_MAX && c->adj &&
                        c->adj->d_bmax && a.S >= 2;
     if (dense) {
         TRY(flag_tables(c, l));
@@ -2011,7 +2198,7 @@ adjamr_status create_impl(const adjamr_params *p, adjamr_ctx **out)
         if (p->ratio[l] < 2 || p->ratio[l] > kMaxSubsteps) return ADJAMR_EINVAL;
     for (int k = 0; k < 4; k++)
         if (p->bc[k] < 0 || p->bc[k] > 2) return ADJAMR_EINVAL;
-    if (p->flag_mode < ADJAMR_FLAG_BRACKET_MAX || p->flag_mode > ADJAMR_FLAG_SURFACE) return ADJAMR_EINVAL;
+    if (p->flag_mode < ADJAMR_FLAG_BRACKET_MAX || p->flag_mode > ADJAMR_FLAG_ERROR) return ADJAMR_EINVAL;
     if (p->launch_mode < ADJAMR_LAUNCH_WORKLIST || p->launch_mode > ADJAMR_LAUNCH_SUBSTEPS) return ADJAMR_EINVAL;
     if (p->reflux != 0 && p->reflux != 1) return ADJAMR_EINVAL;
     adjamr_ctx *c = new (std::nothrow) adjamr_ctx();
@@ -2172,7 +2359,8 @@ adjamr_status create_impl(const adjamr_params *p, adjamr_ctx **out)
 }
 
 // interior of a level, patch by patch, field-major per patch
-adjamr_status read_level_impl(adjamr_ctx *c, int l, double *dst, size_t cap, bool write, const double *src)
+adjamr_status read_level_impl(adjamr_ctx *c, int l, double *dst, size_t cap, bool write, const double *src,
+                              const double *from = nullptr)
 {
     Level &L = c->L[l];
     size_t need = (size_t)c->m * L.ninterior;
@@ -2182,7 +2370,7 @@ adjamr_status read_level_impl(adjamr_ctx *c, int l, double *dst, size_t cap, boo
     }
     if (L.ncell == 0) return ADJAMR_OK;
     std::vector<double> host((size_t)c->m * L.ncell);
-    double *buf = L.q[L.cur];
+    const double *buf = from ? from : L.q[L.cur];
     CKR(c, cudaMemcpyAsync(host.data(), buf, host.size() * sizeof(double), cudaMemcpyDeviceToHost, c->s));
     CKR(c, cudaStreamSynchronize(c->s));
     size_t o = 0;
@@ -2195,7 +2383,7 @@ adjamr_status read_level_impl(adjamr_ctx *c, int l, double *dst, size_t cap, boo
                     else dst[o] = host[idx];
                 }
     if (write) {
-        CKR(c, cudaMemcpyAsync(buf, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, c->s));
+        CKR(c, cudaMemcpyAsync(L.q[L.cur], host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, c->s));
         CKR(c, cudaStreamSynchronize(c->s));
     }
     return ADJAMR_OK;
@@ -2687,6 +2875,25 @@ adjamr_status adjamr_write_level(adjamr_ctx *ctx, int level, const double *src, 
     if (!ctx || level < 0 || level >= ctx->P.nlevels || (!src && count)) return ADJAMR_EINVAL;
     try {
         return read_level_impl(ctx, level, nullptr, count, true, src);
+    } catch (...) {
+        return ADJAMR_ENOMEM;
+    }
+}
+
+adjamr_status adjamr_error_estimate(adjamr_ctx *ctx, int level, double *dst, size_t cap)
+{
+    if (!ctx || level < 0 || level >= ctx->P.nlevels || (!dst && cap)) return ADJAMR_EINVAL;
+    if (!ctx->have_medium) {
+        ctx->err = "error estimate: no medium set";
+        return ADJAMR_ESTATE;
+    }
+    try {
+        double *tau = nullptr;
+        TRY(error_estimate(ctx, level, &tau));
+        adjamr_status st = read_level_impl(ctx, level, dst, cap, false, nullptr, tau);
+        if (tau) cput(ctx, tau);
+        if (st != ADJAMR_OK) return st;
+        return check_err(ctx);
     } catch (...) {
         return ADJAMR_ENOMEM;
     }

@@ -375,6 +375,37 @@ struct LevelIdx {
     int bc[4];
 };
 
+// Richardson error estimate of one level (flag mode ADJAMR_FLAG_ERROR).
+// Every patch of the level is extended to even extents (ne, me) (1D: me = 1)
+// with a ring of 4 cells: storage "E", pitch ne + 8, me + 8 rows (1D: one),
+// at ebase; the same coarsened by 2: storage "C", pitch ne/2 + 4, me/2 + 4
+// rows (1D: one), at cbase.  abase/asx: the patch in the level arena.
+struct ErrEstPatch {
+    int ilo, jlo, nx, ny;
+    int ne, me, asx, pad;
+    long long ebase, cbase, abase;
+};
+struct ErrEstArgs {
+    const ErrEstPatch *ep;
+    const long long *eprefix, *cprefix;  // [np + 1]: E / C storage cells before patch p
+    int np, dim, m, eqn;
+    long long nE, nC;                    // E / C storage cells (the buffers' field strides)
+    double *E, *F, *auxE, *medE;         // E storage: state, first-step state, coefficients
+    double *C, *C1, *auxC, *medC;        // C storage
+};
+// the extended patches (state as ghost cells get it at substep k with time
+// fraction th of level l - 1: q the level's current state, owner its owner
+// map; qo / qn, owner_c the coarser level's) and their coefficients; then the
+// coarsened copies (mean of the children, medium included).  err |= 1 where
+// an interpolation stencil leaves the coarser level.
+cudaError_t launch_errest_fill(const ErrEstArgs &a, LevelIdx g, const int *owner, const double *q, long long sq,
+                               const int *owner_c, LevelIdx gc, int r, const double *qo, const double *qn,
+                               long long sc, int k, const MediumDev *md, LevelGeom geom, int *err, cudaStream_t s);
+// tau[f * st + arena cell] = (mean of the 2^d children of the two-step state
+// (in E) - the coarse step's (C1)) / 6 for every interior cell of the level
+cudaError_t launch_errest_tau(const ErrEstArgs &a, const long long *iprefix, long long ninterior, double *tau,
+                              long long st, cudaStream_t s);
+
 // Device-side regrid support.  owner[J*N + I] = arena index of interior cell
 // (I, J) of the level, or -1.  Prefix arrays have np+1 entries.
 cudaError_t launch_owner_fill(const PatchDesc *p, const long long *prefix, int np, long long ncells, LevelIdx g,

@@ -162,13 +162,11 @@ __device__ void medium_at(const MediumDev &md, const LevelGeom &g, int I, int J,
     }
 }
 
-__device__ void aux_cell(int eqn, int dim, const MediumDev &md, const LevelGeom &g, int I, int J, long long idx,
-                         double *aux, double *med, long long stride)
+// coefficients of a cell from the primary medium of the cell (c0), of its
+// x-neighbour below (cl) and of its y-neighbour below (cb)
+__device__ void aux_from_medium(int eqn, int dim, const double *c0, const double *cl, const double *cb, long long idx,
+                                double *aux, double *med, long long stride)
 {
-    double c0[2] = {0, 0}, cl[2] = {0, 0}, cb[2] = {0, 0};
-    medium_at(md, g, I, J, c0);
-    medium_at(md, g, I - 1, J, cl);
-    if (dim == 2) medium_at(md, g, I, J - 1, cb);
     med[idx] = c0[0];
     if (eqn == 0 || eqn == 1) med[stride + idx] = c0[1];
     if (eqn == 0 || eqn == 1) {
@@ -212,6 +210,16 @@ __device__ void aux_cell(int eqn, int dim, const MediumDev &md, const LevelGeom 
             aux[4 * stride + idx] = kGrav * c0[0];
         }
     }
+}
+
+__device__ void aux_cell(int eqn, int dim, const MediumDev &md, const LevelGeom &g, int I, int J, long long idx,
+                         double *aux, double *med, long long stride)
+{
+    double c0[2] = {0, 0}, cl[2] = {0, 0}, cb[2] = {0, 0};
+    medium_at(md, g, I, J, c0);
+    medium_at(md, g, I - 1, J, cl);
+    if (dim == 2) medium_at(md, g, I, J - 1, cb);
+    aux_from_medium(eqn, dim, c0, cl, cb, idx, aux, med, stride);
 }
 
 // the coefficients of every cell of the bordered index space (aux_cell's
@@ -455,6 +463,120 @@ __global__ void k_aux_patches(int eqn, const PatchDesc *__restrict__ pd, const l
         }
     }
     aux_cell(eqn, g.dim, *mdp, geom, I, J, idx, aux, med, stride);
+}
+
+// ---------------------------------------------------------------- error estimate (Sec. 7)
+// One thread per storage cell of the extended patches: the value as a ghost
+// cell gets it (the level's own cell where it has one, else the coarse
+// space-time interpolation), boundary-mapped, and the cell's coefficients.
+__global__ void k_errest_ext(ErrEstArgs a, LevelIdx g, const int *__restrict__ owner, const double *__restrict__ q,
+                             long long sq, const int *__restrict__ owner_c, LevelIdx gc, int r,
+                             const double *__restrict__ qo, const double *__restrict__ qn, long long sc, int k,
+                             double th, const MediumDev *__restrict__ md, LevelGeom geom, int *err)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.nE) return;
+    const int p = find_in_prefix(a.eprefix, a.np, t);
+    const ErrEstPatch P = a.ep[p];
+    const long long e = t - a.eprefix[p];
+    const int ex = P.ne + 8, ge = (a.dim == 2) ? 4 : 0;
+    const int sj = (int)(e / ex), si = (int)(e - (long long)sj * ex);
+    const int I0 = P.ilo + si - 4, J0 = (a.dim == 2) ? P.jlo + sj - ge : 0;
+    int I = I0, J = J0, f1, f2;
+    bc_map_dev(g, I, J, f1, f2);
+    GhostDesc d;
+    d.dst = 0;
+    d.src = d.cxm = d.cxp = d.cym = d.cyp = 0;
+    d.kind = 0;
+    d.signs = 0;
+    d.fx = d.fy = 0.0;
+    const int o = owner_at(owner, g, I, J);
+    if (o >= 0) {
+        d.src = o;
+    } else if (owner_c) {
+        if (!coarse_desc_dev(I, J, r, owner_c, gc, d)) atomicOr(err, 1);
+    } else {
+        atomicOr(err, 2);
+    }
+    d.signs |= f1 | (f2 << 1);
+    const long long idx = P.ebase + e;
+    for (int f = 0; f < a.m; f++) a.E[(long long)f * a.nE + idx] = ghost_value_direct(d, q, sq, qo, qn, sc, f, k, th, a.dim);
+    aux_cell(a.eqn, a.dim, *md, geom, I0, J0, idx, a.auxE, a.medE, a.nE);
+}
+
+// primary medium of coarsened cell (a, b) of patch P (coarse storage
+// coordinates): the mean of its children's, summed row by row
+__device__ void errest_coarse_medium(const ErrEstPatch &P, int dim, int nmed, const MediumDev &md,
+                                     const LevelGeom &geom, int ca, int cb, double *out)
+{
+    const int rr = (dim == 2) ? 2 : 1, ge = (dim == 2) ? 4 : 0;
+    const double inv = 1.0 / (double)(2 * rr);
+    double s[2] = {0.0, 0.0};
+    for (int jj = 0; jj < rr; jj++)
+        for (int ii = 0; ii < 2; ii++) {
+            double v[2] = {0.0, 0.0};
+            const int I = P.ilo + 2 * ca + ii - 4, J = (dim == 2) ? P.jlo + 2 * cb + jj - ge : 0;
+            medium_at(md, geom, I, J, v);
+            for (int f = 0; f < nmed; f++) s[f] = s[f] + v[f];
+        }
+    for (int f = 0; f < nmed; f++) out[f] = s[f] * inv;
+    if (nmed < 2) out[1] = 0.0;
+}
+
+// One thread per storage cell of the coarsened patches: the mean of the
+// children's state and medium, and the coefficients of that medium.
+__global__ void k_errest_coarse(ErrEstArgs a, const MediumDev *__restrict__ md, LevelGeom geom)
+{
+    pdl_wait();
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.nC) return;
+    const int p = find_in_prefix(a.cprefix, a.np, t);
+    const ErrEstPatch P = a.ep[p];
+    const long long e = t - a.cprefix[p];
+    const int cx = P.ne / 2 + 4, ex = P.ne + 8, rr = (a.dim == 2) ? 2 : 1;
+    const int b = (int)(e / cx), ca = (int)(e - (long long)b * cx);
+    const double inv = 1.0 / (double)(2 * rr);
+    const long long idx = P.cbase + e;
+    for (int f = 0; f < a.m; f++) {
+        double s = 0.0;
+        for (int jj = 0; jj < rr; jj++)
+            for (int ii = 0; ii < 2; ii++)
+                s = s + a.E[(long long)f * a.nE + P.ebase + (long long)(b * rr + jj) * ex + 2 * ca + ii];
+        a.C[(long long)f * a.nC + idx] = s * inv;
+    }
+    const int nmed = nmed_of(a.eqn);
+    double c0[2], cl[2], cb_[2] = {0.0, 0.0};
+    errest_coarse_medium(P, a.dim, nmed, *md, geom, ca, b, c0);
+    errest_coarse_medium(P, a.dim, nmed, *md, geom, ca - 1, b, cl);
+    if (a.dim == 2) errest_coarse_medium(P, a.dim, nmed, *md, geom, ca, b - 1, cb_);
+    aux_from_medium(a.eqn, a.dim, c0, cl, cb_, idx, a.auxC, a.medC, a.nC);
+}
+
+// One thread per interior cell of the level: tau of its 2 x 2 (1D: 2) block.
+__global__ void k_errest_tau(ErrEstArgs a, const long long *__restrict__ iprefix, long long n, double *tau,
+                             long long st)
+{
+    pdl_wait();
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int p = find_in_prefix(iprefix, a.np, t);
+    const ErrEstPatch P = a.ep[p];
+    const long long e = t - iprefix[p];
+    const int j = (int)(e / P.nx), i = (int)(e - (long long)j * P.nx);
+    const int ca = i / 2, cb = (a.dim == 2) ? j / 2 : 0;
+    const int rr = (a.dim == 2) ? 2 : 1, ge = (a.dim == 2) ? 4 : 0, gc = (a.dim == 2) ? 2 : 0, gy = gc;
+    const int ex = P.ne + 8, cx = P.ne / 2 + 4;
+    const double inv = 1.0 / (double)(2 * rr);
+    const long long dst = P.abase + (long long)(j + gy) * P.asx + (i + 2);
+    for (int f = 0; f < a.m; f++) {
+        double s = 0.0;
+        for (int jj = 0; jj < rr; jj++)
+            for (int ii = 0; ii < 2; ii++)
+                s = s + a.E[(long long)f * a.nE + P.ebase + (long long)(cb * rr + jj + ge) * ex + 2 * ca + ii + 4];
+        const double fc = s * inv;
+        const double c1 = a.C1[(long long)f * a.nC + P.cbase + (long long)(cb + gc) * cx + ca + 2];
+        tau[(long long)f * st + dst] = (fc - c1) / 6.0;
+    }
 }
 
 // ---------------------------------------------------------------- flagging
@@ -992,6 +1114,25 @@ cudaError_t launch_avg_build(const PatchDesc *p, const long long *aprefix, int n
     if (navg <= 0) return cudaSuccess;
     k_avg_build<<<nblk(navg), kT, 0, s>>>(p, aprefix, np, navg, dim, r, owner_c, gc, out, err);
     return cudaGetLastError();
+}
+
+cudaError_t launch_errest_fill(const ErrEstArgs &a, LevelIdx g, const int *owner, const double *q, long long sq,
+                               const int *owner_c, LevelIdx gc, int r, const double *qo, const double *qn,
+                               long long sc, int k, const MediumDev *md, LevelGeom geom, int *err, cudaStream_t s)
+{
+    if (a.nE <= 0 || a.nC <= 0) return cudaSuccess;
+    const double th = (r > 0) ? (double)k / (double)r : 0.0;  // as the ghost fill's, on the host
+    k_errest_ext<<<nblk(a.nE), kT, 0, s>>>(a, g, owner, q, sq, owner_c, gc, r, qo, qn, sc, k, th, md, geom, err);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_pdl(k_errest_coarse, dim3(nblk(a.nC)), dim3(kT), 0, s, a, md, geom);
+}
+
+cudaError_t launch_errest_tau(const ErrEstArgs &a, const long long *iprefix, long long ninterior, double *tau,
+                              long long st, cudaStream_t s)
+{
+    if (ninterior <= 0) return cudaSuccess;
+    return launch_pdl(k_errest_tau, dim3(nblk(ninterior)), dim3(kT), 0, s, a, iprefix, ninterior, tau, st);
 }
 
 cudaError_t launch_init_new(const PatchDesc *p, const long long *prefix, int np, long long ncells, LevelIdx g, int m,

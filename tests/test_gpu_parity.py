@@ -96,6 +96,40 @@ def test_uniform_grid_steps_match_oracle_bitwise(A, dim, eqn, bc):
     assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("dim,eqn,bc", CASES)
+def test_error_estimate_matches_oracle_bitwise(A, dim, eqn, bc):
+    """The Richardson error estimate (Sec. 7) of a uniform grid of ragged,
+    odd-sized patches (random medium and state, every boundary kind, after
+    two steps): identical to the oracle's."""
+    rng = np.random.default_rng(200 + 10 * dim + eqn)
+    N = 83 if dim == 2 else 301
+    M = N if dim == 2 else 1
+    if eqn in (W.EQ_SW, W.EQ_SW_ADJ):
+        fields = rng.uniform(100, 4000, (1, M, N))
+        L = 8e5
+    else:
+        fields = np.stack([rng.uniform(1, 3, (M, N)), rng.uniform(1, 30, (M, N))])
+        L = 8.0
+    wl = dense_wl(dim, eqn, N, fields, bc, L=L, tf=1.0)
+    wl.max_patch0 = 41 if dim == 2 else 121
+    q0 = rng.normal(size=(wl.m, M, N))
+    o = O.OracleHierarchy(wl, nlevels=1, with_qinit=False)
+    g = A.Hierarchy(wl, nlevels=1, with_qinit=False)
+    assert np.array_equal(g.patches(0), o.patches(0))
+    scatter_write(o, 0, q0)
+    scatter_write(g, 0, q0)
+    o.advance(2)
+    g.advance(2)
+    cu = g.stats()["cell_updates"]
+    a, b = g.error_estimate(0), o.error_estimate(0)
+    assert np.any(b != 0.0)
+    close(a, b)
+    assert np.array_equal(a, b)
+    # the estimate's steps are not forward steps
+    assert g.stats()["cell_updates"] == cu
+    assert np.array_equal(g.read_level(0), o.read_level(0))
+
+
 @pytest.mark.parametrize("tile", [(16, 8), (16, 16), (32, 16), (64, 8), (8, 8), (12, 8), (24, 12), (5, 3)])
 @pytest.mark.parametrize("mode", [0, 1, 2, 3])
 def test_tile_shapes_and_launch_modes_agree_bitwise(A, tile, mode):
@@ -163,17 +197,24 @@ def _compare_all(o, g, nlev):
                                    "p521", "p522", "p523", "p523_diff", "c2_sub", "c2_walls_sub",
                                    "c3_sub", "p523_sub",
                                    "c1_rx", "c2_rx", "c2_walls_rx", "c3_rx", "c3_surface_rx", "p521_rx",
-                                   "p523_diff_rx", "c2_rx_sub", "c3_rx_sub"])
+                                   "p523_diff_rx", "c2_rx_sub", "c3_rx_sub",
+                                   "c1_err", "c2_err", "c2_walls_err", "c3_err", "p521_err", "p523_err",
+                                   "c2_err_rx", "p523_err_rx", "c2_err_sub"])
 def test_amr_run_matches_oracle(A, which):
     """Adjoint-guided AMR runs (reduced sizes of the workloads): layouts of
     every level bit-exact after every regrid, states within 1e-12, flags
     bit-exact, J within 1e-12.  The _sub variants run the finest level's
     substeps as single substep launches; the _rx variants add the
-    conservation fix-up at coarse-fine interfaces."""
+    conservation fix-up at coarse-fine interfaces; the _err variants flag by
+    the adjoint-weighted error estimate (Sec. 7), whose values are compared
+    on every flagged level too (their rings interpolate from coarser
+    levels)."""
     sub = which.endswith("_sub")
     which = which[:-4] if sub else which
     rx = which.endswith("_rx")
     which = which[:-3] if rx else which
+    err = which.endswith("_err")
+    which = which[:-4] if err else which
     if which.startswith("p52"):
         # the paper's Sec. 5.2 examples at their own sizes
         wl = W.paper_5_2({"p521": "timepoint_walls", "p522": "range_walls"}.get(which[:4], "range_mixed"))
@@ -201,6 +242,9 @@ def test_amr_run_matches_oracle(A, which):
             wl.flag_mode, wl.tol = W.FLAG_SURFACE, 0.02
         chunks = 4
     wl.reflux = 1 if rx else 0
+    if err:
+        wl.flag_mode = W.FLAG_ERROR
+        wl.tol = {"p": 1e-4, "c1": 1e-7, "c2": 1e-5, "c3": 1e-7}[which[:2] if which[0] == "c" else "p"]
     snaps = O.adjoint_solve(wl, medium_dense=None if wl.medium.kind != "dense" else _adj_medium(wl))
     o, g = _amr_pair(A, wl, snaps=snaps)
     if sub:
@@ -219,6 +263,8 @@ def test_amr_run_matches_oracle(A, which):
             fo, co = o.flag(lev, wl.tol)
             fg, cg = g.flag(lev, wl.tol)
             assert co == cg and np.array_equal(fo, fg)
+            if err and len(o.patches(lev)):
+                assert np.array_equal(g.error_estimate(lev), o.error_estimate(lev)), f"estimate of level {lev}"
     assert refined > 0, "the case never refined"
     if sub:
         st = g.stats()
