@@ -573,6 +573,11 @@ def run_ours(args, rank, world):
             rnd(r["adjoint_flagging"]["gauge_max_abs_err_vs_uniform_fine"], 3) for r in paper.values()]
         summ["sec_5_2_gauge_err_pressure_vs_fine"] = [
             rnd(r["pressure_flagging"]["gauge_max_abs_err_vs_uniform_fine"], 3) for r in paper.values()]
+        summ["sec_5_2_J_err_error_flagging_vs_fine"] = [
+            rnd(r["error_flagging_reflux"]["J_rel_err_vs_uniform_fine"], 3) for r in paper.values()]
+    if flaggers and flaggers.get("error_estimate"):
+        summ["config2_error_flagging"] = [[r["tol"], rnd(r["J_rel_err_vs_uniform_fine"], 3), rnd(r["ms_per_solve"], 4)]
+                                          for r in flaggers["error_estimate"]]
     line["summary"] = summ
     log("autotune (ms of the timed coarse steps per candidate, by level): " + json.dumps(
         {f"level{r['level']}": {f"{c['tile'][0]}x{c['tile'][1]}{'' if c['fuse_ghosts'] else '+fill'}": round(c["ms"], 2)
@@ -675,12 +680,14 @@ def run_case_batch(args):
     b.close()
 
 
-def compare_flaggers(A, W, wl, adj, adj_s, s, tuned=None, diff_tols=(0.1, 0.03, 0.01, 0.003)):
+def compare_flaggers(A, W, wl, adj, adj_s, s, tuned=None, diff_tols=(0.1, 0.03, 0.01, 0.003),
+                     err_tols=(1e-6, 1e-7, 1e-8)):
     """The paper's comparison (Sec. 5.2.4): the same forward solve refined by
     adjoint flagging and by the standard undivided-difference ("pressure")
-    flagging over a range of tolerances (0.1 is the paper's); GPU time per
-    solve, cell-updates, and the error of J and of the gauge at the centre of
-    the target region against the uniform run on the finest grid."""
+    flagging over a range of tolerances (0.1 is the paper's), and by the
+    adjoint-weighted error estimate (Sec. 7); GPU time per solve,
+    cell-updates, and the error of J and of the gauge at the centre of the
+    target region against the uniform run on the finest grid."""
     import copy
     import torch
     from paper_1511_03645_gb300 import autotune as AT
@@ -744,6 +751,12 @@ def compare_flaggers(A, W, wl, adj, adj_s, s, tuned=None, diff_tols=(0.1, 0.03, 
         accuracy(rd, gd)
         rd["time_over_adjoint_forward"] = rd["ms_per_solve"] / ra["ms_per_solve"]
         out["difference"].append(rd)
+    out["error_estimate"] = []
+    for tol in err_tols:
+        re_, ge = one(W.FLAG_ERROR, tol)
+        accuracy(re_, ge)
+        re_["time_over_adjoint_forward"] = re_["ms_per_solve"] / ra["ms_per_solve"]
+        out["error_estimate"].append(re_)
     out["paper_context"] = ("Sec. 5.2.4 (laptop): pressure-flagging 3.1-15.7 s vs adjoint-flagging forward "
                             "1.3-6.9 s + adjoint 0.47-0.68 s")
     return out
@@ -759,10 +772,11 @@ PAPER_TABLE_5_2_4 = {  # Sec. 5.2.4 (a laptop): pressure-flagging; adjoint-flagg
 def paper_table(A, W, s, reps=3):
     """The Sec. 5.2 examples at the paper's sizes on this GPU: adjoint solve,
     adjoint-flagged forward solve (tol 0.02; also with the conservation
-    fix-up) and pressure-flagged forward solve (undivided differences, tol
-    0.1), best of `reps` wall times each; J and the gauge at (3.5, 0.5) of
-    every run against the uniform run on the finest grid (200^2 with the
-    finest time step)."""
+    fix-up), pressure-flagged forward solve (undivided differences, tol
+    0.1) and the forward solve flagged by the adjoint-weighted error estimate
+    (Sec. 7; tol 1e-4, with the fix-up), best of `reps` wall times each; J
+    and the gauge at (3.5, 0.5) of every run against the uniform run on the
+    finest grid (200^2 with the finest time step)."""
     import copy
     import torch
     out = {}
@@ -798,7 +812,8 @@ def paper_table(A, W, s, reps=3):
         gauges = {}
         for name, mode, tol, reflux in (("adjoint_flagging", W.FLAG_BRACKET_MAX, wl.tol, 0),
                                         ("adjoint_flagging_reflux", W.FLAG_BRACKET_MAX, wl.tol, 1),
-                                        ("pressure_flagging", W.FLAG_DIFFERENCE, 0.1, 0)):
+                                        ("pressure_flagging", W.FLAG_DIFFERENCE, 0.1, 0),
+                                        ("error_flagging_reflux", W.FLAG_ERROR, 1e-4, 1)):
             w = copy.copy(wl)
             w.flag_mode, w.tol, w.reflux = mode, tol, reflux
             best = None

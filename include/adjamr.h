@@ -221,7 +221,7 @@ adjamr_status adjamr_load_adjoint_snapshots(adjamr_ctx *ctx, const double *snaps
  * nsnap snapshots of that grid on the device (Sec. 4: q^(x, tf - t_n) =
  * q~(x, t_n)).  The level-0 step is dt = dT/ceil(dT/dt_cfl), dT = (tf -
  * t0)/(nsnap - 1).  ap->nlevels = 1: a fixed grid, as in the paper.
- * ap->nlevels > 1: the adjoint solved with AMR (Sec. 6 proposes it for a
+ * ap->nlevels > 1: the adjoint solved with AMR (Sec. 7 proposes it for a
  * more accurate inner product): finer levels by ap->ratio, flagged by the
  * standard flagger ap->flag_mode (DIFFERENCE or SURFACE; EINVAL otherwise)
  * at ap->tol and regridded every ap->regrid_interval steps as in a forward

@@ -2087,7 +2087,7 @@ int orc_adjoint_solve(const orc_params *P, int axis, int nl, const double *iface
     return 0;
 }
 
-/* The adjoint solved on an AMR hierarchy of its own (Sec. 6 names this as a
+/* The adjoint solved on an AMR hierarchy of its own (Sec. 7 names this as a
    way to a more accurate inner product): P describes the adjoint hierarchy
    (eqn = adjoint system, nlevels >= 1, ratios, a standard flag mode and its
    tolerance, regrid interval and buffer); its level 0 is the snapshot grid.

@@ -636,7 +636,7 @@ def _adjoint_fine_reference(wl, N, ratios, S):
 
 
 def test_adjoint_with_amr_limits_and_accuracy():
-    """The adjoint solved with AMR (Sec. 6 proposes it for a more accurate
+    """The adjoint solved with AMR (Sec. 7 proposes it for a more accurate
     inner product), snapshots from its level 0 after each Berger-Oliger step.
     Limits: tol = +inf refines nothing and gives the fixed-grid adjoint bit
     for bit; tol < 0 refines everything and gives the uniform finest-grid
