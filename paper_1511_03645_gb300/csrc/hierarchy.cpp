@@ -130,9 +130,11 @@ struct adjamr_ctx {
     MediumDev mh[ADJAMR_MAX_LEVELS];
     std::vector<double *> dense_dev;
     adjamr_adjoint *adj = nullptr;
-    unsigned long long *d_cfl = nullptr, *d_count = nullptr;
+    unsigned long long *d_cfl = nullptr;
+    // flag head (kPinHead bytes: count, bounding box, list counters) of the
+    // flag calls that make no bitmap; a regrid's head sits in front of its bitmap
+    unsigned long long *d_fhead = nullptr;
     int *d_err = nullptr;  // device-side invariant violations (nesting), checked after syncs
-    int *d_bbox = nullptr; // bounding box of flagged cells of the last flag call
     Bits h_fl, h_unc;               // host clustering scratch (regrid window)
     std::vector<int> h_sort_cnt;    // work-list ordering scratch
     std::vector<WorkItem> h_sort_tmp;
@@ -154,14 +156,15 @@ struct adjamr_ctx {
     std::vector<std::pair<size_t, void *>> blk_free;
     size_t blk_free_bytes = 0;
     size_t blk_cache_cap = (size_t)512 << 20;  // bytes the cache may hold (0: no caching)
-    uint64_t *d_flagbuf = nullptr;  // flag bitmap of the level being regridded
+    uint64_t *d_flagall = nullptr;  // flag head + bitmap of the level being regridded
+    uint64_t *d_flagbuf = nullptr;  // the bitmap: d_flagall + kPinHead / 8
     // pinned readback of the flag count, bounding box and (when small) the
     // whole bitmap: one synchronisation per flagged level
     char *h_pin = nullptr;
     size_t h_pin_bytes = 0;
     bool pin_has_bits = false;
     // work list of the two-pass flags
-    unsigned long long *d_fitems = nullptr, *d_fctr = nullptr;
+    unsigned long long *d_fitems = nullptr;
     long long fcap = 0;
     // per-level bilinear tables of the adjoint grid for the dense flag kernel
     char *d_ftab[ADJAMR_MAX_LEVELS] = {};
@@ -455,6 +458,24 @@ adjamr_status build_work(adjamr_ctx *c, int l, int tx, int ty)
                 txx = std::min(txx, cu[0]);
                 tyy = std::min(tyy, cu[1]);
                 if (count(txx, tyy) >= want) break;
+            }
+    }
+    if (c->P.dim == 1 && c->lmode[l] == ADJAMR_LAUNCH_WORKLIST && c->nsm > 0) {
+        // A small 1D level cut at the level's tile leaves each phase's FP64
+        // work to one or two SMs, whose narrow FP64 pipe then serialises
+        // several warps: cut it finer, down to 24 cells (one warp per phase),
+        // until the tiles reach the SM count.  Every cut gives the same bits.
+        auto count1 = [&](int a) {
+            long long n = 0;
+            for (const HPatch &p : L.patches) n += (long long)tile_count(p.nx, a);
+            return n;
+        };
+        static const int cuts1[3] = {64, 32, 24};
+        if (count1(txx) < c->nsm)
+            for (int cu : cuts1) {
+                if (cu >= txx) continue;
+                txx = cu;
+                if (count1(txx) >= c->nsm) break;
             }
     }
     for (int k = 0; k < (int)L.patches.size(); k++) {
@@ -1219,7 +1240,6 @@ adjamr_status grow_flag_list(adjamr_ctx *c, long long n)
     cput(c, c->d_fitems);
     c->fcap = 0;
     CKR(c, cget(c, &c->d_fitems, (size_t)n));
-    if (!c->d_fctr) CKR(c, cget(c, &c->d_fctr, 2));
     c->fcap = n;
     return ADJAMR_OK;
 }
@@ -1427,11 +1447,14 @@ adjamr_status regrid_flags(adjamr_ctx *c, int lev, long long *nf, int *bb)
     const int pitch64 = (C.N + 63) >> 6;
     size_t nb = (size_t)pitch64 * C.M * sizeof(uint64_t);
     if (c->flagbuf_bytes < nb) {
-        dfree(c->d_flagbuf, c->s);
-        CKR(c, dalloc(&c->d_flagbuf, nb / sizeof(uint64_t), c->s));
+        dfree(c->d_flagall, c->s);
+        c->d_flagbuf = nullptr;
+        CKR(c, dalloc(&c->d_flagall, (kPinHead + nb) / sizeof(uint64_t), c->s));
+        c->d_flagbuf = c->d_flagall + kPinHead / sizeof(uint64_t);
         c->flagbuf_bytes = nb;
     }
-    CKR(c, cudaMemsetAsync(c->d_flagbuf, 0, nb, c->s));
+    // one memset clears the head (count, box, list counters) and the bitmap
+    CKR(c, cudaMemsetAsync(c->d_flagall, 0, kPinHead + nb, c->s));
     return flag_dense(c, lev, c->P.tol, c->d_flagbuf, pitch64, nullptr, nf, bb);
 }
 
@@ -1707,7 +1730,9 @@ adjamr_status flag_dense(adjamr_ctx *c, int l, double tol, uint64_t *d_bits, int
     a.flags_bits = reinterpret_cast<unsigned long long *>(d_bits);
     a.pitch64 = pitch64;
     a.N = L.N;
-    a.count = c->d_count;
+    // head: count (word 0), bounding box (words 1-2), list counters (words 3-4)
+    unsigned long long *head = d_bits ? reinterpret_cast<unsigned long long *>(d_bits) - kPinHead / 8 : c->d_fhead;
+    a.count = head;
     double t = P.t0 + (double)L.nstep * L.dt;
     double T = std::fmin(t + (P.tf - P.ts), P.tf);
     a.t = t;
@@ -1733,10 +1758,10 @@ adjamr_status flag_dense(adjamr_ctx *c, int l, double tol, uint64_t *d_bits, int
         a.S = 0;
         a.ax = a.ay = 1;
     }
-    static const int bbox_init[4] = {0x7fffffff, -1, 0x7fffffff, -1};
-    a.bbox = c->d_bbox;
-    CKR(c, cudaMemsetAsync(c->d_count, 0, sizeof(unsigned long long), c->s));
-    CKR(c, cudaMemcpyAsync(c->d_bbox, bbox_init, sizeof bbox_init, cudaMemcpyHostToDevice, c->s));
+    a.bbox = reinterpret_cast<int *>(head + 1);
+    unsigned long long *fctr = head + 3;
+    // (a regrid's head was cleared with its bitmap)
+    if (!d_bits) CKR(c, cudaMemsetAsync(head, 0, kPinHead, c->s));
     // regrid flags (dense only, bracket max, block maxima present): one thread
     // per (cell, group of snapshot blocks) over the level's index space
     if (P.flag_mode == ADJAMR_FLAG_DIFFERENCE) {
@@ -1778,15 +1803,11 @@ adjamr_status flag_dense(adjamr_ctx *c, int l, double tol, uint64_t *d_bits, int
         const long long want = std::min((long long)L.N * L.M * nblk, kFlagItemsMax);
         if (c->fcap < std::min(want, (long long)1 << 20)) TRY(grow_flag_list(c, std::min(want, (long long)1 << 20)));
         for (int attempt = 0;; attempt++) {
-            if (attempt > 0) {
-                CKR(c, cudaMemsetAsync(d_bits, 0, (size_t)pitch64 * L.M * sizeof(uint64_t), c->s));
-                CKR(c, cudaMemsetAsync(c->d_count, 0, sizeof(unsigned long long), c->s));
-                CKR(c, cudaMemcpyAsync(c->d_bbox, bbox_init, sizeof bbox_init, cudaMemcpyHostToDevice, c->s));
-            }
+            if (attempt > 0)
+                CKR(c, cudaMemsetAsync(head, 0, kPinHead + (size_t)pitch64 * L.M * sizeof(uint64_t), c->s));
             const bool twopass = attempt == 0 || c->fcap >= (long long)L.N * L.M * nblk;
             if (twopass) {
-                CKR(c, cudaMemsetAsync(c->d_fctr, 0, 2 * sizeof(unsigned long long), c->s));
-                CKR(c, launch_flag_twopass(a, FlagWork{c->d_fitems, c->d_fctr, c->fcap}, c->nsm * 8, c->s));
+                CKR(c, launch_flag_twopass(a, FlagWork{c->d_fitems, fctr, c->fcap}, c->nsm * 8, c->s));
                 c->st.kernel_launches += 2;
             } else {
                 CKR(c, launch_flag_dense(a, (int)((nblk + a.gblk - 1) / a.gblk), c->s));
@@ -1821,17 +1842,24 @@ adjamr_status flag_readback(adjamr_ctx *c, int l, uint64_t *d_bits, int pitch64,
         CKR(c, cudaMallocHost((void **)&c->h_pin, std::max(need, (size_t)kPinHead + 4096)));
         c->h_pin_bytes = std::max(need, (size_t)kPinHead + 4096);
     }
-    CKR(c, cudaMemcpyAsync(c->h_pin, c->d_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->s));
-    CKR(c, cudaMemcpyAsync(c->h_pin + 8, c->d_bbox, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->s));
-    if (twopass)
-        CKR(c, cudaMemcpyAsync(c->h_pin + 24, c->d_fctr, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->s));
-    if (with_bits) CKR(c, cudaMemcpyAsync(c->h_pin + kPinHead, d_bits, bits_bytes, cudaMemcpyDeviceToHost, c->s));
+    // the head (and a small bitmap right behind it) in one copy
+    const unsigned long long *head =
+        d_bits ? reinterpret_cast<const unsigned long long *>(d_bits) - kPinHead / 8 : c->d_fhead;
+    CKR(c, cudaMemcpyAsync(c->h_pin, head, need, cudaMemcpyDeviceToHost, c->s));
+    (void)twopass;
     c->pin_has_bits = with_bits;
     CKR(c, cudaStreamSynchronize(c->s));
     unsigned long long cnt = 0;
     std::memcpy(&cnt, c->h_pin, sizeof cnt);
     *nflag_out = (long long)cnt;
-    if (bbox_out) std::memcpy(bbox_out, c->h_pin + 8, 4 * sizeof(int));
+    if (bbox_out) {
+        int v[4];
+        std::memcpy(v, c->h_pin + 8, sizeof v);
+        bbox_out[0] = 0x7fffffff - v[0];  // (no flag: INT_MAX, -1, INT_MAX, -1)
+        bbox_out[1] = v[1] - 1;
+        bbox_out[2] = 0x7fffffff - v[2];
+        bbox_out[3] = v[3] - 1;
+    }
     return ADJAMR_OK;
 }
 
@@ -2289,9 +2317,8 @@ adjamr_status create_impl(const adjamr_params *p, adjamr_ctx **out)
         }                                                                                             \
     } while (0)
     if (cudaMalloc(&c->d_cfl, sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMalloc(&c->d_count, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&c->d_fhead, kPinHead) != cudaSuccess ||
         cudaMalloc(&c->d_fout, sizeof(double)) != cudaSuccess || cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&c->d_bbox, 4 * sizeof(int)) != cudaSuccess ||
         cudaMalloc(&c->d_wctr, sizeof(unsigned long long)) != cudaSuccess) {
         adjamr_destroy(c);
         return ADJAMR_ENOMEM;
@@ -3075,10 +3102,10 @@ void adjamr_destroy(adjamr_ctx *ctx)
         dfree(ctx->L[l].d_auxtab, ctx->s);
     }
     for (double *p : ctx->dense_dev) cudaFreeAsync(p, ctx->s);
-    dfree(ctx->d_flagbuf, ctx->s);
+    dfree(ctx->d_flagall, ctx->s);
+    ctx->d_flagbuf = nullptr;
     for (int l = 0; l < ADJAMR_MAX_LEVELS; l++) cput(ctx, ctx->d_ftab[l]);
     cput(ctx, ctx->d_fitems);
-    cput(ctx, ctx->d_fctr);
     cput(ctx, ctx->d_gij);
     dfree(ctx->d_grec, ctx->s);
     dfree(ctx->d_fscratch, ctx->s);
@@ -3091,10 +3118,9 @@ void adjamr_destroy(adjamr_ctx *ctx)
     }
     if (ctx->ev_flag) cudaEventDestroy(ctx->ev_flag);
     if (ctx->d_cfl) cudaFree(ctx->d_cfl);
-    if (ctx->d_count) cudaFree(ctx->d_count);
+    if (ctx->d_fhead) cudaFree(ctx->d_fhead);
     if (ctx->d_fout) cudaFree(ctx->d_fout);
     if (ctx->d_err) cudaFree(ctx->d_err);
-    if (ctx->d_bbox) cudaFree(ctx->d_bbox);
     if (ctx->d_wctr) cudaFree(ctx->d_wctr);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);

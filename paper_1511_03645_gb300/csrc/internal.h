@@ -305,7 +305,8 @@ struct FlagArgs {
     int pitch64;
     int N;
     unsigned long long *count;
-    int *bbox;                      // [4]: min I, max I, min J, max J of flagged cells (atomics)
+    int *bbox;                      // [4]: bounding box of the flagged cells, as atomic maxima of
+                                    // INT_MAX - min I, max I + 1, INT_MAX - min J, max J + 1 (zero: none)
     const double *bmax;             // block maxima for culling (may be null)
     // dense bracket-max variant: the level's owner map ([M][N] storage index
     // or -1) and per-column / per-row bilinear tables of the adjoint grid

@@ -733,10 +733,10 @@ __global__ void k_flag(FlagArgs A)
         if ((threadIdx.x & 31) == 0) {
             atomicAdd(A.count, (unsigned long long)__popc(bal));
             if (A.bbox) {
-                atomicMin(A.bbox + 0, fI);
-                atomicMax(A.bbox + 1, gI);
-                atomicMin(A.bbox + 2, fJ);
-                atomicMax(A.bbox + 3, gJ);
+                atomicMax(A.bbox + 0, 0x7fffffff - fI);
+                atomicMax(A.bbox + 1, gI + 1);
+                atomicMax(A.bbox + 2, 0x7fffffff - fJ);
+                atomicMax(A.bbox + 3, gJ + 1);
             }
         }
     }
@@ -838,10 +838,10 @@ __global__ void k_flag_dense(FlagArgs A)
         gJ = __reduce_max_sync(0xffffffffu, gJ);
         if ((threadIdx.x & 31) == 0) {
             if (fr) atomicAdd(A.count, (unsigned long long)__popc(fr));
-            atomicMin(A.bbox + 0, fI);
-            atomicMax(A.bbox + 1, gI);
-            atomicMin(A.bbox + 2, fJ);
-            atomicMax(A.bbox + 3, gJ);
+            atomicMax(A.bbox + 0, 0x7fffffff - fI);
+            atomicMax(A.bbox + 1, gI + 1);
+            atomicMax(A.bbox + 2, 0x7fffffff - fJ);
+            atomicMax(A.bbox + 3, gJ + 1);
         }
     }
 }
@@ -859,10 +859,10 @@ __device__ __forceinline__ void flag_reduce(const FlagArgs &A, bool any_hit, uns
         gJ = __reduce_max_sync(0xffffffffu, gJ);
         if ((threadIdx.x & 31) == 0) {
             if (total) atomicAdd(A.count, (unsigned long long)total);
-            atomicMin(A.bbox + 0, fI);
-            atomicMax(A.bbox + 1, gI);
-            atomicMin(A.bbox + 2, fJ);
-            atomicMax(A.bbox + 3, gJ);
+            atomicMax(A.bbox + 0, 0x7fffffff - fI);
+            atomicMax(A.bbox + 1, gI + 1);
+            atomicMax(A.bbox + 2, 0x7fffffff - fJ);
+            atomicMax(A.bbox + 3, gJ + 1);
         }
     }
 }
