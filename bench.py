@@ -862,7 +862,8 @@ def run_case_solve(args):
     first) with the step-kernel tile and ghost mode of every level given by
     --kernels (default: the configuration the autotuner picks on a GB300,
     12x8 fused, 8x8 fused, 16x12 with a separate ghost fill); prints
-    per-level step statistics."""
+    per-level step statistics.  --flag error --tol T: flagged by the
+    adjoint-weighted error estimate (Sec. 7) instead."""
     import torch
     from paper_1511_03645_gb300 import adjamr as A
     torch.cuda.set_device(0)
@@ -870,6 +871,11 @@ def run_case_solve(args):
     wl = workload()
     if args.tf:
         wl.tf = args.tf
+    if args.flag == "error":
+        from paper_1511_03645_gb300 import workloads as W
+        wl.flag_mode = W.FLAG_ERROR
+    if args.tol > 0:
+        wl.tol = args.tol
     adj = A.solve_adjoint(wl, stream=s.cuda_stream)
     for rep in range(1 + args.warmup):
         h = A.Hierarchy(wl, stream=s.cuda_stream)
@@ -907,6 +913,9 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--case", default="main", choices=["main", "batch", "serve", "solve", "paper"])
     ap.add_argument("--tf", type=float, default=0.0, help="solve case: final time (0: the workload's)")
+    ap.add_argument("--flag", default="adjoint", choices=["adjoint", "error"],
+                    help="solve case: adjoint flagging (bracket rule) or the adjoint-weighted error estimate")
+    ap.add_argument("--tol", type=float, default=0.0, help="solve case: flag tolerance (0: the workload's)")
     ap.add_argument("--kernels", default="12x8f,8x8f,16x12",
                     help="solve case: per-level step tile, suffix f = ghost ring computed in the step kernel")
     ap.add_argument("--nreq", type=int, default=512)

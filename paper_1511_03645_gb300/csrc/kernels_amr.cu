@@ -1041,6 +1041,7 @@ __global__ void k_gather(int m, const long long *__restrict__ map, long long n, 
 }
 
 inline unsigned nblk(long long n) { return (unsigned)((n + kT - 1) / kT); }
+constexpr int kEB = 64;  // block size of the error-estimate kernels
 inline unsigned nblk_of(long long n) { return nblk(n); }
 
 }  // namespace
@@ -1122,17 +1123,21 @@ cudaError_t launch_errest_fill(const ErrEstArgs &a, LevelIdx g, const int *owner
 {
     if (a.nE <= 0 || a.nC <= 0) return cudaSuccess;
     const double th = (r > 0) ? (double)k / (double)r : 0.0;  // as the ghost fill's, on the host
-    k_errest_ext<<<nblk(a.nE), kT, 0, s>>>(a, g, owner, q, sq, owner_c, gc, r, qo, qn, sc, k, th, md, geom, err);
+    // blocks of 64: these kernels are FP64-latency bound on levels of a few
+    // thousand cells, so they are spread over as many SMs as possible
+    k_errest_ext<<<(unsigned)((a.nE + kEB - 1) / kEB), kEB, 0, s>>>(a, g, owner, q, sq, owner_c, gc, r, qo, qn, sc, k,
+                                                                    th, md, geom, err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return launch_pdl(k_errest_coarse, dim3(nblk(a.nC)), dim3(kT), 0, s, a, md, geom);
+    return launch_pdl(k_errest_coarse, dim3((unsigned)((a.nC + kEB - 1) / kEB)), dim3(kEB), 0, s, a, md, geom);
 }
 
 cudaError_t launch_errest_tau(const ErrEstArgs &a, const long long *iprefix, long long ninterior, double *tau,
                               long long st, cudaStream_t s)
 {
     if (ninterior <= 0) return cudaSuccess;
-    return launch_pdl(k_errest_tau, dim3(nblk(ninterior)), dim3(kT), 0, s, a, iprefix, ninterior, tau, st);
+    return launch_pdl(k_errest_tau, dim3((unsigned)((ninterior + kEB - 1) / kEB)), dim3(kEB), 0, s, a, iprefix,
+                      ninterior, tau, st);
 }
 
 cudaError_t launch_init_new(const PatchDesc *p, const long long *prefix, int np, long long ncells, LevelIdx g, int m,

@@ -59,6 +59,12 @@ extern "C" size_t adjamr_estimate_bytes(const adjamr_params *p)
         if (l > 0) total += (size_t)prev * (3 * sizeof(double) * m * p->ratio[l - 1] + sizeof(int)) + (size_t)cells * 8;
         // conservation fix-up: arena map and records (refluxing runs only)
         if (p->reflux) total += (size_t)cells * 8;
+        // error-estimate flagging: the extended patches (rings of 4 cells: at
+        // most 4.5x the cells of patches of 8 or more cells a side) with their
+        // coarsened copies (a quarter), state, first-step state and
+        // coefficients, and the estimate itself
+        if (p->flag_mode == ADJAMR_FLAG_ERROR && l < p->nlevels - 1)
+            total += (size_t)cells * sizeof(double) * ((size_t)per * 45 / 10 * 5 / 4 + (size_t)m);
         prev = cells;
         if (l < p->nlevels - 1) {
             N *= p->ratio[l];
