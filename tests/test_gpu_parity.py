@@ -616,6 +616,37 @@ def test_full_size_config2_sampled_step_parity(A):
     close(snaps[-1], wl.adjoint_phi())
 
 
+def test_full_size_config2_error_estimate_matches_oracle(A):
+    """Config 2 at full size flagged by the adjoint-weighted error estimate
+    (tol 1e-6), in the benchmark's per-level launch configuration: after 24
+    coarse steps (every level at the same time), the estimate of each flagged
+    level equals, bit for bit, the one the oracle computes on the GPU's layout
+    from the GPU's interior states of that level and the coarser ones."""
+    wl = W.config2(seed=0, ts=0.0, tol=1e-6)
+    wl.flag_mode = W.FLAG_ERROR
+    adj = A.solve_adjoint(wl)
+    g = A.Hierarchy(wl)
+    g.set_adjoint(adj)
+    for lev, (t, fuse) in enumerate((((16, 8), True), ((8, 8), True), ((16, 12), False))):
+        g.set_level_kernel(lev, t, fuse, A.LAUNCH_WORKLIST)
+    g.regrid(0, init=True)
+    g.advance(24)
+    assert len(g.patches(2)) > 0
+    n0 = 24
+    for lev in range(wl.nlevels - 1):
+        o = O.OracleHierarchy(wl, with_qinit=False)
+        r = 1
+        for k in range(lev + 1):
+            o.set_layout(k, g.patches(k))
+            o.write_level(k, g.read_level(k))
+            o.set_level_time(k, n0 * r)
+            if k < lev:
+                r *= wl.ratios[k]
+        a, b = g.error_estimate(lev), o.error_estimate(lev)
+        assert np.any(b != 0.0)
+        assert np.array_equal(a, b), f"level {lev}"
+
+
 def test_full_size_config1_matches_oracle_everywhere(A):
     """Config 1 at full size (200 coarse cells, ratio 4, adjoint 800 cells x
     100 snapshots, t_f = 20): the whole run, element by element, with the

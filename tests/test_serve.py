@@ -28,8 +28,15 @@ def _small_requests(n=6, seed=3):
     return media, reqs, wls
 
 
-def test_results_identical_alone_and_in_the_mix(A):
+@pytest.mark.parametrize("flag", ["adjoint", "error"])
+def test_results_identical_alone_and_in_the_mix(A, flag):
+    """Each request's J and cell-updates are the same served alone, served
+    in a mix of concurrent slots, and solved directly; requests flagged by the
+    adjoint-weighted error estimate (Sec. 7) too."""
     media, reqs, wls = _small_requests()
+    if flag == "error":
+        for wl in wls:
+            wl.flag_mode, wl.tol = W.FLAG_ERROR, 1e-6
     adjs = {}
     for r, wl in zip(reqs, wls):
         if r.medium_id not in adjs:
