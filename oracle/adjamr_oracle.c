@@ -47,7 +47,7 @@
 
 enum { O_ACOU = 0, O_ACOU_ADJ = 1, O_SW = 2, O_SW_ADJ = 3 };
 enum { O_EXTRAP = 0, O_WALL = 1, O_PERIODIC = 2 };
-enum { O_BRACKET = 0, O_LINEAR = 1, O_DIFF = 2, O_SURFACE = 3, O_ERROR = 4 };
+enum { O_BRACKET = 0, O_LINEAR = 1, O_DIFF = 2, O_SURFACE = 3, O_ERROR = 4, O_RICHARDSON = 5 };
 enum { O_MED_NONE = 0, O_MED_LAYERED = 1, O_MED_DENSE = 2 };
 
 typedef void (*orc_qinit_fn)(int level, int n, const double *xc, const double *yc, double *q_out, void *user);
@@ -1405,6 +1405,10 @@ static long flag_level(OHier *h, int l, double tol, unsigned char *flags)
                     }
                 } else if (h->P.flag_mode == O_SURFACE) {
                     val = fabs(Q[0]);  /* perturbation of the surface (first component) */
+                } else if (h->P.flag_mode == O_RICHARDSON) {
+                    /* the standard Richardson flagger (Sec. 1): the error estimate
+                       itself, largest component */
+                    for (int f = 0; f < h->m; f++) val = fmax(val, fabs(h->tau[o * h->m + f]));
                 } else if (S >= 2 && h->snaps) {
                     if (h->P.flag_mode == O_ERROR) {
                         const double *tq = &h->tau[o * h->m];
@@ -1433,7 +1437,7 @@ int orc_flag(void *hv, int level, double tol, unsigned char *flags, long *nflag)
     OHier *h = hv;
     if (level < 0 || level >= h->P.nlevels) return 1;
     if (h->P.flag_mode == O_DIFF && fill_ghosts(h, level, level_sub(h, level))) return 1;
-    if (h->P.flag_mode == O_ERROR && error_estimate(h, level)) return 1;
+    if ((h->P.flag_mode == O_ERROR || h->P.flag_mode == O_RICHARDSON) && error_estimate(h, level)) return 1;
     long c = flag_level(h, level, tol, flags);
     if (nflag) *nflag = c;
     return 0;
@@ -1626,7 +1630,7 @@ static int regrid_from(OHier *h, int l, int init)
         for (int k = 0; k < C->np; k++) ncell += (long)C->p[k].nx * C->p[k].ny;
         unsigned char *pf = xcalloc(ncell, 1);
         if ((h->P.flag_mode == O_DIFF && fill_ghosts(h, lev, level_sub(h, lev))) ||
-            (h->P.flag_mode == O_ERROR && error_estimate(h, lev))) {
+            ((h->P.flag_mode == O_ERROR || h->P.flag_mode == O_RICHARDSON) && error_estimate(h, lev))) {
             free(pf);
             return 1;
         }
@@ -1660,7 +1664,8 @@ static int regrid_from(OHier *h, int l, int init)
            r = 2, 3), so that its interpolation stencils stay on this level */
         unsigned char *nest = xcalloc((size_t)N * M, 1);
         int nw = 2;
-        if (h->P.flag_mode == O_ERROR && (4 + r - 1) / r + 1 > nw) nw = (4 + r - 1) / r + 1;
+        if ((h->P.flag_mode == O_ERROR || h->P.flag_mode == O_RICHARDSON) && (4 + r - 1) / r + 1 > nw)
+            nw = (4 + r - 1) / r + 1;
         int nwy = (dim == 2) ? nw : 0;
         for (int j = 0; j < M; j++)
             for (int i = 0; i < N; i++) {

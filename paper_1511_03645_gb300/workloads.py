@@ -41,6 +41,7 @@ FLAG_LINEAR = 1
 FLAG_DIFFERENCE = 2   # standard flagging: undivided differences of every component
 FLAG_SURFACE = 3      # standard flagging: |first component| (surface elevation)
 FLAG_ERROR = 4        # adjoint-weighted Richardson error estimate (Sec. 7)
+FLAG_RICHARDSON = 5   # standard flagging: the Richardson error estimate itself (Sec. 1)
 
 GRAV = 9.81
 

@@ -10,7 +10,9 @@ method (dx^3) and matches that error's size against exact solutions (1D
 d'Alembert, 2D standing wave), the coarse step's error is 8 times the fine
 step's (the premise of the factor 6), the flags are the bracket rule applied
 to tau, and the functional of an error-flagged AMR run converges to the
-uniform finest-grid one as the tolerance shrinks."""
+uniform finest-grid one as the tolerance shrinks.  The standard Richardson
+flagger (Sec. 1) thresholds tau itself, and needs several times the cells
+for the same accuracy of J -- the paper's case for weighing by the adjoint."""
 import copy
 import math
 
@@ -292,3 +294,73 @@ def test_error_flagged_functional_converges_to_the_uniform_fine_one():
     assert abs(e4 - Jf) <= 1e-4 * abs(Jf), (e4, Jf)
     assert abs(e5 - Jf) <= 1e-9 * abs(Jf), (e5, Jf)
     assert c4 < c5 < 0.1 * cf, (c4, c5, cf)
+
+
+# ------------------------------------------------------------ Richardson
+def test_richardson_flags_are_the_thresholded_estimate():
+    """Mode RICHARDSON flags a cell iff the largest component of |tau| exceeds
+    the tolerance (no adjoint involved), on a two-level run at several
+    times; the medium's impedance (0.01) makes the velocity components'
+    estimates the large ones, so flags from the first component alone would
+    differ."""
+    wl = W.config2(seed=1, n0=24, ratios=(2, 4), tf=2.0, adj_n=48, nsnap=20, ts=0.0, tol=1e-3)
+    wl.medium = W.Medium(kind="layered", axis=0, iface=np.array([0.0]), rho=np.array([0.01, 0.01]),
+                         K=np.array([0.01, 0.01]), cmax=1.0)
+    wl.flag_mode = W.FLAG_RICHARDSON
+    h = O.OracleHierarchy(wl)
+    h.regrid(0, init=True)
+    seen = 0
+    differs = False
+    for _ in range(3):
+        h.advance(5)
+        for lev in range(wl.nlevels - 1):
+            if len(h.patches(lev)) == 0:
+                continue
+            f, c = h.flag(lev, wl.tol)
+            tau = h.error_estimate(lev)
+            want, o = [], 0
+            for ilo, jlo, nx, ny in h.patches(lev):
+                t = tau[o:o + 3 * nx * ny].reshape(3, ny * nx)
+                want.append(np.max(np.abs(t), axis=0) > wl.tol)
+                differs |= bool(np.any((np.abs(t[0]) > wl.tol) != want[-1]))
+                o += 3 * nx * ny
+            want = np.concatenate(want)
+            assert c == int(want.sum()) and np.array_equal(f.astype(bool), want)
+            seen += c
+    assert seen > 0 and differs
+
+
+def test_richardson_needs_more_cells_than_the_adjoint_weighted_estimate():
+    """Sec. 5.2.1 (walls, time point, the paper's sizes, with the fix-up):
+    the fewest cell-updates with which each flagging brings J within 1e-4
+    (relative) of the uniform finest-grid J, over a range of tolerances --
+    the Richardson flagger refines wherever the error is large, also where it
+    cannot reach the target, and needs at least twice the cell-updates of
+    the estimate weighed by the adjoint (Sec. 1, Sec. 7)."""
+    wl = W.paper_5_2("timepoint_walls")
+    wl.reflux = 1
+    snaps = O.adjoint_solve(wl)
+
+    def run(mode, tol):
+        w = copy.copy(wl)
+        w.flag_mode = mode
+        h = O.OracleHierarchy(w, tol=tol)
+        h.set_adjoint(snaps)
+        h.regrid(0, init=True)
+        h.advance(h.nsteps_total())
+        return h.functional(), h.cell_updates()
+
+    Jf, _ = run(W.FLAG_BRACKET_MAX, -1.0)
+
+    def cheapest(mode, tols):
+        best = None
+        for tol in tols:
+            J, cu = run(mode, tol)
+            if abs(J - Jf) <= 1e-4 * abs(Jf) and (best is None or cu < best):
+                best = cu
+        return best
+
+    ce = cheapest(W.FLAG_ERROR, (1e-3, 3e-4, 1e-4, 3e-5, 1e-5))
+    cr = cheapest(W.FLAG_RICHARDSON, (1e-2, 3e-3, 1e-3, 3e-4, 1e-4))
+    assert ce is not None and cr is not None
+    assert cr >= 2 * ce, (cr, ce)
