@@ -575,9 +575,14 @@ def run_ours(args, rank, world):
             rnd(r["pressure_flagging"]["gauge_max_abs_err_vs_uniform_fine"], 3) for r in paper.values()]
         summ["sec_5_2_J_err_error_flagging_vs_fine"] = [
             rnd(r["error_flagging_reflux"]["J_rel_err_vs_uniform_fine"], 3) for r in paper.values()]
+        summ["sec_5_2_J_err_richardson_vs_fine"] = [
+            rnd(r["richardson_flagging_reflux"]["J_rel_err_vs_uniform_fine"], 3) for r in paper.values()]
     if flaggers and flaggers.get("error_estimate"):
         summ["config2_error_flagging"] = [[r["tol"], rnd(r["J_rel_err_vs_uniform_fine"], 3), rnd(r["ms_per_solve"], 4)]
                                           for r in flaggers["error_estimate"]]
+    if flaggers and flaggers.get("richardson"):
+        summ["config2_richardson"] = [[r["tol"], rnd(r["J_rel_err_vs_uniform_fine"], 3), rnd(r["ms_per_solve"], 4)]
+                                      for r in flaggers["richardson"]]
     line["summary"] = summ
     log("autotune (ms of the timed coarse steps per candidate, by level): " + json.dumps(
         {f"level{r['level']}": {f"{c['tile'][0]}x{c['tile'][1]}{'' if c['fuse_ghosts'] else '+fill'}": round(c["ms"], 2)
@@ -681,11 +686,12 @@ def run_case_batch(args):
 
 
 def compare_flaggers(A, W, wl, adj, adj_s, s, tuned=None, diff_tols=(0.1, 0.03, 0.01, 0.003),
-                     err_tols=(1e-6, 1e-7, 1e-8)):
+                     err_tols=(1e-6, 1e-7, 1e-8), rich_tols=(1e-3, 1e-4, 1e-5)):
     """The paper's comparison (Sec. 5.2.4): the same forward solve refined by
     adjoint flagging and by the standard undivided-difference ("pressure")
-    flagging over a range of tolerances (0.1 is the paper's), and by the
-    adjoint-weighted error estimate (Sec. 7); GPU time per solve,
+    flagging over a range of tolerances (0.1 is the paper's), by the
+    adjoint-weighted error estimate (Sec. 7) and by the estimate alone (the
+    standard Richardson flagger, Sec. 1); GPU time per solve,
     cell-updates, and the error of J and of the gauge at the centre of the
     target region against the uniform run on the finest grid."""
     import copy
@@ -757,6 +763,12 @@ def compare_flaggers(A, W, wl, adj, adj_s, s, tuned=None, diff_tols=(0.1, 0.03, 
         accuracy(re_, ge)
         re_["time_over_adjoint_forward"] = re_["ms_per_solve"] / ra["ms_per_solve"]
         out["error_estimate"].append(re_)
+    out["richardson"] = []
+    for tol in rich_tols:
+        rr, gr = one(W.FLAG_RICHARDSON, tol)
+        accuracy(rr, gr)
+        rr["time_over_adjoint_forward"] = rr["ms_per_solve"] / ra["ms_per_solve"]
+        out["richardson"].append(rr)
     out["paper_context"] = ("Sec. 5.2.4 (laptop): pressure-flagging 3.1-15.7 s vs adjoint-flagging forward "
                             "1.3-6.9 s + adjoint 0.47-0.68 s")
     return out
@@ -773,8 +785,10 @@ def paper_table(A, W, s, reps=3):
     """The Sec. 5.2 examples at the paper's sizes on this GPU: adjoint solve,
     adjoint-flagged forward solve (tol 0.02; also with the conservation
     fix-up), pressure-flagged forward solve (undivided differences, tol
-    0.1) and the forward solve flagged by the adjoint-weighted error estimate
-    (Sec. 7; tol 1e-4, with the fix-up), best of `reps` wall times each; J
+    0.1), the forward solve flagged by the adjoint-weighted error estimate
+    (Sec. 7; tol 1e-4, with the fix-up) and by the estimate alone (Sec. 1's
+    Richardson flagging; tol 1e-3, with the fix-up), best of `reps` wall
+    times each; J
     and the gauge at (3.5, 0.5) of every run against the uniform run on the
     finest grid (200^2 with the finest time step)."""
     import copy
@@ -813,7 +827,8 @@ def paper_table(A, W, s, reps=3):
         for name, mode, tol, reflux in (("adjoint_flagging", W.FLAG_BRACKET_MAX, wl.tol, 0),
                                         ("adjoint_flagging_reflux", W.FLAG_BRACKET_MAX, wl.tol, 1),
                                         ("pressure_flagging", W.FLAG_DIFFERENCE, 0.1, 0),
-                                        ("error_flagging_reflux", W.FLAG_ERROR, 1e-4, 1)):
+                                        ("error_flagging_reflux", W.FLAG_ERROR, 1e-4, 1),
+                                        ("richardson_flagging_reflux", W.FLAG_RICHARDSON, 1e-3, 1)):
             w = copy.copy(wl)
             w.flag_mode, w.tol, w.reflux = mode, tol, reflux
             best = None
@@ -871,9 +886,9 @@ def run_case_solve(args):
     wl = workload()
     if args.tf:
         wl.tf = args.tf
-    if args.flag == "error":
+    if args.flag != "adjoint":
         from paper_1511_03645_gb300 import workloads as W
-        wl.flag_mode = W.FLAG_ERROR
+        wl.flag_mode = W.FLAG_ERROR if args.flag == "error" else W.FLAG_RICHARDSON
     if args.tol > 0:
         wl.tol = args.tol
     adj = A.solve_adjoint(wl, stream=s.cuda_stream)
@@ -913,8 +928,9 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--case", default="main", choices=["main", "batch", "serve", "solve", "paper"])
     ap.add_argument("--tf", type=float, default=0.0, help="solve case: final time (0: the workload's)")
-    ap.add_argument("--flag", default="adjoint", choices=["adjoint", "error"],
-                    help="solve case: adjoint flagging (bracket rule) or the adjoint-weighted error estimate")
+    ap.add_argument("--flag", default="adjoint", choices=["adjoint", "error", "richardson"],
+                    help="solve case: adjoint flagging (bracket rule), the adjoint-weighted error estimate, or "
+                         "the estimate alone (Richardson)")
     ap.add_argument("--tol", type=float, default=0.0, help="solve case: flag tolerance (0: the workload's)")
     ap.add_argument("--kernels", default="12x8f,8x8f,16x12",
                     help="solve case: per-level step tile, suffix f = ghost ring computed in the step kernel")

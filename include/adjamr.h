@@ -69,13 +69,17 @@ enum { ADJAMR_BC_EXTRAP = 0, ADJAMR_BC_WALL = 1, ADJAMR_BC_PERIODIC = 2 };
  * snapshots of |q^ . tau| exceeds tol, tau being the cell's estimate of one
  * step's local error (adjamr_error_estimate).  It needs the adjoint, and it
  * nests refined levels ceil(4/r) + 1 cells of the coarser level deep (3 for
- * r = 2, 3) instead of 2, so that the estimate's ring stays on that level. */
+ * r = 2, 3) instead of 2, so that the estimate's ring stays on that level.
+ * RICHARDSON is the standard flagger of that estimate (Sec. 1, AMRClaw's
+ * Richardson error estimation): flag when the largest component of |tau|
+ * exceeds tol, wherever that is; it needs no adjoint and nests as ERROR does. */
 enum {
     ADJAMR_FLAG_BRACKET_MAX = 0,
     ADJAMR_FLAG_LINEAR = 1,
     ADJAMR_FLAG_DIFFERENCE = 2,
     ADJAMR_FLAG_SURFACE = 3,
-    ADJAMR_FLAG_ERROR = 4
+    ADJAMR_FLAG_ERROR = 4,
+    ADJAMR_FLAG_RICHARDSON = 5
 };
 
 enum { ADJAMR_MEDIUM_LAYERED = 1, ADJAMR_MEDIUM_DENSE = 2 };
@@ -118,7 +122,8 @@ typedef struct adjamr_params {
     double cmax;                 /* maximum wave speed of the medium */
     double dt0;                  /* > 0: use this level-0 step instead of the CFL rule */
     double t0, tf, ts;           /* start, final time, start of the time range of interest */
-    double tol;                  /* flag tolerance: flag iff max |q^ . q| > tol */
+    double tol;                  /* flag tolerance: flag iff max |q^ . q| > tol (ERROR: max |q^ . tau| > tol;
+                                    RICHARDSON: max_f |tau_f| > tol) */
     int regrid_interval;         /* regrid finer levels every k steps of a level (0 = never) */
     int buffer;                  /* flag buffer width (cells) */
     double cluster_eff;          /* Berger-Rigoutsos efficiency cut-off */

@@ -1066,20 +1066,37 @@ constexpr size_t kPinHead = 64;          // count, bounding box and list counter
 constexpr long long kFlagItemsMax = (long long)1 << 26;  // longest (cell, block) list of the two-pass flags
 constexpr size_t kPinBits = 256 << 10;   // bitmaps up to this size come back with the count
 
-// Richardson error estimate of level l at its current time (flag mode
-// ADJAMR_FLAG_ERROR): into *tau (the level's arena layout, m fields, taken
-// from the block cache; the caller returns it with cput).  Every patch is
+// Scratch of one error estimate: the estimate itself (the level's arena
+// layout, m fields) and the buffers its kernels work in.  The caller releases
+// it (errest_release) once the stream that ran the estimate has been
+// synchronised: on the flag side stream the block cache orders its frees on
+// the main stream, so blocks still in use there must not go back earlier.
+struct ErrEstScratch {
+    double *tau = nullptr, *buf = nullptr;
+    unsigned long long *cfl = nullptr;
+    char *meta = nullptr;
+};
+
+void errest_release(adjamr_ctx *c, ErrEstScratch &x)
+{
+    cput(c, x.tau);
+    cput(c, x.buf);
+    cput(c, x.cfl);
+    cput(c, x.meta);
+}
+
+// Richardson error estimate of level l at its current time (flag modes
+// ADJAMR_FLAG_ERROR, _RICHARDSON): into x.tau.  Every patch is
 // extended to even extents with a ring of 4 cells (values as ghost cells get
 // them), advanced two steps of dt by the step kernel (the first over the
 // region widened by 2, the second over the even patch), coarsened by 2 and
 // advanced one step of 2 dt (dt/dx unchanged), and tau = (coarsened two-step
 // state - coarse step) / 6 on every 2^d block.
-adjamr_status error_estimate(adjamr_ctx *c, int l, double **tau)
+adjamr_status error_estimate(adjamr_ctx *c, int l, ErrEstScratch &x)
 {
     Level &L = c->L[l];
     const adjamr_params &P = c->P;
     const int dim = P.dim, m = c->m;
-    *tau = nullptr;
     if (L.patches.empty()) return ADJAMR_OK;
     const int kx = (dim == 2) ? 16 : 128, ky = (dim == 2) ? 8 : 1;
     std::vector<ErrEstPatch> ep;
@@ -1161,12 +1178,16 @@ adjamr_status error_estimate(adjamr_ctx *c, int l, double **tau)
                           {wc.data(), sizeof(WorkItem) * wc.size()}},
                          &meta, offs));
     const int per = 2 * m + c->naux + c->nmed;
-    double *buf = nullptr;
-    unsigned long long *cfl = nullptr;
-    double *t = nullptr;
-    CKR(c, cget(c, &buf, (size_t)per * (nE + nC)));
-    CKR(c, cget(c, &cfl, 1));
-    CKR(c, cget(c, &t, (size_t)m * L.ncell));
+    x.meta = meta;
+    cudaError_t ea = cget(c, &x.buf, (size_t)per * (nE + nC));
+    if (ea == cudaSuccess) ea = cget(c, &x.cfl, 1);
+    if (ea == cudaSuccess) ea = cget(c, &x.tau, (size_t)m * L.ncell);
+    if (ea != cudaSuccess) {
+        c->err = std::string("error estimate: ") + cudaGetErrorString(ea);
+        return ADJAMR_ECUDA;
+    }
+    double *buf = x.buf, *t = x.tau;
+    unsigned long long *cfl = x.cfl;
     ErrEstArgs a{};
     a.ep = reinterpret_cast<const ErrEstPatch *>(meta + offs[0]);
     a.eprefix = reinterpret_cast<const long long *>(meta + offs[1]);
@@ -1200,7 +1221,6 @@ adjamr_status error_estimate(adjamr_ctx *c, int l, double **tau)
         r = P.ratio[l - 1];
         k = (int)(L.nstep - C.nstep * r);
     }
-    adjamr_status st = ADJAMR_OK;
     cudaError_t e = launch_errest_fill(a, idx_of(c, l), L.d_owner, L.q[L.cur], L.ncell, oc, gc, r, qo, qn, sc, k,
                                        L.d_med, geom_of(c, l), c->d_err, c->s);
     const PatchDesc *d1 = reinterpret_cast<const PatchDesc *>(meta + offs[3]);
@@ -1217,16 +1237,11 @@ adjamr_status error_estimate(adjamr_ctx *c, int l, double **tau)
                         reinterpret_cast<const WorkItem *>(meta + offs[8]), (int)wc.size(), 0, cfl, c->s);
     if (e == cudaSuccess) e = launch_errest_tau(a, L.d_prefix, L.ninterior, t, L.ncell, c->s);
     c->st.kernel_launches += 6;
-    cput(c, buf);
-    cput(c, cfl);
-    cput(c, meta);
     if (e != cudaSuccess) {
-        cput(c, t);
         c->err = std::string("error estimate: ") + cudaGetErrorString(e);
         return ADJAMR_ECUDA;
     }
-    *tau = t;
-    return st;
+    return ADJAMR_OK;
 }
 
 adjamr_status flag_dense(adjamr_ctx *c, int l, double tol, uint64_t *d_bits, int pitch64, unsigned char *d_patchflags,
@@ -1249,12 +1264,13 @@ void harvest_timing(adjamr_ctx *c);
 
 // Proper-nesting distance of a refinement by r, in cells of the coarser
 // level: the ghost ring of 2 fine cells needs 2; the error estimate's ring of
-// 4 fine cells (flag mode ADJAMR_FLAG_ERROR) ceil(4 / r) + 1, so that its
+// 4 fine cells (flag modes ADJAMR_FLAG_ERROR, _RICHARDSON) ceil(4 / r) + 1, so that its
 // interpolation stencils stay on the coarser level.
 int nest_width(const adjamr_ctx *c, int r)
 {
     int nw = 2;
-    if (c->P.flag_mode == ADJAMR_FLAG_ERROR && r > 0) nw = std::max(nw, (4 + r - 1) / r + 1);
+    if ((c->P.flag_mode == ADJAMR_FLAG_ERROR || c->P.flag_mode == ADJAMR_FLAG_RICHARDSON) && r > 0)
+        nw = std::max(nw, (4 + r - 1) / r + 1);
     return nw;
 }
 
@@ -1769,17 +1785,25 @@ adjamr_status flag_dense(adjamr_ctx *c, int l, double tol, uint64_t *d_bits, int
         const int sub = l > 0 ? (int)(L.nstep - c->L[l - 1].nstep * P.ratio[l - 1]) : 0;
         TRY(ghost_fill(c, l, sub));
     }
-    // error flagging: the bracket rule on the error estimate instead of the state
-    double *tau = nullptr;
-    struct TauRelease {
+    // error flagging: the bracket rule on the error estimate instead of the state;
+    // Richardson flagging: the estimate's largest component
+    // (released on every return path, all of which come after the stream's
+    // synchronisation in flag_readback or after an error)
+    ErrEstScratch ex;
+    struct Release {
         adjamr_ctx *c;
-        double *&t;
-        ~TauRelease() { if (t) cput(c, t); }
-    } tau_release{c, tau};
-    if (P.flag_mode == ADJAMR_FLAG_ERROR) {
-        TRY(error_estimate(c, l, &tau));
-        a.q = tau;
-        a.mode = ADJAMR_FLAG_BRACKET_MAX;
+        ErrEstScratch &x;
+        ~Release()
+        {
+            if (!x.tau && !x.buf && !x.cfl && !x.meta) return;
+            cudaStreamSynchronize(c->s);
+            errest_release(c, x);
+        }
+    } release{c, ex};
+    if (P.flag_mode == ADJAMR_FLAG_ERROR || P.flag_mode == ADJAMR_FLAG_RICHARDSON) {
+        TRY(error_estimate(c, l, ex));
+        a.q = ex.tau;
+        a.mode = P.flag_mode == ADJAMR_FLAG_ERROR ? ADJAMR_FLAG_BRACKET_MAX : ADJAMR_FLAG_RICHARDSON;
     }
     const bool dense = d_bits && !d_patchflags && a.mode == ADJAMR_FLAG_BRACKET_MAX && c->adj &&
                        c->adj->d_bmax && a.S >= 2;
@@ -2111,12 +2135,15 @@ adjamr_status step_level(adjamr_ctx *c, int l)
     const GhostMode gm = c->lfuse[l] ? GHOST_FUSED : GHOST_FILL;
     // (with the fix-up the step records for the new finer level: regrid first)
     if (regrid && c->s_flag && !P.reflux &&
-        (P.flag_mode == ADJAMR_FLAG_BRACKET_MAX || P.flag_mode == ADJAMR_FLAG_LINEAR)) {
+        (P.flag_mode == ADJAMR_FLAG_BRACKET_MAX || P.flag_mode == ADJAMR_FLAG_LINEAR ||
+         P.flag_mode == ADJAMR_FLAG_ERROR || P.flag_mode == ADJAMR_FLAG_RICHARDSON)) {
         // The adjoint flags of level l read its current interior state, which
         // its step leaves alone (it writes the other buffer): the flags run on
         // the side stream while the step runs, so the host clusters and builds
         // level l + 1 during the step.  The rebuilt levels come after the step
-        // in stream order, as their first use does.
+        // in stream order, as their first use does.  The error estimate reads
+        // the same state and the coarser level's two states, which stay as
+        // they are until the average-down; it writes only buffers of its own.
         CKR(c, cudaEventRecord(c->ev_flag, c->s));
         TRY(step_patches(c, l, sub, gm, false));
         TRY(regrid_from(c, l, 0, true));
@@ -2226,7 +2253,7 @@ adjamr_status create_impl(const adjamr_params *p, adjamr_ctx **out)
         if (p->ratio[l] < 2 || p->ratio[l] > kMaxSubsteps) return ADJAMR_EINVAL;
     for (int k = 0; k < 4; k++)
         if (p->bc[k] < 0 || p->bc[k] > 2) return ADJAMR_EINVAL;
-    if (p->flag_mode < ADJAMR_FLAG_BRACKET_MAX || p->flag_mode > ADJAMR_FLAG_ERROR) return ADJAMR_EINVAL;
+    if (p->flag_mode < ADJAMR_FLAG_BRACKET_MAX || p->flag_mode > ADJAMR_FLAG_RICHARDSON) return ADJAMR_EINVAL;
     if (p->launch_mode < ADJAMR_LAUNCH_WORKLIST || p->launch_mode > ADJAMR_LAUNCH_SUBSTEPS) return ADJAMR_EINVAL;
     if (p->reflux != 0 && p->reflux != 1) return ADJAMR_EINVAL;
     adjamr_ctx *c = new (std::nothrow) adjamr_ctx();
@@ -2915,10 +2942,11 @@ adjamr_status adjamr_error_estimate(adjamr_ctx *ctx, int level, double *dst, siz
         return ADJAMR_ESTATE;
     }
     try {
-        double *tau = nullptr;
-        TRY(error_estimate(ctx, level, &tau));
-        adjamr_status st = read_level_impl(ctx, level, dst, cap, false, nullptr, tau);
-        if (tau) cput(ctx, tau);
+        ErrEstScratch ex;
+        adjamr_status st = error_estimate(ctx, level, ex);
+        if (st == ADJAMR_OK) st = read_level_impl(ctx, level, dst, cap, false, nullptr, ex.tau);  // synchronises
+        cudaStreamSynchronize(ctx->s);
+        errest_release(ctx, ex);
         if (st != ADJAMR_OK) return st;
         return check_err(ctx);
     } catch (...) {

@@ -645,6 +645,11 @@ __global__ void k_flag(FlagArgs A)
             hit = val > A.tol;
         } else if (A.mode == ADJAMR_FLAG_SURFACE) {
             hit = fabs(Q[0]) > A.tol;
+        } else if (A.mode == ADJAMR_FLAG_RICHARDSON) {
+            // q holds the error estimate: its largest component
+            double val = 0.0;
+            for (int f = 0; f < A.m; f++) val = fmax(val, fabs(Q[f]));
+            hit = val > A.tol;
         } else if (A.S >= 2) {
             double dxa = (A.hi0 - A.lo0) / (double)A.ax;
             int ac = (int)floor((x - A.lo0) / dxa);

@@ -63,7 +63,7 @@ extern "C" size_t adjamr_estimate_bytes(const adjamr_params *p)
         // most 4.5x the cells of patches of 8 or more cells a side) with their
         // coarsened copies (a quarter), state, first-step state and
         // coefficients, and the estimate itself
-        if (p->flag_mode == ADJAMR_FLAG_ERROR && l < p->nlevels - 1)
+        if ((p->flag_mode == ADJAMR_FLAG_ERROR || p->flag_mode == ADJAMR_FLAG_RICHARDSON) && l < p->nlevels - 1)
             total += (size_t)cells * sizeof(double) * ((size_t)per * 45 / 10 * 5 / 4 + (size_t)m);
         prev = cells;
         if (l < p->nlevels - 1) {

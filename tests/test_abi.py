@@ -83,10 +83,11 @@ def test_parameters_are_validated_before_any_device_call():
     assert not out.value
     p.reflux = 1
     assert L.adjamr_estimate_bytes(ctypes.byref(p)) > est[4]
-    # flag modes 0..4 (4: the adjoint-weighted error estimate, whose scratch
-    # the estimate counts); anything else is refused
+    # flag modes 0..5 (4, 5: flagging by the Richardson error estimate,
+    # adjoint-weighted or not, whose scratch the estimate counts); anything
+    # else is refused
     p = A.make_params(wl)
-    p.flag_mode = 5
+    p.flag_mode = 6
     assert L.adjamr_init_grid_hierarchy(ctypes.byref(p), ctypes.byref(out)) == A.EINVAL
     assert not out.value
     p.flag_mode = W.FLAG_ERROR

@@ -199,22 +199,26 @@ def _compare_all(o, g, nlev):
                                    "c1_rx", "c2_rx", "c2_walls_rx", "c3_rx", "c3_surface_rx", "p521_rx",
                                    "p523_diff_rx", "c2_rx_sub", "c3_rx_sub",
                                    "c1_err", "c2_err", "c2_walls_err", "c3_err", "p521_err", "p523_err",
-                                   "c2_err_rx", "p523_err_rx", "c2_err_sub"])
+                                   "c2_err_rx", "p523_err_rx", "c2_err_sub",
+                                   "c1_rich", "c2_rich", "c3_rich", "p523_rich", "c2_rich_rx"])
 def test_amr_run_matches_oracle(A, which):
     """Adjoint-guided AMR runs (reduced sizes of the workloads): layouts of
     every level bit-exact after every regrid, states within 1e-12, flags
     bit-exact, J within 1e-12.  The _sub variants run the finest level's
     substeps as single substep launches; the _rx variants add the
     conservation fix-up at coarse-fine interfaces; the _err variants flag by
-    the adjoint-weighted error estimate (Sec. 7), whose values are compared
-    on every flagged level too (their rings interpolate from coarser
-    levels)."""
+    the adjoint-weighted error estimate (Sec. 7) and the _rich variants by
+    the estimate alone (the standard Richardson flagger, Sec. 1), whose
+    values are compared on every flagged level too (their rings interpolate
+    from coarser levels)."""
     sub = which.endswith("_sub")
     which = which[:-4] if sub else which
     rx = which.endswith("_rx")
     which = which[:-3] if rx else which
     err = which.endswith("_err")
     which = which[:-4] if err else which
+    rich = which.endswith("_rich")
+    which = which[:-5] if rich else which
     if which.startswith("p52"):
         # the paper's Sec. 5.2 examples at their own sizes
         wl = W.paper_5_2({"p521": "timepoint_walls", "p522": "range_walls"}.get(which[:4], "range_mixed"))
@@ -245,6 +249,9 @@ def test_amr_run_matches_oracle(A, which):
     if err:
         wl.flag_mode = W.FLAG_ERROR
         wl.tol = {"p": 1e-4, "c1": 1e-7, "c2": 1e-5, "c3": 1e-7}[which[:2] if which[0] == "c" else "p"]
+    if rich:
+        wl.flag_mode = W.FLAG_RICHARDSON
+        wl.tol = {"p": 1e-3, "c1": 1e-3, "c2": 1e-3, "c3": 1e-2}[which[:2] if which[0] == "c" else "p"]
     snaps = O.adjoint_solve(wl, medium_dense=None if wl.medium.kind != "dense" else _adj_medium(wl))
     o, g = _amr_pair(A, wl, snaps=snaps)
     if sub:
@@ -263,7 +270,7 @@ def test_amr_run_matches_oracle(A, which):
             fo, co = o.flag(lev, wl.tol)
             fg, cg = g.flag(lev, wl.tol)
             assert co == cg and np.array_equal(fo, fg)
-            if err and len(o.patches(lev)):
+            if (err or rich) and len(o.patches(lev)):
                 assert np.array_equal(g.error_estimate(lev), o.error_estimate(lev)), f"estimate of level {lev}"
     assert refined > 0, "the case never refined"
     if sub:
