@@ -334,16 +334,31 @@ def test_per_level_kernels_compute_the_same_bits(A, reflux):
     h.close()
 
 
-def test_dry_adjoint_cells_match_oracle(A):
+@pytest.mark.parametrize("case", ["acoustics", "shallow_water", "acoustics_error_flags"])
+def test_dry_adjoint_cells_match_oracle(A, case):
     """Adjoint cells marked dry (Sec. 5.3: no flag where the adjoint grid is
-    dry) over the part of the grid where this run flags (x >= 1.5): flags,
-    layouts and states of the AMR run agree with the oracle's, no flag lies
-    in a dry adjoint cell, and without the mask some would."""
-    wl = W.config2(seed=3, n0=32, ratios=(2, 4), tf=1.5, adj_n=64, nsnap=20, ts=0.0, tol=1e-6,
-                   min_patch=8, max_patch=32)
-    snaps = O.adjoint_solve(wl)
-    wet = np.ones((64, 64), np.uint8)
-    wet[:, 44:] = 0   # adjoint columns with x >= 1.5
+    dry) over part of the grid where this run flags: flags, layouts and
+    states of the AMR run agree with the oracle's, no flag lies in a dry
+    adjoint cell, and without the mask some would.  Acoustics (config 2
+    reduced, x >= 1.5 dry), shallow water over bathymetry (config 3 reduced,
+    x >= 250 km dry) and acoustics flagged by the adjoint-weighted error
+    estimate, whose weight the mask zeroes as well."""
+    if case == "shallow_water":
+        wl = W.config3(seed=2, n0=24, ratios=(2, 2), tf=4 * 3600.0, adj_n=48, nsnap=20, tol=1e-5, L=2.0e6,
+                       dense_levels=3)
+        snaps = O.adjoint_solve(wl, medium_dense=_adj_medium(wl))
+        wet = np.ones((48, 48), np.uint8)
+        wet[:, 6:] = 0    # adjoint columns with x >= 250 km
+        x_dry = 250000.0
+    else:
+        wl = W.config2(seed=3, n0=32, ratios=(2, 4), tf=1.5, adj_n=64, nsnap=20, ts=0.0, tol=1e-6,
+                       min_patch=8, max_patch=32)
+        if case == "acoustics_error_flags":
+            wl.flag_mode = W.FLAG_ERROR
+        snaps = O.adjoint_solve(wl)
+        wet = np.ones((64, 64), np.uint8)
+        wet[:, 44:] = 0   # adjoint columns with x >= 1.5
+        x_dry = 1.5
 
     def flagged_x(h, lev, fl):
         dx = (wl.hi[0] - wl.lo[0]) / (wl.n0[0] * int(np.prod(wl.ratios[:lev])))
@@ -357,7 +372,7 @@ def test_dry_adjoint_cells_match_oracle(A):
     plain = O.OracleHierarchy(wl)
     plain.set_adjoint(snaps)
     plain.regrid(0, init=True)
-    assert (flagged_x(plain, 0, plain.flag(0, wl.tol)[0]) >= 1.5).any()
+    assert (flagged_x(plain, 0, plain.flag(0, wl.tol)[0]) >= x_dry).any()
     o = O.OracleHierarchy(wl)
     o.set_adjoint(snaps, wet=wet)
     o.regrid(0, init=True)
@@ -375,7 +390,7 @@ def test_dry_adjoint_cells_match_oracle(A):
             fo, co = o.flag(lev, wl.tol)
             fg, cg = g.flag(lev, wl.tol)
             assert co == cg and np.array_equal(fo, fg)
-            assert not (flagged_x(g, lev, fg) >= 1.5).any()
+            assert not (flagged_x(g, lev, fg) >= x_dry).any()
     assert abs(g.functional() - o.functional()) <= RTOL * max(abs(o.functional()), 1e-300)
 
 
