@@ -244,6 +244,16 @@ adjamr_status adjamr_adjoint_read(adjamr_adjoint *adj, double *dst, size_t cap);
 /* Drop one reference; frees the device copy with the last one. */
 void adjamr_adjoint_release(adjamr_adjoint *adj);
 
+/* Start a new solve in the same context: finer levels dropped, every level
+ * back at t0, level 0 re-sampled from qinit (zero without it), the CFL record,
+ * the device error word, gauge records and statistics cleared; the layout of
+ * level 0, the medium, the attached adjoint set, the gauges' points and the
+ * per-level kernel choices stay.  A solve after a reset gives the bits of a
+ * solve in a new context (tested); the context keeps its cached device blocks,
+ * so repeated solves skip the allocations of a new context.  Synchronises.
+ * (No counterpart in the paper: context reuse.) */
+adjamr_status adjamr_reset(adjamr_ctx *ctx);
+
 /* Rebuild levels base_level+1 .. nlevels-1 top-down (Sec. 3, regridding):
  * adjoint flags on level l, buffered, properly nested, clustered by
  * Berger-Rigoutsos, split to max_patch, refined; new cells copied from old

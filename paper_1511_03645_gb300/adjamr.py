@@ -97,7 +97,7 @@ SYMBOLS = [
     "adjamr_init_grid_hierarchy", "adjamr_set_medium", "adjamr_load_adjoint_snapshots", "adjamr_solve_adjoint",
     "adjamr_set_adjoint", "adjamr_adjoint_read", "adjamr_adjoint_release", "adjamr_regrid",
     "adjamr_advance_level", "adjamr_flag_cells", "adjamr_integrate_functional", "adjamr_get_patches",
-    "adjamr_read_level", "adjamr_write_level", "adjamr_error_estimate", "adjamr_fill_ghosts",
+    "adjamr_read_level", "adjamr_write_level", "adjamr_error_estimate", "adjamr_reset", "adjamr_fill_ghosts",
     "adjamr_read_patch_ghosted",
     "adjamr_step_level_only", "adjamr_get_stats", "adjamr_set_timing", "adjamr_set_level_kernel",
     "adjamr_substep_wait_selftest", "adjamr_set_gauges",
@@ -147,6 +147,7 @@ def load(build_if_missing: bool = True):
             "adjamr_get_patches": [vp, i, P(Patch), i, ip],
             "adjamr_read_level": [vp, i, dp, sz],
             "adjamr_error_estimate": [vp, i, dp, sz],
+            "adjamr_reset": [vp],
             "adjamr_write_level": [vp, i, dp, sz],
             "adjamr_fill_ghosts": [vp, i],
             "adjamr_read_patch_ghosted": [vp, i, i, dp, dp],
@@ -427,6 +428,11 @@ class Hierarchy:
         out = np.zeros(max(n, 1))
         _check(load().adjamr_read_level(self.h, level, _dp(out), out.size), self.h, "read_level")
         return out[:n]
+
+    def reset(self) -> None:
+        """Start a new solve in this context (level 0 from qinit at t0, finer
+        levels dropped, statistics cleared; adjoint, medium and kernels kept)."""
+        _check(load().adjamr_reset(self.h), self.h, "reset")
 
     def error_estimate(self, level: int) -> np.ndarray:
         """Richardson estimate of one step's local error on the level at its

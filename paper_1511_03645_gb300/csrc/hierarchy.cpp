@@ -2240,6 +2240,39 @@ adjamr_status set_medium_impl(adjamr_ctx *c, const adjamr_medium *m)
     return ADJAMR_OK;
 }
 
+// level 0's state from qinit at its cell centres (zero without qinit), into
+// q[0]; synchronises
+adjamr_status sample_level0(adjamr_ctx *c)
+{
+    const adjamr_params *p = &c->P;
+    Level &L0 = c->L[0];
+    L0.cur = 0;
+    std::vector<double> host(p->qinit ? (size_t)c->m * L0.ncell : 0, 0.0);
+    if (p->qinit) {
+        long long n = L0.ninterior;
+        std::vector<double> xc(n), yc(n), qv((size_t)n * c->m);
+        long long o = 0;
+        for (const HPatch &q : L0.patches)
+            for (int j = 0; j < q.ny; j++)
+                for (int i = 0; i < q.nx; i++, o++) {
+                    xc[o] = p->lo[0] + ((double)(q.ilo + i) + 0.5) * L0.dx;
+                    yc[o] = (p->dim == 2) ? p->lo[1] + ((double)(q.jlo + j) + 0.5) * L0.dy : 0.0;
+                }
+        p->qinit(0, (int)n, xc.data(), yc.data(), qv.data(), p->qinit_user);
+        o = 0;
+        for (const HPatch &q : L0.patches)
+            for (int j = 0; j < q.ny; j++)
+                for (int i = 0; i < q.nx; i++, o++)
+                    for (int f = 0; f < c->m; f++) host[(size_t)f * L0.ncell + cell_of(c, q, i, j)] = qv[(size_t)f * n + o];
+    }
+    if (p->qinit)
+        CKR(c, cudaMemcpyAsync(L0.q[0], host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, c->s));
+    else if (L0.ncell > 0)
+        CKR(c, cudaMemsetAsync(L0.q[0], 0, sizeof(double) * (size_t)c->m * L0.ncell, c->s));
+    CKR(c, cudaStreamSynchronize(c->s));
+    return ADJAMR_OK;
+}
+
 adjamr_status create_impl(const adjamr_params *p, adjamr_ctx **out)
 {
     if (!p || !out) return ADJAMR_EINVAL;
@@ -2380,29 +2413,7 @@ adjamr_status create_impl(const adjamr_params *p, adjamr_ctx **out)
         }
     FAIL(alloc_level(c, 0, boxes));
     FAIL(build_ghost_map(c, 0));
-    if (p->qinit) {
-        long long n = L0.ninterior;
-        std::vector<double> xc(n), yc(n), qv((size_t)n * c->m), host((size_t)c->m * L0.ncell, 0.0);
-        long long o = 0;
-        for (const HPatch &q : L0.patches)
-            for (int j = 0; j < q.ny; j++)
-                for (int i = 0; i < q.nx; i++, o++) {
-                    xc[o] = p->lo[0] + ((double)(q.ilo + i) + 0.5) * L0.dx;
-                    yc[o] = (p->dim == 2) ? p->lo[1] + ((double)(q.jlo + j) + 0.5) * L0.dy : 0.0;
-                }
-        p->qinit(0, (int)n, xc.data(), yc.data(), qv.data(), p->qinit_user);
-        o = 0;
-        for (const HPatch &q : L0.patches)
-            for (int j = 0; j < q.ny; j++)
-                for (int i = 0; i < q.nx; i++, o++)
-                    for (int f = 0; f < c->m; f++) host[(size_t)f * L0.ncell + cell_of(c, q, i, j)] = qv[(size_t)f * n + o];
-        if (cudaMemcpyAsync(L0.q[0], host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, c->s) !=
-                cudaSuccess ||
-            cudaStreamSynchronize(c->s) != cudaSuccess) {
-            adjamr_destroy(c);
-            return ADJAMR_ECUDA;
-        }
-    }
+    FAIL(sample_level0(c));
 #undef FAIL
     if (cudaStreamSynchronize(c->s) != cudaSuccess) {
         adjamr_destroy(c);
@@ -2929,6 +2940,29 @@ adjamr_status adjamr_write_level(adjamr_ctx *ctx, int level, const double *src, 
     if (!ctx || level < 0 || level >= ctx->P.nlevels || (!src && count)) return ADJAMR_EINVAL;
     try {
         return read_level_impl(ctx, level, nullptr, count, true, src);
+    } catch (...) {
+        return ADJAMR_ENOMEM;
+    }
+}
+
+adjamr_status adjamr_reset(adjamr_ctx *ctx)
+{
+    if (!ctx) return ADJAMR_EINVAL;
+    try {
+        CKR(ctx, cudaStreamSynchronize(ctx->s));
+        if (ctx->s_flag) CKR(ctx, cudaStreamSynchronize(ctx->s_flag));
+        for (int l = ctx->P.nlevels - 1; l >= 1; l--) free_level(ctx, ctx->L[l]);
+        reflux_release(ctx, ctx->L[0]);
+        for (int l = 0; l < ctx->P.nlevels; l++) {
+            ctx->L[l].nstep = 0;
+            ctx->L[l].cur = 0;
+        }
+        for (int l = 0; l < ADJAMR_MAX_LEVELS; l++) ctx->rebuilt_tick[l] = -1;
+        ctx->ngrec = 0;
+        ctx->st = adjamr_stats{};
+        CKR(ctx, cudaMemsetAsync(ctx->d_cfl, 0, sizeof(unsigned long long), ctx->s));
+        CKR(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->s));
+        return sample_level0(ctx);
     } catch (...) {
         return ADJAMR_ENOMEM;
     }

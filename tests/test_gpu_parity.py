@@ -669,6 +669,39 @@ def test_full_size_config2_error_estimate_matches_oracle(A):
         assert np.array_equal(a, b), f"level {lev}"
 
 
+@pytest.mark.parametrize("case", ["bracket", "error_reflux"])
+def test_reset_gives_the_bits_of_a_new_context(A, case):
+    """adjamr_reset: a second solve in the same context (after a first one
+    that refined and recorded gauges) gives the layouts, states, J, gauge
+    records and cell-update count of the first, bit for bit."""
+    wl = W.config2(seed=3, n0=32, ratios=(2, 4), tf=2.0, adj_n=64, nsnap=20, ts=0.0, tol=1e-4, min_patch=8,
+                   max_patch=32)
+    if case == "error_reflux":
+        wl.flag_mode, wl.tol, wl.reflux = W.FLAG_ERROR, 1e-5, 1
+    snaps = O.adjoint_solve(wl)
+    g = A.Hierarchy(wl)
+    g.load_adjoint(snaps)
+    g.set_gauges([0.3, -1.1], [0.2, 0.7])
+
+    def solve():
+        g.regrid(0, init=True)
+        g.advance(g.nsteps_total())
+        levels = [(g.patches(lev), g.read_level(lev)) for lev in range(wl.nlevels)]
+        return levels, g.functional(), g.gauges(), g.stats()["cell_updates"]
+
+    first = solve()
+    assert sum(len(p) for p, _ in first[0][1:]) > 0
+    g.reset()
+    assert g.stats()["cell_updates"] == 0 and len(g.patches(1)) == 0
+    second = solve()
+    for (pa, qa), (pb, qb) in zip(first[0], second[0]):
+        assert np.array_equal(pa, pb) and np.array_equal(qa, qb)
+    assert first[1] == second[1]
+    assert np.array_equal(first[2], second[2])
+    assert first[3] == second[3]
+    g.close()
+
+
 def test_full_size_config1_matches_oracle_everywhere(A):
     """Config 1 at full size (200 coarse cells, ratio 4, adjoint 800 cells x
     100 snapshots, t_f = 20): the whole run, element by element, with the
