@@ -174,7 +174,7 @@ def run_reference(args, rank, world):
 
 # ------------------------------------------------------------------ configs 1 and 3
 def measure_config(A, W, wl, s, peak_ops, cpu_budget, adj_medium=None, label=""):
-    """One more BASELINE configuration measured whole: its adjoint solved on
+    """One more workload of the benchmark measured whole: its adjoint solved on
     the GPU (untimed), one warm-up and one timed forward solve (CUDA events on
     the solve's stream, inputs resident), one instrumented solve for the
     step-kernel roofline, and the CPU oracle on a bounded sample of the same
