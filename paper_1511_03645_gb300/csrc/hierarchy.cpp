@@ -2976,13 +2976,24 @@ adjamr_status adjamr_error_estimate(adjamr_ctx *ctx, int level, double *dst, siz
         return ADJAMR_ESTATE;
     }
     try {
+        // a level nested only as the other flag modes nest it may leave the
+        // estimate's ring without coarse cells: reported for this call, the
+        // context's error word is then put back
+        TRY(check_err(ctx));
         ErrEstScratch ex;
         adjamr_status st = error_estimate(ctx, level, ex);
         if (st == ADJAMR_OK) st = read_level_impl(ctx, level, dst, cap, false, nullptr, ex.tau);  // synchronises
         cudaStreamSynchronize(ctx->s);
         errest_release(ctx, ex);
         if (st != ADJAMR_OK) return st;
-        return check_err(ctx);
+        st = check_err(ctx);
+        if (st == ADJAMR_ENEST) {
+            CKR(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->s));
+            CKR(ctx, cudaStreamSynchronize(ctx->s));
+            ctx->err = "error estimate: the level is not nested deeply enough for the estimate's ring "
+                       "(nest it as ADJAMR_FLAG_ERROR does)";
+        }
+        return st;
     } catch (...) {
         return ADJAMR_ENOMEM;
     }

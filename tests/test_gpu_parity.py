@@ -702,6 +702,31 @@ def test_reset_gives_the_bits_of_a_new_context(A, case):
     g.close()
 
 
+def test_error_estimate_of_a_shallowly_nested_level_is_refused_and_the_run_goes_on(A):
+    """A hierarchy flagged by the bracket rule nests its finest level only 2
+    coarse cells deep; with ratio 2 the estimate's ring of 4 fine cells then
+    needs coarse cells outside the coarser level, and both sides refuse the
+    estimate (ENEST on the GPU).  The refusal leaves the context usable: the
+    run goes on to the oracle's bits."""
+    wl = W.config2(seed=1, n0=32, ratios=(2, 2), tf=2.0, adj_n=64, nsnap=20, ts=0.0, tol=1e-4, min_patch=8,
+                   max_patch=32)
+    o, g = _amr_pair(A, wl)
+    o.advance(1)
+    g.advance(1)
+    _compare_all(o, g, wl.nlevels)
+    assert len(g.patches(2)) > 0
+    with pytest.raises(RuntimeError):
+        o.error_estimate(2)
+    with pytest.raises(A.AdjamrError) as ei:
+        g.error_estimate(2)
+    assert ei.value.code == A.ENEST
+    assert np.array_equal(g.error_estimate(0), o.error_estimate(0))
+    o.advance(4)
+    g.advance(4)
+    _compare_all(o, g, wl.nlevels)
+    assert abs(g.functional() - o.functional()) <= RTOL * max(abs(o.functional()), 1e-300)
+
+
 def test_full_size_config1_matches_oracle_everywhere(A):
     """Config 1 at full size (200 coarse cells, ratio 4, adjoint 800 cells x
     100 snapshots, t_f = 20): the whole run, element by element, with the
