@@ -201,13 +201,15 @@ typedef struct adjamr_stats {
 typedef struct adjamr_ctx adjamr_ctx;
 typedef struct adjamr_adjoint adjamr_adjoint;
 
-/* Create a hierarchy: level 0 tiles the domain with near-equal patches of at
+/* Create a hierarchy (Sec. 3: block-structured nested levels carrying the
+ * linear system of Sec. 2): level 0 tiles the domain with near-equal patches of at
  * most max_patch0 cells per side; its state is sampled from p->qinit at cell
  * centres.  Finer levels are created by adjamr_regrid.  Errors: EINVAL for
  * inconsistent parameters, ENOMEM, ECUDA. */
 adjamr_status adjamr_init_grid_hierarchy(const adjamr_params *p, adjamr_ctx **out);
 
-/* Set the medium; copies the layer table or the dense per-level arrays to
+/* Set the medium (Secs. 5.1-5.3: layered rho, K; bathymetry hbar); copies the
+ * layer table or the dense per-level arrays to
  * the device and fills the per-cell coefficients of existing patches
  * (impedance, sound speed, edge coefficients).  Must precede stepping. */
 adjamr_status adjamr_set_medium(adjamr_ctx *ctx, const adjamr_medium *m);
@@ -237,11 +239,12 @@ adjamr_status adjamr_load_adjoint_snapshots(adjamr_ctx *ctx, const double *snaps
 adjamr_status adjamr_solve_adjoint(adjamr_ctx *ctx, const adjamr_params *ap, const adjamr_medium *am,
                                    const double *phi, int nsnap, adjamr_adjoint **out);
 
-/* Attach a (shared) snapshot set to ctx; takes a reference. */
+/* Attach a (shared) snapshot set (Sec. 4) to ctx; takes a reference. */
 adjamr_status adjamr_set_adjoint(adjamr_ctx *ctx, adjamr_adjoint *adj);
-/* Copy snapshots to the host: dst[nsnap][m][ay][ax]. */
+/* Copy snapshots (Sec. 4) to the host: dst[nsnap][m][ay][ax]. */
 adjamr_status adjamr_adjoint_read(adjamr_adjoint *adj, double *dst, size_t cap);
-/* Drop one reference; frees the device copy with the last one. */
+/* Drop one reference to a snapshot set (Sec. 4); frees the device copy with
+ * the last one. */
 void adjamr_adjoint_release(adjamr_adjoint *adj);
 
 /* Start a new solve in the same context: finer levels dropped, every level
@@ -285,14 +288,14 @@ adjamr_status adjamr_flag_cells(adjamr_ctx *ctx, int level, double tol, double t
  * eq:J_general), fixed pairwise summation order.  Synchronises. */
 adjamr_status adjamr_integrate_functional(adjamr_ctx *ctx, const adjamr_target *phi, double *J_out);
 
-/* Patch layout of a level, sorted by (jlo, ilo).  *n = number of patches
+/* Patch layout of a level (Sec. 3, regridding), sorted by (jlo, ilo).  *n = number of patches
  * (written even if cap is too small; then EINVAL). */
 adjamr_status adjamr_get_patches(adjamr_ctx *ctx, int level, adjamr_patch *out, int cap, int *n);
 
-/* Interior state of a level, patch by patch (q[f][j][i] per patch).
+/* Interior state of a level (Sec. 3), patch by patch (q[f][j][i] per patch).
  * cap in doubles.  Synchronises. */
 adjamr_status adjamr_read_level(adjamr_ctx *ctx, int level, double *dst, size_t cap);
-/* Overwrite the interior state of a level (same layout). */
+/* Overwrite the interior state of a level (Sec. 3; same layout). */
 adjamr_status adjamr_write_level(adjamr_ctx *ctx, int level, const double *src, size_t count);
 
 /* Richardson estimate tau of one step's local error on `level` at its current
@@ -310,19 +313,23 @@ adjamr_status adjamr_write_level(adjamr_ctx *ctx, int level, const double *src, 
  * counters and the CFL record are unchanged.  Synchronises. */
 adjamr_status adjamr_error_estimate(adjamr_ctx *ctx, int level, double *dst, size_t cap);
 
-/* Fill the ghost cells of `level` for its current time (as a step would). */
+/* Fill the ghost cells of `level` for its current time (Sec. 3: same-level
+ * copies, boundary conditions, coarse space-time interpolation; as a step would). */
 adjamr_status adjamr_fill_ghosts(adjamr_ctx *ctx, int level);
 
-/* Ghosted storage of patch k of `level`: q[m][sy][sx] with sx = nx + 4,
+/* Ghosted storage of patch k of `level` (Sec. 3): q[m][sy][sx] with sx = nx + 4,
  * sy = ny + 4 (1D: 1); med[nmed][sy][sx] = primary medium (rho, K | hbar). */
 adjamr_status adjamr_read_patch_ghosted(adjamr_ctx *ctx, int level, int k, double *q, double *med);
 
-/* Step every patch of `level` once, without recursion, regrid or ghost fill
- * (for sampled parity checks). */
+/* Step every patch of `level` once (the Sec. 3 wave-propagation step),
+ * without recursion, regrid or ghost fill (for sampled parity checks). */
 adjamr_status adjamr_step_level_only(adjamr_ctx *ctx, int level);
 
+/* Counters and timings of the context (no counterpart in the paper:
+ * measurement). */
 adjamr_status adjamr_get_stats(adjamr_ctx *ctx, adjamr_stats *out);
-/* Enable/disable CUDA-event timing of step kernels (adds events only). */
+/* Enable/disable CUDA-event timing of step kernels (adds events only; no
+ * counterpart in the paper: measurement). */
 adjamr_status adjamr_set_timing(adjamr_ctx *ctx, int enable);
 /* Step-kernel configuration of one level (level = -1: every level), used
  * from the next step on: the tile size the level's patches are cut to
@@ -339,7 +346,8 @@ adjamr_status adjamr_set_timing(adjamr_ctx *ctx, int enable);
  * or level. */
 adjamr_status adjamr_set_level_kernel(adjamr_ctx *ctx, int level, int tile_x, int tile_y, int fuse_ghosts,
                                       int launch_mode);
-/* Check of the bounded waits of ADJAMR_LAUNCH_SUBSTEPS: one substep launch
+/* Check of the bounded waits of ADJAMR_LAUNCH_SUBSTEPS (no counterpart in
+ * the paper: the failure path of this GPU launch mode): one substep launch
  * (2 substeps) of the finest level in which every tile's second substep
  * waits on a completion counter that nothing advances.  The waits give up
  * after about 1 s; the call returns ADJAMR_ETIMEOUT and the elapsed device
@@ -354,7 +362,7 @@ adjamr_status adjamr_substep_wait_selftest(adjamr_ctx *ctx, double *wait_ms);
  * finest level with a patch there.  Replaces earlier gauges and drops their
  * records.  Errors: EINVAL (n < 0, or null points with n > 0), ENOMEM. */
 adjamr_status adjamr_set_gauges(adjamr_ctx *ctx, int n, const double *x, const double *y);
-/* Gauge records so far: out[r][k][1 + m] for r < min(*nrec, cap) (out may be
+/* Gauge records so far (Sec. 5.2.4, Sec. 5.3): out[r][k][1 + m] for r < min(*nrec, cap) (out may be
  * null with cap = 0); *nrec = number of records held.  Synchronises the
  * context's stream. */
 adjamr_status adjamr_read_gauges(adjamr_ctx *ctx, double *out, long long cap, long long *nrec);
@@ -369,9 +377,13 @@ adjamr_status adjamr_read_gauges(adjamr_ctx *ctx, double *out, long long cap, lo
  * involved.  Errors: EINVAL. */
 adjamr_status adjamr_cluster_boxes(const unsigned char *flags, const unsigned char *nestable, int N, int M, int dim,
                                    int min_cells, double efficiency, int *boxes, int cap, int *nboxes);
-/* Level-0 step and number of level-0 steps to reach tf. */
+/* Level-0 step and number of level-0 steps to reach tf (Sec. 3: the levels'
+ * steps are dt0 / (r_0 ... r_{l-1})). */
 adjamr_status adjamr_time_info(adjamr_ctx *ctx, double *dt0, int *nsteps_to_tf);
+/* Text of the context's last error (no counterpart in the paper). */
 const char *adjamr_last_error(adjamr_ctx *ctx);
+/* Free the context and its device memory; drops its snapshot-set reference
+ * (no counterpart in the paper). */
 void adjamr_destroy(adjamr_ctx *ctx);
 
 /* Measurement utility (no counterpart in the paper): FP64 instruction
@@ -388,7 +400,8 @@ adjamr_status adjamr_fp64_peak(int kind, int iters, double *flops_per_s, double 
 /* ------------------------------------------------------------------ */
 typedef struct adjamr_batch adjamr_batch;
 
-/* npatch patches, 2D acoustics: patch k covers [x0[k], x1[k]] x [y0[k], y1[k]]
+/* (No counterpart in the paper: batching; every patch advances by the Sec. 3
+ * step.)  npatch patches, 2D acoustics: patch k covers [x0[k], x1[k]] x [y0[k], y1[k]]
  * with nx[k] x ny[k] cells (dx = (x1 - x0)/nx as on a level) and steps with
  * dt[k]; medium_id[k] indexes `media` (LAYERED only); q0 = interiors
  * concatenated in patch order (q[3][ny][nx] each). */
@@ -396,20 +409,24 @@ adjamr_status adjamr_batch_create(int npatch, const int *nx, const int *ny, cons
                                   const double *x1, const double *y1, const double *dt, const int *medium_id,
                                   const adjamr_medium *media, int nmedia, const double *q0, void *stream,
                                   adjamr_batch **out);
-/* Order of the tile work-list: patch order given here (a permutation). */
+/* Order of the tile work-list: patch order given here (a permutation; no
+ * counterpart in the paper). */
 adjamr_status adjamr_batch_set_order(adjamr_batch *b, const int *order);
-/* Ghost ring of the batch's patches computed inside the step kernel while
+/* (No counterpart in the paper.)  Ghost ring of the batch's patches computed inside the step kernel while
  * it stages its tiles (1) or by a separate ghost-fill kernel launched before
  * it (0, the default).  Same bits either way. */
 adjamr_status adjamr_batch_set_ghost_fusion(adjamr_batch *b, int fuse_ghosts);
-/* Advance all patches nsteps steps with the given launch mode and tile size
- * (as in adjamr_set_level_kernel). */
+/* Advance all patches nsteps steps of Sec. 3 with the given launch mode and
+ * tile size (as in adjamr_set_level_kernel). */
 adjamr_status adjamr_batch_step(adjamr_batch *b, int nsteps, int launch_mode, int tile_x, int tile_y);
-/* Capture one step (ghost fill + fused step) in a CUDA graph and replay it
- * nsteps times. */
+/* Capture one step (ghost fill + fused step of Sec. 3) in a CUDA graph and
+ * replay it nsteps times. */
 adjamr_status adjamr_batch_step_graph(adjamr_batch *b, int nsteps, int launch_mode, int tile_x, int tile_y);
+/* Interiors of all patches, concatenated as q0 was (no counterpart in the paper). */
 adjamr_status adjamr_batch_read(adjamr_batch *b, double *dst, size_t cap);
+/* Interior cells of the batch (no counterpart in the paper). */
 adjamr_status adjamr_batch_cells(adjamr_batch *b, long long *cells);
+/* Free the batch (no counterpart in the paper). */
 void adjamr_batch_destroy(adjamr_batch *b);
 
 /* ------------------------------------------------------------------ */
@@ -473,24 +490,31 @@ typedef struct adjamr_result {
     char error[128];
 } adjamr_result;
 
-/* Projected device bytes of one solve (upper bound: every level fully
+/* (No counterpart in the paper: serving, as every serving call below.)
+ * Projected device bytes of one solve (upper bound: every level fully
  * refined), used for admission.  0 for parameters no hierarchy accepts
  * (nlevels outside 1 .. ADJAMR_MAX_LEVELS, a refinement ratio outside
  * 2 .. 16); adjamr_server_submit refuses those requests with EINVAL. */
 size_t adjamr_estimate_bytes(const adjamr_params *p);
-/* max_slots worker threads on the current device; budget in bytes. */
+/* Serving (no counterpart in the paper): max_slots worker threads on the
+ * current device; budget in bytes. */
 adjamr_status adjamr_server_create(size_t budget_bytes, int max_slots, adjamr_server **out);
-/* Queue a request; EBUDGET if it can never fit the budget, EINVAL if its
+/* Queue a request (serving; no counterpart in the paper); EBUDGET if it can never fit the budget, EINVAL if its
  * parameters are refused (adjamr_estimate_bytes gives 0). */
 adjamr_status adjamr_server_submit(adjamr_server *srv, const adjamr_request *rq, long long *ticket);
-/* Non-blocking status of a ticket (res.done = 0 while queued or running). */
+/* Non-blocking status of a ticket (res.done = 0 while queued or running;
+ * serving, no counterpart in the paper). */
 adjamr_status adjamr_server_poll(adjamr_server *srv, long long ticket, adjamr_result *out);
-/* Block until the ticket is done. */
+/* Block until the ticket is done (serving, no counterpart in the paper). */
 adjamr_status adjamr_server_wait(adjamr_server *srv, long long ticket, adjamr_result *out);
+/* Reserved bytes, running and queued requests (serving, no counterpart in
+ * the paper). */
 adjamr_status adjamr_server_info(adjamr_server *srv, size_t *used_bytes, int *active, int *queued);
+/* Seconds since the server was created: the clock of the results' times
+ * (serving, no counterpart in the paper). */
 double adjamr_server_now(adjamr_server *srv);
 /* Stops the workers after the running requests finish; queued requests are
- * dropped (status ESTATE). */
+ * dropped (status ESTATE; serving, no counterpart in the paper). */
 void adjamr_server_destroy(adjamr_server *srv);
 
 #ifdef __cplusplus

@@ -92,3 +92,24 @@ def test_parameters_are_validated_before_any_device_call():
     assert not out.value
     p.flag_mode = W.FLAG_ERROR
     assert L.adjamr_estimate_bytes(ctypes.byref(p)) > est[4]
+
+
+def test_every_entry_point_cites_its_passage_or_says_it_has_none():
+    """Each function declared in include/adjamr.h is preceded by a comment
+    that cites the passage of the paper it implements (a section or an
+    equation) or states that it has no counterpart in the paper."""
+    import re
+    lines = open(os.path.join(ROOT, "include", "adjamr.h")).read().splitlines()
+    missing = []
+    for i, line in enumerate(lines):
+        m = re.match(r"^(?:adjamr_status|void|size_t|double|int|const char \*)\s*(adjamr_\w+)\(", line)
+        if not m:
+            continue
+        j, com = i - 1, []
+        while j >= 0 and (lines[j].strip().startswith(("*", "/*", "#define")) or lines[j].strip().endswith("*/")):
+            com.insert(0, lines[j])
+            j -= 1
+        text = re.sub(r"\s+", " ", re.sub(r"(/\*|\*/|^\s*\*)", " ", "\n".join(com), flags=re.M))
+        if not re.search(r"Secs?\.|Eq\.|[Nn]o counterpart", text):
+            missing.append(m.group(1))
+    assert not missing, missing
