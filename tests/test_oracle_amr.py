@@ -655,3 +655,11 @@ def test_adjoint_with_amr_limits_and_accuracy():
             for tol in (0.1, 0.03, 0.01)]
     assert errs[0] > errs[1] > errs[2], errs
     assert errs[2] < 1e-3 * e_uni, (errs, e_uni)
+    # the same with the standard Richardson flagger (Sec. 1) on the adjoint's
+    # own error estimate: exact limits, and the error falls with the tolerance
+    assert np.array_equal(O.adjoint_solve_amr(wl, ratios, W.FLAG_RICHARDSON, math.inf), uni)
+    assert np.array_equal(O.adjoint_solve_amr(wl, ratios, W.FLAG_RICHARDSON, -1.0), ref)
+    errs = [float(np.abs(O.adjoint_solve_amr(wl, ratios, W.FLAG_RICHARDSON, tol) - ref).max())
+            for tol in (3e-3, 1e-3, 3e-4)]
+    assert errs[0] > errs[1] > errs[2], errs
+    assert errs[2] < 1e-3 * e_uni, (errs, e_uni)
