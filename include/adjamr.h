@@ -230,7 +230,7 @@ adjamr_status adjamr_load_adjoint_snapshots(adjamr_ctx *ctx, const double *snaps
  * t0)/(nsnap - 1).  ap->nlevels = 1: a fixed grid, as in the paper.
  * ap->nlevels > 1: the adjoint solved with AMR (Sec. 7 proposes it for a
  * more accurate inner product): finer levels by ap->ratio, flagged by the
- * standard flagger ap->flag_mode (DIFFERENCE or SURFACE; EINVAL otherwise)
+ * standard flagger ap->flag_mode (DIFFERENCE, SURFACE or RICHARDSON; EINVAL otherwise)
  * at ap->tol and regridded every ap->regrid_interval steps as in a forward
  * run; their initial cells are interpolated from phi on level 0; each
  * level-0 step is a full Berger-Oliger step, so the snapshot is level 0

@@ -2569,7 +2569,9 @@ adjamr_status adjamr_solve_adjoint(adjamr_ctx *ctx, const adjamr_params *ap, con
                                                                 ap->eqn != ADJAMR_SW_ADJOINT))
         return ADJAMR_EINVAL;
     const bool amr = ap->nlevels > 1;
-    if (amr && ap->flag_mode != ADJAMR_FLAG_DIFFERENCE && ap->flag_mode != ADJAMR_FLAG_SURFACE) return ADJAMR_EINVAL;
+    if (amr && ap->flag_mode != ADJAMR_FLAG_DIFFERENCE && ap->flag_mode != ADJAMR_FLAG_SURFACE &&
+        ap->flag_mode != ADJAMR_FLAG_RICHARDSON)
+        return ADJAMR_EINVAL;
     if (!(ap->cmax > 0.0) || ap->n0[0] < 1 || (ap->dim == 2 && ap->n0[1] < 1) || !(ap->tf > ap->t0))
         return ADJAMR_EINVAL;
     try {

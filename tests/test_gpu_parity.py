@@ -872,13 +872,17 @@ def test_flag_time_range_per_call_and_level0_only_advance(A):
     g.close()
 
 
-@pytest.mark.parametrize("case", ["acoustics2d", "acoustics2d_reflux", "acoustics1d", "shallow_water2d"])
+@pytest.mark.parametrize("case", ["acoustics2d", "acoustics2d_reflux", "acoustics1d", "shallow_water2d",
+                                  "acoustics2d_richardson", "shallow_water2d_richardson"])
 def test_adjoint_with_amr_matches_oracle(A, case):
     """The adjoint solved with AMR (finer levels flagged by the undivided
-    differences of the adjoint solution, snapshots from level 0 after every
+    differences of the adjoint solution -- or, the _richardson cases, by its
+    Richardson error estimate --, snapshots from level 0 after every
     Berger-Oliger step): every snapshot equal to the oracle's bit for bit, in
     1D and 2D acoustics (with and without the conservation fix-up) and the
     shallow-water adjoint over bathymetry; the fixed-grid adjoint differs."""
+    flag = W.FLAG_RICHARDSON if case.endswith("_richardson") else W.FLAG_DIFFERENCE
+    case = case.replace("_richardson", "")
     med = None
     if case.startswith("acoustics2d"):
         wl = W.config2(seed=3, n0=32, adj_n=32, tf=2.0, nsnap=6, bc=(W.BC_WALL,) * 4)
@@ -891,8 +895,10 @@ def test_adjoint_with_amr_matches_oracle(A, case):
         ratios, tol = (2, 2), 0.02
         med = W.config3_adjoint_medium(wl, ratios=ratios)
     reflux = 1 if case.endswith("reflux") else 0
-    ref = O.adjoint_solve_amr(wl, ratios, W.FLAG_DIFFERENCE, tol, medium_dense_levels=med, reflux=reflux)
-    adj = A.solve_adjoint(wl, amr=(ratios, W.FLAG_DIFFERENCE, tol, reflux), medium_dense=med)
+    if flag == W.FLAG_RICHARDSON:
+        tol = 1e-3 if case.startswith("acoustics") else 1e-4
+    ref = O.adjoint_solve_amr(wl, ratios, flag, tol, medium_dense_levels=med, reflux=reflux)
+    adj = A.solve_adjoint(wl, amr=(ratios, flag, tol, reflux), medium_dense=med)
     got = adj.read()
     adj.release()
     assert np.array_equal(got, ref)
