@@ -324,6 +324,8 @@ __device__ bool coarse_desc_dev(int I, int J, int r, const int *__restrict__ own
 __global__ void k_owner_fill(const PatchDesc *__restrict__ pd, const long long *__restrict__ prefix, int np,
                              long long ncells, LevelIdx g, int *owner)
 {
+    pdl_wait();
+    pdl_launch_dependents();
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ncells) return;
     int p = find_in_prefix(prefix, np, t);
@@ -338,6 +340,8 @@ __global__ void k_ghost_build(const PatchDesc *__restrict__ pd, const long long 
                               const int *__restrict__ owner_c, LevelIdx gc, int r, GhostDesc *out, int *err,
                               int *cmark, int cgen, unsigned long long *clist)
 {
+    pdl_wait();
+    pdl_launch_dependents();
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nghost) return;
     int p = find_in_prefix(gprefix, np, t);
@@ -387,6 +391,8 @@ __global__ void k_avg_build(const PatchDesc *__restrict__ pd, const long long *_
                             long long navg, int dim, int r, const int *__restrict__ owner_c, LevelIdx gc,
                             AvgDesc *out, int *err)
 {
+    pdl_wait();
+    pdl_launch_dependents();
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= navg) return;
     int p = find_in_prefix(aprefix, np, t);
@@ -416,6 +422,8 @@ __global__ void k_init_new(const PatchDesc *__restrict__ pd, const long long *__
                            const int *__restrict__ owner_c, LevelIdx gc, const double *__restrict__ qc, long long sc,
                            int r, int *err)
 {
+    pdl_wait();
+    pdl_launch_dependents();
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ncells) return;
     int p = find_in_prefix(prefix, np, t);
@@ -439,6 +447,8 @@ __global__ void k_aux_patches(int eqn, const PatchDesc *__restrict__ pd, const l
                               int np, long long nstore, LevelIdx g, double *aux, double *med, long long stride,
                               const MediumDev *__restrict__ mdp, LevelGeom geom, AuxReuse ru, AuxTable tb)
 {
+    pdl_wait();
+    pdl_launch_dependents();
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nstore) return;
     int p = find_in_prefix(sprefix, np, t);
@@ -1099,8 +1109,7 @@ cudaError_t launch_owner_fill(const PatchDesc *p, const long long *prefix, int n
                               int *owner, cudaStream_t s)
 {
     if (ncells <= 0) return cudaSuccess;
-    k_owner_fill<<<nblk(ncells), kT, 0, s>>>(p, prefix, np, ncells, g, owner);
-    return cudaGetLastError();
+    return launch_pdl(k_owner_fill, dim3(nblk(ncells)), dim3(kT), 0, s, p, prefix, np, ncells, g, owner);
 }
 
 cudaError_t launch_ghost_build(const PatchDesc *p, const long long *gprefix, int np, long long nghost, LevelIdx g,
@@ -1109,17 +1118,16 @@ cudaError_t launch_ghost_build(const PatchDesc *p, const long long *gprefix, int
 {
     if (nghost <= 0) return cudaSuccess;
     if (cmark && (cgen <= 0 || !clist)) return cudaErrorInvalidValue;
-    k_ghost_build<<<nblk(nghost), kT, 0, s>>>(p, gprefix, np, nghost, g, owner, owner_c, gc, r, out, err, cmark, cgen,
-                                              clist);
-    return cudaGetLastError();
+    return launch_pdl(k_ghost_build, dim3(nblk(nghost)), dim3(kT), 0, s, p, gprefix, np, nghost, g, owner, owner_c, gc,
+                      r, out, err, cmark, cgen, clist);
 }
 
 cudaError_t launch_avg_build(const PatchDesc *p, const long long *aprefix, int np, long long navg, int dim, int r,
                              const int *owner_c, LevelIdx gc, AvgDesc *out, int *err, cudaStream_t s)
 {
     if (navg <= 0) return cudaSuccess;
-    k_avg_build<<<nblk(navg), kT, 0, s>>>(p, aprefix, np, navg, dim, r, owner_c, gc, out, err);
-    return cudaGetLastError();
+    return launch_pdl(k_avg_build, dim3(nblk(navg)), dim3(kT), 0, s, p, aprefix, np, navg, dim, r, owner_c, gc, out,
+                      err);
 }
 
 cudaError_t launch_errest_fill(const ErrEstArgs &a, LevelIdx g, const int *owner, const double *q, long long sq,
@@ -1151,9 +1159,8 @@ cudaError_t launch_init_new(const PatchDesc *p, const long long *prefix, int np,
                             cudaStream_t s)
 {
     if (ncells <= 0) return cudaSuccess;
-    k_init_new<<<nblk(ncells), kT, 0, s>>>(p, prefix, np, ncells, g, m, qf, sf, owner_old, qold, so, owner_c, gc, qc,
-                                            sc, r, err);
-    return cudaGetLastError();
+    return launch_pdl(k_init_new, dim3(nblk(ncells)), dim3(kT), 0, s, p, prefix, np, ncells, g, m, qf, sf, owner_old,
+                      qold, so, owner_c, gc, qc, sc, r, err);
 }
 
 cudaError_t launch_aux_patches(int eqn, const PatchDesc *p, const long long *sprefix, int np, long long nstore,
@@ -1161,8 +1168,8 @@ cudaError_t launch_aux_patches(int eqn, const PatchDesc *p, const long long *spr
                                LevelGeom geom, cudaStream_t s, AuxReuse ru, AuxTable tb)
 {
     if (nstore <= 0) return cudaSuccess;
-    k_aux_patches<<<nblk(nstore), kT, 0, s>>>(eqn, p, sprefix, np, nstore, g, aux, med, stride, mdev, geom, ru, tb);
-    return cudaGetLastError();
+    return launch_pdl(k_aux_patches, dim3(nblk(nstore)), dim3(kT), 0, s, eqn, p, sprefix, np, nstore, g, aux, med,
+                      stride, mdev, geom, ru, tb);
 }
 
 cudaError_t launch_aux_table(int eqn, const MediumDev *mdev, LevelGeom geom, double *tab, cudaStream_t s)
