@@ -881,12 +881,14 @@ def run_case_solve(args):
     --kernels (default: the configuration the autotuner picks on a GB300,
     12x8 fused, 8x8 fused, 16x12 with a separate ghost fill); prints
     per-level step statistics.  --flag error --tol T: flagged by the
-    adjoint-weighted error estimate (Sec. 7) instead."""
+    adjoint-weighted error estimate (Sec. 7) instead; --config 1 or 3: that
+    workload instead of config 2 (config 1 with its default kernels)."""
     import torch
     from paper_1511_03645_gb300 import adjamr as A
     torch.cuda.set_device(0)
     s = torch.cuda.Stream()
-    wl = workload()
+    from paper_1511_03645_gb300 import workloads as W
+    wl = {"2": workload, "1": W.config1, "3": lambda: W.config3(seed=0)}[args.config]()
     if args.tf:
         wl.tf = args.tf
     if args.flag != "adjoint":
@@ -894,10 +896,11 @@ def run_case_solve(args):
         wl.flag_mode = W.FLAG_ERROR if args.flag == "error" else W.FLAG_RICHARDSON
     if args.tol > 0:
         wl.tol = args.tol
-    adj = A.solve_adjoint(wl, stream=s.cuda_stream)
+    adj = A.solve_adjoint(wl, stream=s.cuda_stream,
+                          medium_dense=W.config3_adjoint_medium(wl) if args.config == "3" else None)
     for rep in range(1 + args.warmup):
         h = A.Hierarchy(wl, stream=s.cuda_stream)
-        for lev, spec in enumerate(args.kernels.split(",")[:wl.nlevels]):
+        for lev, spec in enumerate(args.kernels.split(",")[:wl.nlevels] if args.config != "1" else []):
             # suffix f: ghost ring in the step kernel; s: substep launches (finest level)
             fused, sub = spec.endswith("f"), spec.endswith("s")
             tx, ty = (int(v) for v in spec.rstrip("fs").split("x"))
@@ -935,6 +938,8 @@ def main():
                     help="solve case: adjoint flagging (bracket rule), the adjoint-weighted error estimate, or "
                          "the estimate alone (Richardson)")
     ap.add_argument("--tol", type=float, default=0.0, help="solve case: flag tolerance (0: the workload's)")
+    ap.add_argument("--config", default="2", choices=["1", "2", "3"],
+                    help="solve case: the workload (config 1 runs with the default 1D kernels)")
     ap.add_argument("--kernels", default="12x8f,8x8f,16x12",
                     help="solve case: per-level step tile, suffix f = ghost ring computed in the step kernel")
     ap.add_argument("--nreq", type=int, default=512)
