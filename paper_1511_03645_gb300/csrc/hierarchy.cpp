@@ -1667,6 +1667,7 @@ adjamr_status regrid_body(adjamr_ctx *c, int base, int init, bool side_flags)
 }
 
 constexpr int kFlagBlocksPerThread = 1;
+constexpr long long kFlagOnePassMax = 1ll << 16;  // (cell, snapshot block) pairs decided in one pass
 
 // Per-column and per-row bilinear tables of the attached adjoint grid for
 // level l (the same arithmetic as the flag kernel's per-cell setup: cell
@@ -1824,12 +1825,17 @@ adjamr_status flag_dense(adjamr_ctx *c, int l, double tol, uint64_t *d_bits, int
         // two passes through a work list of (cell, block) pairs; a list too
         // short for this call is grown (up to kFlagItemsMax) and the call redone,
         // beyond that the one-pass kernel decides
+        // A level of few (cell, block) pairs (a 1D level of a few hundred
+        // cells) is decided by the one-pass kernel alone: its single launch
+        // costs less than the two passes' two there (the same decisions).
+        const bool tiny = (long long)L.N * L.M * nblk <= kFlagOnePassMax;
         const long long want = std::min((long long)L.N * L.M * nblk, kFlagItemsMax);
-        if (c->fcap < std::min(want, (long long)1 << 20)) TRY(grow_flag_list(c, std::min(want, (long long)1 << 20)));
+        if (!tiny && c->fcap < std::min(want, (long long)1 << 20))
+            TRY(grow_flag_list(c, std::min(want, (long long)1 << 20)));
         for (int attempt = 0;; attempt++) {
             if (attempt > 0)
                 CKR(c, cudaMemsetAsync(head, 0, kPinHead + (size_t)pitch64 * L.M * sizeof(uint64_t), c->s));
-            const bool twopass = attempt == 0 || c->fcap >= (long long)L.N * L.M * nblk;
+            const bool twopass = !tiny && (attempt == 0 || c->fcap >= (long long)L.N * L.M * nblk);
             if (twopass) {
                 CKR(c, launch_flag_twopass(a, FlagWork{c->d_fitems, fctr, c->fcap}, c->nsm * 8, c->s));
                 c->st.kernel_launches += 2;
