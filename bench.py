@@ -329,7 +329,7 @@ def run_ours(args, rank, world):
     Js = []
     regrid_ms = 0.0
     cluster_ms = 0.0
-    rebuilds = 0
+    rebuilds = kept = 0
     phases = [0.0] * 6
     cphases = [0.0] * 4
     lev_ms = [0.0] * wl.nlevels
@@ -352,6 +352,7 @@ def run_ours(args, rank, world):
         regrid_ms += st["regrid_host_ms"]
         cluster_ms += st["cluster_host_ms"]
         rebuilds += st["level_rebuilds"]
+        kept += st["level_rebuilds_skipped"]
         phases = [a + b for a, b in zip(phases, st["regrid_phase_ms"])]
         cphases = [a + b for a, b in zip(cphases, st["cluster_phase_ms"])]
         Js.append(J)
@@ -541,6 +542,7 @@ def run_ours(args, rank, world):
         "breakdown_per_step_ms": {"step_kernels": step_ms / args.steps, "regrid_host_wall": regrid_ms / args.steps,
                                   "of_which_clustering": cluster_ms / args.steps,
                                   "level_rebuilds": rebuilds / args.steps,
+                                  "levels_kept_unchanged": kept / args.steps,
                                   "regrid_phases": dict(zip(["flag_and_wait", "window_copy", "clustering",
                                                              "arena_alloc_upload", "builder_kernels", "release_old"],
                                                             [v / args.steps for v in phases])),
@@ -921,7 +923,9 @@ def run_case_solve(args):
                       "level_step_ms": st["level_step_ms"][:wl.nlevels],
                       "level_step_launches": st["level_step_launches"][:wl.nlevels],
                       "level_cell_updates": st["level_cell_updates"][:wl.nlevels],
-                      "regrid_phase_ms": st["regrid_phase_ms"]}), flush=True)
+                      "regrid_phase_ms": st["regrid_phase_ms"], "regrids": st["regrids"],
+                      "level_rebuilds": st["level_rebuilds"],
+                      "levels_kept_unchanged": st["level_rebuilds_skipped"]}), flush=True)
 
 
 def main():

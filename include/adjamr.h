@@ -196,6 +196,10 @@ typedef struct adjamr_stats {
      * (the separate ghost fill and the coarse stencil values), if timing
      * enabled; level_step_ms counts the step kernels alone */
     double level_ghost_ms[ADJAMR_MAX_LEVELS];
+    /* regrids that found a level's new boxes equal to its current ones over an
+     * unchanged coarser level (an empty level staying empty included) and kept
+     * it as it was: the rebuild would have reproduced it bit for bit */
+    long long level_rebuilds_skipped;
 } adjamr_stats;
 
 typedef struct adjamr_ctx adjamr_ctx;

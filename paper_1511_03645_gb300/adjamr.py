@@ -89,7 +89,8 @@ class Stats(ctypes.Structure):
                 ("level_step_launches", ctypes.c_longlong * MAXLEV),
                 ("level_cell_updates", ctypes.c_longlong * MAXLEV),
                 ("cluster_phase_ms", ctypes.c_double * 4),
-                ("level_ghost_ms", ctypes.c_double * MAXLEV)]
+                ("level_ghost_ms", ctypes.c_double * MAXLEV),
+                ("level_rebuilds_skipped", ctypes.c_longlong)]
 
 
 # every entry point declared in include/adjamr.h

@@ -373,6 +373,18 @@ int find_patch(Level &L, int I, int J)
     return -1;
 }
 
+// the level's patches are exactly the boxes b, in order
+bool same_layout(const Level &L, const std::vector<Box> &b)
+{
+    if (L.patches.size() != b.size()) return false;
+    for (size_t k = 0; k < b.size(); k++) {
+        const HPatch &p = L.patches[k];
+        if (p.ilo != b[k].i0 || p.jlo != b[k].j0 || p.nx != b[k].i1 - b[k].i0 + 1 || p.ny != b[k].j1 - b[k].j0 + 1)
+            return false;
+    }
+    return true;
+}
+
 void reflux_release(adjamr_ctx *c, Level &L)
 {
     cput(c, L.d_rcells);
@@ -1477,6 +1489,7 @@ adjamr_status regrid_flags(adjamr_ctx *c, int lev, long long *nf, int *bb)
 adjamr_status regrid_body(adjamr_ctx *c, int base, int init, bool side_flags)
 {
     const adjamr_params &P = c->P;
+    bool coarser_rebuilt = false;  // level lev was rebuilt earlier in this call
     for (int lev = base; lev < P.nlevels - 1; lev++) {
         Level &C = c->L[lev];
         Level &F = c->L[lev + 1];
@@ -1600,6 +1613,20 @@ adjamr_status regrid_body(adjamr_ctx *c, int base, int init, bool side_flags)
         std::vector<Box> fb;
         for (const Box &b : fin)
             fb.push_back(Box{b.i0 * r, (b.i1 + 1) * r - 1, dim == 2 ? b.j0 * r : 0, dim == 2 ? (b.j1 + 1) * r - 1 : 0});
+        // The boxes the level has now, over a coarser level this call left as
+        // it was: the rebuild would give every cell its old value at its old
+        // storage index (new patches take the old fine values wherever they
+        // exist), the same ghost and average-down maps and the same work
+        // lists, so the level stays as it is.  An empty level stays empty.
+        if (!init && !coarser_rebuilt && F.d_owner && same_layout(F, fb)) {
+            F.nstep = C.nstep * r;
+            if (F.patches.empty()) F.cur = 0;
+            c->rebuilt_tick[lev + 1] = tick;
+            c->st.level_rebuilds_skipped++;
+            if (F.patches.empty()) break;
+            continue;
+        }
+        coarser_rebuilt = true;
         Level old;
         std::swap(old.patches, F.patches);
         std::swap(old.buckets, F.buckets);

@@ -503,6 +503,46 @@ def test_degenerate_parameters_match_oracle(A, case):
     assert abs(g.functional() - o.functional()) <= RTOL * max(abs(o.functional()), 1e-300)
 
 
+@pytest.mark.parametrize("case", ["c2", "c2_rx", "c1"])
+def test_unchanged_layout_is_kept(A, case):
+    """A regrid that finds a level's current boxes again, over a coarser level
+    it left as it was, keeps the level (a rebuild would reproduce it bit for
+    bit): a second regrid at the same state keeps every finer level, an empty
+    level stays empty without a rebuild, and the runs then go on to the
+    oracle's results, whose regrids always rebuild."""
+    if case == "c1":
+        wl = W.config1(n0=100, tf=6.0, adj_n=400, nsnap=30)
+    else:
+        wl = W.config2(seed=3, n0=32, ratios=(2, 4), tf=2.0, adj_n=64, nsnap=20, ts=0.0, tol=1e-4,
+                       min_patch=8, max_patch=32)
+    wl.reflux = 1 if case.endswith("_rx") else 0
+    snaps = O.adjoint_solve(wl)
+    o, g = _amr_pair(A, wl, snaps=snaps)
+    n = o.nsteps_total()
+    k = n // 3
+    o.advance(k)
+    g.advance(k)
+    # the first regrid at this state may change the layout (the last one ran
+    # at an earlier step); the second finds the same boxes on every level
+    o.regrid(0)
+    g.regrid(0)
+    _compare_all(o, g, wl.nlevels)
+    nfine = [len(g.patches(lev)) for lev in range(1, wl.nlevels)]
+    kept0, built0 = g.stats()["level_rebuilds_skipped"], g.stats()["level_rebuilds"]
+    o.regrid(0)
+    g.regrid(0)
+    _compare_all(o, g, wl.nlevels)
+    st = g.stats()
+    # every finer level up to the first empty one is kept, none rebuilt
+    want = next((i + 1 for i, c in enumerate(nfine) if c == 0), len(nfine))
+    assert st["level_rebuilds_skipped"] - kept0 == want
+    assert st["level_rebuilds"] == built0
+    o.advance(n - k)
+    g.advance(n - k)
+    _compare_all(o, g, wl.nlevels)
+    assert abs(g.functional() - o.functional()) <= RTOL * max(abs(o.functional()), 1e-300)
+
+
 def test_cfl_violation_is_reported(A):
     """Courant number above cfl_max returns ADJAMR_ECFL, not a crash."""
     wl = W.config2(seed=5, n0=16, ratios=(2,), tf=0.5)
