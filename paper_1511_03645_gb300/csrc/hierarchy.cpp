@@ -18,6 +18,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <unordered_map>
 #include <vector>
 
@@ -197,6 +198,14 @@ struct adjamr_ctx {
     int *d_gij = nullptr;           // [2][nlevels][ngauge]: I then J
     double *d_grec = nullptr;       // [gcap][ngauge][1 + m]
     long long ngrec = 0, gcap = 0;
+    // the builders of the level a regrid is rebuilding, recorded (pend_on)
+    // instead of launched and then launched together by launch_rebuild
+    bool pend_on = false;
+    adjamr::OwnerFillArgs pend_o{};
+    adjamr::AuxPatchesArgs pend_x{};
+    adjamr::InitNewArgs pend_in{};
+    adjamr::GhostBuildArgs pend_gb{};
+    adjamr::AvgBuildArgs pend_ab{};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // step-kernel timing without host synchronisation: event pairs recorded
     // around every step launch, read when the stream is synchronised
@@ -624,6 +633,51 @@ LevelIdx idx_of(const adjamr_ctx *c, int l)
 }
 
 // allocate the arena of a level for the given boxes (level index space)
+// A builder kernel of a level's layout: launched now, or recorded for the
+// combined launches of the rebuild in progress (flush_rebuild).
+template <typename Args>
+adjamr_status run_builder(adjamr_ctx *c, const Args &a)
+{
+    if (c->pend_on) {
+        if constexpr (std::is_same_v<Args, OwnerFillArgs>) c->pend_o = a;
+        else if constexpr (std::is_same_v<Args, AuxPatchesArgs>) c->pend_x = a;
+        else if constexpr (std::is_same_v<Args, InitNewArgs>) c->pend_in = a;
+        else if constexpr (std::is_same_v<Args, GhostBuildArgs>) c->pend_gb = a;
+        else c->pend_ab = a;
+        return ADJAMR_OK;
+    }
+    cudaError_t e;
+    if constexpr (std::is_same_v<Args, OwnerFillArgs>) e = launch_owner_fill(a, c->s);
+    else if constexpr (std::is_same_v<Args, AuxPatchesArgs>) e = launch_aux_patches(a, c->s);
+    else if constexpr (std::is_same_v<Args, InitNewArgs>) e = launch_init_new(a, c->s);
+    else if constexpr (std::is_same_v<Args, GhostBuildArgs>) e = launch_ghost_build(a, c->s);
+    else e = launch_avg_build(a, c->s);
+    CKR(c, e);
+    if (a.n > 0) c->st.kernel_launches++;
+    return ADJAMR_OK;
+}
+
+void pend_clear(adjamr_ctx *c)
+{
+    c->pend_on = false;
+    c->pend_o = {};
+    c->pend_x = {};
+    c->pend_in = {};
+    c->pend_gb = {};
+    c->pend_ab = {};
+}
+
+// Launch the recorded builders (two kernels at most) and stop recording.
+adjamr_status flush_rebuild(adjamr_ctx *c)
+{
+    int nl = 0;
+    const cudaError_t e = launch_rebuild(c->pend_o, c->pend_x, c->pend_in, c->pend_gb, c->pend_ab, c->s, &nl);
+    c->st.kernel_launches += nl;
+    pend_clear(c);
+    CKR(c, e);
+    return ADJAMR_OK;
+}
+
 adjamr_status alloc_level(adjamr_ctx *c, int l, const std::vector<Box> &boxes)
 {
     Level &L = c->L[l];
@@ -685,11 +739,9 @@ adjamr_status alloc_level(adjamr_ctx *c, int l, const std::vector<Box> &boxes)
     }
     CKR(c, cget(c, &L.d_owner, (size_t)L.N * L.M));
     CKR(c, cudaMemsetAsync(L.d_owner, 0xff, sizeof(int) * (size_t)L.N * L.M, c->s));
-    if (!L.patches.empty()) {
-        CKR(c, launch_owner_fill(L.d_patches, L.d_prefix, (int)L.patches.size(), L.ninterior, idx_of(c, l), L.d_owner,
-                                 c->s));
-        c->st.kernel_launches++;
-    }
+    if (!L.patches.empty())
+        TRY(run_builder(c, OwnerFillArgs{L.d_patches, L.d_prefix, (int)L.patches.size(), L.ninterior, idx_of(c, l),
+                                         L.d_owner}));
     L.buckets.clear();  // rebuilt on demand by the host lookups
     L.work_tx = L.work_ty = 0;
     return build_work(c, l, c->ltx[l], c->lty[l]);
@@ -725,10 +777,8 @@ adjamr_status fill_aux(adjamr_ctx *c, int l, const Level *old = nullptr)
         ru.med = old->med;
         ru.stride = old->ncell;
     }
-    CKR(c, launch_aux_patches(c->P.eqn, L.d_patches, L.d_sprefix, (int)L.patches.size(), L.nstore, idx_of(c, l),
-                              L.aux, L.med, L.ncell, L.d_med, geom_of(c, l), c->s, ru, tb));
-    c->st.kernel_launches++;
-    return ADJAMR_OK;
+    return run_builder(c, AuxPatchesArgs{c->P.eqn, L.d_patches, L.d_sprefix, (int)L.patches.size(), L.nstore,
+                                         idx_of(c, l), L.aux, L.med, L.ncell, L.d_med, geom_of(c, l), ru, tb});
 }
 
 // ghost map of level l (needs level l-1 when l > 0), built on the device
@@ -766,11 +816,9 @@ adjamr_status build_ghost_map(adjamr_ctx *c, int l)
         gen = c->cgen;
         L.cpre_sc = C.ncell;
     }
-    CKR(c, launch_ghost_build(L.d_patches, L.d_gprefix, (int)L.patches.size(), L.nghost, idx_of(c, l), L.d_owner, oc,
-                              gc, r, L.d_ghost, c->d_err, c->s, l > 0 ? L.d_cmark : nullptr, gen,
-                              l > 0 ? L.d_clist : nullptr));
-    c->st.kernel_launches++;
-    return ADJAMR_OK;
+    return run_builder(c, GhostBuildArgs{L.d_patches, L.d_gprefix, (int)L.patches.size(), L.nghost, idx_of(c, l),
+                                         L.d_owner, oc, gc, r, L.d_ghost, c->d_err, l > 0 ? L.d_cmark : nullptr, gen,
+                                         l > 0 ? L.d_clist : nullptr});
 }
 
 // Coarse stencil values of level l's kind-1 ghost cells for all substeps of
@@ -829,10 +877,8 @@ adjamr_status build_avg_map(adjamr_ctx *c, int l)
     F.navg = F.navg_cells;
     if (F.navg == 0) return ADJAMR_OK;
     CKR(c, cget(c, &F.d_avg, (size_t)F.navg));
-    CKR(c, launch_avg_build(F.d_patches, F.d_aprefix, (int)F.patches.size(), F.navg, c->P.dim, c->P.ratio[l - 1],
-                            c->L[l - 1].d_owner, idx_of(c, l - 1), F.d_avg, c->d_err, c->s));
-    c->st.kernel_launches++;
-    return ADJAMR_OK;
+    return run_builder(c, AvgBuildArgs{F.d_patches, F.d_aprefix, (int)F.patches.size(), F.navg, c->P.dim,
+                                       c->P.ratio[l - 1], c->L[l - 1].d_owner, idx_of(c, l - 1), F.d_avg, c->d_err});
 }
 
 // ---------------------------------------------------------------- clustering
@@ -1644,6 +1690,15 @@ adjamr_status regrid_body(adjamr_ctx *c, int base, int init, bool side_flags)
         F.d_gprefix = F.d_sprefix = F.d_aprefix = nullptr;
         F.d_owner = nullptr;
         tp = std::chrono::steady_clock::now();
+        // The level's builders go out as two launches (launch_rebuild), except
+        // under substep launches, whose work list reads the new owner map as it
+        // is built.  Recording stops, and a record left by an error is dropped,
+        // on every way out of this iteration.
+        struct PendOff {
+            adjamr_ctx *c;
+            ~PendOff() { pend_clear(c); }
+        } pend_off{c};
+        c->pend_on = c->lmode[lev + 1] != ADJAMR_LAUNCH_SUBSTEPS;
         TRY(alloc_level(c, lev + 1, fb));
         c->st.regrid_phase_ms[3] += ms_since(tp);
         tp = std::chrono::steady_clock::now();
@@ -1670,15 +1725,17 @@ adjamr_status regrid_body(adjamr_ctx *c, int base, int init, bool side_flags)
                             for (int f = 0; f < c->m; f++) host[(size_t)f * F.ncell + cell_of(c, p, i, j)] = qv[(size_t)f * n + o];
                 CKR(c, cudaMemcpyAsync(F.q[0], host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, c->s));
             } else {
-                CKR(c, launch_init_new(F.d_patches, F.d_prefix, (int)F.patches.size(), F.ninterior, idx_of(c, lev + 1),
-                                       c->m, F.q[0], F.ncell, old.patches.empty() ? nullptr : old.d_owner,
-                                       old.q[0] ? old.q[old.cur] : F.q[0], old.ncell, C.d_owner, idx_of(c, lev),
-                                       C.q[C.cur], C.ncell, r, c->d_err, c->s));
-                c->st.kernel_launches++;
+                TRY(run_builder(c, InitNewArgs{F.d_patches, F.d_prefix, (int)F.patches.size(), F.ninterior,
+                                               idx_of(c, lev + 1), c->m, F.q[0], F.ncell,
+                                               old.patches.empty() ? nullptr : old.d_owner,
+                                               old.q[0] ? old.q[old.cur] : F.q[0], old.ncell, C.d_owner,
+                                               idx_of(c, lev), C.q[C.cur], C.ncell, r, c->d_err}));
             }
             TRY(build_ghost_map(c, lev + 1));
             TRY(build_avg_map(c, lev + 1));
         }
+        // (before the old arena goes back to the cache: the new cells read it)
+        if (c->pend_on) TRY(flush_rebuild(c));
         c->st.regrid_phase_ms[4] += ms_since(tp);
         tp = std::chrono::steady_clock::now();
         free_level(c, old);

@@ -407,29 +407,77 @@ cudaError_t launch_errest_fill(const ErrEstArgs &a, LevelIdx g, const int *owner
 cudaError_t launch_errest_tau(const ErrEstArgs &a, const long long *iprefix, long long ninterior, double *tau,
                               long long st, cudaStream_t s);
 
-// Device-side regrid support.  owner[J*N + I] = arena index of interior cell
-// (I, J) of the level, or -1.  Prefix arrays have np+1 entries.
-cudaError_t launch_owner_fill(const PatchDesc *p, const long long *prefix, int np, long long ncells, LevelIdx g,
-                              int *owner, cudaStream_t s);
+// Device-side regrid support: the kernels that build a level's new layout,
+// one thread per interior cell, storage cell, ghost cell or coarse cell under
+// the level (n = 0: nothing to do).  Prefix arrays have np+1 entries.
+//
+// owner[J*N + I] = arena index of interior cell (I, J) of the level, or -1
+// (the map is set to -1 beforehand).
+struct OwnerFillArgs {
+    const PatchDesc *pd;
+    const long long *prefix;
+    int np;
+    long long n;
+    LevelIdx g;
+    int *owner;
+};
 // ghost descriptors of every patch of a level; gprefix = ghost-cell prefix.
 // owner_c / gc describe the coarser level (owner_c null on level 0).
 // cmark / clist (levels > 0): also lists one kind-1 ghost cell per distinct
 // coarse cell, clist[0] = count (zeroed beforehand), clist[1 + e] = ghost
 // index; a coarse cell is taken when its mark was not yet cgen (> 0)
-cudaError_t launch_ghost_build(const PatchDesc *p, const long long *gprefix, int np, long long nghost, LevelIdx g,
-                               const int *owner, const int *owner_c, LevelIdx gc, int r, GhostDesc *out, int *err,
-                               cudaStream_t s, int *cmark = nullptr, int cgen = 0,
-                               unsigned long long *clist = nullptr);
+struct GhostBuildArgs {
+    const PatchDesc *pd;
+    const long long *gprefix;
+    int np;
+    long long n;
+    LevelIdx g;
+    const int *owner, *owner_c;
+    LevelIdx gc;
+    int r;
+    GhostDesc *out;
+    int *err;
+    int *cmark;
+    int cgen;
+    unsigned long long *clist;
+};
 // average-down descriptors; aprefix = prefix of coarse-footprint cells per fine patch
-cudaError_t launch_avg_build(const PatchDesc *p, const long long *aprefix, int np, long long navg, int dim, int r,
-                             const int *owner_c, LevelIdx gc, AvgDesc *out, int *err, cudaStream_t s);
+struct AvgBuildArgs {
+    const PatchDesc *pd;
+    const long long *aprefix;
+    int np;
+    long long n;
+    int dim, r;
+    const int *owner_c;
+    LevelIdx gc;
+    AvgDesc *out;
+    int *err;
+};
 // new interior cells: copy from the old arena (owner_old) or interpolate from
 // the coarser level (owner_c, qc) at its current time
-cudaError_t launch_init_new(const PatchDesc *p, const long long *prefix, int np, long long ncells, LevelIdx g, int m,
-                            double *qf, long long sf, const int *owner_old, const double *qold, long long so,
-                            const int *owner_c, LevelIdx gc, const double *qc, long long sc, int r, int *err,
-                            cudaStream_t s);
-// medium coefficients of every storage cell; sprefix = storage-cell prefix
+struct InitNewArgs {
+    const PatchDesc *pd;
+    const long long *prefix;
+    int np;
+    long long n;
+    LevelIdx g;
+    int m;
+    double *qf;
+    long long sf;
+    const int *owner_old;
+    const double *qold;
+    long long so;
+    const int *owner_c;
+    LevelIdx gc;
+    const double *qc;
+    long long sc;
+    int r;
+    int *err;
+};
+cudaError_t launch_owner_fill(const OwnerFillArgs &a, cudaStream_t s);
+cudaError_t launch_ghost_build(const GhostBuildArgs &a, cudaStream_t s);
+cudaError_t launch_avg_build(const AvgBuildArgs &a, cudaStream_t s);
+cudaError_t launch_init_new(const InitNewArgs &a, cudaStream_t s);
 // coefficients a rebuilt level may copy from its previous arena: a storage
 // cell whose (I, J) was an interior cell of the previous patches takes that
 // cell's values (they depend on (I, J) only); owner == nullptr: compute all
@@ -448,10 +496,28 @@ struct AuxTable {
     int width;         // N + 4
 };
 cudaError_t launch_aux_table(int eqn, const MediumDev *mdev, LevelGeom geom, double *tab, cudaStream_t s);
-// tab.tab != nullptr: the storage cells copy their coefficients from the table
-cudaError_t launch_aux_patches(int eqn, const PatchDesc *p, const long long *sprefix, int np, long long nstore,
-                               LevelIdx g, double *aux, double *med, long long stride, const MediumDev *mdev,
-                               LevelGeom geom, cudaStream_t s, AuxReuse ru = AuxReuse{nullptr, nullptr, nullptr, 0, 0, 0},
-                               AuxTable tab = AuxTable{nullptr, 0, 0});
+// coefficients of every storage cell (sprefix = storage-cell prefix);
+// tb.tab != nullptr: copied from the table
+struct AuxPatchesArgs {
+    int eqn;
+    const PatchDesc *pd;
+    const long long *sprefix;
+    int np;
+    long long n;
+    LevelIdx g;
+    double *aux, *med;
+    long long stride;
+    const MediumDev *mdp;
+    LevelGeom geom;
+    AuxReuse ru;
+    AuxTable tb;
+};
+cudaError_t launch_aux_patches(const AuxPatchesArgs &a, cudaStream_t s);
+// The five builders of one level in two launches: the owner map, the
+// coefficients and the new interior state (none reads another's output) side
+// by side in one grid, then the ghost and average-down maps (which read the
+// new owner map) in the next.  *nlaunch = kernels launched (0 to 2).
+cudaError_t launch_rebuild(const OwnerFillArgs &o, const AuxPatchesArgs &x, const InitNewArgs &in,
+                           const GhostBuildArgs &gb, const AvgBuildArgs &ab, cudaStream_t s, int *nlaunch);
 
 }  // namespace adjamr

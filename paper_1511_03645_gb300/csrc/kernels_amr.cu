@@ -321,32 +321,21 @@ __device__ bool coarse_desc_dev(int I, int J, int r, const int *__restrict__ own
     return ok;
 }
 
-__global__ void k_owner_fill(const PatchDesc *__restrict__ pd, const long long *__restrict__ prefix, int np,
-                             long long ncells, LevelIdx g, int *owner)
+__device__ __forceinline__ void owner_fill_at(const OwnerFillArgs &a, long long t)
 {
-    pdl_wait();
-    pdl_launch_dependents();
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ncells) return;
-    int p = find_in_prefix(prefix, np, t);
-    const PatchDesc P = pd[p];
-    long long k = t - prefix[p];
+    int p = find_in_prefix(a.prefix, a.np, t);
+    const PatchDesc P = a.pd[p];
+    long long k = t - a.prefix[p];
     int j = (int)(k / P.nx), i = (int)(k - (long long)j * P.nx);
-    owner[(long long)(P.jlo + j) * g.N + P.ilo + i] = (int)(P.base + (long long)(j + g.gy) * P.sx + (i + 2));
+    a.owner[(long long)(P.jlo + j) * a.g.N + P.ilo + i] = (int)(P.base + (long long)(j + a.g.gy) * P.sx + (i + 2));
 }
 
-__global__ void k_ghost_build(const PatchDesc *__restrict__ pd, const long long *__restrict__ gprefix, int np,
-                              long long nghost, LevelIdx g, const int *__restrict__ owner,
-                              const int *__restrict__ owner_c, LevelIdx gc, int r, GhostDesc *out, int *err,
-                              int *cmark, int cgen, unsigned long long *clist)
+__device__ __forceinline__ void ghost_build_at(const GhostBuildArgs &a, long long t)
 {
-    pdl_wait();
-    pdl_launch_dependents();
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nghost) return;
-    int p = find_in_prefix(gprefix, np, t);
-    const PatchDesc P = pd[p];
-    long long k = t - gprefix[p];
+    const LevelIdx &g = a.g;
+    int p = find_in_prefix(a.gprefix, a.np, t);
+    const PatchDesc P = a.pd[p];
+    long long k = t - a.gprefix[p];
     const long long bottom = (long long)g.gy * P.sx, mid = (long long)P.ny * 4;
     int si, sj;
     if (k < bottom) {
@@ -371,108 +360,175 @@ __global__ void k_ghost_build(const PatchDesc *__restrict__ pd, const long long 
     d.kind = 0;
     d.signs = 0;
     d.fx = d.fy = 0.0;
-    int o = owner_at(owner, g, I, J);
+    int o = owner_at(a.owner, g, I, J);
     if (o >= 0) {
         d.src = o;
-    } else if (owner_c) {
-        if (!coarse_desc_dev(I, J, r, owner_c, gc, d)) atomicOr(err, 1);
+    } else if (a.owner_c) {
+        if (!coarse_desc_dev(I, J, a.r, a.owner_c, a.gc, d)) atomicOr(a.err, 1);
     } else {
-        atomicOr(err, 2);
+        atomicOr(a.err, 2);
         d.src = d.dst;  // harmless self-copy
     }
     d.signs |= f1 | (f2 << 1);
-    out[t] = d;
+    a.out[t] = d;
     // list the coarse cell once (which of its ghost cells is listed is immaterial)
-    if (d.kind != 0 && cmark && atomicExch(&cmark[d.src], cgen) != cgen)
-        clist[1 + atomicAdd(&clist[0], 1ull)] = (unsigned long long)t;
+    if (d.kind != 0 && a.cmark && atomicExch(&a.cmark[d.src], a.cgen) != a.cgen)
+        a.clist[1 + atomicAdd(&a.clist[0], 1ull)] = (unsigned long long)t;
 }
 
-__global__ void k_avg_build(const PatchDesc *__restrict__ pd, const long long *__restrict__ aprefix, int np,
-                            long long navg, int dim, int r, const int *__restrict__ owner_c, LevelIdx gc,
-                            AvgDesc *out, int *err)
+__device__ __forceinline__ void avg_build_at(const AvgBuildArgs &a, long long t)
 {
-    pdl_wait();
-    pdl_launch_dependents();
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= navg) return;
-    int p = find_in_prefix(aprefix, np, t);
-    const PatchDesc P = pd[p];
-    long long k = t - aprefix[p];
+    const int r = a.r, dim = a.dim;
+    int p = find_in_prefix(a.aprefix, a.np, t);
+    const PatchDesc P = a.pd[p];
+    long long k = t - a.aprefix[p];
     int na = P.nx / r;
     int bj = (int)(k / na), ai = (int)(k - (long long)bj * na);
-    int a = P.ilo / r + ai, b = (dim == 2) ? P.jlo / r + bj : 0;
-    int o = owner_at(owner_c, gc, a, b);
+    int ca = P.ilo / r + ai, cb = (dim == 2) ? P.jlo / r + bj : 0;
+    int o = owner_at(a.owner_c, a.gc, ca, cb);
     if (o < 0) {
-        atomicOr(err, 4);
+        atomicOr(a.err, 4);
         o = 0;
     }
     AvgDesc d;
     d.dst = o;
     int gy = (dim == 2) ? 2 : 0;
-    int fj = (dim == 2) ? b * r - P.jlo : 0;
-    d.src = P.base + (long long)(fj + gy) * P.sx + (a * r - P.ilo + 2);
+    int fj = (dim == 2) ? cb * r - P.jlo : 0;
+    d.src = P.base + (long long)(fj + gy) * P.sx + (ca * r - P.ilo + 2);
     d.fsx = P.sx;
     d.pad = 0;
-    out[t] = d;
+    a.out[t] = d;
 }
 
-__global__ void k_init_new(const PatchDesc *__restrict__ pd, const long long *__restrict__ prefix, int np,
-                           long long ncells, LevelIdx g, int m, double *qf, long long sf,
-                           const int *__restrict__ owner_old, const double *__restrict__ qold, long long so,
-                           const int *__restrict__ owner_c, LevelIdx gc, const double *__restrict__ qc, long long sc,
-                           int r, int *err)
+__device__ __forceinline__ void init_new_at(const InitNewArgs &a, long long t)
 {
-    pdl_wait();
-    pdl_launch_dependents();
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ncells) return;
-    int p = find_in_prefix(prefix, np, t);
-    const PatchDesc P = pd[p];
-    long long k = t - prefix[p];
+    int p = find_in_prefix(a.prefix, a.np, t);
+    const PatchDesc P = a.pd[p];
+    long long k = t - a.prefix[p];
     int j = (int)(k / P.nx), i = (int)(k - (long long)j * P.nx);
     int I = P.ilo + i, J = P.jlo + j;
-    long long dst = P.base + (long long)(j + g.gy) * P.sx + (i + 2);
-    int o = owner_old ? owner_at(owner_old, g, I, J) : -1;
+    long long dst = P.base + (long long)(j + a.g.gy) * P.sx + (i + 2);
+    int o = a.owner_old ? owner_at(a.owner_old, a.g, I, J) : -1;
     if (o >= 0) {
-        for (int f = 0; f < m; f++) qf[(long long)f * sf + dst] = qold[(long long)f * so + o];
+        for (int f = 0; f < a.m; f++) a.qf[(long long)f * a.sf + dst] = a.qold[(long long)f * a.so + o];
         return;
     }
     GhostDesc d;
     d.signs = 0;
-    if (!coarse_desc_dev(I, J, r, owner_c, gc, d)) atomicOr(err, 8);
-    for (int f = 0; f < m; f++) qf[(long long)f * sf + dst] = interp_field(d, qc, qc, sc, f, 0, 0.0, g.dim);
+    if (!coarse_desc_dev(I, J, a.r, a.owner_c, a.gc, d)) atomicOr(a.err, 8);
+    for (int f = 0; f < a.m; f++) a.qf[(long long)f * a.sf + dst] = interp_field(d, a.qc, a.qc, a.sc, f, 0, 0.0, a.g.dim);
 }
 
-__global__ void k_aux_patches(int eqn, const PatchDesc *__restrict__ pd, const long long *__restrict__ sprefix,
-                              int np, long long nstore, LevelIdx g, double *aux, double *med, long long stride,
-                              const MediumDev *__restrict__ mdp, LevelGeom geom, AuxReuse ru, AuxTable tb)
+__device__ __forceinline__ void aux_patches_at(const AuxPatchesArgs &a, long long t)
 {
-    pdl_wait();
-    pdl_launch_dependents();
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nstore) return;
-    int p = find_in_prefix(sprefix, np, t);
-    const PatchDesc P = pd[p];
-    long long k = t - sprefix[p];
+    const LevelIdx &g = a.g;
+    int p = find_in_prefix(a.sprefix, a.np, t);
+    const PatchDesc P = a.pd[p];
+    long long k = t - a.sprefix[p];
     int sj = (int)(k / P.sx), si = (int)(k - (long long)sj * P.sx);
     const int I = P.ilo + si - 2, J = P.jlo + sj - g.gy;
     const long long idx = P.base + k;
-    if (tb.tab) {
-        const long long ti = (long long)(J + g.gy) * tb.width + (I + 2);
-        for (int f = 0; f < ru.naux; f++) aux[(long long)f * stride + idx] = tb.tab[(long long)f * tb.stride + ti];
+    const AuxReuse &ru = a.ru;
+    if (a.tb.tab) {
+        const long long ti = (long long)(J + g.gy) * a.tb.width + (I + 2);
+        for (int f = 0; f < ru.naux; f++)
+            a.aux[(long long)f * a.stride + idx] = a.tb.tab[(long long)f * a.tb.stride + ti];
         for (int f = 0; f < ru.nmed; f++)
-            med[(long long)f * stride + idx] = tb.tab[(long long)(ru.naux + f) * tb.stride + ti];
+            a.med[(long long)f * a.stride + idx] = a.tb.tab[(long long)(ru.naux + f) * a.tb.stride + ti];
         return;
     }
     if (ru.owner) {
         const int o = owner_at(ru.owner, g, I, J);
         if (o >= 0) {
-            for (int f = 0; f < ru.naux; f++) aux[(long long)f * stride + idx] = ru.aux[(long long)f * ru.stride + o];
-            for (int f = 0; f < ru.nmed; f++) med[(long long)f * stride + idx] = ru.med[(long long)f * ru.stride + o];
+            for (int f = 0; f < ru.naux; f++)
+                a.aux[(long long)f * a.stride + idx] = ru.aux[(long long)f * ru.stride + o];
+            for (int f = 0; f < ru.nmed; f++)
+                a.med[(long long)f * a.stride + idx] = ru.med[(long long)f * ru.stride + o];
             return;
         }
     }
-    aux_cell(eqn, g.dim, *mdp, geom, I, J, idx, aux, med, stride);
+    aux_cell(a.eqn, g.dim, *a.mdp, a.geom, I, J, idx, a.aux, a.med, a.stride);
+}
+
+// thread index of the calling thread within a part of a grid that starts at
+// block b0; -1 outside it
+__device__ __forceinline__ long long part_thread(unsigned b0, long long n)
+{
+    const long long t = (long long)(blockIdx.x - b0) * blockDim.x + threadIdx.x;
+    return t < n ? t : -1;
+}
+
+__global__ void k_owner_fill(OwnerFillArgs a)
+{
+    pdl_wait();
+    pdl_launch_dependents();
+    const long long t = part_thread(0, a.n);
+    if (t >= 0) owner_fill_at(a, t);
+}
+
+__global__ void k_ghost_build(GhostBuildArgs a)
+{
+    pdl_wait();
+    pdl_launch_dependents();
+    const long long t = part_thread(0, a.n);
+    if (t >= 0) ghost_build_at(a, t);
+}
+
+__global__ void k_avg_build(AvgBuildArgs a)
+{
+    pdl_wait();
+    pdl_launch_dependents();
+    const long long t = part_thread(0, a.n);
+    if (t >= 0) avg_build_at(a, t);
+}
+
+__global__ void k_init_new(InitNewArgs a)
+{
+    pdl_wait();
+    pdl_launch_dependents();
+    const long long t = part_thread(0, a.n);
+    if (t >= 0) init_new_at(a, t);
+}
+
+__global__ void k_aux_patches(AuxPatchesArgs a)
+{
+    pdl_wait();
+    pdl_launch_dependents();
+    const long long t = part_thread(0, a.n);
+    if (t >= 0) aux_patches_at(a, t);
+}
+
+// A level's rebuild, first launch: blocks [0, b1) fill the owner map, [b1,
+// b2) the coefficients, [b2, grid) the new interior state.
+__global__ void k_rebuild_a(OwnerFillArgs o, AuxPatchesArgs x, InitNewArgs in, unsigned b1, unsigned b2)
+{
+    pdl_wait();
+    pdl_launch_dependents();
+    if (blockIdx.x < b1) {
+        const long long t = part_thread(0, o.n);
+        if (t >= 0) owner_fill_at(o, t);
+    } else if (blockIdx.x < b2) {
+        const long long t = part_thread(b1, x.n);
+        if (t >= 0) aux_patches_at(x, t);
+    } else {
+        const long long t = part_thread(b2, in.n);
+        if (t >= 0) init_new_at(in, t);
+    }
+}
+
+// second launch: blocks [0, b1) the ghost descriptors, [b1, grid) the
+// average-down descriptors (both read the owner map of the first)
+__global__ void k_rebuild_b(GhostBuildArgs gb, AvgBuildArgs ab, unsigned b1)
+{
+    pdl_wait();
+    pdl_launch_dependents();
+    if (blockIdx.x < b1) {
+        const long long t = part_thread(0, gb.n);
+        if (t >= 0) ghost_build_at(gb, t);
+    } else {
+        const long long t = part_thread(b1, ab.n);
+        if (t >= 0) avg_build_at(ab, t);
+    }
 }
 
 // ---------------------------------------------------------------- error estimate (Sec. 7)
@@ -1105,29 +1161,44 @@ cudaError_t launch_aux_fill(int eqn, int dim, const AuxDesc *d, long long n, dou
     return cudaGetLastError();
 }
 
-cudaError_t launch_owner_fill(const PatchDesc *p, const long long *prefix, int np, long long ncells, LevelIdx g,
-                              int *owner, cudaStream_t s)
+cudaError_t launch_owner_fill(const OwnerFillArgs &a, cudaStream_t s)
 {
-    if (ncells <= 0) return cudaSuccess;
-    return launch_pdl(k_owner_fill, dim3(nblk(ncells)), dim3(kT), 0, s, p, prefix, np, ncells, g, owner);
+    if (a.n <= 0) return cudaSuccess;
+    return launch_pdl(k_owner_fill, dim3(nblk(a.n)), dim3(kT), 0, s, a);
 }
 
-cudaError_t launch_ghost_build(const PatchDesc *p, const long long *gprefix, int np, long long nghost, LevelIdx g,
-                               const int *owner, const int *owner_c, LevelIdx gc, int r, GhostDesc *out, int *err,
-                               cudaStream_t s, int *cmark, int cgen, unsigned long long *clist)
+cudaError_t launch_ghost_build(const GhostBuildArgs &a, cudaStream_t s)
 {
-    if (nghost <= 0) return cudaSuccess;
-    if (cmark && (cgen <= 0 || !clist)) return cudaErrorInvalidValue;
-    return launch_pdl(k_ghost_build, dim3(nblk(nghost)), dim3(kT), 0, s, p, gprefix, np, nghost, g, owner, owner_c, gc,
-                      r, out, err, cmark, cgen, clist);
+    if (a.n <= 0) return cudaSuccess;
+    if (a.cmark && (a.cgen <= 0 || !a.clist)) return cudaErrorInvalidValue;
+    return launch_pdl(k_ghost_build, dim3(nblk(a.n)), dim3(kT), 0, s, a);
 }
 
-cudaError_t launch_avg_build(const PatchDesc *p, const long long *aprefix, int np, long long navg, int dim, int r,
-                             const int *owner_c, LevelIdx gc, AvgDesc *out, int *err, cudaStream_t s)
+cudaError_t launch_avg_build(const AvgBuildArgs &a, cudaStream_t s)
 {
-    if (navg <= 0) return cudaSuccess;
-    return launch_pdl(k_avg_build, dim3(nblk(navg)), dim3(kT), 0, s, p, aprefix, np, navg, dim, r, owner_c, gc, out,
-                      err);
+    if (a.n <= 0) return cudaSuccess;
+    return launch_pdl(k_avg_build, dim3(nblk(a.n)), dim3(kT), 0, s, a);
+}
+
+cudaError_t launch_rebuild(const OwnerFillArgs &o, const AuxPatchesArgs &x, const InitNewArgs &in,
+                           const GhostBuildArgs &gb, const AvgBuildArgs &ab, cudaStream_t s, int *nlaunch)
+{
+    *nlaunch = 0;
+    if (gb.n > 0 && gb.cmark && (gb.cgen <= 0 || !gb.clist)) return cudaErrorInvalidValue;
+    auto blocks = [](long long n) { return n > 0 ? nblk(n) : 0u; };
+    const unsigned a1 = blocks(o.n), a2 = a1 + blocks(x.n), a3 = a2 + blocks(in.n);
+    if (a3 > 0) {
+        const cudaError_t e = launch_pdl(k_rebuild_a, dim3(a3), dim3(kT), 0, s, o, x, in, a1, a2);
+        if (e != cudaSuccess) return e;
+        ++*nlaunch;
+    }
+    const unsigned b1 = blocks(gb.n), b2 = b1 + blocks(ab.n);
+    if (b2 > 0) {
+        const cudaError_t e = launch_pdl(k_rebuild_b, dim3(b2), dim3(kT), 0, s, gb, ab, b1);
+        if (e != cudaSuccess) return e;
+        ++*nlaunch;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_errest_fill(const ErrEstArgs &a, LevelIdx g, const int *owner, const double *q, long long sq,
@@ -1153,23 +1224,16 @@ cudaError_t launch_errest_tau(const ErrEstArgs &a, const long long *iprefix, lon
                       ninterior, tau, st);
 }
 
-cudaError_t launch_init_new(const PatchDesc *p, const long long *prefix, int np, long long ncells, LevelIdx g, int m,
-                            double *qf, long long sf, const int *owner_old, const double *qold, long long so,
-                            const int *owner_c, LevelIdx gc, const double *qc, long long sc, int r, int *err,
-                            cudaStream_t s)
+cudaError_t launch_init_new(const InitNewArgs &a, cudaStream_t s)
 {
-    if (ncells <= 0) return cudaSuccess;
-    return launch_pdl(k_init_new, dim3(nblk(ncells)), dim3(kT), 0, s, p, prefix, np, ncells, g, m, qf, sf, owner_old,
-                      qold, so, owner_c, gc, qc, sc, r, err);
+    if (a.n <= 0) return cudaSuccess;
+    return launch_pdl(k_init_new, dim3(nblk(a.n)), dim3(kT), 0, s, a);
 }
 
-cudaError_t launch_aux_patches(int eqn, const PatchDesc *p, const long long *sprefix, int np, long long nstore,
-                               LevelIdx g, double *aux, double *med, long long stride, const MediumDev *mdev,
-                               LevelGeom geom, cudaStream_t s, AuxReuse ru, AuxTable tb)
+cudaError_t launch_aux_patches(const AuxPatchesArgs &a, cudaStream_t s)
 {
-    if (nstore <= 0) return cudaSuccess;
-    return launch_pdl(k_aux_patches, dim3(nblk(nstore)), dim3(kT), 0, s, eqn, p, sprefix, np, nstore, g, aux, med,
-                      stride, mdev, geom, ru, tb);
+    if (a.n <= 0) return cudaSuccess;
+    return launch_pdl(k_aux_patches, dim3(nblk(a.n)), dim3(kT), 0, s, a);
 }
 
 cudaError_t launch_aux_table(int eqn, const MediumDev *mdev, LevelGeom geom, double *tab, cudaStream_t s)
