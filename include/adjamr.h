@@ -222,7 +222,11 @@ adjamr_status adjamr_set_medium(adjamr_ctx *ctx, const adjamr_medium *m);
  * snapshot n at t_n = t0 + n (tf - t0)/(nsnap - 1), on a uniform ax x ay grid
  * covering the domain; wet[ay][ax] (NULL = all wet).  snaps_on_device != 0:
  * `snaps` is a device pointer (copied device-to-device).  The returned
- * handle holds a device copy and one reference; it is attached to ctx. */
+ * handle holds a device copy and one reference; it is attached to ctx.
+ * When the set ctx holds has the same shape and nothing else holds it, its
+ * device buffers take the new values (after ctx's queued work; the returned
+ * handle is then that set) instead of a new allocation.  Errors: EINVAL for
+ * bad sizes, ENOMEM, ECUDA (a failed refill detaches the set from ctx). */
 adjamr_status adjamr_load_adjoint_snapshots(adjamr_ctx *ctx, const double *snaps, int nsnap, int ax, int ay,
                                             const unsigned char *wet, int snaps_on_device,
                                             adjamr_adjoint **out);

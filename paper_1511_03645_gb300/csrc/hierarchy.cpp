@@ -2588,6 +2588,37 @@ adjamr_status adjamr_load_adjoint_snapshots(adjamr_ctx *ctx, const double *snaps
     if (!ctx || !snaps || nsnap < 2 || ax < 1) return ADJAMR_EINVAL;
     if (ctx->P.dim == 1) ay = 1;
     if (ay < 1 || (ctx->P.dim == 2 && ax < 2) || (ctx->P.dim == 2 && ay < 2)) return ADJAMR_EINVAL;
+    adjamr_adjoint *cur = ctx->adj;
+    if (cur && cur->refs.load() == 1 && cur->S == nsnap && cur->m == ctx->m && cur->ax == ax && cur->ay == ay &&
+        cur->dim == ctx->P.dim && cur->d_bmax) {
+        // The context's own set of the same shape, held by nothing else: it is
+        // refilled in place once no kernel of the context reads it, instead of
+        // a new device allocation per set and a release of the old one.
+        const size_t n = (size_t)nsnap * cur->m * ax * ay;
+        cudaError_t e = cudaStreamSynchronize(ctx->s);
+        if (e == cudaSuccess && ctx->s_flag) e = cudaStreamSynchronize(ctx->s_flag);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(cur->d_snaps, snaps, n * sizeof(double),
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->s);
+        if (e == cudaSuccess) {
+            if (wet) e = cudaMemcpyAsync(cur->d_wet, wet, (size_t)ax * ay, cudaMemcpyHostToDevice, ctx->s);
+            else e = cudaMemsetAsync(cur->d_wet, 1, (size_t)ax * ay, ctx->s);
+        }
+        if (e == cudaSuccess) e = launch_block_max(cur->d_snaps, cur->S, cur->m, ax, ay, cur->dim, cur->d_bmax, ctx->s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->s);
+        if (e != cudaSuccess) {
+            // the set's contents are unknown now: the context lets it go
+            ctx->err = cudaGetErrorString(e);
+            ctx->adj = nullptr;
+            adjamr_adjoint_release(cur);
+            return ADJAMR_ECUDA;
+        }
+        if (out) {
+            cur->refs++;
+            *out = cur;
+        }
+        return ADJAMR_OK;
+    }
     adjamr_adjoint *a = new (std::nothrow) adjamr_adjoint();
     if (!a) return ADJAMR_ENOMEM;
     a->S = nsnap;

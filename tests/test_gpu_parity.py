@@ -742,6 +742,46 @@ def test_reset_gives_the_bits_of_a_new_context(A, case):
     g.close()
 
 
+@pytest.mark.parametrize("keep_first", [False, True])
+def test_second_adjoint_set_in_the_same_context(A, keep_first):
+    """A second snapshot set of the same shape loaded into a context (after a
+    solve with the first): the solve then follows the second set to the
+    oracle's bits.  With no other holder the first set's device buffers take
+    the second (refilled in place); a first set still held elsewhere keeps
+    its values and the second gets buffers of its own."""
+    wl = W.config2(seed=3, n0=32, ratios=(2, 4), tf=2.0, adj_n=64, nsnap=20, ts=0.0, tol=1e-4, min_patch=8,
+                   max_patch=32)
+    snaps_a = O.adjoint_solve(wl)
+    wl_b = W.config2(seed=5, n0=32, ratios=(2, 4), tf=2.0, adj_n=64, nsnap=20, ts=0.0, tol=1e-4, min_patch=8,
+                     max_patch=32)
+    snaps_b = O.adjoint_solve(wl_b)
+    assert snaps_a.shape == snaps_b.shape and not np.array_equal(snaps_a, snaps_b)
+    g = A.Hierarchy(wl)
+    first = g.load_adjoint(snaps_a)
+    if not keep_first:
+        first.release()
+    g.regrid(0, init=True)
+    g.advance(g.nsteps_total() // 2)
+    g.reset()
+    second = g.load_adjoint(snaps_b)
+    assert np.array_equal(second.read(), snaps_b)
+    if keep_first:
+        assert np.array_equal(first.read(), snaps_a)
+        first.release()
+    g.regrid(0, init=True)
+    o = O.OracleHierarchy(wl)
+    o.set_adjoint(snaps_b)
+    o.regrid(0, init=True)
+    _compare_all(o, g, wl.nlevels)
+    n = o.nsteps_total()
+    o.advance(n)
+    g.advance(n)
+    _compare_all(o, g, wl.nlevels)
+    assert abs(g.functional() - o.functional()) <= RTOL * max(abs(o.functional()), 1e-300)
+    second.release()
+    g.close()
+
+
 def test_error_estimate_of_a_shallowly_nested_level_is_refused_and_the_run_goes_on(A):
     """A hierarchy flagged by the bracket rule nests its finest level only 2
     coarse cells deep; with ratio 2 the estimate's ring of 4 fine cells then
