@@ -632,7 +632,6 @@ LevelIdx idx_of(const adjamr_ctx *c, int l)
     return g;
 }
 
-// allocate the arena of a level for the given boxes (level index space)
 // A builder kernel of a level's layout: launched now, or recorded for the
 // combined launches of the rebuild in progress (flush_rebuild).
 template <typename Args>
@@ -678,6 +677,7 @@ adjamr_status flush_rebuild(adjamr_ctx *c)
     return ADJAMR_OK;
 }
 
+// allocate the arena of a level for the given boxes (level index space)
 adjamr_status alloc_level(adjamr_ctx *c, int l, const std::vector<Box> &boxes)
 {
     Level &L = c->L[l];
