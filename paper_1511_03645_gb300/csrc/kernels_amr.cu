@@ -69,16 +69,17 @@ __global__ void k_ghost_fill(int dim, int m, const GhostDesc *__restrict__ gd, l
     const bool valid = t < n * m;
     const long long gi = valid ? t / m : 0;
     const int f = (int)(t - gi * m);
-    bool done = false;
-    if (early && valid && gd[gi].kind != 0) {
-        const GhostDesc &g = gd[gi];
-        qf[(long long)f * sf + g.dst] = fill_value(g, qf, sf, qo, qn_, sc, f, k, th, dim, pre_k);
-        done = true;
+    // early: the descriptor (fixed since the level's rebuild) is read before
+    // the wait too, so that a copy waits for one load of the step's output only
+    GhostDesc g{};
+    if (early && valid) {
+        g = gd[gi];
+        if (g.kind != 0) qf[(long long)f * sf + g.dst] = fill_value(g, qf, sf, qo, qn_, sc, f, k, th, dim, pre_k);
     }
     pdl_wait();
     pdl_launch_dependents();
-    if (!valid || done) return;
-    const GhostDesc &g = gd[gi];
+    if (!valid || (early && g.kind != 0)) return;
+    if (!early) g = gd[gi];
     qf[(long long)f * sf + g.dst] = fill_value(g, qf, sf, qo, qn_, sc, f, k, th, dim, pre_k);
 }
 

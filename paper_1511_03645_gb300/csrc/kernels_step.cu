@@ -263,6 +263,12 @@ __device__ __forceinline__ void cp_async8(double *smem, const double *gmem)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
 }
 
+// fetch the line holding p into L1 (no register result)
+__device__ __forceinline__ void prefetch_l1(const void *p)
+{
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ void cp_async_wait_all()
 {
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
@@ -595,14 +601,25 @@ __global__ void __launch_bounds__(kThreads) k_step2d(const double *__restrict__ 
                                                      const WorkItem *__restrict__ work, int nwork,
                                                      unsigned long long *cfl_bits, GhostArgs ga, TileSched sc)
 {
-    pdl_wait();
-    pdl_launch_dependents();
     extern __shared__ double sm[];
     long long cfl = 0;
     __shared__ int s_next;
+    // One tile per CTA (the work-list launch): the tile's work-list entry,
+    // fixed since the level's rebuild, is read before the wait for the kernel
+    // ahead and its patch descriptor fetched towards L1 meanwhile; the state
+    // that kernel writes is read after the wait.
+    const bool single = !sc.ctr && (long long)gridDim.x >= nwork;
+    WorkItem wi{};
+    if (single && (int)blockIdx.x < nwork) {
+        wi = work[blockIdx.x];
+        prefetch_l1(patches + wi.patch);
+    }
+    pdl_wait();
+    pdl_launch_dependents();
     for (int w = fetch_tile(sc, &s_next, blockIdx.x); w < nwork; w = fetch_tile(sc, &s_next, w + gridDim.x)) {
-        const WorkItem wi = work[w];
+        if (!single) wi = work[w];
         step2d_tile<EQN, TX, TY, false>(q, qn, aux, stride, patches[wi.patch], wi, ga, sm, cfl);
+        if (single) break;
     }
     cfl_reduce(cfl, cfl_bits);
 }
@@ -741,17 +758,14 @@ struct Smem1D {
     static constexpr size_t bytes = sizeof(double) * (size_t)total;
 };
 
+// One tile of one 1D step: stage, Riemann problems, limiter, update of the
+// tile's cells in qn (and the fix-up records of listed cells).
 template <int EQN, int TX>
-__global__ void __launch_bounds__(kThreads) k_step1d(const double *__restrict__ q, double *__restrict__ qn,
-                                                     const double *__restrict__ aux, long long stride,
-                                                     const PatchDesc *__restrict__ patches,
-                                                     const WorkItem *__restrict__ work, int nwork,
-                                                     unsigned long long *cfl_bits, GhostArgs ga, TileSched sc)
+__device__ __forceinline__ void step1d_tile(const double *__restrict__ q, double *__restrict__ qn,
+                                            const double *__restrict__ aux, long long stride, const PatchDesc P,
+                                            const WorkItem wi, const GhostArgs &ga, double *sm, long long &cfl)
 {
     using S = Smem1D<EQN, TX>;
-    pdl_wait();
-    pdl_launch_dependents();
-    extern __shared__ double sm[];
     constexpr int PX = S::PX, XE = S::XE, XNn = S::XN;
     double *sQ = sm;
     double *sA = sQ + 2 * PX;
@@ -759,100 +773,120 @@ __global__ void __launch_bounds__(kThreads) k_step1d(const double *__restrict__ 
     double *XF = XW + 4 * XE;
     double *XN = XF + 4 * XE;
     const int tid = threadIdx.x;
-    long long cfl = 0;
-    __shared__ int s_next;
-    for (int w = fetch_tile(sc, &s_next, blockIdx.x); w < nwork; w = fetch_tile(sc, &s_next, w + gridDim.x)) {
-        const WorkItem wi = work[w];
-        const PatchDesc P = patches[wi.patch];
-        const int x0 = wi.x0;
-        const int tx = wi.tx, rx = tx + 4;
-        const double dtdx = P.dtdx;
-        const bool ring = ga.gd && (x0 < 2 || x0 + tx + 1 >= P.nx);  // staged [x0, x0+tx+4) meets the ring
-        for (int k = tid; k < (2 + S::NA) * rx; k += kThreads) {
-            int f = k / rx, c = k - f * rx;
-            long long g = P.base + x0 + c;
-            if (f < 2) {
-                const int si = x0 + c;
-                if (!(ring && (si < 2 || si >= P.nx + 2))) sQ[f * PX + c] = q[(long long)f * stride + g];
-            } else {
-                sA[(f - 2) * PX + c] = aux[(long long)(f - 2) * stride + g];
-            }
-        }
-        for (int c = tid; ring && c < rx; c += kThreads) {
+    const int x0 = wi.x0;
+    const int tx = wi.tx, rx = tx + 4;
+    const double dtdx = P.dtdx;
+    const bool ring = ga.gd && (x0 < 2 || x0 + tx + 1 >= P.nx);  // staged [x0, x0+tx+4) meets the ring
+    for (int k = tid; k < (2 + S::NA) * rx; k += kThreads) {
+        int f = k / rx, c = k - f * rx;
+        long long g = P.base + x0 + c;
+        if (f < 2) {
             const int si = x0 + c;
-            if (si < 2 || si >= P.nx + 2) {
-                const GhostDesc gdsc = ga.gd[P.gbase + ghost_local_index(P, si, 0, 0)];
-                double v0 = ghost_value(gdsc, q, stride, ga.pre + ga.k * ga.pstride, ga.sc, 0, 1);
-                double v1 = ghost_value(gdsc, q, stride, ga.pre + ga.k * ga.pstride, ga.sc, 1, 1);
-                sQ[c] = v0;
-                sQ[PX + c] = v1;
-            }
+            if (!(ring && (si < 2 || si >= P.nx + 2))) sQ[f * PX + c] = q[(long long)f * stride + g];
+        } else {
+            sA[(f - 2) * PX + c] = aux[(long long)(f - 2) * stride + g];
         }
-        __syncthreads();
-        for (int k = tid; k < tx + 3; k += kThreads) {    // edge ex = k-1 between staged cells k, k+1
-            int l = k, r = k + 1;
-            Edge e;
-            load_edge<EQN, 0>(sA, PX, l, r, e);
-            double d0, dn, w1[2], w2[2];
-            edge_jump<EQN>(e, sA, PX, l, r, sQ[l], sQ[PX + l], sQ[r], sQ[PX + r], d0, dn);
-            decompose<EQN>(e, d0, dn, w1, w2);
-            XW[k] = w1[0]; XW[XE + k] = w1[1]; XW[2 * XE + k] = w2[0]; XW[3 * XE + k] = w2[1];
-            if constexpr (EQN == 0) {
-                XF[k] = e.s1 * w1[0]; XF[XE + k] = e.s1 * w1[1];
-                XF[2 * XE + k] = e.s2 * w2[0]; XF[3 * XE + k] = e.s2 * w2[1];
-            } else {
-                XF[k] = w1[0]; XF[XE + k] = w1[1]; XF[2 * XE + k] = w2[0]; XF[3 * XE + k] = w2[1];
-            }
+    }
+    for (int c = tid; ring && c < rx; c += kThreads) {
+        const int si = x0 + c;
+        if (si < 2 || si >= P.nx + 2) {
+            const GhostDesc gdsc = ga.gd[P.gbase + ghost_local_index(P, si, 0, 0)];
+            double v0 = ghost_value(gdsc, q, stride, ga.pre + ga.k * ga.pstride, ga.sc, 0, 1);
+            double v1 = ghost_value(gdsc, q, stride, ga.pre + ga.k * ga.pstride, ga.sc, 1, 1);
+            sQ[c] = v0;
+            sQ[PX + c] = v1;
         }
-        __syncthreads();
-        long long smx = 0;  // max |s| over this thread's edges (see the 2D kernel)
-        for (int k = tid; k < tx + 1; k += kThreads) {    // edge ex = k
-            int o = k + 1, l = k + 1, r = k + 2;
-            Edge e;
-            load_edge<EQN, 0>(sA, PX, l, r, e);
-            int u1 = positive(e.s1) ? o - 1 : o + 1;
-            int u2 = positive(e.s2) ? o - 1 : o + 1;
-            double w10 = XW[o], w1n = XW[XE + o], w20 = XW[2 * XE + o], w2n = XW[3 * XE + o];
-            double p1 = mc_phi(w10, w1n, XW[u1], XW[XE + u1]);
-            double p2 = mc_phi(w20, w2n, XW[2 * XE + u2], XW[3 * XE + u2]);
-            double cf1 = corr_coef<EQN>(e.s1, dtdx), cf2 = corr_coef<EQN>(e.s2, dtdx);
-            XN[k] = half(cf1 * (p1 * w10) + cf2 * (p2 * w20));
-            XN[XNn + k] = half(cf1 * (p1 * w1n) + cf2 * (p2 * w2n));
-            smx = bmax(smx, maxabs(e.s1, e.s2));
+    }
+    __syncthreads();
+    for (int k = tid; k < tx + 3; k += kThreads) {    // edge ex = k-1 between staged cells k, k+1
+        int l = k, r = k + 1;
+        Edge e;
+        load_edge<EQN, 0>(sA, PX, l, r, e);
+        double d0, dn, w1[2], w2[2];
+        edge_jump<EQN>(e, sA, PX, l, r, sQ[l], sQ[PX + l], sQ[r], sQ[PX + r], d0, dn);
+        decompose<EQN>(e, d0, dn, w1, w2);
+        XW[k] = w1[0]; XW[XE + k] = w1[1]; XW[2 * XE + k] = w2[0]; XW[3 * XE + k] = w2[1];
+        if constexpr (EQN == 0) {
+            XF[k] = e.s1 * w1[0]; XF[XE + k] = e.s1 * w1[1];
+            XF[2 * XE + k] = e.s2 * w2[0]; XF[3 * XE + k] = e.s2 * w2[1];
+        } else {
+            XF[k] = w1[0]; XF[XE + k] = w1[1]; XF[2 * XE + k] = w2[0]; XF[3 * XE + k] = w2[1];
         }
-        if (smx > 0) cfl = bmax(cfl, dtdx * __longlong_as_double(smx));
-        __syncthreads();
-        for (int c = tid; c < tx; c += kThreads) {
-            int oL = c + 1, oR = c + 2;
-            double A0 = (XF[2 * XE + oL] + XF[oR]) + (XN[c + 1] - XN[c]);
-            double A1 = (XF[3 * XE + oL] + XF[XE + oR]) + (XN[XNn + c + 1] - XN[XNn + c]);
-            long long g = P.base + x0 + c + 2;
-            qn[g] = sQ[c + 2] - dtdx * A0;
-            qn[stride + g] = fma(-dtdx, A1, sQ[PX + c + 2]);
-            if (ga.rx.rmap) {
-                const int e = ga.rx.rmap[g];
-                if (e >= 0) {
-                    const RefluxCell rc = ga.rx.cells[e];
-                    for (int sd = 0; sd < 2; sd++) {
-                        if (rc.c[sd] < 0 && rc.f[sd] < 0) continue;
-                        const double a = sd == 0 ? XF[2 * XE + oL] - XN[c] : XF[oR] + XN[c + 1];
-                        const double b = sd == 0 ? XF[3 * XE + oL] - XN[XNn + c] : XF[XE + oR] + XN[XNn + c + 1];
-                        if (rc.c[sd] >= 0) {
-                            ga.rx.lc[2 * (long long)rc.c[sd]] = a;
-                            ga.rx.lc[2 * (long long)rc.c[sd] + 1] = b;
-                        }
-                        if (rc.f[sd] >= 0) {
-                            double *o = ga.rx.lf + ((long long)ga.rx.sub * ga.rx.nfrec + rc.f[sd]) * 4;
-                            o[0] = a;
-                            o[1] = b;
-                            o[2] = sQ[c + 2];
-                            o[3] = sQ[PX + c + 2];
-                        }
+    }
+    __syncthreads();
+    long long smx = 0;  // max |s| over this thread's edges (see the 2D kernel)
+    for (int k = tid; k < tx + 1; k += kThreads) {    // edge ex = k
+        int o = k + 1, l = k + 1, r = k + 2;
+        Edge e;
+        load_edge<EQN, 0>(sA, PX, l, r, e);
+        int u1 = positive(e.s1) ? o - 1 : o + 1;
+        int u2 = positive(e.s2) ? o - 1 : o + 1;
+        double w10 = XW[o], w1n = XW[XE + o], w20 = XW[2 * XE + o], w2n = XW[3 * XE + o];
+        double p1 = mc_phi(w10, w1n, XW[u1], XW[XE + u1]);
+        double p2 = mc_phi(w20, w2n, XW[2 * XE + u2], XW[3 * XE + u2]);
+        double cf1 = corr_coef<EQN>(e.s1, dtdx), cf2 = corr_coef<EQN>(e.s2, dtdx);
+        XN[k] = half(cf1 * (p1 * w10) + cf2 * (p2 * w20));
+        XN[XNn + k] = half(cf1 * (p1 * w1n) + cf2 * (p2 * w2n));
+        smx = bmax(smx, maxabs(e.s1, e.s2));
+    }
+    if (smx > 0) cfl = bmax(cfl, dtdx * __longlong_as_double(smx));
+    __syncthreads();
+    for (int c = tid; c < tx; c += kThreads) {
+        int oL = c + 1, oR = c + 2;
+        double A0 = (XF[2 * XE + oL] + XF[oR]) + (XN[c + 1] - XN[c]);
+        double A1 = (XF[3 * XE + oL] + XF[XE + oR]) + (XN[XNn + c + 1] - XN[XNn + c]);
+        long long g = P.base + x0 + c + 2;
+        qn[g] = sQ[c + 2] - dtdx * A0;
+        qn[stride + g] = fma(-dtdx, A1, sQ[PX + c + 2]);
+        if (ga.rx.rmap) {
+            const int e = ga.rx.rmap[g];
+            if (e >= 0) {
+                const RefluxCell rc = ga.rx.cells[e];
+                for (int sd = 0; sd < 2; sd++) {
+                    if (rc.c[sd] < 0 && rc.f[sd] < 0) continue;
+                    const double a = sd == 0 ? XF[2 * XE + oL] - XN[c] : XF[oR] + XN[c + 1];
+                    const double b = sd == 0 ? XF[3 * XE + oL] - XN[XNn + c] : XF[XE + oR] + XN[XNn + c + 1];
+                    if (rc.c[sd] >= 0) {
+                        ga.rx.lc[2 * (long long)rc.c[sd]] = a;
+                        ga.rx.lc[2 * (long long)rc.c[sd] + 1] = b;
+                    }
+                    if (rc.f[sd] >= 0) {
+                        double *o = ga.rx.lf + ((long long)ga.rx.sub * ga.rx.nfrec + rc.f[sd]) * 4;
+                        o[0] = a;
+                        o[1] = b;
+                        o[2] = sQ[c + 2];
+                        o[3] = sQ[PX + c + 2];
                     }
                 }
             }
         }
-        __syncthreads();
+    }
+    __syncthreads();
+}
+
+template <int EQN, int TX>
+__global__ void __launch_bounds__(kThreads) k_step1d(const double *__restrict__ q, double *__restrict__ qn,
+                                                     const double *__restrict__ aux, long long stride,
+                                                     const PatchDesc *__restrict__ patches,
+                                                     const WorkItem *__restrict__ work, int nwork,
+                                                     unsigned long long *cfl_bits, GhostArgs ga, TileSched sc)
+{
+    extern __shared__ double sm[];
+    long long cfl = 0;
+    __shared__ int s_next;
+    // one tile per CTA: its work-list entry is read before the wait (as in k_step2d)
+    const bool single = !sc.ctr && (long long)gridDim.x >= nwork;
+    WorkItem wi{};
+    if (single && (int)blockIdx.x < nwork) {
+        wi = work[blockIdx.x];
+        prefetch_l1(patches + wi.patch);
+    }
+    pdl_wait();
+    pdl_launch_dependents();
+    for (int w = fetch_tile(sc, &s_next, blockIdx.x); w < nwork; w = fetch_tile(sc, &s_next, w + gridDim.x)) {
+        if (!single) wi = work[w];
+        step1d_tile<EQN, TX>(q, qn, aux, stride, patches[wi.patch], wi, ga, sm, cfl);
+        if (single) break;
     }
     cfl_reduce(cfl, cfl_bits);
 }
