@@ -352,6 +352,36 @@ def test_regrid_invariants_in_hierarchy():
         assert fc.max(initial=0) <= 1
 
 
+@pytest.mark.parametrize("reflux", [0, 1])
+def test_a_second_regrid_at_one_state_changes_nothing(reflux):
+    """Regridding twice at the same state: the second regrid finds the boxes
+    the first made, and the new-patch initialisation (Sec. 3: a new fine cell
+    takes the old fine value where one exists) puts every value back where it
+    was, so every level's layout and state are unchanged bit for bit, and the
+    run continues exactly as without the second regrid."""
+    wl = W.config2(seed=3, n0=32, ratios=(2, 4), tf=2.0, adj_n=64, nsnap=20, ts=0.0, tol=1e-4, min_patch=8,
+                   max_patch=32)
+    wl.reflux = reflux
+    snaps = O.adjoint_solve(wl)
+    runs = []
+    for twice in (False, True):
+        h = O.OracleHierarchy(wl)
+        h.set_adjoint(snaps)
+        h.regrid(0, init=True)
+        h.advance(h.nsteps_total() // 3)
+        h.regrid(0)
+        before = [(h.patches(lev), h.read_level(lev)) for lev in range(wl.nlevels)]
+        assert len(before[1][0]) > 0 and len(before[2][0]) > 0
+        if twice:
+            h.regrid(0)
+            for lev, (p, q) in enumerate(before):
+                assert np.array_equal(h.patches(lev), p) and np.array_equal(h.read_level(lev), q), lev
+        h.advance(4)
+        runs.append(h)
+    _all_levels_equal(runs[0], runs[1], wl.nlevels)
+    assert runs[0].functional() == runs[1].functional()
+
+
 # ------------------------------------------------------ functional
 def test_functional_of_constant_field_on_composite_grid():
     """J of q0 = const over the composite grid is const * weight * |box|,
